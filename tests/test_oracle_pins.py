@@ -1,0 +1,372 @@
+"""Pins for the FP64 CPU oracle, against facts that do not come from the oracle.
+
+Each test names the passage of the paper whose arithmetic it fixes and what
+mistake it would catch.  None of these need a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import oracle as O
+from oracle import estimators as E
+from oracle import rademacher as R
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dense_logm_sym(A):
+    lam, U = np.linalg.eigh(A)
+    return (U * np.log(lam)) @ U.T
+
+
+# ---------------------------------------------------------------------------
+# Probe spec (Algorithms 2 and 3: Rademacher sketch and residual probes)
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_outputs():
+    want = [int(l, 16) for l in open(os.path.join(GOLDEN, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = [int(x) for x in R.splitmix64_sequence(0, 3)]
+    assert got == want
+
+
+def test_rademacher_entry_is_counter_output():
+    # Column c, row i of a stream is output number c*2^32 + i of the generator
+    # seeded with the stream key: for column 0 that is the plain sequence.
+    key = int(R.stream_key(7, 1))
+    seq = R.splitmix64_sequence(key, 50)
+    block = R.rademacher_block(7, 1, 50, 1)[:, 0]
+    assert np.array_equal(block, np.where((seq >> np.uint64(63)) == 0, 1.0, -1.0))
+
+
+def test_rademacher_statistics():
+    n, N = 32, 20000
+    G = R.rademacher_block(11, 1, n, N)
+    assert set(np.unique(G)) == {-1.0, 1.0}
+    assert abs(G.mean()) < 5.0 / math.sqrt(G.size)
+    C = G @ G.T / N                      # E[g g^T] = I
+    off = C - np.diag(np.diag(C))
+    assert np.allclose(np.diag(C), 1.0)
+    assert np.max(np.abs(off)) < 6.0 / math.sqrt(N)
+    # streams and seeds are different draws
+    assert not np.array_equal(R.rademacher_block(11, 0, n, 4), R.rademacher_block(11, 1, n, 4))
+    assert not np.array_equal(R.rademacher_block(11, 0, n, 4), R.rademacher_block(12, 0, n, 4))
+
+
+# ---------------------------------------------------------------------------
+# Spectral interval (Sec. 2.1, Gershgorin; clamp R3)
+# ---------------------------------------------------------------------------
+
+def test_gershgorin_closed_forms():
+    lo, hi = O.gershgorin_interval(W.laplacian_2d(9, shift=0.25).to_scipy())
+    assert lo == pytest.approx(0.25, abs=1e-14) and hi == pytest.approx(8.25, abs=1e-14)
+    lo, hi = O.gershgorin_interval(W.laplacian_3d(5, shift=0.5).to_scipy())
+    assert lo == pytest.approx(0.5, abs=1e-14) and hi == pytest.approx(12.5, abs=1e-14)
+    lo, hi = O.gershgorin_interval(W.matern_2d(8, 0.05).to_scipy())
+    assert lo == pytest.approx(0.05**2 + 8 * 0.05 + 16 + 4 - (8 * 4.05 + 12), abs=1e-12)
+    assert lo == pytest.approx(-23.9975, abs=1e-12) and hi == pytest.approx(64.8025, abs=1e-12)
+    G = W.powerlaw_graph_laplacian(3000, seed=1).with_diagonal_shift(0.03)
+    lo, hi = O.gershgorin_interval(G.to_scipy())
+    deg = np.diff(G.rowptr) - 1
+    assert lo == pytest.approx(0.03, abs=1e-12)
+    assert hi == pytest.approx(2 * deg.max() + 0.03, abs=1e-9)
+
+
+def test_gershgorin_brute_force_dense():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((12, 12))
+    A = A + A.T
+    Ad = np.abs(A)
+    R_ = Ad.sum(axis=1) - np.diag(Ad)
+    lo, hi = O.gershgorin_interval(sp.csr_matrix(A))
+    assert lo == pytest.approx(float(np.min(np.diag(A) - R_)), rel=1e-14)
+    assert hi == pytest.approx(float(np.max(np.diag(A) + R_)), rel=1e-14)
+
+
+def test_spectral_interval_clamp():
+    lo, hi = O.spectral_interval(W.matern_2d(8, 0.05).to_scipy())
+    assert hi == pytest.approx(64.8025) and lo == pytest.approx(1e-6 * 64.8025)
+    assert O.spectral_interval(None, lam=(0.5, 2.0)) == (0.5, 2.0)
+
+
+# ---------------------------------------------------------------------------
+# Lanczos + Gauss quadrature (Sec. 3.1, Eq. gauss_quadrature)
+# ---------------------------------------------------------------------------
+
+def test_gauss_quadrature_moment_exactness():
+    # An m-point Gauss rule integrates t^p exactly for p <= 2m-1:
+    # sum_k tau_k^2 theta_k^p = v^T J^p v / v^T v.  Catches wrong weights
+    # (tau instead of tau^2), a dropped beta or an off-by-one in T.
+    A = W.random_spd_dense_csr(40, seed=2, cond=50.0).to_scipy()
+    J = A / 50.0
+    v = np.random.default_rng(3).standard_normal(40)
+    m = 6
+    al, be = O.lanczos(J, v, m, reorth=True)
+    qd = O.gauss_quadrature_log(al, be)
+    Jd = J.toarray()
+    w = v / np.linalg.norm(v)
+    x = w.copy()
+    for p in range(2 * m):
+        want = float(w @ x)
+        got = float(np.sum(qd.tau2 * qd.theta ** p))
+        assert got == pytest.approx(want, rel=1e-10, abs=1e-13), p
+        x = Jd @ x
+
+
+def test_lanczos_full_dimension_equals_dense_log():
+    A = W.random_spd_dense_csr(30, seed=4, cond=30.0).to_scipy()
+    J = A / 31.0
+    v = np.random.default_rng(1).standard_normal(30)
+    al, be = O.lanczos(J, v, 30, reorth=True)
+    got = O.gauss_quadrature_log(al, be).value
+    w = v / np.linalg.norm(v)
+    want = float(w @ _dense_logm_sym(J.toarray()) @ w)
+    assert got == pytest.approx(want, rel=1e-11, abs=1e-12)
+
+
+def test_lanczos_identity_breaks_down_exactly():
+    Q = W.scaled_identity(25, 3.0).to_scipy()
+    al, be = O.lanczos(Q / 3.0, np.ones(25), 10)
+    assert al.size == 1 and be.size == 0 and al[0] == pytest.approx(1.0)
+    est = O.oslq(Q, 9, 10, seed=0)
+    assert est.logdet == pytest.approx(25 * math.log(3.0), rel=1e-14)
+
+
+def test_lanczos_diagonal_exact_at_distinct_count():
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 7.0], 10)
+    Q = W.diagonal_matrix(d).to_scipy()
+    v = np.random.default_rng(9).standard_normal(d.size)
+    al, be = O.lanczos(Q, v, 5)
+    got = O.gauss_quadrature_log(al, be).value
+    w = v / np.linalg.norm(v)
+    assert got == pytest.approx(float(np.sum(w**2 * np.log(d))), rel=1e-12)
+
+
+def test_lanczos_recurrence_residual():
+    # Without re-orthogonalisation the three-term relation J V_m = V_m T_m +
+    # beta_m v_{m+1} e_m^T still holds to rounding.  Rebuilt here from alpha, beta.
+    Q = W.laplacian_2d(10, shift=0.2).to_scipy()
+    J = Q / 8.2
+    v = np.random.default_rng(0).standard_normal(100)
+    m = 12
+    al, be = O.lanczos(J, v, m + 1)
+    V = [v / np.linalg.norm(v)]
+    vp = np.zeros(100)
+    for j in range(m):
+        w = J @ V[j] - al[j] * V[j] - (be[j - 1] * vp if j else 0)
+        vp = V[j]
+        V.append(w / be[j])
+    Vm = np.stack(V[:m], 1)
+    T = np.diag(al[:m]) + np.diag(be[:m - 1], 1) + np.diag(be[:m - 1], -1)
+    res = J @ Vm - Vm @ T
+    res[:, -1] -= be[m - 1] * V[m]
+    assert np.max(np.abs(res)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 (Arnoldi-IOP-LOG)
+# ---------------------------------------------------------------------------
+
+def test_iop_full_window_is_arnoldi():
+    # k = m: each column orthogonalised against all previous ones (MGS
+    # Arnoldi), so V is orthonormal and H = V^T Q~ V, Arnoldi relation exact.
+    A = W.random_spd_dense_csr(60, seed=6, cond=100.0).to_scipy() / 10.0
+    v = np.random.default_rng(2).standard_normal(60)
+    run = O.arnoldi_iop(A, v, 15, k=15)
+    V, H = run.V, run.H
+    assert np.max(np.abs(V.T @ V - np.eye(15))) < 1e-12
+    assert np.max(np.abs(V.T @ (A @ V) - H)) < 1e-12
+    assert np.max(np.abs(np.tril(H, -2))) == 0.0
+
+
+def test_iop_window_two_matches_lanczos():
+    # For symmetric Q and k = 2, IOP is Lanczos: H is tridiagonal with
+    # diag = alpha_j and subdiag = beta_j (independent code: lanczos()).
+    Q = W.laplacian_2d(12, shift=0.3).to_scipy() / 3.0
+    v = np.random.default_rng(4).standard_normal(Q.shape[0])
+    run = O.arnoldi_iop(Q, v, 10, k=2)
+    al, be = O.lanczos(Q, v, 11)
+    assert np.allclose(np.diag(run.H), al[:10], rtol=1e-12, atol=1e-13)
+    assert np.allclose(np.diag(run.H, -1), be[:9], rtol=1e-12)
+    assert np.allclose(np.diag(run.H, 1), be[:9], rtol=1e-9)
+    assert np.max(np.abs(np.triu(run.H, 2))) == 0.0
+
+
+def test_iop_log_action_full_dimension_is_dense_logm():
+    A = W.random_spd_dense_csr(20, seed=8, cond=40.0).to_scipy()
+    lo, hi = float(np.linalg.eigvalsh(A.toarray())[0]), float(np.linalg.eigvalsh(A.toarray())[-1])
+    gamma = math.sqrt(lo * hi)
+    v = np.random.default_rng(5).standard_normal(20)
+    y = O.iop_log_action(A / gamma, v, 20, 20, math.log(gamma))
+    want = sla.logm(A.toarray()).real @ v
+    assert np.allclose(y, want, rtol=1e-9, atol=1e-10)
+
+
+def test_iop_logm_inverts_expm():
+    Q = W.laplacian_2d(8, shift=0.5).to_scipy() / 3.0
+    run = O.arnoldi_iop(Q, np.ones(64), 12, k=4)
+    L = sla.logm(run.H)
+    assert np.allclose(sla.expm(L), run.H, atol=1e-12)
+
+
+def test_iop_tol_break_keeps_column():
+    # Q~ = I: w = v_1 - (v_1^T v_1) v_1 = 0 at m = 1, so m_eff = 1 and H = [[1]].
+    run = O.arnoldi_iop(sp.identity(10, format="csr"), np.ones(10), 5, k=2)
+    assert run.m_eff == 1 and run.H.shape == (1, 1) and run.H[0, 0] == pytest.approx(1.0)
+
+
+# ---------------------------------------------------------------------------
+# Hutch++ split (Algorithms 2/3) and the assembly n log(alpha) + tr
+# ---------------------------------------------------------------------------
+
+def test_orth_properties():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((50, 6))
+    A = O.orth(Y)
+    assert np.allclose(A.T @ A, np.eye(6), atol=1e-14)
+    assert np.allclose(A @ (A.T @ Y), Y, atol=1e-12)
+    Y2 = np.concatenate([Y, Y[:, :2] @ np.array([[1.0], [2.0]])], axis=1)
+    assert O.orth(Y2).shape[1] == 6
+
+
+def _hadamard(n):
+    H = np.array([[1.0]])
+    while H.shape[0] < n:
+        H = np.block([[H, H], [H, -H]])
+    return H
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_exact_with_hadamard_residual_probes(method):
+    # With G a Hadamard matrix, (1/r) sum_j g_j g_j^T = I exactly, so the
+    # residual term equals tr((I-P) L (I-P)); with m = n the Krylov parts are
+    # exact too, hence the estimate is the exact log-determinant.  This pins
+    # the 1/r weight, the ||z||^2 factor, the projection, n log(alpha) and,
+    # for OSA-IOP, the log(gamma/alpha) shift.
+    A = W.laplacian_2d(4, shift=0.5).to_scipy()
+    n = 16
+    S = O.rademacher_block(3, 0, n, 3)
+    G = _hadamard(n)
+    exact = np.linalg.slogdet(A.toarray())[1]
+    if method == "oslq":
+        est = O.oslq(A, 0 + 3 * 3, n, S=S, G=G, reorth=True)
+    else:
+        est = O.osaiop(A, 9, n, k=n, S=S, G=G)
+    assert est.r == n
+    assert est.logdet == pytest.approx(exact, rel=1e-10)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_full_sketch_recovers_exact(method):
+    # s >= n: A spans R^n, every z_j = 0 and the subspace part is the trace.
+    Q = W.laplacian_2d(3, shift=1.0).to_scipy()
+    n = 9
+    exact = np.linalg.slogdet(Q.toarray())[1]
+    if method == "oslq":
+        est = O.oslq(Q, 3 * n + 2, n, seed=1, reorth=True)
+    else:
+        est = O.osaiop(Q, 3 * n + 2, n, k=n, seed=1)
+    assert est.s_eff == n
+    assert np.allclose(est.z_norm2, 0.0, atol=1e-20)
+    assert est.logdet == pytest.approx(exact, rel=1e-10)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_scale_invariance(method):
+    # log det(cQ) = log det Q + n log c with the same probes: alpha and gamma
+    # scale with c, the scaled operators do not change.
+    Q = W.laplacian_2d(10, shift=0.2).to_scipy()
+    c = 7.5
+    f = (lambda M: O.oslq(M, 9, 15, seed=2)) if method == "oslq" else \
+        (lambda M: O.osaiop(M, 9, 15, k=2, seed=2))
+    a, b = f(Q), f(c * Q)
+    assert b.logdet - a.logdet == pytest.approx(100 * math.log(c), rel=1e-11)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_permutation_invariance(method):
+    A = W.laplacian_2d(7, shift=0.4)
+    n = A.n
+    perm = np.random.default_rng(3).permutation(n)
+    Ap = W.permute_symmetric(A, perm)
+    S = O.rademacher_block(1, 0, n, 3)
+    G = O.rademacher_block(1, 1, n, 4)
+    f = O.oslq if method == "oslq" else (lambda *a, **k: O.osaiop(*a, k=2, **k))
+    e1 = f(A.to_scipy(), 10, 12, S=S, G=G)
+    e2 = f(Ap.to_scipy(), 10, 12, S=S[perm], G=G[perm])
+    assert e2.logdet == pytest.approx(e1.logdet, rel=1e-12)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_unbiased_against_closed_form(method):
+    # Hutch++ is unbiased; with m = 20 on a 12x12 grid the quadrature error is
+    # negligible, so the mean over seeds must match the analytic log-det.
+    Q = W.laplacian_2d(12, shift=0.3).to_scipy()
+    exact = W.closed_form_logdet_laplacian_2d(12, shift=0.3)
+    f = (lambda s: O.oslq(Q, 9, 20, seed=s)) if method == "oslq" else \
+        (lambda s: O.osaiop(Q, 9, 20, k=2, seed=s))
+    vals = np.array([f(s).logdet for s in range(200)])
+    se = vals.std(ddof=1) / math.sqrt(vals.size)
+    assert abs(vals.mean() - exact) < 4 * se + 1e-9 * abs(exact)
+
+
+def test_config1_closed_form_and_band():
+    A = W.laplacian_2d(64, shift=0.1)
+    exact = W.closed_form_logdet_laplacian_2d(64, shift=0.1)
+    assert exact == pytest.approx(5018.309092513560, rel=1e-13)
+    assert exact == pytest.approx(np.linalg.slogdet(A.to_scipy().toarray())[1], rel=1e-12)
+    est = O.oslq(A.to_scipy(), 30, 30, seed=0)
+    assert abs(est.logdet - exact) / exact < 1e-2
+
+
+def test_dense_cholesky_band():
+    A = W.laplacian_3d(11, shift=0.05).to_scipy()
+    exact = 2 * np.sum(np.log(np.diag(np.linalg.cholesky(A.toarray()))))
+    for est in (O.oslq(A, 30, 40, seed=4), O.osaiop(A, 30, 40, k=4, seed=4)):
+        assert abs(est.logdet - exact) / abs(exact) < 1e-2
+
+
+def test_rounding_sensitivity_supports_1e10_tolerance():
+    # Two summation orders (BLAS dot versus correctly rounded fsum) must agree
+    # far inside the 1e-10 parity tolerance on the 64x64 FP64 workload.
+    Q = W.laplacian_2d(64, shift=0.1).to_scipy()
+    a = O.oslq(Q, 30, 30, seed=0)
+    b = O.oslq(Q, 30, 30, seed=0, dot="fsum")
+    assert abs(a.logdet - b.logdet) / abs(a.logdet) < 1e-12
+    c = O.osaiop(Q, 12, 20, k=2, seed=0)
+    d = O.osaiop(Q, 12, 20, k=2, seed=0, dot="fsum")
+    assert abs(c.logdet - d.logdet) / abs(c.logdet) < 1e-12
+
+
+def test_mgs_window_versus_classical_gram_schmidt():
+    # Reading R5 fixes MGS order; a one-pass (classical) window differs only by
+    # rounding on these operators.  Implemented inline from Algorithm 1 with the
+    # window dots taken before any subtraction.
+    Q = W.laplacian_3d(12, shift=0.01).to_scipy()
+    lo, hi = O.spectral_interval(Q)
+    gamma = math.sqrt(lo * hi)
+    Qt = Q / gamma
+    v = O.rademacher_block(0, 0, Q.shape[0], 1)[:, 0]
+    for k in (2, 4, 8):
+        run = O.arnoldi_iop(Qt, v, 30, k=k)
+        V = [v / np.linalg.norm(v)]
+        Hc = np.zeros((31, 30))
+        for m in range(30):
+            w = Qt @ V[m]
+            js = range(max(0, m - k + 1), m + 1)
+            c = [float(V[j] @ w) for j in js]
+            for j, cj in zip(js, c):
+                Hc[j, m] = cj
+                w = w - cj * V[j]
+            h = np.linalg.norm(w)
+            Hc[m + 1, m] = h
+            V.append(w / h)
+        c1, _ = E.principal_logm_e1(run.H)
+        c2, _ = E.principal_logm_e1(Hc[:30, :30])
+        assert np.max(np.abs(c1 - c2)) < 1e-11

@@ -1,0 +1,72 @@
+"""The synthetic inputs: structure, sizes and analytic log-determinants."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _check_csr(A):
+    assert A.rowptr.dtype == np.int32 and A.colind.dtype == np.int32
+    assert A.rowptr[0] == 0 and np.all(np.diff(A.rowptr) >= 1)
+    S = A.to_scipy()
+    assert abs(S - S.T).max() == 0.0
+    for i in range(0, A.n, max(1, A.n // 97)):
+        cols = A.colind[A.rowptr[i]:A.rowptr[i + 1]]
+        assert np.all(np.diff(cols) > 0)
+        assert i in cols
+
+
+def test_sizes_of_the_named_workloads():
+    A = W.laplacian_2d(64, shift=0.1)
+    assert (A.n, A.nnz) == (4096, 20224)
+    B = W.laplacian_3d(128, shift=0.01)
+    assert (B.n, B.nnz) == (2097152, 14581760)
+    _check_csr(A)
+
+
+@pytest.mark.parametrize("maker,closed", [
+    (lambda: W.laplacian_2d(9, 7, shift=0.3), lambda: W.closed_form_logdet_laplacian_2d(9, 7, 0.3)),
+    (lambda: W.laplacian_3d(5, 4, 6, shift=0.02), lambda: W.closed_form_logdet_laplacian_3d(5, 4, 6, 0.02)),
+    (lambda: W.matern_2d(9, 0.05), lambda: W.closed_form_logdet_matern_2d(9, 0.05)),
+])
+def test_closed_forms_match_dense(maker, closed):
+    A = maker()
+    _check_csr(A)
+    dense = np.linalg.slogdet(A.to_scipy().toarray())
+    assert dense[0] > 0
+    assert dense[1] == pytest.approx(closed(), rel=1e-12)
+
+
+def test_laplacian_3d_matches_kronecker_form():
+    import scipy.sparse as sp
+    N = 6
+    L1 = sp.diags([-np.ones(N - 1), 2 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1])
+    I = sp.eye(N)
+    K = sp.kron(sp.kron(I, I), L1) + sp.kron(sp.kron(I, L1), I) + sp.kron(sp.kron(L1, I), I)
+    A = W.laplacian_3d(N, shift=0.0)
+    assert abs(A.to_scipy() - K).max() == 0.0
+
+
+def test_matern_stencil_is_13_point():
+    A = W.matern_2d(16, 0.05)
+    counts = np.diff(A.rowptr)
+    assert counts.max() == 13
+    mid = 8 * 16 + 8
+    assert counts[mid] == 13
+
+
+def test_powerlaw_graph():
+    G = W.powerlaw_graph_laplacian(20000, seed=3)
+    _check_csr(G)
+    S = G.to_scipy()
+    assert np.allclose(S @ np.ones(G.n), 0.0)          # Laplacian rows sum to zero
+    deg = np.diff(G.rowptr) - 1
+    assert 5.0 < deg.mean() < 9.0                      # mean degree ~8 after merging
+    assert deg.max() > 20 * deg.mean()                 # heavy tail
+    G2 = W.powerlaw_graph_laplacian(20000, seed=3)
+    assert np.array_equal(G.colind, G2.colind)         # seeded
+
+
+def test_diagonal_shift():
+    A = W.laplacian_2d(5).with_diagonal_shift(0.5)
+    assert np.allclose(A.to_scipy().diagonal(), 4.5)

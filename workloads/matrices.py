@@ -1,0 +1,252 @@
+"""Synthetic sparse SPD matrices in CSR form.
+
+Every generator returns a :class:`CSR` with int32 ``rowptr``/``colind``,
+columns sorted within each row, no duplicates and an explicit diagonal entry
+in every row.  Grid operators use lexicographic ordering with x fastest and
+Dirichlet boundaries; the stencils are the unscaled integer ones (2D: 4 on the
+diagonal, -1 to each neighbour; 3D: 6 and -1).
+
+These stand in for the paper's sparse test matrices (Sec. 4, Table 1), which
+are not shipped: shifted 2D/3D Laplacians (structured FEM/FD-like operators),
+an SPDE-style Matern precision ``(kappa^2 I + L)^2`` (the GRF workload of
+Sec. 4), and a Chung-Lu power-law graph Laplacian (irregular sparsity).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in compressed-sparse-row form (host arrays)."""
+
+    n: int
+    rowptr: np.ndarray  # int32, n+1
+    colind: np.ndarray  # int32, nnz
+    vals: np.ndarray    # float64 or float32, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_scipy(self, dtype=np.float64) -> sp.csr_matrix:
+        return sp.csr_matrix(
+            (self.vals.astype(dtype, copy=False), self.colind, self.rowptr),
+            shape=(self.n, self.n),
+        )
+
+    def astype(self, dtype) -> "CSR":
+        return CSR(self.n, self.rowptr, self.colind, self.vals.astype(dtype))
+
+    def with_diagonal_shift(self, shift: float) -> "CSR":
+        """Return Q + shift*I (diagonal entries are present by construction)."""
+        vals = self.vals.copy()
+        rows = np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.rowptr))
+        diag = self.colind.astype(np.int64) == rows
+        vals[diag] += vals.dtype.type(shift)
+        return CSR(self.n, self.rowptr, self.colind, vals)
+
+
+def _from_scipy(A: sp.spmatrix, dtype=np.float64) -> CSR:
+    A = sp.csr_matrix(A)
+    A.sum_duplicates()
+    A.sort_indices()
+    n = A.shape[0]
+    # Make sure every diagonal entry is stored (explicit zero if absent).
+    d = A.diagonal()
+    missing = np.flatnonzero(np.asarray(
+        (A != 0).multiply(sp.eye(n, format="csr")).sum(axis=1)).ravel() == 0)
+    if missing.size:
+        A = A + sp.csr_matrix((np.zeros(missing.size), (missing, missing)), shape=(n, n))
+        A = sp.csr_matrix(A)
+        A.sort_indices()
+    del d
+    if A.nnz >= 2**31:
+        raise ValueError("nnz does not fit int32 CSR indices")
+    return CSR(
+        n,
+        A.indptr.astype(np.int32),
+        A.indices.astype(np.int32),
+        A.data.astype(dtype),
+    )
+
+
+def _lap1d(N: int) -> sp.csr_matrix:
+    return sp.diags([-np.ones(N - 1), 2 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1], format="csr")
+
+
+def laplacian_2d(nx: int, ny: int | None = None, shift: float = 0.0, dtype=np.float64) -> CSR:
+    """5-point Dirichlet Laplacian on an nx x ny grid, plus shift*I."""
+    ny = nx if ny is None else ny
+    L = sp.kron(sp.eye(ny), _lap1d(nx)) + sp.kron(_lap1d(ny), sp.eye(nx))
+    L = L + shift * sp.eye(nx * ny)
+    return _from_scipy(L, dtype)
+
+
+def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None,
+                 shift: float = 0.0, dtype=np.float64) -> CSR:
+    """7-point Dirichlet Laplacian on an nx x ny x nz grid, plus shift*I.
+
+    Built directly (not through Kronecker products) so that the 2M-row case
+    is produced in about a second.
+    """
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    x = idx % nx
+    y = (idx // nx) % ny
+    z = idx // (nx * ny)
+    # Column offsets in sorted order: -nx*ny, -nx, -1, 0, +1, +nx, +nx*ny.
+    offs = [-nx * ny, -nx, -1, 0, 1, nx, nx * ny]
+    valid = [z > 0, y > 0, x > 0, np.ones(n, bool), x < nx - 1, y < ny - 1, z < nz - 1]
+    counts = np.zeros(n, dtype=np.int64)
+    for v in valid:
+        counts += v
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    colind = np.empty(nnz, dtype=np.int32)
+    vals = np.empty(nnz, dtype=np.float64)
+    pos = rowptr[:-1].copy()
+    diag_val = 6.0 + shift
+    for off, v in zip(offs, valid):
+        rows = idx[v]
+        p = pos[v]
+        colind[p] = (rows + off).astype(np.int32)
+        vals[p] = diag_val if off == 0 else -1.0
+        pos[v] += 1
+    return CSR(n, rowptr.astype(np.int32), colind, vals.astype(dtype))
+
+
+def matern_2d(N: int, kappa2: float, dtype=np.float64) -> CSR:
+    """SPDE-style Matern precision Q = M @ M with M = kappa2*I + L_2D (N x N grid).
+
+    In the interior this is the 13-point stencil.  The product is formed in
+    FP64 and cast at the end.
+    """
+    M = sp.kron(sp.eye(N), _lap1d(N)) + sp.kron(_lap1d(N), sp.eye(N)) + kappa2 * sp.eye(N * N)
+    M = sp.csr_matrix(M)
+    Q = M @ M
+    return _from_scipy(Q, dtype)
+
+
+def powerlaw_graph_laplacian(n: int, exponent: float = 2.3, mean_degree: float = 8.0,
+                             seed: int = 0, dtype=np.float64) -> CSR:
+    """Chung-Lu random graph Laplacian L = D - A (unit weights, no self loops).
+
+    Expected degrees follow w_i proportional to (i + i0)^(-1/(exponent-1)),
+    scaled to the requested mean; i0 is chosen so the largest expected degree
+    is sqrt(n * mean_degree), the usual Chung-Lu admissibility cap.  Edges are
+    drawn as n*mean/2 independent endpoint pairs with probability w_i/sum(w);
+    duplicates are merged and self loops dropped.  The result is singular
+    (constant null vector): add a diagonal shift before use.
+    """
+    rng = np.random.default_rng(seed)
+    g = 1.0 / (exponent - 1.0)
+    target_max = math.sqrt(n * mean_degree)
+    i = np.arange(n, dtype=np.float64)
+
+    def max_over_mean(i0):
+        w = (i + i0) ** (-g)
+        return w[0] / w.mean()
+
+    lo, hi = 0.0, float(n)
+    want = target_max / mean_degree
+    for _ in range(100):  # max/mean decreases as i0 grows
+        mid = 0.5 * (lo + hi)
+        if max_over_mean(mid) > want:
+            lo = mid
+        else:
+            hi = mid
+    w = (i + hi) ** (-g)
+    w *= mean_degree / w.mean()
+    p = w / w.sum()
+    cdf = np.cumsum(p)
+    cdf[-1] = 1.0
+    m_edges = int(round(n * mean_degree / 2))
+    u = np.searchsorted(cdf, rng.random(m_edges), side="right").astype(np.int64)
+    v = np.searchsorted(cdf, rng.random(m_edges), side="right").astype(np.int64)
+    np.minimum(u, n - 1, out=u)
+    np.minimum(v, n - 1, out=v)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    keys = np.unique(np.concatenate([u * n + v, v * n + u]))
+    rows = keys // n
+    cols = keys % n
+    deg = np.bincount(rows, minlength=n).astype(np.float64)
+    # Assemble with the diagonal in its sorted position.
+    all_rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
+    all_cols = np.concatenate([cols, np.arange(n, dtype=np.int64)])
+    all_vals = np.concatenate([-np.ones(rows.size), deg])
+    order = np.lexsort((all_cols, all_rows))
+    all_rows, all_cols, all_vals = all_rows[order], all_cols[order], all_vals[order]
+    counts = np.bincount(all_rows, minlength=n)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz does not fit int32 CSR indices")
+    return CSR(n, rowptr.astype(np.int32), all_cols.astype(np.int32), all_vals.astype(dtype))
+
+
+def diagonal_matrix(d, dtype=np.float64) -> CSR:
+    d = np.asarray(d, dtype=np.float64)
+    n = d.size
+    return CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d.astype(dtype))
+
+
+def scaled_identity(n: int, c: float, dtype=np.float64) -> CSR:
+    return diagonal_matrix(np.full(n, c), dtype)
+
+
+def random_spd_dense_csr(n: int, seed: int, cond: float = 100.0, dtype=np.float64) -> CSR:
+    """Dense random SPD matrix with eigenvalues log-spaced in [1, cond], stored as CSR."""
+    rng = np.random.default_rng(seed)
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.logspace(0.0, math.log10(cond), n)
+    A = (Qm * lam) @ Qm.T
+    A = 0.5 * (A + A.T)
+    return _from_scipy(sp.csr_matrix(A), dtype)
+
+
+def permute_symmetric(A: CSR, perm: np.ndarray) -> CSR:
+    """Return P A P^T where row i of the result is row perm[i] of A."""
+    S = A.to_scipy()
+    P = S[perm][:, perm]
+    return _from_scipy(P, A.vals.dtype)
+
+
+# ---------------------------------------------------------------------------
+# Closed-form log-determinants from analytic Dirichlet eigenvalues.
+# ---------------------------------------------------------------------------
+
+def _lap1d_eigs(N: int) -> np.ndarray:
+    k = np.arange(1, N + 1, dtype=np.float64)
+    return 2.0 - 2.0 * np.cos(k * math.pi / (N + 1))
+
+
+def closed_form_logdet_laplacian_2d(nx: int, ny: int | None = None, shift: float = 0.0) -> float:
+    ny = nx if ny is None else ny
+    ex, ey = _lap1d_eigs(nx), _lap1d_eigs(ny)
+    return float(math.fsum(np.log(ex[None, :] + ey[:, None] + shift).ravel()))
+
+
+def closed_form_logdet_laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None,
+                                    shift: float = 0.0) -> float:
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    ex, ey, ez = _lap1d_eigs(nx), _lap1d_eigs(ny), _lap1d_eigs(nz)
+    total = []
+    for z in ez:
+        total.append(math.fsum(np.log(ex[None, :] + ey[:, None] + z + shift).ravel()))
+    return float(math.fsum(total))
+
+
+def closed_form_logdet_matern_2d(N: int, kappa2: float) -> float:
+    e = _lap1d_eigs(N)
+    mu = e[None, :] + e[:, None]
+    return float(math.fsum((2.0 * np.log(kappa2 + mu)).ravel()))
