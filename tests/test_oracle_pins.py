@@ -370,3 +370,18 @@ def test_mgs_window_versus_classical_gram_schmidt():
         c1, _ = E.principal_logm_e1(run.H)
         c2, _ = E.principal_logm_e1(Hc[:30, :30])
         assert np.max(np.abs(c1 - c2)) < 1e-11
+
+
+def test_scaling_makes_log_operator_semidefinite():
+    # Sec. 3.2: with alpha = lambda_max bound, J = Q/alpha has spectrum in
+    # (0, 1], so every quadrature K(q) = q^T log(J) q is <= 0.  Sec. 2.2: with
+    # alpha = lambda_min bound, L = log(Q/alpha) is PSD, so every q^T L q >= 0.
+    # A wide spectrum (kappa ~ 1e3) makes any other alpha produce both signs.
+    Q = W.laplacian_2d(20, shift=0.01).to_scipy()
+    a = O.oslq(Q, 30, 25, seed=5)
+    assert np.all(a.per_probe <= 0.0)
+    lo, hi = O.gershgorin_interval(Q)
+    assert a.log_alpha == pytest.approx(math.log(hi), rel=1e-15)
+    b = O.osaiop(Q, 30, 25, k=2, seed=5)
+    assert np.all(b.per_probe >= 0.0)
+    assert b.log_alpha == pytest.approx(math.log(lo), rel=1e-15)
