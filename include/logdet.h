@@ -1,0 +1,200 @@
+/*
+ * liblogdet: GB300 (sm_103a) log-determinant estimation for large sparse SPD
+ * matrices by OSLQ and OSA-IOP (Mbingui, Tambue, Karambal, arXiv 2606.07004).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Return value: 0 (LOGDET_OK) on success, LOGDET_PENDING (> 0) for a
+ *   request still in flight, a negative LOGDET_E* code on error.
+ *   logdet_strerror() names a code; logdet_last_error() gives the detail of
+ *   the calling thread's most recent failure.
+ * - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *   global memory on the handle's device.  Sizes are element counts.
+ * - Dense blocks are row-major: entry (row i, column p) of an n x b block
+ *   with leading dimension ld (ld >= b) is at index i*ld + p.
+ * - CSR input: rowptr[n+1] (int32, rowptr[0] = 0, non-decreasing),
+ *   colind[nnz] (int32, strictly increasing within a row, in [0, n)),
+ *   vals[nnz]; every row must store its diagonal entry.  The matrix must be
+ *   symmetric; symmetry is the caller's promise and is not checked.
+ * - Numerical events that do not stop a solve (Krylov breakdown, a
+ *   non-positive Ritz value, a rank-deficient sketch) are reported in
+ *   logdet_result.status_bits, not as errors.
+ * - All entry points are thread-safe for distinct handles.  A handle must
+ *   not be used by two threads at once.
+ */
+#ifndef LOGDET_H
+#define LOGDET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ------------------------------------------------------ */
+#define LOGDET_OK        0
+#define LOGDET_PENDING   1
+#define LOGDET_EINVAL   (-1)  /* bad argument or malformed CSR */
+#define LOGDET_ENOMEM   (-2)  /* device allocation failed or over budget */
+#define LOGDET_ENOTSPD  (-3)  /* spectral bounds show the matrix is not SPD */
+#define LOGDET_ETIMEOUT (-4)  /* a bounded device wait or a host wait expired */
+#define LOGDET_ECUDA    (-5)  /* a CUDA runtime call failed */
+#define LOGDET_ENOENT   (-6)  /* unknown request id */
+#define LOGDET_ECANCEL  (-7)  /* request cancelled */
+
+/* ---- enums ------------------------------------------------------------- */
+#define LOGDET_VALS_F64  0
+#define LOGDET_VALS_F32  1
+
+#define LOGDET_FP64        0  /* everything in IEEE binary64 */
+#define LOGDET_MIXED_FP32  1  /* FP32 values and vectors, compensated FP32 dots,
+                                 FP64 Hutch++ QR and small solves */
+
+#define LOGDET_METHOD_OSLQ    0
+#define LOGDET_METHOD_OSAIOP  1
+
+/* status_bits */
+#define LOGDET_ST_BREAKDOWN      0x1u  /* a probe's Krylov run stopped at h < tol */
+#define LOGDET_ST_NONPOS_RITZ    0x2u  /* a Ritz value <= 0 was clamped */
+#define LOGDET_ST_RANK_DEFICIENT 0x4u  /* the sketch Y lost rank; columns dropped */
+#define LOGDET_ST_LOG_FAILED     0x8u  /* log(H_m) did not converge for a probe */
+
+typedef struct logdet_ctx* logdet_handle;
+
+typedef struct {
+  double logdet;     /* the estimate of log det Q */
+  double tr_sub;     /* deterministic subspace term sum_i q_i^T f q_i */
+  double tr_res;     /* residual term (1/r) sum_j z_j^T f z_j */
+  double log_alpha;  /* log of the scale alpha: n*log_alpha + tr_sub + tr_res = logdet */
+  double log_gamma;  /* OSA-IOP shift-scale log(gamma); 0 for OSLQ */
+  int32_t s;         /* sketch columns floor(num_probes/3) */
+  int32_t r;         /* residual probes num_probes - 2s */
+  int32_t s_eff;     /* sketch rank kept after the QR */
+  int32_t steps_min; /* smallest Krylov dimension reached over the probes */
+  int32_t steps_max; /* largest */
+  uint32_t status_bits;
+  double device_ms;  /* device time of the solve (CUDA events) */
+} logdet_result;
+
+typedef struct {
+  int32_t precision;   /* LOGDET_FP64 (default) or LOGDET_MIXED_FP32 */
+  double tol;          /* breakdown threshold on h_{m+1,m} / beta_j; 0 = 1e-12 */
+  double lambda_lo;    /* spectral bounds; both 0 = clamped Gershgorin interval */
+  double lambda_hi;
+  int32_t block_width; /* reserved (0) */
+  double* per_probe;   /* optional host out, length s+r: subspace forms q_i^T f q_i
+                          (i < s) then normalised residual forms K(z_j/|z_j|) */
+  double* z_norm2;     /* optional host out, length r: |z_j|^2 */
+  void* stream;        /* optional cudaStream_t for this call; NULL = handle's */
+} logdet_opts;
+
+/* Fill an opts struct with the defaults. */
+void logdet_opts_default(logdet_opts* opts);
+
+const char* logdet_strerror(int code);
+const char* logdet_last_error(void);
+
+/* ---- matrix handle -----------------------------------------------------
+ * logdet_create: copies a host CSR matrix to the current CUDA device,
+ * validates it (Sec. 2, "Q symmetric positive definite"; structural checks
+ * only) and computes its Gershgorin interval (Sec. 2.1, the spectral interval
+ * used by both estimators).  vals_dtype is LOGDET_VALS_F64 or _F32.  The
+ * caller may free its arrays on return.  Errors: EINVAL (n < 1, bad rowptr,
+ * column out of range or unsorted or duplicated, missing diagonal, NaN),
+ * ENOTSPD (Gershgorin upper bound <= 0), ENOMEM, ECUDA.
+ */
+int logdet_create(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                  const void* vals, int32_t vals_dtype, logdet_handle* out);
+
+/* Same, but the three arrays are device pointers that the handle borrows:
+ * they must stay valid and unchanged until logdet_destroy.  Validation runs
+ * on the device. */
+int logdet_create_device(int32_t n, const int32_t* rowptr_dev, const int32_t* colind_dev,
+                         const void* vals_dev, int32_t vals_dtype, logdet_handle* out);
+
+void logdet_destroy(logdet_handle h);
+
+/* n, nnz and the Gershgorin interval [lo, hi] (unclamped) of the handle. */
+int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* gersh_lo, double* gersh_hi);
+
+/* ---- estimators --------------------------------------------------------
+ * logdet_oslq: Algorithm 3 (OSLQ, Sec. 3): J = Q/alpha with alpha the upper
+ * spectral bound; s = floor(num_probes/3) Rademacher sketch columns give
+ * Y = J S and A = orth(Y); each column of A and each projected residual probe
+ * z_j = (I - A A^T) g_j (r = num_probes - 2s of them) runs krylov_steps
+ * Lanczos steps and the Gauss quadrature sum_k tau_k^2 log(theta_k) of
+ * Sec. 3.1.  log det = n log(alpha) + tr_sub + (1/r) sum_j |z_j|^2 K(z_j).
+ * iop_window must be 0 or 2 (three-term Lanczos).  Probes are the
+ * SplitMix64 Rademacher entries of (seed, stream 0 = S, 1 = G).
+ * Blocks until the result is on the host.  Errors: EINVAL (num_probes < 3,
+ * krylov_steps < 1 or > n, bad window), ENOTSPD, ENOMEM, ECUDA.
+ */
+int logdet_oslq(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
+                int32_t iop_window, uint64_t seed, const logdet_opts* opts,
+                logdet_result* out);
+
+/* logdet_osaiop: Algorithm 2 (OSA-IOP, Sec. 2.2) with each action of
+ * L = log(Q/gamma) + log(gamma/alpha) I computed by Algorithm 1
+ * (Arnoldi-IOP-LOG, Sec. 2.1): gamma = sqrt(lambda_lo lambda_hi), alpha =
+ * lambda_lo, incomplete orthogonalisation against the last iop_window basis
+ * vectors (iop_window = 2 is the paper's length-2 IOP; iop_window >=
+ * krylov_steps is full Arnoldi), log(H_m) e_1 of the small Hessenberg
+ * matrix.  Y = L S, A = orth(Y), tr_sub = sum_i a_i^T L a_i,
+ * tr_res = (1/r) sum_j z_j^T L z_j, log det = n log(alpha) + tr_sub + tr_res.
+ * Errors as logdet_oslq; EINVAL also for iop_window < 1.
+ */
+int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
+                  int32_t iop_window, uint64_t seed, const logdet_opts* opts,
+                  logdet_result* out);
+
+/* ---- step-level entry points (each one row of the hot path) ------------
+ * logdet_probe_fill: the Rademacher probe entries of Algorithms 2/3
+ * ("sample S with i.i.d. +-1 entries") by the SplitMix64 counter spec:
+ *   key  = mix(seed + (stream+1)*0x9e3779b97f4a7c15)
+ *   bits = mix(key + (col*2^32 + row + 1)*0x9e3779b97f4a7c15)
+ *   out[row*ld + (col-col0)] = bits>>63 ? -1.0 : +1.0
+ * for row in [0,n), col in [col0, col0+ncols).  out_dev: device, n*ld doubles.
+ */
+int logdet_probe_fill(uint64_t seed, int32_t stream, int32_t n, int32_t ncols, int32_t col0,
+                      double* out_dev, int32_t ld, void* cuda_stream);
+
+/* logdet_spmm: Y = Q X for a device block X (n x b, leading dimension ld,
+ * FP64), the matrix-vector products that are the estimators' only access to
+ * Q (Sec. 1; "w = Q v" in Algorithm 1).  Sums run in CSR order per row. */
+int logdet_spmm(logdet_handle h, const double* x_dev, double* y_dev, int32_t b, int32_t ld,
+                void* cuda_stream);
+
+/* logdet_orth: A = orth(Y) for a device block Y (n x s, ld) in FP64 by two
+ * rounds of Cholesky QR (the "Form an orthonormal basis A via QR" step of
+ * Algorithms 2 and 3).  Column i of A equals column i of the thin QR factor
+ * with positive diag(R).  A column whose |R_ii| <= 1e-6 max_j |y_j| is set to
+ * zero and *s_eff counts the kept ones.  a_dev may alias y_dev. */
+int logdet_orth(int32_t n, int32_t s, const double* y_dev, int32_t ldy, double* a_dev,
+                int32_t lda, int32_t* s_eff, void* cuda_stream);
+
+/* logdet_gauss_quadrature_log: for each of nprobe symmetric tridiagonals
+ * (alpha[p*m .. +m_p), beta[p*m .. +m_p-1), m_p = msteps[p] or m if msteps
+ * is NULL) the Gauss rule of Sec. 3.1: out[p] = sum_k tau_k^2 log(theta_k),
+ * tau_k = e_1^T u_k.  Device pointers.  A theta <= 0 is clamped to
+ * clamp_lo and flagged in *status (host, optional). */
+int logdet_gauss_quadrature_log(const double* alpha_dev, const double* beta_dev,
+                                const int32_t* msteps_dev, int32_t m, int32_t nprobe,
+                                double clamp_lo, double* out_dev, uint32_t* status,
+                                void* cuda_stream);
+
+/* logdet_hessenberg_log_e1: c_p = log(H_p) e_1 (principal logarithm,
+ * Algorithm 1's "L_m = log(H_m)") for nprobe upper Hessenberg matrices,
+ * H_p column-major with leading dimension ldh at H_dev + p*ldh*m, order
+ * m_p = msteps[p] (or m).  c_dev: nprobe x m (row p at c_dev + p*m).
+ * Inverse scaling and squaring (Denman-Beavers square roots, Gauss-Legendre
+ * partial-fraction Pade of degree 8).  status bit LOG_FAILED when a square
+ * root does not converge. */
+int logdet_hessenberg_log_e1(const double* H_dev, int32_t ldh, const int32_t* msteps_dev,
+                             int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
+                             void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOGDET_H */

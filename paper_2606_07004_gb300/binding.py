@@ -1,0 +1,278 @@
+"""Thin ctypes binding over liblogdet.so (argument marshalling only).
+
+Every computation runs inside the CUDA library; this module converts Python
+arguments to the C-ABI declared in ``include/logdet.h`` and back.  PyTorch is
+used only to hold device memory and streams for the step-level entry points.
+There is no CPU fallback: if the library is missing, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.environ.get("LOGDET_LIB", os.path.join(_HERE, "liblogdet.so"))
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"liblogdet.so not found at {LIB_PATH}: build it with "
+        "`python -m paper_2606_07004_gb300.build` (needs nvcc); there is no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+# ---- constants (logdet.h) --------------------------------------------------
+OK, PENDING = 0, 1
+EINVAL, ENOMEM, ENOTSPD, ETIMEOUT, ECUDA, ENOENT, ECANCEL = -1, -2, -3, -4, -5, -6, -7
+VALS_F64, VALS_F32 = 0, 1
+FP64, MIXED_FP32 = 0, 1
+METHOD_OSLQ, METHOD_OSAIOP = 0, 1
+ST_BREAKDOWN, ST_NONPOS_RITZ, ST_RANK_DEFICIENT, ST_LOG_FAILED = 1, 2, 4, 8
+
+# The symbols the header declares (checked by the CPU test suite).
+EXPORTED = [
+    "logdet_opts_default", "logdet_strerror", "logdet_last_error",
+    "logdet_create", "logdet_create_device", "logdet_destroy", "logdet_info",
+    "logdet_oslq", "logdet_osaiop",
+    "logdet_probe_fill", "logdet_spmm", "logdet_orth",
+    "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
+]
+
+
+class logdet_result(C.Structure):
+    _fields_ = [
+        ("logdet", C.c_double), ("tr_sub", C.c_double), ("tr_res", C.c_double),
+        ("log_alpha", C.c_double), ("log_gamma", C.c_double),
+        ("s", C.c_int32), ("r", C.c_int32), ("s_eff", C.c_int32),
+        ("steps_min", C.c_int32), ("steps_max", C.c_int32),
+        ("status_bits", C.c_uint32), ("device_ms", C.c_double),
+    ]
+
+
+class logdet_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32), ("tol", C.c_double),
+        ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
+        ("block_width", C.c_int32),
+        ("per_probe", C.POINTER(C.c_double)), ("z_norm2", C.POINTER(C.c_double)),
+        ("stream", C.c_void_p),
+    ]
+
+
+_P = C.c_void_p
+_i32, _i64, _u64, _u32, _dbl = C.c_int32, C.c_int64, C.c_uint64, C.c_uint32, C.c_double
+
+
+def _sig(name, restype, argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    return f
+
+
+_sig("logdet_opts_default", None, [C.POINTER(logdet_opts)])
+_sig("logdet_strerror", C.c_char_p, [C.c_int])
+_sig("logdet_last_error", C.c_char_p, [])
+_sig("logdet_create", C.c_int, [_i32, _P, _P, _P, _i32, C.POINTER(_P)])
+_sig("logdet_create_device", C.c_int, [_i32, _P, _P, _P, _i32, C.POINTER(_P)])
+_sig("logdet_destroy", None, [_P])
+_sig("logdet_info", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl)])
+for _n in ("logdet_oslq", "logdet_osaiop"):
+    _sig(_n, C.c_int, [_P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts), C.POINTER(logdet_result)])
+_sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
+_sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
+_sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
+_sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
+_sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+
+
+class LogdetError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.logdet_strerror(code).decode()
+        detail = _lib.logdet_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}): {detail}")
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise LogdetError(rc, where)
+    return rc
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    return getattr(stream, "cuda_stream", stream)
+
+
+@dataclass
+class Result:
+    logdet: float
+    tr_sub: float
+    tr_res: float
+    log_alpha: float
+    log_gamma: float
+    s: int
+    r: int
+    s_eff: int
+    steps_min: int
+    steps_max: int
+    status_bits: int
+    device_ms: float
+    per_probe: np.ndarray
+    z_norm2: np.ndarray
+
+
+class Handle:
+    """A CSR matrix resident on the GPU (logdet_create / logdet_create_device)."""
+
+    def __init__(self, n, rowptr, colind, vals, device: bool = False):
+        self._h = _P()
+        if device:
+            dt = VALS_F64 if str(vals.dtype) == "torch.float64" else VALS_F32
+            self._keep = (rowptr, colind, vals)
+            _check(_lib.logdet_create_device(n, _ptr(rowptr), _ptr(colind), _ptr(vals), dt,
+                                             C.byref(self._h)), "logdet_create_device")
+        else:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            colind = np.ascontiguousarray(colind, dtype=np.int32)
+            if vals.dtype == np.float32:
+                vals = np.ascontiguousarray(vals)
+                dt = VALS_F32
+            else:
+                vals = np.ascontiguousarray(vals, dtype=np.float64)
+                dt = VALS_F64
+            _check(_lib.logdet_create(n, _ptr(rowptr), _ptr(colind), _ptr(vals), dt,
+                                      C.byref(self._h)), "logdet_create")
+
+    @classmethod
+    def from_csr(cls, A) -> "Handle":
+        """From any object with n, rowptr, colind, vals (host arrays)."""
+        return cls(A.n, A.rowptr, A.colind, A.vals)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.logdet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def raw(self):
+        return self._h
+
+    def info(self):
+        n, nnz, lo, hi = _i32(), _i64(), _dbl(), _dbl()
+        _check(_lib.logdet_info(self._h, C.byref(n), C.byref(nnz), C.byref(lo), C.byref(hi)),
+               "logdet_info")
+        return n.value, nnz.value, lo.value, hi.value
+
+    def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
+             lam, stream):
+        s = num_probes // 3
+        r = num_probes - 2 * s
+        per = np.zeros(max(s + r, 1))
+        zn = np.zeros(max(r, 1))
+        o = logdet_opts()
+        _lib.logdet_opts_default(C.byref(o))
+        o.precision = precision
+        if tol is not None:
+            o.tol = tol
+        if lam is not None:
+            o.lambda_lo, o.lambda_hi = lam
+        o.per_probe = per.ctypes.data_as(C.POINTER(C.c_double))
+        o.z_norm2 = zn.ctypes.data_as(C.POINTER(C.c_double))
+        o.stream = _stream(stream) or None
+        res = logdet_result()
+        _check(fn(self._h, num_probes, krylov_steps, iop_window, seed, C.byref(o), C.byref(res)),
+               name)
+        return Result(res.logdet, res.tr_sub, res.tr_res, res.log_alpha, res.log_gamma,
+                      res.s, res.r, res.s_eff, res.steps_min, res.steps_max, res.status_bits,
+                      res.device_ms, per[: s + r].copy(), zn[:r].copy())
+
+    def oslq(self, num_probes, krylov_steps, seed=0, iop_window=0, precision=FP64, tol=None,
+             lam=None, stream=None) -> Result:
+        return self._run(_lib.logdet_oslq, "logdet_oslq", num_probes, krylov_steps, iop_window,
+                         seed, precision, tol, lam, stream)
+
+    def osaiop(self, num_probes, krylov_steps, iop_window=2, seed=0, precision=FP64, tol=None,
+               lam=None, stream=None) -> Result:
+        return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
+                         iop_window, seed, precision, tol, lam, stream)
+
+    def spmm(self, x, y, b, ld, stream=None):
+        _check(_lib.logdet_spmm(self._h, _ptr(x), _ptr(y), b, ld, _stream(stream)), "logdet_spmm")
+
+
+def logdet_create(n, rowptr, colind, vals) -> Handle:
+    return Handle(n, rowptr, colind, vals)
+
+
+def logdet_create_device(n, rowptr, colind, vals) -> Handle:
+    return Handle(n, rowptr, colind, vals, device=True)
+
+
+def logdet_oslq(h: Handle, num_probes, krylov_steps, iop_window=0, seed=0, **kw) -> Result:
+    return h.oslq(num_probes, krylov_steps, seed=seed, iop_window=iop_window, **kw)
+
+
+def logdet_osaiop(h: Handle, num_probes, krylov_steps, iop_window=2, seed=0, **kw) -> Result:
+    return h.osaiop(num_probes, krylov_steps, iop_window=iop_window, seed=seed, **kw)
+
+
+def logdet_probe_fill(seed, stream_id, n, ncols, col0, out, ld, stream=None):
+    _check(_lib.logdet_probe_fill(seed, stream_id, n, ncols, col0, _ptr(out), ld, _stream(stream)),
+           "logdet_probe_fill")
+
+
+def logdet_spmm(h: Handle, x, y, b, ld, stream=None):
+    h.spmm(x, y, b, ld, stream)
+
+
+def logdet_orth(n, s, y, ldy, a, lda, stream=None) -> int:
+    se = _i32()
+    _check(_lib.logdet_orth(n, s, _ptr(y), ldy, _ptr(a), lda, C.byref(se), _stream(stream)),
+           "logdet_orth")
+    return se.value
+
+
+def logdet_gauss_quadrature_log(alpha, beta, msteps, m, nprobe, clamp_lo, out, stream=None) -> int:
+    st = _u32()
+    _check(_lib.logdet_gauss_quadrature_log(_ptr(alpha), _ptr(beta), _ptr(msteps), m, nprobe,
+                                            clamp_lo, _ptr(out), C.byref(st), _stream(stream)),
+           "logdet_gauss_quadrature_log")
+    return st.value
+
+
+def logdet_hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, stream=None) -> int:
+    st = _u32()
+    _check(_lib.logdet_hessenberg_log_e1(_ptr(H), ldh, _ptr(msteps), m, nprobe, _ptr(c),
+                                         C.byref(st), _stream(stream)),
+           "logdet_hessenberg_log_e1")
+    return st.value
+
+
+def exported_symbols() -> list[str]:
+    return [name for name in EXPORTED if hasattr(_lib, name)]

@@ -1,0 +1,783 @@
+// Dense and small-matrix kernels (see dense.cuh).  All arithmetic is FP64.
+#include "dense.cuh"
+#include "krylov.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace ld {
+
+// ===========================================================================
+// Hutch++ QR: A = orth(Y) by two rounds of Cholesky QR (Algorithms 2 and 3,
+// "form an orthonormal basis A for the span of Y via QR").  For full-rank Y
+// this gives the thin QR factor with positive diag(R), the same columns as a
+// Householder QR with that sign convention.
+// ===========================================================================
+constexpr int kGramThreads = 256;
+constexpr int kGramRows = 256;   // rows per tile (one partial per tile)
+constexpr int kGramChunk = 32;   // rows staged in shared memory at a time
+constexpr int kGramNP = (kMaxSketch * (kMaxSketch + 1) / 2 + kGramThreads - 1) / kGramThreads;
+
+__device__ __forceinline__ void unrank_upper(int q, int s, int& i, int& j) {
+  i = 0;
+  int rem = q;
+  while (rem >= s - i) { rem -= s - i; ++i; }
+  j = i + rem;
+}
+
+// Per-tile partial Gram sums sum_rows y_i y_j (i <= j), written [pair][tile].
+__global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict__ Y, int ldy,
+                                                       int n, int s, int ntiles,
+                                                       double* __restrict__ part) {
+  __shared__ double sy[kGramChunk * kMaxSketch];
+  const int npairs = s * (s + 1) / 2;
+  int pi[kGramNP], pj[kGramNP];
+#pragma unroll
+  for (int q = 0; q < kGramNP; ++q) {
+    int idx = threadIdx.x + q * blockDim.x;
+    if (idx < npairs) unrank_upper(idx, s, pi[q], pj[q]);
+    else { pi[q] = 0; pj[q] = 0; }
+  }
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double acc[kGramNP];
+#pragma unroll
+    for (int q = 0; q < kGramNP; ++q) acc[q] = 0.0;
+    const int row0 = tile * kGramRows;
+    const int row1 = min(row0 + kGramRows, n);
+    for (int c0 = row0; c0 < row1; c0 += kGramChunk) {
+      const int rows = min(kGramChunk, row1 - c0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
+        int r = e / s, i = e - r * s;
+        sy[r * s + i] = Y[(size_t)(c0 + r) * ldy + i];
+      }
+      __syncthreads();
+      for (int r = 0; r < rows; ++r) {
+#pragma unroll
+        for (int q = 0; q < kGramNP; ++q)
+          acc[q] = fma(sy[r * s + pi[q]], sy[r * s + pj[q]], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGramNP; ++q) {
+      int idx = threadIdx.x + q * blockDim.x;
+      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
+    }
+  }
+}
+
+// Sum the tile partials of each entry in a fixed order: out[e] for e < count.
+// With sym_s > 0 the entries are upper-triangle pairs of an sym_s x sym_s
+// matrix and both (i,j) and (j,i) of out are written.
+__global__ void __launch_bounds__(128) k_reduce_rows(const double* __restrict__ part, int ntiles,
+                                                     int sym_s, double* __restrict__ out) {
+  __shared__ double sh[128];
+  const int e = blockIdx.x;
+  const double* src = part + (size_t)e * ntiles;
+  double a = 0.0;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) a += src[t];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (sym_s > 0) {
+      int i, j;
+      unrank_upper(e, sym_s, i, j);
+      out[i * sym_s + j] = sh[0];
+      out[j * sym_s + i] = sh[0];
+    } else {
+      out[e] = sh[0];
+    }
+  }
+}
+
+// Cholesky C = R^T R of the s x s Gram matrix, dropping a column whose pivot
+// R_jj^2 is <= thr_rel * max_i C_ii (its R row and Rinv column become zero),
+// then Rinv = R^{-1} restricted to the kept columns.  One CTA.
+__global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ C, int s,
+                                                  double thr_rel, double* __restrict__ Rinv,
+                                                  int* __restrict__ keep_out) {
+  __shared__ double R[kMaxSketch * kMaxSketch];
+  __shared__ int keep[kMaxSketch];
+  __shared__ double thr;
+  double* Ri = Rinv;  // written column by column by the thread that owns it
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) { R[e] = C[e]; Ri[e] = 0.0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int i = 0; i < s; ++i) mx = fmax(mx, R[i * s + i]);
+    thr = thr_rel * mx;
+  }
+  __syncthreads();
+  for (int j = 0; j < s; ++j) {
+    if (threadIdx.x == 0) {
+      double piv = R[j * s + j];
+      for (int k = 0; k < j; ++k) piv -= R[k * s + j] * R[k * s + j];
+      keep[j] = piv > thr;
+      R[j * s + j] = keep[j] ? sqrt(piv) : 0.0;
+    }
+    __syncthreads();
+    for (int l = j + 1 + threadIdx.x; l < s; l += blockDim.x) {
+      if (keep[j]) {
+        double v = R[j * s + l];
+        for (int k = 0; k < j; ++k) v -= R[k * s + j] * R[k * s + l];
+        R[j * s + l] = v / R[j * s + j];
+      } else {
+        R[j * s + l] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  // Upper-triangular inverse, one column per thread: R Rinv = I.  The zero
+  // fill above is made visible to every thread before columns are written.
+  __threadfence_block();
+  __syncthreads();
+  for (int l = threadIdx.x; l < s; l += blockDim.x) {
+    if (!keep[l]) continue;
+    for (int i = l; i >= 0; --i) {
+      if (!keep[i]) { Ri[i * s + l] = 0.0; continue; }
+      double v = (i == l) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= l; ++k) v -= R[i * s + k] * Ri[k * s + l];
+      Ri[i * s + l] = v / R[i * s + i];
+    }
+  }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) keep_out[i] = keep[i];
+}
+
+// A[row, l] = sum_{i <= l} Y[row, i] Rinv[i, l]; A may alias Y.
+__global__ void __launch_bounds__(256) k_apply_rinv(const double* Y, int ldy, int n, int s,
+                                                    const double* __restrict__ Rinv, double* A,
+                                                    int lda) {
+  __shared__ double sr[kMaxSketch * kMaxSketch];
+  __shared__ double sy[kGramChunk * kMaxSketch];
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) sr[e] = Rinv[e];
+  for (int c0 = blockIdx.x * kGramChunk; c0 < n; c0 += gridDim.x * kGramChunk) {
+    const int rows = min(kGramChunk, n - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
+      int r = e / s, i = e - r * s;
+      sy[r * s + i] = Y[(size_t)(c0 + r) * ldy + i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
+      int r = e / s, l = e - r * s;
+      double v = 0.0;
+      for (int i = 0; i <= l; ++i) v = fma(sy[r * s + i], sr[i * s + l], v);
+      A[(size_t)(c0 + r) * lda + l] = v;
+    }
+  }
+}
+
+size_t orth_workspace_doubles(int n, int s) {
+  int ntiles = div_up(n, kGramRows);
+  size_t npairs = (size_t)s * (s + 1) / 2;
+  return npairs * ntiles + 2 * (size_t)s * s + 64;
+}
+
+static int grid_for(int tiles) { return std::max(1, std::min(tiles, 4 * sm_count())); }
+
+int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
+              int* keep_dev, int* s_eff_host, cudaStream_t st) {
+  if (s < 1 || s > kMaxSketch || n < 1) {
+    set_error("orth: s=%d must be in [1, %d]", s, kMaxSketch);
+    return LOGDET_EINVAL;
+  }
+  const int ntiles = div_up(n, kGramRows);
+  const int npairs = s * (s + 1) / 2;
+  double* part = ws;
+  double* C = part + (size_t)npairs * ntiles;
+  double* Rinv = C + (size_t)s * s;
+  int* keep = keep_dev;
+  int* keep_tmp = nullptr;
+  if (!keep) {
+    LD_CUDA(cudaMallocAsync(&keep_tmp, sizeof(int) * s, st));
+    keep = keep_tmp;
+  }
+  const double* src = Y;
+  int ldsrc = ldy;
+  for (int round = 0; round < 2; ++round) {
+    k_gram<<<grid_for(ntiles), kGramThreads, 0, st>>>(src, ldsrc, n, s, ntiles, part);
+    LD_CHECK_LAUNCH();
+    k_reduce_rows<<<npairs, 128, 0, st>>>(part, ntiles, s, C);
+    LD_CHECK_LAUNCH();
+    // R14: |R_ii| <= 1e-6 max_j |y_j|  <=>  R_ii^2 <= 1e-12 max_j C_jj.
+    k_chol_inv<<<1, 256, 0, st>>>(C, s, 1e-12, Rinv, keep);
+    LD_CHECK_LAUNCH();
+    k_apply_rinv<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(src, ldsrc, n, s, Rinv, A, lda);
+    LD_CHECK_LAUNCH();
+    src = A;
+    ldsrc = lda;
+  }
+  if (s_eff_host) {
+    std::vector<int> h(s);
+    LD_CUDA(cudaMemcpyAsync(h.data(), keep, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaStreamSynchronize(st));
+    int c = 0;
+    for (int i = 0; i < s; ++i) c += h[i] != 0;
+    *s_eff_host = c;
+  }
+  if (keep_tmp) LD_CUDA(cudaFreeAsync(keep_tmp, st));
+  return LOGDET_OK;
+}
+
+// ===========================================================================
+// Hutch++ residual probes: Z = G - A (A^T G), G generated from the probe hash.
+// ===========================================================================
+constexpr int kProjNP = (kMaxSketch * kMaxSketch + kGramThreads - 1) / kGramThreads;
+
+__global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__ A, int lda,
+                                                      int n, int s, int r, uint64_t key,
+                                                      int ntiles, double* __restrict__ part) {
+  __shared__ double sa[kGramChunk * kMaxSketch];
+  __shared__ double sg[kGramChunk * kMaxSketch];
+  const int npairs = s * r;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    double acc[kProjNP];
+#pragma unroll
+    for (int q = 0; q < kProjNP; ++q) acc[q] = 0.0;
+    const int row0 = tile * kGramRows;
+    const int row1 = min(row0 + kGramRows, n);
+    for (int c0 = row0; c0 < row1; c0 += kGramChunk) {
+      const int rows = min(kGramChunk, row1 - c0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
+        int rr = e / s, i = e - rr * s;
+        sa[rr * s + i] = A[(size_t)(c0 + rr) * lda + i];
+      }
+      for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
+        int rr = e / r, j = e - rr * r;
+        sg[rr * r + j] = (double)probe_sign(key, (uint32_t)j, (uint32_t)(c0 + rr));
+      }
+      __syncthreads();
+      for (int rr = 0; rr < rows; ++rr) {
+#pragma unroll
+        for (int q = 0; q < kProjNP; ++q) {
+          int idx = threadIdx.x + q * blockDim.x;
+          if (idx < npairs) {
+            int i = idx / r, j = idx - i * r;
+            acc[q] = fma(sa[rr * s + i], sg[rr * r + j], acc[q]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kProjNP; ++q) {
+      int idx = threadIdx.x + q * blockDim.x;
+      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
+    }
+  }
+}
+
+// X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j]
+__global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n, int s, int r,
+                                                 uint64_t key, const double* __restrict__ Bm,
+                                                 double* X, int ldx, int zcol0) {
+  __shared__ double sb[kMaxSketch * kMaxSketch];
+  __shared__ double sa[kGramChunk * kMaxSketch];
+  for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = Bm[e];
+  for (int c0 = blockIdx.x * kGramChunk; c0 < n; c0 += gridDim.x * kGramChunk) {
+    const int rows = min(kGramChunk, n - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
+      int rr = e / s, i = e - rr * s;
+      sa[rr * s + i] = A[(size_t)(c0 + rr) * lda + i];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
+      int rr = e / r, j = e - rr * r;
+      double acc = 0.0;
+      for (int i = 0; i < s; ++i) acc = fma(sa[rr * s + i], sb[i * r + j], acc);
+      double g = (double)probe_sign(key, (uint32_t)j, (uint32_t)(c0 + rr));
+      X[(size_t)(c0 + rr) * ldx + zcol0 + j] = g - acc;
+    }
+  }
+}
+
+size_t project_workspace_doubles(int n, int s, int r) {
+  int ntiles = div_up(n, kGramRows);
+  return (size_t)s * r * ntiles + (size_t)s * r + 64;
+}
+
+int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
+                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st) {
+  if (s > kMaxSketch || r > kMaxSketch || r < 1) {
+    set_error("project: s=%d r=%d out of range", s, r);
+    return LOGDET_EINVAL;
+  }
+  const int ntiles = div_up(n, kGramRows);
+  double* part = ws;
+  double* Bm = ws + (size_t)s * r * ntiles;
+  if (s > 0) {
+    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, ntiles, part);
+    LD_CHECK_LAUNCH();
+    k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
+    LD_CHECK_LAUNCH();
+  }
+  k_project<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(A, lda, n, s, r, key, Bm, X, ldx,
+                                                             zcol0);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+// ===========================================================================
+// Column norms (partials in the Krylov layout [ld][ntiles]).
+// ===========================================================================
+template <typename T>
+__global__ void __launch_bounds__(512) k_colnorm(const T* __restrict__ X, int n, int ld,
+                                                  int tile_rows, int ntiles,
+                                                  typename PartOf<T>::type* __restrict__ part) {
+  constexpr int V = Vec16<T>::N;
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* smem = reinterpret_cast<Acc*>(smem_raw);
+  const int G = ld / V;
+  const int R = blockDim.x / G;
+  const int r = threadIdx.x / G, g = threadIdx.x - (threadIdx.x / G) * G;
+  const bool live = r < R;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    Acc acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v].zero();
+    const int row0 = tile * tile_rows, row1 = min(row0 + tile_rows, n);
+    if (live) {
+      for (int row = row0 + r; row < row1; row += R) {
+        T x[V];
+        load_vec<T>(X + (size_t)row * ld + g * V, x);
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v].fma(x[v], x[v]);
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) smem[threadIdx.x * V + v] = acc[v];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+      int gg = c / V, v = c - gg * V;
+      Acc t;
+      t.zero();
+      for (int rr = 0; rr < R; ++rr) t.add(smem[(rr * G + gg) * V + v]);
+      put_part(part + (size_t)c * ntiles + tile, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+int colnorm_partials(const T* X, int n, int ld, int tile_rows, int ntiles,
+                     typename PartOf<T>::type* part, int threads, cudaStream_t st) {
+  using Acc = typename AccOf<T>::type;
+  size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+  k_colnorm<T><<<grid_for(ntiles), threads, smem, st>>>(X, n, ld, tile_rows, ntiles, part);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+template int colnorm_partials<double>(const double*, int, int, int, int, double*, int, cudaStream_t);
+template int colnorm_partials<float>(const float*, int, int, int, int, float2*, int, cudaStream_t);
+
+// ===========================================================================
+// Gauss quadrature of a symmetric tridiagonal (Sec. 3.1): eigenvalues theta_k
+// and first eigenvector components tau_k by implicit symmetric QR steps with
+// a Wilkinson shift (Golub and Van Loan, "Matrix Computations", Sec. 8.3),
+// carrying only the first row of the accumulated rotations (Golub and
+// Welsch, Math. Comp. 1969).  One thread per probe.
+// ===========================================================================
+__device__ double tridiag_gauss_log(double* d, double* e, double* z, int m, double clamp_lo,
+                                    bool* nonpos) {
+  // d[0..m) diagonal, e[0..m-1) off-diagonal, z = e_1 on entry.
+  const double eps = 2.220446049250313e-16;
+  int hi = m - 1;
+  int iters = 0;
+  while (hi > 0) {
+    // Deflate negligible off-diagonals at the bottom.
+    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      iters = 0;
+      continue;
+    }
+    // Find the top of the unreduced block ending at hi.
+    int lo = hi - 1;
+    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+    if (lo > 0) e[lo - 1] = 0.0;
+    if (++iters > 60) { *nonpos = true; break; }  // unconverged: flagged
+    // Wilkinson shift from the trailing 2x2 block.
+    const double t = e[hi - 1];
+    const double delta = 0.5 * (d[hi - 1] - d[hi]);
+    const double den = delta + copysign(hypot(delta, t), delta == 0.0 ? 1.0 : delta);
+    const double mu = d[hi] - t * t / den;
+    double x = d[lo] - mu;
+    double bz = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double rr = hypot(x, bz);
+      const double c = (rr == 0.0) ? 1.0 : x / rr;
+      const double s = (rr == 0.0) ? 0.0 : -bz / rr;
+      if (k > lo) e[k - 1] = rr;
+      const double a = d[k], b = e[k], cc = d[k + 1];
+      d[k] = c * c * a - 2.0 * c * s * b + s * s * cc;
+      d[k + 1] = s * s * a + 2.0 * c * s * b + c * c * cc;
+      e[k] = c * s * (a - cc) + (c * c - s * s) * b;
+      if (k + 1 < hi) {
+        bz = -s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+        x = e[k];
+      }
+      const double z0 = z[k], z1 = z[k + 1];
+      z[k] = c * z0 - s * z1;
+      z[k + 1] = s * z0 + c * z1;
+    }
+  }
+  double sum = 0.0;
+  for (int k = 0; k < m; ++k) {
+    double th = d[k];
+    if (!(th > 0.0)) { *nonpos = true; th = clamp_lo; }
+    sum += z[k] * z[k] * log(th);
+  }
+  return sum;
+}
+
+__global__ void k_gauss_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
+                             int ldab, const int* __restrict__ msteps, int m, int nprobe,
+                             double clamp_lo, double* __restrict__ out,
+                             uint32_t* __restrict__ status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprobe) return;
+  int mp = msteps ? msteps[p] : m;
+  if (mp > m) mp = m;
+  if (mp <= 0) { out[p] = 0.0; return; }
+  double d[kMaxSteps], e[kMaxSteps], z[kMaxSteps];
+  for (int k = 0; k < mp; ++k) {
+    d[k] = alpha[(size_t)p * ldab + k];
+    e[k] = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
+    z[k] = (k == 0) ? 1.0 : 0.0;
+  }
+  bool nonpos = false;
+  out[p] = tridiag_gauss_log(d, e, z, mp, clamp_lo, &nonpos);
+  if (nonpos && status) atomicOr(status + p, LOGDET_ST_NONPOS_RITZ);
+}
+
+int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, const int* msteps,
+                         int m, int nprobe, double clamp_lo, double* out, uint32_t* status,
+                         cudaStream_t st) {
+  if (m < 1 || m > kMaxSteps) {
+    set_error("gauss quadrature: m=%d must be in [1, %d]", m, kMaxSteps);
+    return LOGDET_EINVAL;
+  }
+  k_gauss_quad<<<div_up(nprobe, 32), 32, 0, st>>>(alpha, beta, ldab, msteps, m, nprobe,
+                                                   clamp_lo, out, status);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+// ===========================================================================
+// log(H) e_1 by inverse scaling and squaring (Kenney and Laub 1989; Higham,
+// "Evaluating Pade approximants of the matrix logarithm", SIMAX 2001): take
+// square roots A <- A^{1/2} (product form of the Denman-Beavers iteration)
+// until |A - I|_1 <= 0.25, then log(H) = 2^s log(I + X), X = A - I, with the
+// [8/8] Pade approximant in its partial-fraction form
+//   log(I + X) ~ sum_j w_j X (I + x_j X)^{-1}
+// (x_j, w_j the 8-point Gauss-Legendre rule on [0, 1]).  Only the first
+// column is formed.  One CTA per probe; matrices live in a global workspace.
+// ===========================================================================
+constexpr int kLogThreads = 256;
+constexpr int kPadeNodes = 8;
+
+struct GLRule { double x[kPadeNodes], w[kPadeNodes]; };
+
+// Gauss-Jordan inversion in place with partial (row) pivoting; A row-major m x m.
+__device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
+  __shared__ int s_piv;
+  __shared__ bool s_ok;
+  if (threadIdx.x == 0) s_ok = true;
+  for (int k = 0; k < m; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(A[k * m + k]);
+      for (int i = k + 1; i < m; ++i) {
+        double v = fabs(A[i * m + k]);
+        if (v > best) { best = v; p = i; }
+      }
+      s_piv = p;
+      perm[k] = p;
+      if (best == 0.0) s_ok = false;
+    }
+    __syncthreads();
+    const int p = s_piv;
+    if (p != k) {
+      for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double t = A[k * m + j];
+        A[k * m + j] = A[p * m + j];
+        A[p * m + j] = t;
+      }
+    }
+    __syncthreads();
+    const double piv = A[k * m + k];
+    const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      A[k * m + j] = (j == k) ? ipiv : A[k * m + j] * ipiv;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = (i == k) ? 0.0 : A[i * m + k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e - i * m;
+      if (i == k) continue;
+      const double f = fcol[i];
+      if (j == k) A[e] = -f * A[k * m + k];
+      else A[e] = fma(-f, A[k * m + j], A[e]);
+    }
+  }
+  __syncthreads();
+  for (int k = m - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        double t = A[i * m + k];
+        A[i * m + k] = A[i * m + p];
+        A[i * m + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+  return s_ok;
+}
+
+// max_j sum_i |A_ij - delta_ij|
+__device__ double cta_norm1_minus_identity(const double* A, int m, double* red) {
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += fabs(A[i * m + j] - (i == j ? 1.0 : 0.0));
+    mx = fmax(mx, s);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restrict__ H, int ldh,
+                                                         const int* __restrict__ msteps, int mmax,
+                                                         double* __restrict__ cout, int ldc,
+                                                         double* __restrict__ ws,
+                                                         uint32_t* __restrict__ status,
+                                                         GLRule gl) {
+  __shared__ double red[kLogThreads];
+  __shared__ int perm[kMaxSteps];
+  __shared__ double fcol[kMaxSteps];
+  __shared__ double rhs[kMaxSteps];
+  __shared__ double acc[kMaxSteps];
+  const int p = blockIdx.x;
+  int m = msteps ? msteps[p] : mmax;
+  if (m > mmax) m = mmax;
+  double* c = cout + (size_t)p * ldc;
+  if (m <= 0) {
+    for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = 0.0;
+    return;
+  }
+  const size_t mm = (size_t)mmax * mmax;
+  double* Yb = ws + (size_t)p * 4 * mm;  // current matrix A (square-rooted in place)
+  double* Mb = Yb + mm;
+  double* Wb = Mb + mm;
+  double* Tb = Wb + mm;
+  const double* Hp = H + (size_t)p * ldh * mmax;
+  // Row-major copy of the leading m x m block of the column-major H.
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e / m, j = e - i * m;
+    Yb[e] = Hp[(size_t)j * ldh + i];
+  }
+  __syncthreads();
+  bool ok = true;
+  int nroots = 0;
+  while (cta_norm1_minus_identity(Yb, m, red) > 0.25 && nroots < 64) {
+    // Product-form Denman-Beavers: M0 = Y0 = A;
+    //   Y <- Y (I + M^{-1}) / 2,  M <- (I + (M + M^{-1}) / 2) / 2,  Y -> A^{1/2}.
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Mb[e] = Yb[e];
+    __syncthreads();
+    bool conv = false;
+    double prev = 1e300;
+    for (int it = 0; it < 100; ++it) {
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wb[e] = Mb[e];
+      __syncthreads();
+      if (!cta_invert(Wb, m, perm, fcol)) { ok = false; break; }
+      __syncthreads();
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e - i * m;
+        double v = 0.0;
+        for (int k = 0; k < m; ++k) v = fma(Yb[i * m + k], Wb[k * m + j], v);
+        Tb[e] = 0.5 * (Yb[e] + v);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        int i = e / m, j = e - i * m;
+        Yb[e] = Tb[e];
+        Mb[e] = 0.25 * (Mb[e] + Wb[e]) + (i == j ? 0.5 : 0.0);
+      }
+      __syncthreads();
+      double dev = cta_norm1_minus_identity(Mb, m, red);
+      // Converged at rounding level, or stagnating there.
+      if (dev <= 1e-15 * m || (dev < 1e-9 && dev > 0.5 * prev)) { conv = true; break; }
+      prev = dev;
+    }
+    if (!conv) { ok = false; break; }
+    ++nroots;
+  }
+  // X = A - I ; rhs = X e_1 ; c = 2^s sum_j w_j (I + x_j X)^{-1} rhs
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    rhs[i] = Yb[i * m + 0] - (i == 0 ? 1.0 : 0.0);
+    acc[i] = 0.0;
+  }
+  __syncthreads();
+  for (int q = 0; q < kPadeNodes && ok; ++q) {
+    const double xq = gl.x[q];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e / m, j = e - i * m;
+      Wb[e] = (i == j ? 1.0 : 0.0) + xq * (Yb[e] - (i == j ? 1.0 : 0.0));
+    }
+    __syncthreads();
+    if (!cta_invert(Wb, m, perm, fcol)) { ok = false; break; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v = fma(Wb[i * m + k], rhs[k], v);
+      acc[i] = fma(gl.w[q], v, acc[i]);
+    }
+    __syncthreads();
+  }
+  const double scale = ldexp(1.0, nroots);
+  for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = (i < m && ok) ? scale * acc[i] : 0.0;
+  if (!ok && threadIdx.x == 0 && status) atomicOr(status + p, LOGDET_ST_LOG_FAILED);
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] by Newton's method on P_N.
+static GLRule gauss_legendre01() {
+  GLRule g;
+  const int N = kPadeNodes;
+  for (int i = 0; i < N; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (N + 0.5));
+    double dp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= N; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = N * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= N; ++k) {
+        double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = N * (x * p1 - p0) / (x * x - 1.0);
+    }
+    g.x[i] = 0.5 * (x + 1.0);
+    g.w[i] = 1.0 / ((1.0 - x * x) * dp * dp);  // = (2/((1-x^2)P'^2)) / 2 on [0,1]
+  }
+  return g;
+}
+
+size_t hesslog_workspace_doubles(int m, int nprobe) { return (size_t)nprobe * 4 * m * m + 16; }
+
+int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int nprobe, double* c,
+                      int ldc, double* ws, uint32_t* status, cudaStream_t st) {
+  if (m < 1 || m > kMaxSteps) {
+    set_error("hessenberg log: m=%d must be in [1, %d]", m, kMaxSteps);
+    return LOGDET_EINVAL;
+  }
+  static const GLRule gl = gauss_legendre01();
+  k_hesslog<<<nprobe, kLogThreads, 0, st>>>(H, ldh, msteps, m, c, ldc, ws, status, gl);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+// ===========================================================================
+// Probe fill and block conversion.
+// ===========================================================================
+template <typename T>
+__global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld) {
+  const size_t total = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int row = (int)(e / ld), c = (int)(e - (size_t)row * ld);
+    T v = T(0);
+    if (c < ncols) v = T(probe_sign(key, (uint32_t)(col0 + c), (uint32_t)row));
+    out[e] = v;
+  }
+}
+
+template <typename T>
+int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st) {
+  k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, n, ncols, col0, out, ld);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t);
+template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t);
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols) {
+  const size_t total = (size_t)n * ldout;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int row = (int)(e / ldout), c = (int)(e - (size_t)row * ldout);
+    out[e] = (c < cols) ? (Tout)in[(size_t)row * ldin + c] : Tout(0);
+  }
+}
+
+template <typename Tin, typename Tout>
+int convert_block(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols,
+                  cudaStream_t st) {
+  k_convert<Tin, Tout><<<4 * sm_count(), 256, 0, st>>>(in, ldin, out, ldout, n, cols);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+template int convert_block<double, double>(const double*, int, double*, int, int, int, cudaStream_t);
+template int convert_block<double, float>(const double*, int, float*, int, int, int, cudaStream_t);
+template int convert_block<float, double>(const float*, int, double*, int, int, int, cudaStream_t);
+
+// ===========================================================================
+// OSA-IOP sketch assembly: Y[:, p] = sum_j w[j][p] V_j[:, p]
+// ===========================================================================
+template <typename T>
+__global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ld, int m,
+                                  const double* __restrict__ w, double* __restrict__ Y,
+                                  int ldy) {
+  const size_t total = (size_t)n * ld;
+  const size_t stride_v = (size_t)n * ld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int row = (int)(e / ld), p = (int)(e - (size_t)row * ld);
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) acc = fma(w[(size_t)j * ld + p], (double)V[j * stride_v + e], acc);
+    if (p < ldy) Y[(size_t)row * ldy + p] = acc;
+  }
+}
+
+template <typename T>
+int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y, int ldy,
+                    cudaStream_t st) {
+  k_sketch_assemble<T><<<8 * sm_count(), 256, 0, st>>>(V, n, ld, m, w, Y, ldy);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+template int sketch_assemble<double>(const double*, int, int, int, const double*, double*, int, cudaStream_t);
+template int sketch_assemble<float>(const float*, int, int, int, const double*, double*, int, cudaStream_t);
+
+}  // namespace ld

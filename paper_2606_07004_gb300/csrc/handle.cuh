@@ -1,0 +1,64 @@
+// The matrix handle and small host-side helpers shared by the translation units.
+#pragma once
+
+#include "common.cuh"
+
+#include <algorithm>
+
+struct logdet_ctx {
+  int device = 0;
+  int n = 0;
+  long long nnz = 0;
+  int* rowptr = nullptr;
+  int* colind = nullptr;
+  void* vals = nullptr;
+  int vals_dtype = LOGDET_VALS_F64;
+  bool owns = false;
+  double g_lo = 0.0, g_hi = 0.0;  // Gershgorin interval (unclamped)
+  cudaStream_t stream = nullptr;
+};
+
+namespace ld {
+
+// Stream-ordered device buffer freed when it goes out of scope.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t count = 0;
+  cudaStream_t st;
+  explicit DevBuf(cudaStream_t s) : st(s) {}
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  int alloc(size_t n) {
+    release();
+    count = std::max<size_t>(n, 1);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return LOGDET_ENOMEM;
+    }
+    return LOGDET_OK;
+  }
+  int zero() { return cudaMemsetAsync(p, 0, count * sizeof(T), st) == cudaSuccess ? LOGDET_OK : LOGDET_ECUDA; }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+  }
+  ~DevBuf() { release(); }
+};
+
+int ensure_pool(int device);
+int create_handle(int32_t n, const int32_t* rowptr, const int32_t* colind, const void* vals,
+                  int32_t vals_dtype, bool device_ptrs, logdet_handle* out);
+void destroy_handle(logdet_ctx* h);
+
+template <typename T>
+int scaled_values(logdet_ctx* h, double c, T* out, cudaStream_t st);
+
+template <typename T>
+int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const T* x, T* y,
+               int ld, cudaStream_t st);
+
+}  // namespace ld

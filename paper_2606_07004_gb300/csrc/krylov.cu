@@ -1,0 +1,485 @@
+// Krylov step kernels (see krylov.cuh for the recurrence they implement).
+#include "krylov.cuh"
+
+#include <algorithm>
+
+namespace ld {
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+static int gcd_int(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
+
+// Threads per CTA: a multiple of both 32 (full warps) and of the chunks per
+// row G = ld / vec, so every lane of every warp owns a (row, chunk) slot.
+TileGeom tile_geom(int ld, int vec) {
+  TileGeom g;
+  int G = ld / vec;
+  int lcm = G / gcd_int(G, 32) * 32;          // smallest CTA with whole rows and warps
+  int threads = lcm;
+  while (threads < 256 && threads + lcm <= 512) threads += lcm;
+  if (threads > 512) threads = std::max(1, 512 / G) * G;  // very wide blocks: idle lanes accepted
+  if (G > 512) threads = 512;                               // (not reached for ld <= 1024)
+  g.threads = threads;
+  g.rows_per_iter = threads / G;
+  int iters = std::max(1, 256 / std::max(1, g.rows_per_iter));  // ~256+ rows per tile
+  if (iters < 4) iters = 4;
+  g.tile_rows = g.rows_per_iter * iters;
+  return g;
+}
+
+template <typename Batch>
+__device__ __forceinline__ int find_job(const Batch& B, int gt) {
+  int j = 0;
+  while (j + 1 < B.njobs && gt >= B.tile_start[j + 1]) ++j;
+  return j;
+}
+
+// Reduce the per-thread accumulators of all rows of the CTA for one dot and
+// write one partial per column.  smem holds blockDim.x * V accumulators.
+template <typename T, typename Acc>
+__device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec16<T>::N],
+                                                 bool live, int G, int R, int ld,
+                                                 typename PartOf<T>::type* dst, int ntiles,
+                                                 int tile) {
+  constexpr int V = Vec16<T>::N;
+  __syncthreads();
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) smem[threadIdx.x * V + v] = acc[v];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+    int g = c / V, v = c - (c / V) * V;
+    Acc t;
+    t.zero();
+    for (int rr = 0; rr < R; ++rr) t.add(smem[(rr * G + g) * V + v]);
+    put_part(dst + (size_t)c * ntiles + tile, t);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 1: y = A x (CSR order per row) and d_i += dotv_i . y
+// ---------------------------------------------------------------------------
+template <typename T, int NDOT>
+__global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<T> B) {
+  constexpr int V = Vec16<T>::N;
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* smem = reinterpret_cast<Acc*>(smem_raw);
+
+  for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
+    const int jb = find_job(B, gt);
+    const SpmmJob<T>& J = B.jobs[jb];
+    const int tile = gt - B.tile_start[jb];
+    const int G = J.ld / V;
+    const int R = blockDim.x / G;
+    const int r = threadIdx.x / G;
+    const int g = threadIdx.x - r * G;
+    const bool live = r < R;
+    const int row0 = tile * J.tile_rows;
+    const int row1 = min(row0 + J.tile_rows, J.n);
+    const int col0 = g * V;
+    const int ndots = J.ndots;
+
+    Acc acc[NDOT > 0 ? NDOT : 1][V];
+#pragma unroll
+    for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[d][v].zero();
+
+    double cs[V], csh[V];
+    const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
+    if (live) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        cs[v] = has_scale ? J.colscale[col0 + v] : 1.0;
+        csh[v] = has_shift ? J.colshift[col0 + v] : 0.0;
+      }
+      for (int row = row0 + r; row < row1; row += R) {
+        T s[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) s[v] = T(0);
+        const int p0 = __ldg(J.rowptr + row), p1 = __ldg(J.rowptr + row + 1);
+#pragma unroll 4
+        for (int p = p0; p < p1; ++p) {
+          const int c = __ldg(J.colind + p);
+          const T a = __ldg(J.vals + p);
+          T xv[V];
+          load_vec<T>(J.x + (size_t)c * J.ld + col0, xv);
+#pragma unroll
+          for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
+        }
+        if (has_shift || has_scale) {
+          T xr[V];
+          load_vec<T>(J.x + (size_t)row * J.ld + col0, xr);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            if (has_shift) s[v] = fma(T(csh[v]), xr[v], s[v]);
+            if (has_scale) s[v] = s[v] * T(cs[v]);
+          }
+        }
+        store_vec<T>(J.y + (size_t)row * J.ld + col0, s);
+#pragma unroll
+        for (int d = 0; d < NDOT; ++d) {
+          if (d < ndots) {
+            T u[V];
+            load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < NDOT; ++d) {
+      if (d < ndots)
+        cta_reduce_write<T, Acc>(smem, acc[d], live, G, R, J.ld,
+                                 J.part + (size_t)d * J.ld * J.ntiles, J.ntiles, tile);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: out = ycoef*y - sum_i coef_i basis_i;  |out|^2 [; extra . out]
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch<T> B) {
+  constexpr int V = Vec16<T>::N;
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Acc* smem = reinterpret_cast<Acc*>(smem_raw);
+
+  for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
+    const int jb = find_job(B, gt);
+    const UpdJob<T>& J = B.jobs[jb];
+    const int tile = gt - B.tile_start[jb];
+    const int G = J.ld / V;
+    const int R = blockDim.x / G;
+    const int r = threadIdx.x / G;
+    const int g = threadIdx.x - r * G;
+    const bool live = r < R;
+    const int row0 = tile * J.tile_rows;
+    const int row1 = min(row0 + J.tile_rows, J.n);
+    const int col0 = g * V;
+    const int nb = J.nbasis;
+    const bool has_extra = J.extra != nullptr;
+
+    Acc nrm[V], ex[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) { nrm[v].zero(); ex[v].zero(); }
+
+    if (live) {
+      T cf[NB > 0 ? NB : 1][V];
+      T yc[V];
+      bool unit = true;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        double a = J.ycoef[col0 + v];
+        yc[v] = T(a);
+        unit = unit && (a == 1.0);
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? T(J.coef[i * J.ld + col0 + v]) : T(0);
+
+      for (int row = row0 + r; row < row1; row += R) {
+        const size_t off = (size_t)row * J.ld + col0;
+        T o[V];
+        load_vec<T>(J.y + off, o);
+        if (!unit) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i < nb) {
+            T u[V];
+            load_vec<T>(J.basis[i] + off, u);
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[v], o[v]);
+          }
+        }
+        store_vec<T>(J.out + off, o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
+        if (has_extra) {
+          T u[V];
+          load_vec<T>(J.extra + off, u);
+#pragma unroll
+          for (int v = 0; v < V; ++v) ex[v].fma(u[v], o[v]);
+        }
+      }
+    }
+    cta_reduce_write<T, Acc>(smem, nrm, live, G, R, J.ld, J.part, J.ntiles, tile);
+    if (has_extra)
+      cta_reduce_write<T, Acc>(smem, ex, live, G, R, J.ld, J.part + (size_t)J.ld * J.ntiles,
+                               J.ntiles, tile);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Scalar kernels: one CTA per probe.
+// ---------------------------------------------------------------------------
+constexpr int kRedThreads = 128;
+
+// Sum of the ntiles partials of (dot d, column p) in a fixed order.
+__device__ double reduce_partials(const void* part, int f32, int ld, int ntiles, int d, int p,
+                                  double* sh_d, float2* sh_f) {
+  const int t = threadIdx.x;
+  if (!f32) {
+    const double* src = static_cast<const double*>(part) + ((size_t)d * ld + p) * ntiles;
+    AccD a;
+    a.zero();
+    for (int i = t; i < ntiles; i += blockDim.x) a.s += src[i];
+    sh_d[t] = a.s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (t < w) sh_d[t] += sh_d[t + w];
+      __syncthreads();
+    }
+    double r = sh_d[0];
+    __syncthreads();
+    return r;
+  } else {
+    const float2* src = static_cast<const float2*>(part) + ((size_t)d * ld + p) * ntiles;
+    AccF a;
+    a.zero();
+    for (int i = t; i < ntiles; i += blockDim.x) {
+      AccF o;
+      get_part(src + i, o);
+      a.add(o);
+    }
+    sh_f[t] = make_float2(a.s, a.e);
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if (t < w) {
+        AccF x, y;
+        get_part(&sh_f[t], x);
+        get_part(&sh_f[t + w], y);
+        x.add(y);
+        sh_f[t] = make_float2(x.s, x.e);
+      }
+      __syncthreads();
+    }
+    double r = (double)sh_f[0].x + (double)sh_f[0].y;
+    __syncthreads();
+    return r;
+  }
+}
+
+__device__ __forceinline__ int find_probe_job(const ScalarBatch& B, int gp) {
+  int j = 0;
+  while (j + 1 < B.njobs && gp >= B.probe_start[j + 1]) ++j;
+  return j;
+}
+
+// Power-of-two factor keeping the stored vectors near unit norm when sigma drifts.
+__device__ __forceinline__ double rescale_factor(double sigma, double lim) {
+  double l2 = log2(sigma);
+  if (fabs(l2) <= lim) return 1.0;
+  return exp2(rint(l2));
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_init_sigma(const __grid_constant__ ScalarBatch B) {
+  __shared__ double sh_d[kRedThreads];
+  __shared__ float2 sh_f[kRedThreads];
+  const int gp = blockIdx.x;
+  const int jb = find_probe_job(B, gp);
+  const ScalarJob& J = B.jobs[jb];
+  const int p = gp - B.probe_start[jb];
+  const KrylovState& S = J.st;
+  double nn = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 0, p, sh_d, sh_f);
+  if (threadIdx.x == 0) {
+    const int m2 = S.m + 2;
+    S.status[p] = 0;
+    S.meff[p] = 0;
+    if (nn > 0.0 && p < S.b) {
+      S.sig[p * m2 + 1] = 1.0 / sqrt(nn);
+      S.active[p] = 1;
+    } else {
+      S.sig[p * m2 + 1] = 0.0;
+      S.active[p] = 0;
+    }
+    if (S.edot) S.edot[p * m2 + 1] = nn;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_coef(const __grid_constant__ ScalarBatch B) {
+  __shared__ double sh_d[kRedThreads];
+  __shared__ float2 sh_f[kRedThreads];
+  __shared__ double D[kMaxWin];
+  const int gp = blockIdx.x;
+  const int jb = find_probe_job(B, gp);
+  const ScalarJob& J = B.jobs[jb];
+  const int p = gp - B.probe_start[jb];
+  const KrylovState& S = J.st;
+  for (int d = 0; d < J.ndots; ++d) {
+    double v = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, d, p, sh_d, sh_f);
+    if (threadIdx.x == 0) D[d] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int j = J.step;
+  const int m2 = S.m + 2;
+  const double* sg = S.sig + p * m2;
+  double* coef = S.coef;
+  if (!S.active[p]) {
+    S.ycoef[p] = 0.0;
+    for (int t = 0; t < kMaxWin; ++t) coef[t * S.ld + p] = 0.0;
+    return;
+  }
+  S.meff[p] = j;
+  const double sj = sg[j];
+  const double a = rescale_factor(sj, S.rescale_lim);
+  if (S.method == 0) {
+    const double al = sj * sj * D[0];
+    S.alpha[p * S.m + j - 1] = al;
+    if (j >= 2) {
+      coef[0 * S.ld + p] = a * S.beta[p * S.m + j - 2] * sg[j - 1] / sj;
+      coef[1 * S.ld + p] = a * al;
+    } else {
+      coef[0 * S.ld + p] = a * al;
+    }
+  } else {
+    double* Hc = S.H + (size_t)p * (S.m + 1) * S.m + (size_t)(j - 1) * (S.m + 1);
+    for (int t = 0; t < J.ndots; ++t) {
+      const int i = J.win_lo + t;
+      Hc[i - 1] = sg[i] * sj * D[t];
+      coef[t * S.ld + p] = a * sg[i] * sg[i] * D[t];
+    }
+  }
+  S.ycoef[p] = a;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_norm(const __grid_constant__ ScalarBatch B) {
+  __shared__ double sh_d[kRedThreads];
+  __shared__ float2 sh_f[kRedThreads];
+  const int gp = blockIdx.x;
+  const int jb = find_probe_job(B, gp);
+  const ScalarJob& J = B.jobs[jb];
+  const int p = gp - B.probe_start[jb];
+  const KrylovState& S = J.st;
+  double nn = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 0, p, sh_d, sh_f);
+  double ee = 0.0;
+  if (J.ndots > 1) ee = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 1, p, sh_d, sh_f);
+  if (threadIdx.x != 0) return;
+  if (!S.active[p]) return;
+  const int j = J.step;
+  const int m2 = S.m + 2;
+  double* sg = S.sig + p * m2;
+  const double a = S.ycoef[p];
+  const double h = sg[j] * sqrt(nn) / a;
+  bool stop;
+  if (S.method == 0) {
+    S.beta[p * S.m + j - 1] = h;
+    stop = !(h > S.tol);          // beta_j <= tol
+  } else {
+    S.H[(size_t)p * (S.m + 1) * S.m + (size_t)(j - 1) * (S.m + 1) + j] = h;
+    stop = h < S.tol;
+  }
+  if (stop) {
+    S.active[p] = 0;
+    S.status[p] |= LOGDET_ST_BREAKDOWN;
+    sg[j + 1] = 0.0;
+  } else {
+    sg[j + 1] = sg[j] / (a * h);
+  }
+  if (S.edot) S.edot[p * m2 + j + 1] = ee;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, int total_tiles) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  return std::max(1, std::min(total_tiles, per_sm * sm_count()));
+}
+
+template <typename T>
+int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
+  int nd = 0;
+  for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
+  using Acc = typename AccOf<T>::type;
+  size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+#define LD_SPMM_CASE(ND)                                                      \
+  {                                                                           \
+    auto kern = k_spmm<T, ND>;                                                \
+    int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
+    kern<<<grid, threads, smem, s>>>(b);                                      \
+    break;                                                                    \
+  }
+  do {
+    if (nd == 0) LD_SPMM_CASE(0)
+    if (nd == 1) LD_SPMM_CASE(1)
+    if (nd == 2) LD_SPMM_CASE(2)
+    if (nd <= 4) LD_SPMM_CASE(4)
+    LD_SPMM_CASE(kMaxWin)
+  } while (0);
+#undef LD_SPMM_CASE
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+template <typename T>
+int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
+  int nb = 0;
+  for (int j = 0; j < b.njobs; ++j) nb = std::max(nb, b.jobs[j].nbasis);
+  using Acc = typename AccOf<T>::type;
+  size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+#define LD_UPD_CASE(NB)                                                       \
+  {                                                                           \
+    auto kern = k_update<T, NB>;                                              \
+    int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
+    kern<<<grid, threads, smem, s>>>(b);                                      \
+    break;                                                                    \
+  }
+  do {
+    if (nb <= 1) LD_UPD_CASE(1)
+    if (nb == 2) LD_UPD_CASE(2)
+    if (nb <= 4) LD_UPD_CASE(4)
+    LD_UPD_CASE(kMaxWin)
+  } while (0);
+#undef LD_UPD_CASE
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+static int total_probes(const ScalarBatch& b) { return b.probe_start[b.njobs]; }
+
+int launch_coef(const ScalarBatch& b, cudaStream_t s) {
+  k_coef<<<total_probes(b), kRedThreads, 0, s>>>(b);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+int launch_norm(const ScalarBatch& b, cudaStream_t s) {
+  k_norm<<<total_probes(b), kRedThreads, 0, s>>>(b);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) {
+  k_init_sigma<<<total_probes(b), kRedThreads, 0, s>>>(b);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
+template int launch_spmm<double>(const SpmmBatch<double>&, int, cudaStream_t);
+template int launch_spmm<float>(const SpmmBatch<float>&, int, cudaStream_t);
+template int launch_update<double>(const UpdBatch<double>&, int, cudaStream_t);
+template int launch_update<float>(const UpdBatch<float>&, int, cudaStream_t);
+
+}  // namespace ld

@@ -1,0 +1,133 @@
+// Krylov step kernels: the per-step block passes and the per-probe scalar
+// updates shared by Lanczos (OSLQ, Sec. 3.1) and Arnoldi-IOP (Algorithm 1).
+//
+// Vectors are stored unnormalised: the basis vector v_j of probe p is
+// sigma_j[p] * u_j[:, p], with u_j the stored column and sigma_j a per-probe
+// FP64 scalar.  One step j of a block of probes is
+//
+//   pass 1  (k_spmm)    y = A u_j                     (A = Q/alpha or Q/gamma)
+//                       d_i = u_i^T y  for the window vectors u_i
+//   scalar  (k_coef)    H_{i,j} = sigma_i sigma_j d_i  (Lanczos: alpha_j)
+//                       coefficients of pass 2
+//   pass 2  (k_update)  u_{j+1} = a (y - sum_i c_i u_i),  |u_{j+1}|^2 [, u_1^T u_{j+1}]
+//   scalar  (k_norm)    h = sigma_j |u_{j+1}| / a, sigma_{j+1} = sigma_j / (a h)
+//
+// a is 1 unless sigma drifts out of range, then an exact power of two.  In
+// exact arithmetic this is the normalised recurrence of the paper: only the
+// rounding of the stored vectors differs.
+//
+// Every kernel takes a batch of independent jobs (blocks of probes, possibly
+// on different matrices) in one launch; a single solve is a batch of one.
+// Per-tile partial sums are reduced in a fixed order, so a job's result does
+// not depend on what else is in the batch.
+#pragma once
+
+#include "common.cuh"
+
+namespace ld {
+
+constexpr int kMaxWin = 9;    // window vectors per pass (window k <= 8, plus slack)
+constexpr int kMaxJobs = 24;  // jobs per batched launch
+
+// ---------------------------------------------------------------------------
+// pass 1: SpMM with fused window dots
+// ---------------------------------------------------------------------------
+template <typename T>
+struct SpmmJob {
+  const int* rowptr;
+  const int* colind;
+  const T* vals;
+  const T* x;                      // gather source, n x ld
+  T* y;                            // output, n x ld (may be null: dots only is not supported)
+  const T* dotv[kMaxWin];          // vectors dotted with y, n x ld each
+  typename PartOf<T>::type* part;  // [ndots][ld][ntiles]
+  const double* colscale;          // optional [ld]: y[:,p] *= colscale[p]
+  const double* colshift;          // optional [ld]: y[:,p] += colshift[p] * x[:,p] (before scale)
+  int n, ld, ndots, tile_rows, ntiles;
+};
+
+template <typename T>
+struct SpmmBatch {
+  int njobs, total_tiles;
+  int tile_start[kMaxJobs + 1];
+  SpmmJob<T> jobs[kMaxJobs];
+};
+
+// ---------------------------------------------------------------------------
+// pass 2: window update with fused norm (and optional dot with u_1)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct UpdJob {
+  const T* y;
+  const T* basis[kMaxWin];
+  const double* coef;              // [nbasis][ld]
+  const double* ycoef;             // [ld]
+  T* out;
+  const T* extra;                  // optional: dot out with extra
+  typename PartOf<T>::type* part;  // [1 or 2][ld][ntiles]
+  int n, ld, nbasis, tile_rows, ntiles;
+};
+
+template <typename T>
+struct UpdBatch {
+  int njobs, total_tiles;
+  int tile_start[kMaxJobs + 1];
+  UpdJob<T> jobs[kMaxJobs];
+};
+
+// ---------------------------------------------------------------------------
+// per-probe scalar state of one Krylov run over a block (device arrays)
+// ---------------------------------------------------------------------------
+struct KrylovState {
+  int method;        // 0 = Lanczos (3-term), 1 = IOP window k
+  int b, ld, m, k;   // probes, leading dim, max steps, window
+  double tol;
+  double rescale_lim;  // |log2 sigma| beyond which a power-of-two rescale is applied
+  double* alpha;     // Lanczos: [p*m + j-1]
+  double* beta;      // Lanczos: [p*m + j-1]  (beta_j, j = 1..m-1)
+  double* H;         // IOP: [p*(m+1)*m + (j-1)*(m+1) + (i-1)]  column-major H(i,j)
+  double* sig;       // [p*(m+2) + j]  sigma_j, j = 1..m+1
+  double* edot;      // optional [p*(m+2) + j]  u_1^T u_j
+  double* coef;      // [kMaxWin][ld]  pass-2 coefficients (window order)
+  double* ycoef;     // [ld]
+  int* meff;         // [p] completed steps
+  int* active;       // [p]
+  uint32_t* status;  // [p] status bits
+};
+
+struct ScalarJob {
+  KrylovState st;
+  const void* part;   // partials to reduce
+  int part_f32;       // 1 = float2 (compensated FP32) partials
+  int ntiles;
+  int step;           // j (1-based)
+  int ndots;          // number of dots in part
+  int win_lo;         // first window index i (1-based) for IOP / Lanczos
+  int last;           // 1 = last step (no pass 2 follows)
+};
+
+struct ScalarBatch {
+  int njobs;
+  int probe_start[kMaxJobs + 1];
+  ScalarJob jobs[kMaxJobs];
+};
+
+// Tile geometry for a block of leading dimension ld with elements of
+// `vec` entries per 16-byte load: threads per CTA and rows per tile.
+struct TileGeom {
+  int threads;   // CTA size
+  int rows_per_iter;
+  int tile_rows;
+};
+TileGeom tile_geom(int ld, int vec);
+
+// Launchers (krylov.cu).  `grid_cap` bounds the persistent grid.
+template <typename T> int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s);
+template <typename T> int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s);
+int launch_coef(const ScalarBatch& b, cudaStream_t s);
+int launch_norm(const ScalarBatch& b, cudaStream_t s);
+int launch_init_sigma(const ScalarBatch& b, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace ld

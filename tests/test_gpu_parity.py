@@ -1,0 +1,299 @@
+"""CUDA path (through the C-ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances: bit-exact for the probe entries and for SpMM on integer-valued
+data; relative log-determinant error <= 1e-10 for the FP64 path (the oracle's
+own summation-order sensitivity is ~1e-15 on these operators); <= 1e-4 for the
+mixed FP32 path against the FP64 CUDA path with the same seed.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_07004_gb300 import binding as B  # noqa: E402
+
+RTOL_FP64 = 1e-10
+RTOL_MIXED = 1e-4
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# step rows
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,ncols,col0,ld", [(1000, 7, 0, 8), (4097, 20, 3, 20), (1, 1, 0, 2)])
+def test_probe_fill_bit_exact(n, ncols, col0, ld):
+    out = torch.full((n * ld,), 7.0, dtype=torch.float64, device="cuda")
+    B.logdet_probe_fill(123, 1, n, ncols, col0, out, ld)
+    got = out.view(n, ld).cpu().numpy()
+    want = O.rademacher_block(123, 1, n, ncols, col0)
+    assert np.array_equal(got[:, :ncols], want)
+    assert np.all(got[:, ncols:] == 0.0)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: W.laplacian_2d(37, 23, shift=2.0),
+    lambda: W.laplacian_3d(9, 7, 5, shift=1.0),
+    lambda: W.powerlaw_graph_laplacian(5003, seed=2).with_diagonal_shift(3.0),
+])
+def test_spmm_integer_bit_exact(maker):
+    A = maker()
+    b, ld = 13, 14
+    X = np.zeros((A.n, ld))
+    X[:, :b] = O.rademacher_block(5, 0, A.n, b)
+    with B.Handle.from_csr(A) as h:
+        y = torch.zeros(A.n * ld, dtype=torch.float64, device="cuda")
+        h.spmm(cuda(X.ravel()), y, b, ld)
+        got = y.view(A.n, ld).cpu().numpy()
+    want = A.to_scipy() @ X
+    assert np.array_equal(got, want)
+
+
+def test_gershgorin_on_device_matches_oracle():
+    for A in (W.laplacian_2d(64, shift=0.1), W.matern_2d(30, 0.05)):
+        with B.Handle.from_csr(A) as h:
+            n, nnz, lo, hi = h.info()
+        olo, ohi = O.gershgorin_interval(A.to_scipy())
+        assert (n, nnz) == (A.n, A.nnz)
+        assert lo == pytest.approx(olo, rel=1e-14, abs=1e-14)
+        assert hi == pytest.approx(ohi, rel=1e-14)
+
+
+@pytest.mark.parametrize("n,s", [(3001, 20), (257, 40), (70, 64)])
+def test_orth_matches_thin_qr(n, s):
+    rng = np.random.default_rng(n + s)
+    Y = rng.standard_normal((n, s)) @ np.diag(np.logspace(0, 2, s))
+    ld = s + 2
+    Yd = np.zeros((n, ld))
+    Yd[:, :s] = Y
+    yd = cuda(Yd.ravel())
+    ad = torch.zeros(n * ld, dtype=torch.float64, device="cuda")
+    s_eff = B.logdet_orth(n, s, yd, ld, ad, ld)
+    A = ad.view(n, ld).cpu().numpy()[:, :s]
+    assert s_eff == s
+    assert np.max(np.abs(A - O.orth(Y))) < 1e-12
+
+
+def test_orth_rank_deficient_drops_column():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((500, 6))
+    Y[:, 3] = Y[:, 0] - 2 * Y[:, 1]
+    yd = cuda(Y.ravel())
+    ad = torch.zeros(500 * 6, dtype=torch.float64, device="cuda")
+    assert B.logdet_orth(500, 6, yd, 6, ad, 6) == 5
+    A = ad.view(500, 6).cpu().numpy()
+    assert np.all(A[:, 3] == 0.0)
+    keep = [0, 1, 2, 4, 5]
+    assert np.max(np.abs(A[:, keep] - O.orth(Y))) < 1e-12
+
+
+def test_gauss_quadrature_matches_eigh_tridiagonal():
+    rng = np.random.default_rng(1)
+    nprobe, m = 37, 60
+    ms = rng.integers(1, m + 1, nprobe).astype(np.int32)
+    ms[0], ms[1] = m, 1
+    al = np.zeros((nprobe, m))
+    be = np.zeros((nprobe, m))
+    for p in range(nprobe):
+        # Lanczos coefficients of a real operator: positive definite T.
+        A = W.laplacian_2d(8 + p % 5, shift=0.05 + 0.1 * p).to_scipy()
+        a_, b_ = O.lanczos(A / 9.0, rng.standard_normal(A.shape[0]), int(ms[p]))
+        ms[p] = a_.size
+        al[p, :a_.size] = a_
+        be[p, :b_.size] = b_
+    out = torch.zeros(nprobe, dtype=torch.float64, device="cuda")
+    st = B.logdet_gauss_quadrature_log(cuda(al.ravel()), cuda(be.ravel()), cuda(ms, torch.int32),
+                                       m, nprobe, 1e-300, out)
+    got = out.cpu().numpy()
+    assert st == 0
+    for p in range(nprobe):
+        want = O.gauss_quadrature_log(al[p, :ms[p]], be[p, :ms[p] - 1]).value
+        assert abs(got[p] - want) <= 1e-12 * max(1.0, abs(want)), p
+
+
+@pytest.mark.parametrize("k", [2, 4, 8, 30])
+def test_hessenberg_log_matches_logm(k):
+    Q = W.laplacian_3d(10, shift=0.01).to_scipy()
+    lo, hi = O.spectral_interval(Q)
+    gamma = math.sqrt(lo * hi)
+    nprobe, m = 12, 30
+    ldh = m + 1
+    Hs = np.zeros((nprobe, m, ldh))  # per probe column-major (m columns of length ldh)
+    ms = np.zeros(nprobe, dtype=np.int32)
+    want = []
+    for p in range(nprobe):
+        v = O.rademacher_block(p, 0, Q.shape[0], 1)[:, 0]
+        run = O.arnoldi_iop(Q / gamma, v, m - (p % 4), k=k)
+        me = run.m_eff
+        ms[p] = me
+        Hs[p, :me, :me] = run.H.T
+        want.append(np.real(sla.logm(run.H))[:, 0])
+    c = torch.zeros(nprobe * m, dtype=torch.float64, device="cuda")
+    st = B.logdet_hessenberg_log_e1(cuda(Hs.ravel()), ldh, cuda(ms, torch.int32), m, nprobe, c)
+    got = c.view(nprobe, m).cpu().numpy()
+    assert st == 0
+    for p in range(nprobe):
+        w = want[p]
+        assert np.max(np.abs(got[p, :ms[p]] - w)) <= 1e-11 * max(1.0, np.max(np.abs(w))), p
+        assert np.all(got[p, ms[p]:] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+
+def _compare(est, res, tol=RTOL_FP64):
+    assert rel(res.logdet, est.logdet) <= tol, (res.logdet, est.logdet)
+    s = est.s_eff
+    np.testing.assert_allclose(res.per_probe[:s], est.per_probe[:s], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(res.z_norm2, est.z_norm2, rtol=1e-12)
+    np.testing.assert_allclose(res.per_probe[res.s:], est.per_probe[s:], rtol=0, atol=1e-9)
+
+
+def test_oslq_64x64_laplacian_parity():
+    A = W.laplacian_2d(64, shift=0.1)
+    est = O.oslq(A.to_scipy(), 30, 30, seed=0)
+    with B.Handle.from_csr(A) as h:
+        res = h.oslq(30, 30, seed=0)
+    assert (res.s, res.r, res.s_eff) == (10, 10, 10)
+    assert res.steps_min == res.steps_max == 30
+    assert res.log_alpha == pytest.approx(est.log_alpha, rel=1e-15)
+    _compare(est, res)
+
+
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_osaiop_parity(k):
+    A = W.laplacian_2d(40, 37, shift=0.05)
+    est = O.osaiop(A.to_scipy(), 30, 25, k=k, seed=3)
+    with B.Handle.from_csr(A) as h:
+        res = h.osaiop(30, 25, iop_window=k, seed=3)
+    assert res.log_gamma == pytest.approx(est.log_gamma, rel=1e-15)
+    _compare(est, res)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_ragged_sizes_and_odd_probe_count(method):
+    A = W.laplacian_3d(11, 9, 10, shift=0.02)   # n = 990: several tiles plus a ragged tail
+    P = 31                                      # s = 10, r = 11, block width 21 (odd)
+    if method == "oslq":
+        est = O.oslq(A.to_scipy(), P, 17, seed=9)
+        with B.Handle.from_csr(A) as h:
+            res = h.oslq(P, 17, seed=9)
+    else:
+        est = O.osaiop(A.to_scipy(), P, 17, k=3, seed=9)
+        with B.Handle.from_csr(A) as h:
+            res = h.osaiop(P, 17, iop_window=3, seed=9)
+    assert (res.s, res.r) == (10, 11)
+    _compare(est, res)
+
+
+def test_powerlaw_graph_parity():
+    A = W.powerlaw_graph_laplacian(6000, seed=4).with_diagonal_shift(0.05)
+    est = O.oslq(A.to_scipy(), 12, 20, seed=1)
+    with B.Handle.from_csr(A) as h:
+        res = h.oslq(12, 20, seed=1)
+    _compare(est, res)
+    est = O.osaiop(A.to_scipy(), 12, 20, k=4, seed=1)
+    with B.Handle.from_csr(A) as h:
+        res = h.osaiop(12, 20, iop_window=4, seed=1)
+    _compare(est, res)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_identity_breaks_down_and_is_exact(method):
+    A = W.scaled_identity(300, 2.5)
+    with B.Handle.from_csr(A) as h:
+        res = h.oslq(9, 10) if method == "oslq" else h.osaiop(9, 10, iop_window=2)
+    assert res.steps_max == 1
+    assert res.status_bits & B.ST_BREAKDOWN
+    assert res.logdet == pytest.approx(300 * math.log(2.5), rel=1e-13)
+
+
+def test_diagonal_exact_at_distinct_count():
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 7.0], 40)
+    A = W.diagonal_matrix(d)
+    est = O.oslq(A.to_scipy(), 12, 5, seed=2)
+    with B.Handle.from_csr(A) as h:
+        res = h.oslq(12, 5, seed=2)
+    _compare(est, res)
+
+
+def test_single_step_and_tiny_matrix():
+    A = W.laplacian_2d(3, shift=1.0)      # n = 9
+    for P, m in ((9, 1), (29, 7)):        # 29 probes: s = 9 >= n, residual vanishes
+        est = O.oslq(A.to_scipy(), P, m, seed=1)
+        with B.Handle.from_csr(A) as h:
+            res = h.oslq(P, m, seed=1)
+        assert res.s_eff == est.s_eff
+        assert rel(res.logdet, est.logdet) <= RTOL_FP64
+    est = O.osaiop(A.to_scipy(), 29, 7, k=2, seed=1)
+    with B.Handle.from_csr(A) as h:
+        res = h.osaiop(29, 7, iop_window=2, seed=1)
+    assert rel(res.logdet, est.logdet) <= RTOL_FP64
+
+
+def test_caller_spectral_bounds():
+    A = W.laplacian_2d(20, shift=0.3)
+    lam = (0.3, 8.3)
+    est = O.osaiop(A.to_scipy(), 15, 12, k=2, seed=4, lam=lam)
+    with B.Handle.from_csr(A) as h:
+        res = h.osaiop(15, 12, iop_window=2, seed=4, lam=lam)
+    assert rel(res.logdet, est.logdet) <= RTOL_FP64
+
+
+def test_create_device_matches_host():
+    A = W.laplacian_2d(50, shift=0.2)
+    rp, ci, vv = cuda(A.rowptr, torch.int32), cuda(A.colind, torch.int32), cuda(A.vals)
+    with B.logdet_create_device(A.n, rp, ci, vv) as hd, B.Handle.from_csr(A) as hh:
+        r1 = hd.oslq(15, 10, seed=5)
+        r2 = hh.oslq(15, 10, seed=5)
+    assert r1.logdet == r2.logdet
+
+
+@pytest.mark.parametrize("method,k", [("oslq", 0), ("osaiop", 2), ("osaiop", 4)])
+def test_mixed_precision_within_1e4_of_fp64(method, k):
+    A = W.laplacian_2d(64, shift=0.1)
+    with B.Handle.from_csr(A) as h:
+        f = h.oslq if method == "oslq" else (lambda *a, **kw: h.osaiop(*a, iop_window=k, **kw))
+        r64 = f(30, 30, seed=0)
+        r32 = f(30, 30, seed=0, precision=B.MIXED_FP32)
+    assert rel(r32.logdet, r64.logdet) <= RTOL_MIXED
+
+
+def test_invalid_arguments_are_errors():
+    A = W.laplacian_2d(10, shift=0.1)
+    with B.Handle.from_csr(A) as h:
+        for call in (lambda: h.oslq(2, 5), lambda: h.oslq(9, 101), lambda: h.oslq(9, 5, iop_window=3),
+                     lambda: h.osaiop(9, 5, iop_window=0), lambda: h.osaiop(9, 5, iop_window=9)):
+            with pytest.raises(B.LogdetError) as e:
+                call()
+            assert e.value.code == B.EINVAL
+    bad = W.laplacian_2d(4)
+    colind = bad.colind.copy()
+    colind[1], colind[2] = colind[2], colind[1]       # unsorted row
+    with pytest.raises(B.LogdetError):
+        B.Handle(bad.n, bad.rowptr, colind, bad.vals)
+    nodiag = W.laplacian_2d(4)
+    with pytest.raises(B.LogdetError):
+        B.Handle(nodiag.n, nodiag.rowptr, np.where(nodiag.colind == 0, 1, nodiag.colind), nodiag.vals)
+    neg = W.scaled_identity(5, -1.0)
+    with pytest.raises(B.LogdetError) as e:
+        B.Handle.from_csr(neg)
+    assert e.value.code == B.ENOTSPD
