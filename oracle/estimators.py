@@ -262,16 +262,21 @@ def iop_log_action(Qt, v, m_max: int, k: int, shift: float, tol: float = DEFAULT
 # ---------------------------------------------------------------------------
 
 def orth(Y: np.ndarray) -> np.ndarray:
-    """Thin QR factor of Y with diag(R) > 0; numerically dependent columns dropped (R14)."""
+    """Orthonormal basis of span(Y) (R14): the thin QR factor, diag(R) > 0, of Y
+    with its numerically dependent columns removed.  Columns are taken left to
+    right; column j is dependent when the R_jj of the QR of the kept columns
+    plus column j is at most RANK_TOL * max_i |y_i|."""
     Y = np.asarray(Y, dtype=np.float64)
     if Y.shape[1] == 0:
         return Y
-    Qf, R = np.linalg.qr(Y, mode="reduced")
-    d = np.diag(R)
     ref = float(np.max(np.linalg.norm(Y, axis=0)))
-    keep = np.abs(d) > RANK_TOL * ref
-    Qf = Qf[:, keep] * np.sign(d[keep])[None, :]
-    return Qf
+    kept = []
+    for j in range(Y.shape[1]):
+        _, R = np.linalg.qr(Y[:, kept + [j]], mode="reduced")
+        if R.shape[0] > len(kept) and abs(R[len(kept), len(kept)]) > RANK_TOL * ref:
+            kept.append(j)
+    Qf, R = np.linalg.qr(Y[:, kept], mode="reduced")
+    return Qf * np.sign(np.diag(R))[None, :]
 
 
 def _split(num_probes: int) -> tuple[int, int]:

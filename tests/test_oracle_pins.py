@@ -232,6 +232,13 @@ def test_orth_properties():
     assert np.allclose(A @ (A.T @ Y), Y, atol=1e-12)
     Y2 = np.concatenate([Y, Y[:, :2] @ np.array([[1.0], [2.0]])], axis=1)
     assert O.orth(Y2).shape[1] == 6
+    # A dependent column in the middle: the basis must still span every column.
+    Y3 = Y.copy()
+    Y3[:, 2] = Y[:, 0] - 3.0 * Y[:, 1]
+    A3 = O.orth(Y3)
+    assert A3.shape[1] == 5
+    assert np.allclose(A3.T @ A3, np.eye(5), atol=1e-14)
+    assert np.allclose(A3 @ (A3.T @ Y3), Y3, atol=1e-12)
 
 
 def _hadamard(n):
