@@ -1,0 +1,434 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the OSLQ / OSA-IOP hot path on one or more GPUs.
+
+Workload (one "step"): the 3D 7-point Dirichlet Laplacian on a 128^3 grid plus
+0.01 I (n = 2,097,152, nnz = 14,581,760, FP64 values), 60 Rademacher probes,
+50 Krylov steps; OSLQ once and OSA-IOP with windows k = 2, 4 and 8 -- four
+log-determinant solves that together run every step of the hot path (sketch,
+Hutch++ QR and projection, SpMM + window dots, window update + norms,
+tridiagonal Gauss rules, Hessenberg logarithms, assembly).
+
+  python bench.py [--gpus N --steps K --warmup W]           # CUDA path
+  python bench.py --impl reference [...]                    # FP64 CPU oracle
+
+Under torchrun every rank solves its own copy of the workload (independent
+problems, no data-path collective: weak scaling); the barrier and the max over
+ranks of the timed region use torch.distributed.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "logdet solves/s, p50/p99 at rel err ≤1e-4 vs FP64; SpMM+Krylov HBM GB/s"
+UNIT = "solves/s"
+GRID, SHIFT, PROBES, STEPS_M, WINDOWS = 128, 0.01, 60, 50, (2, 4, 8)
+SOLVES_PER_STEP = 1 + len(WINDOWS)
+# FP64 FMA peak of this GPU: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_spmm_fp64_laplacian3d_128.md")
+KRYLOV_SRC = os.path.join(ROOT, "paper_2606_07004_gb300", "csrc", "krylov.cu")
+
+
+def workload_config():
+    return {
+        "workload": f"3D 7-point Dirichlet Laplacian {GRID}^3 + {SHIFT} I (n=2097152, "
+                    "nnz=14581760), FP64; per step OSLQ + OSA-IOP k=2,4,8, m=50, 60 probes",
+        "matrix": "laplacian_3d", "grid": GRID, "shift": SHIFT, "n": GRID ** 3, "nnz": 14581760,
+        "num_probes": PROBES, "krylov_steps": STEPS_M, "iop_windows": list(WINDOWS),
+        "solves_per_step": SOLVES_PER_STEP, "seed": "1000 + step index",
+        "l2": "inputs larger than L2 (CSR 183 MB, 40-probe FP64 block 671 MB per vector)",
+        "parallelism": "replicas (one independent workload per GPU)",
+    }
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(ws, backend):
+    if ws <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(dist, x, device=None):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}", "--format=csv",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, names = [], [], set()
+        keys = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit():
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for k, v in zip(keys, parts[5:9]):
+                if v.lower() == "active":
+                    names.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(names)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(seed: int) -> dict:
+    """Time the FP64 oracle on a bounded sample of one step and extrapolate.
+
+    OSLQ: the full Hutch++ split (Y = J S, orth, projection) plus the Lanczos
+    quadrature of one range probe and one residual probe; a full solve is
+    split + 20 x (range probe) + 20 x (residual probe).  OSA-IOP (each k): one
+    L-action by Algorithm 1 (a residual probe) plus an orth + projection of a
+    same-size sketch; a full solve is 60 L-actions + that split.
+    """
+    import numpy as np
+    import oracle as O
+    from oracle import estimators as E
+    import workloads as W
+
+    A = W.laplacian_3d(GRID, shift=SHIFT)
+    Q = A.to_scipy()
+    n = A.n
+    s = PROBES // 3
+    r = PROBES - 2 * s
+    lo, hi = O.spectral_interval(Q)
+    out = {}
+    t0 = time.perf_counter()
+    J = Q / hi
+    S = O.rademacher_block(seed, 0, n, s)
+    G = O.rademacher_block(seed, 1, n, r)
+    Y = J @ S
+    Aq = O.orth(Y)
+    Z = G - Aq @ (Aq.T @ G)
+    t_split = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    al, be = O.lanczos(J, Aq[:, 0], STEPS_M)
+    O.gauss_quadrature_log(al, be)
+    t_q = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    al, be = O.lanczos(J, Z[:, 0], STEPS_M)
+    O.gauss_quadrature_log(al, be)
+    t_z = time.perf_counter() - t0
+    out["oslq"] = t_split + s * t_q + r * t_z
+    gamma = math.sqrt(lo * hi)
+    Qt = Q / gamma
+    shift = math.log(gamma / lo)
+    t0 = time.perf_counter()
+    Aq2 = O.orth(Y)
+    Aq2 @ (Aq2.T @ G)
+    t_sp = time.perf_counter() - t0          # the OSA-IOP split (orth + projection)
+    for k in WINDOWS:
+        t0 = time.perf_counter()
+        y = E.iop_log_action(Qt, Z[:, 0], STEPS_M, k, shift)
+        float(np.dot(Z[:, 0], y))
+        t_act = time.perf_counter() - t0
+        out[f"osaiop_k{k}"] = (2 * s + r) * t_act + t_sp
+    total = sum(out.values())
+    return {"est_solve_s": out, "est_step_s": total, "solves_per_s": SOLVES_PER_STEP / total}
+
+
+def run_oracle_sample_child(seed: int) -> dict:
+    """Run oracle_sample in a fresh single-threaded interpreter (BLAS threads = 1)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample-child",
+                        str(seed)], env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["wall_s"] = time.perf_counter() - t0
+    return res
+
+
+SAMPLE_DESC = ("FP64 NumPy/SciPy oracle, 1 thread: full Hutch++ split + 2 Lanczos probes for OSLQ, "
+               "1 Algorithm-1 L-action + orth/projection per OSA-IOP window; per-solve time "
+               "extrapolated to 40 Lanczos probes (OSLQ) and 60 L-actions (OSA-IOP)")
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return 0
+    vals, steps = [], []
+    for i in range(args.warmup + args.steps):
+        res = run_oracle_sample_child(1000 + i)
+        if i >= args.warmup:
+            vals.append(res["solves_per_s"])
+            steps.append(res["est_step_s"])
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": SAMPLE_DESC},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# CUDA arm
+# ---------------------------------------------------------------------------
+def traffic_from_profile():
+    """Per-launch DRAM bytes of the SpMM kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        text = open(PROFILE_MD).read()
+        src = hashlib.sha256(open(KRYLOV_SRC, "rb").read()).hexdigest()
+        m_src = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+        m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if m_src and m_tr and m_src.group(1) == src:
+            return float(m_tr.group(1))
+    except Exception:
+        pass
+    return None
+
+
+def d2h_bytes_per_step(n_blocks_gersh: int) -> int:
+    """Device-to-host bytes the library copies per step (counted from its copies)."""
+    s = PROBES // 3
+    b = PROBES
+    ld = b + (b % 2)
+    lds = s + (s % 2)
+    total = 2 * 8 * n_blocks_gersh + 4          # Gershgorin partials + flags (handle creation)
+    per_collect = ld * (8 + 4 + 4) + ld * (STEPS_M + 2) * 8
+    total += per_collect + 4 * s                  # OSLQ: results + kept-column flags
+    for _ in WINDOWS:
+        total += per_collect + 4 * s + 4 * lds    # OSA-IOP: + phase-1 status
+    return total
+
+
+def cuda_arm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(ws, "nccl")
+    dev = torch.device("cuda", local)
+    from paper_2606_07004_gb300 import binding as B
+    import workloads as W
+
+    A = W.laplacian_3d(GRID, shift=SHIFT)
+    stream = torch.cuda.Stream(device=dev)
+    h = B.Handle.from_csr(A)
+
+    def run_step(handle, seed, lat):
+        rs = [("oslq", handle.oslq(PROBES, STEPS_M, seed=seed, stream=stream))]
+        for k in WINDOWS:
+            rs.append((f"osaiop_k{k}", handle.osaiop(PROBES, STEPS_M, iop_window=k, seed=seed,
+                                                     stream=stream)))
+        for name, r in rs:
+            lat.setdefault(name, []).append(r.device_ms)
+        return rs
+
+    for i in range(args.warmup):
+        run_step(h, 1000 + i, {})
+    torch.cuda.synchronize()
+
+    # ---- device-timed region ----
+    lat = {}
+    clocks = ClockSampler(local)
+    B.logdet_profile_reset()
+    B.logdet_profile_enable(True)
+    launches0 = B.logdet_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        run_step(h, 1000 + args.warmup + i, lat)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    launches = B.logdet_launch_count() - launches0
+    B.logdet_profile_enable(False)
+    prof = B.profile_snapshot()
+    t_dev = e0.elapsed_time(e1) / 1e3
+    t_dev_max = max_over_ranks(dist, t_dev, dev)
+    value = SOLVES_PER_STEP * args.steps * ws / t_dev_max
+
+    # ---- end-to-end through the public API from pinned host buffers ----
+    rp = torch.from_numpy(A.rowptr).pin_memory().numpy()
+    ci = torch.from_numpy(A.colind).pin_memory().numpy()
+    vv = torch.from_numpy(A.vals).pin_memory().numpy()
+    h2d = rp.nbytes + ci.nbytes + vv.nbytes
+    e2e_steps = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        with B.Handle(A.n, rp, ci, vv) as he:
+            rs = run_step(he, 5000 + i, {})
+            _ = [float(r.logdet) for _, r in rs]
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0, dev)
+    e2e_value = SOLVES_PER_STEP * e2e_steps * ws / t_e2e
+    h.close()
+
+    pk, pk_kind = peaks()
+    sp = prof["spmm"]
+    achieved = sp["flops"] / (sp["ms"] / 1e3) / 1e12 if sp["ms"] > 0 else 0.0
+    kr_bytes = prof["spmm"]["bytes"] + prof["update"]["bytes"]
+    kr_ms = prof["spmm"]["ms"] + prof["update"]["ms"]
+    kr_gbs = kr_bytes / (kr_ms / 1e3) / 1e9 if kr_ms > 0 else 0.0
+    traffic = traffic_from_profile()
+    all_lat = sorted(x for v in lat.values() for x in v)
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(),
+        "roofline": {
+            "kernel": "k_spmm<double> (SpMM + fused window dots)",
+            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": traffic,
+            "peak_source": "FP64 FMA peak from unit counts and clock: 152 SMs x 2 DFMA/clk x "
+                           "2 flop x 2.070 GHz (a DFMA loop measured 1.20 TFLOP/s)",
+            "launches": sp["launches"], "avg_launch_ms": sp["ms"] / max(1, sp["launches"]),
+            "flops_per_launch": sp["flops"] / max(1, sp["launches"]),
+            "bytes_per_launch": sp["bytes"] / max(1, sp["launches"]),
+            "algorithmic_gbs": sp["bytes"] / (sp["ms"] / 1e3) / 1e9 if sp["ms"] > 0 else 0.0,
+        },
+        "krylov_hbm": {"algorithmic_gbs": kr_gbs, "peak_gbs": pk.get("hbm_gbs"),
+                       "frac": kr_gbs / pk.get("hbm_gbs", 6776.6),
+                       "peak_source": pk_kind,
+                       "note": "SpMM + update passes; FP64 here is ALU-bound, see roofline"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": d2h_bytes_per_step(min((A.n + 255) // 256, 4 * 152)),
+                "steps": e2e_steps,
+                "includes": "logdet_create from pinned host CSR (validation, H2D, Gershgorin), "
+                            "4 solves, results to host, logdet_destroy"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "latency_ms": {k: {"p50": pct(v, 0.5), "p99": pct(v, 0.99), "mean": statistics.mean(v)}
+                       for k, v in lat.items()},
+        "latency_ms_all": {"p50": pct(all_lat, 0.5), "p99": pct(all_lat, 0.99)},
+        "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        try:
+            res = run_oracle_sample_child(1000)
+            line["cpu_baseline"] = {"value": res["solves_per_s"], "unit": UNIT, "cores": 1,
+                                    "kind": "oracle", "sample": SAMPLE_DESC,
+                                    "est_solve_s": res["est_solve_s"], "wall_s": res["wall_s"]}
+        except Exception as e:  # reported, not hidden
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": SAMPLE_DESC, "error": str(e)[:300]}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample-child", type=int, default=None, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample_child is not None:
+        print(json.dumps(oracle_sample(args.oracle_sample_child)))
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    return cuda_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -194,6 +194,32 @@ int logdet_hessenberg_log_e1(const double* H_dev, int32_t ldh, const int32_t* ms
                              int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
                              void* cuda_stream);
 
+/* ---- instrumentation (the paper has no counterpart: it reports only
+ * wall-clock seconds per solve) -------------------------------------------
+ * logdet_launch_count: kernels this process has launched through the library.
+ * logdet_profile_enable(1): from then on every launch is bracketed by CUDA
+ * events on its own stream and tagged with a class and its algorithmic work
+ * (FLOPs and the bytes it must move once: CSR once, each vector once).
+ * logdet_profile_read sums, for one class, the launches recorded since the
+ * last logdet_profile_reset: count, device milliseconds, FLOPs, bytes.  It
+ * waits for the recorded events.  Classes: 0 SpMM pass, 1 update pass,
+ * 2 per-probe scalar kernels, 3 Cholesky QR, 4 residual projection,
+ * 5 small solves (Gauss rules, Hessenberg logs), 6 other.
+ */
+#define LOGDET_KC_SPMM    0
+#define LOGDET_KC_UPDATE  1
+#define LOGDET_KC_SCALAR  2
+#define LOGDET_KC_QR      3
+#define LOGDET_KC_PROJECT 4
+#define LOGDET_KC_SMALL   5
+#define LOGDET_KC_OTHER   6
+#define LOGDET_KC_COUNT   7
+int64_t logdet_launch_count(void);
+int logdet_profile_enable(int on);
+int logdet_profile_reset(void);
+int logdet_profile_read(int32_t kclass, int64_t* launches, double* device_ms, double* flops,
+                        double* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -270,6 +270,9 @@ def orth(Y: np.ndarray) -> np.ndarray:
     if Y.shape[1] == 0:
         return Y
     ref = float(np.max(np.linalg.norm(Y, axis=0)))
+    Qf, R = np.linalg.qr(Y, mode="reduced")
+    if R.shape[0] == Y.shape[1] and np.all(np.abs(np.diag(R)) > RANK_TOL * ref):
+        return Qf * np.sign(np.diag(R))[None, :]        # full rank: one QR suffices
     kept = []
     for j in range(Y.shape[1]):
         _, R = np.linalg.qr(Y[:, kept + [j]], mode="reduced")

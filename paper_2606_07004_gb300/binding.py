@@ -38,7 +38,9 @@ EXPORTED = [
     "logdet_oslq", "logdet_osaiop",
     "logdet_probe_fill", "logdet_spmm", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
+    "logdet_launch_count", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
 ]
+KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
 
 
 class logdet_result(C.Structure):
@@ -86,6 +88,11 @@ _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+_sig("logdet_launch_count", C.c_int64, [])
+_sig("logdet_profile_enable", C.c_int, [C.c_int])
+_sig("logdet_profile_reset", C.c_int, [])
+_sig("logdet_profile_read", C.c_int, [_i32, C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl),
+                                      C.POINTER(_dbl)])
 
 
 class LogdetError(RuntimeError):
@@ -272,6 +279,29 @@ def logdet_hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, stream=None) -> int:
                                          C.byref(st), _stream(stream)),
            "logdet_hessenberg_log_e1")
     return st.value
+
+
+def logdet_launch_count() -> int:
+    return int(_lib.logdet_launch_count())
+
+
+def logdet_profile_enable(on: bool = True):
+    _check(_lib.logdet_profile_enable(1 if on else 0), "logdet_profile_enable")
+
+
+def logdet_profile_reset():
+    _check(_lib.logdet_profile_reset(), "logdet_profile_reset")
+
+
+def logdet_profile_read(kclass: int) -> dict:
+    n, ms, fl, by = _i64(), _dbl(), _dbl(), _dbl()
+    _check(_lib.logdet_profile_read(kclass, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by)),
+           "logdet_profile_read")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+
+
+def profile_snapshot() -> dict:
+    return {name: logdet_profile_read(i) for i, name in enumerate(KC_NAMES)}
 
 
 def exported_symbols() -> list[str]:

@@ -1,6 +1,7 @@
 // Dense and small-matrix kernels (see dense.cuh).  All arithmetic is FP64.
 #include "dense.cuh"
 #include "krylov.cuh"
+#include "profile.cuh"
 
 #include <algorithm>
 #include <vector>
@@ -199,6 +200,10 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
   const double* src = Y;
   int ldsrc = ldy;
   for (int round = 0; round < 2; ++round) {
+    ProfScope prof(KC_QR, st, 2.0 * n * (double)s * s * 2.0, 2.0 * 8.0 * n * s);
+    prof_count();
+    prof_count();
+    prof_count();
     k_gram<<<grid_for(ntiles), kGramThreads, 0, st>>>(src, ldsrc, n, s, ntiles, part);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<npairs, 128, 0, st>>>(part, ntiles, s, C);
@@ -310,6 +315,9 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
   const int ntiles = div_up(n, kGramRows);
   double* part = ws;
   double* Bm = ws + (size_t)s * r * ntiles;
+  ProfScope prof(KC_PROJECT, st, 4.0 * n * (double)s * r, 8.0 * n * (2.0 * s + r));
+  prof_count();
+  prof_count();
   if (s > 0) {
     k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, ntiles, part);
     LD_CHECK_LAUNCH();
@@ -372,6 +380,7 @@ int colnorm_partials(const T* X, int n, int ld, int tile_rows, int ntiles,
                      typename PartOf<T>::type* part, int threads, cudaStream_t st) {
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+  ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ld, (double)n * ld * sizeof(T));
   k_colnorm<T><<<grid_for(ntiles), threads, smem, st>>>(X, n, ld, tile_rows, ntiles, part);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
@@ -467,6 +476,7 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
     set_error("gauss quadrature: m=%d must be in [1, %d]", m, kMaxSteps);
     return LOGDET_EINVAL;
   }
+  ProfScope prof(KC_SMALL, st);
   k_gauss_quad<<<div_up(nprobe, 32), 32, 0, st>>>(alpha, beta, ldab, msteps, m, nprobe,
                                                    clamp_lo, out, status);
   LD_CHECK_LAUNCH();
@@ -702,6 +712,7 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
     return LOGDET_EINVAL;
   }
   static const GLRule gl = gauss_legendre01();
+  ProfScope prof(KC_SMALL, st);
   k_hesslog<<<nprobe, kLogThreads, 0, st>>>(H, ldh, msteps, m, c, ldc, ws, status, gl);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
@@ -724,6 +735,7 @@ __global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, i
 
 template <typename T>
 int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st) {
+  ProfScope prof(KC_OTHER, st, 0.0, (double)n * ld * sizeof(T));
   k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, n, ncols, col0, out, ld);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
@@ -744,6 +756,7 @@ __global__ void k_convert(const Tin* in, int ldin, Tout* out, int ldout, int n, 
 template <typename Tin, typename Tout>
 int convert_block(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols,
                   cudaStream_t st) {
+  ProfScope prof(KC_OTHER, st, 0.0, (double)n * (ldin * sizeof(Tin) + ldout * sizeof(Tout)));
   k_convert<Tin, Tout><<<4 * sm_count(), 256, 0, st>>>(in, ldin, out, ldout, n, cols);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
@@ -773,6 +786,7 @@ __global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ld, int m,
 template <typename T>
 int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y, int ldy,
                     cudaStream_t st) {
+  ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ld * m, (double)n * ld * (m * sizeof(T) + 8.0));
   k_sketch_assemble<T><<<8 * sm_count(), 256, 0, st>>>(V, n, ld, m, w, Y, ldy);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;

@@ -3,6 +3,7 @@
 #include "dense.cuh"
 #include "handle.cuh"
 #include "krylov.cuh"
+#include "profile.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -86,8 +87,9 @@ template <> constexpr double rescale_limit<float>() { return 20.0; }
 // Vfull non-null the basis is kept: u_j = Vfull + (j-1)*n*ld and X0 == Vfull.
 // track_e: accumulate u_1^T u_j for the OSA-IOP quadratic forms.
 template <typename T>
-int krylov_block(const int* rowptr, const int* colind, const T* vals, int n, int b, int ld, int m,
-                 int k, int method, bool track_e, T* X0, T* Vfull, KState& ks, cudaStream_t st) {
+int krylov_block(const int* rowptr, const int* colind, const T* vals, int n, long long nnz, int b,
+                 int ld, int m, int k, int method, bool track_e, T* X0, T* Vfull, KState& ks,
+                 cudaStream_t st) {
   using Part = typename PartOf<T>::type;
   constexpr bool f32 = std::is_same<T, float>::value;
   const TileGeom g = tile_geom(ld, Vec16<T>::N);
@@ -140,6 +142,8 @@ int krylov_block(const int* rowptr, const int* colind, const T* vals, int n, int
   pj.part = part.p;
   pj.n = n;
   pj.ld = ld;
+  pj.b = b;
+  pj.nnz = nnz;
   pj.tile_rows = g.tile_rows;
   pj.ntiles = ntiles;
 
@@ -157,6 +161,7 @@ int krylov_block(const int* rowptr, const int* colind, const T* vals, int n, int
   uj.part = part.p;
   uj.n = n;
   uj.ld = ld;
+  uj.b = b;
   uj.tile_rows = g.tile_rows;
   uj.ntiles = ntiles;
 
@@ -348,7 +353,7 @@ int oslq_impl(logdet_ctx* h, const SolveCfg& c, SolveOut& o, cudaStream_t st) {
   }
   KState ks(st);
   LD_TRY(ks.alloc(0, b, ld, c.m, 2, c.tol, rescale_limit<T>()));
-  LD_TRY(krylov_block<T>(h->rowptr, h->colind, jv.p, n, b, ld, c.m, 2, 0, false, X0, nullptr, ks, st));
+  LD_TRY(krylov_block<T>(h->rowptr, h->colind, jv.p, n, h->nnz, b, ld, c.m, 2, 0, false, X0, nullptr, ks, st));
   DevBuf<double> K(st);
   LD_TRY(K.alloc(ld));
   LD_TRY(gauss_quadrature_log(ks.alpha.p, ks.beta.p, c.m, ks.meff.p, c.m, ld, lo / alpha, K.p,
@@ -410,13 +415,14 @@ int osaiop_impl(logdet_ctx* h, const SolveCfg& c, SolveOut& o, cudaStream_t st) 
     LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
     KState k1(st);
     LD_TRY(k1.alloc(1, s, lds, m, kk, c.tol, rescale_limit<T>()));
-    LD_TRY(krylov_block<T>(h->rowptr, h->colind, qv.p, n, s, lds, m, kk, 1, false, Vst.p, Vst.p,
+    LD_TRY(krylov_block<T>(h->rowptr, h->colind, qv.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p, Vst.p,
                            k1, st));
     DevBuf<double> cc(st), ws(st), w(st);
     LD_TRY(cc.alloc((size_t)lds * m));
     LD_TRY(ws.alloc(hesslog_workspace_doubles(m, lds)));
     LD_TRY(w.alloc((size_t)m * lds));
     LD_TRY(hessenberg_log_e1(k1.H.p, m + 1, k1.meff.p, m, lds, cc.p, m, ws.p, k1.status.p, st));
+    prof_count();
     k_iop_weights<<<div_up(m * lds, 256), 256, 0, st>>>(cc.p, m, k1.sig.p, k1.edot.p, k1.meff.p, m,
                                                         lds, shift, w.p);
     LD_CHECK_LAUNCH();
@@ -443,12 +449,13 @@ int osaiop_impl(logdet_ctx* h, const SolveCfg& c, SolveOut& o, cudaStream_t st) 
   // Phase 2: quadratic forms of L on [A | Z].
   KState k2(st);
   LD_TRY(k2.alloc(1, b, ld, m, kk, c.tol, rescale_limit<T>()));
-  LD_TRY(krylov_block<T>(h->rowptr, h->colind, qv.p, n, b, ld, m, kk, 1, true, X0, nullptr, k2, st));
+  LD_TRY(krylov_block<T>(h->rowptr, h->colind, qv.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr, k2, st));
   DevBuf<double> cc(st), ws(st), qf(st);
   LD_TRY(cc.alloc((size_t)ld * m));
   LD_TRY(ws.alloc(hesslog_workspace_doubles(m, ld)));
   LD_TRY(qf.alloc(ld));
   LD_TRY(hessenberg_log_e1(k2.H.p, m + 1, k2.meff.p, m, ld, cc.p, m, ws.p, k2.status.p, st));
+  prof_count();
   k_iop_qf<<<div_up(ld, 64), 64, 0, st>>>(cc.p, m, k2.sig.p, k2.edot.p, k2.meff.p, m, ld, shift, qf.p);
   LD_CHECK_LAUNCH();
   std::vector<double> qh, e1;

@@ -1,5 +1,6 @@
 // Krylov step kernels (see krylov.cuh for the recurrence they implement).
 #include "krylov.cuh"
+#include "profile.cuh"
 
 #include <algorithm>
 
@@ -416,6 +417,15 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+  double flops = 0.0, bytes = 0.0;
+  for (int j = 0; j < b.njobs; ++j) {
+    const SpmmJob<T>& J = b.jobs[j];
+    const double vb = (double)J.n * J.b * sizeof(T);
+    const int extra_reads = J.ndots - ((J.ndots > 0 && J.dotv[0] == J.x) ? 1 : 0);
+    flops += 2.0 * (double)J.nnz * J.b + 2.0 * (double)J.n * J.b * J.ndots;
+    bytes += 4.0 * (J.n + 1) + (double)J.nnz * (4 + sizeof(T)) + vb * (2 + extra_reads);
+  }
+  ProfScope prof(KC_SPMM, s, flops, bytes);
 #define LD_SPMM_CASE(ND)                                                      \
   {                                                                           \
     auto kern = k_spmm<T, ND>;                                                \
@@ -441,6 +451,15 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
   for (int j = 0; j < b.njobs; ++j) nb = std::max(nb, b.jobs[j].nbasis);
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+  double flops = 0.0, bytes = 0.0;
+  for (int j = 0; j < b.njobs; ++j) {
+    const UpdJob<T>& J = b.jobs[j];
+    const int ex = J.extra ? 1 : 0;
+    const double vb = (double)J.n * J.b * sizeof(T);
+    flops += 2.0 * (double)J.n * J.b * (J.nbasis + 1 + ex);
+    bytes += vb * (2 + J.nbasis + ex);
+  }
+  ProfScope prof(KC_UPDATE, s, flops, bytes);
 #define LD_UPD_CASE(NB)                                                       \
   {                                                                           \
     auto kern = k_update<T, NB>;                                              \
@@ -462,16 +481,19 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
 static int total_probes(const ScalarBatch& b) { return b.probe_start[b.njobs]; }
 
 int launch_coef(const ScalarBatch& b, cudaStream_t s) {
+  ProfScope prof(KC_SCALAR, s);
   k_coef<<<total_probes(b), kRedThreads, 0, s>>>(b);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
 int launch_norm(const ScalarBatch& b, cudaStream_t s) {
+  ProfScope prof(KC_SCALAR, s);
   k_norm<<<total_probes(b), kRedThreads, 0, s>>>(b);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
 int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) {
+  ProfScope prof(KC_SCALAR, s);
   k_init_sigma<<<total_probes(b), kRedThreads, 0, s>>>(b);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;

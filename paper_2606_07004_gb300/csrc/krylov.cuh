@@ -44,6 +44,8 @@ struct SpmmJob {
   const double* colscale;          // optional [ld]: y[:,p] *= colscale[p]
   const double* colshift;          // optional [ld]: y[:,p] += colshift[p] * x[:,p] (before scale)
   int n, ld, ndots, tile_rows, ntiles;
+  int b;                           // live columns (accounting only)
+  long long nnz;                   // (accounting only)
 };
 
 template <typename T>
@@ -66,6 +68,7 @@ struct UpdJob {
   const T* extra;                  // optional: dot out with extra
   typename PartOf<T>::type* part;  // [1 or 2][ld][ntiles]
   int n, ld, nbasis, tile_rows, ntiles;
+  int b;                           // live columns (accounting only)
 };
 
 template <typename T>

@@ -2,6 +2,7 @@
 // scaled value copies, error plumbing and the step-level SpMM entry point.
 #include "handle.cuh"
 #include "krylov.cuh"
+#include "profile.cuh"
 
 #include <cstdarg>
 #include <cstring>
@@ -91,6 +92,7 @@ static int compute_gershgorin(logdet_ctx* h, bool check_structure) {
   LD_TRY(hi.alloc(blocks));
   LD_TRY(fl.alloc(1));
   LD_CUDA(cudaMemsetAsync(fl.p, 0, sizeof(int), h->stream));
+  ProfScope prof(KC_OTHER, h->stream);
   if (h->vals_dtype == LOGDET_VALS_F64)
     k_gershgorin<double><<<blocks, 256, 0, h->stream>>>(h->rowptr, h->colind, (const double*)h->vals,
                                                        h->n, h->nnz, lo.p, hi.p, fl.p);
@@ -228,6 +230,7 @@ __global__ void k_scale_vals(const Vin* __restrict__ in, long long nnz, double c
 template <typename T>
 int scaled_values(logdet_ctx* h, double c, T* out, cudaStream_t st) {
   const int blocks = 4 * sm_count();
+  ProfScope prof(KC_OTHER, st);
   if (h->vals_dtype == LOGDET_VALS_F64)
     k_scale_vals<double, T><<<blocks, 256, 0, st>>>((const double*)h->vals, h->nnz, c, out);
   else
@@ -256,6 +259,8 @@ int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const
   J.n = n;
   J.ld = ld;
   J.ndots = 0;
+  J.b = ld;
+  J.nnz = 0;
   J.tile_rows = g.tile_rows;
   J.ntiles = div_up(n, g.tile_rows);
   B.tile_start[0] = 0;
