@@ -413,6 +413,25 @@ def cuda_arm(args):
     return 0
 
 
+def small_case(args):
+    """One OSLQ (m=12) and one OSA-IOP (k=4, m=12) solve with 60 probes on the 3D
+    Laplacian 100^3 + 0.01 I: the capture target for ncu (blocks larger than
+    L2, about 3 GB on the device)."""
+    import torch
+    from paper_2606_07004_gb300 import binding as B
+    import workloads as W
+    A = W.laplacian_3d(100, shift=SHIFT, dtype=__import__("numpy").float32 if args.small_case_fp32
+                       else __import__("numpy").float64)
+    prec = B.MIXED_FP32 if args.small_case_fp32 else B.FP64
+    with B.Handle.from_csr(A) as h:
+        r1 = h.oslq(PROBES, 12, seed=1, precision=prec)
+        r2 = h.osaiop(PROBES, 12, iop_window=4, seed=1, precision=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"small_case": True, "oslq": r1.logdet, "osaiop_k4": r2.logdet,
+                      "oslq_ms": r1.device_ms, "osaiop_ms": r2.device_ms}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,8 +439,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small-case", action="store_true",
+                    help="one OSLQ + one OSA-IOP solve on a 100^3 Laplacian (profiling target)")
+    ap.add_argument("--small-case-fp32", action="store_true", help="the small case in mixed FP32")
     ap.add_argument("--oracle-sample-child", type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.small_case or args.small_case_fp32:
+        return small_case(args)
     if args.oracle_sample_child is not None:
         print(json.dumps(oracle_sample(args.oracle_sample_child)))
         return 0

@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
                                                        double* __restrict__ part) {
   __shared__ double sy[kGramChunk * kMaxSketch];
   const int npairs = s * (s + 1) / 2;
+  // Pairs owned by this thread: threadIdx.x + q * blockDim.x for q < nq.
+  const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
   int pi[kGramNP], pj[kGramNP];
 #pragma unroll
   for (int q = 0; q < kGramNP; ++q) {
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
       for (int r = 0; r < rows; ++r) {
 #pragma unroll
         for (int q = 0; q < kGramNP; ++q)
-          acc[q] = fma(sy[r * s + pi[q]], sy[r * s + pj[q]], acc[q]);
+          if (q < nq) acc[q] = fma(sy[r * s + pi[q]], sy[r * s + pj[q]], acc[q]);
       }
     }
 #pragma unroll
@@ -239,6 +241,14 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
   __shared__ double sa[kGramChunk * kMaxSketch];
   __shared__ double sg[kGramChunk * kMaxSketch];
   const int npairs = s * r;
+  const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
+  int pi[kProjNP], pj[kProjNP];
+#pragma unroll
+  for (int q = 0; q < kProjNP; ++q) {
+    int idx = threadIdx.x + q * blockDim.x;
+    pi[q] = idx < npairs ? idx / r : 0;
+    pj[q] = idx < npairs ? idx - (idx / r) * r : 0;
+  }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     double acc[kProjNP];
 #pragma unroll
@@ -259,13 +269,8 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
       __syncthreads();
       for (int rr = 0; rr < rows; ++rr) {
 #pragma unroll
-        for (int q = 0; q < kProjNP; ++q) {
-          int idx = threadIdx.x + q * blockDim.x;
-          if (idx < npairs) {
-            int i = idx / r, j = idx - i * r;
-            acc[q] = fma(sa[rr * s + i], sg[rr * r + j], acc[q]);
-          }
-        }
+        for (int q = 0; q < kProjNP; ++q)
+          if (q < nq) acc[q] = fma(sa[rr * s + pi[q]], sg[rr * r + pj[q]], acc[q]);
       }
     }
 #pragma unroll
@@ -505,16 +510,23 @@ __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
   if (threadIdx.x == 0) s_ok = true;
   for (int k = 0; k < m; ++k) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int p = k;
-      double best = fabs(A[k * m + k]);
-      for (int i = k + 1; i < m; ++i) {
-        double v = fabs(A[i * m + k]);
-        if (v > best) { best = v; p = i; }
+    if (threadIdx.x < 32) {  // pivot: largest |A_ik|, i >= k, smallest index on ties
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + (int)threadIdx.x; i < m; i += 32) {
+        const double v = fabs(A[i * m + k]);
+        if (v > best) { best = v; bi = i; }
       }
-      s_piv = p;
-      perm[k] = p;
-      if (best == 0.0) s_ok = false;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        s_piv = bi;
+        perm[k] = bi;
+        if (!(best > 0.0)) s_ok = false;
+      }
     }
     __syncthreads();
     const int p = s_piv;
@@ -581,7 +593,8 @@ __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restric
                                                          double* __restrict__ cout, int ldc,
                                                          double* __restrict__ ws,
                                                          uint32_t* __restrict__ status,
-                                                         GLRule gl) {
+                                                         GLRule gl, int use_smem) {
+  extern __shared__ double dyn[];
   __shared__ double red[kLogThreads];
   __shared__ int perm[kMaxSteps];
   __shared__ double fcol[kMaxSteps];
@@ -595,8 +608,8 @@ __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restric
     for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = 0.0;
     return;
   }
-  const size_t mm = (size_t)mmax * mmax;
-  double* Yb = ws + (size_t)p * 4 * mm;  // current matrix A (square-rooted in place)
+  const size_t mm = use_smem ? (size_t)m * m : (size_t)mmax * mmax;
+  double* Yb = use_smem ? dyn : ws + (size_t)p * 4 * mm;  // current matrix (square-rooted in place)
   double* Mb = Yb + mm;
   double* Wb = Mb + mm;
   double* Tb = Wb + mm;
@@ -712,8 +725,14 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
     return LOGDET_EINVAL;
   }
   static const GLRule gl = gauss_legendre01();
+  // Four m x m work matrices per CTA: in shared memory when they fit.
+  const size_t smem = 4 * sizeof(double) * (size_t)m * m;
+  const int use_smem = smem <= 200 * 1024;
+  if (use_smem && smem > 48 * 1024)
+    LD_CUDA(cudaFuncSetAttribute(k_hesslog, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope prof(KC_SMALL, st);
-  k_hesslog<<<nprobe, kLogThreads, 0, st>>>(H, ldh, msteps, m, c, ldc, ws, status, gl);
+  k_hesslog<<<nprobe, kLogThreads, use_smem ? smem : 0, st>>>(H, ldh, msteps, m, c, ldc, ws, status,
+                                                              gl, use_smem);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }

@@ -33,10 +33,12 @@ struct SolveOut {
 struct KState {
   DevBuf<double> alpha, beta, H, sig, edot, coef, ycoef;
   DevBuf<int> meff, active;
-  DevBuf<uint32_t> status;
+  DevBuf<uint32_t> status, cnt;
+  DevBuf<double> dbuf;
   KrylovState st{};
   explicit KState(cudaStream_t s)
-      : alpha(s), beta(s), H(s), sig(s), edot(s), coef(s), ycoef(s), meff(s), active(s), status(s) {}
+      : alpha(s), beta(s), H(s), sig(s), edot(s), coef(s), ycoef(s), meff(s), active(s), status(s),
+        cnt(s), dbuf(s) {}
   int alloc(int method, int b, int ld, int m, int k, double tol, double rescale_lim) {
     if (method == 0) {
       LD_TRY(alpha.alloc((size_t)ld * m));
@@ -54,6 +56,9 @@ struct KState {
     LD_TRY(meff.alloc(ld));
     LD_TRY(active.alloc(ld));
     LD_TRY(status.alloc(ld));
+    LD_TRY(cnt.alloc(ld));
+    LD_TRY(dbuf.alloc((size_t)kMaxWin * ld));
+    LD_TRY(cnt.zero());
     LD_TRY(sig.zero());
     LD_TRY(edot.zero());
     LD_TRY(coef.zero());
@@ -74,6 +79,8 @@ struct KState {
     st.meff = meff.p;
     st.active = active.p;
     st.status = status.p;
+    st.cnt = cnt.p;
+    st.dbuf = dbuf.p;
     return LOGDET_OK;
   }
 };

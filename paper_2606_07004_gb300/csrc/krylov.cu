@@ -231,53 +231,54 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 }
 
 // ---------------------------------------------------------------------------
-// Scalar kernels: one CTA per probe.
+// Scalar kernels.  One CTA per (probe, dot) reduces that dot's ntiles
+// partials in a fixed order; the last CTA of a probe to finish (an arrival
+// counter behind a fence) runs the probe's scalar recurrence on the reduced
+// values.  Which CTA arrives last does not change any value.
 // ---------------------------------------------------------------------------
-constexpr int kRedThreads = 128;
+constexpr int kRedThreads = 256;
+constexpr int kRedLanes = 4;  // independent accumulators per thread
 
-// Sum of the ntiles partials of (dot d, column p) in a fixed order.
-__device__ double reduce_partials(const void* part, int f32, int ld, int ntiles, int d, int p,
-                                  double* sh_d, float2* sh_f) {
+enum ScalarKind { SK_INIT = 0, SK_COEF = 1, SK_NORM = 2 };
+
+// Sum of the ntiles partials of (dot d, column p): thread t adds tiles
+// t + blockDim*(kRedLanes*i + l) into accumulator l, the lanes are combined in
+// order, then a shared-memory tree.  Returns the value to every thread.
+template <typename Acc, typename PartT>
+__device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, int p,
+                                  Acc* sh) {
   const int t = threadIdx.x;
-  if (!f32) {
-    const double* src = static_cast<const double*>(part) + ((size_t)d * ld + p) * ntiles;
-    AccD a;
-    a.zero();
-    for (int i = t; i < ntiles; i += blockDim.x) a.s += src[i];
-    sh_d[t] = a.s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (t < w) sh_d[t] += sh_d[t + w];
-      __syncthreads();
-    }
-    double r = sh_d[0];
-    __syncthreads();
-    return r;
-  } else {
-    const float2* src = static_cast<const float2*>(part) + ((size_t)d * ld + p) * ntiles;
-    AccF a;
-    a.zero();
-    for (int i = t; i < ntiles; i += blockDim.x) {
-      AccF o;
-      get_part(src + i, o);
-      a.add(o);
-    }
-    sh_f[t] = make_float2(a.s, a.e);
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-      if (t < w) {
-        AccF x, y;
-        get_part(&sh_f[t], x);
-        get_part(&sh_f[t + w], y);
-        x.add(y);
-        sh_f[t] = make_float2(x.s, x.e);
+  const PartT* src = part + ((size_t)d * ld + p) * ntiles;
+  Acc a[kRedLanes];
+#pragma unroll
+  for (int l = 0; l < kRedLanes; ++l) a[l].zero();
+  const int stride = blockDim.x * kRedLanes;
+  for (int base = t; base < ntiles; base += stride) {
+#pragma unroll
+    for (int l = 0; l < kRedLanes; ++l) {
+      const int i = base + l * blockDim.x;
+      if (i < ntiles) {
+        Acc o;
+        get_part(src + i, o);
+        a[l].add(o);
       }
-      __syncthreads();
     }
-    double r = (double)sh_f[0].x + (double)sh_f[0].y;
-    __syncthreads();
-    return r;
   }
+#pragma unroll
+  for (int l = 1; l < kRedLanes; ++l) a[0].add(a[l]);
+  sh[t] = a[0];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      Acc x = sh[t];
+      x.add(sh[t + w]);
+      sh[t] = x;
+    }
+    __syncthreads();
+  }
+  const double r = sh[0].value();
+  __syncthreads();
+  return r;
 }
 
 __device__ __forceinline__ int find_probe_job(const ScalarBatch& B, int gp) {
@@ -293,45 +294,24 @@ __device__ __forceinline__ double rescale_factor(double sigma, double lim) {
   return exp2(rint(l2));
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_init_sigma(const __grid_constant__ ScalarBatch B) {
-  __shared__ double sh_d[kRedThreads];
-  __shared__ float2 sh_f[kRedThreads];
-  const int gp = blockIdx.x;
-  const int jb = find_probe_job(B, gp);
-  const ScalarJob& J = B.jobs[jb];
-  const int p = gp - B.probe_start[jb];
+__device__ void scalar_init(const ScalarJob& J, int p, const double* D) {
   const KrylovState& S = J.st;
-  double nn = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 0, p, sh_d, sh_f);
-  if (threadIdx.x == 0) {
-    const int m2 = S.m + 2;
-    S.status[p] = 0;
-    S.meff[p] = 0;
-    if (nn > 0.0 && p < S.b) {
-      S.sig[p * m2 + 1] = 1.0 / sqrt(nn);
-      S.active[p] = 1;
-    } else {
-      S.sig[p * m2 + 1] = 0.0;
-      S.active[p] = 0;
-    }
-    if (S.edot) S.edot[p * m2 + 1] = nn;
+  const double nn = D[0];
+  const int m2 = S.m + 2;
+  S.status[p] = 0;
+  S.meff[p] = 0;
+  if (nn > 0.0 && p < S.b) {
+    S.sig[p * m2 + 1] = 1.0 / sqrt(nn);
+    S.active[p] = 1;
+  } else {
+    S.sig[p * m2 + 1] = 0.0;
+    S.active[p] = 0;
   }
+  if (S.edot) S.edot[p * m2 + 1] = nn;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_coef(const __grid_constant__ ScalarBatch B) {
-  __shared__ double sh_d[kRedThreads];
-  __shared__ float2 sh_f[kRedThreads];
-  __shared__ double D[kMaxWin];
-  const int gp = blockIdx.x;
-  const int jb = find_probe_job(B, gp);
-  const ScalarJob& J = B.jobs[jb];
-  const int p = gp - B.probe_start[jb];
+__device__ void scalar_coef(const ScalarJob& J, int p, const double* D) {
   const KrylovState& S = J.st;
-  for (int d = 0; d < J.ndots; ++d) {
-    double v = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, d, p, sh_d, sh_f);
-    if (threadIdx.x == 0) D[d] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
   const int j = J.step;
   const int m2 = S.m + 2;
   const double* sg = S.sig + p * m2;
@@ -364,19 +344,11 @@ __global__ void __launch_bounds__(kRedThreads) k_coef(const __grid_constant__ Sc
   S.ycoef[p] = a;
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_norm(const __grid_constant__ ScalarBatch B) {
-  __shared__ double sh_d[kRedThreads];
-  __shared__ float2 sh_f[kRedThreads];
-  const int gp = blockIdx.x;
-  const int jb = find_probe_job(B, gp);
-  const ScalarJob& J = B.jobs[jb];
-  const int p = gp - B.probe_start[jb];
+__device__ void scalar_norm(const ScalarJob& J, int p, const double* D) {
   const KrylovState& S = J.st;
-  double nn = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 0, p, sh_d, sh_f);
-  double ee = 0.0;
-  if (J.ndots > 1) ee = reduce_partials(J.part, J.part_f32, S.ld, J.ntiles, 1, p, sh_d, sh_f);
-  if (threadIdx.x != 0) return;
   if (!S.active[p]) return;
+  const double nn = D[0];
+  const double ee = J.ndots > 1 ? D[1] : 0.0;
   const int j = J.step;
   const int m2 = S.m + 2;
   double* sg = S.sig + p * m2;
@@ -398,6 +370,43 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(const __grid_constant__ Sc
     sg[j + 1] = sg[j] / (a * h);
   }
   if (S.edot) S.edot[p * m2 + j + 1] = ee;
+}
+
+template <typename Acc, typename PartT>
+__device__ void scalar_body(const ScalarBatch& B, int kind, Acc* sh) {
+  __shared__ int s_last;
+  const int gp = blockIdx.x;
+  const int d = blockIdx.y;
+  const int jb = find_probe_job(B, gp);
+  const ScalarJob& J = B.jobs[jb];
+  const int p = gp - B.probe_start[jb];
+  if (d >= J.ndots) return;
+  const KrylovState& S = J.st;
+  const double v = reduce_partials<Acc, PartT>(static_cast<const PartT*>(J.part), S.ld, J.ntiles,
+                                               d, p, sh);
+  if (threadIdx.x == 0) {
+    S.dbuf[d * S.ld + p] = v;
+    __threadfence();
+    const unsigned ticket = atomicAdd(S.cnt + p, 1u);
+    s_last = ticket == (unsigned)(J.ndots - 1);
+    if (s_last) {
+      S.cnt[p] = 0;
+      __threadfence();
+      double D[kMaxWin];
+      for (int t = 0; t < J.ndots; ++t) D[t] = __ldcg(S.dbuf + t * S.ld + p);
+      if (kind == SK_INIT) scalar_init(J, p, D);
+      else if (kind == SK_COEF) scalar_coef(J, p, D);
+      else scalar_norm(J, p, D);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_scalar(const __grid_constant__ ScalarBatch B,
+                                                        int kind, int f32) {
+  __shared__ AccD shd[kRedThreads];
+  __shared__ AccF shf[kRedThreads];
+  if (f32) scalar_body<AccF, float2>(B, kind, shf);
+  else scalar_body<AccD, double>(B, kind, shd);
 }
 
 // ---------------------------------------------------------------------------
@@ -480,24 +489,18 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
 
 static int total_probes(const ScalarBatch& b) { return b.probe_start[b.njobs]; }
 
-int launch_coef(const ScalarBatch& b, cudaStream_t s) {
+static int launch_scalar(const ScalarBatch& b, int kind, cudaStream_t s) {
+  int nd = 1, f32 = b.jobs[0].part_f32;
+  for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
   ProfScope prof(KC_SCALAR, s);
-  k_coef<<<total_probes(b), kRedThreads, 0, s>>>(b);
+  k_scalar<<<dim3(total_probes(b), nd), kRedThreads, 0, s>>>(b, kind, f32);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
-int launch_norm(const ScalarBatch& b, cudaStream_t s) {
-  ProfScope prof(KC_SCALAR, s);
-  k_norm<<<total_probes(b), kRedThreads, 0, s>>>(b);
-  LD_CHECK_LAUNCH();
-  return LOGDET_OK;
-}
-int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) {
-  ProfScope prof(KC_SCALAR, s);
-  k_init_sigma<<<total_probes(b), kRedThreads, 0, s>>>(b);
-  LD_CHECK_LAUNCH();
-  return LOGDET_OK;
-}
+
+int launch_coef(const ScalarBatch& b, cudaStream_t s) { return launch_scalar(b, SK_COEF, s); }
+int launch_norm(const ScalarBatch& b, cudaStream_t s) { return launch_scalar(b, SK_NORM, s); }
+int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) { return launch_scalar(b, SK_INIT, s); }
 
 template int launch_spmm<double>(const SpmmBatch<double>&, int, cudaStream_t);
 template int launch_spmm<float>(const SpmmBatch<float>&, int, cudaStream_t);

@@ -96,6 +96,8 @@ struct KrylovState {
   int* meff;         // [p] completed steps
   int* active;       // [p]
   uint32_t* status;  // [p] status bits
+  double* dbuf;      // [kMaxWin][ld] reduced dots of the current scalar step
+  unsigned* cnt;     // [ld] arrival counters (zero between launches)
 };
 
 struct ScalarJob {
