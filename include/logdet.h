@@ -194,6 +194,25 @@ int logdet_hessenberg_log_e1(const double* H_dev, int32_t ldh, const int32_t* ms
                              int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
                              void* cuda_stream);
 
+/* logdet_hessenberg_log_e1_noalloc: the same computation as
+ * logdet_hessenberg_log_e1, for callers that cannot allocate device memory
+ * while they run (inside a stream capture that must not gain allocation
+ * nodes, on hosts whose memory budget is fixed at start-up, or under an
+ * allocator that forbids cudaMalloc/cudaFree).  The paper has no counterpart;
+ * this is a deployment variant.  It allocates nothing: its scratch is a
+ * statically sized device array of 8 MiB + 16 KiB inside the library, which
+ * every GPU that loads the library holds until the process exits.  The first
+ * call on each device looks up that array's device address; make that first
+ * call before any stream capture.  Limits: nprobe <= 4096 and, for m >= 80
+ * (work matrices beyond shared memory), 4 m^2 nprobe <= 1048576; larger
+ * requests return LOGDET_EINVAL without running.  All calls share the one
+ * array, so calls whose kernels may overlap on the GPU (different streams
+ * with no ordering between them) race; order them on one stream.  Arguments,
+ * layouts and status bits as logdet_hessenberg_log_e1. */
+int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int32_t* msteps_dev,
+                                     int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
+                                     void* cuda_stream);
+
 /* ---- instrumentation (the paper has no counterpart: it reports only
  * wall-clock seconds per solve) -------------------------------------------
  * logdet_launch_count: kernels this process has launched through the library.

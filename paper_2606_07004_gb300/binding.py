@@ -39,6 +39,7 @@ EXPORTED = [
     "logdet_probe_fill", "logdet_spmm", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
+    "logdet_hessenberg_log_e1_noalloc",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
 
@@ -88,6 +89,8 @@ _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+_sig("logdet_hessenberg_log_e1_noalloc", C.c_int,
+     [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_launch_count", C.c_int64, [])
 _sig("logdet_profile_enable", C.c_int, [C.c_int])
 _sig("logdet_profile_reset", C.c_int, [])
@@ -278,6 +281,15 @@ def logdet_hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, stream=None) -> int:
     _check(_lib.logdet_hessenberg_log_e1(_ptr(H), ldh, _ptr(msteps), m, nprobe, _ptr(c),
                                          C.byref(st), _stream(stream)),
            "logdet_hessenberg_log_e1")
+    return st.value
+
+
+def logdet_hessenberg_log_e1_noalloc(H, ldh, msteps, m, nprobe, c, stream=None) -> int:
+    """Allocation-free variant of logdet_hessenberg_log_e1 (static scratch in the library)."""
+    st = _u32()
+    _check(_lib.logdet_hessenberg_log_e1_noalloc(_ptr(H), ldh, _ptr(msteps), m, nprobe, _ptr(c),
+                                                 C.byref(st), _stream(stream)),
+           "logdet_hessenberg_log_e1_noalloc")
     return st.value
 
 

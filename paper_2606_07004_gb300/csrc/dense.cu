@@ -4,6 +4,7 @@
 #include "profile.cuh"
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 namespace ld {
@@ -814,3 +815,101 @@ template int sketch_assemble<double>(const double*, int, int, int, const double*
 template int sketch_assemble<float>(const float*, int, int, int, const double*, double*, int, cudaStream_t);
 
 }  // namespace ld
+
+// ===========================================================================
+// Allocation-free Hessenberg logarithm.
+//
+// Some callers cannot allocate device memory while they run: code executing
+// inside a CUDA stream capture that must not add allocation nodes, real-time
+// or embedded hosts whose memory budget is fixed at start-up, and callers
+// running under an external allocator that forbids cudaMalloc/cudaFree on
+// their stream.  For them the same Hessenberg-log kernel can run on scratch
+// that lives in this file: a statically sized device array, loaded once with
+// the library and held by every GPU that loads it until the process exits.
+//
+// Limits: nprobe <= kNoAllocMaxProbes (status words), and when the four m x m
+// work matrices do not fit in shared memory (m >= 80), 4 m^2 nprobe doubles
+// must fit in kNoAllocMatDoubles (8 MiB).  Larger requests are rejected.
+// All calls share the one array; two calls whose kernels overlap on the GPU
+// (different streams, no ordering between them) race on it.
+// ===========================================================================
+namespace ld {
+
+constexpr size_t kNoAllocMatDoubles = (size_t)1 << 20;  // 8 MiB of work matrices
+constexpr int kNoAllocMaxProbes = 4096;                 // 16 KiB of status words
+constexpr size_t kNoAllocBytes = kNoAllocMatDoubles * sizeof(double) + kNoAllocMaxProbes * sizeof(uint32_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the first call on a device does it; make that first call
+// outside any stream capture).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  LD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal %d out of range for the allocation-free path", dev);
+    return LOGDET_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+      return LOGDET_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return LOGDET_OK;
+}
+}  // namespace
+
+}  // namespace ld
+
+extern "C" int logdet_hessenberg_log_e1_noalloc(const double* H, int32_t ldh,
+                                                const int32_t* msteps, int32_t m,
+                                                int32_t nprobe, double* c, uint32_t* status,
+                                                void* cuda_stream) {
+  using namespace ld;
+  if (!H || !c || m < 1 || m > kMaxSteps || nprobe < 1 || ldh < m) {
+    set_error("hessenberg_log_e1_noalloc: bad arguments (1 <= m <= %d, ldh >= m)", kMaxSteps);
+    return LOGDET_EINVAL;
+  }
+  if (nprobe > kNoAllocMaxProbes) {
+    set_error("hessenberg_log_e1_noalloc: nprobe=%d exceeds the static limit %d", nprobe,
+              kNoAllocMaxProbes);
+    return LOGDET_EINVAL;
+  }
+  const bool fits_smem = 4 * sizeof(double) * (size_t)m * m <= 200 * 1024;
+  if (!fits_smem && 4 * (size_t)m * m * nprobe > kNoAllocMatDoubles) {
+    set_error("hessenberg_log_e1_noalloc: 4*m^2*nprobe = %zu doubles exceeds the static "
+              "scratch of %zu doubles (m=%d, nprobe=%d)",
+              4 * (size_t)m * m * nprobe, kNoAllocMatDoubles, m, nprobe);
+    return LOGDET_EINVAL;
+  }
+  void* base = nullptr;
+  LD_TRY(noalloc_scratch(&base));
+  double* ws = static_cast<double*>(base);
+  uint32_t* st_words = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(base) +
+                                                   kNoAllocMatDoubles * sizeof(double));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // Status words accumulate with atomicOr: they must start at zero.  The work
+  // matrices are written before they are read and need no clearing.
+  LD_CUDA(cudaMemsetAsync(st_words, 0, sizeof(uint32_t) * nprobe, st));
+  LD_TRY(hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, m, ws, st_words, st));
+  uint32_t acc = 0, buf[256];
+  for (int p0 = 0; p0 < nprobe; p0 += 256) {
+    const int cnt = std::min(256, nprobe - p0);
+    LD_CUDA(cudaMemcpyAsync(buf, st_words + p0, sizeof(uint32_t) * cnt, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < cnt; ++i) acc |= buf[i];
+  }
+  if (status) *status = acc;
+  return LOGDET_OK;
+}
