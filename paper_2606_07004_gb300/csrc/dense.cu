@@ -428,9 +428,21 @@ __device__ double tridiag_gauss_log(double* d, double* e, double* z, int m, doub
     double x = d[lo] - mu;
     double bz = e[lo];
     for (int k = lo; k < hi; ++k) {
-      const double rr = hypot(x, bz);
-      const double c = (rr == 0.0) ? 1.0 : x / rr;
-      const double s = (rr == 0.0) ? 0.0 : -bz / rr;
+      // Givens pair (c, s) with c x - s bz = r, s x + c bz = 0: one reciprocal
+      // square root (the entries are O(1) for the scaled operators); hypot
+      // only for arguments near underflow.
+      const double rr2 = x * x + bz * bz;
+      double rr, c, s;
+      if (rr2 > 1e-280) {
+        const double ri = rsqrt(rr2);
+        rr = rr2 * ri;
+        c = x * ri;
+        s = -bz * ri;
+      } else {
+        rr = hypot(x, bz);
+        c = (rr == 0.0) ? 1.0 : x / rr;
+        s = (rr == 0.0) ? 0.0 : -bz / rr;
+      }
       if (k > lo) e[k - 1] = rr;
       const double a = d[k], b = e[k], cc = d[k + 1];
       d[k] = c * c * a - 2.0 * c * s * b + s * s * cc;
