@@ -147,44 +147,58 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
     const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
     if (live) {
       const T* xcol = J.x + col0;
-      // When the first dot vector is x itself its own-row entries come from
-      // the diagonal gather, which every row stores.
-      const bool dot0_x = ndots > 0 && J.dotv[0] == J.x;
       for (int row = row0 + r; row < row1; row += R) {
-        T s[V], xr[V];
+        T s[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) { s[v] = T(0); xr[v] = T(0); }
+        for (int v = 0; v < V; ++v) s[v] = T(0);
         const int q0 = s_rp[row - row0], q1 = s_rp[row - row0 + 1];
-        // Gathers in predicated batches of kGather: one memory round trip per
-        // batch.  Lanes past the row's end contribute fma(0, 0, s) = s.
-        for (int q = q0; q < q1; q += kGather) {
-          int c[kGather];
-          T a[kGather], xv[kGather][V];
+        if constexpr (sizeof(T) == 4) {
+          // HBM-bound: gathers in batches of kGather with no branches; a lane
+          // past the row's end re-reads the row's last column (a cached line)
+          // with weight 0, adding an exact zero.
+          for (int q = q0; q < q1; q += kGather) {
+            int c[kGather];
+            T a[kGather], xv[kGather][V];
 #pragma unroll
-          for (int u = 0; u < kGather; ++u) {
-            const bool in = q + u < q1;
-            c[u] = in ? colp[q + u] : -1;
-            a[u] = in ? valp[q + u] : T(0);
-          }
-#pragma unroll
-          for (int u = 0; u < kGather; ++u) {
-            if (c[u] >= 0) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
-            else {
-#pragma unroll
-              for (int v = 0; v < V; ++v) xv[u][v] = T(0);
+            for (int u = 0; u < kGather; ++u) {
+              const int qq = min(q + u, q1 - 1);
+              c[u] = colp[qq];
+              a[u] = (q + u < q1) ? valp[qq] : T(0);
             }
+#pragma unroll
+            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+#pragma unroll
+            for (int u = 0; u < kGather; ++u)
+#pragma unroll
+              for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
           }
+        } else {
+          // FP64-ALU-bound: exact count, batches of kGather plus a remainder.
+          int q = q0;
+          for (; q + kGather <= q1; q += kGather) {
+            int c[kGather];
+            T a[kGather], xv[kGather][V];
 #pragma unroll
-          for (int u = 0; u < kGather; ++u) {
+            for (int u = 0; u < kGather; ++u) { c[u] = colp[q + u]; a[u] = valp[q + u]; }
 #pragma unroll
-            for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
-            if (c[u] == row) {
+            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
 #pragma unroll
-              for (int v = 0; v < V; ++v) xr[v] = xv[u][v];
-            }
+            for (int u = 0; u < kGather; ++u)
+#pragma unroll
+              for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
+          }
+          for (; q < q1; ++q) {
+            const int c = colp[q];
+            const T a = valp[q];
+            T xv[V];
+            load_vec<T>(xcol + (size_t)c * J.ld, xv);
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
           }
         }
         if (has_shift || has_scale) {
+          T xr[V];
+          load_vec<T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             if (has_shift) s[v] = fma(T(J.colshift[col0 + v]), xr[v], s[v]);
@@ -196,12 +210,7 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
         for (int d = 0; d < NDOT; ++d) {
           if (d < ndots) {
             T u[V];
-            if (d == 0 && dot0_x) {
-#pragma unroll
-              for (int v = 0; v < V; ++v) u[v] = xr[v];
-            } else {
-              load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
-            }
+            load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
           }
@@ -510,6 +519,7 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
     auto kern = k_spmm<T, ND>;                                                \
     if (smem > 48 * 1024)                                                     \
       LD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+    LD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)); \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
     kern<<<grid, threads, smem, s>>>(b);                                      \
     break;                                                                    \
