@@ -316,7 +316,6 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 constexpr int kRedThreads = 256;
 constexpr int kRedLanes = 4;  // independent accumulators per thread
 
-enum ScalarKind { SK_INIT = 0, SK_COEF = 1, SK_NORM = 2 };
 
 // Sum of the ntiles partials of (dot d, column p): thread t adds tiles
 // t + blockDim*(kRedLanes*i + l) into accumulator l, the lanes are combined in

@@ -129,6 +129,7 @@ TileGeom tile_geom(int ld, int vec);
 // Launchers (krylov.cu).  `grid_cap` bounds the persistent grid.
 template <typename T> int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s);
 template <typename T> int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s);
+enum ScalarKind { SK_INIT = 0, SK_COEF = 1, SK_NORM = 2 };
 int launch_coef(const ScalarBatch& b, cudaStream_t s);
 int launch_norm(const ScalarBatch& b, cudaStream_t s);
 int launch_init_sigma(const ScalarBatch& b, cudaStream_t s);

@@ -1,0 +1,706 @@
+// Resumable OSLQ / OSA-IOP solves (see solve.cuh).
+#include "profile.cuh"
+#include "solve.cuh"
+
+#include <cmath>
+#include <cstring>
+
+namespace ld {
+
+// ---------------------------------------------------------------------------
+// configuration checks and spectral bounds
+// ---------------------------------------------------------------------------
+void spectral_bounds(const logdet_ctx* h, const SolveCfg& c, double& lo, double& hi) {
+  if (c.lam_lo > 0.0 && c.lam_hi > 0.0) {
+    lo = c.lam_lo;
+    hi = c.lam_hi;
+    return;
+  }
+  hi = h->g_hi;
+  lo = h->g_lo > 0.0 ? h->g_lo : kClampRel * hi;
+}
+
+int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
+  if (c.P < 3) { set_error("num_probes must be >= 3"); return LOGDET_EINVAL; }
+  if (c.m < 1 || c.m > h->n || c.m > kMaxSteps) {
+    set_error("krylov_steps=%d must be in [1, min(n, %d)]", c.m, kMaxSteps);
+    return LOGDET_EINVAL;
+  }
+  const int s = c.P / 3, r = c.P - 2 * s;
+  if (s > kMaxSketch || r > kMaxSketch) {
+    set_error("num_probes=%d: s and r must be <= %d", c.P, kMaxSketch);
+    return LOGDET_EINVAL;
+  }
+  if (c.method != 0 && c.method != 1) { set_error("method %d unknown", c.method); return LOGDET_EINVAL; }
+  if (c.method == 0 && !(c.k == 0 || c.k == 2)) {
+    set_error("OSLQ uses three-term Lanczos: iop_window must be 0 or 2");
+    return LOGDET_EINVAL;
+  }
+  if (c.method == 1 && (c.k < 1 || c.k > kMaxWin - 1)) {
+    set_error("iop_window=%d must be in [1, %d]", c.k, kMaxWin - 1);
+    return LOGDET_EINVAL;
+  }
+  if (c.precision != LOGDET_FP64 && c.precision != LOGDET_MIXED_FP32) {
+    set_error("precision %d unknown", c.precision);
+    return LOGDET_EINVAL;
+  }
+  double lo, hi;
+  spectral_bounds(h, c, lo, hi);
+  if (!(hi > 0.0) || !(lo > 0.0) || lo > hi) {
+    set_error("spectral bounds [%g, %g] invalid", lo, hi);
+    return LOGDET_ENOTSPD;
+  }
+  return LOGDET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// KState / KRun
+// ---------------------------------------------------------------------------
+int KState::alloc(int method, int b, int ld, int m, int k, double tol, double rescale_lim) {
+  if (method == 0) {
+    LD_TRY(alpha.alloc((size_t)ld * m));
+    LD_TRY(beta.alloc((size_t)ld * m));
+    LD_TRY(alpha.zero());
+    LD_TRY(beta.zero());
+  } else {
+    LD_TRY(H.alloc((size_t)ld * (m + 1) * m));
+    LD_TRY(H.zero());
+  }
+  LD_TRY(sig.alloc((size_t)ld * (m + 2)));
+  LD_TRY(edot.alloc((size_t)ld * (m + 2)));
+  LD_TRY(coef.alloc((size_t)kMaxWin * ld));
+  LD_TRY(ycoef.alloc(ld));
+  LD_TRY(dbuf.alloc((size_t)kMaxWin * ld));
+  LD_TRY(meff.alloc(ld));
+  LD_TRY(active.alloc(ld));
+  LD_TRY(status.alloc(ld));
+  LD_TRY(cnt.alloc(ld));
+  LD_TRY(cnt.zero());
+  LD_TRY(sig.zero());
+  LD_TRY(edot.zero());
+  LD_TRY(coef.zero());
+  st.method = method;
+  st.b = b;
+  st.ld = ld;
+  st.m = m;
+  st.k = k;
+  st.tol = tol;
+  st.rescale_lim = rescale_lim;
+  st.alpha = alpha.p;
+  st.beta = beta.p;
+  st.H = H.p;
+  st.sig = sig.p;
+  st.edot = edot.p;
+  st.coef = coef.p;
+  st.ycoef = ycoef.p;
+  st.meff = meff.p;
+  st.active = active.p;
+  st.status = status.p;
+  st.cnt = cnt.p;
+  st.dbuf = dbuf.p;
+  return LOGDET_OK;
+}
+
+template <typename T>
+int KRun<T>::init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
+                  int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol) {
+  rowptr = rp;
+  colind = ci;
+  vals = v;
+  n = n_;
+  nnz = nnz_;
+  b = b_;
+  ld = ld_;
+  m = m_;
+  k = k_;
+  method = method_;
+  track_e = track_e_;
+  X0 = X0_;
+  Vfull = Vfull_;
+  g = tile_geom(ld, Vec16<T>::N);
+  ntiles = div_up(n, g.tile_rows);
+  blk = (size_t)n * ld;
+  const int win = method == 0 ? 2 : k;
+  if (method == 1 && win > kMaxWin - 1) {
+    set_error("iop_window %d exceeds the supported maximum %d", k, kMaxWin - 1);
+    return LOGDET_EINVAL;
+  }
+  ndmax = std::max(win, 2);
+  nring = win + 1;
+  LD_TRY(part.alloc((size_t)ndmax * ld * ntiles));
+  LD_TRY(y.alloc(blk));
+  if (!Vfull) LD_TRY(ring.alloc(blk * nring));
+  LD_TRY(ks.alloc(method, b, ld, m, k, tol, rescale_limit<T>()));
+  LD_TRY(colnorm_partials<T>(X0, n, ld, g.tile_rows, ntiles, part.p, g.threads, st));
+  std::vector<ScalarJob> jobs{scalar_job(0, 1)};
+  std::vector<int> widths{ld};
+  return launch_scalar_jobs(jobs, widths, SK_INIT, st);
+}
+
+template <typename T>
+T* KRun<T>::ptr(int i) const {
+  if (Vfull) return Vfull + (size_t)(i - 1) * blk;
+  if (i == 1) return X0;
+  return ring.p + (size_t)((i - 2) % nring) * blk;
+}
+
+template <typename T>
+void KRun<T>::spmm_job(int j, SpmmJob<T>& J) const {
+  memset(&J, 0, sizeof J);
+  J.rowptr = rowptr;
+  J.colind = colind;
+  J.vals = vals;
+  J.x = ptr(j);
+  J.y = y.p;
+  J.part = part.p;
+  J.n = n;
+  J.ld = ld;
+  J.b = b;
+  J.nnz = nnz;
+  J.tile_rows = g.tile_rows;
+  J.ntiles = ntiles;
+  if (method == 0) {
+    J.ndots = 1;
+    J.dotv[0] = ptr(j);
+  } else {
+    const int lo = win_lo(j);
+    J.ndots = j - lo + 1;
+    for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
+  }
+}
+
+template <typename T>
+void KRun<T>::upd_job(int j, UpdJob<T>& U) const {
+  memset(&U, 0, sizeof U);
+  U.y = y.p;
+  U.coef = ks.coef.p;
+  U.ycoef = ks.ycoef.p;
+  U.extra = track_e ? X0 : nullptr;
+  U.part = part.p;
+  U.n = n;
+  U.ld = ld;
+  U.b = b;
+  U.tile_rows = g.tile_rows;
+  U.ntiles = ntiles;
+  if (method == 0) {
+    if (j >= 2) {
+      U.nbasis = 2;
+      U.basis[0] = ptr(j - 1);
+      U.basis[1] = ptr(j);
+    } else {
+      U.nbasis = 1;
+      U.basis[0] = ptr(j);
+    }
+  } else {
+    const int lo = win_lo(j);
+    U.nbasis = j - lo + 1;
+    for (int i = lo; i <= j; ++i) U.basis[i - lo] = ptr(i);
+  }
+  U.out = ptr(j + 1);
+}
+
+template <typename T>
+ScalarJob KRun<T>::scalar_job(int j, int ndots) const {
+  ScalarJob sj;
+  memset(&sj, 0, sizeof sj);
+  sj.st = ks.st;
+  sj.part = part.p;
+  sj.part_f32 = std::is_same<T, float>::value ? 1 : 0;
+  sj.ntiles = ntiles;
+  sj.step = j;
+  sj.ndots = ndots;
+  sj.win_lo = j >= 1 ? win_lo(j) : 1;
+  sj.last = j == m;
+  return sj;
+}
+
+template struct KRun<double>;
+template struct KRun<float>;
+
+// ---------------------------------------------------------------------------
+// batched launches
+// ---------------------------------------------------------------------------
+template <typename T>
+int launch_spmm_jobs(const std::vector<SpmmJob<T>>& jobs, int threads, cudaStream_t s) {
+  for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxJobs) {
+    SpmmBatch<T> B;
+    memset(&B, 0, sizeof B);
+    const int nj = (int)std::min<size_t>(kMaxJobs, jobs.size() - i0);
+    int t = 0;
+    for (int q = 0; q < nj; ++q) {
+      B.jobs[q] = jobs[i0 + q];
+      B.tile_start[q] = t;
+      t += jobs[i0 + q].ntiles;
+    }
+    B.njobs = nj;
+    B.tile_start[nj] = t;
+    B.total_tiles = t;
+    LD_TRY(launch_spmm<T>(B, threads, s));
+  }
+  return LOGDET_OK;
+}
+
+template <typename T>
+int launch_update_jobs(const std::vector<UpdJob<T>>& jobs, int threads, cudaStream_t s) {
+  for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxJobs) {
+    UpdBatch<T> B;
+    memset(&B, 0, sizeof B);
+    const int nj = (int)std::min<size_t>(kMaxJobs, jobs.size() - i0);
+    int t = 0;
+    for (int q = 0; q < nj; ++q) {
+      B.jobs[q] = jobs[i0 + q];
+      B.tile_start[q] = t;
+      t += jobs[i0 + q].ntiles;
+    }
+    B.njobs = nj;
+    B.tile_start[nj] = t;
+    B.total_tiles = t;
+    LD_TRY(launch_update<T>(B, threads, s));
+  }
+  return LOGDET_OK;
+}
+
+template int launch_spmm_jobs<double>(const std::vector<SpmmJob<double>>&, int, cudaStream_t);
+template int launch_spmm_jobs<float>(const std::vector<SpmmJob<float>>&, int, cudaStream_t);
+template int launch_update_jobs<double>(const std::vector<UpdJob<double>>&, int, cudaStream_t);
+template int launch_update_jobs<float>(const std::vector<UpdJob<float>>&, int, cudaStream_t);
+
+int launch_scalar_jobs(const std::vector<ScalarJob>& jobs, const std::vector<int>& widths, int kind,
+                       cudaStream_t s) {
+  // Jobs with FP64 and FP32 partials go to separate launches.
+  for (int f32 = 0; f32 < 2; ++f32) {
+    ScalarBatch B;
+    memset(&B, 0, sizeof B);
+    int nj = 0, pcount = 0;
+    auto flush = [&]() -> int {
+      if (!nj) return LOGDET_OK;
+      B.njobs = nj;
+      B.probe_start[nj] = pcount;
+      int rc = kind == SK_INIT ? launch_init_sigma(B, s)
+                               : kind == SK_COEF ? launch_coef(B, s) : launch_norm(B, s);
+      memset(&B, 0, sizeof B);
+      nj = 0;
+      pcount = 0;
+      return rc;
+    };
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      if (jobs[i].part_f32 != f32) continue;
+      B.jobs[nj] = jobs[i];
+      B.probe_start[nj] = pcount;
+      pcount += widths[i];
+      ++nj;
+      if (nj == kMaxJobs) LD_TRY(flush());
+    }
+    LD_TRY(flush());
+  }
+  return LOGDET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small assembly kernels of OSA-IOP
+// ---------------------------------------------------------------------------
+// Sketch weights: w[j][p] = |s_p| c_j sigma_j (+ shift for j = 1), so that
+// Y[:, p] = sum_j w[j][p] u_j = |s| V_m log(H_m) e_1 + shift s (Algorithm 1's
+// return line with L's shift).
+__global__ void k_iop_weights(const double* __restrict__ c, int ldc, const double* __restrict__ sig,
+                              const double* __restrict__ edot, const int* __restrict__ meff,
+                              int m, int ld, double shift, double* __restrict__ w) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * ld) return;
+  const int j = e / ld + 1, p = e - (e / ld) * ld;
+  const int m2 = m + 2;
+  double v = 0.0;
+  if (j <= meff[p]) {
+    v = sqrt(edot[p * m2 + 1]) * c[(size_t)p * ldc + j - 1] * sig[p * m2 + j];
+    if (j == 1) v += shift;
+  }
+  w[(size_t)(j - 1) * ld + p] = v;
+}
+
+// Quadratic form x^T L x = |x| sum_j c_j sigma_j (u_1^T u_j) + shift |x|^2.
+__global__ void k_iop_qf(const double* __restrict__ c, int ldc, const double* __restrict__ sig,
+                         const double* __restrict__ edot, const int* __restrict__ meff, int m,
+                         int ld, double shift, double* __restrict__ qf) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= ld) return;
+  const int m2 = m + 2;
+  const int me = meff[p];
+  if (me <= 0) { qf[p] = 0.0; return; }
+  double acc = 0.0;
+  for (int j = 1; j <= me; ++j)
+    acc = fma(c[(size_t)p * ldc + j - 1] * sig[p * m2 + j], edot[p * m2 + j], acc);
+  const double e1 = edot[p * m2 + 1];
+  qf[p] = sqrt(e1) * acc + shift * e1;
+}
+
+// Hutch++ split shared by both estimators: A = orth(Y) into X64[:, 0:s],
+// Z = G - A A^T G into X64[:, s:s+r].  No host synchronisation.
+static int hutchpp_split(int n, int s, int r, const double* Y64, int lds, uint64_t key_g,
+                         DevBuf<double>& X64, int ld, int* keep, cudaStream_t st) {
+  LD_TRY(X64.alloc((size_t)n * ld));
+  LD_TRY(X64.zero());
+  DevBuf<double> ws(st);
+  LD_TRY(ws.alloc(std::max(orth_workspace_doubles(n, s), project_workspace_doubles(n, s, r))));
+  LD_TRY(orth_fp64(n, s, Y64, lds, X64.p, ld, ws.p, keep, nullptr, st));
+  LD_TRY(project_residual_fp64(n, s, r, X64.p, ld, key_g, X64.p, ld, s, ws.p, st));
+  return LOGDET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solve<T>
+// ---------------------------------------------------------------------------
+struct PinnedHost {
+  void* p = nullptr;
+  ~PinnedHost() { if (p) cudaFreeHost(p); }
+};
+
+template <typename T>
+struct Solve : ISolve {
+  logdet_ctx* h;
+  SolveCfg c;
+  cudaStream_t st;
+  int ph = PH_SETUP;
+  int n, s, r, b, ld, lds, m, kk;
+  double lo, hi, alpha, gamma, shift;
+  DevBuf<T> vals, Vst, Xc;
+  DevBuf<double> X64, outv;
+  DevBuf<int> keep;
+  std::unique_ptr<KRun<T>> run;
+  PinnedHost pin;
+  double *h_out = nullptr, *h_edot = nullptr;
+  int *h_meff = nullptr, *h_keep = nullptr;
+  uint32_t *h_status = nullptr, *h_status1 = nullptr;
+  cudaEvent_t ev_done = nullptr;
+
+  Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
+      : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), keep(st_) {
+    n = h->n;
+    s = c.P / 3;
+    r = c.P - 2 * s;
+    b = s + r;
+    ld = round_up(b, Vec16<T>::N);
+    lds = round_up(s, Vec16<T>::N);
+    m = c.m;
+    kk = c.method == 0 ? 2 : std::min(c.k, m);
+    spectral_bounds(h, c, lo, hi);
+    gamma = std::sqrt(lo * hi);        // Proposition 2.1
+    alpha = c.method == 0 ? hi : lo;   // readings R1 / R2
+    shift = std::log(gamma / alpha);
+  }
+  ~Solve() override {
+    if (ev_done) cudaEventDestroy(ev_done);
+  }
+
+  int alloc_pinned() {
+    const size_t bytes = sizeof(double) * ld + sizeof(double) * (size_t)ld * (m + 2) +
+                         sizeof(int) * ld + sizeof(int) * s + sizeof(uint32_t) * ld +
+                         sizeof(uint32_t) * lds + 64;
+    LD_CUDA(cudaMallocHost(&pin.p, bytes));
+    memset(pin.p, 0, bytes);
+    char* q = static_cast<char*>(pin.p);
+    h_out = reinterpret_cast<double*>(q);
+    q += sizeof(double) * ld;
+    h_edot = reinterpret_cast<double*>(q);
+    q += sizeof(double) * (size_t)ld * (m + 2);
+    h_meff = reinterpret_cast<int*>(q);
+    q += sizeof(int) * ld;
+    h_keep = reinterpret_cast<int*>(q);
+    q += sizeof(int) * s;
+    h_status = reinterpret_cast<uint32_t*>(q);
+    q += sizeof(uint32_t) * ld;
+    h_status1 = reinterpret_cast<uint32_t*>(q);
+    return LOGDET_OK;
+  }
+
+  int phase() const override { return ph; }
+  bool in_krylov() const override { return ph == PH_K1 || ph == PH_K2; }
+  int krylov_threads() const override { return run ? run->g.threads : 0; }
+  bool is_fp32() const override { return std::is_same<T, float>::value; }
+  cudaEvent_t done_event() const override { return ev_done; }
+  size_t bytes_estimate() const override { return estimate_solve_bytes(h, c); }
+
+  // X0 for the next Krylov run from X64 (a copy in FP32 for the mixed path).
+  int make_x0(T** X0) {
+    if constexpr (std::is_same<T, double>::value) {
+      *X0 = X64.p;
+    } else {
+      LD_TRY(Xc.alloc((size_t)n * ld));
+      LD_TRY((convert_block<double, T>(X64.p, ld, Xc.p, ld, n, ld, st)));
+      X64.release();
+      *X0 = Xc.p;
+    }
+    return LOGDET_OK;
+  }
+
+  int setup() {
+    LD_TRY(alloc_pinned());
+    LD_TRY(keep.alloc(s));
+    LD_TRY(vals.alloc(h->nnz));
+    LD_TRY(scaled_values<T>(h, c.method == 0 ? alpha : gamma, vals.p, st));
+    run.reset(new KRun<T>(st));
+    if (c.method == 0) {
+      // Algorithm 3: Y = J S, A = orth(Y), Z = (I - A A^T) G.
+      DevBuf<T> S(st), Yt(st);
+      LD_TRY(S.alloc((size_t)n * lds));
+      LD_TRY(Yt.alloc((size_t)n * lds));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st));
+      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st));
+      S.release();
+      if constexpr (std::is_same<T, double>::value) {
+        LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+      } else {
+        DevBuf<double> Y64(st);
+        LD_TRY(Y64.alloc((size_t)n * lds));
+        LD_TRY((convert_block<T, double>(Yt.p, lds, Y64.p, lds, n, lds, st)));
+        Yt.release();
+        LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+      }
+      T* X0;
+      LD_TRY(make_x0(&X0));
+      LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
+                       nullptr, c.tol));
+    } else {
+      // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
+      LD_TRY(Vst.alloc((size_t)n * lds * m));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
+      LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
+                       Vst.p, c.tol));
+    }
+    ph = PH_K1;
+    return LOGDET_OK;
+  }
+
+  int mid() {
+    // Y = L S from the kept bases, then the Hutch++ split and phase 2.
+    KRun<T>& r1 = *run;
+    DevBuf<double> cc(st), ws(st), w(st), Y64(st);
+    LD_TRY(cc.alloc((size_t)lds * m));
+    LD_TRY(ws.alloc(hesslog_workspace_doubles(m, lds)));
+    LD_TRY(w.alloc((size_t)m * lds));
+    LD_TRY(hessenberg_log_e1(r1.ks.H.p, m + 1, r1.ks.meff.p, m, lds, cc.p, m, ws.p, r1.ks.status.p, st));
+    {
+      ProfScope prof(KC_SMALL, st);
+      k_iop_weights<<<div_up(m * lds, 256), 256, 0, st>>>(cc.p, m, r1.ks.sig.p, r1.ks.edot.p,
+                                                          r1.ks.meff.p, m, lds, shift, w.p);
+      LD_CHECK_LAUNCH();
+    }
+    LD_TRY(Y64.alloc((size_t)n * lds));
+    LD_TRY(sketch_assemble<T>(Vst.p, n, lds, m, w.p, Y64.p, lds, st));
+    LD_CUDA(cudaMemcpyAsync(h_status1, r1.ks.status.p, sizeof(uint32_t) * lds, cudaMemcpyDeviceToHost, st));
+    run.reset();
+    Vst.release();
+    cc.release();
+    ws.release();
+    w.release();
+    LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+    Y64.release();
+    T* X0;
+    LD_TRY(make_x0(&X0));
+    run.reset(new KRun<T>(st));
+    LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr, c.tol));
+    ph = PH_K2;
+    return LOGDET_OK;
+  }
+
+  int finish() {
+    KRun<T>& rr = *run;
+    LD_TRY(outv.alloc(ld));
+    if (c.method == 0) {
+      LD_TRY(gauss_quadrature_log(rr.ks.alpha.p, rr.ks.beta.p, m, rr.ks.meff.p, m, ld, lo / alpha,
+                                  outv.p, rr.ks.status.p, st));
+    } else {
+      DevBuf<double> cc(st), ws(st);
+      LD_TRY(cc.alloc((size_t)ld * m));
+      LD_TRY(ws.alloc(hesslog_workspace_doubles(m, ld)));
+      LD_TRY(hessenberg_log_e1(rr.ks.H.p, m + 1, rr.ks.meff.p, m, ld, cc.p, m, ws.p, rr.ks.status.p, st));
+      ProfScope prof(KC_SMALL, st);
+      k_iop_qf<<<div_up(ld, 64), 64, 0, st>>>(cc.p, m, rr.ks.sig.p, rr.ks.edot.p, rr.ks.meff.p, m,
+                                               ld, shift, outv.p);
+      LD_CHECK_LAUNCH();
+    }
+    LD_CUDA(cudaMemcpyAsync(h_out, outv.p, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaMemcpyAsync(h_meff, rr.ks.meff.p, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaMemcpyAsync(h_status, rr.ks.status.p, sizeof(uint32_t) * ld, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaMemcpyAsync(h_edot, rr.ks.edot.p, sizeof(double) * ld * (m + 2), cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaMemcpyAsync(h_keep, keep.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+    LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    LD_CUDA(cudaEventRecord(ev_done, st));
+    // Device buffers are released in stream order; the copies above read them first.
+    run.reset();
+    vals.release();
+    X64.release();
+    Xc.release();
+    outv.release();
+    keep.release();
+    ph = PH_WAIT;
+    return LOGDET_OK;
+  }
+
+  int run_phase() override {
+    int rc = LOGDET_OK;
+    if (ph == PH_SETUP) rc = setup();
+    else if (ph == PH_MID) rc = mid();
+    else if (ph == PH_FINISH) rc = finish();
+    if (rc) ph = PH_FAILED;
+    return rc;
+  }
+
+  void add_pass1(void* vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) override {
+    auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
+    const int j = run->next_step();
+    SpmmJob<T> J;
+    run->spmm_job(j, J);
+    v.push_back(J);
+    coef.push_back(run->scalar_job(j, run->pass1_dots(j)));
+    widths.push_back(run->ld);
+  }
+
+  bool add_pass2(void* vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) override {
+    const int j = run->next_step();
+    if (!run->has_pass2(j)) return false;
+    auto& v = *static_cast<std::vector<UpdJob<T>>*>(vec);
+    UpdJob<T> U;
+    run->upd_job(j, U);
+    v.push_back(U);
+    norm.push_back(run->scalar_job(j, run->track_e ? 2 : 1));
+    widths.push_back(run->ld);
+    return true;
+  }
+
+  void step_issued() override {
+    run->done_steps++;
+    if (run->finished()) ph = (c.method == 1 && ph == PH_K1) ? PH_MID : PH_FINISH;
+  }
+
+  int assemble(SolveOut& o) override {
+    memset(&o.res, 0, sizeof o.res);
+    uint32_t status = 0;
+    int s_eff = 0;
+    for (int i = 0; i < s; ++i) s_eff += h_keep[i] != 0;
+    if (s_eff < s) status |= LOGDET_ST_RANK_DEFICIENT;
+    int smin = 1 << 30, smax = 0;
+    for (int p = 0; p < b; ++p) {
+      status |= h_status[p];
+      if (h_meff[p] > 0) {
+        smin = std::min(smin, h_meff[p]);
+        smax = std::max(smax, h_meff[p]);
+      }
+    }
+    if (c.method == 1)
+      for (int p = 0; p < s; ++p) status |= h_status1[p];
+    if (smax == 0) smin = 0;
+    double tr_sub = 0.0, tr_res = 0.0;
+    o.per_probe.assign(b, 0.0);
+    o.zn2.assign(r, 0.0);
+    for (int i = 0; i < s; ++i) {
+      o.per_probe[i] = h_out[i];
+      tr_sub += h_out[i];
+    }
+    for (int j = 0; j < r; ++j) {
+      const double z2 = h_edot[(size_t)(s + j) * (m + 2) + 1];
+      o.zn2[j] = z2;
+      if (c.method == 0) {
+        o.per_probe[s + j] = h_out[s + j];
+        tr_res += z2 * h_out[s + j];
+      } else {
+        o.per_probe[s + j] = z2 > 0.0 ? h_out[s + j] / z2 : 0.0;
+        tr_res += h_out[s + j];
+      }
+    }
+    tr_res /= r;
+    logdet_result& R = o.res;
+    R.log_alpha = std::log(alpha);
+    R.log_gamma = c.method == 0 ? 0.0 : std::log(gamma);
+    R.tr_sub = tr_sub;
+    R.tr_res = tr_res;
+    R.logdet = n * R.log_alpha + tr_sub + tr_res;
+    R.s = s;
+    R.r = r;
+    R.s_eff = s_eff;
+    R.steps_min = smin;
+    R.steps_max = smax;
+    R.status_bits = status;
+    ph = PH_DONE;
+    return LOGDET_OK;
+  }
+};
+
+size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
+  const bool f32 = c.precision == LOGDET_MIXED_FP32;
+  const size_t es = f32 ? 4 : 8;
+  const int vec = f32 ? 4 : 2;
+  const size_t n = h->n;
+  const int s = c.P / 3, r = c.P - 2 * s, b = s + r;
+  const size_t ld = round_up(b, vec), lds = round_up(s, vec);
+  const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
+  const size_t vals = (size_t)h->nnz * es;
+  const TileGeom g = tile_geom((int)ld, vec);
+  const size_t ntiles = div_up((int)n, g.tile_rows);
+  const size_t part = (size_t)std::max(k, 2) * ld * ntiles * (f32 ? 8 : 8);
+  const size_t kstate = ld * (m + 2) * 8 * 4 + ld * (size_t)(m + 1) * m * 8 + 64 * ld;
+  const size_t split = n * ld * 8 + 8 * std::max(orth_workspace_doubles((int)n, s),
+                                                 project_workspace_doubles((int)n, s, r));
+  size_t peak;
+  if (c.method == 0) {
+    const size_t setup = 2 * n * lds * es + (f32 ? n * lds * 8 : 0) + split;
+    const size_t krylov = (f32 ? n * ld * es : n * ld * 8) + part + n * ld * es * 4 + kstate;
+    peak = vals + std::max(setup, krylov + (f32 ? 0 : 0));
+  } else {
+    const size_t phase1 = n * lds * m * es + part + n * lds * es + kstate +
+                          hesslog_workspace_doubles(m, (int)lds) * 8 + n * lds * 8;
+    const size_t phase2 = (f32 ? n * ld * es : n * ld * 8) + part + n * ld * es * (k + 2) + kstate +
+                          hesslog_workspace_doubles(m, (int)ld) * 8;
+    peak = vals + std::max(phase1, std::max(split + n * lds * 8, phase2));
+  }
+  return peak + (16u << 20);
+}
+
+std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, int* rc) {
+  *rc = validate_cfg(h, c);
+  if (*rc) return nullptr;
+  if (c.precision == LOGDET_FP64) return std::unique_ptr<ISolve>(new Solve<double>(h, c, st));
+  return std::unique_ptr<ISolve>(new Solve<float>(h, c, st));
+}
+
+// The blocking path: one solve advanced step by step with batches of one.
+int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o) {
+  int rc = LOGDET_OK;
+  std::unique_ptr<ISolve> sv = make_solve(h, c, st, &rc);
+  if (!sv) return rc;
+  std::vector<SpmmJob<double>> sd;
+  std::vector<SpmmJob<float>> sf;
+  std::vector<UpdJob<double>> ud;
+  std::vector<UpdJob<float>> uf;
+  std::vector<ScalarJob> sj;
+  std::vector<int> widths;
+  while (sv->phase() != PH_WAIT) {
+    if (sv->phase() == PH_FAILED) {
+      cudaStreamSynchronize(st);
+      return rc ? rc : LOGDET_ECUDA;
+    }
+    if (!sv->in_krylov()) {
+      rc = sv->run_phase();
+      if (rc) {
+        cudaStreamSynchronize(st);
+        return rc;
+      }
+      continue;
+    }
+    const int th = sv->krylov_threads();
+    const bool f32 = sv->is_fp32();
+    sd.clear(); sf.clear(); ud.clear(); uf.clear(); sj.clear(); widths.clear();
+    sv->add_pass1(f32 ? (void*)&sf : (void*)&sd, sj, widths);
+    LD_TRY(f32 ? launch_spmm_jobs<float>(sf, th, st) : launch_spmm_jobs<double>(sd, th, st));
+    LD_TRY(launch_scalar_jobs(sj, widths, SK_COEF, st));
+    sj.clear(); widths.clear();
+    if (sv->add_pass2(f32 ? (void*)&uf : (void*)&ud, sj, widths)) {
+      LD_TRY(f32 ? launch_update_jobs<float>(uf, th, st) : launch_update_jobs<double>(ud, th, st));
+      LD_TRY(launch_scalar_jobs(sj, widths, SK_NORM, st));
+    }
+    sv->step_issued();
+  }
+  LD_CUDA(cudaEventSynchronize(sv->done_event()));
+  return sv->assemble(o);
+}
+
+}  // namespace ld

@@ -1,0 +1,140 @@
+// Resumable solves.  A Solve is one OSLQ (Algorithm 3) or OSA-IOP
+// (Algorithm 2 with Algorithm 1) log-determinant estimate, split into phases
+// so that many solves can advance together:
+//
+//   SETUP   scaled values, probes, (OSLQ) sketch + Hutch++ split, first Krylov run set up
+//   K1      Krylov steps (OSLQ: its only run; OSA-IOP: the sketch columns, basis kept)
+//   MID     (OSA-IOP) log(H) e_1, Y = L S, Hutch++ split, second Krylov run set up
+//   K2      (OSA-IOP) Krylov steps on [A | Z] with the u_1 dots
+//   FINISH  Gauss rules / quadratic forms, results copied to pinned host memory
+//
+// Krylov phases advance one step at a time through job descriptors
+// (KRun::spmm_job, coef_job, upd_job, norm_job) that a caller gathers from
+// many solves into one batched launch per pass.  Everything else runs per
+// solve on the solve's stream.  A solve's arithmetic depends only on its own
+// data and its block geometry, never on the other jobs of a batch.
+#pragma once
+
+#include "dense.cuh"
+#include "handle.cuh"
+#include "krylov.cuh"
+
+#include <memory>
+#include <vector>
+
+namespace ld {
+
+constexpr double kDefaultTol = 1e-12;
+constexpr double kClampRel = 1e-6;  // lambda_lo = 1e-6 * lambda_hi when Gershgorin's lo <= 0
+
+struct SolveCfg {
+  int method = 0;  // 0 OSLQ, 1 OSA-IOP
+  int P = 0, m = 0, k = 2;
+  uint64_t seed = 0;
+  double tol = kDefaultTol;
+  double lam_lo = 0.0, lam_hi = 0.0;
+  int precision = LOGDET_FP64;
+};
+
+struct SolveOut {
+  logdet_result res;
+  std::vector<double> per_probe;  // s + r
+  std::vector<double> zn2;        // r
+};
+
+int validate_cfg(const logdet_ctx* h, const SolveCfg& c);
+void spectral_bounds(const logdet_ctx* h, const SolveCfg& c, double& lo, double& hi);
+
+// Device arrays of one Krylov run (see KrylovState).
+struct KState {
+  DevBuf<double> alpha, beta, H, sig, edot, coef, ycoef, dbuf;
+  DevBuf<int> meff, active;
+  DevBuf<uint32_t> status, cnt;
+  KrylovState st{};
+  explicit KState(cudaStream_t s)
+      : alpha(s), beta(s), H(s), sig(s), edot(s), coef(s), ycoef(s), dbuf(s), meff(s), active(s),
+        status(s), cnt(s) {}
+  int alloc(int method, int b, int ld, int m, int k, double tol, double rescale_lim);
+};
+
+template <typename T> constexpr double rescale_limit();
+template <> constexpr double rescale_limit<double>() { return 200.0; }
+template <> constexpr double rescale_limit<float>() { return 20.0; }
+
+// One Krylov run over a block X0 (n x ld, b live columns): method 0 is
+// three-term Lanczos, method 1 IOP with window k.  With Vfull the basis is
+// kept (u_j = Vfull + (j-1) n ld, X0 == Vfull); otherwise a ring of k+1
+// blocks follows u_1 = X0.  track_e accumulates u_1^T u_j.
+template <typename T>
+struct KRun {
+  using Part = typename PartOf<T>::type;
+  const int* rowptr = nullptr;
+  const int* colind = nullptr;
+  const T* vals = nullptr;
+  int n = 0;
+  long long nnz = 0;
+  int b = 0, ld = 0, m = 0, k = 2, method = 0;
+  bool track_e = false;
+  T* X0 = nullptr;
+  T* Vfull = nullptr;
+  TileGeom g{};
+  int ntiles = 0, nring = 0, ndmax = 0;
+  size_t blk = 0;
+  DevBuf<Part> part;
+  DevBuf<T> y, ring;
+  KState ks;
+  int done_steps = 0;  // steps whose pass 1 has been issued
+  cudaStream_t st;
+
+  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), st(s) {}
+
+  // Allocate and queue the start-block norms and sigma_1 (one launch pair).
+  int init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
+           int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol);
+  T* ptr(int i) const;
+  int win_lo(int j) const { return method == 0 ? j : (j - k + 1 > 1 ? j - k + 1 : 1); }
+  int next_step() const { return done_steps + 1; }
+  bool finished() const { return done_steps >= m; }
+  bool has_pass2(int j) const { return j < m; }
+  int pass1_dots(int j) const { return method == 0 ? 1 : j - win_lo(j) + 1; }
+  void spmm_job(int j, SpmmJob<T>& J) const;
+  void upd_job(int j, UpdJob<T>& U) const;
+  ScalarJob scalar_job(int j, int ndots) const;
+};
+
+// Batched launches of jobs that share element type and CTA size.
+template <typename T>
+int launch_spmm_jobs(const std::vector<SpmmJob<T>>& jobs, int threads, cudaStream_t s);
+template <typename T>
+int launch_update_jobs(const std::vector<UpdJob<T>>& jobs, int threads, cudaStream_t s);
+int launch_scalar_jobs(const std::vector<ScalarJob>& jobs, const std::vector<int>& widths, int kind,
+                       cudaStream_t s);
+
+enum SolvePhase { PH_SETUP = 0, PH_K1, PH_MID, PH_K2, PH_FINISH, PH_WAIT, PH_DONE, PH_FAILED };
+
+// Type-erased solve (FP64 or mixed FP32).
+struct ISolve {
+  virtual ~ISolve() {}
+  virtual int phase() const = 0;
+  virtual bool in_krylov() const = 0;
+  virtual int krylov_threads() const = 0;
+  virtual bool is_fp32() const = 0;
+  // Run the current non-Krylov phase (SETUP, MID, FINISH) and move on.
+  virtual int run_phase() = 0;
+  // Krylov step: append this solve's pass-1 job etc. for its next step.
+  virtual void add_pass1(void* spmm_vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) = 0;
+  virtual bool add_pass2(void* upd_vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) = 0;
+  virtual void step_issued() = 0;
+  // After FINISH's copies completed: assemble the host result.
+  virtual int assemble(SolveOut& o) = 0;
+  virtual cudaEvent_t done_event() const = 0;
+  virtual size_t bytes_estimate() const = 0;
+};
+
+std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, int* rc);
+size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c);
+
+// Run one solve to completion on its stream (the blocking API).
+int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o);
+
+}  // namespace ld
