@@ -74,7 +74,9 @@ typedef struct {
   int32_t steps_min; /* smallest Krylov dimension reached over the probes */
   int32_t steps_max; /* largest */
   uint32_t status_bits;
-  double device_ms;  /* device time of the solve (CUDA events) */
+  double device_ms;  /* device time of the solve (CUDA events; blocking calls) */
+  double latency_ms; /* submit -> result on the host (server requests; blocking: wall time) */
+  double queue_ms;   /* submit -> admission (server requests; blocking: 0) */
 } logdet_result;
 
 typedef struct {
@@ -87,6 +89,8 @@ typedef struct {
                           (i < s) then normalised residual forms K(z_j/|z_j|) */
   double* z_norm2;     /* optional host out, length r: |z_j|^2 */
   void* stream;        /* optional cudaStream_t for this call; NULL = handle's */
+  double shift;        /* solve for Q + shift*I (shift >= 0) without copying Q; the
+                          Gershgorin interval moves by exactly shift.  0 = Q itself */
 } logdet_opts;
 
 /* Fill an opts struct with the defaults. */
@@ -193,6 +197,52 @@ int logdet_gauss_quadrature_log(const double* alpha_dev, const double* beta_dev,
 int logdet_hessenberg_log_e1(const double* H_dev, int32_t ldh, const int32_t* msteps_dev,
                              int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
                              void* cuda_stream);
+
+/* ---- serving (continuous batching) --------------------------------------
+ * The paper solves one log-determinant at a time; a GP hyper-parameter search
+ * issues many.  A server admits requests of any size and method while slots
+ * (max_slots) and an estimate of their device memory fit the budget, keeps
+ * each one's Krylov state resident, and advances all requests that are in a
+ * Krylov phase together: one batched launch per pass per tick.  Requests
+ * join and leave the batch as they arrive and finish.  A request's result is
+ * bit-identical to logdet_oslq / logdet_osaiop with the same arguments.
+ *
+ * logdet_server_create: budget in bytes (> 0), max_slots >= 1, optional
+ *   cudaStream_t (NULL = a stream of its own).  Starts one scheduler thread.
+ * logdet_server_destroy: cancels queued requests, finishes resident ones,
+ *   joins the thread.
+ * logdet_submit: non-blocking.  method LOGDET_METHOD_OSLQ / _OSAIOP; other
+ *   arguments as logdet_oslq / logdet_osaiop.  The handle must stay alive
+ *   until the request completes; opts->per_probe / z_norm2 (if set) are
+ *   written when it completes and must stay valid until then.  Errors:
+ *   EINVAL (bad arguments), ENOMEM (the request alone exceeds the budget).
+ * logdet_poll: LOGDET_PENDING while queued or running, LOGDET_OK with *out
+ *   filled (latency_ms, queue_ms set), or the request's error / ECANCEL.
+ * logdet_wait: as poll but blocks up to timeout_us (< 0 = forever);
+ *   ETIMEOUT when still pending.
+ * logdet_cancel: queued requests never run; running ones leave at the next
+ *   tick.  logdet_release forgets a finished request.  ENOENT: unknown id.
+ */
+typedef struct logdet_server logdet_server;
+typedef struct {
+  int64_t submitted, admitted, completed, failed, cancelled;
+  int64_t queued, resident, max_resident;
+  int64_t ticks;          /* scheduler iterations */
+  int64_t batched_steps;  /* request-steps advanced by batched launches */
+  size_t bytes_in_use, bytes_budget;
+  double busy_ms;         /* scheduler time spent issuing work */
+} logdet_stats;
+int logdet_server_create(size_t device_mem_budget, int32_t max_slots, void* cuda_stream,
+                         logdet_server** out);
+void logdet_server_destroy(logdet_server* s);
+int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num_probes,
+                  int32_t krylov_steps, int32_t iop_window, uint64_t seed, const logdet_opts* opts,
+                  uint64_t* req_id);
+int logdet_poll(logdet_server* s, uint64_t req_id, logdet_result* out);
+int logdet_wait(logdet_server* s, uint64_t req_id, int64_t timeout_us, logdet_result* out);
+int logdet_cancel(logdet_server* s, uint64_t req_id);
+int logdet_release(logdet_server* s, uint64_t req_id);
+int logdet_server_stats(logdet_server* s, logdet_stats* out);
 
 /* logdet_hessenberg_log_e1_noalloc: the same computation as
  * logdet_hessenberg_log_e1, for callers that cannot allocate device memory

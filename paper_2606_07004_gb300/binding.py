@@ -40,6 +40,8 @@ EXPORTED = [
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc",
+    "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
+    "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
 
@@ -51,6 +53,17 @@ class logdet_result(C.Structure):
         ("s", C.c_int32), ("r", C.c_int32), ("s_eff", C.c_int32),
         ("steps_min", C.c_int32), ("steps_max", C.c_int32),
         ("status_bits", C.c_uint32), ("device_ms", C.c_double),
+        ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+    ]
+
+
+class logdet_server_stats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+        ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
+        ("resident", C.c_int64), ("max_resident", C.c_int64), ("ticks", C.c_int64),
+        ("batched_steps", C.c_int64), ("bytes_in_use", C.c_size_t), ("bytes_budget", C.c_size_t),
+        ("busy_ms", C.c_double),
     ]
 
 
@@ -60,7 +73,7 @@ class logdet_opts(C.Structure):
         ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
         ("block_width", C.c_int32),
         ("per_probe", C.POINTER(C.c_double)), ("z_norm2", C.POINTER(C.c_double)),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("shift", C.c_double),
     ]
 
 
@@ -91,6 +104,15 @@ _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, 
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1_noalloc", C.c_int,
      [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+_sig("logdet_server_create", C.c_int, [C.c_size_t, _i32, _P, C.POINTER(_P)])
+_sig("logdet_server_destroy", None, [_P])
+_sig("logdet_submit", C.c_int, [_P, _P, _i32, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts),
+                                C.POINTER(_u64)])
+_sig("logdet_poll", C.c_int, [_P, _u64, C.POINTER(logdet_result)])
+_sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
+_sig("logdet_cancel", C.c_int, [_P, _u64])
+_sig("logdet_release", C.c_int, [_P, _u64])
+_sig("logdet_server_stats", C.c_int, [_P, C.POINTER(logdet_server_stats)])
 _sig("logdet_launch_count", C.c_int64, [])
 _sig("logdet_profile_enable", C.c_int, [C.c_int])
 _sig("logdet_profile_reset", C.c_int, [])
@@ -127,6 +149,27 @@ def _stream(stream) -> int:
     return getattr(stream, "cuda_stream", stream)
 
 
+def _make_opts(precision, tol, lam, stream, shift, per, zn):
+    o = logdet_opts()
+    _lib.logdet_opts_default(C.byref(o))
+    o.precision = precision
+    if tol is not None:
+        o.tol = tol
+    if lam is not None:
+        o.lambda_lo, o.lambda_hi = lam
+    o.per_probe = per.ctypes.data_as(C.POINTER(C.c_double))
+    o.z_norm2 = zn.ctypes.data_as(C.POINTER(C.c_double))
+    o.stream = _stream(stream) or None
+    o.shift = shift
+    return o
+
+
+def _result(res, per, zn, s, r):
+    return Result(res.logdet, res.tr_sub, res.tr_res, res.log_alpha, res.log_gamma,
+                  res.s, res.r, res.s_eff, res.steps_min, res.steps_max, res.status_bits,
+                  res.device_ms, per[: s + r].copy(), zn[:r].copy(), res.latency_ms, res.queue_ms)
+
+
 @dataclass
 class Result:
     logdet: float
@@ -143,6 +186,8 @@ class Result:
     device_ms: float
     per_probe: np.ndarray
     z_norm2: np.ndarray
+    latency_ms: float = 0.0
+    queue_ms: float = 0.0
 
 
 class Handle:
@@ -200,40 +245,98 @@ class Handle:
         return n.value, nnz.value, lo.value, hi.value
 
     def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
-             lam, stream):
+             lam, stream, shift=0.0):
         s = num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = logdet_opts()
-        _lib.logdet_opts_default(C.byref(o))
-        o.precision = precision
-        if tol is not None:
-            o.tol = tol
-        if lam is not None:
-            o.lambda_lo, o.lambda_hi = lam
-        o.per_probe = per.ctypes.data_as(C.POINTER(C.c_double))
-        o.z_norm2 = zn.ctypes.data_as(C.POINTER(C.c_double))
-        o.stream = _stream(stream) or None
+        o = _make_opts(precision, tol, lam, stream, shift, per, zn)
         res = logdet_result()
         _check(fn(self._h, num_probes, krylov_steps, iop_window, seed, C.byref(o), C.byref(res)),
                name)
-        return Result(res.logdet, res.tr_sub, res.tr_res, res.log_alpha, res.log_gamma,
-                      res.s, res.r, res.s_eff, res.steps_min, res.steps_max, res.status_bits,
-                      res.device_ms, per[: s + r].copy(), zn[:r].copy())
+        return _result(res, per, zn, s, r)
 
     def oslq(self, num_probes, krylov_steps, seed=0, iop_window=0, precision=FP64, tol=None,
-             lam=None, stream=None) -> Result:
+             lam=None, stream=None, shift=0.0) -> Result:
         return self._run(_lib.logdet_oslq, "logdet_oslq", num_probes, krylov_steps, iop_window,
-                         seed, precision, tol, lam, stream)
+                         seed, precision, tol, lam, stream, shift)
 
     def osaiop(self, num_probes, krylov_steps, iop_window=2, seed=0, precision=FP64, tol=None,
-               lam=None, stream=None) -> Result:
+               lam=None, stream=None, shift=0.0) -> Result:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
-                         iop_window, seed, precision, tol, lam, stream)
+                         iop_window, seed, precision, tol, lam, stream, shift)
 
     def spmm(self, x, y, b, ld, stream=None):
         _check(_lib.logdet_spmm(self._h, _ptr(x), _ptr(y), b, ld, _stream(stream)), "logdet_spmm")
+
+
+class Server:
+    """Continuous-batching server (logdet_server_create / submit / poll / wait)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 64, stream=None):
+        self._s = _P()
+        _check(_lib.logdet_server_create(int(budget_bytes), max_slots, _stream(stream) or None,
+                                         C.byref(self._s)), "logdet_server_create")
+        self._pending = {}
+
+    def submit(self, handle: Handle, method: int, num_probes: int, krylov_steps: int,
+               iop_window: int = 0, seed: int = 0, precision=FP64, tol=None, lam=None,
+               shift=0.0) -> int:
+        s = num_probes // 3
+        r = num_probes - 2 * s
+        per = np.zeros(max(s + r, 1))
+        zn = np.zeros(max(r, 1))
+        o = _make_opts(precision, tol, lam, None, shift, per, zn)
+        rid = _u64()
+        _check(_lib.logdet_submit(self._s, handle.raw, method, num_probes, krylov_steps, iop_window,
+                                  seed, C.byref(o), C.byref(rid)), "logdet_submit")
+        self._pending[rid.value] = (per, zn, s, r, handle)
+        return rid.value
+
+    def poll(self, rid: int):
+        """None while pending, else the Result (raises LogdetError on failure)."""
+        res = logdet_result()
+        rc = _lib.logdet_poll(self._s, rid, C.byref(res))
+        if rc == PENDING:
+            return None
+        _check(rc, "logdet_poll")
+        per, zn, s, r, _ = self._pending[rid]
+        return _result(res, per, zn, s, r)
+
+    def wait(self, rid: int, timeout_us: int = -1):
+        res = logdet_result()
+        _check(_lib.logdet_wait(self._s, rid, timeout_us, C.byref(res)), "logdet_wait")
+        per, zn, s, r, _ = self._pending[rid]
+        return _result(res, per, zn, s, r)
+
+    def cancel(self, rid: int):
+        _check(_lib.logdet_cancel(self._s, rid), "logdet_cancel")
+
+    def release(self, rid: int):
+        _check(_lib.logdet_release(self._s, rid), "logdet_release")
+        self._pending.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = logdet_server_stats()
+        _check(_lib.logdet_server_stats(self._s, C.byref(st)), "logdet_server_stats")
+        return {f[0]: getattr(st, f[0]) for f in st._fields_}
+
+    def close(self):
+        if getattr(self, "_s", None):
+            _lib.logdet_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def logdet_create(n, rowptr, colind, vals) -> Handle:

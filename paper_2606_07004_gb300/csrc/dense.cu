@@ -775,6 +775,19 @@ int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStr
 template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t);
 template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t);
 
+__global__ void k_fill_double(double* out, size_t count, double value) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = value;
+}
+
+int fill_double(double* out, size_t count, double value, cudaStream_t st) {
+  ProfScope prof(KC_OTHER, st);
+  k_fill_double<<<std::max(1, std::min(div_up((int)count, 256), 64)), 256, 0, st>>>(out, count, value);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols) {
   const size_t total = (size_t)n * ldout;

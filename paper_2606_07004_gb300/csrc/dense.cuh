@@ -48,6 +48,9 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
 template <typename T>
 int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st);
 
+// out[i] = value for i < count.
+int fill_double(double* out, size_t count, double value, cudaStream_t st);
+
 // Copy/convert a block with the same layout (FP64 <-> FP32).
 template <typename Tin, typename Tout>
 int convert_block(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols,

@@ -55,6 +55,7 @@ static SolveCfg make_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t s
     c.tol = opts->tol > 0.0 ? opts->tol : kDefaultTol;
     c.lam_lo = opts->lambda_lo;
     c.lam_hi = opts->lambda_hi;
+    c.shift = opts->shift;
   }
   return c;
 }

@@ -59,6 +59,6 @@ int scaled_values(logdet_ctx* h, double c, T* out, cudaStream_t st);
 
 template <typename T>
 int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const T* x, T* y,
-               int ld, cudaStream_t st);
+               int ld, cudaStream_t st, const double* colshift = nullptr);
 
 }  // namespace ld

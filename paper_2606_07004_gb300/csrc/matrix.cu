@@ -245,7 +245,7 @@ template int scaled_values<float>(logdet_ctx*, double, float*, cudaStream_t);
 // and by the OSLQ sketch.
 template <typename T>
 int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const T* x, T* y,
-               int ld, cudaStream_t st) {
+               int ld, cudaStream_t st, const double* colshift) {
   TileGeom g = tile_geom(ld, Vec16<T>::N);
   SpmmBatch<T> B;
   memset(&B, 0, sizeof B);
@@ -259,6 +259,7 @@ int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const
   J.n = n;
   J.ld = ld;
   J.ndots = 0;
+  J.colshift = colshift;
   J.b = ld;
   J.nnz = 0;
   J.tile_rows = g.tile_rows;
@@ -268,7 +269,7 @@ int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const
   B.total_tiles = J.ntiles;
   return launch_spmm<T>(B, g.threads, st);
 }
-template int spmm_block<double>(const int*, const int*, const double*, int, const double*, double*, int, cudaStream_t);
-template int spmm_block<float>(const int*, const int*, const float*, int, const float*, float*, int, cudaStream_t);
+template int spmm_block<double>(const int*, const int*, const double*, int, const double*, double*, int, cudaStream_t, const double*);
+template int spmm_block<float>(const int*, const int*, const float*, int, const float*, float*, int, cudaStream_t, const double*);
 
 }  // namespace ld

@@ -1,0 +1,437 @@
+// Continuous-batching log-determinant server.
+//
+// Requests (a matrix handle plus OSLQ / OSA-IOP parameters) are queued by
+// logdet_submit from any thread.  One scheduler thread owns the device work:
+// every tick it admits queued requests while slots and the device-memory
+// budget allow, runs the pending non-Krylov phase of each resident request
+// (set-up, OSA-IOP mid-phase, finish), and then advances every request that
+// is in a Krylov phase by one step with ONE batched launch per pass (SpMM +
+// dots, scalar coefficients, update + norms, scalar norms) over all of them.
+// Requests therefore enter and leave the batch as they arrive and finish.
+// Because each job keeps its own block geometry and fixed-order reductions,
+// a request's result is bit-identical whether it runs alone, in any mix, or
+// through the blocking logdet_oslq / logdet_osaiop calls.
+#include "handle.cuh"
+#include "solve.cuh"
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+struct logdet_server;
+
+namespace ld {
+
+static double now_us() {
+  using namespace std::chrono;
+  return duration_cast<duration<double, std::micro>>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING, RQ_DONE, RQ_FAILED, RQ_CANCELLED };
+
+struct Request {
+  uint64_t id = 0;
+  logdet_ctx* h = nullptr;
+  SolveCfg cfg;
+  double* user_per_probe = nullptr;
+  double* user_zn2 = nullptr;
+  std::unique_ptr<ISolve> solve;
+  int state = RQ_QUEUED;
+  int rc = LOGDET_OK;
+  size_t bytes = 0;
+  bool cancel = false;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  SolveOut out;
+};
+
+}  // namespace ld
+
+using namespace ld;
+
+struct logdet_server {
+  size_t budget = 0;
+  int max_slots = 1;
+  int device = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::vector<std::shared_ptr<Request>> active;
+  std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+  uint64_t next_id = 1;
+  size_t used = 0;
+  bool stop = false;
+  std::thread worker;
+  std::deque<cudaEvent_t> ticks;  // run-ahead limiter
+  // statistics
+  int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_failed = 0, n_cancelled = 0;
+  int64_t n_ticks = 0, n_batched_steps = 0, max_resident = 0;
+  double busy_us = 0.0;
+
+  void loop();
+  int tick(std::vector<std::shared_ptr<Request>>& act);
+  void complete(const std::shared_ptr<Request>& r, int state, int rc);
+};
+
+void logdet_server::complete(const std::shared_ptr<Request>& r, int state_, int rc_) {
+  // Called with mu held.
+  r->state = state_;
+  r->rc = rc_;
+  r->t_done = now_us();
+  if (state_ == RQ_DONE) {
+    r->out.res.latency_ms = (r->t_done - r->t_submit) / 1e3;
+    r->out.res.queue_ms = (r->t_admit - r->t_submit) / 1e3;
+    if (r->user_per_probe)
+      for (size_t i = 0; i < r->out.per_probe.size(); ++i) r->user_per_probe[i] = r->out.per_probe[i];
+    if (r->user_zn2)
+      for (size_t i = 0; i < r->out.zn2.size(); ++i) r->user_zn2[i] = r->out.zn2[i];
+    ++n_completed;
+  } else if (state_ == RQ_FAILED) {
+    ++n_failed;
+  } else if (state_ == RQ_CANCELLED) {
+    ++n_cancelled;
+  }
+  // Device buffers are freed in stream order, after any work still queued.
+  r->solve.reset();
+  used -= r->bytes;
+  cv_done.notify_all();
+}
+
+int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
+  // 1. non-Krylov phases, per request
+  for (auto& r : act) {
+    ISolve* sv = r->solve.get();
+    if (!sv || sv->in_krylov()) continue;
+    const int ph = sv->phase();
+    if (ph == PH_SETUP || ph == PH_MID || ph == PH_FINISH) {
+      int rc = sv->run_phase();
+      if (rc) r->rc = rc;
+    }
+  }
+  // 2. one batched Krylov step over every request in a Krylov phase, grouped
+  //    by element type and CTA size
+  std::map<int, std::vector<SpmmJob<double>>> sd;
+  std::map<int, std::vector<SpmmJob<float>>> sf;
+  std::map<int, std::vector<UpdJob<double>>> ud;
+  std::map<int, std::vector<UpdJob<float>>> uf;
+  std::vector<ScalarJob> coef, norm;
+  std::vector<int> wc, wn;
+  std::vector<ISolve*> stepping;
+  for (auto& r : act) {
+    ISolve* sv = r->solve.get();
+    if (!sv || !sv->in_krylov() || r->rc) continue;
+    const int th = sv->krylov_threads();
+    if (sv->is_fp32()) sv->add_pass1(&sf[th], coef, wc);
+    else sv->add_pass1(&sd[th], coef, wc);
+    stepping.push_back(sv);
+  }
+  if (stepping.empty()) return 0;
+  for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first, st));
+  for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first, st));
+  LD_TRY(launch_scalar_jobs(coef, wc, SK_COEF, st));
+  for (ISolve* sv : stepping) {
+    const int th = sv->krylov_threads();
+    if (sv->is_fp32()) sv->add_pass2(&uf[th], norm, wn);
+    else sv->add_pass2(&ud[th], norm, wn);
+  }
+  for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first, st));
+  for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first, st));
+  if (!norm.empty()) LD_TRY(launch_scalar_jobs(norm, wn, SK_NORM, st));
+  for (ISolve* sv : stepping) sv->step_issued();
+  n_batched_steps += (int64_t)stepping.size();
+  return (int)stepping.size();
+}
+
+void logdet_server::loop() {
+  cudaSetDevice(device);
+  std::vector<std::shared_ptr<Request>> act;
+  while (true) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      // Admission: FIFO while a slot is free and the budget allows.
+      while (!queue.empty() && (int)active.size() < max_slots) {
+        auto r = queue.front();
+        if (r->cancel) {
+          queue.pop_front();
+          r->state = RQ_CANCELLED;
+          ++n_cancelled;
+          cv_done.notify_all();
+          continue;
+        }
+        if (used + r->bytes > budget) break;
+        queue.pop_front();
+        used += r->bytes;
+        r->state = RQ_RUNNING;
+        r->t_admit = now_us();
+        active.push_back(r);
+        ++n_admitted;
+      }
+      max_resident = std::max<int64_t>(max_resident, (int64_t)active.size());
+      if (active.empty()) {
+        if (stop) break;
+        cv_work.wait_for(lk, std::chrono::milliseconds(20));
+        continue;
+      }
+      // Running requests that were cancelled leave at the tick boundary.
+      for (size_t i = 0; i < active.size();) {
+        if (active[i]->cancel) {
+          complete(active[i], RQ_CANCELLED, LOGDET_ECANCEL);
+          active.erase(active.begin() + i);
+        } else {
+          ++i;
+        }
+      }
+      act = active;
+    }
+    const double t0 = now_us();
+    // Solves for newly admitted requests (allocation happens in their SETUP phase).
+    for (auto& r : act) {
+      if (!r->solve && !r->rc) {
+        int rc = LOGDET_OK;
+        r->solve = make_solve(r->h, r->cfg, st, &rc);
+        if (!r->solve) r->rc = rc ? rc : LOGDET_EINVAL;
+      }
+    }
+    int rc = tick(act);
+    bool issued = rc > 0;
+    if (rc < 0) {
+      // A launch failed: fail every resident request.
+      std::lock_guard<std::mutex> lk(mu);
+      for (auto& r : act) r->rc = rc;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(ev, st);
+      ticks.push_back(ev);
+    }
+    // Keep at most two ticks in flight ahead of the device.  With no Krylov
+    // step issued, wait for the oldest tick (or a finishing request) instead
+    // of spinning.
+    while (ticks.size() > 2 || (!issued && !ticks.empty())) {
+      cudaEventSynchronize(ticks.front());
+      cudaEventDestroy(ticks.front());
+      ticks.pop_front();
+      if (!issued) break;
+    }
+    if (!issued) {
+      for (auto& r : act)
+        if (r->solve && r->solve->phase() == PH_WAIT) {
+          cudaEventSynchronize(r->solve->done_event());
+          break;
+        }
+    }
+    ++n_ticks;
+    busy_us += now_us() - t0;
+    // Completions.
+    std::lock_guard<std::mutex> lk(mu);
+    for (size_t i = 0; i < active.size();) {
+      auto& r = active[i];
+      bool gone = false;
+      if (r->rc) {
+        cudaStreamSynchronize(st);
+        complete(r, RQ_FAILED, r->rc);
+        gone = true;
+      } else if (r->solve && r->solve->phase() == PH_WAIT &&
+                 cudaEventQuery(r->solve->done_event()) == cudaSuccess) {
+        int arc = r->solve->assemble(r->out);
+        complete(r, arc ? RQ_FAILED : RQ_DONE, arc);
+        gone = true;
+      }
+      if (gone) active.erase(active.begin() + i);
+      else ++i;
+    }
+  }
+  while (!ticks.empty()) {
+    cudaEventSynchronize(ticks.front());
+    cudaEventDestroy(ticks.front());
+    ticks.pop_front();
+  }
+}
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int logdet_server_create(size_t budget, int32_t max_slots, void* cuda_stream, logdet_server** out) {
+  if (!out || budget == 0 || max_slots < 1) {
+    set_error("server: need out != NULL, budget > 0, max_slots >= 1");
+    return LOGDET_EINVAL;
+  }
+  *out = nullptr;
+  auto* s = new logdet_server();
+  s->budget = budget;
+  s->max_slots = max_slots;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    set_error("server: no CUDA device");
+    return LOGDET_ECUDA;
+  }
+  int rc = ensure_pool(s->device);
+  if (rc) { delete s; return rc; }
+  if (cuda_stream) {
+    s->st = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      set_error("server: cudaStreamCreate failed");
+      return LOGDET_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  s->worker = std::thread([s] { s->loop(); });
+  *out = s;
+  return LOGDET_OK;
+}
+
+void logdet_server_destroy(logdet_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& r : s->queue) {
+      r->state = RQ_CANCELLED;
+      ++s->n_cancelled;
+    }
+    s->queue.clear();
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  s->cv_done.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  cudaStreamSynchronize(s->st);
+  if (s->own_stream) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num_probes,
+                  int32_t krylov_steps, int32_t iop_window, uint64_t seed, const logdet_opts* opts,
+                  uint64_t* req_id) {
+  if (!s || !h || !req_id) {
+    set_error("submit: NULL server, handle or req_id");
+    return LOGDET_EINVAL;
+  }
+  auto r = std::make_shared<Request>();
+  r->h = h;
+  SolveCfg& c = r->cfg;
+  c.method = method;
+  c.P = num_probes;
+  c.m = krylov_steps;
+  c.k = iop_window;
+  c.seed = seed;
+  if (opts) {
+    c.precision = opts->precision;
+    c.tol = opts->tol > 0.0 ? opts->tol : kDefaultTol;
+    c.lam_lo = opts->lambda_lo;
+    c.lam_hi = opts->lambda_hi;
+    c.shift = opts->shift;
+    r->user_per_probe = opts->per_probe;
+    r->user_zn2 = opts->z_norm2;
+  }
+  LD_TRY(validate_cfg(h, c));
+  r->bytes = estimate_solve_bytes(h, c);
+  if (r->bytes > s->budget) {
+    set_error("submit: request needs ~%zu bytes, more than the server budget %zu", r->bytes, s->budget);
+    return LOGDET_ENOMEM;
+  }
+  r->t_submit = now_us();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      set_error("submit: server is shutting down");
+      return LOGDET_ECANCEL;
+    }
+    r->id = s->next_id++;
+    s->all[r->id] = r;
+    s->queue.push_back(r);
+    ++s->n_submitted;
+    *req_id = r->id;
+  }
+  s->cv_work.notify_all();
+  return LOGDET_OK;
+}
+
+static int result_of(const std::shared_ptr<Request>& r, logdet_result* out) {
+  switch (r->state) {
+    case RQ_QUEUED:
+    case RQ_RUNNING: return LOGDET_PENDING;
+    case RQ_DONE:
+      if (out) *out = r->out.res;
+      return LOGDET_OK;
+    case RQ_CANCELLED: return LOGDET_ECANCEL;
+    default: return r->rc ? r->rc : LOGDET_ECUDA;
+  }
+}
+
+int logdet_poll(logdet_server* s, uint64_t id, logdet_result* out) {
+  if (!s) { set_error("poll: NULL server"); return LOGDET_EINVAL; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) { set_error("poll: unknown request %llu", (unsigned long long)id); return LOGDET_ENOENT; }
+  return result_of(it->second, out);
+}
+
+int logdet_wait(logdet_server* s, uint64_t id, int64_t timeout_us, logdet_result* out) {
+  if (!s) { set_error("wait: NULL server"); return LOGDET_EINVAL; }
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) { set_error("wait: unknown request %llu", (unsigned long long)id); return LOGDET_ENOENT; }
+  auto r = it->second;
+  auto pending = [&] { return r->state == RQ_QUEUED || r->state == RQ_RUNNING; };
+  if (timeout_us < 0) {
+    s->cv_done.wait(lk, [&] { return !pending() || s->stop; });
+  } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return !pending(); })) {
+    set_error("wait: request %llu still pending after %lld us", (unsigned long long)id, (long long)timeout_us);
+    return LOGDET_ETIMEOUT;
+  }
+  return result_of(r, out);
+}
+
+int logdet_cancel(logdet_server* s, uint64_t id) {
+  if (!s) { set_error("cancel: NULL server"); return LOGDET_EINVAL; }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) { set_error("cancel: unknown request"); return LOGDET_ENOENT; }
+    it->second->cancel = true;
+  }
+  s->cv_work.notify_all();
+  return LOGDET_OK;
+}
+
+int logdet_release(logdet_server* s, uint64_t id) {
+  if (!s) { set_error("release: NULL server"); return LOGDET_EINVAL; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) { set_error("release: unknown request"); return LOGDET_ENOENT; }
+  const int st = it->second->state;
+  if (st == RQ_QUEUED || st == RQ_RUNNING) { set_error("release: request still pending"); return LOGDET_PENDING; }
+  s->all.erase(it);
+  return LOGDET_OK;
+}
+
+int logdet_server_stats(logdet_server* s, logdet_stats* out) {
+  if (!s || !out) { set_error("stats: NULL argument"); return LOGDET_EINVAL; }
+  std::lock_guard<std::mutex> lk(s->mu);
+  out->submitted = s->n_submitted;
+  out->admitted = s->n_admitted;
+  out->completed = s->n_completed;
+  out->failed = s->n_failed;
+  out->cancelled = s->n_cancelled;
+  out->queued = (int64_t)s->queue.size();
+  out->resident = (int64_t)s->active.size();
+  out->max_resident = s->max_resident;
+  out->ticks = s->n_ticks;
+  out->batched_steps = s->n_batched_steps;
+  out->bytes_in_use = s->used;
+  out->bytes_budget = s->budget;
+  out->busy_ms = s->busy_us / 1e3;
+  return LOGDET_OK;
+}
+
+}  // extern "C"

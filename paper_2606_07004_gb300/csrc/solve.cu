@@ -16,8 +16,10 @@ void spectral_bounds(const logdet_ctx* h, const SolveCfg& c, double& lo, double&
     hi = c.lam_hi;
     return;
   }
-  hi = h->g_hi;
-  lo = h->g_lo > 0.0 ? h->g_lo : kClampRel * hi;
+  // Gershgorin of Q + shift I is [lo + shift, hi + shift].
+  hi = h->g_hi + c.shift;
+  const double glo = h->g_lo + c.shift;
+  lo = glo > 0.0 ? glo : kClampRel * hi;
 }
 
 int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
@@ -32,6 +34,10 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
     return LOGDET_EINVAL;
   }
   if (c.method != 0 && c.method != 1) { set_error("method %d unknown", c.method); return LOGDET_EINVAL; }
+  if (!(c.shift >= 0.0) || !std::isfinite(c.shift)) {
+    set_error("shift must be finite and >= 0");
+    return LOGDET_EINVAL;
+  }
   if (c.method == 0 && !(c.k == 0 || c.k == 2)) {
     set_error("OSLQ uses three-term Lanczos: iop_window must be 0 or 2");
     return LOGDET_EINVAL;
@@ -159,6 +165,7 @@ void KRun<T>::spmm_job(int j, SpmmJob<T>& J) const {
   J.nnz = nnz;
   J.tile_rows = g.tile_rows;
   J.ntiles = ntiles;
+  J.colshift = colshift;
   if (method == 0) {
     J.ndots = 1;
     J.dotv[0] = ptr(j);
@@ -363,7 +370,7 @@ struct Solve : ISolve {
   int n, s, r, b, ld, lds, m, kk;
   double lo, hi, alpha, gamma, shift;
   DevBuf<T> vals, Vst, Xc;
-  DevBuf<double> X64, outv;
+  DevBuf<double> X64, outv, cshift;
   DevBuf<int> keep;
   std::unique_ptr<KRun<T>> run;
   PinnedHost pin;
@@ -373,7 +380,8 @@ struct Solve : ISolve {
   cudaEvent_t ev_done = nullptr;
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
-      : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), keep(st_) {
+      : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
+        keep(st_) {
     n = h->n;
     s = c.P / 3;
     r = c.P - 2 * s;
@@ -436,7 +444,14 @@ struct Solve : ISolve {
     LD_TRY(alloc_pinned());
     LD_TRY(keep.alloc(s));
     LD_TRY(vals.alloc(h->nnz));
-    LD_TRY(scaled_values<T>(h, c.method == 0 ? alpha : gamma, vals.p, st));
+    const double cscale = c.method == 0 ? alpha : gamma;
+    LD_TRY(scaled_values<T>(h, cscale, vals.p, st));
+    if (c.shift != 0.0) {
+      // (Q + shift I)/c applied as vals/c plus (shift/c) times the row's own entry.
+      const size_t cnt = std::max(ld, lds);
+      LD_TRY(cshift.alloc(cnt));
+      LD_TRY(fill_double(cshift.p, cnt, c.shift / cscale, st));
+    }
     run.reset(new KRun<T>(st));
     if (c.method == 0) {
       // Algorithm 3: Y = J S, A = orth(Y), Z = (I - A A^T) G.
@@ -444,7 +459,7 @@ struct Solve : ISolve {
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st));
-      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st));
+      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p));
       S.release();
       if constexpr (std::is_same<T, double>::value) {
         LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
@@ -457,12 +472,14 @@ struct Solve : ISolve {
       }
       T* X0;
       LD_TRY(make_x0(&X0));
+      run->colshift = cshift.p;
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
                        nullptr, c.tol));
     } else {
       // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
       LD_TRY(Vst.alloc((size_t)n * lds * m));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
+      run->colshift = cshift.p;
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
                        Vst.p, c.tol));
     }
@@ -497,6 +514,7 @@ struct Solve : ISolve {
     T* X0;
     LD_TRY(make_x0(&X0));
     run.reset(new KRun<T>(st));
+    run->colshift = cshift.p;
     LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr, c.tol));
     ph = PH_K2;
     return LOGDET_OK;
@@ -528,6 +546,7 @@ struct Solve : ISolve {
     // Device buffers are released in stream order; the copies above read them first.
     run.reset();
     vals.release();
+    cshift.release();
     X64.release();
     Xc.release();
     outv.release();

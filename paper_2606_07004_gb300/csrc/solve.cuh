@@ -33,6 +33,7 @@ struct SolveCfg {
   uint64_t seed = 0;
   double tol = kDefaultTol;
   double lam_lo = 0.0, lam_hi = 0.0;
+  double shift = 0.0;  // solve for Q + shift I
   int precision = LOGDET_FP64;
 };
 
@@ -77,6 +78,7 @@ struct KRun {
   bool track_e = false;
   T* X0 = nullptr;
   T* Vfull = nullptr;
+  const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
   TileGeom g{};
   int ntiles = 0, nring = 0, ndmax = 0;
   size_t blk = 0;
