@@ -223,6 +223,13 @@ int logdet_hessenberg_log_e1(const double* H_dev, int32_t ldh, const int32_t* ms
  * logdet_cancel: queued requests never run; running ones leave at the next
  *   tick.  logdet_release forgets a finished request.  ENOENT: unknown id.
  */
+/* logdet_estimate_bytes: the device memory (bytes, an upper estimate of the
+ * peak) one solve with these arguments uses -- the amount a server reserves
+ * against its budget when it admits the request.  Errors as logdet_submit. */
+int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes,
+                          int32_t krylov_steps, int32_t iop_window, const logdet_opts* opts,
+                          size_t* bytes);
+
 typedef struct logdet_server logdet_server;
 typedef struct {
   int64_t submitted, admitted, completed, failed, cancelled;

@@ -40,7 +40,7 @@ EXPORTED = [
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc",
-    "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
+    "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
@@ -104,6 +104,8 @@ _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, 
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1_noalloc", C.c_int,
      [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+_sig("logdet_estimate_bytes", C.c_int, [_P, _i32, _i32, _i32, _i32, C.POINTER(logdet_opts),
+                                        C.POINTER(C.c_size_t)])
 _sig("logdet_server_create", C.c_int, [C.c_size_t, _i32, _P, C.POINTER(_P)])
 _sig("logdet_server_destroy", None, [_P])
 _sig("logdet_submit", C.c_int, [_P, _P, _i32, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts),
@@ -265,6 +267,17 @@ class Handle:
                lam=None, stream=None, shift=0.0) -> Result:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
                          iop_window, seed, precision, tol, lam, stream, shift)
+
+    def estimate_bytes(self, method, num_probes, krylov_steps, iop_window=0, precision=FP64,
+                       shift=0.0) -> int:
+        o = logdet_opts()
+        _lib.logdet_opts_default(C.byref(o))
+        o.precision = precision
+        o.shift = shift
+        out = C.c_size_t()
+        _check(_lib.logdet_estimate_bytes(self._h, method, num_probes, krylov_steps, iop_window,
+                                          C.byref(o), C.byref(out)), "logdet_estimate_bytes")
+        return out.value
 
     def spmm(self, x, y, b, ld, stream=None):
         _check(_lib.logdet_spmm(self._h, _ptr(x), _ptr(y), b, ld, _stream(stream)), "logdet_spmm")

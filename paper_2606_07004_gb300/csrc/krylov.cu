@@ -70,40 +70,21 @@ __device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec
 // ---------------------------------------------------------------------------
 // pass 1: y = A x (CSR order per row) and d_i += dotv_i . y
 //
-// Each tile first stages its slice of the CSR arrays (row offsets, column
-// indices, values) in shared memory with coalesced loads, so a row's gathers
-// of x depend on one shared-memory read instead of two dependent global
-// loads; the gathers of a row are then issued four at a time.  A tile whose
-// slice exceeds the staging area (very dense rows) reads the CSR directly.
+// Thread (r, g) of a tile owns row r (stepping by R rows) and the 16-byte
+// chunk g of the probe columns.  A row's gathers of x are issued four at a
+// time (one memory round trip per four nonzeros), then the remainder.  The
+// CSR arrays are read through the read-only cache; measured on GB300 this
+// beats staging each tile's CSR slice in shared memory, which takes L1
+// capacity away from the gathers of x.
 // ---------------------------------------------------------------------------
-constexpr int kStageNnzPerRow = 16;  // staged nonzeros per tile row
-// x gathers in flight per thread and row: 8 for FP32 blocks (HBM-bound), 4
-// for FP64 blocks (FP64-ALU-bound; fewer registers keep 3 CTAs per SM).
-template <typename T> struct GatherBatch { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
-
-// Staging layout (byte offsets from the start of the staging area, each
-// sub-array 16-byte aligned): row offsets, column indices, values.
-__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-__host__ __device__ constexpr size_t stage_col_off(int tile_rows) {
-  return align16((size_t)(tile_rows + 1) * sizeof(int));
-}
-template <typename T>
-__host__ __device__ constexpr size_t stage_val_off(int tile_rows) {
-  return stage_col_off(tile_rows) + align16((size_t)tile_rows * kStageNnzPerRow * sizeof(int));
-}
-template <typename T>
-__host__ __device__ constexpr size_t spmm_stage_bytes(int tile_rows) {
-  return stage_val_off<T>(tile_rows) + align16((size_t)tile_rows * kStageNnzPerRow * sizeof(T));
-}
+constexpr int kGather = 4;
 
 template <typename T, int NDOT>
 __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   constexpr int V = Vec16<T>::N;
-  constexpr int kGather = GatherBatch<T>::value;
   using Acc = typename AccOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* smem = reinterpret_cast<Acc*>(smem_raw);
-  unsigned char* stage = smem_raw + (size_t)blockDim.x * V * sizeof(Acc);
 
   for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
     const int jb = find_job(B, gt);
@@ -119,25 +100,6 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
     const int col0 = g * V;
     const int ndots = J.ndots;
 
-    // Stage the tile's CSR slice.
-    int* s_rp = reinterpret_cast<int*>(stage);
-    int* s_col = reinterpret_cast<int*>(stage + stage_col_off(J.tile_rows));
-    T* s_val = reinterpret_cast<T*>(stage + stage_val_off<T>(J.tile_rows));
-    const int p_base = __ldg(J.rowptr + row0);
-    const int p_end = __ldg(J.rowptr + row1);
-    const bool staged = (p_end - p_base) <= J.tile_rows * kStageNnzPerRow;
-    for (int i = threadIdx.x; i <= row1 - row0; i += blockDim.x)
-      s_rp[i] = __ldg(J.rowptr + row0 + i) - p_base;
-    if (staged) {
-      for (int i = threadIdx.x; i < p_end - p_base; i += blockDim.x) {
-        s_col[i] = __ldg(J.colind + p_base + i);
-        s_val[i] = __ldg(J.vals + p_base + i);
-      }
-    }
-    __syncthreads();
-    const int* colp = staged ? s_col : J.colind + p_base;
-    const T* valp = staged ? s_val : J.vals + p_base;
-
     Acc acc[NDOT > 0 ? NDOT : 1][V];
 #pragma unroll
     for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
@@ -151,50 +113,30 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
         T s[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) s[v] = T(0);
-        const int q0 = s_rp[row - row0], q1 = s_rp[row - row0 + 1];
-        if constexpr (sizeof(T) == 4) {
-          // HBM-bound: gathers in batches of kGather with no branches; a lane
-          // past the row's end re-reads the row's last column (a cached line)
-          // with weight 0, adding an exact zero.
-          for (int q = q0; q < q1; q += kGather) {
-            int c[kGather];
-            T a[kGather], xv[kGather][V];
+        const int q0 = __ldg(J.rowptr + row), q1 = __ldg(J.rowptr + row + 1);
+        int q = q0;
+        for (; q + kGather <= q1; q += kGather) {
+          int c[kGather];
+          T a[kGather], xv[kGather][V];
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-              const int qq = min(q + u, q1 - 1);
-              c[u] = colp[qq];
-              a[u] = (q + u < q1) ? valp[qq] : T(0);
-            }
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
-#pragma unroll
-            for (int u = 0; u < kGather; ++u)
-#pragma unroll
-              for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
+          for (int u = 0; u < kGather; ++u) {
+            c[u] = __ldg(J.colind + q + u);
+            a[u] = __ldg(J.vals + q + u);
           }
-        } else {
-          // FP64-ALU-bound: exact count, batches of kGather plus a remainder.
-          int q = q0;
-          for (; q + kGather <= q1; q += kGather) {
-            int c[kGather];
-            T a[kGather], xv[kGather][V];
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) { c[u] = colp[q + u]; a[u] = valp[q + u]; }
+          for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+          for (int u = 0; u < kGather; ++u)
 #pragma unroll
-            for (int u = 0; u < kGather; ++u)
+            for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
+        }
+        for (; q < q1; ++q) {
+          const int c = __ldg(J.colind + q);
+          const T a = __ldg(J.vals + q);
+          T xv[V];
+          load_vec<T>(xcol + (size_t)c * J.ld, xv);
 #pragma unroll
-              for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
-          }
-          for (; q < q1; ++q) {
-            const int c = colp[q];
-            const T a = valp[q];
-            T xv[V];
-            load_vec<T>(xcol + (size_t)c * J.ld, xv);
-#pragma unroll
-            for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
-          }
+          for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
         }
         if (has_shift || has_scale) {
           T xr[V];
@@ -501,9 +443,7 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   int nd = 0;
   for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
   using Acc = typename AccOf<T>::type;
-  int max_tile_rows = 1;
-  for (int j = 0; j < b.njobs; ++j) max_tile_rows = std::max(max_tile_rows, b.jobs[j].tile_rows);
-  size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc) + spmm_stage_bytes<T>(max_tile_rows);
+  size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
   double flops = 0.0, bytes = 0.0;
   for (int j = 0; j < b.njobs; ++j) {
     const SpmmJob<T>& J = b.jobs[j];
@@ -516,9 +456,6 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
 #define LD_SPMM_CASE(ND)                                                      \
   {                                                                           \
     auto kern = k_spmm<T, ND>;                                                \
-    if (smem > 48 * 1024)                                                     \
-      LD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-    LD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)); \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
     kern<<<grid, threads, smem, s>>>(b);                                      \
     break;                                                                    \

@@ -356,6 +356,25 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
   return LOGDET_OK;
 }
 
+int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes, int32_t krylov_steps,
+                          int32_t iop_window, const logdet_opts* opts, size_t* bytes) {
+  if (!h || !bytes) { set_error("estimate_bytes: NULL argument"); return LOGDET_EINVAL; }
+  SolveCfg c;
+  c.method = method;
+  c.P = num_probes;
+  c.m = krylov_steps;
+  c.k = iop_window;
+  if (opts) {
+    c.precision = opts->precision;
+    c.lam_lo = opts->lambda_lo;
+    c.lam_hi = opts->lambda_hi;
+    c.shift = opts->shift;
+  }
+  LD_TRY(validate_cfg(h, c));
+  *bytes = estimate_solve_bytes(h, c);
+  return LOGDET_OK;
+}
+
 static int result_of(const std::shared_ptr<Request>& r, logdet_result* out) {
   switch (r->state) {
     case RQ_QUEUED:

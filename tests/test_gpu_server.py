@@ -86,7 +86,9 @@ def test_admission_by_memory_budget(mats):
     with B.Server(8 * GB) as srv:
         one = srv.wait(srv.submit(h, B.METHOD_OSLQ, 30, 12, seed=9))
     # A budget that holds only one such request at a time: all still complete.
-    with B.Server(int(1.5 * 200 * (1 << 20)), max_slots=8) as srv:
+    need = h.estimate_bytes(B.METHOD_OSLQ, 30, 12)
+    assert need > 0
+    with B.Server(int(1.5 * need), max_slots=8) as srv:
         ids = [srv.submit(h, B.METHOD_OSLQ, 30, 12, seed=9) for _ in range(5)]
         res = [srv.wait(i, 120_000_000) for i in ids]
         st = srv.stats()
