@@ -475,6 +475,168 @@ def matern_case(args):
     return 0
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def serving_case(args):
+    """Continuous-batching serving workload (a GP hyper-parameter search's
+    stream of log-determinants).  Requests: type uniform over {2D Laplacian,
+    3D Laplacian, Matern (kappa^2 = 0.05)}, n log-uniform in [1e4, 4e6]
+    (snapped to a pool of 4 grid sizes per type), diagonal shift log-uniform in
+    [1e-3, 1] (applied matrix-free), OSLQ m = 50 with 30 probes, seed = index.
+    The mixed-precision batched server is timed on a burst (capacity) and on a
+    Poisson stream at 0.8 x capacity; the plain FP64 one-at-a-time form is
+    timed solve by solve and its FIFO queue replayed on the same arrival times.
+    """
+    import threading
+    import numpy as np
+    import torch
+    from paper_2606_07004_gb300 import binding as B
+    import workloads as W
+
+    rng = np.random.default_rng(2024)
+    N = args.requests
+    t_build = time.perf_counter()
+    pool = {}
+    for typ in ("l2d", "l3d", "mat"):
+        for nt in np.geomspace(1e4, 4e6, 4):
+            if typ == "l3d":
+                side = int(round(nt ** (1 / 3)))
+                A = W.laplacian_3d(side)
+            elif typ == "l2d":
+                side = int(round(nt ** 0.5))
+                A = W.laplacian_2d(side)
+            else:
+                side = int(round(nt ** 0.5))
+                A = W.matern_2d(side, 0.05)
+            pool[(typ, int(nt))] = (A.n, B.Handle.from_csr(A))
+    t_build = time.perf_counter() - t_build
+    sizes = sorted({k[1] for k in pool})
+    reqs = []
+    for i in range(N):
+        typ = ("l2d", "l3d", "mat")[int(rng.integers(3))]
+        n = math.exp(rng.uniform(math.log(1e4), math.log(4e6)))
+        nt = min(sizes, key=lambda s: abs(math.log(s) - math.log(n)))
+        shift = math.exp(rng.uniform(math.log(1e-3), 0.0))
+        reqs.append((pool[(typ, nt)][1], shift, i, pool[(typ, nt)][0]))
+    P, m = 30, 50
+    budget = int(args.budget_gb * (1 << 30))
+    # 1. burst through the server (mixed FP32): capacity
+    with B.Server(budget, max_slots=args.slots) as srv:
+        srv.wait(srv.submit(reqs[0][0], B.METHOD_OSLQ, P, m, seed=0, precision=B.MIXED_FP32,
+                            shift=reqs[0][1]))  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [srv.submit(h, B.METHOD_OSLQ, P, m, seed=s, precision=B.MIXED_FP32, shift=sh)
+               for h, sh, s, _ in reqs]
+        burst = [srv.wait(i) for i in ids]
+        t_burst = time.perf_counter() - t0
+        st_burst = srv.stats()
+    cap = N / t_burst
+    lam = 0.8 * cap
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+    # 2. Poisson stream through the server
+    with B.Server(budget, max_slots=args.slots) as srv:
+        ids = [None] * N
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, (h, sh, s, _) in enumerate(reqs):
+                dt = arrivals[i] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = srv.submit(h, B.METHOD_OSLQ, P, m, seed=s, precision=B.MIXED_FP32, shift=sh)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        stream = [srv.wait(i) for i in ids]
+        t_stream = time.perf_counter() - t0
+        st_stream = srv.stats()
+    lat_srv = [r.latency_ms for r in stream]
+    # 3. plain FP64 one at a time (blocking), FIFO replay on the same arrivals
+    svc, r64 = [], []
+    for h, sh, s, _ in reqs:
+        t1 = time.perf_counter()
+        r64.append(h.oslq(P, m, seed=s, shift=sh))
+        svc.append(time.perf_counter() - t1)
+    done, lat64 = 0.0, []
+    for a, sv in zip(arrivals, svc):
+        done = max(done, a) + sv
+        lat64.append(1e3 * (done - a))
+    errs = [abs(a.logdet - b.logdet) / abs(b.logdet) for a, b in zip(stream, r64)]
+    same = all(a.logdet == b.logdet for a, b in zip(stream, burst))
+    for _, h in pool.values():
+        h.close()
+    print(json.dumps({
+        "workload": "serving: %d OSLQ requests (m=50, 30 probes), 2D/3D Laplacian and Matern, "
+                    "n log-uniform [1e4, 4e6] (pool of 4 sizes per type), shift log-uniform "
+                    "[1e-3, 1]" % N,
+        "metric": METRIC, "unit": UNIT,
+        "mixed_batched": {"burst_solves_per_s": cap, "stream_rate": lam,
+                          "stream_solves_per_s": N / t_stream,
+                          "p50_ms": _pct(lat_srv, 0.5), "p99_ms": _pct(lat_srv, 0.99),
+                          "max_resident": st_stream["max_resident"],
+                          "batched_steps_per_tick": st_burst["batched_steps"] / max(1, st_burst["ticks"])},
+        "fp64_one_at_a_time": {"solves_per_s": N / sum(svc), "p50_ms": _pct(lat64, 0.5),
+                               "p99_ms": _pct(lat64, 0.99)},
+        "speedup_solves_per_s": cap / (N / sum(svc)),
+        "max_rel_err_mixed_vs_fp64": max(errs), "burst_equals_stream_bitwise": same,
+        "matrix_build_s": t_build}))
+    return 0
+
+
+def multishift_case(args):
+    """Batched irregular workload: the Laplacian of a Chung-Lu power-law graph
+    (n = 2,097,152, exponent 2.3, mean degree 8) with 8 diagonal shifts drawn
+    uniformly from [1e-3, 1e-1]; OSA-IOP m = 100, k = 4, 64 probes per shift,
+    FP32 values and vectors.  The 8 shifted operators share the CSR and
+    advance together (one launch per pass); compared with the same 8 solves
+    one after the other."""
+    import numpy as np
+    import torch
+    from paper_2606_07004_gb300 import binding as B
+    import workloads as W
+
+    t0 = time.perf_counter()
+    A = W.powerlaw_graph_laplacian(2 ** 21, exponent=2.3, mean_degree=8.0, seed=7,
+                                   dtype=np.float32)
+    t_build = time.perf_counter() - t0
+    shifts = np.random.default_rng(11).uniform(1e-3, 1e-1, 8)
+    P, m, k = 64, 100, 4
+    h = B.Handle.from_csr(A)
+    need = h.estimate_bytes(B.METHOD_OSAIOP, P, m, k, precision=B.MIXED_FP32)
+    budget = int(min(args.budget_gb * (1 << 30), 8 * need * 1.05))
+    with B.Server(budget, max_slots=8) as srv:
+        srv.wait(srv.submit(h, B.METHOD_OSAIOP, P, 10, k, seed=0, precision=B.MIXED_FP32,
+                            shift=float(shifts[0])))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ids = [srv.submit(h, B.METHOD_OSAIOP, P, m, k, seed=t, precision=B.MIXED_FP32,
+                          shift=float(sh)) for t, sh in enumerate(shifts)]
+        batched = [srv.wait(i) for i in ids]
+        t_batched = time.perf_counter() - t1
+        st = srv.stats()
+    t1 = time.perf_counter()
+    serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh))
+              for t, sh in enumerate(shifts)]
+    t_serial = time.perf_counter() - t1
+    h.close()
+    print(json.dumps({
+        "workload": "power-law graph Laplacian n=%d nnz=%d, 8 shifts U[1e-3,1e-1], OSA-IOP m=100 "
+                    "k=4, 64 probes each, mixed FP32" % (A.n, A.nnz),
+        "metric": METRIC, "unit": UNIT,
+        "batched_solves_per_s": 8 / t_batched, "serial_solves_per_s": 8 / t_serial,
+        "batched_s": t_batched, "serial_s": t_serial,
+        "bitwise_equal_batched_vs_serial": all(a.logdet == b.logdet for a, b in zip(batched, serial)),
+        "logdets": [r.logdet for r in batched], "shifts": list(map(float, shifts)),
+        "bytes_per_solve_estimate": need, "max_resident": st["max_resident"],
+        "graph_build_s": t_build}))
+    return 0
+
+
 def small_case(args):
     """One OSLQ (m=12) and one OSA-IOP (k=4, m=12) solve with 60 probes on the 3D
     Laplacian 100^3 + 0.01 I: the capture target for ncu (blocks larger than
@@ -501,8 +663,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["laplacian3d", "matern"], default="laplacian3d",
-                    help="matern: the mixed-precision measurement line (not the default bench)")
+    ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift"],
+                    default="laplacian3d",
+                    help="extra measurement lines (not the default bench): matern = mixed "
+                         "precision; serving = continuous batching; multishift = 8 shifts")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
+    ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
+    ap.add_argument("--budget-gb", type=float, default=200.0, help="server memory budget")
     ap.add_argument("--small-case", action="store_true",
                     help="one OSLQ + one OSA-IOP solve on a 100^3 Laplacian (profiling target)")
     ap.add_argument("--small-case-fp32", action="store_true", help="the small case in mixed FP32")
@@ -512,6 +679,10 @@ def main():
         return small_case(args)
     if args.workload == "matern":
         return matern_case(args)
+    if args.workload == "serving":
+        return serving_case(args)
+    if args.workload == "multishift":
+        return multishift_case(args)
     if args.oracle_sample_child is not None:
         print(json.dumps(oracle_sample(args.oracle_sample_child)))
         return 0
