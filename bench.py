@@ -299,11 +299,13 @@ def cuda_arm(args):
     stream = torch.cuda.Stream(device=dev)
     h = B.Handle.from_csr(A)
 
+    at = 1 if args.autotune else 0
+
     def run_step(handle, seed, lat):
-        rs = [("oslq", handle.oslq(PROBES, STEPS_M, seed=seed, stream=stream))]
+        rs = [("oslq", handle.oslq(PROBES, STEPS_M, seed=seed, stream=stream, autotune=at))]
         for k in WINDOWS:
             rs.append((f"osaiop_k{k}", handle.osaiop(PROBES, STEPS_M, iop_window=k, seed=seed,
-                                                     stream=stream)))
+                                                     stream=stream, autotune=at)))
         for name, r in rs:
             lat.setdefault(name, []).append(r.device_ms)
         return rs
@@ -376,7 +378,7 @@ def cuda_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_dev_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(),
+        "data": "synthetic", "config": dict(workload_config(), autotune=bool(args.autotune)),
         "roofline": {
             "kernel": "k_spmm<double> (SpMM + fused window dots)",
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -669,6 +671,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="1 = autotuned Krylov kernel layout (tuned during warm-up)")
     ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift"],
                     default="laplacian3d",
                     help="extra measurement lines (not the default bench): matern = mixed "

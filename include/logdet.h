@@ -84,7 +84,10 @@ typedef struct {
   double tol;          /* breakdown threshold on h_{m+1,m} / beta_j; 0 = 1e-12 */
   double lambda_lo;    /* spectral bounds; both 0 = clamped Gershgorin interval */
   double lambda_hi;
-  int32_t block_width; /* reserved (0) */
+  int32_t autotune;    /* 1 = pick the Krylov kernels' layout (probe-block slices,
+                          CTA size, tile depth) by timing candidates on this matrix,
+                          cached per shape (and in the file LOGDET_TUNE_CACHE if set);
+                          changes results at rounding level only.  0 = defaults */
   double* per_probe;   /* optional host out, length s+r: subspace forms q_i^T f q_i
                           (i < s) then normalised residual forms K(z_j/|z_j|) */
   double* z_norm2;     /* optional host out, length r: |z_j|^2 */
@@ -291,6 +294,8 @@ int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int
 #define LOGDET_KC_OTHER   6
 #define LOGDET_KC_COUNT   7
 int64_t logdet_launch_count(void);
+/* Forget the autotuner's in-memory cache (the file, if any, is kept). */
+int logdet_autotune_clear(void);
 int logdet_profile_enable(int on);
 int logdet_profile_reset(void);
 int logdet_profile_read(int32_t kclass, int64_t* launches, double* device_ms, double* flops,

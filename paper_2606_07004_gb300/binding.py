@@ -38,7 +38,7 @@ EXPORTED = [
     "logdet_oslq", "logdet_osaiop",
     "logdet_probe_fill", "logdet_spmm", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
-    "logdet_launch_count", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
+    "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc",
     "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
@@ -71,7 +71,7 @@ class logdet_opts(C.Structure):
     _fields_ = [
         ("precision", C.c_int32), ("tol", C.c_double),
         ("lambda_lo", C.c_double), ("lambda_hi", C.c_double),
-        ("block_width", C.c_int32),
+        ("autotune", C.c_int32),
         ("per_probe", C.POINTER(C.c_double)), ("z_norm2", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("shift", C.c_double),
     ]
@@ -116,6 +116,7 @@ _sig("logdet_cancel", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
 _sig("logdet_server_stats", C.c_int, [_P, C.POINTER(logdet_server_stats)])
 _sig("logdet_launch_count", C.c_int64, [])
+_sig("logdet_autotune_clear", C.c_int, [])
 _sig("logdet_profile_enable", C.c_int, [C.c_int])
 _sig("logdet_profile_reset", C.c_int, [])
 _sig("logdet_profile_read", C.c_int, [_i32, C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl),
@@ -151,7 +152,7 @@ def _stream(stream) -> int:
     return getattr(stream, "cuda_stream", stream)
 
 
-def _make_opts(precision, tol, lam, stream, shift, per, zn):
+def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0):
     o = logdet_opts()
     _lib.logdet_opts_default(C.byref(o))
     o.precision = precision
@@ -163,6 +164,7 @@ def _make_opts(precision, tol, lam, stream, shift, per, zn):
     o.z_norm2 = zn.ctypes.data_as(C.POINTER(C.c_double))
     o.stream = _stream(stream) or None
     o.shift = shift
+    o.autotune = int(autotune)
     return o
 
 
@@ -247,26 +249,26 @@ class Handle:
         return n.value, nnz.value, lo.value, hi.value
 
     def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
-             lam, stream, shift=0.0):
+             lam, stream, shift=0.0, autotune=0):
         s = num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = _make_opts(precision, tol, lam, stream, shift, per, zn)
+        o = _make_opts(precision, tol, lam, stream, shift, per, zn, autotune)
         res = logdet_result()
         _check(fn(self._h, num_probes, krylov_steps, iop_window, seed, C.byref(o), C.byref(res)),
                name)
         return _result(res, per, zn, s, r)
 
     def oslq(self, num_probes, krylov_steps, seed=0, iop_window=0, precision=FP64, tol=None,
-             lam=None, stream=None, shift=0.0) -> Result:
+             lam=None, stream=None, shift=0.0, autotune=0) -> Result:
         return self._run(_lib.logdet_oslq, "logdet_oslq", num_probes, krylov_steps, iop_window,
-                         seed, precision, tol, lam, stream, shift)
+                         seed, precision, tol, lam, stream, shift, autotune)
 
     def osaiop(self, num_probes, krylov_steps, iop_window=2, seed=0, precision=FP64, tol=None,
-               lam=None, stream=None, shift=0.0) -> Result:
+               lam=None, stream=None, shift=0.0, autotune=0) -> Result:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
-                         iop_window, seed, precision, tol, lam, stream, shift)
+                         iop_window, seed, precision, tol, lam, stream, shift, autotune)
 
     def estimate_bytes(self, method, num_probes, krylov_steps, iop_window=0, precision=FP64,
                        shift=0.0) -> int:
@@ -294,12 +296,12 @@ class Server:
 
     def submit(self, handle: Handle, method: int, num_probes: int, krylov_steps: int,
                iop_window: int = 0, seed: int = 0, precision=FP64, tol=None, lam=None,
-               shift=0.0) -> int:
+               shift=0.0, autotune=0) -> int:
         s = num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = _make_opts(precision, tol, lam, None, shift, per, zn)
+        o = _make_opts(precision, tol, lam, None, shift, per, zn, autotune)
         rid = _u64()
         _check(_lib.logdet_submit(self._s, handle.raw, method, num_probes, krylov_steps, iop_window,
                                   seed, C.byref(o), C.byref(rid)), "logdet_submit")

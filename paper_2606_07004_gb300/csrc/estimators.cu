@@ -56,6 +56,7 @@ static SolveCfg make_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t s
     c.lam_lo = opts->lambda_lo;
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
+    c.autotune = opts->autotune;
   }
   return c;
 }

@@ -21,18 +21,21 @@ static int gcd_int(int a, int b) { while (b) { int t = a % b; a = b; b = t; } re
 
 // Threads per CTA: a multiple of both 32 (full warps) and of the chunks per
 // row G = ld / vec, so every lane of every warp owns a (row, chunk) slot.
-TileGeom tile_geom(int ld, int vec) {
+TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint) {
   TileGeom g;
-  int G = ld / vec;
+  int G = width / vec;
   int lcm = G / gcd_int(G, 32) * 32;          // smallest CTA with whole rows and warps
   int threads = lcm;
   while (threads < 256 && threads + lcm <= 512) threads += lcm;
   if (threads > 512) threads = std::max(1, 512 / G) * G;  // very wide blocks: idle lanes accepted
   if (G > 512) threads = 512;                               // (not reached for ld <= 1024)
+  if (threads_hint > 0 && threads_hint <= 512 && threads_hint % 32 == 0 && threads_hint % G == 0)
+    threads = threads_hint;
   g.threads = threads;
   g.rows_per_iter = threads / G;
   int iters = std::max(1, 256 / std::max(1, g.rows_per_iter));  // ~256+ rows per tile
   if (iters < 4) iters = 4;
+  if (iters_hint > 0 && iters_hint <= 256) iters = iters_hint;
   g.tile_rows = g.rows_per_iter * iters;
   return g;
 }
@@ -46,9 +49,11 @@ __device__ __forceinline__ int find_job(const Batch& B, int gt) {
 
 // Reduce the per-thread accumulators of all rows of the CTA for one dot and
 // write one partial per column.  smem holds blockDim.x * V accumulators.
+// The CTA owns columns [col_off, col_off + width) of the block; partials are
+// indexed by the block column.
 template <typename T, typename Acc>
 __device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec16<T>::N],
-                                                 bool live, int G, int R, int ld,
+                                                 bool live, int G, int R, int col_off, int width,
                                                  typename PartOf<T>::type* dst, int ntiles,
                                                  int tile) {
   constexpr int V = Vec16<T>::N;
@@ -58,12 +63,12 @@ __device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec
     for (int v = 0; v < V; ++v) smem[threadIdx.x * V + v] = acc[v];
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) {
+  for (int c = threadIdx.x; c < width; c += blockDim.x) {
     int g = c / V, v = c - (c / V) * V;
     Acc t;
     t.zero();
     for (int rr = 0; rr < R; ++rr) t.add(smem[(rr * G + g) * V + v]);
-    put_part(dst + (size_t)c * ntiles + tile, t);
+    put_part(dst + (size_t)(col_off + c) * ntiles + tile, t);
   }
 }
 
@@ -90,14 +95,14 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
     const int jb = find_job(B, gt);
     const SpmmJob<T>& J = B.jobs[jb];
     const int tile = gt - B.tile_start[jb];
-    const int G = J.ld / V;
+    const int G = J.width / V;
     const int R = blockDim.x / G;
     const int r = threadIdx.x / G;
     const int g = threadIdx.x - r * G;
     const bool live = r < R;
     const int row0 = tile * J.tile_rows;
     const int row1 = min(row0 + J.tile_rows, J.n);
-    const int col0 = g * V;
+    const int col0 = J.col_off + g * V;
     const int ndots = J.ndots;
 
     Acc acc[NDOT > 0 ? NDOT : 1][V];
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
 #pragma unroll
     for (int d = 0; d < NDOT; ++d) {
       if (d < ndots)
-        cta_reduce_write<T, Acc>(smem, acc[d], live, G, R, J.ld,
+        cta_reduce_write<T, Acc>(smem, acc[d], live, G, R, J.col_off, J.width,
                                  J.part + (size_t)d * J.ld * J.ntiles, J.ntiles, tile);
     }
     __syncthreads();
@@ -183,14 +188,14 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
     const int jb = find_job(B, gt);
     const UpdJob<T>& J = B.jobs[jb];
     const int tile = gt - B.tile_start[jb];
-    const int G = J.ld / V;
+    const int G = J.width / V;
     const int R = blockDim.x / G;
     const int r = threadIdx.x / G;
     const int g = threadIdx.x - r * G;
     const bool live = r < R;
     const int row0 = tile * J.tile_rows;
     const int row1 = min(row0 + J.tile_rows, J.n);
-    const int col0 = g * V;
+    const int col0 = J.col_off + g * V;
     const int nb = J.nbasis;
     const bool has_extra = J.extra != nullptr;
 
@@ -241,9 +246,10 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
         }
       }
     }
-    cta_reduce_write<T, Acc>(smem, nrm, live, G, R, J.ld, J.part, J.ntiles, tile);
+    cta_reduce_write<T, Acc>(smem, nrm, live, G, R, J.col_off, J.width, J.part, J.ntiles, tile);
     if (has_extra)
-      cta_reduce_write<T, Acc>(smem, ex, live, G, R, J.ld, J.part + (size_t)J.ld * J.ntiles,
+      cta_reduce_write<T, Acc>(smem, ex, live, G, R, J.col_off, J.width,
+                               J.part + (size_t)J.ld * J.ntiles,
                                J.ntiles, tile);
     __syncthreads();
   }

@@ -44,7 +44,8 @@ struct SpmmJob {
   const double* colscale;          // optional [ld]: y[:,p] *= colscale[p]
   const double* colshift;          // optional [ld]: y[:,p] += colshift[p] * x[:,p] (before scale)
   int n, ld, ndots, tile_rows, ntiles;
-  int b;                           // live columns (accounting only)
+  int col_off, width;              // columns [col_off, col_off+width) of the block (width % vec == 0)
+  int b;                           // live columns in this slice (accounting only)
   long long nnz;                   // (accounting only)
 };
 
@@ -68,7 +69,8 @@ struct UpdJob {
   const T* extra;                  // optional: dot out with extra
   typename PartOf<T>::type* part;  // [1 or 2][ld][ntiles]
   int n, ld, nbasis, tile_rows, ntiles;
-  int b;                           // live columns (accounting only)
+  int col_off, width;              // column slice, as in SpmmJob
+  int b;                           // live columns in this slice (accounting only)
 };
 
 template <typename T>
@@ -124,7 +126,18 @@ struct TileGeom {
   int rows_per_iter;
   int tile_rows;
 };
-TileGeom tile_geom(int ld, int vec);
+// Geometry for a slice of `width` columns.  threads_hint (a multiple of both
+// 32 and width/vec, <= 512) and iters_hint (rows per tile = rows per CTA
+// iteration x iters) override the defaults when valid.
+TileGeom tile_geom(int width, int vec, int threads_hint = 0, int iters_hint = 0);
+
+// Tunable layout of a Krylov run: the block's columns are processed as
+// `split` slices of ld/split columns, with the CTA size and tile depth above.
+struct TuneCfg {
+  int split = 1;
+  int threads = 0;  // 0 = default
+  int iters = 0;    // 0 = default
+};
 
 // Launchers (krylov.cu).  `grid_cap` bounds the persistent grid.
 template <typename T> int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s);

@@ -260,6 +260,8 @@ int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const
   J.ld = ld;
   J.ndots = 0;
   J.colshift = colshift;
+  J.col_off = 0;
+  J.width = ld;
   J.b = ld;
   J.nnz = 0;
   J.tile_rows = g.tile_rows;

@@ -330,6 +330,7 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
     c.lam_lo = opts->lambda_lo;
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
+    c.autotune = opts->autotune;
     r->user_per_probe = opts->per_probe;
     r->user_zn2 = opts->z_norm2;
   }
@@ -369,6 +370,7 @@ int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes, i
     c.lam_lo = opts->lambda_lo;
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
+    c.autotune = opts->autotune;
   }
   LD_TRY(validate_cfg(h, c));
   *bytes = estimate_solve_bytes(h, c);

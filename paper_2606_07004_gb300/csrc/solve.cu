@@ -1,6 +1,7 @@
 // Resumable OSLQ / OSA-IOP solves (see solve.cuh).
 #include "profile.cuh"
 #include "solve.cuh"
+#include "tune.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -109,7 +110,8 @@ int KState::alloc(int method, int b, int ld, int m, int k, double tol, double re
 
 template <typename T>
 int KRun<T>::init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
-                  int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol) {
+                  int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol,
+                  TuneCfg tc) {
   rowptr = rp;
   colind = ci;
   vals = v;
@@ -123,7 +125,10 @@ int KRun<T>::init(const int* rp, const int* ci, const T* v, int n_, long long nn
   track_e = track_e_;
   X0 = X0_;
   Vfull = Vfull_;
-  g = tile_geom(ld, Vec16<T>::N);
+  tune = tc;
+  if (tune.split < 1 || ld % tune.split || (ld / tune.split) % Vec16<T>::N) tune.split = 1;
+  width = ld / tune.split;
+  g = tile_geom(width, Vec16<T>::N, tune.threads, tune.iters);
   ntiles = div_up(n, g.tile_rows);
   blk = (size_t)n * ld;
   const int win = method == 0 ? 2 : k;
@@ -137,7 +142,11 @@ int KRun<T>::init(const int* rp, const int* ci, const T* v, int n_, long long nn
   LD_TRY(y.alloc(blk));
   if (!Vfull) LD_TRY(ring.alloc(blk * nring));
   LD_TRY(ks.alloc(method, b, ld, m, k, tol, rescale_limit<T>()));
-  LD_TRY(colnorm_partials<T>(X0, n, ld, g.tile_rows, ntiles, part.p, g.threads, st));
+  {
+    // Column norms of the start block over the same tiles (full-width CTAs).
+    const TileGeom gf = tile_geom(ld, Vec16<T>::N);
+    LD_TRY(colnorm_partials<T>(X0, n, ld, g.tile_rows, ntiles, part.p, gf.threads, st));
+  }
   std::vector<ScalarJob> jobs{scalar_job(0, 1)};
   std::vector<int> widths{ld};
   return launch_scalar_jobs(jobs, widths, SK_INIT, st);
@@ -151,59 +160,77 @@ T* KRun<T>::ptr(int i) const {
 }
 
 template <typename T>
-void KRun<T>::spmm_job(int j, SpmmJob<T>& J) const {
-  memset(&J, 0, sizeof J);
-  J.rowptr = rowptr;
-  J.colind = colind;
-  J.vals = vals;
-  J.x = ptr(j);
-  J.y = y.p;
-  J.part = part.p;
-  J.n = n;
-  J.ld = ld;
-  J.b = b;
-  J.nnz = nnz;
-  J.tile_rows = g.tile_rows;
-  J.ntiles = ntiles;
-  J.colshift = colshift;
-  if (method == 0) {
-    J.ndots = 1;
-    J.dotv[0] = ptr(j);
-  } else {
-    const int lo = win_lo(j);
-    J.ndots = j - lo + 1;
-    for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
+int KRun<T>::slice_live(int q) const {
+  const int lo = q * width;
+  return std::max(0, std::min(width, b - lo));
+}
+
+template <typename T>
+void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
+  for (int q = 0; q < tune.split; ++q) {
+    SpmmJob<T> J;
+    memset(&J, 0, sizeof J);
+    J.rowptr = rowptr;
+    J.colind = colind;
+    J.vals = vals;
+    J.x = ptr(j);
+    J.y = y.p;
+    J.part = part.p;
+    J.n = n;
+    J.ld = ld;
+    J.col_off = q * width;
+    J.width = width;
+    J.b = slice_live(q);
+    J.nnz = nnz;
+    J.tile_rows = g.tile_rows;
+    J.ntiles = ntiles;
+    J.colshift = colshift;
+    if (method == 0) {
+      J.ndots = 1;
+      J.dotv[0] = ptr(j);
+    } else {
+      const int lo = win_lo(j);
+      J.ndots = j - lo + 1;
+      for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
+    }
+    out.push_back(J);
   }
 }
 
 template <typename T>
-void KRun<T>::upd_job(int j, UpdJob<T>& U) const {
-  memset(&U, 0, sizeof U);
-  U.y = y.p;
-  U.coef = ks.coef.p;
-  U.ycoef = ks.ycoef.p;
-  U.extra = track_e ? X0 : nullptr;
-  U.part = part.p;
-  U.n = n;
-  U.ld = ld;
-  U.b = b;
-  U.tile_rows = g.tile_rows;
-  U.ntiles = ntiles;
-  if (method == 0) {
-    if (j >= 2) {
-      U.nbasis = 2;
-      U.basis[0] = ptr(j - 1);
-      U.basis[1] = ptr(j);
+void KRun<T>::upd_jobs(int j, std::vector<UpdJob<T>>& out) const {
+  for (int q = 0; q < tune.split; ++q) {
+    UpdJob<T> U;
+    memset(&U, 0, sizeof U);
+    U.y = y.p;
+    U.coef = ks.coef.p;
+    U.ycoef = ks.ycoef.p;
+    U.extra = track_e ? X0 : nullptr;
+    U.part = part.p;
+    U.n = n;
+    U.ld = ld;
+    U.col_off = q * width;
+    U.width = width;
+    U.b = slice_live(q);
+    U.tile_rows = g.tile_rows;
+    U.ntiles = ntiles;
+    if (method == 0) {
+      if (j >= 2) {
+        U.nbasis = 2;
+        U.basis[0] = ptr(j - 1);
+        U.basis[1] = ptr(j);
+      } else {
+        U.nbasis = 1;
+        U.basis[0] = ptr(j);
+      }
     } else {
-      U.nbasis = 1;
-      U.basis[0] = ptr(j);
+      const int lo = win_lo(j);
+      U.nbasis = j - lo + 1;
+      for (int i = lo; i <= j; ++i) U.basis[i - lo] = ptr(i);
     }
-  } else {
-    const int lo = win_lo(j);
-    U.nbasis = j - lo + 1;
-    for (int i = lo; i <= j; ++i) U.basis[i - lo] = ptr(i);
+    U.out = ptr(j + 1);
+    out.push_back(U);
   }
-  U.out = ptr(j + 1);
 }
 
 template <typename T>
@@ -427,6 +454,14 @@ struct Solve : ISolve {
   cudaEvent_t done_event() const override { return ev_done; }
   size_t bytes_estimate() const override { return estimate_solve_bytes(h, c); }
 
+  // Layout of the Krylov kernels for a block of width w: defaults, or the
+  // autotuner's choice for this matrix.
+  int layout(int w, TuneCfg* tc) {
+    *tc = TuneCfg();
+    if (!c.autotune) return LOGDET_OK;
+    return autotune_krylov<T>(h->rowptr, h->colind, vals.p, n, h->nnz, w, st, tc);
+  }
+
   // X0 for the next Krylov run from X64 (a copy in FP32 for the mixed path).
   int make_x0(T** X0) {
     if constexpr (std::is_same<T, double>::value) {
@@ -473,15 +508,19 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
+      TuneCfg tc;
+      LD_TRY(layout(ld, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
-                       nullptr, c.tol));
+                       nullptr, c.tol, tc));
     } else {
       // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
       LD_TRY(Vst.alloc((size_t)n * lds * m));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
       run->colshift = cshift.p;
+      TuneCfg tc;
+      LD_TRY(layout(lds, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
-                       Vst.p, c.tol));
+                       Vst.p, c.tol, tc));
     }
     ph = PH_K1;
     return LOGDET_OK;
@@ -515,7 +554,10 @@ struct Solve : ISolve {
     LD_TRY(make_x0(&X0));
     run.reset(new KRun<T>(st));
     run->colshift = cshift.p;
-    LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr, c.tol));
+    TuneCfg tc;
+    LD_TRY(layout(ld, &tc));
+    LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
+                     c.tol, tc));
     ph = PH_K2;
     return LOGDET_OK;
   }
@@ -567,9 +609,7 @@ struct Solve : ISolve {
   void add_pass1(void* vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) override {
     auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
     const int j = run->next_step();
-    SpmmJob<T> J;
-    run->spmm_job(j, J);
-    v.push_back(J);
+    run->spmm_jobs(j, v);
     coef.push_back(run->scalar_job(j, run->pass1_dots(j)));
     widths.push_back(run->ld);
   }
@@ -578,9 +618,7 @@ struct Solve : ISolve {
     const int j = run->next_step();
     if (!run->has_pass2(j)) return false;
     auto& v = *static_cast<std::vector<UpdJob<T>>*>(vec);
-    UpdJob<T> U;
-    run->upd_job(j, U);
-    v.push_back(U);
+    run->upd_jobs(j, v);
     norm.push_back(run->scalar_job(j, run->track_e ? 2 : 1));
     widths.push_back(run->ld);
     return true;

@@ -35,6 +35,7 @@ struct SolveCfg {
   double lam_lo = 0.0, lam_hi = 0.0;
   double shift = 0.0;  // solve for Q + shift I
   int precision = LOGDET_FP64;
+  int autotune = 0;    // layout of the Krylov kernels from the autotuner
 };
 
 struct SolveOut {
@@ -80,6 +81,8 @@ struct KRun {
   T* Vfull = nullptr;
   const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
   TileGeom g{};
+  TuneCfg tune{};
+  int width = 0;  // columns per slice job (ld / tune.split)
   int ntiles = 0, nring = 0, ndmax = 0;
   size_t blk = 0;
   DevBuf<Part> part;
@@ -92,15 +95,18 @@ struct KRun {
 
   // Allocate and queue the start-block norms and sigma_1 (one launch pair).
   int init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
-           int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol);
+           int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol,
+           TuneCfg tc = TuneCfg());
   T* ptr(int i) const;
   int win_lo(int j) const { return method == 0 ? j : (j - k + 1 > 1 ? j - k + 1 : 1); }
   int next_step() const { return done_steps + 1; }
   bool finished() const { return done_steps >= m; }
   bool has_pass2(int j) const { return j < m; }
   int pass1_dots(int j) const { return method == 0 ? 1 : j - win_lo(j) + 1; }
-  void spmm_job(int j, SpmmJob<T>& J) const;
-  void upd_job(int j, UpdJob<T>& U) const;
+  // Step j's jobs, one per column slice.
+  void spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const;
+  void upd_jobs(int j, std::vector<UpdJob<T>>& out) const;
+  int slice_live(int q) const;
   ScalarJob scalar_job(int j, int ndots) const;
 };
 

@@ -1,0 +1,13 @@
+// Autotuner of the Krylov step kernels' layout (see tune.cu).
+#pragma once
+
+#include "krylov.cuh"
+
+namespace ld {
+
+// The fastest TuneCfg for a matrix and block width, timed once and cached.
+template <typename T>
+int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, long long nnz, int ld,
+                    cudaStream_t st, TuneCfg* out);
+
+}  // namespace ld

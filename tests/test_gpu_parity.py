@@ -297,3 +297,36 @@ def test_invalid_arguments_are_errors():
     with pytest.raises(B.LogdetError) as e:
         B.Handle.from_csr(neg)
     assert e.value.code == B.ENOTSPD
+
+
+# ---------------------------------------------------------------------------
+# autotuned layouts: same mathematics, different fixed-order partial sums
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_autotuned_layout_parity(method, tmp_path, monkeypatch):
+    monkeypatch.setenv("LOGDET_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    B._lib.logdet_autotune_clear()
+    A = W.laplacian_3d(22, 20, 19, shift=0.02)     # n = 8360, 40-probe block: splits 1, 2, 4
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        if method == "oslq":
+            est = O.oslq(Q, 60, 20, seed=6)
+            res = h.oslq(60, 20, seed=6, autotune=1)
+            again = h.oslq(60, 20, seed=6, autotune=1)   # cached layout: same result
+        else:
+            est = O.osaiop(Q, 60, 20, k=4, seed=6)
+            res = h.osaiop(60, 20, iop_window=4, seed=6, autotune=1)
+            again = h.osaiop(60, 20, iop_window=4, seed=6, autotune=1)
+    assert rel(res.logdet, est.logdet) <= RTOL_FP64
+    assert again.logdet == res.logdet
+    lines = (tmp_path / "tune.txt").read_text().strip().splitlines()
+    assert lines and all(len(l.split()) == 8 for l in lines)
+
+
+def test_autotuned_mixed_within_1e4_of_fp64():
+    A = W.matern_2d(200, 0.05)
+    with B.Handle.from_csr(A) as h:
+        r64 = h.oslq(120, 40, seed=1)
+        r32 = h.oslq(120, 40, seed=1, precision=B.MIXED_FP32, autotune=1)
+    assert rel(r32.logdet, r64.logdet) <= RTOL_MIXED
