@@ -656,8 +656,8 @@ def small_case(args):
                        else __import__("numpy").float64)
     prec = B.MIXED_FP32 if args.small_case_fp32 else B.FP64
     with B.Handle.from_csr(A) as h:
-        r1 = h.oslq(PROBES, 12, seed=1, precision=prec)
-        r2 = h.osaiop(PROBES, 12, iop_window=4, seed=1, precision=prec)
+        r1 = h.oslq(PROBES, 12, seed=1, precision=prec, autotune=args.autotune)
+        r2 = h.osaiop(PROBES, 12, iop_window=4, seed=1, precision=prec, autotune=args.autotune)
     torch.cuda.synchronize()
     print(json.dumps({"small_case": True, "oslq": r1.logdet, "osaiop_k4": r2.logdet,
                       "oslq_ms": r1.device_ms, "osaiop_ms": r2.device_ms}))
@@ -671,8 +671,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", type=int, default=0,
-                    help="1 = autotuned Krylov kernel layout (tuned during warm-up)")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1 = autotuned Krylov kernel layout (tuned during warm-up); 0 = defaults")
     ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift"],
                     default="laplacian3d",
                     help="extra measurement lines (not the default bench): matern = mixed "
