@@ -38,7 +38,7 @@ GRID, SHIFT, PROBES, STEPS_M, WINDOWS = 128, 0.01, 60, 50, (2, 4, 8)
 SOLVES_PER_STEP = 1 + len(WINDOWS)
 # FP64 FMA peak of this GPU: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-PROFILE_MD = os.path.join(ROOT, "profiles", "k_spmm_fp64_laplacian3d_100.md")
+PROFILE_MD = os.path.join(ROOT, "profiles", "k_spmm_fp64_laplacian3d_100.md")  # noqa
 KRYLOV_SRC = os.path.join(ROOT, "paper_2606_07004_gb300", "csrc", "krylov.cu")
 
 
