@@ -49,7 +49,7 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
-from .rademacher import rademacher_block
+from .rademacher import gaussian_block, rademacher_block
 
 CLAMP_REL = 1e-6       # R3
 RANK_TOL = 1e-6        # R14
@@ -309,11 +309,12 @@ FLAG_COMPLEX_LOG = 2
 FLAG_RANK_DEFICIENT = 4
 
 
-def _probes(n, s, r, seed, S, G):
+def _probes(n, s, r, seed, S, G, gaussian=False):
+    gen = gaussian_block if gaussian else rademacher_block
     if S is None:
-        S = rademacher_block(seed, 0, n, s)
+        S = gen(seed, 0, n, s)
     if G is None:
-        G = rademacher_block(seed, 1, n, r)
+        G = gen(seed, 1, n, r)
     return np.asarray(S, dtype=np.float64), np.asarray(G, dtype=np.float64)
 
 
@@ -322,19 +323,25 @@ def _probes(n, s, r, seed, S, G):
 # ---------------------------------------------------------------------------
 
 def oslq(Q, num_probes: int, m: int, seed: int = 0, *, S=None, G=None, lam=None,
-         tol: float = DEFAULT_TOL, reorth: bool = False, dot="numpy") -> Estimate:
-    """log det Q by Algorithm 3 with readings R1, R4, R6, R9, R11-R15."""
+         tol: float = DEFAULT_TOL, reorth: bool = False, dot="numpy", hutchpp: bool = True,
+         gaussian: bool = False) -> Estimate:
+    """log det Q by Algorithm 3 with readings R1, R4, R6, R9, R11-R15.
+
+    hutchpp=False is plain stochastic Lanczos quadrature (Hutchinson, Eq. TE
+    with each quadratic form by the Gauss rule): no sketch, all num_probes
+    probes residual (s = 0, r = num_probes).  gaussian=True draws N(0, 1)
+    probes instead of +-1 (the alternative the paper allows for S)."""
     Q = sp.csr_matrix(Q, dtype=np.float64)
     n = Q.shape[0]
     lam_lo, lam_hi = spectral_interval(Q, lam)
     alpha = lam_hi                                   # R1
     J = sp.csr_matrix((Q.data / alpha, Q.indices, Q.indptr), shape=Q.shape)
-    s, r = _split(num_probes)
+    s, r = _split(num_probes) if hutchpp else (0, num_probes)
     if S is not None:
         s = S.shape[1]
     if G is not None:
         r = G.shape[1]
-    S, G = _probes(n, s, r, seed, S, G)
+    S, G = _probes(n, s, r, seed, S, G, gaussian)
     flags = 0
     Y = J @ S                                        # Eq. power_sketch
     A = orth(Y)
@@ -371,7 +378,8 @@ def oslq(Q, num_probes: int, m: int, seed: int = 0, *, S=None, G=None, lam=None,
 # ---------------------------------------------------------------------------
 
 def osaiop(Q, num_probes: int, m: int, k: int = 2, seed: int = 0, *, S=None, G=None,
-           lam=None, tol: float = DEFAULT_TOL, dot="numpy") -> Estimate:
+           lam=None, tol: float = DEFAULT_TOL, dot="numpy", hutchpp: bool = True,
+           gaussian: bool = False) -> Estimate:
     """log det Q by Algorithm 2 (each L-action by Algorithm 1), readings R2, R3,
     R5-R9, R14-R16."""
     Q = sp.csr_matrix(Q, dtype=np.float64)
@@ -381,18 +389,19 @@ def osaiop(Q, num_probes: int, m: int, k: int = 2, seed: int = 0, *, S=None, G=N
     alpha = lam_lo                                   # R2
     shift = math.log(gamma / alpha)
     Qt = sp.csr_matrix((Q.data / gamma, Q.indices, Q.indptr), shape=Q.shape)
-    s, r = _split(num_probes)
+    s, r = _split(num_probes) if hutchpp else (0, num_probes)
     if S is not None:
         s = S.shape[1]
     if G is not None:
         r = G.shape[1]
-    S, G = _probes(n, s, r, seed, S, G)
+    S, G = _probes(n, s, r, seed, S, G, gaussian)
 
     def L_action(v):
         return iop_log_action(Qt, v, m, k, shift, tol, dot)
 
     flags = 0
-    Y = np.stack([L_action(S[:, i]) for i in range(s)], axis=1)   # R8
+    Y = (np.stack([L_action(S[:, i]) for i in range(s)], axis=1) if s
+         else np.zeros((n, 0)))                                     # R8
     A = orth(Y)
     if A.shape[1] < s:
         flags |= FLAG_RANK_DEFICIENT

@@ -62,6 +62,23 @@ def rademacher_bits(seed: int, stream: int, n: int, ncols: int, col0: int = 0) -
         return splitmix64_mix(key + ctr * GOLDEN)
 
 
+def gaussian_block(seed: int, stream: int, n: int, ncols: int, col0: int = 0) -> np.ndarray:
+    """n x ncols standard normal entries from the same counters (Box-Muller).
+
+    For entry (row, col) with counter output z (as in rademacher_bits) and
+    w = mix(z) (the output finaliser applied once more):
+        u1 = ((z >> 11) + 1) * 2^-53   in (0, 1]
+        u2 = (w >> 11) * 2^-53         in [0, 1)
+        g  = sqrt(-2 log u1) cos(2 pi u2).
+    """
+    z = rademacher_bits(seed, stream, n, ncols, col0)
+    with np.errstate(over="ignore"):
+        w = splitmix64_mix(z)
+    u1 = ((z >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0**-53
+    u2 = (w >> np.uint64(11)).astype(np.float64) * 2.0**-53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
 def rademacher_block(seed: int, stream: int, n: int, ncols: int, col0: int = 0) -> np.ndarray:
     """n x ncols matrix of +-1.0 (float64)."""
     bits = rademacher_bits(seed, stream, n, ncols, col0)

@@ -456,10 +456,12 @@ struct Solve : ISolve {
 
   // Layout of the Krylov kernels for a block of width w: defaults, or the
   // autotuner's choice for this matrix.
-  int layout(int w, TuneCfg* tc) {
+  int layout(int w, bool track_e, TuneCfg* tc) {
     *tc = TuneCfg();
     if (!c.autotune) return LOGDET_OK;
-    return autotune_krylov<T>(h->rowptr, h->colind, vals.p, n, h->nnz, w, st, tc);
+    const int nd = c.method == 0 ? 1 : kk, nb = c.method == 0 ? 2 : kk;
+    return autotune_krylov<T>(h->rowptr, h->colind, vals.p, n, h->nnz, w, nd, nb, track_e ? 1 : 0,
+                              st, tc);
   }
 
   // X0 for the next Krylov run from X64 (a copy in FP32 for the mixed path).
@@ -509,7 +511,7 @@ struct Solve : ISolve {
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
       TuneCfg tc;
-      LD_TRY(layout(ld, &tc));
+      LD_TRY(layout(ld, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
                        nullptr, c.tol, tc));
     } else {
@@ -518,7 +520,7 @@ struct Solve : ISolve {
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
       run->colshift = cshift.p;
       TuneCfg tc;
-      LD_TRY(layout(lds, &tc));
+      LD_TRY(layout(lds, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
                        Vst.p, c.tol, tc));
     }
@@ -555,7 +557,7 @@ struct Solve : ISolve {
     run.reset(new KRun<T>(st));
     run->colshift = cshift.p;
     TuneCfg tc;
-    LD_TRY(layout(ld, &tc));
+    LD_TRY(layout(ld, true, &tc));
     LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
                      c.tol, tc));
     ph = PH_K2;

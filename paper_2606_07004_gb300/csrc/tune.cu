@@ -2,12 +2,12 @@
 //
 // The tunables are the probe-block width of a pass (the block's columns run
 // as 1, 2 or 4 slices), the CTA size (hence rows per CTA iteration) and the
-// tile depth (rows per partial sum).  For a matrix and block width the tuner
-// times every valid combination of one Lanczos-like step -- pass 1 (SpMM and
-// one fused dot) plus pass 2 (update with two basis vectors and the norm) --
-// on scratch blocks with CUDA events, keeps the fastest and caches it per
-// (element type, ld, n, nnz, SM count) in memory and, when LOGDET_TUNE_CACHE
-// names a file, on disk (one line per shape).  A tuned layout changes the
+// tile depth (rows per partial sum).  For a matrix, block width and step
+// shape (window dots of pass 1, basis vectors of pass 2, the extra u_1 dot)
+// the tuner times every valid combination of one such step on scratch blocks
+// with CUDA events, keeps the fastest and caches it per (element type, ld,
+// n, nnz, SM count, step shape) in memory and, when LOGDET_TUNE_CACHE names
+// a file, on disk (one line per shape).  A tuned layout changes the
 // order of the fixed-order partial sums, so its results differ from the
 // default layout's at rounding level only.
 #include "dense.cuh"
@@ -25,7 +25,7 @@
 namespace ld {
 
 namespace {
-using Key = std::tuple<int, int, int, long long, int>;
+using Key = std::tuple<int, int, int, long long, int, int, int, int>;
 std::mutex g_mu;
 std::map<Key, TuneCfg> g_cache;
 bool g_loaded = false;
@@ -37,15 +37,15 @@ void load_file() {
   if (!path) return;
   FILE* f = std::fopen(path, "r");
   if (!f) return;
-  int f32, ld, n, sms, split, threads, iters;
+  int f32, ld, n, sms, nd, nb, ex, split, threads, iters;
   long long nnz;
-  while (std::fscanf(f, "%d %d %d %lld %d %d %d %d", &f32, &ld, &n, &nnz, &sms, &split, &threads,
-                     &iters) == 8) {
+  while (std::fscanf(f, "%d %d %d %lld %d %d %d %d %d %d %d", &f32, &ld, &n, &nnz, &sms, &nd, &nb,
+                     &ex, &split, &threads, &iters) == 11) {
     TuneCfg c;
     c.split = split;
     c.threads = threads;
     c.iters = iters;
-    g_cache[Key(f32, ld, n, nnz, sms)] = c;
+    g_cache[Key(f32, ld, n, nnz, sms, nd, nb, ex)] = c;
   }
   std::fclose(f);
 }
@@ -55,8 +55,9 @@ void save_entry(const Key& k, const TuneCfg& c) {
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%d %d %d %lld %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
-               std::get<3>(k), std::get<4>(k), c.split, c.threads, c.iters);
+  std::fprintf(f, "%d %d %d %lld %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k),
+               std::get<2>(k), std::get<3>(k), std::get<4>(k), std::get<5>(k), std::get<6>(k),
+               std::get<7>(k), c.split, c.threads, c.iters);
   std::fclose(f);
 }
 
@@ -65,10 +66,13 @@ int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
 
 template <typename T>
 int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, long long nnz, int ld,
-                    cudaStream_t st, TuneCfg* out) {
+                    int ndots, int nbasis, int extra, cudaStream_t st, TuneCfg* out) {
   constexpr int V = Vec16<T>::N;
   using Part = typename PartOf<T>::type;
-  const Key key(std::is_same<T, float>::value ? 1 : 0, ld, n, nnz, sm_count());
+  ndots = std::max(1, std::min(ndots, kMaxWin - 1));
+  nbasis = std::max(1, std::min(nbasis, kMaxWin - 1));
+  extra = extra ? 1 : 0;
+  const Key key(std::is_same<T, float>::value ? 1 : 0, ld, n, nnz, sm_count(), ndots, nbasis, extra);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file();
@@ -110,7 +114,7 @@ int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, 
     TileGeom g = tile_geom(ld / c.split, V, c.threads, c.iters);
     min_rows = std::min(min_rows, g.tile_rows);
   }
-  LD_TRY(part.alloc((size_t)2 * ld * div_up(n, min_rows)));
+  LD_TRY(part.alloc((size_t)std::max(ndots, 2) * ld * div_up(n, min_rows)));
   LD_TRY(coef.alloc((size_t)kMaxWin * ld));
   LD_TRY(ycoef.alloc(ld));
   LD_TRY(probe_fill<T>(probe_key(12345, 7), n, ld, 0, x.p, ld, st));
@@ -135,8 +139,8 @@ int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, 
       J.vals = vals;
       J.x = x.p;
       J.y = y.p;
-      J.dotv[0] = x.p;
-      J.ndots = 1;
+      J.ndots = ndots;
+      for (int d = 0; d < ndots; ++d) J.dotv[d] = (d & 1) ? z.p : x.p;
       J.part = part.p;
       J.n = n;
       J.ld = ld;
@@ -150,9 +154,9 @@ int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, 
       UpdJob<T> U;
       memset(&U, 0, sizeof U);
       U.y = y.p;
-      U.basis[0] = x.p;
-      U.basis[1] = y.p;
-      U.nbasis = 2;
+      U.nbasis = nbasis;
+      for (int i = 0; i < nbasis; ++i) U.basis[i] = (i & 1) ? y.p : x.p;
+      U.extra = extra ? x.p : nullptr;
       U.coef = coef.p;
       U.ycoef = ycoef.p;
       U.out = z.p;
@@ -194,9 +198,9 @@ int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, 
 }
 
 template int autotune_krylov<double>(const int*, const int*, const double*, int, long long, int,
-                                     cudaStream_t, TuneCfg*);
+                                     int, int, int, cudaStream_t, TuneCfg*);
 template int autotune_krylov<float>(const int*, const int*, const float*, int, long long, int,
-                                    cudaStream_t, TuneCfg*);
+                                    int, int, int, cudaStream_t, TuneCfg*);
 
 }  // namespace ld
 

@@ -321,7 +321,7 @@ def test_autotuned_layout_parity(method, tmp_path, monkeypatch):
     assert rel(res.logdet, est.logdet) <= RTOL_FP64
     assert again.logdet == res.logdet
     lines = (tmp_path / "tune.txt").read_text().strip().splitlines()
-    assert lines and all(len(l.split()) == 8 for l in lines)
+    assert lines and all(len(l.split()) == 11 for l in lines)
 
 
 def test_autotuned_mixed_within_1e4_of_fp64():

@@ -392,3 +392,54 @@ def test_scaling_makes_log_operator_semidefinite():
     b = O.osaiop(Q, 30, 25, k=2, seed=5)
     assert np.all(b.per_probe >= 0.0)
     assert b.log_alpha == pytest.approx(math.log(lo), rel=1e-15)
+
+
+def test_gaussian_probes_statistics_and_definition():
+    from oracle.rademacher import gaussian_block, rademacher_bits, splitmix64_mix
+    G = gaussian_block(4, 1, 64, 4000)
+    assert abs(G.mean()) < 5 / math.sqrt(G.size)
+    assert abs(G.var() - 1.0) < 0.02
+    assert abs(np.mean(G ** 4) - 3.0) < 0.1                 # normal kurtosis
+    z = int(rademacher_bits(4, 1, 1, 1)[0, 0])
+    w = int(splitmix64_mix(np.uint64(z)))
+    u1 = ((z >> 11) + 1) * 2.0 ** -53
+    u2 = (w >> 11) * 2.0 ** -53
+    assert G[0, 0] == pytest.approx(math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2), rel=1e-15)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_plain_slq_is_hutchinson_with_gauss_rules(method):
+    # hutchpp=False: logdet = n log alpha + (1/r) sum_j |g_j|^2 K(g_j); with
+    # Hadamard probes (1/r) G G^T = I and m = n that is the exact log det.
+    A = W.laplacian_2d(4, shift=0.5).to_scipy()
+    G = _hadamard(16)
+    exact = np.linalg.slogdet(A.toarray())[1]
+    if method == "oslq":
+        est = O.oslq(A, 16, 16, G=G, hutchpp=False, reorth=True)
+    else:
+        est = O.osaiop(A, 16, 16, k=16, G=G, hutchpp=False)
+    assert est.s == 0 and est.r == 16
+    assert est.logdet == pytest.approx(exact, rel=1e-10)
+    # and it is unbiased over seeds with Rademacher probes
+    Q = W.laplacian_2d(10, shift=0.3).to_scipy()
+    vals = [O.oslq(Q, 6, 20, seed=s, hutchpp=False).logdet for s in range(150)]
+    exact = W.closed_form_logdet_laplacian_2d(10, shift=0.3)
+    assert abs(np.mean(vals) - exact) < 4 * np.std(vals) / math.sqrt(len(vals))
+
+
+def test_paper_tolerance_mode_stops_probes_early():
+    # tol = 1e-6 (the GRF experiment's setting) on Q = diag with 4 distinct
+    # values: every Krylov run stops at dimension 4 with exact forms, and with
+    # Hadamard residual probes the whole estimate is the exact log det.
+    d = np.repeat([1.0, 2.0, 4.0, 8.0], 16)
+    Q = W.diagonal_matrix(d).to_scipy()
+    v = np.random.default_rng(0).standard_normal(64)
+    run = O.arnoldi_iop(Q / 2.0, v, 20, k=2, tol=1e-6)
+    assert run.m_eff == 4
+    al, be = O.lanczos(Q / 8.0, v, 20, tol=1e-6)
+    assert al.size == 4
+    S = O.rademacher_block(1, 0, 64, 3)
+    G = _hadamard(64)
+    exact = float(np.sum(np.log(d)))
+    assert O.osaiop(Q, 9, 20, k=2, S=S, G=G, tol=1e-6).logdet == pytest.approx(exact, rel=1e-10)
+    assert O.oslq(Q, 9, 20, S=S, G=G, tol=1e-6).logdet == pytest.approx(exact, rel=1e-10)
