@@ -94,6 +94,12 @@ typedef struct {
   void* stream;        /* optional cudaStream_t for this call; NULL = handle's */
   double shift;        /* solve for Q + shift*I (shift >= 0) without copying Q; the
                           Gershgorin interval moves by exactly shift.  0 = Q itself */
+  int32_t plain_slq;   /* 1 = no Hutch++ split: all num_probes probes are residual
+                          probes (s = 0), i.e. Hutchinson's estimator (Eq. TE) with
+                          each form by the Gauss rule / Algorithm 1; num_probes >= 1 */
+  int32_t gaussian_probes; /* 1 = N(0,1) probes by Box-Muller from the same counters:
+                          u1 = ((z>>11)+1) 2^-53, u2 = (mix(z)>>11) 2^-53,
+                          g = sqrt(-2 log u1) cos(2 pi u2); 0 = Rademacher */
 } logdet_opts;
 
 /* Fill an opts struct with the defaults. */
@@ -165,6 +171,12 @@ int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
  */
 int logdet_probe_fill(uint64_t seed, int32_t stream, int32_t n, int32_t ncols, int32_t col0,
                       double* out_dev, int32_t ld, void* cuda_stream);
+
+/* logdet_probe_fill_gaussian: the Gaussian alternative for the probes
+ * (Algorithms 2/3 allow "Rademacher or Gaussian"), entry formula as for
+ * logdet_opts.gaussian_probes; layout as logdet_probe_fill. */
+int logdet_probe_fill_gaussian(uint64_t seed, int32_t stream, int32_t n, int32_t ncols,
+                               int32_t col0, double* out_dev, int32_t ld, void* cuda_stream);
 
 /* logdet_spmm: Y = Q X for a device block X (n x b, leading dimension ld,
  * FP64), the matrix-vector products that are the estimators' only access to

@@ -36,7 +36,7 @@ EXPORTED = [
     "logdet_opts_default", "logdet_strerror", "logdet_last_error",
     "logdet_create", "logdet_create_device", "logdet_destroy", "logdet_info",
     "logdet_oslq", "logdet_osaiop",
-    "logdet_probe_fill", "logdet_spmm", "logdet_orth",
+    "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc",
@@ -74,6 +74,7 @@ class logdet_opts(C.Structure):
         ("autotune", C.c_int32),
         ("per_probe", C.POINTER(C.c_double)), ("z_norm2", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("shift", C.c_double),
+        ("plain_slq", C.c_int32), ("gaussian_probes", C.c_int32),
     ]
 
 
@@ -98,6 +99,7 @@ _sig("logdet_info", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_d
 for _n in ("logdet_oslq", "logdet_osaiop"):
     _sig(_n, C.c_int, [_P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts), C.POINTER(logdet_result)])
 _sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
+_sig("logdet_probe_fill_gaussian", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
 _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
@@ -152,7 +154,7 @@ def _stream(stream) -> int:
     return getattr(stream, "cuda_stream", stream)
 
 
-def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0):
+def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0, plain=0, gaussian=0):
     o = logdet_opts()
     _lib.logdet_opts_default(C.byref(o))
     o.precision = precision
@@ -165,6 +167,8 @@ def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0):
     o.stream = _stream(stream) or None
     o.shift = shift
     o.autotune = int(autotune)
+    o.plain_slq = int(plain)
+    o.gaussian_probes = int(gaussian)
     return o
 
 
@@ -249,26 +253,27 @@ class Handle:
         return n.value, nnz.value, lo.value, hi.value
 
     def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
-             lam, stream, shift=0.0, autotune=0):
-        s = num_probes // 3
+             lam, stream, shift=0.0, autotune=0, plain=0, gaussian=0):
+        s = 0 if plain else num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = _make_opts(precision, tol, lam, stream, shift, per, zn, autotune)
+        o = _make_opts(precision, tol, lam, stream, shift, per, zn, autotune, plain, gaussian)
         res = logdet_result()
         _check(fn(self._h, num_probes, krylov_steps, iop_window, seed, C.byref(o), C.byref(res)),
                name)
         return _result(res, per, zn, s, r)
 
     def oslq(self, num_probes, krylov_steps, seed=0, iop_window=0, precision=FP64, tol=None,
-             lam=None, stream=None, shift=0.0, autotune=0) -> Result:
+             lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0) -> Result:
         return self._run(_lib.logdet_oslq, "logdet_oslq", num_probes, krylov_steps, iop_window,
-                         seed, precision, tol, lam, stream, shift, autotune)
+                         seed, precision, tol, lam, stream, shift, autotune, plain, gaussian)
 
     def osaiop(self, num_probes, krylov_steps, iop_window=2, seed=0, precision=FP64, tol=None,
-               lam=None, stream=None, shift=0.0, autotune=0) -> Result:
+               lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0) -> Result:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
-                         iop_window, seed, precision, tol, lam, stream, shift, autotune)
+                         iop_window, seed, precision, tol, lam, stream, shift, autotune, plain,
+                         gaussian)
 
     def estimate_bytes(self, method, num_probes, krylov_steps, iop_window=0, precision=FP64,
                        shift=0.0) -> int:
@@ -373,6 +378,11 @@ def logdet_osaiop(h: Handle, num_probes, krylov_steps, iop_window=2, seed=0, **k
 def logdet_probe_fill(seed, stream_id, n, ncols, col0, out, ld, stream=None):
     _check(_lib.logdet_probe_fill(seed, stream_id, n, ncols, col0, _ptr(out), ld, _stream(stream)),
            "logdet_probe_fill")
+
+
+def logdet_probe_fill_gaussian(seed, stream_id, n, ncols, col0, out, ld, stream=None):
+    _check(_lib.logdet_probe_fill_gaussian(seed, stream_id, n, ncols, col0, _ptr(out), ld,
+                                           _stream(stream)), "logdet_probe_fill_gaussian")
 
 
 def logdet_spmm(h: Handle, x, y, b, ld, stream=None):

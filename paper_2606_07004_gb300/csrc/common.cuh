@@ -60,6 +60,22 @@ __host__ __device__ __forceinline__ int probe_sign(uint64_t key, uint32_t col, u
   return (sm64_mix(key + ctr * kGolden) >> 63) ? -1 : 1;
 }
 
+// Standard normal entry (row, col) from the same counter (Box-Muller): with z
+// the counter output and w = mix(z), u1 = ((z >> 11) + 1) 2^-53 in (0, 1],
+// u2 = (w >> 11) 2^-53 in [0, 1), g = sqrt(-2 log u1) cos(2 pi u2).
+__device__ __forceinline__ double probe_gauss(uint64_t key, uint32_t col, uint32_t row) {
+  const uint64_t ctr = ((uint64_t)col << 32) + (uint64_t)row + 1ull;
+  const uint64_t z = sm64_mix(key + ctr * kGolden);
+  const uint64_t w = sm64_mix(z);
+  const double u1 = ((double)(z >> 11) + 1.0) * 0x1p-53;
+  const double u2 = (double)(w >> 11) * 0x1p-53;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+}
+
+__device__ __forceinline__ double probe_value(uint64_t key, uint32_t col, uint32_t row, int gaussian) {
+  return gaussian ? probe_gauss(key, col, row) : (double)probe_sign(key, col, row);
+}
+
 // ---------------------------------------------------------------------------
 // 16-byte vectors of the block element type.
 // ---------------------------------------------------------------------------

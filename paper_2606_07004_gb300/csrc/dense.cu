@@ -238,7 +238,8 @@ constexpr int kProjNP = (kMaxSketch * kMaxSketch + kGramThreads - 1) / kGramThre
 
 __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__ A, int lda,
                                                       int n, int s, int r, uint64_t key,
-                                                      int ntiles, double* __restrict__ part) {
+                                                      int ntiles, double* __restrict__ part,
+                                                      int gaussian) {
   __shared__ double sa[kGramChunk * kMaxSketch];
   __shared__ double sg[kGramChunk * kMaxSketch];
   const int npairs = s * r;
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
       }
       for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
         int rr = e / r, j = e - rr * r;
-        sg[rr * r + j] = (double)probe_sign(key, (uint32_t)j, (uint32_t)(c0 + rr));
+        sg[rr * r + j] = probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
       }
       __syncthreads();
       for (int rr = 0; rr < rows; ++rr) {
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
 // X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j]
 __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n, int s, int r,
                                                  uint64_t key, const double* __restrict__ Bm,
-                                                 double* X, int ldx, int zcol0) {
+                                                 double* X, int ldx, int zcol0, int gaussian) {
   __shared__ double sb[kMaxSketch * kMaxSketch];
   __shared__ double sa[kGramChunk * kMaxSketch];
   for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = Bm[e];
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n
       int rr = e / r, j = e - rr * r;
       double acc = 0.0;
       for (int i = 0; i < s; ++i) acc = fma(sa[rr * s + i], sb[i * r + j], acc);
-      double g = (double)probe_sign(key, (uint32_t)j, (uint32_t)(c0 + rr));
+      double g = probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
       X[(size_t)(c0 + rr) * ldx + zcol0 + j] = g - acc;
     }
   }
@@ -313,7 +314,8 @@ size_t project_workspace_doubles(int n, int s, int r) {
 }
 
 int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
-                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st) {
+                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
+                          int gaussian) {
   if (s > kMaxSketch || r > kMaxSketch || r < 1) {
     set_error("project: s=%d r=%d out of range", s, r);
     return LOGDET_EINVAL;
@@ -325,13 +327,13 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
   prof_count();
   prof_count();
   if (s > 0) {
-    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, ntiles, part);
+    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, ntiles, part, gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
   }
   k_project<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(A, lda, n, s, r, key, Bm, X, ldx,
-                                                             zcol0);
+                                                             zcol0, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
@@ -754,26 +756,27 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
 // Probe fill and block conversion.
 // ===========================================================================
 template <typename T>
-__global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld) {
+__global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, int gaussian) {
   const size_t total = (size_t)n * ld;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     int row = (int)(e / ld), c = (int)(e - (size_t)row * ld);
     T v = T(0);
-    if (c < ncols) v = T(probe_sign(key, (uint32_t)(col0 + c), (uint32_t)row));
+    if (c < ncols) v = T(probe_value(key, (uint32_t)(col0 + c), (uint32_t)row, gaussian));
     out[e] = v;
   }
 }
 
 template <typename T>
-int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st) {
+int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st,
+               int gaussian) {
   ProfScope prof(KC_OTHER, st, 0.0, (double)n * ld * sizeof(T));
-  k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, n, ncols, col0, out, ld);
+  k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, n, ncols, col0, out, ld, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
-template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t);
-template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t);
+template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t, int);
+template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t, int);
 
 __global__ void k_fill_double(double* out, size_t count, double value) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;

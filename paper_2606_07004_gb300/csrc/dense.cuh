@@ -24,7 +24,8 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
 // generated on the fly; written into X[:, zcol0 .. zcol0+r) (leading dim ldx).
 // A is X[:, 0..s) when a_in_x, else a separate block (lda).
 int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
-                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st);
+                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
+                          int gaussian = 0);
 size_t project_workspace_doubles(int n, int s, int r);
 
 // Per-column squared norms of a block (FP64 or FP32 elements): partials
@@ -46,7 +47,8 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
 
 // Probe fill (FP64 or FP32 +-1 block), columns col0..col0+ncols of stream key.
 template <typename T>
-int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st);
+int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st,
+               int gaussian = 0);
 
 // out[i] = value for i < count.
 int fill_double(double* out, size_t count, double value, cudaStream_t st);

@@ -57,6 +57,8 @@ static SolveCfg make_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t s
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
     c.autotune = opts->autotune;
+    c.plain = opts->plain_slq;
+    c.gaussian = opts->gaussian_probes;
   }
   return c;
 }
@@ -149,6 +151,18 @@ int logdet_probe_fill(uint64_t seed, int32_t stream, int32_t n, int32_t ncols, i
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   LD_TRY(probe_fill<double>(probe_key(seed, stream), n, ncols, col0, out_dev, ld, st));
+  LD_CUDA(cudaStreamSynchronize(st));
+  return LOGDET_OK;
+}
+
+int logdet_probe_fill_gaussian(uint64_t seed, int32_t stream, int32_t n, int32_t ncols,
+                               int32_t col0, double* out_dev, int32_t ld, void* cuda_stream) {
+  if (n < 1 || ncols < 0 || col0 < 0 || ld < ncols || !out_dev || stream < 0) {
+    set_error("probe_fill_gaussian: bad arguments");
+    return LOGDET_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  LD_TRY(probe_fill<double>(probe_key(seed, stream), n, ncols, col0, out_dev, ld, st, 1));
   LD_CUDA(cudaStreamSynchronize(st));
   return LOGDET_OK;
 }

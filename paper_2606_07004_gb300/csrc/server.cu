@@ -331,6 +331,8 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
     c.autotune = opts->autotune;
+    c.plain = opts->plain_slq;
+    c.gaussian = opts->gaussian_probes;
     r->user_per_probe = opts->per_probe;
     r->user_zn2 = opts->z_norm2;
   }
@@ -371,6 +373,8 @@ int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes, i
     c.lam_hi = opts->lambda_hi;
     c.shift = opts->shift;
     c.autotune = opts->autotune;
+    c.plain = opts->plain_slq;
+    c.gaussian = opts->gaussian_probes;
   }
   LD_TRY(validate_cfg(h, c));
   *bytes = estimate_solve_bytes(h, c);

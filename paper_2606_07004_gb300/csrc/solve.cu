@@ -24,12 +24,15 @@ void spectral_bounds(const logdet_ctx* h, const SolveCfg& c, double& lo, double&
 }
 
 int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
-  if (c.P < 3) { set_error("num_probes must be >= 3"); return LOGDET_EINVAL; }
+  if (c.P < (c.plain ? 1 : 3)) {
+    set_error("num_probes must be >= %d", c.plain ? 1 : 3);
+    return LOGDET_EINVAL;
+  }
   if (c.m < 1 || c.m > h->n || c.m > kMaxSteps) {
     set_error("krylov_steps=%d must be in [1, min(n, %d)]", c.m, kMaxSteps);
     return LOGDET_EINVAL;
   }
-  const int s = c.P / 3, r = c.P - 2 * s;
+  const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s;
   if (s > kMaxSketch || r > kMaxSketch) {
     set_error("num_probes=%d: s and r must be <= %d", c.P, kMaxSketch);
     return LOGDET_EINVAL;
@@ -370,13 +373,14 @@ __global__ void k_iop_qf(const double* __restrict__ c, int ldc, const double* __
 // Hutch++ split shared by both estimators: A = orth(Y) into X64[:, 0:s],
 // Z = G - A A^T G into X64[:, s:s+r].  No host synchronisation.
 static int hutchpp_split(int n, int s, int r, const double* Y64, int lds, uint64_t key_g,
-                         DevBuf<double>& X64, int ld, int* keep, cudaStream_t st) {
+                         DevBuf<double>& X64, int ld, int* keep, cudaStream_t st, int gaussian) {
   LD_TRY(X64.alloc((size_t)n * ld));
   LD_TRY(X64.zero());
   DevBuf<double> ws(st);
-  LD_TRY(ws.alloc(std::max(orth_workspace_doubles(n, s), project_workspace_doubles(n, s, r))));
-  LD_TRY(orth_fp64(n, s, Y64, lds, X64.p, ld, ws.p, keep, nullptr, st));
-  LD_TRY(project_residual_fp64(n, s, r, X64.p, ld, key_g, X64.p, ld, s, ws.p, st));
+  LD_TRY(ws.alloc(std::max(s ? orth_workspace_doubles(n, s) : 0,
+                           project_workspace_doubles(n, s, r))));
+  if (s > 0) LD_TRY(orth_fp64(n, s, Y64, lds, X64.p, ld, ws.p, keep, nullptr, st));
+  LD_TRY(project_residual_fp64(n, s, r, X64.p, ld, key_g, X64.p, ld, s, ws.p, st, gaussian));
   return LOGDET_OK;
 }
 
@@ -410,11 +414,11 @@ struct Solve : ISolve {
       : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
         keep(st_) {
     n = h->n;
-    s = c.P / 3;
-    r = c.P - 2 * s;
+    s = c.plain ? 0 : c.P / 3;
+    r = c.plain ? c.P : c.P - 2 * s;
     b = s + r;
     ld = round_up(b, Vec16<T>::N);
-    lds = round_up(s, Vec16<T>::N);
+    lds = std::max(round_up(s, Vec16<T>::N), Vec16<T>::N);
     m = c.m;
     kk = c.method == 0 ? 2 : std::min(c.k, m);
     spectral_bounds(h, c, lo, hi);
@@ -428,7 +432,7 @@ struct Solve : ISolve {
 
   int alloc_pinned() {
     const size_t bytes = sizeof(double) * ld + sizeof(double) * (size_t)ld * (m + 2) +
-                         sizeof(int) * ld + sizeof(int) * s + sizeof(uint32_t) * ld +
+                         sizeof(int) * ld + sizeof(int) * (s + 1) + sizeof(uint32_t) * ld +
                          sizeof(uint32_t) * lds + 64;
     LD_CUDA(cudaMallocHost(&pin.p, bytes));
     memset(pin.p, 0, bytes);
@@ -440,7 +444,7 @@ struct Solve : ISolve {
     h_meff = reinterpret_cast<int*>(q);
     q += sizeof(int) * ld;
     h_keep = reinterpret_cast<int*>(q);
-    q += sizeof(int) * s;
+    q += sizeof(int) * (s + 1);
     h_status = reinterpret_cast<uint32_t*>(q);
     q += sizeof(uint32_t) * ld;
     h_status1 = reinterpret_cast<uint32_t*>(q);
@@ -479,7 +483,7 @@ struct Solve : ISolve {
 
   int setup() {
     LD_TRY(alloc_pinned());
-    LD_TRY(keep.alloc(s));
+    LD_TRY(keep.alloc(std::max(s, 1)));
     LD_TRY(vals.alloc(h->nnz));
     const double cscale = c.method == 0 ? alpha : gamma;
     LD_TRY(scaled_values<T>(h, cscale, vals.p, st));
@@ -490,22 +494,42 @@ struct Solve : ISolve {
       LD_TRY(fill_double(cshift.p, cnt, c.shift / cscale, st));
     }
     run.reset(new KRun<T>(st));
+    if (s == 0) {
+      // Plain SLQ: no sketch; the residual probes are the probes themselves.
+      LD_TRY(hutchpp_split(n, 0, r, nullptr, lds, probe_key(c.seed, 1), X64, ld, keep.p, st,
+                           c.gaussian));
+      T* X0;
+      LD_TRY(make_x0(&X0));
+      run->colshift = cshift.p;
+      TuneCfg tc;
+      LD_TRY(layout(ld, c.method == 1, &tc));
+      if (c.method == 0) {
+        LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
+                         nullptr, c.tol, tc));
+        ph = PH_K1;
+      } else {
+        LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0,
+                         nullptr, c.tol, tc));
+        ph = PH_K2;
+      }
+      return LOGDET_OK;
+    }
     if (c.method == 0) {
       // Algorithm 3: Y = J S, A = orth(Y), Z = (I - A A^T) G.
       DevBuf<T> S(st), Yt(st);
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
-      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian));
       LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p));
       S.release();
       if constexpr (std::is_same<T, double>::value) {
-        LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+        LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
       } else {
         DevBuf<double> Y64(st);
         LD_TRY(Y64.alloc((size_t)n * lds));
         LD_TRY((convert_block<T, double>(Yt.p, lds, Y64.p, lds, n, lds, st)));
         Yt.release();
-        LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+        LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
       }
       T* X0;
       LD_TRY(make_x0(&X0));
@@ -517,7 +541,7 @@ struct Solve : ISolve {
     } else {
       // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
       LD_TRY(Vst.alloc((size_t)n * lds * m));
-      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian));
       run->colshift = cshift.p;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
@@ -550,7 +574,7 @@ struct Solve : ISolve {
     cc.release();
     ws.release();
     w.release();
-    LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st));
+    LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
     Y64.release();
     T* X0;
     LD_TRY(make_x0(&X0));
@@ -584,7 +608,7 @@ struct Solve : ISolve {
     LD_CUDA(cudaMemcpyAsync(h_meff, rr.ks.meff.p, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_status, rr.ks.status.p, sizeof(uint32_t) * ld, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_edot, rr.ks.edot.p, sizeof(double) * ld * (m + 2), cudaMemcpyDeviceToHost, st));
-    LD_CUDA(cudaMemcpyAsync(h_keep, keep.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
+    if (s > 0) LD_CUDA(cudaMemcpyAsync(h_keep, keep.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
     LD_CUDA(cudaEventRecord(ev_done, st));
     // Device buffers are released in stream order; the copies above read them first.
@@ -689,8 +713,8 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
   const size_t es = f32 ? 4 : 8;
   const int vec = f32 ? 4 : 2;
   const size_t n = h->n;
-  const int s = c.P / 3, r = c.P - 2 * s, b = s + r;
-  const size_t ld = round_up(b, vec), lds = round_up(s, vec);
+  const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
+  const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
   const size_t vals = (size_t)h->nnz * es;
   const TileGeom g = tile_geom((int)ld, vec);

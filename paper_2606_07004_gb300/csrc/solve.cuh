@@ -36,6 +36,8 @@ struct SolveCfg {
   double shift = 0.0;  // solve for Q + shift I
   int precision = LOGDET_FP64;
   int autotune = 0;    // layout of the Krylov kernels from the autotuner
+  int plain = 0;       // 1 = plain SLQ: no sketch, s = 0, r = P
+  int gaussian = 0;    // 1 = Gaussian probes
 };
 
 struct SolveOut {

@@ -330,3 +330,62 @@ def test_autotuned_mixed_within_1e4_of_fp64():
         r64 = h.oslq(120, 40, seed=1)
         r32 = h.oslq(120, 40, seed=1, precision=B.MIXED_FP32, autotune=1)
     assert rel(r32.logdet, r64.logdet) <= RTOL_MIXED
+
+
+# ---------------------------------------------------------------------------
+# plain SLQ (s = 0), Gaussian probes, the paper's tol = 1e-6 mode
+# ---------------------------------------------------------------------------
+
+def test_gaussian_probe_fill_matches_definition():
+    from oracle.rademacher import gaussian_block
+    n, ncols, ld = 3001, 9, 10
+    out = torch.zeros(n * ld, dtype=torch.float64, device="cuda")
+    B.logdet_probe_fill_gaussian(77, 1, n, ncols, 2, out, ld)
+    got = out.view(n, ld).cpu().numpy()[:, :ncols]
+    want = gaussian_block(77, 1, n, ncols, 2)
+    np.testing.assert_allclose(got, want, rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_plain_slq_parity(method):
+    A = W.laplacian_2d(40, 35, shift=0.2)
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        if method == "oslq":
+            est = O.oslq(Q, 20, 25, seed=2, hutchpp=False)
+            res = h.oslq(20, 25, seed=2, plain=1)
+        else:
+            est = O.osaiop(Q, 20, 25, k=3, seed=2, hutchpp=False)
+            res = h.osaiop(20, 25, iop_window=3, seed=2, plain=1)
+    assert (res.s, res.r) == (0, 20)
+    assert rel(res.logdet, est.logdet) <= RTOL_FP64
+    np.testing.assert_allclose(res.per_probe, est.per_probe, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("method", ["oslq", "osaiop"])
+def test_gaussian_probes_parity(method):
+    A = W.laplacian_3d(13, 12, 11, shift=0.05)
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        if method == "oslq":
+            est = O.oslq(Q, 30, 20, seed=5, gaussian=True)
+            res = h.oslq(30, 20, seed=5, gaussian=1)
+        else:
+            est = O.osaiop(Q, 30, 20, k=2, seed=5, gaussian=True)
+            res = h.osaiop(30, 20, iop_window=2, seed=5, gaussian=1)
+    assert rel(res.logdet, est.logdet) <= RTOL_FP64
+
+
+def test_paper_tolerance_mode_parity():
+    d = np.repeat([1.0, 2.0, 4.0, 8.0, 16.0], 200)
+    A = W.diagonal_matrix(d)
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        r1 = h.osaiop(21, 20, iop_window=2, seed=3, tol=1e-6)
+        r2 = h.oslq(21, 20, seed=3, tol=1e-6)
+    e1 = O.osaiop(Q, 21, 20, k=2, seed=3, tol=1e-6)
+    e2 = O.oslq(Q, 21, 20, seed=3, tol=1e-6)
+    assert r1.steps_max == 5 and r2.steps_max == 5
+    assert r1.status_bits & B.ST_BREAKDOWN
+    assert rel(r1.logdet, e1.logdet) <= RTOL_FP64
+    assert rel(r2.logdet, e2.logdet) <= RTOL_FP64
