@@ -459,6 +459,21 @@ def matern_case(args):
     t = e0.elapsed_time(e1) / 1e3
     ref = h.oslq(P, m, seed=100, precision=B.FP64)
     err = abs(res[0].logdet - ref.logdet) / abs(ref.logdet)
+    # BF16 vector storage trial: same workload, Krylov vectors in BF16.
+    h.oslq(P, m, seed=0, precision=B.MIXED_BF16VEC)
+    B.logdet_profile_reset()
+    B.logdet_profile_enable(True)
+    e0.record(stream)
+    rb = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_BF16VEC, stream=stream)
+          for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.logdet_profile_enable(False)
+    pb = B.profile_snapshot()
+    tb = e0.elapsed_time(e1) / 1e3
+    errb = abs(rb[0].logdet - ref.logdet) / abs(ref.logdet)
+    kbb = pb["spmm"]["bytes"] + pb["update"]["bytes"]
+    kmb = pb["spmm"]["ms"] + pb["update"]["ms"]
     h.close()
     pk, kind = peaks()
     kb = prof["spmm"]["bytes"] + prof["update"]["bytes"]
@@ -479,6 +494,9 @@ def matern_case(args):
                      "spmm_gbs": sp["bytes"] / (sp["ms"] / 1e3) / 1e9,
                      "update_gbs": prof["update"]["bytes"] / (prof["update"]["ms"] / 1e3) / 1e9},
         "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "bf16_vector_trial": {"value": args.steps / tb, "unit": UNIT, "rel_err_vs_fp64": errb,
+                              "within_1e-4": errb <= 1e-4, "krylov_gbs": kbb / (kmb / 1e3) / 1e9,
+                              "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in pb.items()}},
         "clocks": clk}))
     return 0
 

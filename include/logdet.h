@@ -50,6 +50,8 @@ extern "C" {
 #define LOGDET_FP64        0  /* everything in IEEE binary64 */
 #define LOGDET_MIXED_FP32  1  /* FP32 values and vectors, compensated FP32 dots,
                                  FP64 Hutch++ QR and small solves */
+#define LOGDET_MIXED_BF16VEC 2 /* as MIXED_FP32 but the Krylov vectors are stored in
+                                 BF16 (FP32 arithmetic): a trial of the error budget */
 
 #define LOGDET_METHOD_OSLQ    0
 #define LOGDET_METHOD_OSAIOP  1

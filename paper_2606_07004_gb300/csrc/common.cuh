@@ -2,12 +2,14 @@
 // probe generator, vector load/store helpers and compensated FP32 sums.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
 #include <cstdio>
 #include <string>
+#include <type_traits>
 
 #include "../../include/logdet.h"
 
@@ -77,36 +79,64 @@ __device__ __forceinline__ double probe_value(uint64_t key, uint32_t col, uint32
 }
 
 // ---------------------------------------------------------------------------
-// 16-byte vectors of the block element type.
+// Block element types.  A block stores T; arithmetic runs in Compute<T>
+// (BF16 vectors compute in FP32); matrix values are ValOf<T> (FP32 for BF16
+// vectors).  A 16-byte load brings Vec16<T>::N elements.
 // ---------------------------------------------------------------------------
+using bf16 = __nv_bfloat16;
+
+template <typename T> struct Compute { using type = T; };
+template <> struct Compute<bf16> { using type = float; };
+template <typename T> struct ValOf { using type = T; };
+template <> struct ValOf<bf16> { using type = float; };
+
 template <typename T> struct Vec16;
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 template <> struct Vec16<float>  { using type = float4;  static constexpr int N = 4; };
+template <> struct Vec16<bf16>   { using type = uint4;   static constexpr int N = 8; };
 
 template <typename T>
-__device__ __forceinline__ void load_vec(const T* p, T (&v)[Vec16<T>::N]) {
+__device__ __forceinline__ void load_vec(const T* p, typename Compute<T>::type (&v)[Vec16<T>::N]) {
   using V = typename Vec16<T>::type;
   V t = __ldg(reinterpret_cast<const V*>(p));
-  if constexpr (Vec16<T>::N == 2) { v[0] = t.x; v[1] = t.y; }
-  else { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  if constexpr (std::is_same<T, double>::value) { v[0] = t.x; v[1] = t.y; }
+  else if constexpr (std::is_same<T, float>::value) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  else {
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+      float2 f = __bfloat1622float2(h2);
+      v[2 * i] = f.x;
+      v[2 * i + 1] = f.y;
+    }
+  }
 }
 
-// Plain (coherent) load for data written earlier in the same kernel chain.
 template <typename T>
-__device__ __forceinline__ void load_vec_cg(const T* p, T (&v)[Vec16<T>::N]) {
-  using V = typename Vec16<T>::type;
-  V t = *reinterpret_cast<const V*>(p);
-  if constexpr (Vec16<T>::N == 2) { v[0] = t.x; v[1] = t.y; }
-  else { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
-}
-
-template <typename T>
-__device__ __forceinline__ void store_vec(T* p, const T (&v)[Vec16<T>::N]) {
+__device__ __forceinline__ void store_vec(T* p, const typename Compute<T>::type (&v)[Vec16<T>::N]) {
   using V = typename Vec16<T>::type;
   V t;
-  if constexpr (Vec16<T>::N == 2) { t.x = v[0]; t.y = v[1]; }
-  else { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
+  if constexpr (std::is_same<T, double>::value) { t.x = v[0]; t.y = v[1]; }
+  else if constexpr (std::is_same<T, float>::value) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
+  else {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    t.x = w[0]; t.y = w[1]; t.z = w[2]; t.w = w[3];
+  }
   *reinterpret_cast<V*>(p) = t;
+}
+
+// Scalar conversions between block element types (BF16 via FP32, round to nearest).
+template <typename To, typename From>
+__host__ __device__ __forceinline__ To cvt(From x) {
+  if constexpr (std::is_same<To, bf16>::value) return __float2bfloat16_rn((float)x);
+  else if constexpr (std::is_same<From, bf16>::value) return (To)__bfloat162float(x);
+  else return (To)x;
 }
 
 // ---------------------------------------------------------------------------
@@ -150,12 +180,14 @@ struct AccF {
 template <typename T> struct AccOf;
 template <> struct AccOf<double> { using type = AccD; };
 template <> struct AccOf<float>  { using type = AccF; };
+template <> struct AccOf<bf16>   { using type = AccF; };
 
 // Partial sums written by the block kernels and reduced by the scalar kernels.
 // FP64 blocks store one double per partial; FP32 blocks store the (s, e) pair.
 template <typename T> struct PartOf;
 template <> struct PartOf<double> { using type = double; };
 template <> struct PartOf<float>  { using type = float2; };
+template <> struct PartOf<bf16>   { using type = float2; };
 
 __device__ __forceinline__ void put_part(double* p, const AccD& a) { *p = a.s; }
 __device__ __forceinline__ void put_part(float2* p, const AccF& a) { *p = make_float2(a.s, a.e); }

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(512) k_colnorm(const T* __restrict__ X, int n,
     const int row0 = tile * tile_rows, row1 = min(row0 + tile_rows, n);
     if (live) {
       for (int row = row0 + r; row < row1; row += R) {
-        T x[V];
+        typename Compute<T>::type x[V];
         load_vec<T>(X + (size_t)row * ld + g * V, x);
 #pragma unroll
         for (int v = 0; v < V; ++v) acc[v].fma(x[v], x[v]);
@@ -395,6 +395,7 @@ int colnorm_partials(const T* X, int n, int ld, int tile_rows, int ntiles,
 }
 template int colnorm_partials<double>(const double*, int, int, int, int, double*, int, cudaStream_t);
 template int colnorm_partials<float>(const float*, int, int, int, int, float2*, int, cudaStream_t);
+template int colnorm_partials<bf16>(const bf16*, int, int, int, int, float2*, int, cudaStream_t);
 
 // ===========================================================================
 // Gauss quadrature of a symmetric tridiagonal (Sec. 3.1): eigenvalues theta_k
@@ -761,9 +762,9 @@ __global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, i
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     int row = (int)(e / ld), c = (int)(e - (size_t)row * ld);
-    T v = T(0);
-    if (c < ncols) v = T(probe_value(key, (uint32_t)(col0 + c), (uint32_t)row, gaussian));
-    out[e] = v;
+    double v = 0.0;
+    if (c < ncols) v = probe_value(key, (uint32_t)(col0 + c), (uint32_t)row, gaussian);
+    out[e] = cvt<T>(v);
   }
 }
 
@@ -777,6 +778,7 @@ int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStr
 }
 template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t, int);
 template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t, int);
+template int probe_fill<bf16>(uint64_t, int, int, int, bf16*, int, cudaStream_t, int);
 
 __global__ void k_fill_double(double* out, size_t count, double value) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
@@ -797,7 +799,7 @@ __global__ void k_convert(const Tin* in, int ldin, Tout* out, int ldout, int n, 
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     int row = (int)(e / ldout), c = (int)(e - (size_t)row * ldout);
-    out[e] = (c < cols) ? (Tout)in[(size_t)row * ldin + c] : Tout(0);
+    out[e] = (c < cols) ? cvt<Tout>(in[(size_t)row * ldin + c]) : cvt<Tout>(0.0);
   }
 }
 
@@ -812,6 +814,8 @@ int convert_block(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols
 template int convert_block<double, double>(const double*, int, double*, int, int, int, cudaStream_t);
 template int convert_block<double, float>(const double*, int, float*, int, int, int, cudaStream_t);
 template int convert_block<float, double>(const float*, int, double*, int, int, int, cudaStream_t);
+template int convert_block<double, bf16>(const double*, int, bf16*, int, int, int, cudaStream_t);
+template int convert_block<bf16, double>(const bf16*, int, double*, int, int, int, cudaStream_t);
 
 // ===========================================================================
 // OSA-IOP sketch assembly: Y[:, p] = sum_j w[j][p] V_j[:, p]
@@ -826,7 +830,8 @@ __global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ld, int m,
        e += (size_t)gridDim.x * blockDim.x) {
     int row = (int)(e / ld), p = (int)(e - (size_t)row * ld);
     double acc = 0.0;
-    for (int j = 0; j < m; ++j) acc = fma(w[(size_t)j * ld + p], (double)V[j * stride_v + e], acc);
+    for (int j = 0; j < m; ++j)
+      acc = fma(w[(size_t)j * ld + p], cvt<double>(V[j * stride_v + e]), acc);
     if (p < ldy) Y[(size_t)row * ldy + p] = acc;
   }
 }
@@ -841,6 +846,7 @@ int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y
 }
 template int sketch_assemble<double>(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 template int sketch_assemble<float>(const float*, int, int, int, const double*, double*, int, cudaStream_t);
+template int sketch_assemble<bf16>(const bf16*, int, int, int, const double*, double*, int, cudaStream_t);
 
 }  // namespace ld
 

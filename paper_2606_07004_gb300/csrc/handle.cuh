@@ -58,7 +58,7 @@ template <typename T>
 int scaled_values(logdet_ctx* h, double c, T* out, cudaStream_t st);
 
 template <typename T>
-int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const T* x, T* y,
-               int ld, cudaStream_t st, const double* colshift = nullptr);
+int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
+               const T* x, T* y, int ld, cudaStream_t st, const double* colshift = nullptr);
 
 }  // namespace ld

@@ -88,6 +88,7 @@ template <typename T, int NDOT>
 __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
+  using CT = typename Compute<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* smem = reinterpret_cast<Acc*>(smem_raw);
 
@@ -115,14 +116,14 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
     if (live) {
       const T* xcol = J.x + col0;
       for (int row = row0 + r; row < row1; row += R) {
-        T s[V];
+        CT s[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) s[v] = T(0);
+        for (int v = 0; v < V; ++v) s[v] = CT(0);
         const int q0 = __ldg(J.rowptr + row), q1 = __ldg(J.rowptr + row + 1);
         int q = q0;
         for (; q + kGather <= q1; q += kGather) {
           int c[kGather];
-          T a[kGather], xv[kGather][V];
+          CT a[kGather], xv[kGather][V];
 #pragma unroll
           for (int u = 0; u < kGather; ++u) {
             c[u] = __ldg(J.colind + q + u);
@@ -137,26 +138,26 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
         }
         for (; q < q1; ++q) {
           const int c = __ldg(J.colind + q);
-          const T a = __ldg(J.vals + q);
-          T xv[V];
+          const CT a = __ldg(J.vals + q);
+          CT xv[V];
           load_vec<T>(xcol + (size_t)c * J.ld, xv);
 #pragma unroll
           for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
         }
         if (has_shift || has_scale) {
-          T xr[V];
+          CT xr[V];
           load_vec<T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            if (has_shift) s[v] = fma(T(J.colshift[col0 + v]), xr[v], s[v]);
-            if (has_scale) s[v] = s[v] * T(J.colscale[col0 + v]);
+            if (has_shift) s[v] = fma(CT(J.colshift[col0 + v]), xr[v], s[v]);
+            if (has_scale) s[v] = s[v] * CT(J.colscale[col0 + v]);
           }
         }
         store_vec<T>(J.y + (size_t)row * J.ld + col0, s);
 #pragma unroll
         for (int d = 0; d < NDOT; ++d) {
           if (d < ndots) {
-            T u[V];
+            CT u[V];
             load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
@@ -181,6 +182,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch<T> B) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
+  using CT = typename Compute<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* smem = reinterpret_cast<Acc*>(smem_raw);
 
@@ -204,23 +206,23 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
     for (int v = 0; v < V; ++v) { nrm[v].zero(); ex[v].zero(); }
 
     if (live) {
-      T cf[NB > 0 ? NB : 1][V];
-      T yc[V];
+      CT cf[NB > 0 ? NB : 1][V];
+      CT yc[V];
       bool unit = true;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         double a = J.ycoef[col0 + v];
-        yc[v] = T(a);
+        yc[v] = CT(a);
         unit = unit && (a == 1.0);
       }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
 #pragma unroll
-        for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? T(J.coef[i * J.ld + col0 + v]) : T(0);
+        for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? CT(J.coef[i * J.ld + col0 + v]) : CT(0);
 
       for (int row = row0 + r; row < row1; row += R) {
         const size_t off = (size_t)row * J.ld + col0;
-        T o[V];
+        CT o[V];
         load_vec<T>(J.y + off, o);
         if (!unit) {
 #pragma unroll
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
           if (i < nb) {
-            T u[V];
+            CT u[V];
             load_vec<T>(J.basis[i] + off, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[v], o[v]);
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 #pragma unroll
         for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
         if (has_extra) {
-          T u[V];
+          CT u[V];
           load_vec<T>(J.extra + off, u);
 #pragma unroll
           for (int v = 0; v < V; ++v) ex[v].fma(u[v], o[v]);
@@ -456,7 +458,8 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
     const double vb = (double)J.n * J.b * sizeof(T);
     const int extra_reads = J.ndots - ((J.ndots > 0 && J.dotv[0] == J.x) ? 1 : 0);
     flops += 2.0 * (double)J.nnz * J.b + 2.0 * (double)J.n * J.b * J.ndots;
-    bytes += 4.0 * (J.n + 1) + (double)J.nnz * (4 + sizeof(T)) + vb * (2 + extra_reads);
+    bytes += 4.0 * (J.n + 1) + (double)J.nnz * (4 + sizeof(typename ValOf<T>::type)) +
+             vb * (2 + extra_reads);
   }
   ProfScope prof(KC_SPMM, s, flops, bytes);
 #define LD_SPMM_CASE(ND)                                                      \
@@ -528,7 +531,9 @@ int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) { return launch_scal
 
 template int launch_spmm<double>(const SpmmBatch<double>&, int, cudaStream_t);
 template int launch_spmm<float>(const SpmmBatch<float>&, int, cudaStream_t);
+template int launch_spmm<bf16>(const SpmmBatch<bf16>&, int, cudaStream_t);
 template int launch_update<double>(const UpdBatch<double>&, int, cudaStream_t);
 template int launch_update<float>(const UpdBatch<float>&, int, cudaStream_t);
+template int launch_update<bf16>(const UpdBatch<bf16>&, int, cudaStream_t);
 
 }  // namespace ld

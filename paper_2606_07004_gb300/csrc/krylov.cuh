@@ -36,7 +36,7 @@ template <typename T>
 struct SpmmJob {
   const int* rowptr;
   const int* colind;
-  const T* vals;
+  const typename ValOf<T>::type* vals;  // matrix values (FP32 for BF16 blocks)
   const T* x;                      // gather source, n x ld
   T* y;                            // output, n x ld (may be null: dots only is not supported)
   const T* dotv[kMaxWin];          // vectors dotted with y, n x ld each

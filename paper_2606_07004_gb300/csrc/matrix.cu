@@ -244,8 +244,8 @@ template int scaled_values<float>(logdet_ctx*, double, float*, cudaStream_t);
 // One SpMM y = (vals * 1) x over a block (no dots), used by the step entry point
 // and by the OSLQ sketch.
 template <typename T>
-int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const T* x, T* y,
-               int ld, cudaStream_t st, const double* colshift) {
+int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
+               const T* x, T* y, int ld, cudaStream_t st, const double* colshift) {
   TileGeom g = tile_geom(ld, Vec16<T>::N);
   SpmmBatch<T> B;
   memset(&B, 0, sizeof B);
@@ -273,5 +273,6 @@ int spmm_block(const int* rowptr, const int* colind, const T* vals, int n, const
 }
 template int spmm_block<double>(const int*, const int*, const double*, int, const double*, double*, int, cudaStream_t, const double*);
 template int spmm_block<float>(const int*, const int*, const float*, int, const float*, float*, int, cudaStream_t, const double*);
+template int spmm_block<bf16>(const int*, const int*, const float*, int, const bf16*, bf16*, int, cudaStream_t, const double*);
 
 }  // namespace ld

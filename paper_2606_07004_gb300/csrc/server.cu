@@ -118,8 +118,10 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   //    by element type and CTA size
   std::map<int, std::vector<SpmmJob<double>>> sd;
   std::map<int, std::vector<SpmmJob<float>>> sf;
+  std::map<int, std::vector<SpmmJob<bf16>>> sb;
   std::map<int, std::vector<UpdJob<double>>> ud;
   std::map<int, std::vector<UpdJob<float>>> uf;
+  std::map<int, std::vector<UpdJob<bf16>>> ub;
   std::vector<ScalarJob> coef, norm;
   std::vector<int> wc, wn;
   std::vector<ISolve*> stepping;
@@ -127,21 +129,27 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     ISolve* sv = r->solve.get();
     if (!sv || !sv->in_krylov() || r->rc) continue;
     const int th = sv->krylov_threads();
-    if (sv->is_fp32()) sv->add_pass1(&sf[th], coef, wc);
-    else sv->add_pass1(&sd[th], coef, wc);
+    const int ek = sv->elem_kind();
+    if (ek == 0) sv->add_pass1(&sd[th], coef, wc);
+    else if (ek == 1) sv->add_pass1(&sf[th], coef, wc);
+    else sv->add_pass1(&sb[th], coef, wc);
     stepping.push_back(sv);
   }
   if (stepping.empty()) return 0;
   for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first, st));
   for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first, st));
+  for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first, st));
   LD_TRY(launch_scalar_jobs(coef, wc, SK_COEF, st));
   for (ISolve* sv : stepping) {
     const int th = sv->krylov_threads();
-    if (sv->is_fp32()) sv->add_pass2(&uf[th], norm, wn);
-    else sv->add_pass2(&ud[th], norm, wn);
+    const int ek = sv->elem_kind();
+    if (ek == 0) sv->add_pass2(&ud[th], norm, wn);
+    else if (ek == 1) sv->add_pass2(&uf[th], norm, wn);
+    else sv->add_pass2(&ub[th], norm, wn);
   }
   for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first, st));
   for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first, st));
+  for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first, st));
   if (!norm.empty()) LD_TRY(launch_scalar_jobs(norm, wn, SK_NORM, st));
   for (ISolve* sv : stepping) sv->step_issued();
   n_batched_steps += (int64_t)stepping.size();

@@ -50,7 +50,8 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
     set_error("iop_window=%d must be in [1, %d]", c.k, kMaxWin - 1);
     return LOGDET_EINVAL;
   }
-  if (c.precision != LOGDET_FP64 && c.precision != LOGDET_MIXED_FP32) {
+  if (c.precision != LOGDET_FP64 && c.precision != LOGDET_MIXED_FP32 &&
+      c.precision != LOGDET_MIXED_BF16VEC) {
     set_error("precision %d unknown", c.precision);
     return LOGDET_EINVAL;
   }
@@ -112,7 +113,8 @@ int KState::alloc(int method, int b, int ld, int m, int k, double tol, double re
 }
 
 template <typename T>
-int KRun<T>::init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
+int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v, int n_,
+                  long long nnz_, int b_, int ld_,
                   int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol,
                   TuneCfg tc) {
   rowptr = rp;
@@ -242,7 +244,7 @@ ScalarJob KRun<T>::scalar_job(int j, int ndots) const {
   memset(&sj, 0, sizeof sj);
   sj.st = ks.st;
   sj.part = part.p;
-  sj.part_f32 = std::is_same<T, float>::value ? 1 : 0;
+  sj.part_f32 = std::is_same<T, double>::value ? 0 : 1;
   sj.ntiles = ntiles;
   sj.step = j;
   sj.ndots = ndots;
@@ -253,6 +255,7 @@ ScalarJob KRun<T>::scalar_job(int j, int ndots) const {
 
 template struct KRun<double>;
 template struct KRun<float>;
+template struct KRun<bf16>;
 
 // ---------------------------------------------------------------------------
 // batched launches
@@ -299,8 +302,10 @@ int launch_update_jobs(const std::vector<UpdJob<T>>& jobs, int threads, cudaStre
 
 template int launch_spmm_jobs<double>(const std::vector<SpmmJob<double>>&, int, cudaStream_t);
 template int launch_spmm_jobs<float>(const std::vector<SpmmJob<float>>&, int, cudaStream_t);
+template int launch_spmm_jobs<bf16>(const std::vector<SpmmJob<bf16>>&, int, cudaStream_t);
 template int launch_update_jobs<double>(const std::vector<UpdJob<double>>&, int, cudaStream_t);
 template int launch_update_jobs<float>(const std::vector<UpdJob<float>>&, int, cudaStream_t);
+template int launch_update_jobs<bf16>(const std::vector<UpdJob<bf16>>&, int, cudaStream_t);
 
 int launch_scalar_jobs(const std::vector<ScalarJob>& jobs, const std::vector<int>& widths, int kind,
                        cudaStream_t s) {
@@ -400,7 +405,8 @@ struct Solve : ISolve {
   int ph = PH_SETUP;
   int n, s, r, b, ld, lds, m, kk;
   double lo, hi, alpha, gamma, shift;
-  DevBuf<T> vals, Vst, Xc;
+  DevBuf<typename ValOf<T>::type> vals;
+  DevBuf<T> Vst, Xc;
   DevBuf<double> X64, outv, cshift;
   DevBuf<int> keep;
   std::unique_ptr<KRun<T>> run;
@@ -454,7 +460,8 @@ struct Solve : ISolve {
   int phase() const override { return ph; }
   bool in_krylov() const override { return ph == PH_K1 || ph == PH_K2; }
   int krylov_threads() const override { return run ? run->g.threads : 0; }
-  bool is_fp32() const override { return std::is_same<T, float>::value; }
+  bool is_fp32() const override { return !std::is_same<T, double>::value; }
+  int elem_kind() const override { return std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2; }
   cudaEvent_t done_event() const override { return ev_done; }
   size_t bytes_estimate() const override { return estimate_solve_bytes(h, c); }
 
@@ -486,7 +493,7 @@ struct Solve : ISolve {
     LD_TRY(keep.alloc(std::max(s, 1)));
     LD_TRY(vals.alloc(h->nnz));
     const double cscale = c.method == 0 ? alpha : gamma;
-    LD_TRY(scaled_values<T>(h, cscale, vals.p, st));
+    LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
     if (c.shift != 0.0) {
       // (Q + shift I)/c applied as vals/c plus (shift/c) times the row's own entry.
       const size_t cnt = std::max(ld, lds);
@@ -709,14 +716,15 @@ struct Solve : ISolve {
 };
 
 size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
-  const bool f32 = c.precision == LOGDET_MIXED_FP32;
-  const size_t es = f32 ? 4 : 8;
-  const int vec = f32 ? 4 : 2;
+  const bool f32 = c.precision != LOGDET_FP64;
+  const bool b16 = c.precision == LOGDET_MIXED_BF16VEC;
+  const size_t es = b16 ? 2 : f32 ? 4 : 8;
+  const int vec = b16 ? 8 : f32 ? 4 : 2;
   const size_t n = h->n;
   const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
-  const size_t vals = (size_t)h->nnz * es;
+  const size_t vals = (size_t)h->nnz * (f32 ? 4 : 8);
   const TileGeom g = tile_geom((int)ld, vec);
   const size_t ntiles = div_up((int)n, g.tile_rows);
   const size_t part = (size_t)std::max(k, 2) * ld * ntiles * (f32 ? 8 : 8);
@@ -742,6 +750,7 @@ std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_
   *rc = validate_cfg(h, c);
   if (*rc) return nullptr;
   if (c.precision == LOGDET_FP64) return std::unique_ptr<ISolve>(new Solve<double>(h, c, st));
+  if (c.precision == LOGDET_MIXED_BF16VEC) return std::unique_ptr<ISolve>(new Solve<bf16>(h, c, st));
   return std::unique_ptr<ISolve>(new Solve<float>(h, c, st));
 }
 
@@ -752,8 +761,10 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
   if (!sv) return rc;
   std::vector<SpmmJob<double>> sd;
   std::vector<SpmmJob<float>> sf;
+  std::vector<SpmmJob<bf16>> sb;
   std::vector<UpdJob<double>> ud;
   std::vector<UpdJob<float>> uf;
+  std::vector<UpdJob<bf16>> ub;
   std::vector<ScalarJob> sj;
   std::vector<int> widths;
   while (sv->phase() != PH_WAIT) {
@@ -770,14 +781,18 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
       continue;
     }
     const int th = sv->krylov_threads();
-    const bool f32 = sv->is_fp32();
-    sd.clear(); sf.clear(); ud.clear(); uf.clear(); sj.clear(); widths.clear();
-    sv->add_pass1(f32 ? (void*)&sf : (void*)&sd, sj, widths);
-    LD_TRY(f32 ? launch_spmm_jobs<float>(sf, th, st) : launch_spmm_jobs<double>(sd, th, st));
+    const int ek = sv->elem_kind();
+    sd.clear(); sf.clear(); sb.clear(); ud.clear(); uf.clear(); ub.clear(); sj.clear(); widths.clear();
+    sv->add_pass1(ek == 0 ? (void*)&sd : ek == 1 ? (void*)&sf : (void*)&sb, sj, widths);
+    if (ek == 0) LD_TRY(launch_spmm_jobs<double>(sd, th, st));
+    else if (ek == 1) LD_TRY(launch_spmm_jobs<float>(sf, th, st));
+    else LD_TRY(launch_spmm_jobs<bf16>(sb, th, st));
     LD_TRY(launch_scalar_jobs(sj, widths, SK_COEF, st));
     sj.clear(); widths.clear();
-    if (sv->add_pass2(f32 ? (void*)&uf : (void*)&ud, sj, widths)) {
-      LD_TRY(f32 ? launch_update_jobs<float>(uf, th, st) : launch_update_jobs<double>(ud, th, st));
+    if (sv->add_pass2(ek == 0 ? (void*)&ud : ek == 1 ? (void*)&uf : (void*)&ub, sj, widths)) {
+      if (ek == 0) LD_TRY(launch_update_jobs<double>(ud, th, st));
+      else if (ek == 1) LD_TRY(launch_update_jobs<float>(uf, th, st));
+      else LD_TRY(launch_update_jobs<bf16>(ub, th, st));
       LD_TRY(launch_scalar_jobs(sj, widths, SK_NORM, st));
     }
     sv->step_issued();

@@ -64,6 +64,7 @@ struct KState {
 template <typename T> constexpr double rescale_limit();
 template <> constexpr double rescale_limit<double>() { return 200.0; }
 template <> constexpr double rescale_limit<float>() { return 20.0; }
+template <> constexpr double rescale_limit<bf16>() { return 20.0; }
 
 // One Krylov run over a block X0 (n x ld, b live columns): method 0 is
 // three-term Lanczos, method 1 IOP with window k.  With Vfull the basis is
@@ -74,7 +75,7 @@ struct KRun {
   using Part = typename PartOf<T>::type;
   const int* rowptr = nullptr;
   const int* colind = nullptr;
-  const T* vals = nullptr;
+  const typename ValOf<T>::type* vals = nullptr;
   int n = 0;
   long long nnz = 0;
   int b = 0, ld = 0, m = 0, k = 2, method = 0;
@@ -96,7 +97,8 @@ struct KRun {
   explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), st(s) {}
 
   // Allocate and queue the start-block norms and sigma_1 (one launch pair).
-  int init(const int* rp, const int* ci, const T* v, int n_, long long nnz_, int b_, int ld_,
+  int init(const int* rp, const int* ci, const typename ValOf<T>::type* v, int n_, long long nnz_,
+           int b_, int ld_,
            int m_, int k_, int method_, bool track_e_, T* X0_, T* Vfull_, double tol,
            TuneCfg tc = TuneCfg());
   T* ptr(int i) const;
@@ -129,6 +131,7 @@ struct ISolve {
   virtual bool in_krylov() const = 0;
   virtual int krylov_threads() const = 0;
   virtual bool is_fp32() const = 0;
+  virtual int elem_kind() const = 0;  // 0 FP64, 1 FP32, 2 BF16 vectors
   // Run the current non-Krylov phase (SETUP, MID, FINISH) and move on.
   virtual int run_phase() = 0;
   // Krylov step: append this solve's pass-1 job etc. for its next step.

@@ -65,14 +65,16 @@ int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
 }  // namespace
 
 template <typename T>
-int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, long long nnz, int ld,
-                    int ndots, int nbasis, int extra, cudaStream_t st, TuneCfg* out) {
+int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
+                    long long nnz, int ld, int ndots, int nbasis, int extra, cudaStream_t st,
+                    TuneCfg* out) {
   constexpr int V = Vec16<T>::N;
   using Part = typename PartOf<T>::type;
   ndots = std::max(1, std::min(ndots, kMaxWin - 1));
   nbasis = std::max(1, std::min(nbasis, kMaxWin - 1));
   extra = extra ? 1 : 0;
-  const Key key(std::is_same<T, float>::value ? 1 : 0, ld, n, nnz, sm_count(), ndots, nbasis, extra);
+  const int kind = std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2;
+  const Key key(kind, ld, n, nnz, sm_count(), ndots, nbasis, extra);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     load_file();
@@ -201,6 +203,8 @@ template int autotune_krylov<double>(const int*, const int*, const double*, int,
                                      int, int, int, cudaStream_t, TuneCfg*);
 template int autotune_krylov<float>(const int*, const int*, const float*, int, long long, int,
                                     int, int, int, cudaStream_t, TuneCfg*);
+template int autotune_krylov<bf16>(const int*, const int*, const float*, int, long long, int,
+                                   int, int, int, cudaStream_t, TuneCfg*);
 
 }  // namespace ld
 

@@ -7,7 +7,8 @@ namespace ld {
 
 // The fastest TuneCfg for a matrix and block width, timed once and cached.
 template <typename T>
-int autotune_krylov(const int* rowptr, const int* colind, const T* vals, int n, long long nnz, int ld,
-                    int ndots, int nbasis, int extra, cudaStream_t st, TuneCfg* out);
+int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
+                    long long nnz, int ld, int ndots, int nbasis, int extra, cudaStream_t st,
+                    TuneCfg* out);
 
 }  // namespace ld

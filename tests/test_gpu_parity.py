@@ -389,3 +389,18 @@ def test_paper_tolerance_mode_parity():
     assert r1.status_bits & B.ST_BREAKDOWN
     assert rel(r1.logdet, e1.logdet) <= RTOL_FP64
     assert rel(r2.logdet, e2.logdet) <= RTOL_FP64
+
+
+@pytest.mark.parametrize("method,k", [("oslq", 0), ("osaiop", 2)])
+def test_bf16_vector_trial_error_band(method, k):
+    # The BF16-vector trial: FP32 arithmetic, vectors rounded to BF16 (8-bit
+    # mantissa) at every store.  The estimate stays within a 1e-2 relative
+    # band of the FP64 path on this workload (its measured error is reported
+    # by the Matern benchmark line against the 1e-4 budget).
+    A = W.matern_2d(96, 0.05)
+    with B.Handle.from_csr(A) as h:
+        f = h.oslq if method == "oslq" else (lambda *a, **kw: h.osaiop(*a, iop_window=k, **kw))
+        r64 = f(60, 40, seed=4)
+        rb = f(60, 40, seed=4, precision=B.MIXED_BF16VEC)
+    assert rel(rb.logdet, r64.logdet) <= 1e-2
+    assert np.all(np.isfinite(rb.per_probe))
