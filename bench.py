@@ -440,7 +440,8 @@ def matern_case(args):
     P, m = 120, 80
     stream = torch.cuda.Stream()
     for i in range(args.warmup):
-        h.oslq(P, m, seed=i, precision=B.MIXED_FP32, stream=stream)
+        h.oslq(P, m, seed=i, precision=B.MIXED_FP32, stream=stream,
+                   autotune=args.autotune)
     torch.cuda.synchronize()
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
@@ -449,8 +450,8 @@ def matern_case(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_FP32, stream=stream)
-           for i in range(args.steps)]
+    res = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_FP32, stream=stream,
+                  autotune=args.autotune) for i in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
