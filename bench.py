@@ -650,6 +650,12 @@ def multishift_case(args):
     serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh))
               for t, sh in enumerate(shifts)]
     t_serial = time.perf_counter() - t1
+    # Device time per kernel class of one of the solves run alone.
+    B.logdet_profile_reset()
+    B.logdet_profile_enable(True)
+    h.osaiop(P, m, iop_window=k, seed=0, precision=B.MIXED_FP32, shift=float(shifts[0]))
+    B.logdet_profile_enable(False)
+    prof = B.profile_snapshot()
     h.close()
     print(json.dumps({
         "workload": "power-law graph Laplacian n=%d nnz=%d, 8 shifts U[1e-3,1e-1], OSA-IOP m=100 "
@@ -660,17 +666,109 @@ def multishift_case(args):
         "bitwise_equal_batched_vs_serial": all(a.logdet == b.logdet for a, b in zip(batched, serial)),
         "logdets": [r.logdet for r in batched], "shifts": list(map(float, shifts)),
         "bytes_per_solve_estimate": need, "max_resident": st["max_resident"],
+        "kernel_ms_one_solve": {k: v["ms"] for k, v in prof.items()},
+        "krylov_algorithmic_gbs_one_solve": (prof["spmm"]["bytes"] + prof["update"]["bytes"]) /
+        ((prof["spmm"]["ms"] + prof["update"]["ms"]) / 1e3) / 1e9,
         "graph_build_s": t_build}))
+    return 0
+
+
+def small2d_case(args):
+    """Latency-bound workload: 2D 5-point Dirichlet Laplacian 64^2 + 0.1 I
+    (n = 4096, nnz = 20,224; the whole working set sits in L2), OSLQ m = 30
+    with 30 probes, FP64, one seed per solve.  Three ways to run the same
+    solves: the blocking call (about 135 launches issued from the host per
+    solve), a graph plan (the solve captured once, one graph launch per seed;
+    bit-identical results) and the batched server (many solves per launch).
+    Reports solves/s and per-solve latency of each."""
+    import numpy as np
+    import torch
+    from paper_2606_07004_gb300 import binding as B
+    import workloads as W
+
+    A = W.laplacian_2d(64, shift=0.1)
+    P, m = 30, 30
+    N = max(args.steps, 50)
+    with B.Handle.from_csr(A) as h:
+        for i in range(args.warmup):
+            h.oslq(P, m, seed=i)
+        torch.cuda.synchronize()
+        c0 = B.logdet_launch_count()
+        t0 = time.perf_counter()
+        lat_b = []
+        blocking = []
+        for i in range(N):
+            t1 = time.perf_counter()
+            blocking.append(h.oslq(P, m, seed=1000 + i))
+            lat_b.append((time.perf_counter() - t1) * 1e3)
+        t_b = time.perf_counter() - t0
+        launches_b = (B.logdet_launch_count() - c0) / N
+        t0 = time.perf_counter()
+        plan = B.Plan(h, B.METHOD_OSLQ, P, m)
+        t_plan_make = time.perf_counter() - t0
+        for i in range(args.warmup):
+            plan.run(i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat_p = []
+        replay = []
+        for i in range(N):
+            t1 = time.perf_counter()
+            replay.append(plan.run(1000 + i))
+            lat_p.append((time.perf_counter() - t1) * 1e3)
+        t_p = time.perf_counter() - t0
+        same = all(a.logdet == b.logdet and np.array_equal(a.per_probe, b.per_probe)
+                   for a, b in zip(blocking, replay))
+        # Device time per kernel class of one blocking solve (CUDA events per launch).
+        B.logdet_profile_reset()
+        B.logdet_profile_enable(True)
+        for i in range(10):
+            h.oslq(P, m, seed=2000 + i)
+        B.logdet_profile_enable(False)
+        prof = {k: {"ms": v["ms"] / 10, "launches": v["launches"] / 10}
+                for k, v in B.profile_snapshot().items()}
+        kernels = plan.kernels()
+        plan.close()
+        with B.Server(8 << 30) as srv:
+            srv.wait(srv.submit(h, B.METHOD_OSLQ, P, m, seed=0))
+            M = 4 * N
+            t0 = time.perf_counter()
+            ids = [srv.submit(h, B.METHOD_OSLQ, P, m, seed=1000 + i) for i in range(M)]
+            served = [srv.wait(i) for i in ids]
+            t_s = time.perf_counter() - t0
+        same_srv = all(a.logdet == b.logdet for a, b in zip(blocking, served[:N]))
+    exact = W.closed_form_logdet_laplacian_2d(64, shift=0.1)
+    print(json.dumps({
+        "workload": "2D Laplacian 64^2 + 0.1 I (n=4096, nnz=%d), OSLQ m=30, 30 probes, FP64" % A.nnz,
+        "metric": METRIC, "unit": UNIT, "dtype": "f64",
+        "blocking": {"value": N / t_b, "latency_ms": {"p50": _pct(lat_b, 0.5), "p99": _pct(lat_b, 0.99)},
+                     "launches_per_solve": launches_b},
+        "graph_plan": {"value": N / t_p, "latency_ms": {"p50": _pct(lat_p, 0.5), "p99": _pct(lat_p, 0.99)},
+                       "kernels_per_replay": kernels, "capture_s": t_plan_make,
+                       "bitwise_equal_to_blocking": same},
+        "server_batched": {"value": M / t_s, "requests": M, "bitwise_equal_to_blocking": same_srv},
+        "kernel_ms_per_solve": prof,
+        "mean_rel_err_vs_exact": float(np.mean([abs(r.logdet - exact) / exact for r in blocking])),
+        "timing": "host wall clock per solve (submit to result on host), inputs resident"}))
     return 0
 
 
 def small_case(args):
     """One OSLQ (m=12) and one OSA-IOP (k=4, m=12) solve with 60 probes on the 3D
     Laplacian 100^3 + 0.01 I: the capture target for ncu (blocks larger than
-    L2, about 3 GB on the device)."""
+    L2, about 3 GB on the device).  With --workload matern: one mixed-FP32
+    OSLQ solve (m=12, 120 probes) on the Matern 1024^2 operator instead."""
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
+    if args.workload == "matern":
+        import numpy as np
+        A = W.matern_2d(1024, 0.05, dtype=np.float32)
+        with B.Handle.from_csr(A) as h:
+            r = h.oslq(120, 12, seed=1, precision=B.MIXED_FP32, autotune=args.autotune)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_case": "matern", "oslq": r.logdet, "oslq_ms": r.device_ms}))
+        return 0
     A = W.laplacian_3d(100, shift=SHIFT, dtype=__import__("numpy").float32 if args.small_case_fp32
                        else __import__("numpy").float64)
     prec = B.MIXED_FP32 if args.small_case_fp32 else B.FP64
@@ -692,10 +790,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1 = autotuned Krylov kernel layout (tuned during warm-up); 0 = defaults")
-    ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift"],
+    ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift",
+                                           "small2d"],
                     default="laplacian3d",
                     help="extra measurement lines (not the default bench): matern = mixed "
-                         "precision; serving = continuous batching; multishift = 8 shifts")
+                         "precision; serving = continuous batching; multishift = 8 shifts; "
+                         "small2d = latency-bound 64^2 case (blocking, graph plan, server)")
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="server memory budget")
@@ -712,6 +812,8 @@ def main():
         return serving_case(args)
     if args.workload == "multishift":
         return multishift_case(args)
+    if args.workload == "small2d":
+        return small2d_case(args)
     if args.oracle_sample_child is not None:
         print(json.dumps(oracle_sample(args.oracle_sample_child)))
         return 0

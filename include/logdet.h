@@ -268,6 +268,36 @@ int logdet_cancel(logdet_server* s, uint64_t req_id);
 int logdet_release(logdet_server* s, uint64_t req_id);
 int logdet_server_stats(logdet_server* s, logdet_stats* out);
 
+/* ---- graph plans (the paper has no counterpart: a deployment variant of
+ * Algorithms 2 and 3 for repeated estimates of one shape) -------------------
+ * A plan captures one complete OSLQ (method 0) or OSA-IOP (method 1) solve,
+ * with the arguments of logdet_oslq / logdet_osaiop minus the seed, into a
+ * CUDA graph; each logdet_plan_run replays it with a new seed as one graph
+ * launch.  The result for a seed is bit-identical to logdet_oslq /
+ * logdet_osaiop with that seed and the same options.
+ *
+ * logdet_plan_create: validates like logdet_oslq (LOGDET_EINVAL), runs one
+ *   ordinary solve (kernel loading, autotuned layout) and captures the next
+ *   on a stream of its own.  opts->stream (optional) is the stream runs are
+ *   launched on; opts->per_probe / z_norm2 are ignored (see run).  The plan
+ *   borrows the handle: destroy the plan first.  LOGDET_ECUDA if the capture
+ *   or the instantiation fails (logdet_last_error says why).
+ * logdet_plan_run: one estimate for `seed`; blocks until its result is on
+ *   the host.  per_probe (s + r doubles) and z_norm2 (r doubles) are optional
+ *   outputs as in logdet_opts.  result.device_ms times the seed copy and the
+ *   graph launch with CUDA events.  A plan runs one estimate at a time: calls
+ *   on one plan from several threads must be serialised by the caller.
+ * logdet_plan_kernels: kernel launches one run replays.
+ * Memory: between runs a plan holds the graph's device allocations (about
+ *   logdet_estimate_bytes of its shape) and a pinned result buffer. */
+typedef struct logdet_plan_s* logdet_plan;
+int logdet_plan_create(logdet_handle h, int32_t method, int32_t num_probes, int32_t krylov_steps,
+                       int32_t iop_window, const logdet_opts* opts, logdet_plan* out);
+int logdet_plan_run(logdet_plan p, uint64_t seed, logdet_result* out, double* per_probe,
+                    double* z_norm2);
+int logdet_plan_kernels(logdet_plan p, int64_t* kernels);
+void logdet_plan_destroy(logdet_plan p);
+
 /* logdet_hessenberg_log_e1_noalloc: the same computation as
  * logdet_hessenberg_log_e1, for callers that cannot allocate device memory
  * while they run (inside a stream capture that must not gain allocation

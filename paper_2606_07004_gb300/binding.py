@@ -42,6 +42,7 @@ EXPORTED = [
     "logdet_hessenberg_log_e1_noalloc",
     "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
+    "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
 
@@ -117,6 +118,11 @@ _sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
 _sig("logdet_cancel", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
 _sig("logdet_server_stats", C.c_int, [_P, C.POINTER(logdet_server_stats)])
+_sig("logdet_plan_create", C.c_int, [_P, _i32, _i32, _i32, _i32, C.POINTER(logdet_opts),
+                                     C.POINTER(_P)])
+_sig("logdet_plan_run", C.c_int, [_P, _u64, C.POINTER(logdet_result), _P, _P])
+_sig("logdet_plan_kernels", C.c_int, [_P, C.POINTER(_i64)])
+_sig("logdet_plan_destroy", None, [_P])
 _sig("logdet_launch_count", C.c_int64, [])
 _sig("logdet_autotune_clear", C.c_int, [])
 _sig("logdet_profile_enable", C.c_int, [C.c_int])
@@ -288,6 +294,56 @@ class Handle:
 
     def spmm(self, x, y, b, ld, stream=None):
         _check(_lib.logdet_spmm(self._h, _ptr(x), _ptr(y), b, ld, _stream(stream)), "logdet_spmm")
+
+
+class Plan:
+    """A solve of fixed shape captured into a CUDA graph (logdet_plan_create);
+    run(seed) replays it (logdet_plan_run).  Keep the Handle open while the
+    plan lives."""
+
+    def __init__(self, handle: Handle, method: int, num_probes: int, krylov_steps: int,
+                 iop_window: int = 0, precision=FP64, tol=None, lam=None, stream=None,
+                 shift=0.0, autotune=0, plain=0, gaussian=0):
+        self._p = _P()
+        self._handle = handle
+        self.s = 0 if plain else num_probes // 3
+        self.r = num_probes - 2 * self.s
+        dummy = np.zeros(1)
+        o = _make_opts(precision, tol, lam, stream, shift, dummy, dummy, autotune, plain, gaussian)
+        o.per_probe = None
+        o.z_norm2 = None
+        _check(_lib.logdet_plan_create(handle.raw, method, num_probes, krylov_steps, iop_window,
+                                       C.byref(o), C.byref(self._p)), "logdet_plan_create")
+
+    def run(self, seed: int) -> Result:
+        per = np.zeros(max(self.s + self.r, 1))
+        zn = np.zeros(max(self.r, 1))
+        res = logdet_result()
+        _check(_lib.logdet_plan_run(self._p, seed, C.byref(res), _ptr(per), _ptr(zn)),
+               "logdet_plan_run")
+        return _result(res, per, zn, self.s, self.r)
+
+    def kernels(self) -> int:
+        k = _i64()
+        _check(_lib.logdet_plan_kernels(self._p, C.byref(k)), "logdet_plan_kernels")
+        return k.value
+
+    def close(self):
+        if getattr(self, "_p", None):
+            _lib.logdet_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Server:

@@ -81,7 +81,9 @@ __device__ __forceinline__ double probe_value(uint64_t key, uint32_t col, uint32
 // ---------------------------------------------------------------------------
 // Block element types.  A block stores T; arithmetic runs in Compute<T>
 // (BF16 vectors compute in FP32); matrix values are ValOf<T> (FP32 for BF16
-// vectors).  A 16-byte load brings Vec16<T>::N elements.
+// vectors).  One vector load brings Vec16<T>::N elements: 16 bytes for FP64
+// and FP32, 8 bytes (four elements) for BF16, so that a thread holds as many
+// compensated FP32 accumulators for a BF16 block as for an FP32 one.
 // ---------------------------------------------------------------------------
 using bf16 = __nv_bfloat16;
 
@@ -93,7 +95,7 @@ template <> struct ValOf<bf16> { using type = float; };
 template <typename T> struct Vec16;
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 template <> struct Vec16<float>  { using type = float4;  static constexpr int N = 4; };
-template <> struct Vec16<bf16>   { using type = uint4;   static constexpr int N = 8; };
+template <> struct Vec16<bf16>   { using type = uint2;   static constexpr int N = 4; };
 
 template <typename T>
 __device__ __forceinline__ void load_vec(const T* p, typename Compute<T>::type (&v)[Vec16<T>::N]) {
@@ -102,9 +104,9 @@ __device__ __forceinline__ void load_vec(const T* p, typename Compute<T>::type (
   if constexpr (std::is_same<T, double>::value) { v[0] = t.x; v[1] = t.y; }
   else if constexpr (std::is_same<T, float>::value) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
   else {
-    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+    const uint32_t w[2] = {t.x, t.y};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
       __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
       float2 f = __bfloat1622float2(h2);
       v[2 * i] = f.x;
@@ -120,13 +122,13 @@ __device__ __forceinline__ void store_vec(T* p, const typename Compute<T>::type 
   if constexpr (std::is_same<T, double>::value) { t.x = v[0]; t.y = v[1]; }
   else if constexpr (std::is_same<T, float>::value) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
   else {
-    uint32_t w[4];
+    uint32_t w[2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
       __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
       w[i] = *reinterpret_cast<const uint32_t*>(&h2);
     }
-    t.x = w[0]; t.y = w[1]; t.z = w[2]; t.w = w[3];
+    t.x = w[0]; t.y = w[1];
   }
   *reinterpret_cast<V*>(p) = t;
 }

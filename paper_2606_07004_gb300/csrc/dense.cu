@@ -238,8 +238,10 @@ constexpr int kProjNP = (kMaxSketch * kMaxSketch + kGramThreads - 1) / kGramThre
 
 __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__ A, int lda,
                                                       int n, int s, int r, uint64_t key,
+                                                      const uint64_t* __restrict__ keyp,
                                                       int ntiles, double* __restrict__ part,
                                                       int gaussian) {
+  if (keyp) key = *keyp;
   __shared__ double sa[kGramChunk * kMaxSketch];
   __shared__ double sg[kGramChunk * kMaxSketch];
   const int npairs = s * r;
@@ -285,8 +287,10 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
 
 // X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j]
 __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n, int s, int r,
-                                                 uint64_t key, const double* __restrict__ Bm,
+                                                 uint64_t key, const uint64_t* __restrict__ keyp,
+                                                 const double* __restrict__ Bm,
                                                  double* X, int ldx, int zcol0, int gaussian) {
+  if (keyp) key = *keyp;
   __shared__ double sb[kMaxSketch * kMaxSketch];
   __shared__ double sa[kGramChunk * kMaxSketch];
   for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = Bm[e];
@@ -315,7 +319,7 @@ size_t project_workspace_doubles(int n, int s, int r) {
 
 int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
                           double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
-                          int gaussian) {
+                          int gaussian, const uint64_t* keyp) {
   if (s > kMaxSketch || r > kMaxSketch || r < 1) {
     set_error("project: s=%d r=%d out of range", s, r);
     return LOGDET_EINVAL;
@@ -324,16 +328,17 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
   double* part = ws;
   double* Bm = ws + (size_t)s * r * ntiles;
   ProfScope prof(KC_PROJECT, st, 4.0 * n * (double)s * r, 8.0 * n * (2.0 * s + r));
-  prof_count();
-  prof_count();
   if (s > 0) {
-    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, ntiles, part, gaussian);
+    prof_count();
+    prof_count();
+    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, keyp, ntiles, part,
+                                                     gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
   }
-  k_project<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(A, lda, n, s, r, key, Bm, X, ldx,
-                                                             zcol0, gaussian);
+  k_project<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(A, lda, n, s, r, key, keyp, Bm, X,
+                                                             ldx, zcol0, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
@@ -757,7 +762,9 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
 // Probe fill and block conversion.
 // ===========================================================================
 template <typename T>
-__global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, int gaussian) {
+__global__ void k_probe_fill(uint64_t key, const uint64_t* __restrict__ keyp, int n, int ncols,
+                             int col0, T* out, int ld, int gaussian) {
+  if (keyp) key = *keyp;
   const size_t total = (size_t)n * ld;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -770,15 +777,18 @@ __global__ void k_probe_fill(uint64_t key, int n, int ncols, int col0, T* out, i
 
 template <typename T>
 int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st,
-               int gaussian) {
+               int gaussian, const uint64_t* keyp) {
   ProfScope prof(KC_OTHER, st, 0.0, (double)n * ld * sizeof(T));
-  k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, n, ncols, col0, out, ld, gaussian);
+  k_probe_fill<T><<<4 * sm_count(), 256, 0, st>>>(key, keyp, n, ncols, col0, out, ld, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
-template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t, int);
-template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t, int);
-template int probe_fill<bf16>(uint64_t, int, int, int, bf16*, int, cudaStream_t, int);
+template int probe_fill<double>(uint64_t, int, int, int, double*, int, cudaStream_t, int,
+                                 const uint64_t*);
+template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_t, int,
+                                 const uint64_t*);
+template int probe_fill<bf16>(uint64_t, int, int, int, bf16*, int, cudaStream_t, int,
+                                 const uint64_t*);
 
 __global__ void k_fill_double(double* out, size_t count, double value) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;

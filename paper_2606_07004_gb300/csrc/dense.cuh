@@ -20,12 +20,13 @@ size_t orth_workspace_doubles(int n, int s);
 int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
               int* keep_dev, int* s_eff_host, cudaStream_t st);
 
-// Z = G - A (A^T G) with G the Rademacher block of (key, columns 0..r-1)
+// Z = G - A (A^T G) with G the probe block of (key, columns 0..r-1)
 // generated on the fly; written into X[:, zcol0 .. zcol0+r) (leading dim ldx).
-// A is X[:, 0..s) when a_in_x, else a separate block (lda).
+// With keyp non-null the kernels read the key from device memory at run time
+// instead (graph replays with a new seed).
 int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
                           double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
-                          int gaussian = 0);
+                          int gaussian = 0, const uint64_t* keyp = nullptr);
 size_t project_workspace_doubles(int n, int s, int r);
 
 // Per-column squared norms of a block (FP64 or FP32 elements): partials
@@ -45,10 +46,11 @@ size_t hesslog_workspace_doubles(int m, int nprobe);
 int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int nprobe,
                       double* c, int ldc, double* ws, uint32_t* status, cudaStream_t st);
 
-// Probe fill (FP64 or FP32 +-1 block), columns col0..col0+ncols of stream key.
+// Probe fill, columns col0..col0+ncols of stream key (keyp: as for
+// project_residual_fp64).
 template <typename T>
 int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStream_t st,
-               int gaussian = 0);
+               int gaussian = 0, const uint64_t* keyp = nullptr);
 
 // out[i] = value for i < count.
 int fill_double(double* out, size_t count, double value, cudaStream_t st);

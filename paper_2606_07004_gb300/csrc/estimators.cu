@@ -42,31 +42,10 @@ int solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o) {
   return LOGDET_OK;
 }
 
-static SolveCfg make_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t seed,
-                         const logdet_opts* opts) {
-  SolveCfg c;
-  c.method = method;
-  c.P = P;
-  c.m = m;
-  c.k = k;
-  c.seed = seed;
-  if (opts) {
-    c.precision = opts->precision;
-    c.tol = opts->tol > 0.0 ? opts->tol : kDefaultTol;
-    c.lam_lo = opts->lambda_lo;
-    c.lam_hi = opts->lambda_hi;
-    c.shift = opts->shift;
-    c.autotune = opts->autotune;
-    c.plain = opts->plain_slq;
-    c.gaussian = opts->gaussian_probes;
-  }
-  return c;
-}
-
 static int run_estimator(int method, logdet_handle h, int32_t P, int32_t m, int32_t k, uint64_t seed,
                          const logdet_opts* opts, logdet_result* out) {
   if (!h || !out) { set_error("NULL handle or result"); return LOGDET_EINVAL; }
-  SolveCfg c = make_cfg(method, P, m, k, seed, opts);
+  SolveCfg c = make_solve_cfg(method, P, m, k, seed, opts);
   cudaStream_t st = (opts && opts->stream) ? (cudaStream_t)opts->stream : h->stream;
   SolveOut o;
   int rc = solve(h, c, st, o);

@@ -50,6 +50,15 @@ struct DevBuf {
 };
 
 int ensure_pool(int device);
+
+// Pinned host blocks for per-solve results, kept in a process-wide cache
+// instead of allocated and freed per solve (cudaFreeHost synchronises the
+// whole device, which would stall solves queued behind the current one).
+// A released block is handed out again only once the work queued on its
+// stream at release time has finished.  Blocks come in power-of-two sizes
+// (>= 4 KiB); acquire returns nullptr when pinned allocation fails.
+void* pinned_acquire(size_t bytes, size_t* cap);
+void pinned_release(void* p, size_t cap, cudaStream_t st);
 int create_handle(int32_t n, const int32_t* rowptr, const int32_t* colind, const void* vals,
                   int32_t vals_dtype, bool device_ptrs, logdet_handle* out);
 void destroy_handle(logdet_ctx* h);

@@ -3,6 +3,7 @@
 #include "profile.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace ld {
 
@@ -75,7 +76,7 @@ __device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec
 // ---------------------------------------------------------------------------
 // pass 1: y = A x (CSR order per row) and d_i += dotv_i . y
 //
-// Thread (r, g) of a tile owns row r (stepping by R rows) and the 16-byte
+// Thread (r, g) of a tile owns row r (stepping by R rows) and the vector
 // chunk g of the probe columns.  A row's gathers of x are issued four at a
 // time (one memory round trip per four nonzeros), then the remainder.  The
 // CSR arrays are read through the read-only cache; measured on GB300 this
@@ -438,11 +439,21 @@ __global__ void __launch_bounds__(kRedThreads) k_scalar(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM of (kernel, CTA size, shared memory), looked up once
+// per thread and shape instead of once per launch.
 template <typename K>
 static int persistent_grid(K kernel, int threads, size_t smem, int total_tiles) {
+  struct Entry { const void* f; int threads; size_t smem; int per_sm; };
+  thread_local std::vector<Entry> cache;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-  if (per_sm < 1) per_sm = 1;
+  const void* f = reinterpret_cast<const void*>(kernel);
+  for (const Entry& e : cache)
+    if (e.f == f && e.threads == threads && e.smem == smem) per_sm = e.per_sm;
+  if (per_sm == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    cache.push_back(Entry{f, threads, smem, per_sm});
+  }
   return std::max(1, std::min(total_tiles, per_sm * sm_count()));
 }
 

@@ -6,6 +6,7 @@
 
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace ld {
@@ -32,6 +33,75 @@ int ensure_pool(int device) {
     done[device] = true;
   }
   return LOGDET_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pinned host block cache (see handle.cuh).  At most kPinnedCacheMax bytes
+// stay cached; beyond that a released block is freed.
+// ---------------------------------------------------------------------------
+namespace {
+struct PinnedFree {
+  void* p;
+  size_t cap;
+  cudaEvent_t ev;  // recorded on the releasing stream; nullptr = idle
+};
+std::mutex g_pin_mu;
+std::vector<PinnedFree> g_pin_free;
+size_t g_pin_cached = 0;
+constexpr size_t kPinnedCacheMax = size_t(256) << 20;
+}  // namespace
+
+void* pinned_acquire(size_t bytes, size_t* cap) {
+  size_t c = 4096;
+  while (c < bytes) c <<= 1;
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    for (size_t i = 0; i < g_pin_free.size(); ++i) {
+      PinnedFree& f = g_pin_free[i];
+      if (f.cap != c) continue;
+      if (f.ev && cudaEventQuery(f.ev) != cudaSuccess) continue;
+      void* p = f.p;
+      if (f.ev) cudaEventDestroy(f.ev);
+      g_pin_cached -= c;
+      g_pin_free.erase(g_pin_free.begin() + i);
+      *cap = c;
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, c) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *cap = c;
+  return p;
+}
+
+void pinned_release(void* p, size_t cap, cudaStream_t st) {
+  if (!p) return;
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ev = nullptr;
+  } else if (cudaEventRecord(ev, st) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ev);
+    ev = nullptr;
+  }
+  if (!ev) cudaStreamSynchronize(st);
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_cached + cap <= kPinnedCacheMax) {
+      g_pin_free.push_back(PinnedFree{p, cap, ev});
+      g_pin_cached += cap;
+      return;
+    }
+  }
+  if (ev) {
+    cudaEventSynchronize(ev);
+    cudaEventDestroy(ev);
+  }
+  cudaFreeHost(p);
 }
 
 // ---------------------------------------------------------------------------

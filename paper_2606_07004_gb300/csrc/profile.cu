@@ -34,10 +34,14 @@ cudaEvent_t get_event() {
 }  // namespace
 
 void prof_count() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void prof_add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 bool prof_enabled() { return g_on.load(std::memory_order_relaxed); }
 
 int prof_begin(cudaStream_t s) {
   if (!prof_enabled()) return -1;
+  // A stream being captured into a graph takes no timing events.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return -1;
   std::lock_guard<std::mutex> lk(g_mu);
   Rec r{};
   r.a = get_event();

@@ -19,6 +19,7 @@ enum KClass {
 };
 
 void prof_count();  // one kernel launch
+void prof_add_launches(long long n);  // n kernel launches (a graph replay)
 bool prof_enabled();
 // Bracket a launch: begin() records a start event when profiling is on and
 // returns a token; end() records the stop event with the launch's work.

@@ -378,14 +378,16 @@ __global__ void k_iop_qf(const double* __restrict__ c, int ldc, const double* __
 // Hutch++ split shared by both estimators: A = orth(Y) into X64[:, 0:s],
 // Z = G - A A^T G into X64[:, s:s+r].  No host synchronisation.
 static int hutchpp_split(int n, int s, int r, const double* Y64, int lds, uint64_t key_g,
-                         DevBuf<double>& X64, int ld, int* keep, cudaStream_t st, int gaussian) {
+                         DevBuf<double>& X64, int ld, int* keep, cudaStream_t st, int gaussian,
+                         const uint64_t* keyp_g) {
   LD_TRY(X64.alloc((size_t)n * ld));
   LD_TRY(X64.zero());
   DevBuf<double> ws(st);
   LD_TRY(ws.alloc(std::max(s ? orth_workspace_doubles(n, s) : 0,
                            project_workspace_doubles(n, s, r))));
   if (s > 0) LD_TRY(orth_fp64(n, s, Y64, lds, X64.p, ld, ws.p, keep, nullptr, st));
-  LD_TRY(project_residual_fp64(n, s, r, X64.p, ld, key_g, X64.p, ld, s, ws.p, st, gaussian));
+  LD_TRY(project_residual_fp64(n, s, r, X64.p, ld, key_g, X64.p, ld, s, ws.p, st, gaussian,
+                               keyp_g));
   return LOGDET_OK;
 }
 
@@ -394,7 +396,9 @@ static int hutchpp_split(int n, int s, int r, const double* Y64, int lds, uint64
 // ---------------------------------------------------------------------------
 struct PinnedHost {
   void* p = nullptr;
-  ~PinnedHost() { if (p) cudaFreeHost(p); }
+  size_t cap = 0;
+  cudaStream_t st = nullptr;
+  ~PinnedHost() { pinned_release(p, cap, st); }
 };
 
 template <typename T>
@@ -415,6 +419,7 @@ struct Solve : ISolve {
   int *h_meff = nullptr, *h_keep = nullptr;
   uint32_t *h_status = nullptr, *h_status1 = nullptr;
   cudaEvent_t ev_done = nullptr;
+  const uint64_t* dev_keys = nullptr;  // graph plans: probe keys in device memory
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
       : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
@@ -436,11 +441,24 @@ struct Solve : ISolve {
     if (ev_done) cudaEventDestroy(ev_done);
   }
 
+  const uint64_t* dkey(int i) const { return dev_keys ? dev_keys + i : nullptr; }
+  void set_dev_keys(const uint64_t* keys) override { dev_keys = keys; }
+  int prepare_host() override {
+    if (!ev_done) LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    return alloc_pinned();
+  }
+
   int alloc_pinned() {
+    if (pin.p) return LOGDET_OK;
     const size_t bytes = sizeof(double) * ld + sizeof(double) * (size_t)ld * (m + 2) +
                          sizeof(int) * ld + sizeof(int) * (s + 1) + sizeof(uint32_t) * ld +
                          sizeof(uint32_t) * lds + 64;
-    LD_CUDA(cudaMallocHost(&pin.p, bytes));
+    pin.st = st;
+    pin.p = pinned_acquire(bytes, &pin.cap);
+    if (!pin.p) {
+      set_error("pinned host allocation of %zu bytes failed", bytes);
+      return LOGDET_ENOMEM;
+    }
     memset(pin.p, 0, bytes);
     char* q = static_cast<char*>(pin.p);
     h_out = reinterpret_cast<double*>(q);
@@ -504,7 +522,7 @@ struct Solve : ISolve {
     if (s == 0) {
       // Plain SLQ: no sketch; the residual probes are the probes themselves.
       LD_TRY(hutchpp_split(n, 0, r, nullptr, lds, probe_key(c.seed, 1), X64, ld, keep.p, st,
-                           c.gaussian));
+                           c.gaussian, dkey(1)));
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
@@ -526,17 +544,19 @@ struct Solve : ISolve {
       DevBuf<T> S(st), Yt(st);
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
-      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian, dkey(0)));
       LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p));
       S.release();
       if constexpr (std::is_same<T, double>::value) {
-        LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
+        LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
+                             dkey(1)));
       } else {
         DevBuf<double> Y64(st);
         LD_TRY(Y64.alloc((size_t)n * lds));
         LD_TRY((convert_block<T, double>(Yt.p, lds, Y64.p, lds, n, lds, st)));
         Yt.release();
-        LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
+        LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
+                             dkey(1)));
       }
       T* X0;
       LD_TRY(make_x0(&X0));
@@ -548,7 +568,7 @@ struct Solve : ISolve {
     } else {
       // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
       LD_TRY(Vst.alloc((size_t)n * lds * m));
-      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian));
+      LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian, dkey(0)));
       run->colshift = cshift.p;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
@@ -581,7 +601,8 @@ struct Solve : ISolve {
     cc.release();
     ws.release();
     w.release();
-    LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian));
+    LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
+                             dkey(1)));
     Y64.release();
     T* X0;
     LD_TRY(make_x0(&X0));
@@ -616,7 +637,7 @@ struct Solve : ISolve {
     LD_CUDA(cudaMemcpyAsync(h_status, rr.ks.status.p, sizeof(uint32_t) * ld, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_edot, rr.ks.edot.p, sizeof(double) * ld * (m + 2), cudaMemcpyDeviceToHost, st));
     if (s > 0) LD_CUDA(cudaMemcpyAsync(h_keep, keep.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
-    LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    if (!ev_done) LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
     LD_CUDA(cudaEventRecord(ev_done, st));
     // Device buffers are released in stream order; the copies above read them first.
     run.reset();
@@ -719,7 +740,7 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
   const bool f32 = c.precision != LOGDET_FP64;
   const bool b16 = c.precision == LOGDET_MIXED_BF16VEC;
   const size_t es = b16 ? 2 : f32 ? 4 : 8;
-  const int vec = b16 ? 8 : f32 ? 4 : 2;
+  const int vec = f32 ? 4 : 2;  // Vec16<T>::N (BF16 blocks use 8-byte vectors)
   const size_t n = h->n;
   const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
@@ -754,11 +775,43 @@ std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_
   return std::unique_ptr<ISolve>(new Solve<float>(h, c, st));
 }
 
+SolveCfg make_solve_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t seed,
+                        const logdet_opts* opts) {
+  SolveCfg c;
+  c.method = method;
+  c.P = P;
+  c.m = m;
+  c.k = k;
+  c.seed = seed;
+  if (opts) {
+    c.precision = opts->precision;
+    c.tol = opts->tol > 0.0 ? opts->tol : kDefaultTol;
+    c.lam_lo = opts->lambda_lo;
+    c.lam_hi = opts->lambda_hi;
+    c.shift = opts->shift;
+    c.autotune = opts->autotune;
+    c.plain = opts->plain_slq;
+    c.gaussian = opts->gaussian_probes;
+  }
+  return c;
+}
+
 // The blocking path: one solve advanced step by step with batches of one.
 int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o) {
   int rc = LOGDET_OK;
   std::unique_ptr<ISolve> sv = make_solve(h, c, st, &rc);
   if (!sv) return rc;
+  rc = issue_solve(sv.get(), st);
+  if (rc) {
+    cudaStreamSynchronize(st);
+    return rc;
+  }
+  LD_CUDA(cudaEventSynchronize(sv->done_event()));
+  return sv->assemble(o);
+}
+
+int issue_solve(ISolve* sv, cudaStream_t st) {
+  int rc = LOGDET_OK;
   std::vector<SpmmJob<double>> sd;
   std::vector<SpmmJob<float>> sf;
   std::vector<SpmmJob<bf16>> sb;
@@ -768,16 +821,10 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
   std::vector<ScalarJob> sj;
   std::vector<int> widths;
   while (sv->phase() != PH_WAIT) {
-    if (sv->phase() == PH_FAILED) {
-      cudaStreamSynchronize(st);
-      return rc ? rc : LOGDET_ECUDA;
-    }
+    if (sv->phase() == PH_FAILED) return rc ? rc : LOGDET_ECUDA;
     if (!sv->in_krylov()) {
       rc = sv->run_phase();
-      if (rc) {
-        cudaStreamSynchronize(st);
-        return rc;
-      }
+      if (rc) return rc;
       continue;
     }
     const int th = sv->krylov_threads();
@@ -797,8 +844,7 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
     }
     sv->step_issued();
   }
-  LD_CUDA(cudaEventSynchronize(sv->done_event()));
-  return sv->assemble(o);
+  return LOGDET_OK;
 }
 
 }  // namespace ld

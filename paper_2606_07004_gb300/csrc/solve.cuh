@@ -142,6 +142,10 @@ struct ISolve {
   virtual int assemble(SolveOut& o) = 0;
   virtual cudaEvent_t done_event() const = 0;
   virtual size_t bytes_estimate() const = 0;
+  // Graph plans: read the two probe keys (sketch, residual) from device
+  // memory at run time, and take the pinned result buffer before capture.
+  virtual void set_dev_keys(const uint64_t* keys) = 0;
+  virtual int prepare_host() = 0;
 };
 
 std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, int* rc);
@@ -149,5 +153,14 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c);
 
 // Run one solve to completion on its stream (the blocking API).
 int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o);
+
+// Queue every phase of a solve on its stream, with batches of one, until it
+// waits for its result copies; no host synchronisation (so the sequence can
+// be captured into a CUDA graph).
+int issue_solve(ISolve* sv, cudaStream_t st);
+
+// Solver configuration from the C-ABI arguments.
+SolveCfg make_solve_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t seed,
+                        const logdet_opts* opts);
 
 }  // namespace ld
