@@ -159,7 +159,7 @@ int logdet_spmm(logdet_handle h, const double* x, double* y, int32_t b, int32_t 
     LD_TRY(scaled_values<double>(h, 1.0, v.p, st));
     vals = v.p;
   }
-  LD_TRY(spmm_block<double>(h->rowptr, h->colind, vals, h->n, x, y, ld, st));
+  LD_TRY(spmm_block<double>(h->rowptr, h->colind, vals, h->n, x, y, ld, st, nullptr, h));
   LD_CUDA(cudaStreamSynchronize(st));
   return LOGDET_OK;
 }

@@ -4,6 +4,9 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
 
 struct logdet_ctx {
   int device = 0;
@@ -16,6 +19,12 @@ struct logdet_ctx {
   bool owns = false;
   double g_lo = 0.0, g_hi = 0.0;  // Gershgorin interval (unclamped)
   cudaStream_t stream = nullptr;
+  // Irregular sparsity (some row longer than kSplitRowNnz): a host copy of
+  // rowptr and, per tile depth, the SpMM work-item list built from it.
+  int max_row_nnz = 0;
+  std::vector<int> h_rowptr;
+  std::mutex items_mu;
+  std::map<int, std::pair<int4*, int>> items;  // tile_rows -> (device items, count)
 };
 
 namespace ld {
@@ -66,8 +75,14 @@ void destroy_handle(logdet_ctx* h);
 template <typename T>
 int scaled_values(logdet_ctx* h, double c, T* out, cudaStream_t st);
 
+// SpMM work items of a matrix with irregular rows for tiles of tile_rows
+// rows (see SpmmJob::items); *items = nullptr, *count = 0 for a matrix whose
+// rows are all short (uniform row tiles).  Built once per tile depth.
+int spmm_items(logdet_ctx* h, int tile_rows, const int4** items, int* count);
+
 template <typename T>
 int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
-               const T* x, T* y, int ld, cudaStream_t st, const double* colshift = nullptr);
+               const T* x, T* y, int ld, cudaStream_t st, const double* colshift = nullptr,
+               logdet_ctx* h = nullptr);
 
 }  // namespace ld

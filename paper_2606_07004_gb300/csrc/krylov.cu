@@ -96,14 +96,22 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
   for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
     const int jb = find_job(B, gt);
     const SpmmJob<T>& J = B.jobs[jb];
-    const int tile = gt - B.tile_start[jb];
     const int G = J.width / V;
     const int R = blockDim.x / G;
     const int r = threadIdx.x / G;
     const int g = threadIdx.x - r * G;
     const bool live = r < R;
-    const int row0 = tile * J.tile_rows;
-    const int row1 = min(row0 + J.tile_rows, J.n);
+    int tile = gt - B.tile_start[jb];
+    int row0 = tile * J.tile_rows;
+    int row1 = min(row0 + J.tile_rows, J.n);
+    bool split = false;
+    if (J.items) {
+      const int4 it = __ldg(J.items + tile);
+      row0 = it.x;
+      row1 = it.y;
+      tile = it.z;
+      split = it.y < 0;
+    }
     const int col0 = J.col_off + g * V;
     const int ndots = J.ndots;
 
@@ -114,7 +122,76 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
       for (int v = 0; v < V; ++v) acc[d][v].zero();
 
     const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
-    if (live) {
+    if (split) {
+      // One long row: row group r takes nonzeros q0 + r, q0 + r + R, ...;
+      // the groups' sums are added in group order by group 0.
+      const int row = row0;
+      const T* xcol = J.x + col0;
+      CT s[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) s[v] = CT(0);
+      if (live) {
+        const int q0 = __ldg(J.rowptr + row), q1 = __ldg(J.rowptr + row + 1);
+        int q = q0 + r;
+        for (; q + (kGather - 1) * R < q1; q += kGather * R) {
+          int c[kGather];
+          CT a[kGather], xv[kGather][V];
+#pragma unroll
+          for (int u = 0; u < kGather; ++u) {
+            c[u] = __ldg(J.colind + q + u * R);
+            a[u] = __ldg(J.vals + q + u * R);
+          }
+#pragma unroll
+          for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+#pragma unroll
+          for (int u = 0; u < kGather; ++u)
+#pragma unroll
+            for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
+        }
+        for (; q < q1; q += R) {
+          const int c = __ldg(J.colind + q);
+          const CT a = __ldg(J.vals + q);
+          CT xv[V];
+          load_vec<T>(xcol + (size_t)c * J.ld, xv);
+#pragma unroll
+          for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
+        }
+      }
+      CT* sred = reinterpret_cast<CT*>(smem_raw);
+      __syncthreads();
+      if (live) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) sred[threadIdx.x * V + v] = s[v];
+      }
+      __syncthreads();
+      if (live && r == 0) {
+        CT t[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) t[v] = CT(0);
+        for (int rr = 0; rr < R; ++rr)
+#pragma unroll
+          for (int v = 0; v < V; ++v) t[v] += sred[(rr * G + g) * V + v];
+        if (has_shift || has_scale) {
+          CT xr[V];
+          load_vec<T>(xcol + (size_t)row * J.ld, xr);
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            if (has_shift) t[v] = fma(CT(J.colshift[col0 + v]), xr[v], t[v]);
+            if (has_scale) t[v] = t[v] * CT(J.colscale[col0 + v]);
+          }
+        }
+        store_vec<T>(J.y + (size_t)row * J.ld + col0, t);
+#pragma unroll
+        for (int d = 0; d < NDOT; ++d) {
+          if (d < ndots) {
+            CT u[V];
+            load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], t[v]);
+          }
+        }
+      }
+    } else if (live) {
       const T* xcol = J.x + col0;
       for (int row = row0 + r; row < row1; row += R) {
         CT s[V];

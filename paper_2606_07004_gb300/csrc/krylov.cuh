@@ -28,6 +28,7 @@ namespace ld {
 
 constexpr int kMaxWin = 9;    // window vectors per pass (window k <= 8, plus slack)
 constexpr int kMaxJobs = 24;  // jobs per batched launch
+constexpr int kSplitRowNnz = 64;  // rows longer than this are split across a whole CTA
 
 // ---------------------------------------------------------------------------
 // pass 1: SpMM with fused window dots
@@ -43,6 +44,13 @@ struct SpmmJob {
   typename PartOf<T>::type* part;  // [ndots][ld][ntiles]
   const double* colscale;          // optional [ld]: y[:,p] *= colscale[p]
   const double* colshift;          // optional [ld]: y[:,p] += colshift[p] * x[:,p] (before scale)
+  // Work items.  nullptr: ntiles uniform tiles of tile_rows rows, partial
+  // slot = tile.  Otherwise ntiles items in launch order, each {r0, r1, slot,
+  // 0}: rows [r0, r1) spread over the CTA's row groups (r1 > r0), or, with
+  // r1 < 0, the single long row r0 whose nonzeros all row groups share; slot
+  // is the item's partial index (the items in row order), so results do not
+  // depend on the launch order.
+  const int4* items;
   int n, ld, ndots, tile_rows, ntiles;
   int col_off, width;              // columns [col_off, col_off+width) of the block (width % vec == 0)
   int b;                           // live columns in this slice (accounting only)

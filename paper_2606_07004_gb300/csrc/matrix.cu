@@ -273,13 +273,97 @@ int create_handle(int32_t n, const int32_t* rowptr, const int32_t* colind, const
     rc = compute_gershgorin(h, true);
   }
   if (rc) return fail(rc);
+  // Row lengths: keep a host copy of rowptr only when some row is long.
+  {
+    std::vector<int> rp;
+    const int* hp = rowptr;
+    if (device_ptrs) {
+      rp.resize((size_t)n + 1);
+      if (cudaMemcpy(rp.data(), rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        set_error("copy of rowptr to the host failed");
+        return fail(LOGDET_ECUDA);
+      }
+      hp = rp.data();
+    }
+    int mx = 0;
+    for (int i = 0; i < n; ++i) mx = std::max(mx, hp[i + 1] - hp[i]);
+    h->max_row_nnz = mx;
+    if (mx > kSplitRowNnz) h->h_rowptr.assign(hp, hp + n + 1);
+  }
   *out = h;
+  return LOGDET_OK;
+}
+
+// Work items for tiles of tile_rows rows (see SpmmJob::items).  In row order,
+// a row longer than kSplitRowNnz is an item of its own; the rows between long
+// rows are cut into ranges of at most tile_rows rows and at most
+// tile_rows * (mean row length) nonzeros, so that no item holds much more
+// work than a uniform tile.  Items are launched in decreasing order of work
+// (nonzeros + rows), so that persistent CTAs taking every grid-th item end
+// with similar loads.
+int spmm_items(logdet_ctx* h, int tile_rows, const int4** items, int* count) {
+  *items = nullptr;
+  *count = 0;
+  if (h->max_row_nnz <= kSplitRowNnz || h->h_rowptr.empty()) return LOGDET_OK;
+  std::lock_guard<std::mutex> lk(h->items_mu);
+  auto it = h->items.find(tile_rows);
+  if (it != h->items.end()) {
+    *items = it->second.first;
+    *count = it->second.second;
+    return LOGDET_OK;
+  }
+  const int* rp = h->h_rowptr.data();
+  const int n = h->n;
+  const double mean = std::max(1.0, (double)h->nnz / n);
+  const long long budget = std::max<long long>(tile_rows, (long long)(tile_rows * mean));
+  std::vector<int4> list;
+  std::vector<long long> cost;
+  for (int r = 0; r < n;) {
+    const int d = rp[r + 1] - rp[r];
+    if (d > kSplitRowNnz) {
+      list.push_back(make_int4(r, -1, (int)list.size(), 0));
+      cost.push_back((long long)d + 1);
+      ++r;
+      continue;
+    }
+    const int r0 = r;
+    long long sum = 0;
+    while (r < n && r - r0 < tile_rows) {
+      const int dr = rp[r + 1] - rp[r];
+      if (dr > kSplitRowNnz) break;
+      if (r > r0 && sum + dr > budget) break;
+      sum += dr;
+      ++r;
+    }
+    list.push_back(make_int4(r0, r, (int)list.size(), 0));
+    cost.push_back(sum + (r - r0));
+  }
+  std::vector<int> order(list.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int4> launch(list.size());
+  for (size_t i = 0; i < order.size(); ++i) launch[i] = list[order[i]];
+  int4* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int4) * launch.size()) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of %zu SpMM work items failed", launch.size());
+    return LOGDET_ENOMEM;
+  }
+  if (cudaMemcpy(d, launch.data(), sizeof(int4) * launch.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(d);
+    set_error("copy of the SpMM work items failed");
+    return LOGDET_ECUDA;
+  }
+  h->items[tile_rows] = std::make_pair(d, (int)launch.size());
+  *items = d;
+  *count = (int)launch.size();
   return LOGDET_OK;
 }
 
 void destroy_handle(logdet_ctx* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->items) cudaFree(kv.second.first);
   if (h->owns) {
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colind) cudaFree(h->colind);
@@ -315,7 +399,7 @@ template int scaled_values<float>(logdet_ctx*, double, float*, cudaStream_t);
 // and by the OSLQ sketch.
 template <typename T>
 int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
-               const T* x, T* y, int ld, cudaStream_t st, const double* colshift) {
+               const T* x, T* y, int ld, cudaStream_t st, const double* colshift, logdet_ctx* h) {
   TileGeom g = tile_geom(ld, Vec16<T>::N);
   SpmmBatch<T> B;
   memset(&B, 0, sizeof B);
@@ -336,13 +420,21 @@ int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::ty
   J.nnz = 0;
   J.tile_rows = g.tile_rows;
   J.ntiles = div_up(n, g.tile_rows);
+  if (h) {
+    int cnt = 0;
+    LD_TRY(spmm_items(h, g.tile_rows, &J.items, &cnt));
+    if (J.items) J.ntiles = cnt;
+  }
   B.tile_start[0] = 0;
   B.tile_start[1] = J.ntiles;
   B.total_tiles = J.ntiles;
   return launch_spmm<T>(B, g.threads, st);
 }
-template int spmm_block<double>(const int*, const int*, const double*, int, const double*, double*, int, cudaStream_t, const double*);
-template int spmm_block<float>(const int*, const int*, const float*, int, const float*, float*, int, cudaStream_t, const double*);
-template int spmm_block<bf16>(const int*, const int*, const float*, int, const bf16*, bf16*, int, cudaStream_t, const double*);
+template int spmm_block<double>(const int*, const int*, const double*, int, const double*, double*, int,
+                                cudaStream_t, const double*, logdet_ctx*);
+template int spmm_block<float>(const int*, const int*, const float*, int, const float*, float*, int,
+                                cudaStream_t, const double*, logdet_ctx*);
+template int spmm_block<bf16>(const int*, const int*, const float*, int, const bf16*, bf16*, int,
+                                cudaStream_t, const double*, logdet_ctx*);
 
 }  // namespace ld

@@ -135,6 +135,13 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
   width = ld / tune.split;
   g = tile_geom(width, Vec16<T>::N, tune.threads, tune.iters);
   ntiles = div_up(n, g.tile_rows);
+  nslots = ntiles;
+  items = nullptr;
+  if (hctx) {
+    int cnt = 0;
+    LD_TRY(spmm_items(hctx, g.tile_rows, &items, &cnt));
+    if (items) nslots = cnt;
+  }
   blk = (size_t)n * ld;
   const int win = method == 0 ? 2 : k;
   if (method == 1 && win > kMaxWin - 1) {
@@ -143,7 +150,7 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
   }
   ndmax = std::max(win, 2);
   nring = win + 1;
-  LD_TRY(part.alloc((size_t)ndmax * ld * ntiles));
+  LD_TRY(part.alloc((size_t)ndmax * ld * std::max(ntiles, nslots)));
   LD_TRY(y.alloc(blk));
   if (!Vfull) LD_TRY(ring.alloc(blk * nring));
   LD_TRY(ks.alloc(method, b, ld, m, k, tol, rescale_limit<T>()));
@@ -188,7 +195,8 @@ void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
     J.b = slice_live(q);
     J.nnz = nnz;
     J.tile_rows = g.tile_rows;
-    J.ntiles = ntiles;
+    J.ntiles = nslots;
+    J.items = items;
     J.colshift = colshift;
     if (method == 0) {
       J.ndots = 1;
@@ -239,13 +247,13 @@ void KRun<T>::upd_jobs(int j, std::vector<UpdJob<T>>& out) const {
 }
 
 template <typename T>
-ScalarJob KRun<T>::scalar_job(int j, int ndots) const {
+ScalarJob KRun<T>::scalar_job(int j, int ndots, bool spmm_pass) const {
   ScalarJob sj;
   memset(&sj, 0, sizeof sj);
   sj.st = ks.st;
   sj.part = part.p;
   sj.part_f32 = std::is_same<T, double>::value ? 0 : 1;
-  sj.ntiles = ntiles;
+  sj.ntiles = spmm_pass ? nslots : ntiles;
   sj.step = j;
   sj.ndots = ndots;
   sj.win_lo = j >= 1 ? win_lo(j) : 1;
@@ -489,7 +497,7 @@ struct Solve : ISolve {
     *tc = TuneCfg();
     if (!c.autotune) return LOGDET_OK;
     const int nd = c.method == 0 ? 1 : kk, nb = c.method == 0 ? 2 : kk;
-    return autotune_krylov<T>(h->rowptr, h->colind, vals.p, n, h->nnz, w, nd, nb, track_e ? 1 : 0,
+    return autotune_krylov<T>(h, vals.p, w, nd, nb, track_e ? 1 : 0,
                               st, tc);
   }
 
@@ -526,6 +534,7 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
+    run->hctx = h;
       TuneCfg tc;
       LD_TRY(layout(ld, c.method == 1, &tc));
       if (c.method == 0) {
@@ -545,7 +554,7 @@ struct Solve : ISolve {
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian, dkey(0)));
-      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p));
+      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
       S.release();
       if constexpr (std::is_same<T, double>::value) {
         LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
@@ -561,6 +570,7 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
+    run->hctx = h;
       TuneCfg tc;
       LD_TRY(layout(ld, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
@@ -570,6 +580,7 @@ struct Solve : ISolve {
       LD_TRY(Vst.alloc((size_t)n * lds * m));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian, dkey(0)));
       run->colshift = cshift.p;
+    run->hctx = h;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
@@ -608,6 +619,7 @@ struct Solve : ISolve {
     LD_TRY(make_x0(&X0));
     run.reset(new KRun<T>(st));
     run->colshift = cshift.p;
+    run->hctx = h;
     TuneCfg tc;
     LD_TRY(layout(ld, true, &tc));
     LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
@@ -664,7 +676,7 @@ struct Solve : ISolve {
     auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
     const int j = run->next_step();
     run->spmm_jobs(j, v);
-    coef.push_back(run->scalar_job(j, run->pass1_dots(j)));
+    coef.push_back(run->scalar_job(j, run->pass1_dots(j), true));
     widths.push_back(run->ld);
   }
 

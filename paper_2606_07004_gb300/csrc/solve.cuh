@@ -83,10 +83,13 @@ struct KRun {
   T* X0 = nullptr;
   T* Vfull = nullptr;
   const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
+  logdet_ctx* hctx = nullptr;        // matrix handle (work items of irregular matrices)
   TileGeom g{};
   TuneCfg tune{};
   int width = 0;  // columns per slice job (ld / tune.split)
   int ntiles = 0, nring = 0, ndmax = 0;
+  const int4* items = nullptr;  // SpMM work items (nullptr: uniform tiles)
+  int nslots = 0;               // SpMM partial slots per column (ntiles or the item count)
   size_t blk = 0;
   DevBuf<Part> part;
   DevBuf<T> y, ring;
@@ -111,7 +114,8 @@ struct KRun {
   void spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const;
   void upd_jobs(int j, std::vector<UpdJob<T>>& out) const;
   int slice_live(int q) const;
-  ScalarJob scalar_job(int j, int ndots) const;
+  // Scalar job over pass-1 partials (spmm_pass) or pass-2 / norm partials.
+  ScalarJob scalar_job(int j, int ndots, bool spmm_pass = false) const;
 };
 
 // Batched launches of jobs that share element type and CTA size.

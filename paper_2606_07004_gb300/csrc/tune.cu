@@ -65,9 +65,12 @@ int gcd_i(int a, int b) { while (b) { int t = a % b; a = b; b = t; } return a; }
 }  // namespace
 
 template <typename T>
-int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
-                    long long nnz, int ld, int ndots, int nbasis, int extra, cudaStream_t st,
-                    TuneCfg* out) {
+int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, int ndots,
+                    int nbasis, int extra, cudaStream_t st, TuneCfg* out) {
+  const int* rowptr = h->rowptr;
+  const int* colind = h->colind;
+  const int n = h->n;
+  const long long nnz = h->nnz;
   constexpr int V = Vec16<T>::N;
   using Part = typename PartOf<T>::type;
   ndots = std::max(1, std::min(ndots, kMaxWin - 1));
@@ -111,12 +114,15 @@ int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T
   LD_TRY(x.alloc(blk));
   LD_TRY(y.alloc(blk));
   LD_TRY(z.alloc(blk));
-  int min_rows = 1 << 30;
+  int max_slots = 1;
   for (auto& c : cands) {
     TileGeom g = tile_geom(ld / c.split, V, c.threads, c.iters);
-    min_rows = std::min(min_rows, g.tile_rows);
+    const int4* items = nullptr;
+    int cnt = 0;
+    LD_TRY(spmm_items(h, g.tile_rows, &items, &cnt));
+    max_slots = std::max(max_slots, std::max(cnt, div_up(n, g.tile_rows)));
   }
-  LD_TRY(part.alloc((size_t)std::max(ndots, 2) * ld * div_up(n, min_rows)));
+  LD_TRY(part.alloc((size_t)std::max(ndots, 2) * ld * max_slots));
   LD_TRY(coef.alloc((size_t)kMaxWin * ld));
   LD_TRY(ycoef.alloc(ld));
   LD_TRY(probe_fill<T>(probe_key(12345, 7), n, ld, 0, x.p, ld, st));
@@ -131,6 +137,9 @@ int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T
     const int width = ld / c.split;
     TileGeom g = tile_geom(width, V, c.threads, c.iters);
     const int ntiles = div_up(n, g.tile_rows);
+    const int4* items = nullptr;
+    int nitems = 0;
+    LD_TRY(spmm_items(h, g.tile_rows, &items, &nitems));
     std::vector<SpmmJob<T>> sj;
     std::vector<UpdJob<T>> uj;
     for (int q = 0; q < c.split; ++q) {
@@ -151,7 +160,8 @@ int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T
       J.b = width;
       J.nnz = nnz;
       J.tile_rows = g.tile_rows;
-      J.ntiles = ntiles;
+      J.ntiles = items ? nitems : ntiles;
+      J.items = items;
       sj.push_back(J);
       UpdJob<T> U;
       memset(&U, 0, sizeof U);
@@ -199,12 +209,12 @@ int autotune_krylov(const int* rowptr, const int* colind, const typename ValOf<T
   return LOGDET_OK;
 }
 
-template int autotune_krylov<double>(const int*, const int*, const double*, int, long long, int,
-                                     int, int, int, cudaStream_t, TuneCfg*);
-template int autotune_krylov<float>(const int*, const int*, const float*, int, long long, int,
-                                    int, int, int, cudaStream_t, TuneCfg*);
-template int autotune_krylov<bf16>(const int*, const int*, const float*, int, long long, int,
-                                   int, int, int, cudaStream_t, TuneCfg*);
+template int autotune_krylov<double>(logdet_ctx*, const double*, int, int, int, int, cudaStream_t,
+                                    TuneCfg*);
+template int autotune_krylov<float>(logdet_ctx*, const float*, int, int, int, int, cudaStream_t,
+                                    TuneCfg*);
+template int autotune_krylov<bf16>(logdet_ctx*, const float*, int, int, int, int, cudaStream_t,
+                                    TuneCfg*);
 
 }  // namespace ld
 

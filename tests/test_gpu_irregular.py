@@ -1,0 +1,86 @@
+"""Matrices with long rows (irregular sparsity): rows longer than the split
+threshold (64 stored entries) are SpMM work items of their own, shared by a
+whole CTA, and the remaining rows are cut into ranges of bounded work.
+Checks: integer SpMM bit-exact against scipy, FP64 estimates against the
+oracle at the FP64 bar, the mixed path against FP64, and the autotuned
+layout (whose tile depth changes the item list) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_07004_gb300 import binding as B  # noqa: E402
+
+RTOL_FP64 = 1e-10
+
+
+def hubs_and_ring(n, hubs, seed, shift):
+    """A ring on n nodes plus hub nodes joined to random subsets of sizes
+    `hubs` (so their rows hold that many off-diagonal entries)."""
+    rng = np.random.default_rng(seed)
+    edges = [np.stack([np.arange(n), (np.arange(n) + 1) % n], 1)]
+    for h, deg in hubs:
+        nb = rng.choice(np.setdiff1d(np.arange(n), [h]), size=deg, replace=False)
+        edges.append(np.stack([np.full(deg, h), nb], 1))
+    return W.graph_laplacian(n, np.concatenate(edges), shift=shift)
+
+
+CASES = {
+    # one hub joined to every other node: a row of n entries
+    "star": lambda: hubs_and_ring(3001, [(0, 3000)], 1, 0.05),
+    # rows right at the threshold: 62 + ring 2 + diagonal = 65 entries (split);
+    # 61 + 2 + 1 = 64 (not split); hubs spread through the matrix
+    "threshold": lambda: hubs_and_ring(4099, [(5, 62), (700, 61), (2048, 62), (4098, 200)], 2, 0.1),
+    "powerlaw": lambda: W.powerlaw_graph_laplacian(7001, seed=9).with_diagonal_shift(0.02),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_spmm_integer_bit_exact_long_rows(name):
+    A = CASES[name]()
+    A = W.CSR(A.n, A.rowptr, A.colind, np.rint(A.vals * 4.0))   # integer values
+    b, ld = 21, 22
+    X = np.zeros((A.n, ld))
+    X[:, :b] = O.rademacher_block(3, 0, A.n, b)
+    with B.Handle.from_csr(A) as h:
+        y = torch.zeros(A.n * ld, dtype=torch.float64, device="cuda")
+        h.spmm(torch.as_tensor(X.ravel(), device="cuda"), y, b, ld)
+        got = y.view(A.n, ld).cpu().numpy()
+    assert np.array_equal(got, A.to_scipy() @ X)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("method,k", [("oslq", 0), ("osaiop", 4)])
+def test_long_rows_fp64_parity(name, method, k):
+    A = CASES[name]()
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        if method == "oslq":
+            est = O.oslq(Q, 24, 25, seed=3)
+            res = h.oslq(24, 25, seed=3)
+        else:
+            est = O.osaiop(Q, 24, 20, k=k, seed=3)
+            res = h.osaiop(24, 20, iop_window=k, seed=3)
+    assert abs(res.logdet - est.logdet) <= RTOL_FP64 * abs(est.logdet)
+    assert res.s_eff == est.s_eff
+    np.testing.assert_allclose(res.per_probe, est.per_probe, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("name", ["star", "powerlaw"])
+def test_long_rows_mixed_and_autotuned(name):
+    A = CASES[name]()
+    with B.Handle.from_csr(A) as h:
+        r64 = h.osaiop(30, 20, iop_window=2, seed=5)
+        r32 = h.osaiop(30, 20, iop_window=2, seed=5, precision=B.MIXED_FP32)
+        rt = h.osaiop(30, 20, iop_window=2, seed=5, autotune=1)
+    assert abs(r32.logdet - r64.logdet) <= 1e-4 * abs(r64.logdet)
+    est = O.osaiop(A.to_scipy(), 30, 20, k=2, seed=5)
+    assert abs(rt.logdet - est.logdet) <= RTOL_FP64 * abs(est.logdet)
+    assert abs(r64.logdet - est.logdet) <= RTOL_FP64 * abs(est.logdet)

@@ -70,3 +70,15 @@ def test_powerlaw_graph():
 def test_diagonal_shift():
     A = W.laplacian_2d(5).with_diagonal_shift(0.5)
     assert np.allclose(A.to_scipy().diagonal(), 4.5)
+
+
+def test_graph_laplacian_from_edges():
+    import scipy.sparse as sp
+    edges = np.array([[0, 1], [1, 2], [2, 0], [3, 0], [0, 1], [2, 2]])  # duplicate and self-loop
+    A = W.graph_laplacian(5, edges, shift=0.5)
+    L = A.to_scipy().toarray()
+    assert np.array_equal(L, L.T)
+    np.testing.assert_allclose(L.sum(axis=1), 0.5)        # rows of D - A sum to zero
+    assert L[0, 0] == 3.5 and L[4, 4] == 0.5 and L[0, 1] == -1.0
+    assert np.all(np.diff(A.rowptr) >= 1)                  # every diagonal entry stored
+    assert sp.csr_matrix(L).nnz == 5 + 2 * 4

@@ -11,6 +11,7 @@ from .matrices import (  # noqa: F401
     laplacian_3d,
     matern_2d,
     powerlaw_graph_laplacian,
+    graph_laplacian,
     diagonal_matrix,
     scaled_identity,
     random_spd_dense_csr,

@@ -75,6 +75,17 @@ def _from_scipy(A: sp.spmatrix, dtype=np.float64) -> CSR:
     )
 
 
+def graph_laplacian(n: int, edges: np.ndarray, shift: float = 0.0, dtype=np.float64) -> CSR:
+    """L = D - A + shift*I of the undirected graph on n nodes with unit-weight
+    edges (an (E, 2) array of node pairs; self-loops dropped, duplicates merged)."""
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    e = e[e[:, 0] != e[:, 1]]
+    Adj = sp.csr_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(n, n))
+    Adj = ((Adj + Adj.T) > 0).astype(np.float64)
+    deg = np.asarray(Adj.sum(axis=1)).ravel()
+    return _from_scipy(sp.diags(deg + shift) - Adj, dtype)
+
+
 def _lap1d(N: int) -> sp.csr_matrix:
     return sp.diags([-np.ones(N - 1), 2 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1], format="csr")
 
