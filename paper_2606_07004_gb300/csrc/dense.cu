@@ -407,34 +407,41 @@ template int colnorm_partials<bf16>(const bf16*, int, int, int, int, float2*, in
 // and first eigenvector components tau_k by implicit symmetric QR steps with
 // a Wilkinson shift (Golub and Van Loan, "Matrix Computations", Sec. 8.3),
 // carrying only the first row of the accumulated rotations (Golub and
-// Welsch, Math. Comp. 1969).  One thread per probe.
+// Welsch, Math. Comp. 1969).  One thread per probe; its d, e, z arrays live
+// in shared memory, interleaved across the CTA's threads (element k of
+// thread t at k * S + t), and the bulge chase carries the entries it has just
+// updated in registers.
 // ===========================================================================
-__device__ double tridiag_gauss_log(double* d, double* e, double* z, int m, double clamp_lo,
-                                    bool* nonpos) {
-  // d[0..m) diagonal, e[0..m-1) off-diagonal, z = e_1 on entry.
+__device__ double tridiag_gauss_log(double* d, double* e, double* z, int S, int m,
+                                    double clamp_lo, bool* nonpos) {
+  // d[0..m) diagonal, e[0..m-1) off-diagonal, z = e_1 on entry; stride S.
+#define TD(k) d[(k) * S]
+#define TE(k) e[(k) * S]
+#define TZ(k) z[(k) * S]
   const double eps = 2.220446049250313e-16;
   int hi = m - 1;
   int iters = 0;
   while (hi > 0) {
     // Deflate negligible off-diagonals at the bottom.
-    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-      e[hi - 1] = 0.0;
+    if (fabs(TE(hi - 1)) <= eps * (fabs(TD(hi - 1)) + fabs(TD(hi)))) {
+      TE(hi - 1) = 0.0;
       --hi;
       iters = 0;
       continue;
     }
     // Find the top of the unreduced block ending at hi.
     int lo = hi - 1;
-    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
-    if (lo > 0) e[lo - 1] = 0.0;
+    while (lo > 0 && fabs(TE(lo - 1)) > eps * (fabs(TD(lo - 1)) + fabs(TD(lo)))) --lo;
+    if (lo > 0) TE(lo - 1) = 0.0;
     if (++iters > 60) { *nonpos = true; break; }  // unconverged: flagged
     // Wilkinson shift from the trailing 2x2 block.
-    const double t = e[hi - 1];
-    const double delta = 0.5 * (d[hi - 1] - d[hi]);
+    const double t = TE(hi - 1);
+    const double delta = 0.5 * (TD(hi - 1) - TD(hi));
     const double den = delta + copysign(hypot(delta, t), delta == 0.0 ? 1.0 : delta);
-    const double mu = d[hi] - t * t / den;
-    double x = d[lo] - mu;
-    double bz = e[lo];
+    const double mu = TD(hi) - t * t / den;
+    double a = TD(lo), b = TE(lo), zc = TZ(lo);  // d[k], e[k], z[k] of the current k
+    double x = a - mu;
+    double bz = b;
     for (int k = lo; k < hi; ++k) {
       // Givens pair (c, s) with c x - s bz = r, s x + c bz = 0: one reciprocal
       // square root (the entries are O(1) for the scaled operators); hypot
@@ -451,47 +458,62 @@ __device__ double tridiag_gauss_log(double* d, double* e, double* z, int m, doub
         c = (rr == 0.0) ? 1.0 : x / rr;
         s = (rr == 0.0) ? 0.0 : -bz / rr;
       }
-      if (k > lo) e[k - 1] = rr;
-      const double a = d[k], b = e[k], cc = d[k + 1];
-      d[k] = c * c * a - 2.0 * c * s * b + s * s * cc;
-      d[k + 1] = s * s * a + 2.0 * c * s * b + c * c * cc;
-      e[k] = c * s * (a - cc) + (c * c - s * s) * b;
+      if (k > lo) TE(k - 1) = rr;
+      const double cc = TD(k + 1);
+      const double dk = c * c * a - 2.0 * c * s * b + s * s * cc;
+      const double dk1 = s * s * a + 2.0 * c * s * b + c * c * cc;
+      const double ek = c * s * (a - cc) + (c * c - s * s) * b;
+      TD(k) = dk;
+      TE(k) = ek;
+      const double z1 = TZ(k + 1);
+      TZ(k) = c * zc - s * z1;
+      zc = s * zc + c * z1;
       if (k + 1 < hi) {
-        bz = -s * e[k + 1];
-        e[k + 1] = c * e[k + 1];
-        x = e[k];
+        const double en = TE(k + 1);
+        bz = -s * en;
+        b = c * en;
+        x = ek;
       }
-      const double z0 = z[k], z1 = z[k + 1];
-      z[k] = c * z0 - s * z1;
-      z[k + 1] = s * z0 + c * z1;
+      a = dk1;
     }
+    TD(hi) = a;
+    TZ(hi) = zc;
   }
   double sum = 0.0;
   for (int k = 0; k < m; ++k) {
-    double th = d[k];
+    double th = TD(k);
     if (!(th > 0.0)) { *nonpos = true; th = clamp_lo; }
-    sum += z[k] * z[k] * log(th);
+    sum += TZ(k) * TZ(k) * log(th);
   }
   return sum;
+#undef TD
+#undef TE
+#undef TZ
 }
+
+constexpr int kQuadThreads = 32;
 
 __global__ void k_gauss_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
                              int ldab, const int* __restrict__ msteps, int m, int nprobe,
                              double clamp_lo, double* __restrict__ out,
                              uint32_t* __restrict__ status) {
+  extern __shared__ double sq[];
+  const int S = blockDim.x;
+  double* d = sq + threadIdx.x;
+  double* e = d + (size_t)m * S;
+  double* z = e + (size_t)m * S;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprobe) return;
   int mp = msteps ? msteps[p] : m;
   if (mp > m) mp = m;
   if (mp <= 0) { out[p] = 0.0; return; }
-  double d[kMaxSteps], e[kMaxSteps], z[kMaxSteps];
   for (int k = 0; k < mp; ++k) {
-    d[k] = alpha[(size_t)p * ldab + k];
-    e[k] = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
-    z[k] = (k == 0) ? 1.0 : 0.0;
+    d[k * S] = alpha[(size_t)p * ldab + k];
+    e[k * S] = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
+    z[k * S] = (k == 0) ? 1.0 : 0.0;
   }
   bool nonpos = false;
-  out[p] = tridiag_gauss_log(d, e, z, mp, clamp_lo, &nonpos);
+  out[p] = tridiag_gauss_log(d, e, z, S, mp, clamp_lo, &nonpos);
   if (nonpos && status) atomicOr(status + p, LOGDET_ST_NONPOS_RITZ);
 }
 
@@ -502,9 +524,17 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
     set_error("gauss quadrature: m=%d must be in [1, %d]", m, kMaxSteps);
     return LOGDET_EINVAL;
   }
+  // kQuadThreads probes per CTA (fewer for long recurrences): 3 m doubles
+  // of shared memory per probe.
+  int threads = kQuadThreads;
+  while (threads > 1 && (size_t)3 * m * threads * sizeof(double) > 200 * 1024) threads >>= 1;
+  const size_t smem = (size_t)3 * m * threads * sizeof(double);
+  if (smem > 48 * 1024)
+    LD_CUDA(cudaFuncSetAttribute(k_gauss_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
   ProfScope prof(KC_SMALL, st);
-  k_gauss_quad<<<div_up(nprobe, 32), 32, 0, st>>>(alpha, beta, ldab, msteps, m, nprobe,
-                                                   clamp_lo, out, status);
+  k_gauss_quad<<<div_up(nprobe, threads), threads, smem, st>>>(alpha, beta, ldab, msteps, m,
+                                                               nprobe, clamp_lo, out, status);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
@@ -517,12 +547,35 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
 // [8/8] Pade approximant in its partial-fraction form
 //   log(I + X) ~ sum_j w_j X (I + x_j X)^{-1}
 // (x_j, w_j the 8-point Gauss-Legendre rule on [0, 1]).  Only the first
-// column is formed.  One CTA per probe; matrices live in a global workspace.
+// column is formed.  One CTA per probe.  The four m x m work matrices sit in
+// shared memory when they fit (m <= 80); for m <= 113 the two that the
+// inversions and products work on (Y, W) stay in shared memory and the other
+// two (M, T) in the global workspace; beyond that all four are global.  When
+// the inverted matrix is in shared memory the CTA is one warp: the
+// inversion's m pivot steps then synchronise with __syncwarp instead of a
+// CTA barrier, which is what bounds these small dense kernels.
 // ===========================================================================
 constexpr int kLogThreads = 256;
 constexpr int kPadeNodes = 8;
 
 struct GLRule { double x[kPadeNodes], w[kPadeNodes]; };
+
+// Barrier of the CTA; a one-warp CTA needs only a warp barrier.
+__device__ __forceinline__ void cta_bar() {
+  if (blockDim.x == 32) __syncwarp();
+  else __syncthreads();
+}
+
+// Row-major element loop over an m x m matrix without a division per step:
+// thread t visits e = t, t + blockDim.x, ... as (i, j) = (e / m, e % m).
+__device__ __forceinline__ void ij_first(int m, int& i, int& j) {
+  i = (int)threadIdx.x / m;
+  j = (int)threadIdx.x - i * m;
+}
+__device__ __forceinline__ void ij_next(int m, int& i, int& j) {
+  j += blockDim.x;
+  while (j >= m) { j -= m; ++i; }
+}
 
 // Gauss-Jordan inversion in place with partial (row) pivoting; A row-major m x m.
 __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
@@ -530,7 +583,7 @@ __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
   __shared__ bool s_ok;
   if (threadIdx.x == 0) s_ok = true;
   for (int k = 0; k < m; ++k) {
-    __syncthreads();
+    cta_bar();
     if (threadIdx.x < 32) {  // pivot: largest |A_ik|, i >= k, smallest index on ties
       double best = -1.0;
       int bi = k;
@@ -549,7 +602,7 @@ __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
         if (!(best > 0.0)) s_ok = false;
       }
     }
-    __syncthreads();
+    cta_bar();
     const int p = s_piv;
     if (p != k) {
       for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -558,24 +611,24 @@ __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
         A[p * m + j] = t;
       }
     }
-    __syncthreads();
+    cta_bar();
     const double piv = A[k * m + k];
     const double ipiv = (piv != 0.0) ? 1.0 / piv : 0.0;
-    __syncthreads();
+    cta_bar();
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
       A[k * m + j] = (j == k) ? ipiv : A[k * m + j] * ipiv;
     }
     for (int i = threadIdx.x; i < m; i += blockDim.x) fcol[i] = (i == k) ? 0.0 : A[i * m + k];
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int i = e / m, j = e - i * m;
+    cta_bar();
+    int i, j;
+    for (ij_first(m, i, j); i < m; ij_next(m, i, j)) {
       if (i == k) continue;
       const double f = fcol[i];
-      if (j == k) A[e] = -f * A[k * m + k];
-      else A[e] = fma(-f, A[k * m + j], A[e]);
+      if (j == k) A[i * m + j] = -f * A[k * m + k];
+      else A[i * m + j] = fma(-f, A[k * m + j], A[i * m + j]);
     }
   }
-  __syncthreads();
+  cta_bar();
   for (int k = m - 1; k >= 0; --k) {
     const int p = perm[k];
     if (p != k) {
@@ -585,7 +638,7 @@ __device__ bool cta_invert(double* A, int m, int* perm, double* fcol) {
         A[i * m + p] = t;
       }
     }
-    __syncthreads();
+    cta_bar();
   }
   return s_ok;
 }
@@ -599,22 +652,25 @@ __device__ double cta_norm1_minus_identity(const double* A, int m, double* red) 
     mx = fmax(mx, s);
   }
   red[threadIdx.x] = mx;
-  __syncthreads();
+  cta_bar();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
-    __syncthreads();
+    cta_bar();
   }
   double r = red[0];
-  __syncthreads();
+  cta_bar();
   return r;
 }
 
+// smem_mats: how many of the four work matrices are in dynamic shared memory
+// (4: Y, M, W, T; 2: Y and W; 0: none).  The global workspace holds 4 mmax^2
+// doubles per probe whatever the split.
 __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restrict__ H, int ldh,
                                                          const int* __restrict__ msteps, int mmax,
                                                          double* __restrict__ cout, int ldc,
                                                          double* __restrict__ ws,
                                                          uint32_t* __restrict__ status,
-                                                         GLRule gl, int use_smem) {
+                                                         GLRule gl, int smem_mats) {
   extern __shared__ double dyn[];
   __shared__ double red[kLogThreads];
   __shared__ int perm[kMaxSteps];
@@ -629,45 +685,47 @@ __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restric
     for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = 0.0;
     return;
   }
-  const size_t mm = use_smem ? (size_t)m * m : (size_t)mmax * mmax;
-  double* Yb = use_smem ? dyn : ws + (size_t)p * 4 * mm;  // current matrix (square-rooted in place)
-  double* Mb = Yb + mm;
-  double* Wb = Mb + mm;
-  double* Tb = Wb + mm;
-  const double* Hp = H + (size_t)p * ldh * mmax;
-  // Row-major copy of the leading m x m block of the column-major H.
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    int i = e / m, j = e - i * m;
-    Yb[e] = Hp[(size_t)j * ldh + i];
+  const size_t mm = (size_t)m * m;
+  double* wsp = ws + (size_t)p * 4 * ((size_t)mmax * mmax);
+  double *Yb, *Mb, *Wb, *Tb;  // current matrix (square-rooted in place), DB M, inverse, product
+  if (smem_mats == 4) {
+    Yb = dyn; Mb = dyn + mm; Wb = dyn + 2 * mm; Tb = dyn + 3 * mm;
+  } else if (smem_mats == 2) {
+    Yb = dyn; Wb = dyn + mm; Mb = wsp; Tb = wsp + mm;
+  } else {
+    Yb = wsp; Mb = wsp + mm; Wb = wsp + 2 * mm; Tb = wsp + 3 * mm;
   }
-  __syncthreads();
+  const double* Hp = H + (size_t)p * ldh * mmax;
+  int i, j;
+  // Row-major copy of the leading m x m block of the column-major H.
+  for (ij_first(m, i, j); i < m; ij_next(m, i, j)) Yb[i * m + j] = Hp[(size_t)j * ldh + i];
+  cta_bar();
   bool ok = true;
   int nroots = 0;
   while (cta_norm1_minus_identity(Yb, m, red) > 0.25 && nroots < 64) {
     // Product-form Denman-Beavers: M0 = Y0 = A;
     //   Y <- Y (I + M^{-1}) / 2,  M <- (I + (M + M^{-1}) / 2) / 2,  Y -> A^{1/2}.
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Mb[e] = Yb[e];
-    __syncthreads();
+    cta_bar();
     bool conv = false;
     double prev = 1e300;
     for (int it = 0; it < 100; ++it) {
       for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wb[e] = Mb[e];
-      __syncthreads();
+      cta_bar();
       if (!cta_invert(Wb, m, perm, fcol)) { ok = false; break; }
-      __syncthreads();
-      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e - i * m;
+      cta_bar();
+      for (ij_first(m, i, j); i < m; ij_next(m, i, j)) {
         double v = 0.0;
         for (int k = 0; k < m; ++k) v = fma(Yb[i * m + k], Wb[k * m + j], v);
-        Tb[e] = 0.5 * (Yb[e] + v);
+        Tb[i * m + j] = 0.5 * (Yb[i * m + j] + v);
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        int i = e / m, j = e - i * m;
+      cta_bar();
+      for (ij_first(m, i, j); i < m; ij_next(m, i, j)) {
+        const int e = i * m + j;
         Yb[e] = Tb[e];
         Mb[e] = 0.25 * (Mb[e] + Wb[e]) + (i == j ? 0.5 : 0.0);
       }
-      __syncthreads();
+      cta_bar();
       double dev = cta_norm1_minus_identity(Mb, m, red);
       // Converged at rounding level, or stagnating there.
       if (dev <= 1e-15 * m || (dev < 1e-9 && dev > 0.5 * prev)) { conv = true; break; }
@@ -677,29 +735,29 @@ __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restric
     ++nroots;
   }
   // X = A - I ; rhs = X e_1 ; c = 2^s sum_j w_j (I + x_j X)^{-1} rhs
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    rhs[i] = Yb[i * m + 0] - (i == 0 ? 1.0 : 0.0);
-    acc[i] = 0.0;
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    rhs[r] = Yb[r * m + 0] - (r == 0 ? 1.0 : 0.0);
+    acc[r] = 0.0;
   }
-  __syncthreads();
+  cta_bar();
   for (int q = 0; q < kPadeNodes && ok; ++q) {
     const double xq = gl.x[q];
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      int i = e / m, j = e - i * m;
+    for (ij_first(m, i, j); i < m; ij_next(m, i, j)) {
+      const int e = i * m + j;
       Wb[e] = (i == j ? 1.0 : 0.0) + xq * (Yb[e] - (i == j ? 1.0 : 0.0));
     }
-    __syncthreads();
+    cta_bar();
     if (!cta_invert(Wb, m, perm, fcol)) { ok = false; break; }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    cta_bar();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
       double v = 0.0;
-      for (int k = 0; k < m; ++k) v = fma(Wb[i * m + k], rhs[k], v);
-      acc[i] = fma(gl.w[q], v, acc[i]);
+      for (int k = 0; k < m; ++k) v = fma(Wb[r * m + k], rhs[k], v);
+      acc[r] = fma(gl.w[q], v, acc[r]);
     }
-    __syncthreads();
+    cta_bar();
   }
   const double scale = ldexp(1.0, nroots);
-  for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = (i < m && ok) ? scale * acc[i] : 0.0;
+  for (int r = threadIdx.x; r < ldc; r += blockDim.x) c[r] = (r < m && ok) ? scale * acc[r] : 0.0;
   if (!ok && threadIdx.x == 0 && status) atomicOr(status + p, LOGDET_ST_LOG_FAILED);
 }
 
@@ -746,14 +804,15 @@ int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int np
     return LOGDET_EINVAL;
   }
   static const GLRule gl = gauss_legendre01();
-  // Four m x m work matrices per CTA: in shared memory when they fit.
-  const size_t smem = 4 * sizeof(double) * (size_t)m * m;
-  const int use_smem = smem <= 200 * 1024;
-  if (use_smem && smem > 48 * 1024)
+  // Work matrices in shared memory as far as they fit (see k_hesslog).
+  const size_t mat = sizeof(double) * (size_t)m * m;
+  const int smem_mats = 4 * mat <= 200 * 1024 ? 4 : 2 * mat <= 200 * 1024 ? 2 : 0;
+  const size_t smem = smem_mats * mat;
+  const int threads = smem_mats ? 32 : kLogThreads;
+  if (smem > 48 * 1024)
     LD_CUDA(cudaFuncSetAttribute(k_hesslog, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope prof(KC_SMALL, st);
-  k_hesslog<<<nprobe, kLogThreads, use_smem ? smem : 0, st>>>(H, ldh, msteps, m, c, ldc, ws, status,
-                                                              gl, use_smem);
+  k_hesslog<<<nprobe, threads, smem, st>>>(H, ldh, msteps, m, c, ldc, ws, status, gl, smem_mats);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }

@@ -22,7 +22,7 @@ static int gcd_int(int a, int b) { while (b) { int t = a % b; a = b; b = t; } re
 
 // Threads per CTA: a multiple of both 32 (full warps) and of the chunks per
 // row G = ld / vec, so every lane of every warp owns a (row, chunk) slot.
-TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint) {
+TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) {
   TileGeom g;
   int G = width / vec;
   int lcm = G / gcd_int(G, 32) * 32;          // smallest CTA with whole rows and warps
@@ -36,6 +36,11 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint) {
   g.rows_per_iter = threads / G;
   int iters = std::max(1, 256 / std::max(1, g.rows_per_iter));  // ~256+ rows per tile
   if (iters < 4) iters = 4;
+  if (n > 0) {
+    const long long want = 2LL * sm_count();  // tiles
+    const int fit = (int)std::max<long long>(1, n / (want * g.rows_per_iter));
+    if (fit < iters) iters = fit;
+  }
   if (iters_hint > 0 && iters_hint <= 256) iters = iters_hint;
   g.tile_rows = g.rows_per_iter * iters;
   return g;

@@ -136,8 +136,11 @@ struct TileGeom {
 };
 // Geometry for a slice of `width` columns.  threads_hint (a multiple of both
 // 32 and width/vec, <= 512) and iters_hint (rows per tile = rows per CTA
-// iteration x iters) override the defaults when valid.
-TileGeom tile_geom(int width, int vec, int threads_hint = 0, int iters_hint = 0);
+// iteration x iters) override the defaults when valid.  Without iters_hint,
+// a block of n rows (n > 0) too short to give two tiles per SM gets shallower
+// tiles (down to one row per thread group), so that small problems still
+// spread over the whole GPU.
+TileGeom tile_geom(int width, int vec, int threads_hint = 0, int iters_hint = 0, int n = 0);
 
 // Tunable layout of a Krylov run: the block's columns are processed as
 // `split` slices of ld/split columns, with the CTA size and tile depth above.

@@ -400,7 +400,7 @@ template int scaled_values<float>(logdet_ctx*, double, float*, cudaStream_t);
 template <typename T>
 int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::type* vals, int n,
                const T* x, T* y, int ld, cudaStream_t st, const double* colshift, logdet_ctx* h) {
-  TileGeom g = tile_geom(ld, Vec16<T>::N);
+  TileGeom g = tile_geom(ld, Vec16<T>::N, 0, 0, n);
   SpmmBatch<T> B;
   memset(&B, 0, sizeof B);
   B.njobs = 1;

@@ -133,7 +133,7 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
   tune = tc;
   if (tune.split < 1 || ld % tune.split || (ld / tune.split) % Vec16<T>::N) tune.split = 1;
   width = ld / tune.split;
-  g = tile_geom(width, Vec16<T>::N, tune.threads, tune.iters);
+  g = tile_geom(width, Vec16<T>::N, tune.threads, tune.iters, n);
   ntiles = div_up(n, g.tile_rows);
   nslots = ntiles;
   items = nullptr;
@@ -758,7 +758,7 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
   const size_t vals = (size_t)h->nnz * (f32 ? 4 : 8);
-  const TileGeom g = tile_geom((int)ld, vec);
+  const TileGeom g = tile_geom((int)ld, vec, 0, 0, (int)n);
   const size_t ntiles = div_up((int)n, g.tile_rows);
   const size_t part = (size_t)std::max(k, 2) * ld * ntiles * (f32 ? 8 : 8);
   const size_t kstate = ld * (m + 2) * 8 * 4 + ld * (size_t)(m + 1) * m * 8 + 64 * ld;

@@ -128,12 +128,14 @@ def test_gauss_quadrature_matches_eigh_tridiagonal():
         assert abs(got[p] - want) <= 1e-12 * max(1.0, abs(want)), p
 
 
-@pytest.mark.parametrize("k", [2, 4, 8, 30])
-def test_hessenberg_log_matches_logm(k):
+# m = 30: work matrices in shared memory (one-warp CTAs); m = 100: two of
+# them in shared memory; m = 120: all in the global workspace.
+@pytest.mark.parametrize("k,m", [(2, 30), (4, 30), (8, 30), (30, 30), (4, 100), (8, 120)])
+def test_hessenberg_log_matches_logm(k, m):
     Q = W.laplacian_3d(10, shift=0.01).to_scipy()
     lo, hi = O.spectral_interval(Q)
     gamma = math.sqrt(lo * hi)
-    nprobe, m = 12, 30
+    nprobe = 12
     ldh = m + 1
     Hs = np.zeros((nprobe, m, ldh))  # per probe column-major (m columns of length ldh)
     ms = np.zeros(nprobe, dtype=np.int32)
