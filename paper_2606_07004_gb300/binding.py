@@ -39,7 +39,7 @@ EXPORTED = [
     "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
-    "logdet_hessenberg_log_e1_noalloc",
+    "logdet_hessenberg_log_e1_noalloc", "logdet_hessenberg_log_e1_banded",
     "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
@@ -105,6 +105,8 @@ _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
+_sig("logdet_hessenberg_log_e1_banded", C.c_int,
+     [_P, _i32, _P, _i32, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1_noalloc", C.c_int,
      [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_estimate_bytes", C.c_int, [_P, _i32, _i32, _i32, _i32, C.POINTER(logdet_opts),
@@ -465,6 +467,14 @@ def logdet_hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, stream=None) -> int:
     _check(_lib.logdet_hessenberg_log_e1(_ptr(H), ldh, _ptr(msteps), m, nprobe, _ptr(c),
                                          C.byref(st), _stream(stream)),
            "logdet_hessenberg_log_e1")
+    return st.value
+
+
+def logdet_hessenberg_log_e1_banded(H, ldh, msteps, m, nprobe, band, c, stream=None) -> int:
+    st = _u32()
+    _check(_lib.logdet_hessenberg_log_e1_banded(_ptr(H), ldh, _ptr(msteps), m, nprobe, band,
+                                                _ptr(c), C.byref(st), _stream(stream)),
+           "logdet_hessenberg_log_e1_banded")
     return st.value
 
 

@@ -491,30 +491,93 @@ __device__ double tridiag_gauss_log(double* d, double* e, double* z, int S, int 
 #undef TZ
 }
 
-constexpr int kQuadThreads = 32;
+// ---------------------------------------------------------------------------
+// The Gauss rule's value sum_k tau_k^2 log(theta_k) is e_1^T log(T) e_1.  For
+// SPD T it follows from log(theta) = int_0^inf [1/(1+s) - 1/(theta+s)] ds as
+//   e_1^T log(T) e_1 = int_R s [1/(1+s) - r(s)] du,   s = e^u,
+//   r(s) = e_1^T (T + s I)^{-1} e_1 = 1 / d_1,
+// with d_1 from the continued fraction d_m = t_m + s,
+// d_i = t_i + s - b_i^2 / d_{i+1} (the pivots of T + s I = U D U^T, all
+// positive for SPD T).  The integrand is analytic in the strip |Im u| < pi
+// and decays like s / lambda_min(T) as u -> -inf and like lambda_max(T) / s
+// as u -> +inf, so the trapezoid rule with step h = 1/2 on u in [-60, 39.5]
+// (200 nodes) has discretisation error ~exp(-2 pi^2 / h) < 1e-17 and
+// truncation error < 1e-17 for spectra in [1e-9, 1] (the scaled operators
+// J = Q / alpha have lambda_max <= 1).  One CTA per probe, one node per
+// thread, node values added in a fixed-order tree.  A T that is not SPD
+// (a non-positive pivot at s = 0, possible only from FP32 rounding) takes
+// the implicit-QR rule above, which clamps and flags non-positive Ritz values.
+// ---------------------------------------------------------------------------
+constexpr int kQuadThreads = 256;
+constexpr int kQuadNodes = 200;
+constexpr double kQuadULo = -60.0;
+constexpr double kQuadH = 0.5;
 
-__global__ void k_gauss_quad(const double* __restrict__ alpha, const double* __restrict__ beta,
-                             int ldab, const int* __restrict__ msteps, int m, int nprobe,
-                             double clamp_lo, double* __restrict__ out,
-                             uint32_t* __restrict__ status) {
-  extern __shared__ double sq[];
-  const int S = blockDim.x;
-  double* d = sq + threadIdx.x;
-  double* e = d + (size_t)m * S;
-  double* z = e + (size_t)m * S;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kQuadThreads) k_gauss_quad(
+    const double* __restrict__ alpha, const double* __restrict__ beta, int ldab,
+    const int* __restrict__ msteps, int m, int nprobe, double clamp_lo, double* __restrict__ out,
+    uint32_t* __restrict__ status) {
+  extern __shared__ double sq[];  // a[m], b2[m], fallback d, e, z [3m]
+  __shared__ double fv[kQuadThreads];
+  __shared__ int s_spd;
+  const int p = blockIdx.x;
   if (p >= nprobe) return;
   int mp = msteps ? msteps[p] : m;
   if (mp > m) mp = m;
-  if (mp <= 0) { out[p] = 0.0; return; }
-  for (int k = 0; k < mp; ++k) {
-    d[k * S] = alpha[(size_t)p * ldab + k];
-    e[k * S] = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
-    z[k * S] = (k == 0) ? 1.0 : 0.0;
+  if (mp <= 0) {
+    if (threadIdx.x == 0) out[p] = 0.0;
+    return;
   }
-  bool nonpos = false;
-  out[p] = tridiag_gauss_log(d, e, z, S, mp, clamp_lo, &nonpos);
-  if (nonpos && status) atomicOr(status + p, LOGDET_ST_NONPOS_RITZ);
+  double* a = sq;
+  double* b2 = sq + m;
+  for (int k = threadIdx.x; k < mp; k += blockDim.x) {
+    a[k] = alpha[(size_t)p * ldab + k];
+    const double b = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
+    b2[k] = b * b;
+  }
+  if (threadIdx.x == 0) s_spd = 1;
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t == kQuadNodes) {
+    // Pivots at s = 0: all positive iff T is SPD (Sylvester's law of inertia).
+    double d = a[mp - 1];
+    bool ok = d > 0.0;
+    for (int i = mp - 2; i >= 0 && ok; --i) {
+      d = a[i] - b2[i] / d;
+      ok = d > 0.0;
+    }
+    if (!ok) s_spd = 0;
+  }
+  double f = 0.0;
+  if (t < kQuadNodes) {
+    const double sn = exp(kQuadULo + kQuadH * t);
+    double d = a[mp - 1] + sn;
+    for (int i = mp - 2; i >= 0; --i) d = (a[i] + sn) - b2[i] / d;
+    f = sn * (1.0 / (1.0 + sn) - 1.0 / d);
+  }
+  fv[t] = f;
+  __syncthreads();
+  for (int w = kQuadThreads / 2; w > 0; w >>= 1) {
+    if (t < w) fv[t] += fv[t + w];
+    __syncthreads();
+  }
+  if (s_spd) {
+    if (t == 0) out[p] = kQuadH * fv[0];
+    return;
+  }
+  if (t == 0) {
+    double* d = sq + 2 * m;
+    double* e = d + m;
+    double* z = e + m;
+    for (int k = 0; k < mp; ++k) {
+      d[k] = alpha[(size_t)p * ldab + k];
+      e[k] = (k + 1 < mp) ? beta[(size_t)p * ldab + k] : 0.0;
+      z[k] = (k == 0) ? 1.0 : 0.0;
+    }
+    bool nonpos = false;
+    out[p] = tridiag_gauss_log(d, e, z, 1, mp, clamp_lo, &nonpos);
+    if (nonpos && status) atomicOr(status + p, LOGDET_ST_NONPOS_RITZ);
+  }
 }
 
 int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, const int* msteps,
@@ -524,17 +587,10 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
     set_error("gauss quadrature: m=%d must be in [1, %d]", m, kMaxSteps);
     return LOGDET_EINVAL;
   }
-  // kQuadThreads probes per CTA (fewer for long recurrences): 3 m doubles
-  // of shared memory per probe.
-  int threads = kQuadThreads;
-  while (threads > 1 && (size_t)3 * m * threads * sizeof(double) > 200 * 1024) threads >>= 1;
-  const size_t smem = (size_t)3 * m * threads * sizeof(double);
-  if (smem > 48 * 1024)
-    LD_CUDA(cudaFuncSetAttribute(k_gauss_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  const size_t smem = (size_t)5 * m * sizeof(double);
   ProfScope prof(KC_SMALL, st);
-  k_gauss_quad<<<div_up(nprobe, threads), threads, smem, st>>>(alpha, beta, ldab, msteps, m,
-                                                               nprobe, clamp_lo, out, status);
+  k_gauss_quad<<<nprobe, kQuadThreads, smem, st>>>(alpha, beta, ldab, msteps, m, nprobe, clamp_lo,
+                                                   out, status);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
@@ -550,10 +606,10 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
 // column is formed.  One CTA per probe.  The four m x m work matrices sit in
 // shared memory when they fit (m <= 80); for m <= 113 the two that the
 // inversions and products work on (Y, W) stay in shared memory and the other
-// two (M, T) in the global workspace; beyond that all four are global.  When
-// the inverted matrix is in shared memory the CTA is one warp: the
-// inversion's m pivot steps then synchronise with __syncwarp instead of a
-// CTA barrier, which is what bounds these small dense kernels.
+// two (M, T) in the global workspace; beyond that all four are global.
+// (One-warp CTAs were measured 4x slower: FP64 issues at 2 lanes per clock
+// per SM on this part, so a probe's work needs the whole CTA's warps in
+// flight, not cheaper barriers.)
 // ===========================================================================
 constexpr int kLogThreads = 256;
 constexpr int kPadeNodes = 8;
@@ -761,6 +817,131 @@ __global__ void __launch_bounds__(kLogThreads) k_hesslog(const double* __restric
   if (!ok && threadIdx.x == 0 && status) atomicOr(status + p, LOGDET_ST_LOG_FAILED);
 }
 
+// ===========================================================================
+// Banded Hessenberg matrices (the IOP window k gives upper bandwidth k - 1):
+// log(H) e_1 by the resolvent quadrature used for the Gauss rules,
+//   log(H) e_1 = int_R s [ e_1 / (1 + s) - (H + s I)^{-1} e_1 ] du,  s = e^u,
+// (log(lambda) = int_0^inf [1/(1+s) - 1/(lambda+s)] ds on each eigenvalue),
+// trapezoid rule with step 1/2 on u in [-60, 60]: 241 nodes, discretisation
+// error ~exp(-2 pi^2 / h) and truncation error < 1e-16 for spectra in
+// [1e-9, 1e9] off the negative real axis.  Each node is one banded solve of
+// (H + s I) x = e_1 by Gaussian elimination with partial pivoting between
+// adjacent rows (the only rows with an entry in the pivot column), O(m k)
+// work; one node per thread, the node vectors added in node order.  This is
+// O(241 m k) per probe against the ~40 dense O(m^3) inversions of inverse
+// scaling and squaring, and its nodes spread over the whole CTA.
+// ===========================================================================
+constexpr int kResMaxBand = 8;
+constexpr int kResNodes = 241;
+constexpr int kResThreads = 256;
+constexpr double kResULo = -60.0;
+constexpr double kResH = 0.5;
+
+size_t hesslog_band_workspace_doubles(int m, int nprobe) {
+  return (size_t)nprobe * kResNodes * m * (kResMaxBand + 3) + 16;
+}
+
+// W = band + 2: the length of a row of U (band, diagonal and one fill entry).
+template <int W>
+__global__ void __launch_bounds__(kResThreads) k_hesslog_band(
+    const double* __restrict__ H, int ldh, const int* __restrict__ msteps, int mmax,
+    double* __restrict__ cout, int ldc, double* __restrict__ ws, uint32_t* __restrict__ status) {
+  constexpr int band = W - 2;
+  extern __shared__ double hb[];  // hb[j * W + l] = H(j - band + l, j), l = 0..band+1
+  __shared__ int s_fail;
+  const int p = blockIdx.x;
+  int m = msteps ? msteps[p] : mmax;
+  if (m > mmax) m = mmax;
+  double* c = cout + (size_t)p * ldc;
+  if (m <= 0) {
+    for (int i = threadIdx.x; i < ldc; i += blockDim.x) c[i] = 0.0;
+    return;
+  }
+  const double* Hp = H + (size_t)p * ldh * mmax;
+  for (int e = threadIdx.x; e < m * W; e += blockDim.x) {
+    const int j = e / W, l = e - j * W, i = j - band + l;
+    hb[e] = (i >= 0 && i < m) ? Hp[(size_t)j * ldh + i] : 0.0;
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  const size_t NN = kResNodes;
+  double* U = ws + (size_t)p * NN * mmax * (kResMaxBand + 3);  // [m][W][node]
+  double* R = U + (size_t)mmax * W * NN;                       // [m][node]
+  const int t = threadIdx.x;
+  if (t < kResNodes) {
+    const double s = exp(kResULo + kResH * t);
+    // Entry (i, j) of H + s I inside the band (0 outside).
+    auto A = [&](int i, int j) -> double {
+      const int l = i - j + band;
+      if (j >= m || l < 0 || l > band + 1) return 0.0;
+      return hb[j * W + l] + (i == j ? s : 0.0);
+    };
+    double act[W], nxt[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) act[q] = A(0, q);
+    double ract = 1.0;
+    bool bad = false;
+    for (int j = 0; j < m; ++j) {
+      double rn = 0.0;
+      if (j + 1 < m) {
+#pragma unroll
+        for (int q = 0; q < W; ++q) nxt[q] = A(j + 1, j + q);
+        if (fabs(nxt[0]) > fabs(act[0])) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const double tmp = act[q];
+            act[q] = nxt[q];
+            nxt[q] = tmp;
+          }
+          rn = ract;
+          ract = 0.0;
+        }
+      }
+      if (!(fabs(act[0]) > 0.0) || !isfinite(act[0])) bad = true;
+#pragma unroll
+      for (int q = 0; q < W; ++q) U[((size_t)j * W + q) * NN + t] = act[q];
+      R[(size_t)j * NN + t] = ract;
+      if (j + 1 < m) {
+        const double lm = nxt[0] / act[0];
+#pragma unroll
+        for (int q = 0; q + 1 < W; ++q) nxt[q] = fma(-lm, act[q + 1], nxt[q + 1]);
+        nxt[W - 1] = 0.0;
+        rn = fma(-lm, ract, rn);
+#pragma unroll
+        for (int q = 0; q < W; ++q) act[q] = nxt[q];
+        ract = rn;
+      }
+    }
+    // Back substitution; R[j] becomes x_j.
+    for (int j = m - 1; j >= 0 && !bad; --j) {
+      double v = R[(size_t)j * NN + t];
+#pragma unroll
+      for (int q = 1; q < W; ++q)
+        if (j + q < m) v = fma(-U[((size_t)j * W + q) * NN + t], R[(size_t)(j + q) * NN + t], v);
+      const double x = v / U[(size_t)j * W * NN + t];
+      if (!isfinite(x)) bad = true;
+      R[(size_t)j * NN + t] = x;
+    }
+    // Node value s (e_1 / (1 + s) - x).
+    for (int j = 0; j < m; ++j) {
+      const double x = R[(size_t)j * NN + t];
+      R[(size_t)j * NN + t] = s * ((j == 0 ? 1.0 / (1.0 + s) : 0.0) - x);
+    }
+    if (bad) atomicOr(&s_fail, 1);
+  }
+  __syncthreads();
+  const bool ok = s_fail == 0;
+  for (int j = threadIdx.x; j < ldc; j += blockDim.x) {
+    double v = 0.0;
+    if (j < m && ok) {
+      for (int q = 0; q < kResNodes; ++q) v += R[(size_t)j * NN + q];
+      v *= kResH;
+    }
+    c[j] = v;
+  }
+  if (!ok && threadIdx.x == 0 && status) atomicOr(status + p, LOGDET_ST_LOG_FAILED);
+}
+
 // Gauss-Legendre nodes and weights on [0, 1] by Newton's method on P_N.
 static GLRule gauss_legendre01() {
   GLRule g;
@@ -795,20 +976,40 @@ static GLRule gauss_legendre01() {
   return g;
 }
 
-size_t hesslog_workspace_doubles(int m, int nprobe) { return (size_t)nprobe * 4 * m * m + 16; }
+size_t hesslog_workspace_doubles(int m, int nprobe, int band) {
+  const size_t dense = (size_t)nprobe * 4 * m * m + 16;
+  if (band < 0 || band > kResMaxBand) return dense;
+  return std::max(dense, hesslog_band_workspace_doubles(m, nprobe));
+}
 
 int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int nprobe, double* c,
-                      int ldc, double* ws, uint32_t* status, cudaStream_t st) {
+                      int ldc, double* ws, uint32_t* status, cudaStream_t st, int band) {
   if (m < 1 || m > kMaxSteps) {
     set_error("hessenberg log: m=%d must be in [1, %d]", m, kMaxSteps);
     return LOGDET_EINVAL;
+  }
+  if (band >= 0 && band <= kResMaxBand && band + 1 < m) {
+    const size_t smem = sizeof(double) * (size_t)m * (band + 2);
+    ProfScope prof(KC_SMALL, st);
+#define LD_RES_CASE(B)                                                                   \
+  case B:                                                                                \
+    k_hesslog_band<B + 2><<<nprobe, kResThreads, smem, st>>>(H, ldh, msteps, m, c, ldc, ws, \
+                                                             status);                    \
+    break;
+    switch (band) {
+      LD_RES_CASE(0) LD_RES_CASE(1) LD_RES_CASE(2) LD_RES_CASE(3) LD_RES_CASE(4)
+      LD_RES_CASE(5) LD_RES_CASE(6) LD_RES_CASE(7) LD_RES_CASE(8)
+    }
+#undef LD_RES_CASE
+    LD_CHECK_LAUNCH();
+    return LOGDET_OK;
   }
   static const GLRule gl = gauss_legendre01();
   // Work matrices in shared memory as far as they fit (see k_hesslog).
   const size_t mat = sizeof(double) * (size_t)m * m;
   const int smem_mats = 4 * mat <= 200 * 1024 ? 4 : 2 * mat <= 200 * 1024 ? 2 : 0;
   const size_t smem = smem_mats * mat;
-  const int threads = smem_mats ? 32 : kLogThreads;
+  const int threads = kLogThreads;
   if (smem > 48 * 1024)
     LD_CUDA(cudaFuncSetAttribute(k_hesslog, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope prof(KC_SMALL, st);

@@ -41,10 +41,14 @@ int gauss_quadrature_log(const double* alpha, const double* beta, int ldab, cons
                          cudaStream_t st);
 
 // c_p = log(H_p) e_1 for nprobe upper Hessenberg matrices (column-major,
-// leading dim ldh, H_p at H + p*ldh*m).  ws: hesslog_workspace_doubles.
-size_t hesslog_workspace_doubles(int m, int nprobe);
+// leading dim ldh, H_p at H + p*ldh*m).  band >= 0: the matrices are zero
+// above upper bandwidth `band` (IOP window k: band = k - 1), which selects
+// the resolvent quadrature for band <= 8 and band + 1 < m; otherwise
+// inverse scaling and squaring.  ws: hesslog_workspace_doubles(m, nprobe, band).
+size_t hesslog_workspace_doubles(int m, int nprobe, int band = -1);
 int hessenberg_log_e1(const double* H, int ldh, const int* msteps, int m, int nprobe,
-                      double* c, int ldc, double* ws, uint32_t* status, cudaStream_t st);
+                      double* c, int ldc, double* ws, uint32_t* status, cudaStream_t st,
+                      int band = -1);
 
 // Probe fill, columns col0..col0+ncols of stream key (keyp: as for
 // project_residual_fp64).

@@ -203,8 +203,9 @@ int logdet_gauss_quadrature_log(const double* alpha, const double* beta, const i
   return LOGDET_OK;
 }
 
-int logdet_hessenberg_log_e1(const double* H, int32_t ldh, const int32_t* msteps, int32_t m,
-                             int32_t nprobe, double* c, uint32_t* status, void* cuda_stream) {
+static int hesslog_entry(const double* H, int32_t ldh, const int32_t* msteps, int32_t m,
+                         int32_t nprobe, int32_t band, double* c, uint32_t* status,
+                         void* cuda_stream) {
   if (!H || !c || m < 1 || nprobe < 1 || ldh < m) {
     set_error("hessenberg_log_e1: bad arguments");
     return LOGDET_EINVAL;
@@ -212,10 +213,10 @@ int logdet_hessenberg_log_e1(const double* H, int32_t ldh, const int32_t* msteps
   cudaStream_t st = (cudaStream_t)cuda_stream;
   DevBuf<double> ws(st);
   DevBuf<uint32_t> sd(st);
-  LD_TRY(ws.alloc(hesslog_workspace_doubles(m, nprobe)));
+  LD_TRY(ws.alloc(hesslog_workspace_doubles(m, nprobe, band)));
   LD_TRY(sd.alloc(nprobe));
   LD_TRY(sd.zero());
-  LD_TRY(hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, m, ws.p, sd.p, st));
+  LD_TRY(hessenberg_log_e1(H, ldh, msteps, m, nprobe, c, m, ws.p, sd.p, st, band));
   std::vector<uint32_t> hs(nprobe);
   LD_CUDA(cudaMemcpyAsync(hs.data(), sd.p, sizeof(uint32_t) * nprobe, cudaMemcpyDeviceToHost, st));
   LD_CUDA(cudaStreamSynchronize(st));
@@ -225,6 +226,21 @@ int logdet_hessenberg_log_e1(const double* H, int32_t ldh, const int32_t* msteps
     *status = acc;
   }
   return LOGDET_OK;
+}
+
+int logdet_hessenberg_log_e1(const double* H, int32_t ldh, const int32_t* msteps, int32_t m,
+                             int32_t nprobe, double* c, uint32_t* status, void* cuda_stream) {
+  return hesslog_entry(H, ldh, msteps, m, nprobe, -1, c, status, cuda_stream);
+}
+
+int logdet_hessenberg_log_e1_banded(const double* H, int32_t ldh, const int32_t* msteps,
+                                    int32_t m, int32_t nprobe, int32_t band, double* c,
+                                    uint32_t* status, void* cuda_stream) {
+  if (band < 0) {
+    set_error("hessenberg_log_e1_banded: band < 0");
+    return LOGDET_EINVAL;
+  }
+  return hesslog_entry(H, ldh, msteps, m, nprobe, band, c, status, cuda_stream);
 }
 
 }  // extern "C"

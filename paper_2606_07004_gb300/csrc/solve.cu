@@ -595,9 +595,10 @@ struct Solve : ISolve {
     KRun<T>& r1 = *run;
     DevBuf<double> cc(st), ws(st), w(st), Y64(st);
     LD_TRY(cc.alloc((size_t)lds * m));
-    LD_TRY(ws.alloc(hesslog_workspace_doubles(m, lds)));
+    LD_TRY(ws.alloc(hesslog_workspace_doubles(m, lds, kk - 1)));
     LD_TRY(w.alloc((size_t)m * lds));
-    LD_TRY(hessenberg_log_e1(r1.ks.H.p, m + 1, r1.ks.meff.p, m, lds, cc.p, m, ws.p, r1.ks.status.p, st));
+    LD_TRY(hessenberg_log_e1(r1.ks.H.p, m + 1, r1.ks.meff.p, m, lds, cc.p, m, ws.p, r1.ks.status.p, st,
+                             kk - 1));
     {
       ProfScope prof(KC_SMALL, st);
       k_iop_weights<<<div_up(m * lds, 256), 256, 0, st>>>(cc.p, m, r1.ks.sig.p, r1.ks.edot.p,
@@ -637,8 +638,9 @@ struct Solve : ISolve {
     } else {
       DevBuf<double> cc(st), ws(st);
       LD_TRY(cc.alloc((size_t)ld * m));
-      LD_TRY(ws.alloc(hesslog_workspace_doubles(m, ld)));
-      LD_TRY(hessenberg_log_e1(rr.ks.H.p, m + 1, rr.ks.meff.p, m, ld, cc.p, m, ws.p, rr.ks.status.p, st));
+      LD_TRY(ws.alloc(hesslog_workspace_doubles(m, ld, kk - 1)));
+      LD_TRY(hessenberg_log_e1(rr.ks.H.p, m + 1, rr.ks.meff.p, m, ld, cc.p, m, ws.p, rr.ks.status.p,
+                               st, kk - 1));
       ProfScope prof(KC_SMALL, st);
       k_iop_qf<<<div_up(ld, 64), 64, 0, st>>>(cc.p, m, rr.ks.sig.p, rr.ks.edot.p, rr.ks.meff.p, m,
                                                ld, shift, outv.p);
@@ -771,9 +773,9 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
     peak = vals + std::max(setup, krylov + (f32 ? 0 : 0));
   } else {
     const size_t phase1 = n * lds * m * es + part + n * lds * es + kstate +
-                          hesslog_workspace_doubles(m, (int)lds) * 8 + n * lds * 8;
+                          hesslog_workspace_doubles(m, (int)lds, k - 1) * 8 + n * lds * 8;
     const size_t phase2 = (f32 ? n * ld * es : n * ld * 8) + part + n * ld * es * (k + 2) + kstate +
-                          hesslog_workspace_doubles(m, (int)ld) * 8;
+                          hesslog_workspace_doubles(m, (int)ld, k - 1) * 8;
     peak = vals + std::max(phase1, std::max(split + n * lds * 8, phase2));
   }
   return peak + (16u << 20);

@@ -128,9 +128,11 @@ def test_gauss_quadrature_matches_eigh_tridiagonal():
         assert abs(got[p] - want) <= 1e-12 * max(1.0, abs(want)), p
 
 
-# m = 30: work matrices in shared memory (one-warp CTAs); m = 100: two of
-# them in shared memory; m = 120: all in the global workspace.
-@pytest.mark.parametrize("k,m", [(2, 30), (4, 30), (8, 30), (30, 30), (4, 100), (8, 120)])
+# Windows k <= 9 with k < m: banded resolvent quadrature.  Otherwise inverse
+# scaling and squaring with the work matrices in shared memory (m = 30), two
+# of them there (m = 100) or all in the global workspace (m = 120).
+@pytest.mark.parametrize("k,m", [(2, 30), (4, 30), (8, 30), (30, 30), (4, 100), (8, 120),
+                                 (100, 100), (120, 120)])
 def test_hessenberg_log_matches_logm(k, m):
     Q = W.laplacian_3d(10, shift=0.01).to_scipy()
     lo, hi = O.spectral_interval(Q)
@@ -147,14 +149,19 @@ def test_hessenberg_log_matches_logm(k, m):
         ms[p] = me
         Hs[p, :me, :me] = run.H.T
         want.append(np.real(sla.logm(run.H))[:, 0])
-    c = torch.zeros(nprobe * m, dtype=torch.float64, device="cuda")
-    st = B.logdet_hessenberg_log_e1(cuda(Hs.ravel()), ldh, cuda(ms, torch.int32), m, nprobe, c)
-    got = c.view(nprobe, m).cpu().numpy()
-    assert st == 0
-    for p in range(nprobe):
-        w = want[p]
-        assert np.max(np.abs(got[p, :ms[p]] - w)) <= 1e-11 * max(1.0, np.max(np.abs(w))), p
-        assert np.all(got[p, ms[p]:] == 0.0)
+    Hd, md = cuda(Hs.ravel()), cuda(ms, torch.int32)
+    runs = [lambda c: B.logdet_hessenberg_log_e1(Hd, ldh, md, m, nprobe, c)]
+    if k - 1 <= 8:
+        runs.append(lambda c: B.logdet_hessenberg_log_e1_banded(Hd, ldh, md, m, nprobe, k - 1, c))
+    for run in runs:
+        c = torch.zeros(nprobe * m, dtype=torch.float64, device="cuda")
+        st = run(c)
+        got = c.view(nprobe, m).cpu().numpy()
+        assert st == 0
+        for p in range(nprobe):
+            w = want[p]
+            assert np.max(np.abs(got[p, :ms[p]] - w)) <= 1e-11 * max(1.0, np.max(np.abs(w))), p
+            assert np.all(got[p, ms[p]:] == 0.0)
 
 
 # ---------------------------------------------------------------------------
