@@ -134,7 +134,9 @@ def test_gauss_quadrature_matches_eigh_tridiagonal():
 @pytest.mark.parametrize("k,m", [(2, 30), (4, 30), (8, 30), (30, 30), (4, 100), (8, 120),
                                  (100, 100), (120, 120)])
 def test_hessenberg_log_matches_logm(k, m):
-    Q = W.laplacian_3d(10, shift=0.01).to_scipy()
+    # n = 1000 is too small for 100 full Arnoldi steps: the Krylov space is
+    # nearly exhausted and H gets an eigenvalue of -3e-14 (no principal log).
+    Q = W.laplacian_3d(10 if m < 100 else 20, shift=0.01).to_scipy()
     lo, hi = O.spectral_interval(Q)
     gamma = math.sqrt(lo * hi)
     nprobe = 12
