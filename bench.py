@@ -38,6 +38,7 @@ GRID, SHIFT, PROBES, STEPS_M, WINDOWS = 128, 0.01, 60, 50, (2, 4, 8)
 SOLVES_PER_STEP = 1 + len(WINDOWS)
 # FP64 FMA peak of this GPU: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 FMA lanes x clock
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_spmm_fp64_laplacian3d_100.md")  # noqa
 KRYLOV_SRC = os.path.join(ROOT, "paper_2606_07004_gb300", "csrc", "krylov.cu")
 
@@ -753,6 +754,70 @@ def small2d_case(args):
     return 0
 
 
+def grf_case(args):
+    """GRF maximum-likelihood sweep (Sec. 4, GRF study): a 900 x 1200 field
+    (n = 1,080,000) drawn with precision Q(50) by circulant embedding, Q(theta)
+    the Wendland C^2 covariance with support theta grid cells plus a 0.1
+    nugget, applied matrix-free (up to 19,600 stencil entries per row at
+    theta = 80: 21.7e9 implied nonzeros); theta in {20, ..., 80}.  OSA-IOP
+    m = 20, m_vec = 21, tol = 1e-6 and OSLQ m = 60, m_vec = 30 (the paper's
+    settings), mixed FP32, all seven thetas through one server.  Reports the
+    sweep times, L(theta), the argmax, the relative error of the mixed
+    log-determinant against FP64 at theta = 20, and the FP32 roofline of the
+    stencil kernel (bound: FP32 FMA issue)."""
+    import numpy as np
+    import torch
+    from paper_2606_07004_gb300 import binding as B, grf
+    import workloads as W
+
+    nx, ny = 1200, 900
+    thetas = [20.0, 30.0, 40.0, 50.0, 60.0, 70.0, 80.0]
+    t0 = time.perf_counter()
+    x = W.grf_sample(nx, ny, W.wendland_table(50.0, 0.1), seed=7)
+    t_field = time.perf_counter() - t0
+    xd = torch.as_tensor(x, device="cuda")
+    # warm-up (kernel loading) on a small sweep
+    grf.loglik_sweep(xd, nx, ny, [20.0], num_probes=21, krylov_steps=4)
+    out = {}
+    B.logdet_profile_reset()
+    B.logdet_profile_enable(True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, kw in (("osaiop", dict(method=B.METHOD_OSAIOP, num_probes=21, krylov_steps=20,
+                                     iop_window=2, tol=1e-6)),
+                     ("oslq", dict(method=B.METHOD_OSLQ, num_probes=30, krylov_steps=60,
+                                   iop_window=0, tol=None))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sw = grf.loglik_sweep(xd, nx, ny, thetas, precision=B.MIXED_FP32, seed=11, **kw)
+        dt = time.perf_counter() - t1
+        out[name] = {"sweep_s": dt, "logdets_per_s": len(thetas) / dt, "theta_hat": sw.theta_hat,
+                     "logdet": sw.logdet, "loglik": sw.loglik,
+                     "steps": [[r.steps_min, r.steps_max] for r in sw.results]}
+    clk = clocks.stop()
+    B.logdet_profile_enable(False)
+    prof = B.profile_snapshot()
+    # mixed against FP64 at theta = 20 (same seed and probes)
+    with B.Handle.grid(nx, ny, grf.wendland_table(20.0, 0.1)) as h:
+        r64 = h.osaiop(21, 20, iop_window=2, seed=11, tol=1e-6)
+        r32 = h.osaiop(21, 20, iop_window=2, seed=11, tol=1e-6, precision=B.MIXED_FP32)
+    g = prof["grid"]
+    achieved = g["flops"] / (g["ms"] / 1e3) / 1e12
+    print(json.dumps({
+        "workload": "GRF MLE sweep: Wendland C2 on 900 x 1200 (n=1080000), theta 20..80 cells, "
+                    "nugget 0.1, field drawn with theta=50, mixed FP32, matrix-free",
+        "metric": METRIC, "unit": "logdets/s", "osaiop": out["osaiop"], "oslq": out["oslq"],
+        "rel_err_mixed_vs_fp64_theta20": abs(r32.logdet - r64.logdet) / abs(r64.logdet),
+        "roofline": {"kernel": "k_grid_apply<float> (+ FP64 at theta 20 excluded)", "bound": "alu",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "peak_source": "FP32 FMA peak from unit counts and clock: 152 SMs x 128 "
+                                    "lanes x 2 flop x 2.070 GHz"},
+        "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+        "field_build_s": t_field, "clocks": clk}))
+    return 0
+
+
 def small_case(args):
     """One OSLQ (m=12) and one OSA-IOP (k=4, m=12) solve with 60 probes on the 3D
     Laplacian 100^3 + 0.01 I: the capture target for ncu (blocks larger than
@@ -791,7 +856,7 @@ def main():
     ap.add_argument("--autotune", type=int, default=1,
                     help="1 = autotuned Krylov kernel layout (tuned during warm-up); 0 = defaults")
     ap.add_argument("--workload", choices=["laplacian3d", "matern", "serving", "multishift",
-                                           "small2d"],
+                                           "small2d", "grf"],
                     default="laplacian3d",
                     help="extra measurement lines (not the default bench): matern = mixed "
                          "precision; serving = continuous batching; multishift = 8 shifts; "
@@ -814,6 +879,8 @@ def main():
         return multishift_case(args)
     if args.workload == "small2d":
         return small2d_case(args)
+    if args.workload == "grf":
+        return grf_case(args)
     if args.oracle_sample_child is not None:
         print(json.dumps(oracle_sample(args.oracle_sample_child)))
         return 0

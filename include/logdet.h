@@ -128,6 +128,24 @@ int logdet_create(int32_t n, const int32_t* rowptr, const int32_t* colind,
 int logdet_create_device(int32_t n, const int32_t* rowptr_dev, const int32_t* colind_dev,
                          const void* vals_dev, int32_t vals_dtype, logdet_handle* out);
 
+/* logdet_create_grid: a matrix-free operator on an nx x ny grid (field value
+ * of point (x, y) at row y * nx + x):
+ *   Q[(y, x), (y', x')] = w[|y - y'| * (radius + 1) + |x - x'|]
+ * when |y - y'| <= radius and |x - x'| <= radius, else 0 — a compactly
+ * supported stationary covariance restricted to the grid, such as the
+ * Wendland covariance of the GRF maximum-likelihood study (Sec. 4), whose
+ * support of tens of grid cells makes a stored CSR matrix impractical.
+ * w: (radius + 1)^2 doubles on the host, copied; w[0] is the diagonal (add
+ * a nugget there).  The caller guarantees that Q is SPD.  The handle works
+ * with every estimator, the server, plans and logdet_spmm (applied by a
+ * convolution kernel, nothing n x stencil is stored); FP64 and mixed FP32
+ * only (EINVAL for LOGDET_MIXED_BF16VEC).  logdet_info reports n = nx * ny
+ * and nnz = the entries of the implied matrix.  Errors: EINVAL (nx, ny < 1,
+ * nx * ny >= 2^31, radius outside [0, 96], non-finite w), ENOTSPD
+ * (Gershgorin upper bound <= 0), ENOMEM, ECUDA. */
+int logdet_create_grid(int32_t nx, int32_t ny, int32_t radius, const double* w,
+                       logdet_handle* out);
+
 void logdet_destroy(logdet_handle h);
 
 /* n, nnz and the Gershgorin interval [lo, hi] (unclamped) of the handle. */
@@ -193,6 +211,14 @@ int logdet_spmm(logdet_handle h, const double* x_dev, double* y_dev, int32_t b, 
  * zero and *s_eff counts the kept ones.  a_dev may alias y_dev. */
 int logdet_orth(int32_t n, int32_t s, const double* y_dev, int32_t ldy, double* a_dev,
                 int32_t lda, int32_t* s_eff, void* cuda_stream);
+
+/* logdet_quadform: *out = x^T (Q + shift I) x for the handle's operator
+ * (CSR or gridded), x an n-vector of doubles on the device — the data term
+ * of the Gaussian log-likelihood L(theta) of the GRF study (Sec. 4).  The
+ * reduction runs on the device in a fixed order; blocks until *out (host) is
+ * written.  Errors: EINVAL (NULL pointer, non-finite shift), ENOMEM, ECUDA. */
+int logdet_quadform(logdet_handle h, const double* x_dev, double shift, double* out,
+                    void* cuda_stream);
 
 /* logdet_gauss_quadrature_log: for each of nprobe symmetric tridiagonals
  * (alpha[p*m .. +m_p), beta[p*m .. +m_p-1), m_p = msteps[p] or m if msteps
@@ -340,7 +366,8 @@ int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int
  * last logdet_profile_reset: count, device milliseconds, FLOPs, bytes.  It
  * waits for the recorded events.  Classes: 0 SpMM pass, 1 update pass,
  * 2 per-probe scalar kernels, 3 Cholesky QR, 4 residual projection,
- * 5 small solves (Gauss rules, Hessenberg logs), 6 other.
+ * 5 small solves (Gauss rules, Hessenberg logs), 6 other, 7 gridded-operator
+ * applications.
  */
 #define LOGDET_KC_SPMM    0
 #define LOGDET_KC_UPDATE  1
@@ -349,7 +376,8 @@ int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int
 #define LOGDET_KC_PROJECT 4
 #define LOGDET_KC_SMALL   5
 #define LOGDET_KC_OTHER   6
-#define LOGDET_KC_COUNT   7
+#define LOGDET_KC_GRID    7
+#define LOGDET_KC_COUNT   8
 int64_t logdet_launch_count(void);
 /* Forget the autotuner's in-memory cache (the file, if any, is kept). */
 int logdet_autotune_clear(void);

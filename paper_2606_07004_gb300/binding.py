@@ -34,9 +34,9 @@ ST_BREAKDOWN, ST_NONPOS_RITZ, ST_RANK_DEFICIENT, ST_LOG_FAILED = 1, 2, 4, 8
 # The symbols the header declares (checked by the CPU test suite).
 EXPORTED = [
     "logdet_opts_default", "logdet_strerror", "logdet_last_error",
-    "logdet_create", "logdet_create_device", "logdet_destroy", "logdet_info",
+    "logdet_create", "logdet_create_device", "logdet_create_grid", "logdet_destroy", "logdet_info",
     "logdet_oslq", "logdet_osaiop",
-    "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_orth",
+    "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_quadform", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc", "logdet_hessenberg_log_e1_banded",
@@ -44,7 +44,7 @@ EXPORTED = [
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
 ]
-KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other"]
+KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid"]
 
 
 class logdet_result(C.Structure):
@@ -95,6 +95,7 @@ _sig("logdet_strerror", C.c_char_p, [C.c_int])
 _sig("logdet_last_error", C.c_char_p, [])
 _sig("logdet_create", C.c_int, [_i32, _P, _P, _P, _i32, C.POINTER(_P)])
 _sig("logdet_create_device", C.c_int, [_i32, _P, _P, _P, _i32, C.POINTER(_P)])
+_sig("logdet_create_grid", C.c_int, [_i32, _i32, _i32, _P, C.POINTER(_P)])
 _sig("logdet_destroy", None, [_P])
 _sig("logdet_info", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl)])
 for _n in ("logdet_oslq", "logdet_osaiop"):
@@ -102,6 +103,7 @@ for _n in ("logdet_oslq", "logdet_osaiop"):
 _sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
 _sig("logdet_probe_fill_gaussian", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
 _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
+_sig("logdet_quadform", C.c_int, [_P, _P, _dbl, C.POINTER(_dbl), _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
@@ -229,6 +231,20 @@ class Handle:
                                       C.byref(self._h)), "logdet_create")
 
     @classmethod
+    def grid(cls, nx: int, ny: int, table) -> "Handle":
+        """Matrix-free gridded operator (logdet_create_grid); table is the
+        (R + 1) x (R + 1) quadrant table W(|dy|, |dx|)."""
+        w = np.ascontiguousarray(table, dtype=np.float64)
+        if w.ndim != 2 or w.shape[0] != w.shape[1]:
+            raise ValueError("table must be (R + 1) x (R + 1)")
+        h = cls.__new__(cls)
+        h._h = _P()
+        h._keep = None
+        _check(_lib.logdet_create_grid(nx, ny, w.shape[0] - 1, _ptr(w), C.byref(h._h)),
+               "logdet_create_grid")
+        return h
+
+    @classmethod
     def from_csr(cls, A) -> "Handle":
         """From any object with n, rowptr, colind, vals (host arrays)."""
         return cls(A.n, A.rowptr, A.colind, A.vals)
@@ -292,6 +308,13 @@ class Handle:
         out = C.c_size_t()
         _check(_lib.logdet_estimate_bytes(self._h, method, num_probes, krylov_steps, iop_window,
                                           C.byref(o), C.byref(out)), "logdet_estimate_bytes")
+        return out.value
+
+    def quadform(self, x, shift: float = 0.0, stream=None) -> float:
+        """x^T (Q + shift I) x for a device vector x of n doubles (logdet_quadform)."""
+        out = _dbl()
+        _check(_lib.logdet_quadform(self._h, _ptr(x), float(shift), C.byref(out), _stream(stream)),
+               "logdet_quadform")
         return out.value
 
     def spmm(self, x, y, b, ld, stream=None):

@@ -312,6 +312,13 @@ __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n
   }
 }
 
+int reduce_partials_fp64(const double* part, int nrows, int ntiles, double* out, cudaStream_t st) {
+  ProfScope prof(KC_SCALAR, st);
+  k_reduce_rows<<<nrows, 128, 0, st>>>(part, ntiles, 0, out);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+
 size_t project_workspace_doubles(int n, int s, int r) {
   int ntiles = div_up(n, kGramRows);
   return (size_t)s * r * ntiles + (size_t)s * r + 64;

@@ -29,6 +29,9 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
                           int gaussian = 0, const uint64_t* keyp = nullptr);
 size_t project_workspace_doubles(int n, int s, int r);
 
+// out[i] = sum_t part[i * ntiles + t] for i < nrows (FP64 partials).
+int reduce_partials_fp64(const double* part, int nrows, int ntiles, double* out, cudaStream_t st);
+
 // Per-column squared norms of a block (FP64 or FP32 elements): partials
 // [ld][ntiles] in the Krylov layout, for k_init_sigma.
 template <typename T>

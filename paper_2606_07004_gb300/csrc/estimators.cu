@@ -1,6 +1,7 @@
 // OSLQ (Algorithm 3) and OSA-IOP (Algorithm 2 with Algorithm 1) on the
 // device, and the C-ABI of liblogdet.
 #include "dense.cuh"
+#include "grid.cuh"
 #include "handle.cuh"
 #include "krylov.cuh"
 #include "profile.cuh"
@@ -101,6 +102,11 @@ int logdet_create_device(int32_t n, const int32_t* rowptr_dev, const int32_t* co
   return create_handle(n, rowptr_dev, colind_dev, vals_dev, vals_dtype, true, out);
 }
 
+int logdet_create_grid(int32_t nx, int32_t ny, int32_t radius, const double* w,
+                       logdet_handle* out) {
+  return create_grid_handle(nx, ny, radius, w, out);
+}
+
 void logdet_destroy(logdet_handle h) { destroy_handle(h); }
 
 int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* lo, double* hi) {
@@ -152,6 +158,11 @@ int logdet_spmm(logdet_handle h, const double* x, double* y, int32_t b, int32_t 
     return LOGDET_EINVAL;
   }
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  if (h->kind == 1) {
+    LD_TRY(grid_apply<double>(h, h->gtab, x, y, ld, nullptr, st));
+    LD_CUDA(cudaStreamSynchronize(st));
+    return LOGDET_OK;
+  }
   DevBuf<double> v(st);
   const double* vals = (const double*)h->vals;
   if (h->vals_dtype != LOGDET_VALS_F64) {
@@ -160,6 +171,46 @@ int logdet_spmm(logdet_handle h, const double* x, double* y, int32_t b, int32_t 
     vals = v.p;
   }
   LD_TRY(spmm_block<double>(h->rowptr, h->colind, vals, h->n, x, y, ld, st, nullptr, h));
+  LD_CUDA(cudaStreamSynchronize(st));
+  return LOGDET_OK;
+}
+
+int logdet_quadform(logdet_handle h, const double* x, double shift, double* out,
+                    void* cuda_stream) {
+  if (!h || !x || !out || !std::isfinite(shift)) {
+    set_error("quadform: NULL argument or non-finite shift");
+    return LOGDET_EINVAL;
+  }
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : h->stream;
+  const int n = h->n, ld = 2;
+  DevBuf<double> X(st), Y(st), part(st), red(st), cs(st);
+  LD_TRY(X.alloc((size_t)n * ld));
+  LD_TRY(Y.alloc((size_t)n * ld));
+  LD_TRY(X.zero());
+  LD_CUDA(cudaMemcpy2DAsync(X.p, ld * sizeof(double), x, sizeof(double), sizeof(double), n,
+                            cudaMemcpyDeviceToDevice, st));
+  LD_TRY(cs.alloc(ld));
+  LD_TRY(fill_double(cs.p, ld, shift, st));
+  if (h->kind == 1) {
+    LD_TRY(grid_apply<double>(h, h->gtab, X.p, Y.p, ld, cs.p, st));
+  } else {
+    DevBuf<double> v(st);
+    const double* vals = (const double*)h->vals;
+    if (h->vals_dtype != LOGDET_VALS_F64) {
+      LD_TRY(v.alloc(h->nnz));
+      LD_TRY(scaled_values<double>(h, 1.0, v.p, st));
+      vals = v.p;
+    }
+    LD_TRY(spmm_block<double>(h->rowptr, h->colind, vals, n, X.p, Y.p, ld, st, cs.p, h));
+  }
+  const TileGeom g = tile_geom(ld, Vec16<double>::N, 0, 0, n);
+  const int ntiles = div_up(n, g.tile_rows);
+  LD_TRY(part.alloc((size_t)ld * ntiles));
+  LD_TRY(red.alloc(ld));
+  const double* dv[1] = {X.p};
+  LD_TRY(dots_pass<double>(Y.p, dv, 1, part.p, n, ld, g.tile_rows, ntiles, g.threads, st));
+  LD_TRY(reduce_partials_fp64(part.p, ld, ntiles, red.p, st));
+  LD_CUDA(cudaMemcpyAsync(out, red.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   LD_CUDA(cudaStreamSynchronize(st));
   return LOGDET_OK;
 }

@@ -25,6 +25,11 @@ struct logdet_ctx {
   std::vector<int> h_rowptr;
   std::mutex items_mu;
   std::map<int, std::pair<int4*, int>> items;  // tile_rows -> (device items, count)
+  // Matrix-free gridded operator (kind == 1; see grid.cuh): no CSR arrays.
+  int kind = 0;                  // 0 CSR, 1 grid operator
+  int gx = 0, gy = 0, gr = 0;    // grid size and stencil radius
+  double* gtab = nullptr;        // device expanded table of W (FP64)
+  int* grx = nullptr;            // device [gr + 1]: last nonzero |dx| per |dy|
 };
 
 namespace ld {

@@ -160,4 +160,29 @@ int launch_init_sigma(const ScalarBatch& b, cudaStream_t s);
 
 int sm_count();
 
+// Reduce the per-thread accumulators of all rows of the CTA for one dot and
+// write one partial per column.  smem holds blockDim.x * V accumulators.
+// The CTA owns columns [col_off, col_off + width) of the block; partials are
+// indexed by the block column.
+template <typename T, typename Acc>
+__device__ __forceinline__ void cta_reduce_write(Acc* smem, const Acc (&acc)[Vec16<T>::N],
+                                                 bool live, int G, int R, int col_off, int width,
+                                                 typename PartOf<T>::type* dst, int ntiles,
+                                                 int tile) {
+  constexpr int V = Vec16<T>::N;
+  __syncthreads();
+  if (live) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) smem[threadIdx.x * V + v] = acc[v];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < width; c += blockDim.x) {
+    int g = c / V, v = c - (c / V) * V;
+    Acc t;
+    t.zero();
+    for (int rr = 0; rr < R; ++rr) t.add(smem[(rr * G + g) * V + v]);
+    put_part(dst + (size_t)(col_off + c) * ntiles + tile, t);
+  }
+}
+
 }  // namespace ld

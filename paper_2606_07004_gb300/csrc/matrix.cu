@@ -364,6 +364,8 @@ void destroy_handle(logdet_ctx* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& kv : h->items) cudaFree(kv.second.first);
+  if (h->gtab) cudaFree(h->gtab);
+  if (h->grx) cudaFree(h->grx);
   if (h->owns) {
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colind) cudaFree(h->colind);

@@ -15,7 +15,8 @@ enum KClass {
   KC_PROJECT = 4, // Hutch++ residual projection
   KC_SMALL = 5,   // tridiagonal Gauss rules, Hessenberg logarithms
   KC_OTHER = 6,   // probe fill, conversions, sketch assembly, Gershgorin, scaling
-  KC_COUNT = 7
+  KC_GRID = 7,    // gridded-operator application (the pass-1 SpMM of a grid handle)
+  KC_COUNT = 8
 };
 
 void prof_count();  // one kernel launch

@@ -130,9 +130,12 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     if (!sv || !sv->in_krylov() || r->rc) continue;
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
-    if (ek == 0) sv->add_pass1(&sd[th], coef, wc);
-    else if (ek == 1) sv->add_pass1(&sf[th], coef, wc);
-    else sv->add_pass1(&sb[th], coef, wc);
+    int rc = ek == 0 ? sv->add_pass1(&sd[th], coef, wc)
+                     : ek == 1 ? sv->add_pass1(&sf[th], coef, wc) : sv->add_pass1(&sb[th], coef, wc);
+    if (rc) {
+      r->rc = rc;  // this request fails; the others step on
+      continue;
+    }
     stepping.push_back(sv);
   }
   if (stepping.empty()) return 0;

@@ -1,6 +1,7 @@
 // Resumable OSLQ / OSA-IOP solves (see solve.cuh).
 #include "profile.cuh"
 #include "solve.cuh"
+#include "grid.cuh"
 #include "tune.cuh"
 
 #include <cmath>
@@ -53,6 +54,10 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
   if (c.precision != LOGDET_FP64 && c.precision != LOGDET_MIXED_FP32 &&
       c.precision != LOGDET_MIXED_BF16VEC) {
     set_error("precision %d unknown", c.precision);
+    return LOGDET_EINVAL;
+  }
+  if (h->kind == 1 && c.precision == LOGDET_MIXED_BF16VEC) {
+    set_error("gridded operators support FP64 and mixed FP32 blocks only");
     return LOGDET_EINVAL;
   }
   double lo, hi;
@@ -132,6 +137,7 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
   Vfull = Vfull_;
   tune = tc;
   if (tune.split < 1 || ld % tune.split || (ld / tune.split) % Vec16<T>::N) tune.split = 1;
+  if (hctx && hctx->kind == 1) tune = TuneCfg();  // gridded operator: full-width default layout
   width = ld / tune.split;
   g = tile_geom(width, Vec16<T>::N, tune.threads, tune.iters, n);
   ntiles = div_up(n, g.tile_rows);
@@ -207,6 +213,25 @@ void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
       for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
     }
     out.push_back(J);
+  }
+}
+
+template <typename T>
+int KRun<T>::grid_pass1(int j) {
+  if constexpr (std::is_same<T, bf16>::value) {
+    set_error("gridded operators do not take BF16 blocks");
+    return LOGDET_EINVAL;
+  } else {
+    using CT = typename Compute<T>::type;
+    LD_TRY(grid_apply<T>(hctx, static_cast<const CT*>(gtab), ptr(j), y.p, ld, colshift, st));
+    const T* dv[kMaxWin];
+    int nd = 0;
+    if (method == 0) {
+      dv[nd++] = ptr(j);
+    } else {
+      for (int i = win_lo(j); i <= j; ++i) dv[nd++] = ptr(i);
+    }
+    return dots_pass<T>(y.p, dv, nd, part.p, n, ld, g.tile_rows, ntiles, g.threads, st);
   }
 }
 
@@ -418,6 +443,7 @@ struct Solve : ISolve {
   int n, s, r, b, ld, lds, m, kk;
   double lo, hi, alpha, gamma, shift;
   DevBuf<typename ValOf<T>::type> vals;
+  DevBuf<typename Compute<T>::type> gtabs;  // gridded operator: scaled table
   DevBuf<T> Vst, Xc;
   DevBuf<double> X64, outv, cshift;
   DevBuf<int> keep;
@@ -430,7 +456,7 @@ struct Solve : ISolve {
   const uint64_t* dev_keys = nullptr;  // graph plans: probe keys in device memory
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
-      : h(h_), c(c_), st(st_), vals(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
+      : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
         keep(st_) {
     n = h->n;
     s = c.plain ? 0 : c.P / 3;
@@ -495,7 +521,7 @@ struct Solve : ISolve {
   // autotuner's choice for this matrix.
   int layout(int w, bool track_e, TuneCfg* tc) {
     *tc = TuneCfg();
-    if (!c.autotune) return LOGDET_OK;
+    if (!c.autotune || h->kind == 1) return LOGDET_OK;
     const int nd = c.method == 0 ? 1 : kk, nb = c.method == 0 ? 2 : kk;
     return autotune_krylov<T>(h, vals.p, w, nd, nb, track_e ? 1 : 0,
                               st, tc);
@@ -517,9 +543,15 @@ struct Solve : ISolve {
   int setup() {
     LD_TRY(alloc_pinned());
     LD_TRY(keep.alloc(std::max(s, 1)));
-    LD_TRY(vals.alloc(h->nnz));
     const double cscale = c.method == 0 ? alpha : gamma;
-    LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
+    if (h->kind == 1) {
+      // Gridded operator: the table of W / c replaces the scaled CSR values.
+      LD_TRY(gtabs.alloc(grid_table_count(h)));
+      LD_TRY(grid_table<typename Compute<T>::type>(h, cscale, gtabs.p, st));
+    } else {
+      LD_TRY(vals.alloc(h->nnz));
+      LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
+    }
     if (c.shift != 0.0) {
       // (Q + shift I)/c applied as vals/c plus (shift/c) times the row's own entry.
       const size_t cnt = std::max(ld, lds);
@@ -534,7 +566,8 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
-    run->hctx = h;
+      run->hctx = h;
+      run->gtab = gtabs.p;
       TuneCfg tc;
       LD_TRY(layout(ld, c.method == 1, &tc));
       if (c.method == 0) {
@@ -554,7 +587,12 @@ struct Solve : ISolve {
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian, dkey(0)));
-      LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
+      if constexpr (std::is_same<T, bf16>::value) {
+        LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
+      } else {
+        if (h->kind == 1) LD_TRY(grid_apply<T>(h, gtabs.p, S.p, Yt.p, lds, cshift.p, st));
+        else LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
+      }
       S.release();
       if constexpr (std::is_same<T, double>::value) {
         LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
@@ -570,7 +608,8 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
-    run->hctx = h;
+      run->hctx = h;
+      run->gtab = gtabs.p;
       TuneCfg tc;
       LD_TRY(layout(ld, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
@@ -580,7 +619,8 @@ struct Solve : ISolve {
       LD_TRY(Vst.alloc((size_t)n * lds * m));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian, dkey(0)));
       run->colshift = cshift.p;
-    run->hctx = h;
+      run->hctx = h;
+      run->gtab = gtabs.p;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
@@ -621,6 +661,7 @@ struct Solve : ISolve {
     run.reset(new KRun<T>(st));
     run->colshift = cshift.p;
     run->hctx = h;
+    run->gtab = gtabs.p;
     TuneCfg tc;
     LD_TRY(layout(ld, true, &tc));
     LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
@@ -656,6 +697,7 @@ struct Solve : ISolve {
     // Device buffers are released in stream order; the copies above read them first.
     run.reset();
     vals.release();
+    gtabs.release();
     cshift.release();
     X64.release();
     Xc.release();
@@ -674,12 +716,14 @@ struct Solve : ISolve {
     return rc;
   }
 
-  void add_pass1(void* vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) override {
+  int add_pass1(void* vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) override {
     auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
     const int j = run->next_step();
-    run->spmm_jobs(j, v);
+    if (h->kind == 1) LD_TRY(run->grid_pass1(j));
+    else run->spmm_jobs(j, v);
     coef.push_back(run->scalar_job(j, run->pass1_dots(j), true));
     widths.push_back(run->ld);
+    return LOGDET_OK;
   }
 
   bool add_pass2(void* vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) override {
@@ -759,7 +803,7 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
   const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
-  const size_t vals = (size_t)h->nnz * (f32 ? 4 : 8);
+  const size_t vals = h->kind == 1 ? grid_table_count(h) * 8 : (size_t)h->nnz * (f32 ? 4 : 8);
   const TileGeom g = tile_geom((int)ld, vec, 0, 0, (int)n);
   const size_t ntiles = div_up((int)n, g.tile_rows);
   const size_t part = (size_t)std::max(k, 2) * ld * ntiles * (f32 ? 8 : 8);
@@ -844,7 +888,7 @@ int issue_solve(ISolve* sv, cudaStream_t st) {
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
     sd.clear(); sf.clear(); sb.clear(); ud.clear(); uf.clear(); ub.clear(); sj.clear(); widths.clear();
-    sv->add_pass1(ek == 0 ? (void*)&sd : ek == 1 ? (void*)&sf : (void*)&sb, sj, widths);
+    LD_TRY(sv->add_pass1(ek == 0 ? (void*)&sd : ek == 1 ? (void*)&sf : (void*)&sb, sj, widths));
     if (ek == 0) LD_TRY(launch_spmm_jobs<double>(sd, th, st));
     else if (ek == 1) LD_TRY(launch_spmm_jobs<float>(sf, th, st));
     else LD_TRY(launch_spmm_jobs<bf16>(sb, th, st));

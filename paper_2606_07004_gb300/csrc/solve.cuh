@@ -84,6 +84,7 @@ struct KRun {
   T* Vfull = nullptr;
   const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
   logdet_ctx* hctx = nullptr;        // matrix handle (work items of irregular matrices)
+  const void* gtab = nullptr;        // gridded operator: scaled expanded table (compute type)
   TileGeom g{};
   TuneCfg tune{};
   int width = 0;  // columns per slice job (ld / tune.split)
@@ -112,6 +113,9 @@ struct KRun {
   int pass1_dots(int j) const { return method == 0 ? 1 : j - win_lo(j) + 1; }
   // Step j's jobs, one per column slice.
   void spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const;
+  // Gridded operator: step j's pass 1 (y = Q~ u_j and the window dots),
+  // launched on the run's stream.
+  int grid_pass1(int j);
   void upd_jobs(int j, std::vector<UpdJob<T>>& out) const;
   int slice_live(int q) const;
   // Scalar job over pass-1 partials (spmm_pass) or pass-2 / norm partials.
@@ -139,7 +143,8 @@ struct ISolve {
   // Run the current non-Krylov phase (SETUP, MID, FINISH) and move on.
   virtual int run_phase() = 0;
   // Krylov step: append this solve's pass-1 job etc. for its next step.
-  virtual void add_pass1(void* spmm_vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) = 0;
+  // (For a gridded operator the pass is launched here, on the solve's stream.)
+  virtual int add_pass1(void* spmm_vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) = 0;
   virtual bool add_pass2(void* upd_vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) = 0;
   virtual void step_issued() = 0;
   // After FINISH's copies completed: assemble the host result.

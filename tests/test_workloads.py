@@ -82,3 +82,35 @@ def test_graph_laplacian_from_edges():
     assert L[0, 0] == 3.5 and L[4, 4] == 0.5 and L[0, 1] == -1.0
     assert np.all(np.diff(A.rowptr) >= 1)                  # every diagonal entry stored
     assert sp.csr_matrix(L).nnz == 5 + 2 * 4
+
+
+def test_wendland_table_and_grid_operator():
+    r = np.array([0.0, 0.25, 0.5, 0.999, 1.0, 2.0])
+    phi = W.wendland_c2(r)
+    assert phi[0] == 1.0 and phi[4] == 0.0 and phi[5] == 0.0
+    assert np.all(np.diff(phi) <= 0)
+    assert phi[1] == pytest.approx(0.75 ** 4 * 2.0)
+    T = W.wendland_table(4.0, nugget=0.1)
+    assert T.shape == (4, 4)                      # offsets 0..3 inside radius 4
+    assert T[0, 0] == pytest.approx(1.1) and T[0, 3] > 0 and np.all(T == T.T)
+    A = W.grid_operator_csr(7, 5, T)
+    Q = A.to_scipy().toarray()
+    assert np.array_equal(Q, Q.T)
+    # entry of points (y=2, x=3) and (y=3, x=1): offsets (1, 2)
+    assert Q[2 * 7 + 3, 3 * 7 + 1] == T[1, 2]
+    assert np.all(np.linalg.eigvalsh(Q) > 0)      # Wendland C^2 is PD in 2D
+    nnz = sum((5 - abs(dy)) * (7 - abs(dx)) for dy in range(-3, 4) for dx in range(-3, 4)
+              if T[abs(dy), abs(dx)] != 0)
+    assert A.nnz == nnz
+
+
+def test_grf_sample_covariance():
+    # covariance of the embedded field: sample variance of many fields close to
+    # the diagonal of Q^{-1} (precision=True) or of Q (precision=False)
+    T = W.wendland_table(3.0, nugget=0.5)
+    A = W.grid_operator_csr(12, 10, T).to_scipy().toarray()
+    xs = np.stack([W.grf_sample(12, 10, T, seed=s, precision=False) for s in range(4000)])
+    assert abs(xs.var(axis=0).mean() / A.diagonal().mean() - 1.0) < 0.05
+    xp = np.stack([W.grf_sample(12, 10, T, seed=s) for s in range(4000)])
+    centre = 5 * 12 + 6
+    assert abs(xp[:, centre].var() / np.linalg.inv(A)[centre, centre] - 1.0) < 0.15

@@ -12,6 +12,10 @@ from .matrices import (  # noqa: F401
     matern_2d,
     powerlaw_graph_laplacian,
     graph_laplacian,
+    wendland_c2,
+    wendland_table,
+    grid_operator_csr,
+    grf_sample,
     diagonal_matrix,
     scaled_identity,
     random_spd_dense_csr,

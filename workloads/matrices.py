@@ -86,6 +86,68 @@ def graph_laplacian(n: int, edges: np.ndarray, shift: float = 0.0, dtype=np.floa
     return _from_scipy(sp.diags(deg + shift) - Adj, dtype)
 
 
+def wendland_c2(r: np.ndarray) -> np.ndarray:
+    """Wendland's C^2 function for d <= 3: (1 - r)^4 (4 r + 1) on [0, 1), 0 beyond."""
+    r = np.asarray(r, dtype=np.float64)
+    return np.where(r < 1.0, (1.0 - r) ** 4 * (4.0 * r + 1.0), 0.0)
+
+
+def wendland_table(theta: float, nugget: float = 0.0) -> np.ndarray:
+    """Quadrant table W[|dy|, |dx|] = phi(sqrt(dx^2 + dy^2) / theta) of the
+    Wendland C^2 covariance with support radius theta grid cells, plus a
+    nugget on W[0, 0]; (R + 1) x (R + 1) with R the largest offset inside the
+    support."""
+    R = max(0, int(math.ceil(theta)) - 1)
+    d = np.hypot(*np.meshgrid(np.arange(R + 1), np.arange(R + 1), indexing="ij"))
+    W = wendland_c2(d / theta)
+    W[0, 0] += nugget
+    return W
+
+
+def grid_operator_csr(nx: int, ny: int, W: np.ndarray, dtype=np.float64) -> CSR:
+    """Explicit CSR of the gridded operator Q[(y,x),(y',x')] = W[|y-y'|, |x-x'|]
+    (row index y * nx + x), for grids small enough to store."""
+    R = W.shape[0] - 1
+    rows, cols, vals = [], [], []
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            w = W[abs(dy), abs(dx)]
+            if w == 0.0:
+                continue
+            ok = (yy + dy >= 0) & (yy + dy < ny) & (xx + dx >= 0) & (xx + dx < nx)
+            r = (yy * nx + xx)[ok]
+            rows.append(r)
+            cols.append(r + dy * nx + dx)
+            vals.append(np.full(r.size, w))
+    n = nx * ny
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n))
+    return _from_scipy(A, dtype)
+
+
+def grf_sample(nx: int, ny: int, W: np.ndarray, seed: int, precision: bool = True) -> np.ndarray:
+    """A seeded Gaussian random field on the nx x ny grid (row-major, y * nx + x)
+    by circulant embedding of the gridded operator W on a periodic grid of at
+    least (ny + R) x (nx + R) points: precision=True draws from N(0, Q^{-1})
+    (Q the embedded operator), else from N(0, Q).  Raises if the embedding is
+    not positive definite."""
+    R = W.shape[0] - 1
+    My, Mx = ny + R + 1, nx + R + 1
+    c = np.zeros((My, Mx))
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            c[dy % My, dx % Mx] += W[abs(dy), abs(dx)]
+    lam = np.real(np.fft.fft2(c))
+    if lam.min() <= 0:
+        raise ValueError("circulant embedding is not positive definite")
+    spec = 1.0 / lam if precision else lam
+    rng = np.random.default_rng(seed)
+    z = rng.standard_normal((My, Mx)) + 1j * rng.standard_normal((My, Mx))
+    f = np.fft.fft2(np.sqrt(spec / (My * Mx)) * z)
+    return np.ascontiguousarray(np.real(f)[:ny, :nx]).ravel()
+
+
 def _lap1d(N: int) -> sp.csr_matrix:
     return sp.diags([-np.ones(N - 1), 2 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1], format="csr")
 
