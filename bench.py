@@ -822,10 +822,19 @@ def small_case(args):
     """One OSLQ (m=12) and one OSA-IOP (k=4, m=12) solve with 60 probes on the 3D
     Laplacian 100^3 + 0.01 I: the capture target for ncu (blocks larger than
     L2, about 3 GB on the device).  With --workload matern: one mixed-FP32
-    OSLQ solve (m=12, 120 probes) on the Matern 1024^2 operator instead."""
+    OSLQ solve (m=12, 120 probes) on the Matern 1024^2 operator instead; with
+    --workload grf: one mixed-FP32 OSLQ solve (m=4, 30 probes) on the
+    Wendland theta=50 gridded operator, 900 x 1200."""
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
+    if args.workload == "grf":
+        from paper_2606_07004_gb300 import grf
+        with B.Handle.grid(1200, 900, grf.wendland_table(50.0, 0.1)) as h:
+            r = h.oslq(30, 4, seed=1, precision=B.MIXED_FP32)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_case": "grf", "oslq": r.logdet, "oslq_ms": r.device_ms}))
+        return 0
     if args.workload == "matern":
         import numpy as np
         A = W.matern_2d(1024, 0.05, dtype=np.float32)

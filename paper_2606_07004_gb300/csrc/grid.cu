@@ -119,16 +119,16 @@ template int grid_table<float>(const logdet_ctx*, double, float*, cudaStream_t);
 
 
 // ---------------------------------------------------------------------------
-// y = Q x.  A CTA owns work items (output row y, segment of kGridThreads *
-// kGridP outputs along x, vector chunk of V block columns) and keeps the
-// expanded table in shared memory for all of them.  For each input row yy
-// within R of y it stages the row's segment plus halo in shared memory, and
-// every thread runs a sliding window over dx for its kGridP consecutive
-// outputs: one shared load of x and one of W per step feed kGridP x V FMAs.
-// The loop over dx is unrolled by kGridP so that the window's register slots
-// are static (position base + k lives in slot k mod kGridP).
-// Items are ordered chunk, segment, row, so that CTAs running together work
-// on neighbouring rows and share their input rows in L2.
+// y = Q x.  A CTA owns work items (a block of kGridTY output rows, a segment
+// of kGridTX * kGridP outputs along x, a vector chunk of V block columns) and
+// keeps the expanded table in shared memory for all of them.  It stages each
+// input row within R of the block once (segment plus halo), and warp ty then
+// accumulates the row's contribution to output row y0 + ty: every lane runs
+// a sliding window over dx for its kGridP consecutive outputs, one shared
+// load of x and one of W per step feeding kGridP x V FMAs.  The loop over dx
+// is unrolled by kGridP so that the window's register slots are static
+// (position base + k lives in slot k mod kGridP).  Items are ordered chunk,
+// segment, row block, so that CTAs running together share input rows in L2.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
@@ -141,33 +141,34 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
   using VT = typename Vec16<T>::type;  // 16 bytes: V values of CT (T is double or float)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = 2 * R + 1 + P;
-  const int TX = kGridThreads * P;
+  const int TX = kGridTX * P;
   const int SL = TX + 2 * R + 2 * P;  // staged positions per input row
   CT* wt = reinterpret_cast<CT*>(smem_raw);
   // Staged row after the table (16-byte aligned).  Position p sits at slot
-  // p + p / P: the threads of a warp read positions P apart, and the skew
+  // p + p / P: the lanes of a warp read positions P apart, and the skew
   // spreads each quarter-warp's 16-byte reads over distinct banks.
   VT* xs = reinterpret_cast<VT*>(smem_raw + ((size_t)(R + 1) * L * sizeof(CT) + 15) / 16 * 16);
   const int t = threadIdx.x;
+  const int tx = t % kGridTX, ty = t / kGridTX;
   for (int i = t; i < (R + 1) * L; i += blockDim.x) wt[i] = tab[i];
-  const long long total = (long long)ny * nseg * nchunk;
+  const int nyb = (ny + kGridTY - 1) / kGridTY;
+  const long long total = (long long)nyb * nseg * nchunk;
   for (long long it = blockIdx.x; it < total; it += gridDim.x) {
-    const int yo = (int)(it % ny);
-    const int seg = (int)((it / ny) % nseg);
-    const int chunk = (int)(it / ((long long)ny * nseg));
+    const int yb = (int)(it % nyb);
+    const int seg = (int)((it / nyb) % nseg);
+    const int chunk = (int)(it / ((long long)nyb * nseg));
     const int col0 = chunk * V;
     const int x0 = seg * TX;
+    const int y0 = yb * kGridTY;
+    const int yo = y0 + ty;
     CT acc[P][V];
 #pragma unroll
     for (int q = 0; q < P; ++q)
 #pragma unroll
       for (int v = 0; v < V; ++v) acc[q][v] = CT(0);
-    const int y_lo = max(0, yo - R), y_hi = min(ny - 1, yo + R);
+    const int y_lo = max(0, y0 - R), y_hi = min(ny - 1, y0 + kGridTY - 1 + R);
     for (int yy = y_lo; yy <= y_hi; ++yy) {
-      const int dy = abs(yy - yo);
-      const int rxd = rx[dy];
       __syncthreads();  // previous row consumed (and the table loaded)
-      if (rxd < 0) continue;
       const T* xrow = x + (size_t)yy * nx * ld + col0;
       for (int i = t; i < SL; i += blockDim.x) {
         const int gxp = x0 - R + i;
@@ -177,7 +178,11 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
         xs[i + i / P] = v;
       }
       __syncthreads();
-      const int base = t * P + (R - rxd);
+      const int dy = abs(yy - yo);
+      if (yo >= ny || dy > R) continue;
+      const int rxd = rx[dy];
+      if (rxd < 0) continue;
+      const int base = tx * P + (R - rxd);
       const int Lc = (2 * rxd + 1 + P - 1) / P * P;
       const CT* wrow = wt + (size_t)dy * L + (R - rxd);
       CT win[P][V];
@@ -201,18 +206,20 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
         }
       }
     }
+    if (yo < ny) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int xo = x0 + t * P + q;
-      if (xo >= nx) break;
-      const size_t off = ((size_t)yo * nx + xo) * ld + col0;
-      if (colshift) {
-        CT xr[V];
-        load_vec<T>(x + off, xr);
+      for (int q = 0; q < P; ++q) {
+        const int xo = x0 + tx * P + q;
+        if (xo >= nx) break;
+        const size_t off = ((size_t)yo * nx + xo) * ld + col0;
+        if (colshift) {
+          CT xr[V];
+          load_vec<T>(x + off, xr);
 #pragma unroll
-        for (int c = 0; c < V; ++c) acc[q][c] = fma(CT(colshift[col0 + c]), xr[c], acc[q][c]);
+          for (int c = 0; c < V; ++c) acc[q][c] = fma(CT(colshift[col0 + c]), xr[c], acc[q][c]);
+        }
+        store_vec<T>(y + off, acc[q]);
       }
-      store_vec<T>(y + off, acc[q]);
     }
   }
 }
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
 static size_t grid_smem_bytes(int R, size_t ct) {
   const size_t tabn = (size_t)(R + 1) * grid_row_len(R);
   const size_t tab_bytes = (tabn * ct + 15) / 16 * 16;
-  const size_t sl = (size_t)kGridThreads * kGridP + 2 * R + 2 * kGridP;
+  const size_t sl = (size_t)kGridTX * kGridP + 2 * R + 2 * kGridP;
   return tab_bytes + (sl + sl / kGridP + 1) * 16;
 }
 
@@ -238,9 +245,9 @@ int grid_apply(const logdet_ctx* h, const typename Compute<T>::type* tab, const 
   if (smem > 48 * 1024)
     LD_CUDA(cudaFuncSetAttribute(k_grid_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  const int nseg = div_up(h->gx, kGridThreads * kGridP);
+  const int nseg = div_up(h->gx, kGridTX * kGridP);
   const int nchunk = ld / V;
-  const long long items = (long long)h->gy * nseg * nchunk;
+  const long long items = (long long)div_up(h->gy, kGridTY) * nseg * nchunk;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_apply<T>, kGridThreads, smem);
   if (per_sm < 1) per_sm = 1;

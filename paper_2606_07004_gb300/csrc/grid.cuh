@@ -14,7 +14,9 @@ namespace ld {
 
 constexpr int kMaxGridRadius = 96;
 constexpr int kGridP = 8;          // outputs per thread along x
-constexpr int kGridThreads = 64;   // threads per CTA: an x segment of 512 outputs
+constexpr int kGridTX = 32;        // threads along x: an x segment of 256 outputs
+constexpr int kGridTY = 8;         // output rows per CTA (one warp each)
+constexpr int kGridThreads = kGridTX * kGridTY;
 
 // Row length of the expanded table: W(dy, dx) at [dy * L + dx + R], dx in
 // [-R, R], followed by kGridP zeros.
