@@ -130,6 +130,22 @@ template int grid_table<float>(const logdet_ctx*, double, float*, cudaStream_t);
 // (position base + k lives in slot k mod kGridP).  Items are ordered chunk,
 // segment, row block, so that CTAs running together share input rows in L2.
 // ---------------------------------------------------------------------------
+// Packed FP32 pairs (Blackwell's fma.rn.f32x2): two IEEE single-precision
+// FMAs per instruction, each rounded exactly as fmaf.  The FP32 kernel is
+// bound by instruction issue, and the four block columns of a thread share
+// the weight, so its FMAs go in pairs.
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b,
+                                                        unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long dup_f32x2(float w) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(w));
+  return d;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
     const typename Compute<T>::type* __restrict__ tab, const int* __restrict__ rx, int nx, int ny,
@@ -185,24 +201,50 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
       const int base = tx * P + (R - rxd);
       const int Lc = (2 * rxd + 1 + P - 1) / P * P;
       const CT* wrow = wt + (size_t)dy * L + (R - rxd);
-      CT win[P][V];
+      if constexpr (std::is_same<T, float>::value) {
+        // acc[q][0..3] as two packed pairs; the same window and order as below.
+        unsigned long long win2[P][2];
+        unsigned long long* acc2 = reinterpret_cast<unsigned long long*>(&acc[0][0]);
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        const int pos = base + q;
-        const VT v = xs[pos + pos / P];
-        memcpy(win[q], &v, sizeof v);
-      }
-      for (int s0 = 0; s0 < Lc; s0 += P) {
-#pragma unroll
-        for (int u = 0; u < P; ++u) {
-          const CT w = wrow[s0 + u];
-#pragma unroll
-          for (int q = 0; q < P; ++q)
-#pragma unroll
-            for (int c = 0; c < V; ++c) acc[q][c] = fma(w, win[(q + u) % P][c], acc[q][c]);
-          const int pos = base + s0 + u + P;
+        for (int q = 0; q < P; ++q) {
+          const int pos = base + q;
           const VT v = xs[pos + pos / P];
-          memcpy(win[u], &v, sizeof v);
+          memcpy(win2[q], &v, sizeof v);
+        }
+        for (int s0 = 0; s0 < Lc; s0 += P) {
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            const unsigned long long w2 = dup_f32x2(wrow[s0 + u]);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              acc2[2 * q] = fma_f32x2(w2, win2[(q + u) % P][0], acc2[2 * q]);
+              acc2[2 * q + 1] = fma_f32x2(w2, win2[(q + u) % P][1], acc2[2 * q + 1]);
+            }
+            const int pos = base + s0 + u + P;
+            const VT v = xs[pos + pos / P];
+            memcpy(win2[u], &v, sizeof v);
+          }
+        }
+      } else {
+        CT win[P][V];
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const int pos = base + q;
+          const VT v = xs[pos + pos / P];
+          memcpy(win[q], &v, sizeof v);
+        }
+        for (int s0 = 0; s0 < Lc; s0 += P) {
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            const CT w = wrow[s0 + u];
+#pragma unroll
+            for (int q = 0; q < P; ++q)
+#pragma unroll
+              for (int c = 0; c < V; ++c) acc[q][c] = fma(w, win[(q + u) % P][c], acc[q][c]);
+            const int pos = base + s0 + u + P;
+            const VT v = xs[pos + pos / P];
+            memcpy(win[u], &v, sizeof v);
+          }
         }
       }
     }
