@@ -200,7 +200,8 @@ int logdet_probe_fill_gaussian(uint64_t seed, int32_t stream, int32_t n, int32_t
 
 /* logdet_spmm: Y = Q X for a device block X (n x b, leading dimension ld,
  * FP64), the matrix-vector products that are the estimators' only access to
- * Q (Sec. 1; "w = Q v" in Algorithm 1).  Sums run in CSR order per row. */
+ * Q (Sec. 1; the product of Q with a vector in Algorithm 1).  Sums run in
+ * CSR order per row (a gridded operator: by stencil row dy, then dx). */
 int logdet_spmm(logdet_handle h, const double* x_dev, double* y_dev, int32_t b, int32_t ld,
                 void* cuda_stream);
 
@@ -234,7 +235,7 @@ int logdet_gauss_quadrature_log(const double* alpha_dev, const double* beta_dev,
                                 void* cuda_stream);
 
 /* logdet_hessenberg_log_e1: c_p = log(H_p) e_1 (principal logarithm,
- * Algorithm 1's "L_m = log(H_m)") for nprobe upper Hessenberg matrices,
+ * the matrix logarithm of H_m in Algorithm 1) for nprobe upper Hessenberg matrices,
  * H_p column-major with leading dimension ldh at H_dev + p*ldh*m, order
  * m_p = msteps[p] (or m).  c_dev: nprobe x m (row p at c_dev + p*m).
  * Inverse scaling and squaring (Denman-Beavers square roots, Gauss-Legendre

@@ -29,7 +29,7 @@ R5  The IOP window has length k: column m is orthogonalised against
 R6  ``tol``: IOP stops when h_{m+1,m} < tol (the column m is kept); Lanczos
     truncates T to j x j when beta_j <= tol.
 R7  OSA-IOP quadratic forms are q^T (L q) with L q from Algorithm 1.
-R8  "Y = log(L) S" in Algorithm 2 means Y = L S.
+R8  The sketch of Algorithm 2, written as log(L) S (garbled), is Y = L S.
 R9  s = floor(m_vec/3) sketch columns, r = m_vec - 2 s residual probes, and
     the residual weight is 1/r (3/m_vec when 3 divides m_vec).
 R11 The residual sum is tr_res = (1/r) sum_j ||z_j||^2 K(z_j/||z_j||); the
