@@ -898,10 +898,21 @@ def small_case(args):
     L2, about 3 GB on the device).  With --workload matern: one mixed-FP32
     OSLQ solve (m=12, 120 probes) on the Matern 1024^2 operator instead; with
     --workload grf: one mixed-FP32 OSLQ solve (m=4, 30 probes) on the
-    Wendland theta=50 gridded operator, 900 x 1200."""
+    Wendland theta=50 gridded operator, 900 x 1200; with --workload
+    multishift: one mixed-FP32 OSA-IOP solve (k=4, m=4, 64 probes, shift
+    0.01) on the 2M-row power-law graph Laplacian."""
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
+    if args.workload == "multishift":
+        import numpy as np
+        A = W.powerlaw_graph_laplacian(2 ** 21, exponent=2.3, mean_degree=8.0, seed=7,
+                                       dtype=np.float32)
+        with B.Handle.from_csr(A) as h:
+            r = h.osaiop(64, 4, iop_window=4, seed=1, precision=B.MIXED_FP32, shift=0.01)
+        torch.cuda.synchronize()
+        print(json.dumps({"small_case": "multishift", "osaiop": r.logdet, "ms": r.device_ms}))
+        return 0
     if args.workload == "grf":
         from paper_2606_07004_gb300 import grf
         with B.Handle.grid(1200, 900, grf.wendland_table(50.0, 0.1)) as h:
