@@ -713,22 +713,23 @@ def multishift_case(args):
     budget = int(min(args.budget_gb * (1 << 30), 8 * need * 1.05))
     with B.Server(budget, max_slots=8) as srv:
         srv.wait(srv.submit(h, B.METHOD_OSAIOP, P, 10, k, seed=0, precision=B.MIXED_FP32,
-                            shift=float(shifts[0])))
+                            shift=float(shifts[0]), autotune=args.autotune))
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ids = [srv.submit(h, B.METHOD_OSAIOP, P, m, k, seed=t, precision=B.MIXED_FP32,
-                          shift=float(sh)) for t, sh in enumerate(shifts)]
+                          shift=float(sh), autotune=args.autotune) for t, sh in enumerate(shifts)]
         batched = [srv.wait(i) for i in ids]
         t_batched = time.perf_counter() - t1
         st = srv.stats()
     t1 = time.perf_counter()
-    serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh))
-              for t, sh in enumerate(shifts)]
+    serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh),
+                       autotune=args.autotune) for t, sh in enumerate(shifts)]
     t_serial = time.perf_counter() - t1
     # Device time per kernel class of one of the solves run alone.
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
-    h.osaiop(P, m, iop_window=k, seed=0, precision=B.MIXED_FP32, shift=float(shifts[0]))
+    h.osaiop(P, m, iop_window=k, seed=0, precision=B.MIXED_FP32, shift=float(shifts[0]),
+             autotune=args.autotune)
     B.logdet_profile_enable(False)
     prof = B.profile_snapshot()
     h.close()
