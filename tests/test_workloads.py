@@ -114,3 +114,10 @@ def test_grf_sample_covariance():
     xp = np.stack([W.grf_sample(12, 10, T, seed=s) for s in range(4000)])
     centre = 5 * 12 + 6
     assert abs(xp[:, centre].var() / np.linalg.inv(A)[centre, centre] - 1.0) < 0.15
+
+
+def test_grf_client_table_matches_generator():
+    # the GRF client builds its own tables; they must equal the generator's
+    grf = pytest.importorskip("paper_2606_07004_gb300.grf")  # needs the built library
+    for theta, nug in ((3.0, 0.0), (20.0, 0.1), (7.5, 0.3)):
+        assert np.array_equal(grf.wendland_table(theta, nug), W.wendland_table(theta, nug))
