@@ -103,6 +103,11 @@ void logdet_server::complete(const std::shared_ptr<Request>& r, int state_, int 
   cv_done.notify_all();
 }
 
+// Kernel variant of a job (the template width it launches with).
+static int width_class(int k) { return k <= 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k <= 4 ? 4 : 9; }
+template <typename T> static int job_class(const SpmmJob<T>& j) { return width_class(j.ndots); }
+template <typename T> static int job_class(const UpdJob<T>& j) { return width_class(j.nbasis); }
+
 int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   // 1. non-Krylov phases, per request
   for (auto& r : act) {
@@ -115,7 +120,14 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     }
   }
   // 2. one batched Krylov step over every request in a Krylov phase, grouped
-  //    by element type and CTA size
+  //    by element type, CTA size and kernel variant (dots / basis vectors
+  //    class): a job never runs in a wider variant than its own, which would
+  //    cost registers and occupancy.  Group key: threads * 16 + class.
+  auto put = [&](auto& groups, auto& tmp, int th) {
+    if (tmp.empty()) return;
+    auto& dst = groups[th * 16 + job_class(tmp[0])];
+    dst.insert(dst.end(), tmp.begin(), tmp.end());
+  };
   std::map<int, std::vector<SpmmJob<double>>> sd;
   std::map<int, std::vector<SpmmJob<float>>> sf;
   std::map<int, std::vector<SpmmJob<bf16>>> sb;
@@ -130,8 +142,20 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     if (!sv || !sv->in_krylov() || r->rc) continue;
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
-    int rc = ek == 0 ? sv->add_pass1(&sd[th], coef, wc)
-                     : ek == 1 ? sv->add_pass1(&sf[th], coef, wc) : sv->add_pass1(&sb[th], coef, wc);
+    int rc;
+    if (ek == 0) {
+      std::vector<SpmmJob<double>> tmp;
+      rc = sv->add_pass1(&tmp, coef, wc);
+      if (!rc) put(sd, tmp, th);
+    } else if (ek == 1) {
+      std::vector<SpmmJob<float>> tmp;
+      rc = sv->add_pass1(&tmp, coef, wc);
+      if (!rc) put(sf, tmp, th);
+    } else {
+      std::vector<SpmmJob<bf16>> tmp;
+      rc = sv->add_pass1(&tmp, coef, wc);
+      if (!rc) put(sb, tmp, th);
+    }
     if (rc) {
       r->rc = rc;  // this request fails; the others step on
       continue;
@@ -139,20 +163,30 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     stepping.push_back(sv);
   }
   if (stepping.empty()) return 0;
-  for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first, st));
-  for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first, st));
-  for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first, st));
+  for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first / 16, st));
+  for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first / 16, st));
+  for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first / 16, st));
   LD_TRY(launch_scalar_jobs(coef, wc, SK_COEF, st));
   for (ISolve* sv : stepping) {
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
-    if (ek == 0) sv->add_pass2(&ud[th], norm, wn);
-    else if (ek == 1) sv->add_pass2(&uf[th], norm, wn);
-    else sv->add_pass2(&ub[th], norm, wn);
+    if (ek == 0) {
+      std::vector<UpdJob<double>> tmp;
+      sv->add_pass2(&tmp, norm, wn);
+      put(ud, tmp, th);
+    } else if (ek == 1) {
+      std::vector<UpdJob<float>> tmp;
+      sv->add_pass2(&tmp, norm, wn);
+      put(uf, tmp, th);
+    } else {
+      std::vector<UpdJob<bf16>> tmp;
+      sv->add_pass2(&tmp, norm, wn);
+      put(ub, tmp, th);
+    }
   }
-  for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first, st));
-  for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first, st));
-  for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first, st));
+  for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first / 16, st));
+  for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first / 16, st));
+  for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first / 16, st));
   if (!norm.empty()) LD_TRY(launch_scalar_jobs(norm, wn, SK_NORM, st));
   for (ISolve* sv : stepping) sv->step_issued();
   n_batched_steps += (int64_t)stepping.size();
