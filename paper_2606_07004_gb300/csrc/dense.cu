@@ -151,26 +151,46 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ C, 
   for (int i = threadIdx.x; i < s; i += blockDim.x) keep_out[i] = keep[i];
 }
 
-// A[row, l] = sum_{i <= l} Y[row, i] Rinv[i, l]; A may alias Y.
-__global__ void __launch_bounds__(256) k_apply_rinv(const double* Y, int ldy, int n, int s,
+// A[row, l] = sum_{i <= l} Y[row, i] Rinv[i, l]; A may alias Y.  A chunk of
+// 32 rows is staged in shared memory (row stride odd, so the lanes' 8-byte
+// reads of one column spread over the banks); warp w computes output columns
+// [4w, 4w + 4) of all 32 rows, lane = row, so every lane of a warp runs the
+// same triangular loop (i <= 4w + 3; the extra terms multiply zeros of the
+// upper-triangular Rinv and change nothing).  Dynamic shared memory:
+// s * s + 32 * (s | 1) doubles.
+constexpr int kApplyCols = 4;
+__global__ void __launch_bounds__(512) k_apply_rinv(const double* Y, int ldy, int n, int s,
                                                     const double* __restrict__ Rinv, double* A,
                                                     int lda) {
-  __shared__ double sr[kMaxSketch * kMaxSketch];
-  __shared__ double sy[kGramChunk * kMaxSketch];
+  extern __shared__ double smem_ar[];
+  const int S1 = s | 1;
+  double* sr = smem_ar;
+  double* sy = smem_ar + s * s;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) sr[e] = Rinv[e];
-  for (int c0 = blockIdx.x * kGramChunk; c0 < n; c0 += gridDim.x * kGramChunk) {
-    const int rows = min(kGramChunk, n - c0);
+  const int lane = threadIdx.x & 31;
+  const int l0 = (threadIdx.x >> 5) * kApplyCols;
+  for (int c0 = blockIdx.x * 32; c0 < n; c0 += gridDim.x * 32) {
+    const int rows = min(32, n - c0);
     __syncthreads();
     for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
-      int r = e / s, i = e - r * s;
-      sy[r * s + i] = Y[(size_t)(c0 + r) * ldy + i];
+      const int r = e / s, i = e - r * s;
+      sy[r * S1 + i] = Y[(size_t)(c0 + r) * ldy + i];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
-      int r = e / s, l = e - r * s;
-      double v = 0.0;
-      for (int i = 0; i <= l; ++i) v = fma(sy[r * s + i], sr[i * s + l], v);
-      A[(size_t)(c0 + r) * lda + l] = v;
+    if (lane < rows && l0 < s) {
+      double acc[kApplyCols];
+#pragma unroll
+      for (int q = 0; q < kApplyCols; ++q) acc[q] = 0.0;
+      const int lmax = min(l0 + kApplyCols, s);
+      for (int i = 0; i < lmax; ++i) {
+        const double y = sy[lane * S1 + i];
+#pragma unroll
+        for (int q = 0; q < kApplyCols; ++q)
+          if (l0 + q < s) acc[q] = fma(y, sr[i * s + l0 + q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kApplyCols; ++q)
+        if (l0 + q < s) A[(size_t)(c0 + lane) * lda + l0 + q] = acc[q];
     }
   }
 }
@@ -202,19 +222,28 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
   }
   const double* src = Y;
   int ldsrc = ldy;
+  // Gram: one thread per (i <= j) pair while they fit in one CTA, so few
+  // lanes idle.  Apply: one warp per 4 output columns.
+  const int gram_threads = npairs <= kGramThreads ? (npairs + 31) / 32 * 32 : kGramThreads;
+  const int apply_threads = 32 * div_up(s, kApplyCols);
+  const size_t apply_smem = sizeof(double) * ((size_t)s * s + 32 * (size_t)(s | 1));
+  if (apply_smem > 48 * 1024)
+    LD_CUDA(cudaFuncSetAttribute(k_apply_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)apply_smem));
   for (int round = 0; round < 2; ++round) {
     ProfScope prof(KC_QR, st, 2.0 * n * (double)s * s * 2.0, 2.0 * 8.0 * n * s);
     prof_count();
     prof_count();
     prof_count();
-    k_gram<<<grid_for(ntiles), kGramThreads, 0, st>>>(src, ldsrc, n, s, ntiles, part);
+    k_gram<<<grid_for(ntiles), gram_threads, 0, st>>>(src, ldsrc, n, s, ntiles, part);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<npairs, 128, 0, st>>>(part, ntiles, s, C);
     LD_CHECK_LAUNCH();
     // R14: |R_ii| <= 1e-6 max_j |y_j|  <=>  R_ii^2 <= 1e-12 max_j C_jj.
     k_chol_inv<<<1, 256, 0, st>>>(C, s, 1e-12, Rinv, keep);
     LD_CHECK_LAUNCH();
-    k_apply_rinv<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(src, ldsrc, n, s, Rinv, A, lda);
+    k_apply_rinv<<<grid_for(div_up(n, 32)), apply_threads, apply_smem, st>>>(src, ldsrc, n, s,
+                                                                             Rinv, A, lda);
     LD_CHECK_LAUNCH();
     src = A;
     ldsrc = lda;
@@ -338,8 +367,11 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
   if (s > 0) {
     prof_count();
     prof_count();
-    k_atg<<<grid_for(ntiles), kGramThreads, 0, st>>>(A, lda, n, s, r, key, keyp, ntiles, part,
-                                                     gaussian);
+    // As few threads as keep the per-thread pair count at its minimum.
+    const int np = s * r, per = div_up(np, kGramThreads);
+    const int atg_threads = std::min(kGramThreads, div_up(div_up(np, per), 32) * 32);
+    k_atg<<<grid_for(ntiles), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp, ntiles, part,
+                                                    gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
