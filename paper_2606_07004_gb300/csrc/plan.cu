@@ -130,6 +130,7 @@ int logdet_plan_create(logdet_handle h, int32_t method, int32_t num_probes, int3
 int logdet_plan_run(logdet_plan p, uint64_t seed, logdet_result* out, double* per_probe,
                     double* z_norm2) {
   if (!p || !out) { set_error("plan_run: NULL plan or result"); return LOGDET_EINVAL; }
+  NvtxRange nv("logdet plan run");
   if (cudaSetDevice(p->h->device) != cudaSuccess) { set_error("cudaSetDevice failed"); return LOGDET_ECUDA; }
   p->h_keys[0] = probe_key(seed, 0);
   p->h_keys[1] = probe_key(seed, 1);

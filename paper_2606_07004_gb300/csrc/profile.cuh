@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace ld {
 
@@ -35,6 +36,15 @@ struct ProfScope {
   ProfScope(KClass c_, cudaStream_t s_, double f = 0, double b = 0)
       : tok(prof_begin(s_)), c(c_), s(s_), flops(f), bytes(b) { prof_count(); }
   ~ProfScope() { prof_end(tok, c, s, flops, bytes); }
+};
+
+// NVTX range around host-side issue work (solve phases, Krylov steps, server
+// ticks, plan replays): visible in Nsight timelines, free without a tool.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 }  // namespace ld

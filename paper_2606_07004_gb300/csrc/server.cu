@@ -13,6 +13,7 @@
 // through the blocking logdet_oslq / logdet_osaiop calls.
 #include "handle.cuh"
 #include "solve.cuh"
+#include "profile.cuh"
 
 #include <chrono>
 #include <condition_variable>
@@ -109,6 +110,7 @@ template <typename T> static int job_class(const SpmmJob<T>& j) { return width_c
 template <typename T> static int job_class(const UpdJob<T>& j) { return width_class(j.nbasis); }
 
 int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
+  NvtxRange nv("logdet server tick");
   // 1. non-Krylov phases, per request
   for (auto& r : act) {
     ISolve* sv = r->solve.get();

@@ -708,6 +708,7 @@ struct Solve : ISolve {
   }
 
   int run_phase() override {
+    NvtxRange nv(ph == PH_SETUP ? "logdet setup" : ph == PH_MID ? "logdet mid" : "logdet finish");
     int rc = LOGDET_OK;
     if (ph == PH_SETUP) rc = setup();
     else if (ph == PH_MID) rc = mid();
@@ -885,6 +886,7 @@ int issue_solve(ISolve* sv, cudaStream_t st) {
       if (rc) return rc;
       continue;
     }
+    NvtxRange nv("logdet krylov step");
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
     sd.clear(); sf.clear(); sb.clear(); ud.clear(); uf.clear(); ub.clear(); sj.clear(); widths.clear();
