@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,6 +15,21 @@
 #include "../../include/logdet.h"
 
 namespace ld {
+
+// Diagonal structure of a CSR matrix whose entries lie on few diagonals
+// (stencil operators): sorted offsets col - row, and the offsets grouped into
+// bands that one staged block of x rows serves (see dia.cu).
+constexpr int kMaxDiags = 16;
+struct DiaInfo {
+  int ndiag;                  // 0: not diagonal-structured
+  int off[kMaxDiags];         // ascending
+  int nbands;
+  int band_lo[kMaxDiags];     // lowest offset of each band
+  int maxext;                 // largest band extent (hi - lo)
+  int diag_band[kMaxDiags];   // band of each diagonal
+  int diag_shift[kMaxDiags];  // offset - band_lo
+};
+
 
 // ---------------------------------------------------------------------------
 // Errors.  Every host function returns an int code; the detail text of the

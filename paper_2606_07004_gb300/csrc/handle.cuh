@@ -30,6 +30,9 @@ struct logdet_ctx {
   int gx = 0, gy = 0, gr = 0;    // grid size and stencil radius
   double* gtab = nullptr;        // device expanded table of W (FP64)
   int* grx = nullptr;            // device [gr + 1]: last nonzero |dx| per |dy|
+  // Diagonal structure (dia.ndiag > 0): CSR entry -> diagonal index.
+  ld::DiaInfo dia{};
+  int* dia_slot = nullptr;       // device [nnz]
 };
 
 namespace ld {

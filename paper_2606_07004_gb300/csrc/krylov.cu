@@ -46,12 +46,6 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
   return g;
 }
 
-template <typename Batch>
-__device__ __forceinline__ int find_job(const Batch& B, int gt) {
-  int j = 0;
-  while (j + 1 < B.njobs && gt >= B.tile_start[j + 1]) ++j;
-  return j;
-}
 
 // ---------------------------------------------------------------------------
 // pass 1: y = A x (CSR order per row) and d_i += dotv_i . y

@@ -55,6 +55,16 @@ struct SpmmJob {
   int col_off, width;              // columns [col_off, col_off+width) of the block (width % vec == 0)
   int b;                           // live columns in this slice (accounting only)
   long long nnz;                   // (accounting only)
+  // Diagonal fast path (FP32 blocks, see dia.cu): values per diagonal
+  // [ndiag][n] (dia == nullptr: CSR path), the tensor map of x (box: width
+  // columns x (dia_T + band extent) rows), the matrix's diagonal structure,
+  // and a flag set if a bounded wait gives up.  Tiles, partial slots and the
+  // per-thread row order are those of the CSR path.
+  const float* dia;
+  int* err;
+  int dia_T;                       // rows per staged sub-tile (a multiple of the row groups)
+  DiaInfo dinfo;
+  CUtensorMap tmap;
 };
 
 template <typename T>
@@ -159,6 +169,14 @@ int launch_norm(const ScalarBatch& b, cudaStream_t s);
 int launch_init_sigma(const ScalarBatch& b, cudaStream_t s);
 
 int sm_count();
+
+// Job of global tile gt in a batch (tile_start ascending).
+template <typename Batch>
+__device__ __forceinline__ int find_job(const Batch& B, int gt) {
+  int j = 0;
+  while (j + 1 < B.njobs && gt >= B.tile_start[j + 1]) ++j;
+  return j;
+}
 
 // Reduce the per-thread accumulators of all rows of the CTA for one dot and
 // write one partial per column.  smem holds blockDim.x * V accumulators.

@@ -1,6 +1,7 @@
 // Matrix handles: CSR upload and validation, Gershgorin interval (Sec. 2.1),
 // scaled value copies, error plumbing and the step-level SpMM entry point.
 #include "handle.cuh"
+#include "dia.cuh"
 #include "krylov.cuh"
 #include "profile.cuh"
 
@@ -258,6 +259,7 @@ int create_handle(int32_t n, const int32_t* rowptr, const int32_t* colind, const
       return fail(LOGDET_ECUDA);
     }
     rc = compute_gershgorin(h, false);
+    if (!rc) rc = dia_build(h, rowptr, colind);
   } else {
     int last = 0;
     if (cudaMemcpy(&last, rowptr + n, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -366,6 +368,7 @@ void destroy_handle(logdet_ctx* h) {
   for (auto& kv : h->items) cudaFree(kv.second.first);
   if (h->gtab) cudaFree(h->gtab);
   if (h->grx) cudaFree(h->grx);
+  if (h->dia_slot) cudaFree(h->dia_slot);
   if (h->owns) {
     if (h->rowptr) cudaFree(h->rowptr);
     if (h->colind) cudaFree(h->colind);

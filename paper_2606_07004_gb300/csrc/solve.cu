@@ -2,6 +2,7 @@
 #include "profile.cuh"
 #include "solve.cuh"
 #include "grid.cuh"
+#include "dia.cuh"
 #include "tune.cuh"
 
 #include <cmath>
@@ -157,6 +158,10 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
   ndmax = std::max(win, 2);
   nring = win + 1;
   LD_TRY(part.alloc((size_t)ndmax * ld * std::max(ntiles, nslots)));
+  if (diavals) {
+    LD_TRY(dia_err.alloc(1));
+    LD_TRY(dia_err.zero());
+  }
   LD_TRY(y.alloc(blk));
   if (!Vfull) LD_TRY(ring.alloc(blk * nring));
   LD_TRY(ks.alloc(method, b, ld, m, k, tol, rescale_limit<T>()));
@@ -211,6 +216,22 @@ void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
       const int lo = win_lo(j);
       J.ndots = j - lo + 1;
       for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      // Diagonal fast path: same tiles and row order, x staged by TMA.
+      const int T0 = (diavals && !items && hctx) ? dia_tile_rows(hctx, width) : 0;
+      if (T0 > 0) {
+        const int R = g.threads / (width / Vec16<T>::N);
+        const int Ts = std::max(R, T0 / R * R);
+        if (R > 0 && Ts + hctx->dia.maxext <= 256) {
+          J.dia = diavals;
+          J.dia_T = Ts;
+          J.dinfo = hctx->dia;
+          J.err = dia_err.p;
+          if (dia_encode_x(J, ptr(j), n, ld, width, Ts + hctx->dia.maxext) != LOGDET_OK)
+            J.dia = nullptr;  // not encodable: the CSR path
+        }
+      }
     }
     out.push_back(J);
   }
@@ -295,6 +316,20 @@ template struct KRun<bf16>;
 // ---------------------------------------------------------------------------
 template <typename T>
 int launch_spmm_jobs(const std::vector<SpmmJob<T>>& jobs, int threads, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    // Diagonal-path jobs launch apart from CSR jobs (same stream, in order).
+    bool any = false, all = true;
+    for (const auto& J : jobs) {
+      any |= J.dia != nullptr;
+      all &= J.dia != nullptr;
+    }
+    if (any && !all) {
+      std::vector<SpmmJob<T>> a, c;
+      for (const auto& J : jobs) (J.dia ? a : c).push_back(J);
+      LD_TRY(launch_spmm_jobs<T>(c, threads, s));
+      return launch_spmm_jobs<T>(a, threads, s);
+    }
+  }
   for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxJobs) {
     SpmmBatch<T> B;
     memset(&B, 0, sizeof B);
@@ -308,6 +343,12 @@ int launch_spmm_jobs(const std::vector<SpmmJob<T>>& jobs, int threads, cudaStrea
     B.njobs = nj;
     B.tile_start[nj] = t;
     B.total_tiles = t;
+    if constexpr (std::is_same<T, float>::value) {
+      if (B.jobs[0].dia) {
+        LD_TRY(launch_spmm_dia(B, threads, s));
+        continue;
+      }
+    }
     LD_TRY(launch_spmm<T>(B, threads, s));
   }
   return LOGDET_OK;
@@ -444,6 +485,7 @@ struct Solve : ISolve {
   double lo, hi, alpha, gamma, shift;
   DevBuf<typename ValOf<T>::type> vals;
   DevBuf<typename Compute<T>::type> gtabs;  // gridded operator: scaled table
+  DevBuf<float> diav;                        // FP32 values per diagonal (diagonal fast path)
   DevBuf<T> Vst, Xc;
   DevBuf<double> X64, outv, cshift;
   DevBuf<int> keep;
@@ -452,11 +494,12 @@ struct Solve : ISolve {
   double *h_out = nullptr, *h_edot = nullptr;
   int *h_meff = nullptr, *h_keep = nullptr;
   uint32_t *h_status = nullptr, *h_status1 = nullptr;
+  int* h_err = nullptr;  // [2]: a diagonal-path wait gave up (phase 1, last run)
   cudaEvent_t ev_done = nullptr;
   const uint64_t* dev_keys = nullptr;  // graph plans: probe keys in device memory
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
-      : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
+      : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), diav(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
         keep(st_) {
     n = h->n;
     s = c.plain ? 0 : c.P / 3;
@@ -486,7 +529,7 @@ struct Solve : ISolve {
     if (pin.p) return LOGDET_OK;
     const size_t bytes = sizeof(double) * ld + sizeof(double) * (size_t)ld * (m + 2) +
                          sizeof(int) * ld + sizeof(int) * (s + 1) + sizeof(uint32_t) * ld +
-                         sizeof(uint32_t) * lds + 64;
+                         sizeof(uint32_t) * lds + 2 * sizeof(int) + 64;
     pin.st = st;
     pin.p = pinned_acquire(bytes, &pin.cap);
     if (!pin.p) {
@@ -506,6 +549,8 @@ struct Solve : ISolve {
     h_status = reinterpret_cast<uint32_t*>(q);
     q += sizeof(uint32_t) * ld;
     h_status1 = reinterpret_cast<uint32_t*>(q);
+    q += sizeof(uint32_t) * lds;
+    h_err = reinterpret_cast<int*>(q);
     return LOGDET_OK;
   }
 
@@ -551,6 +596,10 @@ struct Solve : ISolve {
     } else {
       LD_TRY(vals.alloc(h->nnz));
       LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
+      if (std::is_same<T, float>::value && h->dia.ndiag > 0 && h->dia_slot) {
+        LD_TRY(diav.alloc((size_t)h->dia.ndiag * n));
+        LD_TRY(dia_values_f32(h, cscale, diav.p, st));
+      }
     }
     if (c.shift != 0.0) {
       // (Q + shift I)/c applied as vals/c plus (shift/c) times the row's own entry.
@@ -568,6 +617,7 @@ struct Solve : ISolve {
       run->colshift = cshift.p;
       run->hctx = h;
       run->gtab = gtabs.p;
+      run->diavals = diav.p;
       TuneCfg tc;
       LD_TRY(layout(ld, c.method == 1, &tc));
       if (c.method == 0) {
@@ -610,6 +660,7 @@ struct Solve : ISolve {
       run->colshift = cshift.p;
       run->hctx = h;
       run->gtab = gtabs.p;
+      run->diavals = diav.p;
       TuneCfg tc;
       LD_TRY(layout(ld, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
@@ -621,6 +672,7 @@ struct Solve : ISolve {
       run->colshift = cshift.p;
       run->hctx = h;
       run->gtab = gtabs.p;
+      run->diavals = diav.p;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
       LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
@@ -648,6 +700,8 @@ struct Solve : ISolve {
     LD_TRY(Y64.alloc((size_t)n * lds));
     LD_TRY(sketch_assemble<T>(Vst.p, n, lds, m, w.p, Y64.p, lds, st));
     LD_CUDA(cudaMemcpyAsync(h_status1, r1.ks.status.p, sizeof(uint32_t) * lds, cudaMemcpyDeviceToHost, st));
+    if (r1.dia_err.p)
+      LD_CUDA(cudaMemcpyAsync(h_err, r1.dia_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     run.reset();
     Vst.release();
     cc.release();
@@ -662,6 +716,7 @@ struct Solve : ISolve {
     run->colshift = cshift.p;
     run->hctx = h;
     run->gtab = gtabs.p;
+    run->diavals = diav.p;
     TuneCfg tc;
     LD_TRY(layout(ld, true, &tc));
     LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
@@ -690,6 +745,8 @@ struct Solve : ISolve {
     LD_CUDA(cudaMemcpyAsync(h_out, outv.p, sizeof(double) * ld, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_meff, rr.ks.meff.p, sizeof(int) * ld, cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_status, rr.ks.status.p, sizeof(uint32_t) * ld, cudaMemcpyDeviceToHost, st));
+    if (rr.dia_err.p)
+      LD_CUDA(cudaMemcpyAsync(h_err + 1, rr.dia_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LD_CUDA(cudaMemcpyAsync(h_edot, rr.ks.edot.p, sizeof(double) * ld * (m + 2), cudaMemcpyDeviceToHost, st));
     if (s > 0) LD_CUDA(cudaMemcpyAsync(h_keep, keep.p, sizeof(int) * s, cudaMemcpyDeviceToHost, st));
     if (!ev_done) LD_CUDA(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
@@ -698,6 +755,7 @@ struct Solve : ISolve {
     run.reset();
     vals.release();
     gtabs.release();
+    diav.release();
     cshift.release();
     X64.release();
     Xc.release();
@@ -744,6 +802,10 @@ struct Solve : ISolve {
 
   int assemble(SolveOut& o) override {
     memset(&o.res, 0, sizeof o.res);
+    if (h_err && (h_err[0] || h_err[1])) {
+      set_error("a staged copy of the diagonal SpMM path did not complete in time");
+      return LOGDET_ETIMEOUT;
+    }
     uint32_t status = 0;
     int s_eff = 0;
     for (int i = 0; i < s; ++i) s_eff += h_keep[i] != 0;

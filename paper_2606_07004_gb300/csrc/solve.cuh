@@ -95,10 +95,12 @@ struct KRun {
   DevBuf<Part> part;
   DevBuf<T> y, ring;
   KState ks;
+  const float* diavals = nullptr;  // FP32 values per diagonal: the diagonal fast path
+  DevBuf<int> dia_err;             // set if a staged copy's wait gave up
   int done_steps = 0;  // steps whose pass 1 has been issued
   cudaStream_t st;
 
-  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), st(s) {}
+  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), dia_err(s), st(s) {}
 
   // Allocate and queue the start-block norms and sigma_1 (one launch pair).
   int init(const int* rp, const int* ci, const typename ValOf<T>::type* v, int n_, long long nnz_,
