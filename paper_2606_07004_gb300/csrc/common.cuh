@@ -16,18 +16,19 @@
 
 namespace ld {
 
-// Diagonal structure of a CSR matrix whose entries lie on few diagonals
-// (stencil operators): sorted offsets col - row, and the offsets grouped into
-// bands that one staged block of x rows serves (see dia.cu).
+// Line structure of a stencil matrix: every entry lies on one of a few
+// diagonals, and each diagonal offset is line * L + c with a line stride L,
+// lines in [-A, A] and small c (a 2D grid stencil: L = the grid's row
+// length).  See dia.cu.
 constexpr int kMaxDiags = 16;
 struct DiaInfo {
-  int ndiag;                  // 0: not diagonal-structured
+  int ndiag;                  // 0: no such structure
   int off[kMaxDiags];         // ascending
-  int nbands;
-  int band_lo[kMaxDiags];     // lowest offset of each band
-  int maxext;                 // largest band extent (hi - lo)
-  int diag_band[kMaxDiags];   // band of each diagonal
-  int diag_shift[kMaxDiags];  // offset - band_lo
+  int L;                      // line stride
+  int A;                      // lines -A .. A
+  int cmin, cw;               // c ranges over [cmin, cmin + cw]
+  int line[kMaxDiags];        // line of each diagonal
+  int cpos[kMaxDiags];        // c - cmin of each diagonal
 };
 
 

@@ -1,20 +1,31 @@
-// Diagonal fast path of the SpMM pass for FP32 blocks.
+// Line-sweep path of the SpMM pass for FP32 blocks of stencil matrices.
 //
-// Stencil operators (the Laplacians, the Matérn operator) keep every entry on
-// a few diagonals.  Instead of gathering x rows through the column indices
-// (one dependent round trip per batch of nonzeros), a CTA stages, for a tile
-// of T output rows, one block of x rows per band of nearby diagonals with a
-// TMA 2D copy (cp.async.bulk.tensor, completion on an mbarrier), and reads
-// every neighbour from shared memory.  Rows outside the matrix are filled
-// with zeros by the copy; the values per diagonal are 0 where a row has no
-// entry.  Each row sums over the diagonals in ascending offset order, which
-// is the CSR column order of the CSR path, so y is the same FP32 sum.
+// A 2D grid stencil (the 2D Laplacians, the Matérn operator (kappa^2 I + L)^2)
+// keeps every entry on a few diagonals whose offsets are line * L + c, with L
+// the grid's row length, |line| <= A and c in a short range [cmin, cmin + cw].
+// Output row i needs x rows from the lines i/L - A .. i/L + A.  A CTA owns a
+// segment of T consecutive rows within a line and sweeps it over kc
+// consecutive lines (a "unit").  It keeps the 2A + 1 line windows the current
+// line needs (T + cw rows of x each) in a ring of shared-memory slots; moving
+// to the next line needs one new window, which a TMA 2D copy
+// (cp.async.bulk.tensor, completion on the slot's mbarrier) brings in, with
+// the values of the new line, two lines ahead of the computation.  So each x
+// row crosses from L2 to the SM about (T + cw) / T times per pass instead of
+// once per diagonal line.
+//
+// Rows outside the matrix are filled with zeros by the copy; the value of a
+// diagonal is 0 where a row has no entry.  Each row sums over the diagonals
+// in ascending offset order, the CSR column order, so y is the same FP32 sum
+// as on the CSR path; the window dots are accumulated per unit (the unit is
+// the partial slot), so they differ from the CSR path's only by the order of
+// their compensated partial sums.
 #include "dia.cuh"
 #include "profile.cuh"
 
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -24,6 +35,13 @@ namespace ld {
 // ---------------------------------------------------------------------------
 // Structure
 // ---------------------------------------------------------------------------
+// Nearest line of offset o for stride L (ties toward zero).
+static int nearest_line(int o, int L) {
+  const int a = o >= 0 ? o : -o;
+  const int l = (a + (L - 1) / 2) / L;
+  return o >= 0 ? l : -l;
+}
+
 int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
   memset(&h->dia, 0, sizeof h->dia);
   const int n = h->n;
@@ -34,31 +52,52 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
       const int o = colind[q] - i;
       if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
         offs.push_back(o);
-        if ((int)offs.size() > kMaxDiags) return LOGDET_OK;  // not diagonal-structured
+        if ((int)offs.size() > kMaxDiags) return LOGDET_OK;  // not a stencil
       }
     }
   }
   std::sort(offs.begin(), offs.end());
-  DiaInfo d;
-  memset(&d, 0, sizeof d);
-  d.ndiag = (int)offs.size();
-  for (int k = 0; k < d.ndiag; ++k) d.off[k] = offs[k];
-  int lo = offs[0], prev = offs[0];
-  d.band_lo[0] = lo;
-  int nb = 0;
-  for (int k = 0; k < d.ndiag; ++k) {
-    if (k > 0 && offs[k] - prev > kDiaBandGap) {
-      d.maxext = std::max(d.maxext, prev - lo);
-      lo = offs[k];
-      d.band_lo[++nb] = lo;
+  const int nd = (int)offs.size();
+  // Line stride: the candidate (an offset's magnitude) with the smallest ring
+  // (2A + 1 windows of a nominal 32 + cw rows); among equal rings the one
+  // with the smallest sum of |c| (the grid's own row length, not a
+  // neighbouring diagonal's offset).
+  DiaInfo best;
+  memset(&best, 0, sizeof best);
+  long long best_cost = LLONG_MAX, best_sc = LLONG_MAX;
+  for (int k = 0; k < nd; ++k) {
+    const int L = offs[k] >= 0 ? offs[k] : -offs[k];
+    if (L < kSweepMinL) continue;
+    DiaInfo d;
+    memset(&d, 0, sizeof d);
+    d.ndiag = nd;
+    d.L = L;
+    int cmin = INT_MAX, cmax = INT_MIN;
+    for (int q = 0; q < nd; ++q) {
+      d.off[q] = offs[q];
+      d.line[q] = nearest_line(offs[q], L);
+      const int c = offs[q] - d.line[q] * L;
+      d.A = std::max(d.A, d.line[q] >= 0 ? d.line[q] : -d.line[q]);
+      cmin = std::min(cmin, c);
+      cmax = std::max(cmax, c);
     }
-    d.diag_band[k] = nb;
-    d.diag_shift[k] = offs[k] - lo;
-    prev = offs[k];
+    d.cmin = cmin;
+    d.cw = cmax - cmin;
+    if (d.A > kSweepMaxA || d.cw > kSweepMaxCw) continue;
+    long long sc = 0;
+    for (int q = 0; q < nd; ++q) {
+      const int c = offs[q] - d.line[q] * L;
+      d.cpos[q] = c - cmin;
+      sc += c >= 0 ? c : -c;
+    }
+    const long long cost = (long long)(2 * d.A + 1) * (32 + d.cw);
+    if (cost < best_cost || (cost == best_cost && sc < best_sc)) {
+      best_cost = cost;
+      best_sc = sc;
+      best = d;
+    }
   }
-  d.maxext = std::max(d.maxext, prev - lo);
-  d.nbands = nb + 1;
-  if (d.maxext > kDiaMaxExt) return LOGDET_OK;
+  if (best.ndiag == 0) return LOGDET_OK;
   // CSR entry -> diagonal index.
   std::vector<int> slot((size_t)h->nnz);
   for (int i = 0; i < n; ++i)
@@ -74,44 +113,79 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
     set_error("copy of the diagonal map failed");
     return LOGDET_ECUDA;
   }
-  h->dia = d;
+  h->dia = best;
   return LOGDET_OK;
 }
 
 template <typename V>
 __global__ void k_dia_values(const int* __restrict__ rowptr, const int* __restrict__ slot,
-                             const V* __restrict__ vals, int n, double c, float* __restrict__ out) {
+                             const V* __restrict__ vals, int n, int dp, double c,
+                             float* __restrict__ out) {
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x)
     for (int q = rowptr[row]; q < rowptr[row + 1]; ++q)
-      out[(size_t)slot[q] * n + row] = (float)((double)vals[q] / c);
+      out[(size_t)row * dp + slot[q]] = (float)((double)vals[q] / c);
 }
 
 int dia_values_f32(const logdet_ctx* h, double c, float* out, cudaStream_t st) {
   const int n = h->n;
-  LD_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)h->dia.ndiag * n, st));
+  const int dp = dia_pad(h->dia.ndiag);
+  LD_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)dp * n, st));
   ProfScope prof(KC_OTHER, st);
   const int blocks = std::max(1, std::min(div_up(n, 256), 8 * sm_count()));
   if (h->vals_dtype == LOGDET_VALS_F64)
     k_dia_values<double><<<blocks, 256, 0, st>>>(h->rowptr, h->dia_slot, (const double*)h->vals,
-                                                 n, c, out);
+                                                 n, dp, c, out);
   else
     k_dia_values<float><<<blocks, 256, 0, st>>>(h->rowptr, h->dia_slot, (const float*)h->vals, n,
-                                                c, out);
+                                                dp, c, out);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
 
-// T rows per tile: the staged bands (nbands x (T + maxext) rows x width
-// floats) kept near kDiaSmemTarget, T a multiple of kDiaRows in [8, 128].
-int dia_tile_rows(const logdet_ctx* h, int width) {
+// Floats of one ring slot: the x window (T + cw rows of width floats), then
+// the values of T rows; each part rounded up to 128 bytes (TMA destinations).
+__host__ __device__ inline int sweep_win_floats(int T, int cw, int width) {
+  return ((T + cw) * width + 31) / 32 * 32;
+}
+static int sweep_slot_floats(const DiaInfo& d, int T, int width) {
+  return sweep_win_floats(T, d.cw, width) + (T * dia_pad(d.ndiag) + 31) / 32 * 32;
+}
+// Shared memory of a CTA: barriers, the window-offset table (nr rotations x
+// kMaxDiags), the dot reduction (threads x 4 accumulators), the ring.
+static size_t sweep_smem_bytes(int nr, int slot_floats, int threads) {
+  const size_t tab = ((size_t)nr * kMaxDiags * 4 + 127) / 128 * 128;
+  const size_t red = ((size_t)threads * 4 * sizeof(AccF) + 127) / 128 * 128;
+  return 128 + tab + red + (size_t)nr * slot_floats * sizeof(float);
+}
+
+bool dia_sweep_geom(const logdet_ctx* h, int width, int threads, SweepGeom* out) {
   const DiaInfo& d = h->dia;
-  if (d.ndiag == 0 || !h->dia_slot || width % 4 || width > 256 || width < 4) return 0;
-  const int row_bytes = width * 4;
-  int T = kDiaSmemTarget / (d.nbands * row_bytes) - d.maxext;
-  T = T / kDiaRows * kDiaRows;
-  T = std::max(kDiaRows, std::min(T, 128));
-  if (T + d.maxext > 256) T = (256 - d.maxext) / kDiaRows * kDiaRows;
-  return T;
+  if (d.ndiag == 0 || !h->dia_slot || width % 4 || width < 4 || width > 256) return false;
+  const int G = width / 4;
+  const int R = threads / G;
+  if (R < 1 || threads > 512) return false;
+  const int nr = 2 * d.A + 1 + kSweepPrefetch;
+  int T = 0;
+  for (int m = 1;; ++m) {
+    const int t = R * m;
+    if (t + d.cw > 256 || (m > 1 && t > d.L)) break;
+    if (sweep_smem_bytes(nr, sweep_slot_floats(d, t, width), threads) > (size_t)kSweepSmemBudget)
+      break;
+    T = t;
+  }
+  if (T == 0) return false;
+  SweepGeom g;
+  g.T = T;
+  g.nseg = (d.L + T - 1) / T;
+  g.nlines = (h->n + d.L - 1) / d.L;
+  // About eight units per SM; at least 4A lines per unit (each unit first
+  // loads 2A windows that only fill the ring).
+  const int chunks = std::max(1, 8 * sm_count() / g.nseg);
+  g.kc = (g.nlines + chunks - 1) / chunks;
+  g.kc = std::min(g.nlines, std::max(g.kc, 4 * d.A));
+  g.units = g.nseg * ((g.nlines + g.kc - 1) / g.kc);
+  *out = g;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -122,7 +196,24 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 }  // namespace
 
-int dia_encode_x(SpmmJob<float>& J, const float* x, int n, int ld, int width, int box_rows) {
+static int encode_2d(CUtensorMap* map, const float* base, int inner, int outer, int pitch,
+                     int box_inner, int box_outer) {
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LOGDET_ECUDA;
+  }
+  return LOGDET_OK;
+}
+
+int dia_encode(SpmmJob<float>& J, const float* x, int n, int ld, int width) {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -137,24 +228,19 @@ int dia_encode_x(SpmmJob<float>& J, const float* x, int n, int ld, int width, in
     set_error("cuTensorMapEncodeTiled is not available");
     return LOGDET_ECUDA;
   }
-  if (((uintptr_t)x & 15) || (ld * 4) % 16 || width > 256 || width < 4 || width % 4 ||
-      box_rows > 256 || box_rows < 1) {
-    set_error("diagonal path: block not aligned for TMA");
+  const int T = J.dia_T;
+  const int box_rows = T + J.dinfo.cw;
+  const int dp = dia_pad(J.dinfo.ndiag);
+  // TMA: 16-byte aligned bases and row pitches; the innermost box extent and
+  // every innermost coordinate (J.col_off for x, 0 for the values) a
+  // multiple of four floats.
+  if (((uintptr_t)x & 15) || ((uintptr_t)J.dia & 15) || (ld * 4) % 16 || width > 256 ||
+      width < 4 || width % 4 || J.col_off % 4 || box_rows > 256 || T < 1 || dp > 256) {
+    set_error("line sweep: block not aligned for TMA");
     return LOGDET_EINVAL;
   }
-  const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)n};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)width, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(&J.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(x), dims,
-                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return LOGDET_ECUDA;
-  }
-  return LOGDET_OK;
+  LD_TRY(encode_2d(&J.tmap, x, ld, n, ld, width, box_rows));
+  return encode_2d(&J.vmap, J.dia, dp, n, dp, dp, T);
 }
 
 // ---------------------------------------------------------------------------
@@ -198,133 +284,290 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+
 // ---------------------------------------------------------------------------
-// y = A x and the window dots for FP32 blocks of a diagonal-structured
-// matrix.  Same tiles, CTA shape, per-thread row order and partial slots as
-// k_spmm (thread (r, g) owns rows r, r + R, ... of the tile and 16-byte chunk
-// g), so the result is bit-identical to the CSR path.  A tile is processed in
-// sub-tiles of dia_T rows: thread 0 arms the mbarrier with the byte count and
-// issues one TMA copy per band (dia_T + maxext rows from row r0 + band_lo);
-// every thread waits on the barrier with a bounded poll; the CTA decides
-// together (__syncthreads_or) to go on or, if a wait gave up, to wait once
-// more for the copies in flight, set the job's error flag and return.
+// Units.  Unit u of a job covers segment u % nseg (rows seg0 .. seg0 + segT
+// of every line) over the lines k0 .. k0 + nl - 1, chunk u / nseg.  A CTA
+// takes units gu = blockIdx.x, + gridDim.x, ... of the batch; window q of a
+// unit (q = 0 .. nl + 2A - 1) holds line k0 - A + q, and from q = 2A on it
+// also carries the values of line k0 + q - 2A.
+// ---------------------------------------------------------------------------
+struct SwUnit {
+  int gu, jb, seg0, segT, k0, nl;
+};
+
+__device__ __forceinline__ void sw_unit(SwUnit& U, const SpmmBatch<float>& B, int gu) {
+  U.gu = gu;
+  if (gu >= B.total_tiles) return;
+  U.jb = find_job(B, gu);
+  const SpmmJob<float>& J = B.jobs[U.jb];
+  const int u = gu - B.tile_start[U.jb];
+  const int seg = u % J.dia_nseg, chunk = u / J.dia_nseg;
+  U.seg0 = seg * J.dia_T;
+  U.segT = min(J.dia_T, J.dinfo.L - U.seg0);
+  U.k0 = chunk * J.dia_kc;
+  U.nl = min(J.dia_kc, J.dia_nlines - U.k0);
+}
+
+// Thread 0: arm the slot's barrier with the window's byte count and issue
+// its copies.
+__device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit& U, int q,
+                                         float* slot, uint32_t bar) {
+  const SpmmJob<float>& J = B.jobs[U.jb];
+  const DiaInfo& D = J.dinfo;
+  const int T = J.dia_T;
+  const int dp = dia_pad(D.ndiag);
+  const bool vals = q >= 2 * D.A;
+  const uint32_t bytes =
+      (uint32_t)(((T + D.cw) * J.width + (vals ? T * dp : 0)) * (int)sizeof(float));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, bytes);
+  tma_load_2d(smem_addr(slot), &J.tmap, J.col_off, U.seg0 + (U.k0 - D.A + q) * D.L + D.cmin, bar);
+  if (vals)
+    tma_load_2d(smem_addr(slot + sweep_win_floats(T, D.cw, J.width)), &J.vmap, 0,
+                U.seg0 + (U.k0 + q - 2 * D.A) * D.L, bar);
+}
+
+// ---------------------------------------------------------------------------
+// y = A x and the window dots for FP32 blocks of a matrix with line
+// structure.  Thread (r, g) owns rows r, r + R, ... of the segment and
+// 16-byte column chunk g (R = threads / G, G = width / 4).
+//
+// Ring protocol (uniform across the CTA): load t (a window) goes to slot
+// t % nr and completes phase (t / nr) & 1 of that slot's mbarrier.  The
+// producer issues load t once load t - nr has been released, i.e. the CTA
+// has passed the __syncthreads after its last read: window q of a unit is
+// released after line q (all its windows after the unit's last line).  As
+// nr >= 2A + 3, the two windows after the ones the current line needs are
+// in flight while it is computed.  Waits are bounded: if one gives up, the
+// CTA decides together (__syncthreads_or), waits once more for every copy
+// still in flight, sets the job's error flag and returns.
+//
+// The window-offset table: entry [rot][d] is the shared-memory offset
+// (floats from the ring base) of the first x row diagonal d reads when the
+// current line's window 0 is load index rot (mod nr).
 // ---------------------------------------------------------------------------
 template <int NDOT>
-__global__ void __launch_bounds__(512) k_spmm_dia(const __grid_constant__ SpmmBatch<float> B) {
+__global__ void __launch_bounds__(512)
+    k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr) {
   constexpr int V = 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
-  float* stage = reinterpret_cast<float*>(smem_raw + 128);
-  AccF* red = reinterpret_cast<AccF*>(smem_raw + 128);  // reused for the dot reduction
-  const uint32_t bar_a = smem_addr(bar);
+  const uint32_t bar0 = smem_addr(smem_raw);  // nr barriers, 8 bytes apart
+  int* xo_tab = reinterpret_cast<int*>(smem_raw + 128);
+  const int tab_bytes = (nr * kMaxDiags * 4 + 127) / 128 * 128;
+  AccF* red = reinterpret_cast<AccF*>(smem_raw + 128 + tab_bytes);
+  const int red_bytes = ((int)blockDim.x * V * (int)sizeof(AccF) + 127) / 128 * 128;
+  float* ring = reinterpret_cast<float*>(smem_raw + 128 + tab_bytes + red_bytes);
+
+  SwUnit C;
+  sw_unit(C, B, blockIdx.x);
+  if (C.gu >= B.total_tiles) return;
   if (threadIdx.x == 0) {
-    mbar_init(bar_a, 1);
+    for (int q = 0; q < nr; ++q) mbar_init(bar0 + 8 * q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  uint32_t phase = 0;
-  for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
-    const int jb = find_job(B, gt);
-    const SpmmJob<float>& J = B.jobs[jb];
-    const DiaInfo& D = J.dinfo;
-    const int tile = gt - B.tile_start[jb];
-    const int G = J.width / V;
-    const int R = blockDim.x / G;
-    const int r = threadIdx.x / G;
-    const int g = threadIdx.x - r * G;
-    const bool live = r < R;
-    const int row0 = tile * J.tile_rows;
-    const int row1 = min(row0 + J.tile_rows, J.n);
-    const int col0 = J.col_off + g * V;
-    const int ndots = J.ndots;
-    const int rows_box = J.dia_T + D.maxext;
-    // Band regions start on 128-byte boundaries (TMA destinations).
-    const int band_floats = (rows_box * J.width + 31) / 32 * 32;
-    const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
-    int dz = 0;  // the main diagonal (every row stores it)
-    for (int d = 0; d < D.ndiag; ++d)
-      if (D.off[d] == 0) dz = d;
 
-    AccF acc[NDOT > 0 ? NDOT : 1][V];
-#pragma unroll
-    for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
-#pragma unroll
-      for (int v = 0; v < V; ++v) acc[d][v].zero();
-
-    for (int s0 = row0; s0 < row1; s0 += J.dia_T) {
-      __syncthreads();  // the previous sub-tile's reads of the stage are done
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar_a, (uint32_t)(D.nbands * rows_box * J.width * (int)sizeof(float)));
-        for (int b = 0; b < D.nbands; ++b)
-          tma_load_2d(smem_addr(stage + (size_t)b * band_floats), &J.tmap, J.col_off,
-                      s0 + D.band_lo[b], bar_a);
+  // Producer state (every thread keeps it; thread 0 issues).
+  SwUnit P = C;
+  int pq = 0, issued = 0, pslot = 0;  // pslot = issued % nr
+  auto produce = [&](int released) {
+    while (P.gu < B.total_tiles && issued < released + nr) {
+      if (threadIdx.x == 0)
+        sw_issue(B, P, pq, ring + (size_t)pslot * slot_floats, bar0 + 8 * pslot);
+      ++issued;
+      if (++pslot == nr) pslot = 0;
+      if (++pq == P.nl + 2 * B.jobs[P.jb].dinfo.A) {
+        sw_unit(P, B, P.gu + gridDim.x);
+        pq = 0;
       }
-      const bool ok = mbar_wait_bounded(bar_a, phase);
+    }
+  };
+  produce(0);
+
+  AccF acc[NDOT > 0 ? NDOT : 1][V];
+#pragma unroll
+  for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[d][v].zero();
+
+  // Constants of the current job.
+  int cur_jb = -1, G = 1, R = 1, r = 0, g = 0, width = 0, nd = 0, dp = 0, A = 0, L = 0;
+  int win_floats = 0, dself = 0, col0 = 0, ldy = 0, ndots = 0, n = 0;
+  float* yv = nullptr;
+  unsigned selfmask = 0;
+  bool live = false;
+
+  // Consumer state: every load is waited for once, in order.  wnext is the
+  // index of the next load to wait for, wslot = wnext % nr, bit s of
+  // phases the parity its slot completes next; rslot = (t0 + j) % nr for
+  // the current unit's window 0 t0 and line j.
+  int t0 = 0, wnext = 0, wslot = 0, rslot = 0;
+  uint32_t phases = 0;
+  while (C.gu < B.total_tiles) {
+    const SpmmJob<float>& J = B.jobs[C.jb];
+    if (C.jb != cur_jb) {
+      cur_jb = C.jb;
+      const DiaInfo& D = J.dinfo;
+      G = J.width / V;
+      R = blockDim.x / G;
+      r = threadIdx.x / G;
+      g = threadIdx.x - r * G;
+      live = r < R;
+      width = J.width;
+      nd = D.ndiag;
+      dp = dia_pad(nd);
+      A = D.A;
+      L = D.L;
+      n = J.n;
+      win_floats = sweep_win_floats(J.dia_T, D.cw, width);
+      for (int d = 0; d < nd; ++d)
+        if (D.off[d] == 0) dself = d;
+      col0 = J.col_off + g * V;
+      ldy = J.ld;
+      yv = J.y;
+      ndots = J.ndots;
+      selfmask = 0;
+      for (int d = 0; d < ndots; ++d)
+        if (J.dotv[d] == J.x) selfmask |= 1u << d;
+      // (every read of the previous table ended before the last barrier)
+      for (int e = threadIdx.x; e < nr * kMaxDiags; e += blockDim.x) {
+        const int rot = e / kMaxDiags, d = e - rot * kMaxDiags;
+        xo_tab[e] = d < nd ? ((rot + A + D.line[d]) % nr) * slot_floats + D.cpos[d] * width : 0;
+      }
+      __syncthreads();
+    }
+    const int nwin = C.nl + 2 * A;
+    for (int j = 0; j < C.nl; ++j) {
+      // Windows of line k0 + j: loads t0 + j .. t0 + j + 2A (only the last
+      // is new after the first line).
+      bool ok = true;
+      const int tw = t0 + j + 2 * A;
+      while (ok && wnext <= tw) {
+        ok = mbar_wait_bounded(bar0 + 8 * wslot, (phases >> wslot) & 1u);
+        if (ok) {
+          phases ^= 1u << wslot;
+          ++wnext;
+          if (++wslot == nr) wslot = 0;
+        }
+      }
       if (__syncthreads_or(!ok)) {
-        mbar_wait_bounded(bar_a, phase);  // let copies in flight land before leaving
+        // Copies still in flight: loads wnext .. issued - 1 (distinct slots).
+        for (int t = wnext, sl = wslot; t < issued; ++t) {
+          mbar_wait_bounded(bar0 + 8 * sl, (phases >> sl) & 1u);
+          if (++sl == nr) sl = 0;
+        }
         if (threadIdx.x == 0) atomicExch(J.err, 1);
         return;
       }
-      phase ^= 1;
       if (live) {
-        const int s1 = min(s0 + J.dia_T, row1);
-        for (int row = s0 + r; row < s1; row += R) {
-          const int rr = row - s0;
-          float s[V] = {0.f, 0.f, 0.f, 0.f};
-          for (int d = 0; d < D.ndiag; ++d) {
-            const float a = __ldg(J.dia + (size_t)d * J.n + row);
-            const float4 xv = *reinterpret_cast<const float4*>(
-                stage + (size_t)D.diag_band[d] * band_floats +
-                (size_t)(rr + D.diag_shift[d]) * J.width + g * V);
-            s[0] = fmaf(a, xv.x, s[0]);
-            s[1] = fmaf(a, xv.y, s[1]);
-            s[2] = fmaf(a, xv.z, s[2]);
-            s[3] = fmaf(a, xv.w, s[3]);
+        const int* xt = xo_tab + rslot * kMaxDiags;
+        int xo[kMaxDiags];
+#pragma unroll
+        for (int q = 0; q < kMaxDiags / 4; ++q) {
+          if (4 * q < nd) {
+            const int4 o = reinterpret_cast<const int4*>(xt)[q];
+            xo[4 * q] = o.x;
+            xo[4 * q + 1] = o.y;
+            xo[4 * q + 2] = o.z;
+            xo[4 * q + 3] = o.w;
+          } else {
+            xo[4 * q] = xo[4 * q + 1] = xo[4 * q + 2] = xo[4 * q + 3] = 0;
           }
+        }
+        const int xself = xt[dself];
+        const int vslot = rslot + 2 * A < nr ? rslot + 2 * A : rslot + 2 * A - nr;
+        const float* vs = ring + (size_t)vslot * slot_floats + win_floats;
+        const int rowbase = C.seg0 + (C.k0 + j) * L;
+        const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
+        for (int rr = r; rr < C.segT; rr += R) {
+          const int row = rowbase + rr;
+          if (row >= n) break;
+          const float* xr = ring + rr * width + g * V;
+          const float* vr = vs + rr * dp;
+          // Window vectors other than x itself: loads issued before the
+          // row's sum so that their latency overlaps it (up to four; the
+          // registers of more would spill).
+          constexpr bool kEarly = NDOT <= 4;
+          float u[NDOT > 0 ? NDOT : 1][V];
+#pragma unroll
+          for (int d = 0; d < NDOT; ++d)
+            if (kEarly && d < ndots && !((selfmask >> d) & 1u))
+              load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[d]);
+          float s[V] = {0.f, 0.f, 0.f, 0.f};
+          float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int d = 0; d < kMaxDiags; ++d) {
+            if (d < nd) {
+              if (d % 4 == 0) av = *reinterpret_cast<const float4*>(vr + d);
+              const float a = d % 4 == 0 ? av.x : d % 4 == 1 ? av.y : d % 4 == 2 ? av.z : av.w;
+              const float4 xv = *reinterpret_cast<const float4*>(xr + xo[d]);
+              s[0] = fmaf(a, xv.x, s[0]);
+              s[1] = fmaf(a, xv.y, s[1]);
+              s[2] = fmaf(a, xv.z, s[2]);
+              s[3] = fmaf(a, xv.w, s[3]);
+            }
+          }
+          const float4 xs4 = *reinterpret_cast<const float4*>(xr + xself);
+          const float xs[V] = {xs4.x, xs4.y, xs4.z, xs4.w};
           if (has_shift || has_scale) {
-            const float4 xr = *reinterpret_cast<const float4*>(
-                stage + (size_t)D.diag_band[dz] * band_floats +
-                (size_t)(rr + D.diag_shift[dz]) * J.width + g * V);
-            const float xs[V] = {xr.x, xr.y, xr.z, xr.w};
 #pragma unroll
             for (int v = 0; v < V; ++v) {
               if (has_shift) s[v] = fmaf((float)J.colshift[col0 + v], xs[v], s[v]);
               if (has_scale) s[v] = s[v] * (float)J.colscale[col0 + v];
             }
           }
-          store_vec<float>(J.y + (size_t)row * J.ld + col0, s);
+          store_vec<float>(yv + (size_t)row * ldy + col0, s);
 #pragma unroll
           for (int d = 0; d < NDOT; ++d) {
             if (d < ndots) {
-              float u[V];
-              load_vec<float>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+              const bool self = (selfmask >> d) & 1u;
+              if (!kEarly && !self) load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[d]);
 #pragma unroll
-              for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
+              for (int v = 0; v < V; ++v) acc[d][v].fma(self ? xs[v] : u[d][v], s[v]);
             }
           }
         }
       }
-    }
+      const bool last = j == C.nl - 1;
+      if (last) {
+        const int unit = C.gu - B.tile_start[C.jb];
 #pragma unroll
-    for (int d = 0; d < NDOT; ++d) {
-      if (d < ndots)
-        cta_reduce_write<float, AccF>(red, acc[d], live, G, R, J.col_off, J.width,
-                                      J.part + (size_t)d * J.ld * J.ntiles, J.ntiles, tile);
+        for (int d = 0; d < NDOT; ++d) {
+          if (d < ndots)
+            cta_reduce_write<float, AccF>(red, acc[d], live, G, R, J.col_off, width,
+                                          J.part + (size_t)d * ldy * J.ntiles, J.ntiles, unit);
+        }
+#pragma unroll
+        for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
+#pragma unroll
+          for (int v = 0; v < V; ++v) acc[d][v].zero();
+      }
+      __syncthreads();  // every read of the released windows is done
+      produce(last ? t0 + nwin : t0 + j + 1);
+      if (++rslot == nr) rslot = 0;
     }
+    // The next unit's window 0 follows this unit's last 2A windows.
+    rslot += 2 * A;
+    if (rslot >= nr) rslot -= nr;
+    t0 += nwin;
+    sw_unit(C, B, C.gu + gridDim.x);
   }
 }
 
-static size_t dia_smem_bytes(const SpmmBatch<float>& b, int threads) {
-  size_t mx = 0;
+// Ring slot size (floats, a multiple of 32) and the largest A of a launch.
+// The ring holds 2A + 1 + kSweepPrefetch slots: measured on GB300, deeper
+// prefetch (up to 8 windows, one CTA per SM or two) gives the same time, so
+// the kernel is bound by issue, not by the latency of the copies.
+static void sweep_launch_geom(const SpmmBatch<float>& b, int* slot_floats, int* amax) {
+  int sf = 0, a = 0;
   for (int j = 0; j < b.njobs; ++j) {
     const SpmmJob<float>& J = b.jobs[j];
-    const size_t band = ((size_t)(J.dia_T + J.dinfo.maxext) * J.width + 31) / 32 * 32;
-    const size_t stage = (size_t)J.dinfo.nbands * band * 4;
-    mx = std::max(mx, stage);
+    sf = std::max(sf, sweep_slot_floats(J.dinfo, J.dia_T, J.width));
+    a = std::max(a, J.dinfo.A);
   }
-  const size_t red = (size_t)threads * 4 * sizeof(AccF);
-  return 128 + std::max(mx, red);
+  *slot_floats = (sf + 31) / 32 * 32;
+  *amax = a;
 }
 
 int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
@@ -338,28 +581,31 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
     flops += 2.0 * (double)J.nnz * J.b + 2.0 * (double)J.n * J.b * J.ndots;
     bytes += 4.0 * (J.n + 1) + (double)J.nnz * 8 + vb * (2 + extra_reads);
   }
-  const size_t smem = dia_smem_bytes(b, threads);
+  int slot_floats = 0, amax = 0;
+  sweep_launch_geom(b, &slot_floats, &amax);
   ProfScope prof(KC_SPMM, s, flops, bytes);
-#define LD_DIA_CASE(ND)                                                                      \
+#define LD_SW_CASE(ND)                                                                       \
   {                                                                                          \
-    auto kern = k_spmm_dia<ND>;                                                              \
+    auto kern = k_spmm_sweep<ND>;                                                            \
+    const int nr = 2 * amax + 1 + kSweepPrefetch;                                            \
+    const size_t smem = sweep_smem_bytes(nr, slot_floats, threads);                          \
     if (smem > 48 * 1024)                                                                    \
       LD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
     int per_sm = 0;                                                                          \
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);             \
     if (per_sm < 1) per_sm = 1;                                                              \
     const int grid = std::max(1, std::min(b.total_tiles, per_sm * sm_count()));              \
-    kern<<<grid, threads, smem, s>>>(b);                                                     \
+    kern<<<grid, threads, smem, s>>>(b, slot_floats, nr);                                    \
     break;                                                                                   \
   }
   do {
-    if (nd == 0) LD_DIA_CASE(0)
-    if (nd == 1) LD_DIA_CASE(1)
-    if (nd == 2) LD_DIA_CASE(2)
-    if (nd <= 4) LD_DIA_CASE(4)
-    LD_DIA_CASE(kMaxWin)
+    if (nd == 0) LD_SW_CASE(0)
+    if (nd == 1) LD_SW_CASE(1)
+    if (nd == 2) LD_SW_CASE(2)
+    if (nd <= 4) LD_SW_CASE(4)
+    LD_SW_CASE(kMaxWin)
   } while (0);
-#undef LD_DIA_CASE
+#undef LD_SW_CASE
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }

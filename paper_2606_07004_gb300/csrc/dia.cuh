@@ -1,4 +1,5 @@
-// Diagonal fast path of the SpMM pass for FP32 blocks (see dia.cu).
+// Line-sweep path of the SpMM pass for FP32 blocks of stencil matrices (see
+// dia.cu).
 #pragma once
 
 #include "handle.cuh"
@@ -6,29 +7,38 @@
 
 namespace ld {
 
-constexpr int kDiaBandGap = 8;    // offsets at most this far apart share a staged band
-constexpr int kDiaMaxExt = 16;    // largest band extent handled
-constexpr int kDiaRows = 8;       // rows a CTA computes at once (CTA = 8 x width / 4 threads)
-constexpr int kDiaSmemTarget = 56 * 1024;  // staged bytes per CTA (several CTAs per SM)
+constexpr int kSweepMaxA = 3;           // lines -A..A held at once: at most 7
+constexpr int kSweepMaxCw = 16;         // extra rows of a line window
+constexpr int kSweepMinL = 32;          // shortest line
+constexpr int kSweepPrefetch = 2;       // windows loaded ahead of the sweep
+constexpr int kSweepSmemBudget = 110 * 1024;  // per CTA (two CTAs per SM)
 
-// At handle creation (host CSR): record the diagonal structure when every
-// entry lies on at most kMaxDiags diagonals and the bands are narrow.
+// Diagonal values per row, padded to a multiple of four (one 16-byte vector
+// per four diagonals).
+__host__ __device__ inline int dia_pad(int ndiag) { return (ndiag + 3) & ~3; }
+
+// At handle creation (host CSR): record the line structure when every entry
+// lies on at most kMaxDiags diagonals that fit one (see DiaInfo).
 int dia_build(logdet_ctx* h, const int* rowptr, const int* colind);
 
-// Values of Q / c per diagonal, [ndiag][n] (0 where a row has no entry on a
-// diagonal); the division in FP64 as for the CSR values.
+// Values of Q / c per row and diagonal, [n][dia_pad(ndiag)] (0 where a row
+// has no entry on a diagonal); the division in FP64 as for the CSR values.
 int dia_values_f32(const logdet_ctx* h, double c, float* out, cudaStream_t st);
 
-// Tile rows of the diagonal path for a slice of `width` FP32 columns; 0 when
-// the matrix or the slice does not take it.
-int dia_tile_rows(const logdet_ctx* h, int width);
+// Sweep geometry of a block slice of `width` FP32 columns processed by CTAs
+// of `threads`: segment rows T (a multiple of the row groups), lines per
+// unit, segments per line, lines, units.  Returns false when the matrix or
+// the slice does not take the sweep (then the CSR path runs).
+struct SweepGeom {
+  int T, kc, nseg, nlines, units;
+};
+bool dia_sweep_geom(const logdet_ctx* h, int width, int threads, SweepGeom* g);
 
-// Fill the job's tensor map for x (n x ld FP32, box of width columns and
-// box_rows rows).
-int dia_encode_x(SpmmJob<float>& J, const float* x, int n, int ld, int width, int box_rows);
+// Fill the job's tensor maps: x (n x ld FP32, box of width columns and
+// T + cw rows) and the values (box of T rows).
+int dia_encode(SpmmJob<float>& J, const float* x, int n, int ld, int width);
 
-// Batched launch of diagonal-path jobs (all with dia != nullptr), with the
-// CTA size of the jobs' CSR geometry.
+// Batched launch of sweep jobs (all with dia != nullptr), CTAs of `threads`.
 int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s);
 
 }  // namespace ld

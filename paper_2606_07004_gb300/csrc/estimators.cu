@@ -118,6 +118,17 @@ int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* lo, double* h
   return LOGDET_OK;
 }
 
+int logdet_line_structure(logdet_handle h, int32_t* line_stride, int32_t* lines) {
+  if (!h || !line_stride || !lines) {
+    set_error("NULL handle or output pointer");
+    return LOGDET_EINVAL;
+  }
+  const bool on = h->dia.ndiag > 0 && h->dia_slot;
+  *line_stride = on ? h->dia.L : 0;
+  *lines = on ? h->dia.A : 0;
+  return LOGDET_OK;
+}
+
 int logdet_oslq(logdet_handle h, int32_t P, int32_t m, int32_t k, uint64_t seed,
                 const logdet_opts* opts, logdet_result* out) {
   return run_estimator(0, h, P, m, k, seed, opts, out);

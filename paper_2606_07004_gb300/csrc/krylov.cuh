@@ -55,16 +55,19 @@ struct SpmmJob {
   int col_off, width;              // columns [col_off, col_off+width) of the block (width % vec == 0)
   int b;                           // live columns in this slice (accounting only)
   long long nnz;                   // (accounting only)
-  // Diagonal fast path (FP32 blocks, see dia.cu): values per diagonal
-  // [ndiag][n] (dia == nullptr: CSR path), the tensor map of x (box: width
-  // columns x (dia_T + band extent) rows), the matrix's diagonal structure,
-  // and a flag set if a bounded wait gives up.  Tiles, partial slots and the
-  // per-thread row order are those of the CSR path.
+  // Line-sweep path (FP32 blocks of a matrix with line structure, see
+  // dia.cu); dia == nullptr: CSR path.  The rows are cut into segments of
+  // dia_T rows within each line of L rows; a unit is one segment position
+  // swept over dia_kc consecutive lines, and ntiles counts the units (their
+  // index is the partial slot).  dia: values per row and diagonal
+  // [n][dia_pad(ndiag)]; tmap: x, box of width columns x (dia_T + cw) rows;
+  // vmap: the values, box of dia_T rows; err: set if a bounded wait gives up.
   const float* dia;
   int* err;
-  int dia_T;                       // rows per staged sub-tile (a multiple of the row groups)
+  int dia_T, dia_kc, dia_nseg, dia_nlines;
   DiaInfo dinfo;
   CUtensorMap tmap;
+  CUtensorMap vmap;
 };
 
 template <typename T>

@@ -149,6 +149,20 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
     LD_TRY(spmm_items(hctx, g.tile_rows, &items, &cnt));
     if (items) nslots = cnt;
   }
+  if constexpr (std::is_same<T, float>::value) {
+    // Line sweep: FP32 blocks of a matrix with line structure; its units are
+    // the partial slots.
+    SweepGeom sg;
+    if (diavals && !items && hctx && hctx->kind == 0 && !((uintptr_t)X0 & 15) &&
+        !((uintptr_t)Vfull & 15) && dia_sweep_geom(hctx, width, g.threads, &sg)) {
+      sweep = true;
+      sw_T = sg.T;
+      sw_kc = sg.kc;
+      sw_nseg = sg.nseg;
+      sw_nlines = sg.nlines;
+      nslots = sg.units;
+    }
+  }
   blk = (size_t)n * ld;
   const int win = method == 0 ? 2 : k;
   if (method == 1 && win > kMaxWin - 1) {
@@ -189,7 +203,7 @@ int KRun<T>::slice_live(int q) const {
 }
 
 template <typename T>
-void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
+int KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
   for (int q = 0; q < tune.split; ++q) {
     SpmmJob<T> J;
     memset(&J, 0, sizeof J);
@@ -218,23 +232,20 @@ void KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
       for (int i = lo; i <= j; ++i) J.dotv[i - lo] = ptr(i);
     }
     if constexpr (std::is_same<T, float>::value) {
-      // Diagonal fast path: same tiles and row order, x staged by TMA.
-      const int T0 = (diavals && !items && hctx) ? dia_tile_rows(hctx, width) : 0;
-      if (T0 > 0) {
-        const int R = g.threads / (width / Vec16<T>::N);
-        const int Ts = std::max(R, T0 / R * R);
-        if (R > 0 && Ts + hctx->dia.maxext <= 256) {
-          J.dia = diavals;
-          J.dia_T = Ts;
-          J.dinfo = hctx->dia;
-          J.err = dia_err.p;
-          if (dia_encode_x(J, ptr(j), n, ld, width, Ts + hctx->dia.maxext) != LOGDET_OK)
-            J.dia = nullptr;  // not encodable: the CSR path
-        }
+      if (sweep) {
+        J.dia = diavals;
+        J.err = dia_err.p;
+        J.dia_T = sw_T;
+        J.dia_kc = sw_kc;
+        J.dia_nseg = sw_nseg;
+        J.dia_nlines = sw_nlines;
+        J.dinfo = hctx->dia;
+        LD_TRY(dia_encode(J, ptr(j), n, ld, width));
       }
     }
     out.push_back(J);
   }
+  return LOGDET_OK;
 }
 
 template <typename T>
@@ -597,7 +608,7 @@ struct Solve : ISolve {
       LD_TRY(vals.alloc(h->nnz));
       LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
       if (std::is_same<T, float>::value && h->dia.ndiag > 0 && h->dia_slot) {
-        LD_TRY(diav.alloc((size_t)h->dia.ndiag * n));
+        LD_TRY(diav.alloc((size_t)dia_pad(h->dia.ndiag) * n));
         LD_TRY(dia_values_f32(h, cscale, diav.p, st));
       }
     }
@@ -779,7 +790,7 @@ struct Solve : ISolve {
     auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
     const int j = run->next_step();
     if (h->kind == 1) LD_TRY(run->grid_pass1(j));
-    else run->spmm_jobs(j, v);
+    else LD_TRY(run->spmm_jobs(j, v));
     coef.push_back(run->scalar_job(j, run->pass1_dots(j), true));
     widths.push_back(run->ld);
     return LOGDET_OK;

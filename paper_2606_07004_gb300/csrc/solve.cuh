@@ -95,8 +95,10 @@ struct KRun {
   DevBuf<Part> part;
   DevBuf<T> y, ring;
   KState ks;
-  const float* diavals = nullptr;  // FP32 values per diagonal: the diagonal fast path
+  const float* diavals = nullptr;  // FP32 values per row and diagonal: the line-sweep path
   DevBuf<int> dia_err;             // set if a staged copy's wait gave up
+  bool sweep = false;              // pass 1 runs the line sweep
+  int sw_T = 0, sw_kc = 0, sw_nseg = 0, sw_nlines = 0;
   int done_steps = 0;  // steps whose pass 1 has been issued
   cudaStream_t st;
 
@@ -114,7 +116,7 @@ struct KRun {
   bool has_pass2(int j) const { return j < m; }
   int pass1_dots(int j) const { return method == 0 ? 1 : j - win_lo(j) + 1; }
   // Step j's jobs, one per column slice.
-  void spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const;
+  int spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const;
   // Gridded operator: step j's pass 1 (y = Q~ u_j and the window dots),
   // launched on the run's stream.
   int grid_pass1(int j);

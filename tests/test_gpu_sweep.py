@@ -1,0 +1,118 @@
+"""Line-sweep path of the FP32 SpMM pass (x rows of 2A + 1 grid lines staged
+by TMA copies in a ring of shared-memory windows).  A handle created from
+host arrays of a 2D grid stencil takes it for mixed-FP32 solves; a handle
+over device arrays of the same matrix keeps the CSR gathers.  y is the same
+FP32 sum on both paths; the window dots are reduced per sweep unit instead
+of per CSR tile, so the two agree to the rounding of compensated partial
+sums, far inside the mixed-precision budget (1e-4 against FP64)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_07004_gb300 import binding as B  # noqa: E402
+
+RTOL_PATHS = 1e-6   # sweep vs CSR gathers, both mixed FP32
+RTOL_MIXED = 1e-4   # mixed vs the FP64 oracle
+
+
+def _device_handle(A):
+    rp = torch.as_tensor(A.rowptr.astype(np.int32), device="cuda")
+    ci = torch.as_tensor(A.colind.astype(np.int32), device="cuda")
+    va = torch.as_tensor(np.asarray(A.vals), device="cuda")
+    return B.Handle(A.n, rp, ci, va, device=True)
+
+
+def _band(L, n, dtype=np.float32):
+    # 5-diagonal SPD band (offsets 0, +-1, +-L) whose last line is ragged
+    # (n not a multiple of L).
+    Q = sp.diags([np.full(n - L, -1.0), np.full(n - 1, -1.0), np.full(n, 4.2),
+                  np.full(n - 1, -1.0), np.full(n - L, -1.0)], [-L, -1, 0, 1, L], format="csr")
+    Q.sort_indices()
+    return W.CSR(n, Q.indptr.astype(np.int32), Q.indices.astype(np.int32), Q.data.astype(dtype))
+
+
+MATS = {
+    "lap2d": (lambda: W.laplacian_2d(100, 90, shift=0.05), (100, 1)),
+    "matern": (lambda: W.matern_2d(70, 0.05, dtype=np.float32), (70, 2)),
+    "band-ragged": (lambda: _band(64, 5001), (64, 1)),
+}
+
+
+def _close(a, b, rtol=RTOL_PATHS):
+    assert abs(a.logdet - b.logdet) <= rtol * abs(b.logdet)
+    scale = np.max(np.abs(b.per_probe))
+    np.testing.assert_allclose(a.per_probe, b.per_probe, rtol=0, atol=10 * rtol * scale)
+
+
+def _same(a, b):
+    assert a.logdet == b.logdet
+    assert np.array_equal(a.per_probe, b.per_probe)
+    assert np.array_equal(a.z_norm2, b.z_norm2)
+
+
+def test_line_structure_detection():
+    for name, (mk, want) in MATS.items():
+        A = mk()
+        with B.Handle.from_csr(A) as h, _device_handle(A) as hd:
+            assert h.line_structure() == want, name
+            assert hd.line_structure() == (0, 0)
+    for A in (W.laplacian_3d(24, 21, 19, shift=0.01), W.laplacian_2d(40, 40, shift=0.1)):
+        with B.Handle.from_csr(A) as h:   # 3D stencil; n < 4096
+            assert h.line_structure() == (0, 0)
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("method,k", [("oslq", 0), ("osaiop", 2), ("osaiop", 4), ("osaiop", 8)])
+def test_sweep_matches_csr_path(name, method, k):
+    A = MATS[name][0]()
+    with B.Handle.from_csr(A) as hs, _device_handle(A) as hc:
+        for kw in ({}, {"shift": 0.02}, {"autotune": 1}):
+            if method == "oslq":
+                a = hs.oslq(36, 20, seed=3, precision=B.MIXED_FP32, **kw)
+                b = hc.oslq(36, 20, seed=3, precision=B.MIXED_FP32, **kw)
+            else:
+                a = hs.osaiop(36, 16, iop_window=k, seed=3, precision=B.MIXED_FP32, **kw)
+                b = hc.osaiop(36, 16, iop_window=k, seed=3, precision=B.MIXED_FP32, **kw)
+            _close(a, b)
+
+
+@pytest.mark.parametrize("name", ["matern", "band-ragged"])
+def test_sweep_against_fp64_oracle(name):
+    A = MATS[name][0]()
+    Q = A.to_scipy()
+    with B.Handle.from_csr(A) as h:
+        r1 = h.oslq(30, 25, seed=2, precision=B.MIXED_FP32)
+        r2 = h.osaiop(30, 20, iop_window=4, seed=2, precision=B.MIXED_FP32)
+    e1 = O.oslq(Q, 30, 25, seed=2)
+    e2 = O.osaiop(Q, 30, 20, k=4, seed=2)
+    assert abs(r1.logdet - e1.logdet) <= RTOL_MIXED * abs(e1.logdet)
+    assert abs(r2.logdet - e2.logdet) <= RTOL_MIXED * abs(e2.logdet)
+
+
+def test_sweep_wide_block_deterministic_server_and_plan():
+    # 120 probes (80-column Krylov block); repeated runs, the server and a
+    # graph plan take the same launches and give bit-identical results.
+    A = W.matern_2d(90, 0.05, dtype=np.float32)
+    with B.Handle.from_csr(A) as hs, _device_handle(A) as hc:
+        a = hs.oslq(120, 12, seed=1, precision=B.MIXED_FP32)
+        _same(a, hs.oslq(120, 12, seed=1, precision=B.MIXED_FP32))
+        _close(a, hc.oslq(120, 12, seed=1, precision=B.MIXED_FP32))
+        with B.Server(8 << 30) as srv:
+            ids = [srv.submit(hs, B.METHOD_OSAIOP, 30, 12, 4, seed=s, precision=B.MIXED_FP32)
+                   for s in range(3)]
+            served = [srv.wait(i) for i in ids]
+        with B.Plan(hs, B.METHOD_OSAIOP, 30, 12, 4, precision=B.MIXED_FP32) as plan:
+            replay = [plan.run(s) for s in range(3)]
+        for s in range(3):
+            want = hs.osaiop(30, 12, iop_window=4, seed=s, precision=B.MIXED_FP32)
+            _same(served[s], want)
+            _same(replay[s], want)
