@@ -28,6 +28,7 @@
 #include <climits>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 namespace ld {
@@ -347,8 +348,10 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // (floats from the ring base) of the first x row diagonal d reads when the
 // current line's window 0 is load index rot (mod nr).
 // ---------------------------------------------------------------------------
-template <int NDOT>
-__global__ void __launch_bounds__(512)
+// MAXT: the largest CTA the instance takes (320 or 512); with at most two
+// dots, two CTAs per SM are asked for (the register budget follows).
+template <int NDOT, int MAXT>
+__global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
     k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr) {
   constexpr int V = 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -480,54 +483,91 @@ __global__ void __launch_bounds__(512)
         const float* vs = ring + (size_t)vslot * slot_floats + win_floats;
         const int rowbase = C.seg0 + (C.k0 + j) * L;
         const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
-        for (int rr = r; rr < C.segT; rr += R) {
-          const int row = rowbase + rr;
-          if (row >= n) break;
-          const float* xr = ring + rr * width + g * V;
-          const float* vr = vs + rr * dp;
-          // Window vectors other than x itself: loads issued before the
-          // row's sum so that their latency overlaps it (up to four; the
-          // registers of more would spill).
-          constexpr bool kEarly = NDOT <= 4;
-          float u[NDOT > 0 ? NDOT : 1][V];
+        // Window vectors other than x itself are loaded before the sums, so
+        // that their latency overlaps them (up to four; the registers of
+        // more would spill).
+        constexpr bool kEarly = NDOT <= 4;
+        // kRows rows of the segment per thread at a time (rows rr, rr + R,
+        // ...): independent FMA chains interleave.  Each row's sum, y and
+        // dot updates are those of one row at a time, in row order.
+        auto rows_loop = [&](auto krows) {
+        constexpr int kRows = decltype(krows)::value;
+        for (int rr = r; rr < C.segT; rr += kRows * R) {
+          if (rowbase + rr >= n) break;
+          bool on[kRows];
+          int rq[kRows];
 #pragma unroll
-          for (int d = 0; d < NDOT; ++d)
-            if (kEarly && d < ndots && !((selfmask >> d) & 1u))
-              load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[d]);
-          float s[V] = {0.f, 0.f, 0.f, 0.f};
-          float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int q = 0; q < kRows; ++q) {
+            on[q] = rr + q * R < C.segT && rowbase + rr + q * R < n;
+            rq[q] = on[q] ? rr + q * R : rr;  // an absent row re-reads row rr
+          }
+          float u[kRows][NDOT > 0 ? NDOT : 1][V];
+#pragma unroll
+          for (int q = 0; q < kRows; ++q)
+#pragma unroll
+            for (int d = 0; d < NDOT; ++d)
+              if (kEarly && d < ndots && !((selfmask >> d) & 1u))
+                load_vec<float>(J.dotv[d] + (size_t)(rowbase + rq[q]) * ldy + col0, u[q][d]);
+          float sv[kRows][V];
+#pragma unroll
+          for (int q = 0; q < kRows; ++q)
+#pragma unroll
+            for (int v = 0; v < V; ++v) sv[q][v] = 0.f;
+          float4 av[kRows];
 #pragma unroll
           for (int d = 0; d < kMaxDiags; ++d) {
             if (d < nd) {
-              if (d % 4 == 0) av = *reinterpret_cast<const float4*>(vr + d);
-              const float a = d % 4 == 0 ? av.x : d % 4 == 1 ? av.y : d % 4 == 2 ? av.z : av.w;
-              const float4 xv = *reinterpret_cast<const float4*>(xr + xo[d]);
-              s[0] = fmaf(a, xv.x, s[0]);
-              s[1] = fmaf(a, xv.y, s[1]);
-              s[2] = fmaf(a, xv.z, s[2]);
-              s[3] = fmaf(a, xv.w, s[3]);
+#pragma unroll
+              for (int q = 0; q < kRows; ++q) {
+                if (d % 4 == 0) av[q] = *reinterpret_cast<const float4*>(vs + rq[q] * dp + d);
+                const float a = d % 4 == 0   ? av[q].x
+                                : d % 4 == 1 ? av[q].y
+                                : d % 4 == 2 ? av[q].z
+                                             : av[q].w;
+                const float4 xv =
+                    *reinterpret_cast<const float4*>(ring + rq[q] * width + g * V + xo[d]);
+                sv[q][0] = fmaf(a, xv.x, sv[q][0]);
+                sv[q][1] = fmaf(a, xv.y, sv[q][1]);
+                sv[q][2] = fmaf(a, xv.z, sv[q][2]);
+                sv[q][3] = fmaf(a, xv.w, sv[q][3]);
+              }
             }
           }
-          const float4 xs4 = *reinterpret_cast<const float4*>(xr + xself);
-          const float xs[V] = {xs4.x, xs4.y, xs4.z, xs4.w};
-          if (has_shift || has_scale) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-              if (has_shift) s[v] = fmaf((float)J.colshift[col0 + v], xs[v], s[v]);
-              if (has_scale) s[v] = s[v] * (float)J.colscale[col0 + v];
+          for (int q = 0; q < kRows; ++q) {
+            if (!on[q]) continue;
+            const int row = rowbase + rq[q];
+            float(&s)[V] = sv[q];
+            const float4 xs4 =
+                *reinterpret_cast<const float4*>(ring + rq[q] * width + g * V + xself);
+            const float xs[V] = {xs4.x, xs4.y, xs4.z, xs4.w};
+            if (has_shift || has_scale) {
+#pragma unroll
+              for (int v = 0; v < V; ++v) {
+                if (has_shift) s[v] = fmaf((float)J.colshift[col0 + v], xs[v], s[v]);
+                if (has_scale) s[v] = s[v] * (float)J.colscale[col0 + v];
+              }
             }
-          }
-          store_vec<float>(yv + (size_t)row * ldy + col0, s);
+            store_vec<float>(yv + (size_t)row * ldy + col0, s);
 #pragma unroll
-          for (int d = 0; d < NDOT; ++d) {
-            if (d < ndots) {
-              const bool self = (selfmask >> d) & 1u;
-              if (!kEarly && !self) load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[d]);
+            for (int d = 0; d < NDOT; ++d) {
+              if (d < ndots) {
+                const bool self = (selfmask >> d) & 1u;
+                if (!kEarly && !self)
+                  load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[q][d]);
 #pragma unroll
-              for (int v = 0; v < V; ++v) acc[d][v].fma(self ? xs[v] : u[d][v], s[v]);
+                for (int v = 0; v < V; ++v) acc[d][v].fma(self ? xs[v] : u[q][d][v], s[v]);
+              }
             }
           }
         }
+        };
+        // (pairs in the CTAs of up to 320 threads only: the larger ones run
+        // at two per SM on 64 registers, which pairs would spill)
+        if (NDOT <= 4 && MAXT <= 320 && C.segT >= 2 * R)
+          rows_loop(std::integral_constant<int, 2>{});
+        else
+          rows_loop(std::integral_constant<int, 1>{});
       }
       const bool last = j == C.nl - 1;
       if (last) {
@@ -586,7 +626,7 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
   ProfScope prof(KC_SPMM, s, flops, bytes);
 #define LD_SW_CASE(ND)                                                                       \
   {                                                                                          \
-    auto kern = k_spmm_sweep<ND>;                                                            \
+    auto kern = threads <= 320 ? k_spmm_sweep<ND, 320> : k_spmm_sweep<ND, 512>;              \
     const int nr = 2 * amax + 1 + kSweepPrefetch;                                            \
     const size_t smem = sweep_smem_bytes(nr, slot_floats, threads);                          \
     if (smem > 48 * 1024)                                                                    \
