@@ -9,8 +9,11 @@
 // n, nnz, SM count, step shape) in memory and, when LOGDET_TUNE_CACHE names
 // a file, on disk (one line per shape).  A tuned layout changes the
 // order of the fixed-order partial sums, so its results differ from the
-// default layout's at rounding level only.
+// default layout's at rounding level only.  For FP32 blocks of a matrix with
+// line structure the SpMM pass of each candidate is the line sweep (its own
+// cache key), since that is the kernel the solve will run.
 #include "dense.cuh"
+#include "dia.cuh"
 #include "krylov.cuh"
 #include "solve.cuh"
 #include "tune.cuh"
@@ -76,7 +79,11 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
   ndots = std::max(1, std::min(ndots, kMaxWin - 1));
   nbasis = std::max(1, std::min(nbasis, kMaxWin - 1));
   extra = extra ? 1 : 0;
-  const int kind = std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2;
+  const bool sw_ok = std::is_same<T, float>::value && h->kind == 0 && h->dia.ndiag > 0 &&
+                     h->dia_slot != nullptr;
+  const int kind = std::is_same<T, double>::value ? 0
+                   : std::is_same<T, float>::value ? (sw_ok ? 3 : 1)
+                                                   : 2;
   const Key key(kind, ld, n, nnz, sm_count(), ndots, nbasis, extra);
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -121,6 +128,19 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
     int cnt = 0;
     LD_TRY(spmm_items(h, g.tile_rows, &items, &cnt));
     max_slots = std::max(max_slots, std::max(cnt, div_up(n, g.tile_rows)));
+    SweepGeom sg;
+    if (sw_ok && dia_sweep_geom(h, ld / c.split, g.threads, &sg))
+      max_slots = std::max(max_slots, sg.units);
+  }
+  // Line sweep: FP32 values per row and diagonal (unscaled: only the time
+  // counts) and the wait-failure flag.
+  DevBuf<float> dvals(st);
+  DevBuf<int> derr(st);
+  if (sw_ok) {
+    LD_TRY(dvals.alloc((size_t)dia_pad(h->dia.ndiag) * n));
+    LD_TRY(dia_values_f32(h, 1.0, dvals.p, st));
+    LD_TRY(derr.alloc(1));
+    LD_TRY(derr.zero());
   }
   LD_TRY(part.alloc((size_t)std::max(ndots, 2) * ld * max_slots));
   LD_TRY(coef.alloc((size_t)kMaxWin * ld));
@@ -140,6 +160,8 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
     const int4* items = nullptr;
     int nitems = 0;
     LD_TRY(spmm_items(h, g.tile_rows, &items, &nitems));
+    SweepGeom sg;
+    const bool use_sw = sw_ok && !items && dia_sweep_geom(h, width, g.threads, &sg);
     std::vector<SpmmJob<T>> sj;
     std::vector<UpdJob<T>> uj;
     for (int q = 0; q < c.split; ++q) {
@@ -162,6 +184,19 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
       J.tile_rows = g.tile_rows;
       J.ntiles = items ? nitems : ntiles;
       J.items = items;
+      if constexpr (std::is_same<T, float>::value) {
+        if (use_sw) {
+          J.ntiles = sg.units;
+          J.dia = dvals.p;
+          J.err = derr.p;
+          J.dia_T = sg.T;
+          J.dia_kc = sg.kc;
+          J.dia_nseg = sg.nseg;
+          J.dia_nlines = sg.nlines;
+          J.dinfo = h->dia;
+          LD_TRY(dia_encode(J, x.p, n, ld, width));
+        }
+      }
       sj.push_back(J);
       UpdJob<T> U;
       memset(&U, 0, sizeof U);
