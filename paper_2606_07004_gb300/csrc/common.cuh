@@ -196,6 +196,70 @@ struct AccF {
   __device__ __forceinline__ double value() const { return (double)s + (double)e; }
 };
 
+// Two compensated FP32 accumulators in packed pairs (Blackwell's
+// add/sub/mul/fma .rn.f32x2: two IEEE single-precision operations per
+// instruction, each lane rounded exactly as the scalar _rn intrinsic).  Lane
+// i performs exactly the operations of an AccF in the same order, so
+// lo()/hi() equal what two AccF would hold; the instruction count halves.
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+struct AccF2 {
+  unsigned long long s, e;
+  __device__ __forceinline__ void zero() { s = 0ull; e = 0ull; }
+  // s + e += a * b per lane: TwoProduct (product and its FMA error), TwoSum.
+  __device__ __forceinline__ void fma(unsigned long long a, unsigned long long b) {
+    const unsigned long long p = f2_mul(a, b);
+    const unsigned long long pe = f2_fma(a, b, p ^ 0x8000000080000000ull);  // a b - p
+    const unsigned long long t = f2_add(s, p);
+    const unsigned long long bp = f2_sub(t, s);
+    const unsigned long long err = f2_add(f2_sub(s, f2_sub(t, bp)), f2_sub(p, bp));
+    s = t;
+    e = f2_add(e, err);
+    e = f2_add(e, pe);
+  }
+  __device__ __forceinline__ AccF lo() const {
+    AccF r;
+    float sh, eh;
+    f2_unpack(s, r.s, sh);
+    f2_unpack(e, r.e, eh);
+    return r;
+  }
+  __device__ __forceinline__ AccF hi() const {
+    AccF r;
+    float sl, el;
+    f2_unpack(s, sl, r.s);
+    f2_unpack(e, el, r.e);
+    return r;
+  }
+};
+
 template <typename T> struct AccOf;
 template <> struct AccOf<double> { using type = AccD; };
 template <> struct AccOf<float>  { using type = AccF; };

@@ -388,11 +388,10 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   };
   produce(0);
 
-  AccF acc[NDOT > 0 ? NDOT : 1][V];
+  // Dot accumulators: columns (0, 1) and (2, 3) of the thread's chunk.
+  AccF2 acc[NDOT > 0 ? NDOT : 1][2];
 #pragma unroll
-  for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[d][v].zero();
+  for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d) acc[d][0].zero(), acc[d][1].zero();
 
   // Constants of the current job.
   int cur_jb = -1, G = 1, R = 1, r = 0, g = 0, width = 0, nd = 0, dp = 0, A = 0, L = 0;
@@ -501,18 +500,20 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
             on[q] = rr + q * R < C.segT && rowbase + rr + q * R < n;
             rq[q] = on[q] ? rr + q * R : rr;  // an absent row re-reads row rr
           }
-          float u[kRows][NDOT > 0 ? NDOT : 1][V];
+          // x, y and the window vectors move as pairs of packed columns
+          // (16 bytes = two f32x2 pairs); the row sums use fma.rn.f32x2,
+          // lane for lane the fmaf of the scalar form.
+          ulonglong2 u[kRows][NDOT > 0 ? NDOT : 1];
 #pragma unroll
           for (int q = 0; q < kRows; ++q)
 #pragma unroll
             for (int d = 0; d < NDOT; ++d)
               if (kEarly && d < ndots && !((selfmask >> d) & 1u))
-                load_vec<float>(J.dotv[d] + (size_t)(rowbase + rq[q]) * ldy + col0, u[q][d]);
-          float sv[kRows][V];
+                u[q][d] = __ldg(reinterpret_cast<const ulonglong2*>(
+                    J.dotv[d] + (size_t)(rowbase + rq[q]) * ldy + col0));
+          unsigned long long s2[kRows][2];
 #pragma unroll
-          for (int q = 0; q < kRows; ++q)
-#pragma unroll
-            for (int v = 0; v < V; ++v) sv[q][v] = 0.f;
+          for (int q = 0; q < kRows; ++q) s2[q][0] = s2[q][1] = 0ull;
           float4 av[kRows];
 #pragma unroll
           for (int d = 0; d < kMaxDiags; ++d) {
@@ -524,12 +525,11 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
                                 : d % 4 == 1 ? av[q].y
                                 : d % 4 == 2 ? av[q].z
                                              : av[q].w;
-                const float4 xv =
-                    *reinterpret_cast<const float4*>(ring + rq[q] * width + g * V + xo[d]);
-                sv[q][0] = fmaf(a, xv.x, sv[q][0]);
-                sv[q][1] = fmaf(a, xv.y, sv[q][1]);
-                sv[q][2] = fmaf(a, xv.z, sv[q][2]);
-                sv[q][3] = fmaf(a, xv.w, sv[q][3]);
+                const unsigned long long a2 = f2_pack(a, a);
+                const ulonglong2 xv =
+                    *reinterpret_cast<const ulonglong2*>(ring + rq[q] * width + g * V + xo[d]);
+                s2[q][0] = f2_fma(a2, xv.x, s2[q][0]);
+                s2[q][1] = f2_fma(a2, xv.y, s2[q][1]);
               }
             }
           }
@@ -537,26 +537,34 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
           for (int q = 0; q < kRows; ++q) {
             if (!on[q]) continue;
             const int row = rowbase + rq[q];
-            float(&s)[V] = sv[q];
-            const float4 xs4 =
-                *reinterpret_cast<const float4*>(ring + rq[q] * width + g * V + xself);
-            const float xs[V] = {xs4.x, xs4.y, xs4.z, xs4.w};
+            const ulonglong2 xs2 =
+                *reinterpret_cast<const ulonglong2*>(ring + rq[q] * width + g * V + xself);
             if (has_shift || has_scale) {
+              float sc[V], xs[V];
+              f2_unpack(s2[q][0], sc[0], sc[1]);
+              f2_unpack(s2[q][1], sc[2], sc[3]);
+              f2_unpack(xs2.x, xs[0], xs[1]);
+              f2_unpack(xs2.y, xs[2], xs[3]);
 #pragma unroll
               for (int v = 0; v < V; ++v) {
-                if (has_shift) s[v] = fmaf((float)J.colshift[col0 + v], xs[v], s[v]);
-                if (has_scale) s[v] = s[v] * (float)J.colscale[col0 + v];
+                if (has_shift) sc[v] = fmaf((float)J.colshift[col0 + v], xs[v], sc[v]);
+                if (has_scale) sc[v] = sc[v] * (float)J.colscale[col0 + v];
               }
+              s2[q][0] = f2_pack(sc[0], sc[1]);
+              s2[q][1] = f2_pack(sc[2], sc[3]);
             }
-            store_vec<float>(yv + (size_t)row * ldy + col0, s);
+            *reinterpret_cast<ulonglong2*>(yv + (size_t)row * ldy + col0) =
+                make_ulonglong2(s2[q][0], s2[q][1]);
 #pragma unroll
             for (int d = 0; d < NDOT; ++d) {
               if (d < ndots) {
                 const bool self = (selfmask >> d) & 1u;
                 if (!kEarly && !self)
-                  load_vec<float>(J.dotv[d] + (size_t)row * ldy + col0, u[q][d]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) acc[d][v].fma(self ? xs[v] : u[q][d][v], s[v]);
+                  u[q][d] = __ldg(reinterpret_cast<const ulonglong2*>(
+                      J.dotv[d] + (size_t)row * ldy + col0));
+                const ulonglong2 uu = self ? xs2 : u[q][d];
+                acc[d][0].fma(uu.x, s2[q][0]);
+                acc[d][1].fma(uu.y, s2[q][1]);
               }
             }
           }
@@ -574,14 +582,14 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
         const int unit = C.gu - B.tile_start[C.jb];
 #pragma unroll
         for (int d = 0; d < NDOT; ++d) {
-          if (d < ndots)
-            cta_reduce_write<float, AccF>(red, acc[d], live, G, R, J.col_off, width,
+          if (d < ndots) {
+            const AccF a4[V] = {acc[d][0].lo(), acc[d][0].hi(), acc[d][1].lo(), acc[d][1].hi()};
+            cta_reduce_write<float, AccF>(red, a4, live, G, R, J.col_off, width,
                                           J.part + (size_t)d * ldy * J.ntiles, J.ntiles, unit);
+          }
         }
 #pragma unroll
-        for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d)
-#pragma unroll
-          for (int v = 0; v < V; ++v) acc[d][v].zero();
+        for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d) acc[d][0].zero(), acc[d][1].zero();
       }
       __syncthreads();  // every read of the released windows is done
       produce(last ? t0 + nwin : t0 + j + 1);
