@@ -337,10 +337,13 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // Ring protocol (uniform across the CTA): load t (a window) goes to slot
 // t % nr and completes phase (t / nr) & 1 of that slot's mbarrier.  The
 // producer issues load t once load t - nr has been released, i.e. the CTA
-// has passed the __syncthreads after its last read: window q of a unit is
-// released after line q (all its windows after the unit's last line).  As
-// nr >= 2A + 3, the two windows after the ones the current line needs are
-// in flight while it is computed.  Waits are bounded: if one gives up, the
+// has passed a barrier after its last read: window q of a unit is released
+// by the barrier that starts line q + 1 (all its windows by the barrier
+// after the unit's last line).  One barrier per line: after the threads
+// have waited for the line's new window, the barrier also releases the
+// window the previous line read last, and after the line thread 0 refills
+// that slot, so nr - 2A - 2 windows beyond the current line's are in
+// flight while it is computed.  Waits are bounded: if one gives up, the
 // CTA decides together (__syncthreads_or), waits once more for every copy
 // still in flight, sets the job's error flag and returns.
 //
@@ -442,9 +445,12 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
     const int nwin = C.nl + 2 * A;
     for (int j = 0; j < C.nl; ++j) {
       // Windows of line k0 + j: loads t0 + j .. t0 + j + 2A (only the last
-      // is new after the first line).
-      bool ok = true;
+      // is new after the first line).  Every thread waits (try_wait
+      // suspends the thread until the phase completes or a time limit
+      // passes); the barrier then also marks line j - 1's reads done,
+      // releasing window t0 + j - 1.
       const int tw = t0 + j + 2 * A;
+      bool ok = true;
       while (ok && wnext <= tw) {
         ok = mbar_wait_bounded(bar0 + 8 * wslot, (phases >> wslot) & 1u);
         if (ok) {
@@ -590,9 +596,11 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
         }
 #pragma unroll
         for (int d = 0; d < (NDOT > 0 ? NDOT : 1); ++d) acc[d][0].zero(), acc[d][1].zero();
+        __syncthreads();  // every read of the unit's windows is done
+        produce(t0 + nwin);
+      } else {
+        produce(t0 + j);  // window t0 + j - 1: released by this line's barrier
       }
-      __syncthreads();  // every read of the released windows is done
-      produce(last ? t0 + nwin : t0 + j + 1);
       if (++rslot == nr) rslot = 0;
     }
     // The next unit's window 0 follows this unit's last 2A windows.
