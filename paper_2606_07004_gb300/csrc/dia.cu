@@ -347,9 +347,9 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // CTA decides together (__syncthreads_or), waits once more for every copy
 // still in flight, sets the job's error flag and returns.
 //
-// The window-offset table: entry [rot][d] is the shared-memory offset
-// (floats from the ring base) of the first x row diagonal d reads when the
-// current line's window 0 is load index rot (mod nr).
+// The window-offset table: entry [rot][d] is the byte offset (from the
+// start of dynamic shared memory) of the first x row diagonal d reads when
+// the current line's window 0 is load index rot (mod nr).
 // ---------------------------------------------------------------------------
 // MAXT: the largest CTA the instance takes (320 or 512); with at most two
 // dots, two CTAs per SM are asked for (the register budget follows).
@@ -363,7 +363,10 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   const int tab_bytes = (nr * kMaxDiags * 4 + 127) / 128 * 128;
   AccF* red = reinterpret_cast<AccF*>(smem_raw + 128 + tab_bytes);
   const int red_bytes = ((int)blockDim.x * V * (int)sizeof(AccF) + 127) / 128 * 128;
-  float* ring = reinterpret_cast<float*>(smem_raw + 128 + tab_bytes + red_bytes);
+  // Shared-memory addresses below are byte offsets from smem_raw (32-bit
+  // arithmetic, immediate offsets where they are compile-time).
+  const int ring_bytes = 128 + tab_bytes + red_bytes;
+  float* ring = reinterpret_cast<float*>(smem_raw + ring_bytes);
 
   SwUnit C;
   sw_unit(C, B, blockIdx.x);
@@ -438,7 +441,10 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       // (every read of the previous table ended before the last barrier)
       for (int e = threadIdx.x; e < nr * kMaxDiags; e += blockDim.x) {
         const int rot = e / kMaxDiags, d = e - rot * kMaxDiags;
-        xo_tab[e] = d < nd ? ((rot + A + D.line[d]) % nr) * slot_floats + D.cpos[d] * width : 0;
+        xo_tab[e] = d < nd ? ring_bytes +
+                                 (((rot + A + D.line[d]) % nr) * slot_floats + D.cpos[d] * width) *
+                                     (int)sizeof(float)
+                           : 0;
       }
       __syncthreads();
     }
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
         }
         const int xself = xt[dself];
         const int vslot = rslot + 2 * A < nr ? rslot + 2 * A : rslot + 2 * A - nr;
-        const float* vs = ring + (size_t)vslot * slot_floats + win_floats;
+        const int vs_b = ring_bytes + (vslot * slot_floats + win_floats) * (int)sizeof(float);
         const int rowbase = C.seg0 + (C.k0 + j) * L;
         const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
         // Window vectors other than x itself are loaded before the sums, so
@@ -517,6 +523,12 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
               if (kEarly && d < ndots && !((selfmask >> d) & 1u))
                 u[q][d] = __ldg(reinterpret_cast<const ulonglong2*>(
                     J.dotv[d] + (size_t)(rowbase + rq[q]) * ldy + col0));
+          int xb[kRows], vb[kRows];  // byte offsets of the row's chunk and values
+#pragma unroll
+          for (int q = 0; q < kRows; ++q) {
+            xb[q] = (rq[q] * width + g * V) * (int)sizeof(float);
+            vb[q] = vs_b + rq[q] * dp * (int)sizeof(float);
+          }
           unsigned long long s2[kRows][2];
 #pragma unroll
           for (int q = 0; q < kRows; ++q) s2[q][0] = s2[q][1] = 0ull;
@@ -526,14 +538,15 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
             if (d < nd) {
 #pragma unroll
               for (int q = 0; q < kRows; ++q) {
-                if (d % 4 == 0) av[q] = *reinterpret_cast<const float4*>(vs + rq[q] * dp + d);
+                if (d % 4 == 0)
+                  av[q] = *reinterpret_cast<const float4*>(smem_raw + vb[q] + 4 * d);
                 const float a = d % 4 == 0   ? av[q].x
                                 : d % 4 == 1 ? av[q].y
                                 : d % 4 == 2 ? av[q].z
                                              : av[q].w;
                 const unsigned long long a2 = f2_pack(a, a);
                 const ulonglong2 xv =
-                    *reinterpret_cast<const ulonglong2*>(ring + rq[q] * width + g * V + xo[d]);
+                    *reinterpret_cast<const ulonglong2*>(smem_raw + xb[q] + xo[d]);
                 s2[q][0] = f2_fma(a2, xv.x, s2[q][0]);
                 s2[q][1] = f2_fma(a2, xv.y, s2[q][1]);
               }
@@ -543,8 +556,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
           for (int q = 0; q < kRows; ++q) {
             if (!on[q]) continue;
             const int row = rowbase + rq[q];
-            const ulonglong2 xs2 =
-                *reinterpret_cast<const ulonglong2*>(ring + rq[q] * width + g * V + xself);
+            const ulonglong2 xs2 = *reinterpret_cast<const ulonglong2*>(smem_raw + xb[q] + xself);
             if (has_shift || has_scale) {
               float sc[V], xs[V];
               f2_unpack(s2[q][0], sc[0], sc[1]);
