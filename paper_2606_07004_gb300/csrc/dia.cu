@@ -352,10 +352,14 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // the current line's window 0 is load index rot (mod nr).
 // ---------------------------------------------------------------------------
 // MAXT: the largest CTA the instance takes (320 or 512); with at most two
-// dots, two CTAs per SM are asked for (the register budget follows).
-template <int NDOT, int MAXT>
+// dots, two CTAs per SM are asked for (the register budget follows).  NDC:
+// the diagonal count when every job of the launch has it (5: 2D Laplacian,
+// 13: Matérn), fixed at compile time, which removes a third of the
+// instructions; 0 = any count up to kMaxDiags.
+template <int NDOT, int MAXT, int NDC>
 __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
     k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr) {
+  constexpr int kDiags = NDC > 0 ? NDC : kMaxDiags;
   constexpr int V = 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const uint32_t bar0 = smem_addr(smem_raw);  // nr barriers, 8 bytes apart
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       g = threadIdx.x - r * G;
       live = r < R;
       width = J.width;
-      nd = D.ndiag;
+      nd = NDC > 0 ? NDC : D.ndiag;
       dp = dia_pad(nd);
       A = D.A;
       L = D.L;
@@ -476,10 +480,10 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       }
       if (live) {
         const int* xt = xo_tab + rslot * kMaxDiags;
-        int xo[kMaxDiags];
+        int xo[kDiags + 3 & ~3];
 #pragma unroll
-        for (int q = 0; q < kMaxDiags / 4; ++q) {
-          if (4 * q < nd) {
+        for (int q = 0; q < (kDiags + 3) / 4; ++q) {
+          if (NDC > 0 || 4 * q < nd) {
             const int4 o = reinterpret_cast<const int4*>(xt)[q];
             xo[4 * q] = o.x;
             xo[4 * q + 1] = o.y;
@@ -534,8 +538,8 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
           for (int q = 0; q < kRows; ++q) s2[q][0] = s2[q][1] = 0ull;
           float4 av[kRows];
 #pragma unroll
-          for (int d = 0; d < kMaxDiags; ++d) {
-            if (d < nd) {
+          for (int d = 0; d < kDiags; ++d) {
+            if (NDC > 0 || d < nd) {
 #pragma unroll
               for (int q = 0; q < kRows; ++q) {
                 if (d % 4 == 0)
@@ -651,10 +655,15 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
   }
   int slot_floats = 0, amax = 0;
   sweep_launch_geom(b, &slot_floats, &amax);
+  int ndc = b.jobs[0].dinfo.ndiag;
+  for (int j = 1; j < b.njobs; ++j)
+    if (b.jobs[j].dinfo.ndiag != ndc) ndc = 0;
+  if (ndc != 5 && ndc != 13) ndc = 0;
   ProfScope prof(KC_SPMM, s, flops, bytes);
+#define LD_SW_KERN(ND, NC) (threads <= 320 ? k_spmm_sweep<ND, 320, NC> : k_spmm_sweep<ND, 512, NC>)
 #define LD_SW_CASE(ND)                                                                       \
   {                                                                                          \
-    auto kern = threads <= 320 ? k_spmm_sweep<ND, 320> : k_spmm_sweep<ND, 512>;              \
+    auto kern = ndc == 13 ? LD_SW_KERN(ND, 13) : ndc == 5 ? LD_SW_KERN(ND, 5) : LD_SW_KERN(ND, 0); \
     const int nr = 2 * amax + 1 + kSweepPrefetch;                                            \
     const size_t smem = sweep_smem_bytes(nr, slot_floats, threads);                          \
     if (smem > 48 * 1024)                                                                    \
@@ -674,6 +683,7 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
     LD_SW_CASE(kMaxWin)
   } while (0);
 #undef LD_SW_CASE
+#undef LD_SW_KERN
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
