@@ -336,31 +336,50 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 #pragma unroll
         for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? CT(J.coef[i * J.ld + col0 + v]) : CT(0);
 
-      for (int row = row0 + r; row < row1; row += R) {
-        const size_t off = (size_t)row * J.ld + col0;
-        CT o[V];
-        load_vec<T>(J.y + off, o);
-        if (!unit) {
+      // kU rows per thread at a time (rows row, row + R): every load of
+      // both rows is issued before their arithmetic, doubling the bytes in
+      // flight of the HBM-bound FP32 and BF16 passes (FP64 is bound by its
+      // ALU and keeps one row); each row's operations, and the order in
+      // which the rows enter the norm, are those of one row at a time.
+      constexpr int kU = (!std::is_same<T, double>::value && NB <= 4) ? 2 : 1;
+      for (int row = row0 + r; row < row1; row += kU * R) {
+        bool on[kU];
+        size_t off[kU];
 #pragma unroll
-          for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
+        for (int q = 0; q < kU; ++q) {
+          on[q] = row + q * R < row1;
+          off[q] = (size_t)(on[q] ? row + q * R : row) * J.ld + col0;
+        }
+        CT o[kU][V], ub[kU][NB > 0 ? NB : 1][V], ue[kU][V];
+#pragma unroll
+        for (int q = 0; q < kU; ++q) {
+          load_vec<T>(J.y + off[q], o[q]);
+#pragma unroll
+          for (int i = 0; i < NB; ++i)
+            if (i < nb) load_vec<T>(J.basis[i] + off[q], ub[q][i]);
+          if (has_extra) load_vec<T>(J.extra + off[q], ue[q]);
         }
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-          if (i < nb) {
-            CT u[V];
-            load_vec<T>(J.basis[i] + off, u);
+        for (int q = 0; q < kU; ++q) {
+          if (!on[q]) continue;
+          if (!unit) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[v], o[v]);
+            for (int v = 0; v < V; ++v) o[q][v] = o[q][v] * yc[v];
           }
-        }
-        store_vec<T>(J.out + off, o);
 #pragma unroll
-        for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
-        if (has_extra) {
-          CT u[V];
-          load_vec<T>(J.extra + off, u);
+          for (int i = 0; i < NB; ++i) {
+            if (i < nb) {
 #pragma unroll
-          for (int v = 0; v < V; ++v) ex[v].fma(u[v], o[v]);
+              for (int v = 0; v < V; ++v) o[q][v] = fma(-cf[i][v], ub[q][i][v], o[q][v]);
+            }
+          }
+          store_vec<T>(J.out + off[q], o[q]);
+#pragma unroll
+          for (int v = 0; v < V; ++v) nrm[v].fma(o[q][v], o[q][v]);
+          if (has_extra) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) ex[v].fma(ue[q][v], o[q][v]);
+          }
         }
       }
     }
