@@ -338,10 +338,12 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
 
       // kU rows per thread at a time (rows row, row + R): every load of
       // both rows is issued before their arithmetic, doubling the bytes in
-      // flight of the HBM-bound FP32 and BF16 passes (FP64 is bound by its
-      // ALU and keeps one row); each row's operations, and the order in
-      // which the rows enter the norm, are those of one row at a time.
-      constexpr int kU = (!std::is_same<T, double>::value && NB <= 4) ? 2 : 1;
+      // flight of the HBM-bound FP32 pass; each row's operations, and the
+      // order in which the rows enter the norm, are those of one row at a
+      // time.  (FP64 is bound by its ALU; BF16 blocks measured 2x slower
+      // with two rows: their registers cost occupancy.)
+      constexpr int kU = (std::is_same<T, float>::value && NB <= 4) ? 2 : 1;
+      if constexpr (kU > 1) {
       for (int row = row0 + r; row < row1; row += kU * R) {
         bool on[kU];
         size_t off[kU];
@@ -381,6 +383,35 @@ __global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch
             for (int v = 0; v < V; ++v) ex[v].fma(ue[q][v], o[q][v]);
           }
         }
+      }
+      } else {
+      for (int row = row0 + r; row < row1; row += R) {
+        const size_t off = (size_t)row * J.ld + col0;
+        CT o[V];
+        load_vec<T>(J.y + off, o);
+        if (!unit) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i < nb) {
+            CT u[V];
+            load_vec<T>(J.basis[i] + off, u);
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[v], o[v]);
+          }
+        }
+        store_vec<T>(J.out + off, o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
+        if (has_extra) {
+          CT u[V];
+          load_vec<T>(J.extra + off, u);
+#pragma unroll
+          for (int v = 0; v < V; ++v) ex[v].fma(u[v], o[v]);
+        }
+      }
       }
     }
     cta_reduce_write<T, Acc>(smem, nrm, live, G, R, J.col_off, J.width, J.part, J.ntiles, tile);
