@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -247,7 +248,10 @@ int dia_encode(SpmmJob<float>& J, const float* x, int n, int ld, int width) {
 // ---------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX)
 // ---------------------------------------------------------------------------
-constexpr int kDiaWaitLimit = 1 << 20;  // try_wait polls before a wait is abandoned
+// A wait gives up after wait_ns of the global timer (2 s in normal use), or
+// after kDiaWaitPolls polls whatever the timer says.
+constexpr int kDiaWaitPolls = 1 << 24;
+constexpr unsigned long long kDiaWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -269,10 +273,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for the barrier's phase to complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase) {
-  for (int i = 0; i < kDiaWaitLimit; ++i)
-    if (mbar_try_wait(bar, phase)) return true;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
+                                                  unsigned long long wait_ns) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < kDiaWaitPolls; i += 32) {
+    for (int k = 0; k < 32; ++k)
+      if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > wait_ns) return false;
+  }
   return false;
 }
 // 2D tiled copy of the box at (x = column, y = row) into shared memory.
@@ -313,14 +328,14 @@ __device__ __forceinline__ void sw_unit(SwUnit& U, const SpmmBatch<float>& B, in
 // Thread 0: arm the slot's barrier with the window's byte count and issue
 // its copies.
 __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit& U, int q,
-                                         float* slot, uint32_t bar) {
+                                         float* slot, uint32_t bar, unsigned extra_tx) {
   const SpmmJob<float>& J = B.jobs[U.jb];
   const DiaInfo& D = J.dinfo;
   const int T = J.dia_T;
   const int dp = dia_pad(D.ndiag);
   const bool vals = q >= 2 * D.A;
   const uint32_t bytes =
-      (uint32_t)(((T + D.cw) * J.width + (vals ? T * dp : 0)) * (int)sizeof(float));
+      (uint32_t)(((T + D.cw) * J.width + (vals ? T * dp : 0)) * (int)sizeof(float)) + extra_tx;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_expect_tx(bar, bytes);
   tma_load_2d(smem_addr(slot), &J.tmap, J.col_off, U.seg0 + (U.k0 - D.A + q) * D.L + D.cmin, bar);
@@ -343,9 +358,10 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // have waited for the line's new window, the barrier also releases the
 // window the previous line read last, and after the line thread 0 refills
 // that slot, so nr - 2A - 2 windows beyond the current line's are in
-// flight while it is computed.  Waits are bounded: if one gives up, the
-// CTA decides together (__syncthreads_or), waits once more for every copy
-// still in flight, sets the job's error flag and returns.
+// flight while it is computed.  Waits are bounded (wait_ns of the global
+// timer): if one gives up, the CTA decides together (__syncthreads_or),
+// waits once more for every copy still in flight, sets the job's error flag
+// and returns.
 //
 // The window-offset table: entry [rot][d] is the byte offset (from the
 // start of dynamic shared memory) of the first x row diagonal d reads when
@@ -358,7 +374,8 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // instructions; 0 = any count up to kMaxDiags.
 template <int NDOT, int MAXT, int NDC>
 __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
-    k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr) {
+    k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr,
+                 unsigned extra_tx, unsigned long long wait_ns) {
   constexpr int kDiags = NDC > 0 ? NDC : kMaxDiags;
   constexpr int V = 4;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -387,7 +404,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   auto produce = [&](int released) {
     while (P.gu < B.total_tiles && issued < released + nr) {
       if (threadIdx.x == 0)
-        sw_issue(B, P, pq, ring + (size_t)pslot * slot_floats, bar0 + 8 * pslot);
+        sw_issue(B, P, pq, ring + (size_t)pslot * slot_floats, bar0 + 8 * pslot, extra_tx);
       ++issued;
       if (++pslot == nr) pslot = 0;
       if (++pq == P.nl + 2 * B.jobs[P.jb].dinfo.A) {
@@ -462,7 +479,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       const int tw = t0 + j + 2 * A;
       bool ok = true;
       while (ok && wnext <= tw) {
-        ok = mbar_wait_bounded(bar0 + 8 * wslot, (phases >> wslot) & 1u);
+        ok = mbar_wait_bounded(bar0 + 8 * wslot, (phases >> wslot) & 1u, wait_ns);
         if (ok) {
           phases ^= 1u << wslot;
           ++wnext;
@@ -472,7 +489,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       if (__syncthreads_or(!ok)) {
         // Copies still in flight: loads wnext .. issued - 1 (distinct slots).
         for (int t = wnext, sl = wslot; t < issued; ++t) {
-          mbar_wait_bounded(bar0 + 8 * sl, (phases >> sl) & 1u);
+          mbar_wait_bounded(bar0 + 8 * sl, (phases >> sl) & 1u, wait_ns);
           if (++sl == nr) sl = 0;
         }
         if (threadIdx.x == 0) atomicExch(J.err, 1);
@@ -655,6 +672,13 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
   }
   int slot_floats = 0, amax = 0;
   sweep_launch_geom(b, &slot_floats, &amax);
+  // Test hook: LOGDET_TEST_SWEEP_STALL=1 arms every barrier for 16 bytes
+  // more than its copies deliver, so that every wait runs out (after 20 ms)
+  // and the solve fails with LOGDET_ETIMEOUT; nothing faults or hangs.
+  const char* stall_env = getenv("LOGDET_TEST_SWEEP_STALL");
+  const bool stall = stall_env && stall_env[0] == '1';
+  const unsigned extra_tx = stall ? 16u : 0u;
+  const unsigned long long wait_ns = stall ? 20000000ull : kDiaWaitNs;
   int ndc = b.jobs[0].dinfo.ndiag;
   for (int j = 1; j < b.njobs; ++j)
     if (b.jobs[j].dinfo.ndiag != ndc) ndc = 0;
@@ -672,7 +696,7 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);             \
     if (per_sm < 1) per_sm = 1;                                                              \
     const int grid = std::max(1, std::min(b.total_tiles, per_sm * sm_count()));              \
-    kern<<<grid, threads, smem, s>>>(b, slot_floats, nr);                                    \
+    kern<<<grid, threads, smem, s>>>(b, slot_floats, nr, extra_tx, wait_ns);                 \
     break;                                                                                   \
   }
   do {

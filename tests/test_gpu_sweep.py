@@ -116,3 +116,47 @@ def test_sweep_wide_block_deterministic_server_and_plan():
             want = hs.osaiop(30, 12, iop_window=4, seed=s, precision=B.MIXED_FP32)
             _same(served[s], want)
             _same(replay[s], want)
+
+
+def test_sweep_mixed_batch_in_server():
+    # One server batch holds sweep jobs of different stencils (5 and 13
+    # diagonals, A = 1 and 2, one ragged last line), a CSR job (3D stencil)
+    # and both methods: the launch takes the generic diagonal-count instance
+    # and the largest ring.  Each result must equal the same request alone.
+    mats = [W.laplacian_2d(100, 90, shift=0.05), W.matern_2d(70, 0.05, dtype=np.float32),
+            _band(64, 5001), W.laplacian_3d(24, 21, 19, shift=0.01)]
+    hs = [B.Handle.from_csr(A) for A in mats]
+    try:
+        reqs = []
+        for i, h in enumerate(hs):
+            reqs.append((h, B.METHOD_OSLQ, 0, i, 0.0))
+            reqs.append((h, B.METHOD_OSAIOP, 4, 10 + i, 0.02))
+        with B.Server(8 << 30) as srv:
+            ids = [srv.submit(h, meth, 30, 12, k, seed=sd, precision=B.MIXED_FP32, shift=sh)
+                   for h, meth, k, sd, sh in reqs]
+            got = [srv.wait(i) for i in ids]
+        for (h, meth, k, sd, sh), g in zip(reqs, got):
+            if meth == B.METHOD_OSLQ:
+                want = h.oslq(30, 12, seed=sd, precision=B.MIXED_FP32, shift=sh)
+            else:
+                want = h.osaiop(30, 12, iop_window=k, seed=sd, precision=B.MIXED_FP32, shift=sh)
+            _same(g, want)
+    finally:
+        for h in hs:
+            h.close()
+
+
+def test_sweep_wait_timeout_reports_and_recovers(monkeypatch):
+    # LOGDET_TEST_SWEEP_STALL=1 arms each ring barrier for 16 bytes more than
+    # its copies deliver: every bounded wait runs out (20 ms), the CTAs wait
+    # for their copies, flag the job and return.  The solve must fail with
+    # LOGDET_ETIMEOUT and the next solve on the same handle must be exact.
+    A = W.laplacian_2d(100, 90, shift=0.05)
+    with B.Handle.from_csr(A) as h:
+        want = h.oslq(30, 6, seed=1, precision=B.MIXED_FP32)
+        monkeypatch.setenv("LOGDET_TEST_SWEEP_STALL", "1")
+        with pytest.raises(B.LogdetError) as e:
+            h.oslq(30, 6, seed=1, precision=B.MIXED_FP32)
+        assert e.value.code == B.ETIMEOUT
+        monkeypatch.delenv("LOGDET_TEST_SWEEP_STALL")
+        _same(h.oslq(30, 6, seed=1, precision=B.MIXED_FP32), want)
