@@ -424,6 +424,8 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   int cur_jb = -1, G = 1, R = 1, r = 0, g = 0, width = 0, nd = 0, dp = 0, A = 0, L = 0;
   int win_floats = 0, dself = 0, col0 = 0, ldy = 0, ndots = 0, n = 0;
   float* yv = nullptr;
+  float csh[V], csc[V];
+  bool has_shift = false, has_scale = false;
   unsigned selfmask = 0;
   bool live = false;
 
@@ -453,6 +455,15 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       for (int d = 0; d < nd; ++d)
         if (D.off[d] == 0) dself = d;
       col0 = J.col_off + g * V;
+      // The thread's column shift and scale, converted once per job (the
+      // conversion from FP64 runs on the FP64 pipe, slow on this GPU).
+      has_shift = J.colshift != nullptr;
+      has_scale = J.colscale != nullptr;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        csh[v] = has_shift ? (float)J.colshift[col0 + v] : 0.f;
+        csc[v] = has_scale ? (float)J.colscale[col0 + v] : 1.f;
+      }
       ldy = J.ld;
       yv = J.y;
       ndots = J.ndots;
@@ -514,7 +525,6 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
         const int vslot = rslot + 2 * A < nr ? rslot + 2 * A : rslot + 2 * A - nr;
         const int vs_b = ring_bytes + (vslot * slot_floats + win_floats) * (int)sizeof(float);
         const int rowbase = C.seg0 + (C.k0 + j) * L;
-        const bool has_scale = J.colscale != nullptr, has_shift = J.colshift != nullptr;
         // Window vectors other than x itself are loaded before the sums, so
         // that their latency overlaps them (up to four; the registers of
         // more would spill).
@@ -586,8 +596,8 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
               f2_unpack(xs2.y, xs[2], xs[3]);
 #pragma unroll
               for (int v = 0; v < V; ++v) {
-                if (has_shift) sc[v] = fmaf((float)J.colshift[col0 + v], xs[v], sc[v]);
-                if (has_scale) sc[v] = sc[v] * (float)J.colscale[col0 + v];
+                if (has_shift) sc[v] = fmaf(csh[v], xs[v], sc[v]);
+                if (has_scale) sc[v] = sc[v] * csc[v];
               }
               s2[q][0] = f2_pack(sc[0], sc[1]);
               s2[q][1] = f2_pack(sc[2], sc[3]);

@@ -250,6 +250,11 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
       }
     }
     if (yo < ny) {
+      // The shift of the thread's columns, converted once (for FP32 blocks
+      // the conversion from FP64 runs on the FP64 pipe).
+      CT csh[V];
+#pragma unroll
+      for (int c = 0; c < V; ++c) csh[c] = colshift ? CT(colshift[col0 + c]) : CT(0);
 #pragma unroll
       for (int q = 0; q < P; ++q) {
         const int xo = x0 + tx * P + q;
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(kGridThreads) k_grid_apply(
           CT xr[V];
           load_vec<T>(x + off, xr);
 #pragma unroll
-          for (int c = 0; c < V; ++c) acc[q][c] = fma(CT(colshift[col0 + c]), xr[c], acc[q][c]);
+          for (int c = 0; c < V; ++c) acc[q][c] = fma(csh[c], xr[c], acc[q][c]);
         }
         store_vec<T>(y + off, acc[q]);
       }
