@@ -1102,19 +1102,6 @@ int fill_double(double* out, size_t count, double value, cudaStream_t st) {
   return LOGDET_OK;
 }
 
-__global__ void k_fill_float(float* out, size_t count, float value) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
-       i += (size_t)gridDim.x * blockDim.x)
-    out[i] = value;
-}
-
-int fill_float(float* out, size_t count, float value, cudaStream_t st) {
-  ProfScope prof(KC_OTHER, st);
-  k_fill_float<<<std::max(1, std::min(div_up((int)count, 256), 64)), 256, 0, st>>>(out, count, value);
-  LD_CHECK_LAUNCH();
-  return LOGDET_OK;
-}
-
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols) {
   const size_t total = (size_t)n * ldout;

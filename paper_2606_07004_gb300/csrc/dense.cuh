@@ -61,7 +61,6 @@ int probe_fill(uint64_t key, int n, int ncols, int col0, T* out, int ld, cudaStr
 
 // out[i] = value for i < count.
 int fill_double(double* out, size_t count, double value, cudaStream_t st);
-int fill_float(float* out, size_t count, float value, cudaStream_t st);
 
 // Copy/convert a block with the same layout (FP64 <-> FP32).
 template <typename Tin, typename Tout>

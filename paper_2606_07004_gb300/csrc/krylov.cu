@@ -59,17 +59,6 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
 
-// The diagonal shift of column c in the compute type: FP32 blocks read the
-// FP32 copy when the job has one (no conversion on the FP64 pipe per row).
-template <typename T>
-__device__ __forceinline__ typename Compute<T>::type shift_of(const SpmmJob<T>& J, int c) {
-  if constexpr (std::is_same<T, double>::value) {
-    return J.colshift[c];
-  } else {
-    return J.colshift_f ? J.colshift_f[c] : (float)J.colshift[c];
-  }
-}
-
 template <typename T, int NDOT>
 __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   constexpr int V = Vec16<T>::N;
@@ -161,7 +150,7 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
           load_vec<T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            if (has_shift) t[v] = fma(shift_of(J, col0 + v), xr[v], t[v]);
+            if (has_shift) t[v] = fma(CT(J.colshift[col0 + v]), xr[v], t[v]);
             if (has_scale) t[v] = t[v] * CT(J.colscale[col0 + v]);
           }
         }
@@ -274,7 +263,7 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
           load_vec<T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            if (has_shift) s[v] = fma(shift_of(J, col0 + v), xr[v], s[v]);
+            if (has_shift) s[v] = fma(CT(J.colshift[col0 + v]), xr[v], s[v]);
             if (has_scale) s[v] = s[v] * CT(J.colscale[col0 + v]);
           }
         }

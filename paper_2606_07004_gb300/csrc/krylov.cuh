@@ -44,8 +44,6 @@ struct SpmmJob {
   typename PartOf<T>::type* part;  // [ndots][ld][ntiles]
   const double* colscale;          // optional [ld]: y[:,p] *= colscale[p]
   const double* colshift;          // optional [ld]: y[:,p] += colshift[p] * x[:,p] (before scale)
-  const float* colshift_f;         // optional: colshift rounded to FP32 (FP32 and BF16 blocks
-                                   // read it, saving a conversion on the FP64 pipe per row)
   // Work items.  nullptr: ntiles uniform tiles of tile_rows rows, partial
   // slot = tile.  Otherwise ntiles items in launch order, each {r0, r1, slot,
   // 0}: rows [r0, r1) spread over the CTA's row groups (r1 > r0), or, with

@@ -223,7 +223,6 @@ int KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
     J.ntiles = nslots;
     J.items = items;
     J.colshift = colshift;
-    J.colshift_f = colshift_f;
     if (method == 0) {
       J.ndots = 1;
       J.dotv[0] = ptr(j);
@@ -500,7 +499,6 @@ struct Solve : ISolve {
   DevBuf<float> diav;                        // FP32 values per diagonal (diagonal fast path)
   DevBuf<T> Vst, Xc;
   DevBuf<double> X64, outv, cshift;
-  DevBuf<float> cshift_f;                    // cshift rounded to FP32 (FP32 and BF16 blocks)
   DevBuf<int> keep;
   std::unique_ptr<KRun<T>> run;
   PinnedHost pin;
@@ -512,7 +510,7 @@ struct Solve : ISolve {
   const uint64_t* dev_keys = nullptr;  // graph plans: probe keys in device memory
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
-      : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), diav(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_), cshift_f(st_),
+      : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), diav(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
         keep(st_) {
     n = h->n;
     s = c.plain ? 0 : c.P / 3;
@@ -619,10 +617,6 @@ struct Solve : ISolve {
       const size_t cnt = std::max(ld, lds);
       LD_TRY(cshift.alloc(cnt));
       LD_TRY(fill_double(cshift.p, cnt, c.shift / cscale, st));
-      if (!std::is_same<T, double>::value) {
-        LD_TRY(cshift_f.alloc(cnt));
-        LD_TRY(fill_float(cshift_f.p, cnt, (float)(c.shift / cscale), st));
-      }
     }
     run.reset(new KRun<T>(st));
     if (s == 0) {
@@ -632,7 +626,6 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
-    run->colshift_f = cshift_f.p;
       run->hctx = h;
       run->gtab = gtabs.p;
       run->diavals = diav.p;
@@ -676,7 +669,6 @@ struct Solve : ISolve {
       T* X0;
       LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
-    run->colshift_f = cshift_f.p;
       run->hctx = h;
       run->gtab = gtabs.p;
       run->diavals = diav.p;
@@ -689,7 +681,6 @@ struct Solve : ISolve {
       LD_TRY(Vst.alloc((size_t)n * lds * m));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian, dkey(0)));
       run->colshift = cshift.p;
-    run->colshift_f = cshift_f.p;
       run->hctx = h;
       run->gtab = gtabs.p;
       run->diavals = diav.p;
@@ -734,7 +725,6 @@ struct Solve : ISolve {
     LD_TRY(make_x0(&X0));
     run.reset(new KRun<T>(st));
     run->colshift = cshift.p;
-    run->colshift_f = cshift_f.p;
     run->hctx = h;
     run->gtab = gtabs.p;
     run->diavals = diav.p;
@@ -778,7 +768,6 @@ struct Solve : ISolve {
     gtabs.release();
     diav.release();
     cshift.release();
-    cshift_f.release();
     X64.release();
     Xc.release();
     outv.release();

@@ -83,7 +83,6 @@ struct KRun {
   T* X0 = nullptr;
   T* Vfull = nullptr;
   const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
-  const float* colshift_f = nullptr;  // the same rounded to FP32 (FP32 and BF16 blocks)
   logdet_ctx* hctx = nullptr;        // matrix handle (work items of irregular matrices)
   const void* gtab = nullptr;        // gridded operator: scaled expanded table (compute type)
   TileGeom g{};
