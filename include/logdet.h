@@ -151,15 +151,18 @@ void logdet_destroy(logdet_handle h);
 /* n, nnz and the Gershgorin interval [lo, hi] (unclamped) of the handle. */
 int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* gersh_lo, double* gersh_hi);
 
-/* Line structure found at creation from host CSR arrays (n >= 4096): every
- * entry on one of at most 16 diagonals whose offsets are l * L + c with
- * |l| <= A <= 3 and c within a range of at most 16 (a 2D grid stencil, L the
- * grid's row length).  Mixed-FP32 solves of such a matrix run the SpMM pass
- * as a line sweep (x rows staged by TMA copies into a ring of line windows).
- * *line_stride = L and *lines = A, both 0 when there is no such structure
- * (device-array handles, gridded operators, 3D stencils).  Errors: EINVAL
- * (null pointer). */
-int logdet_line_structure(logdet_handle h, int32_t* line_stride, int32_t* lines);
+/* Grid structure found at creation from host CSR arrays (n >= 4096), which
+ * mixed-FP32 solves use to run the SpMM pass as a sweep over TMA-staged
+ * windows of x instead of CSR gathers.  *dim = 2: every entry on one of at
+ * most 16 diagonals with offsets l * L + c, |l| <= *reach <= 3, c within a
+ * range of at most 16 (a 2D grid stencil, L the grid's row length): a line
+ * sweep.  *dim = 3: a stencil on an L x ny x nz grid (row (z ny + y) L + x)
+ * with offsets dz L ny + dy L + dx, |dz| <= *reach <= 2, |dy| <= 2,
+ * |dx| <= 4, no entry wrapping across a line or plane edge, at most 16
+ * diagonals: a plane sweep.  *line_stride = L.  All three are 0 when there
+ * is no such structure (device-array handles, gridded operators, other
+ * matrices).  Errors: EINVAL (null pointer). */
+int logdet_grid_structure(logdet_handle h, int32_t* dim, int32_t* line_stride, int32_t* reach);
 
 /* ---- estimators --------------------------------------------------------
  * logdet_oslq: Algorithm 3 (OSLQ, Sec. 3): J = Q/alpha with alpha the upper

@@ -35,7 +35,7 @@ ST_BREAKDOWN, ST_NONPOS_RITZ, ST_RANK_DEFICIENT, ST_LOG_FAILED = 1, 2, 4, 8
 EXPORTED = [
     "logdet_opts_default", "logdet_strerror", "logdet_last_error",
     "logdet_create", "logdet_create_device", "logdet_create_grid", "logdet_destroy", "logdet_info",
-    "logdet_line_structure", "logdet_oslq", "logdet_osaiop",
+    "logdet_grid_structure", "logdet_oslq", "logdet_osaiop",
     "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_quadform", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
@@ -98,7 +98,7 @@ _sig("logdet_create_device", C.c_int, [_i32, _P, _P, _P, _i32, C.POINTER(_P)])
 _sig("logdet_create_grid", C.c_int, [_i32, _i32, _i32, _P, C.POINTER(_P)])
 _sig("logdet_destroy", None, [_P])
 _sig("logdet_info", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl)])
-_sig("logdet_line_structure", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i32)])
+_sig("logdet_grid_structure", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)])
 for _n in ("logdet_oslq", "logdet_osaiop"):
     _sig(_n, C.c_int, [_P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts), C.POINTER(logdet_result)])
 _sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
@@ -277,13 +277,14 @@ class Handle:
                "logdet_info")
         return n.value, nnz.value, lo.value, hi.value
 
-    def line_structure(self):
-        """(L, A): line stride and half-width of the line-sweep structure,
-        (0, 0) when the matrix has none."""
-        L, A = _i32(), _i32()
-        _check(_lib.logdet_line_structure(self._h, C.byref(L), C.byref(A)),
-               "logdet_line_structure")
-        return L.value, A.value
+    def grid_structure(self):
+        """(dim, L, reach): 2 = line sweep (line stride L, lines -reach..reach),
+        3 = plane sweep (grid row length L, planes -reach..reach), (0, 0, 0)
+        when the matrix has no grid structure (logdet_grid_structure)."""
+        dim, L, A = _i32(), _i32(), _i32()
+        _check(_lib.logdet_grid_structure(self._h, C.byref(dim), C.byref(L), C.byref(A)),
+               "logdet_grid_structure")
+        return dim.value, L.value, A.value
 
     def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
              lam, stream, shift=0.0, autotune=0, plain=0, gaussian=0):

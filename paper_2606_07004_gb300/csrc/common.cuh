@@ -16,19 +16,25 @@
 
 namespace ld {
 
-// Line structure of a stencil matrix: every entry lies on one of a few
-// diagonals, and each diagonal offset is line * L + c with a line stride L,
-// lines in [-A, A] and small c (a 2D grid stencil: L = the grid's row
-// length).  See dia.cu.
+// Grid structure of a stencil matrix: every entry lies on one of a few
+// diagonals.  dim 2: each diagonal offset is line * L + c with a line
+// stride L, lines in [-A, A] and small c (a 2D grid stencil: L = the grid's
+// row length).  dim 3: the matrix is a stencil on an L x ny x nz grid (row
+// = (z * ny + y) * L + x) with offsets dz * P + dy * L + dx (P = L ny),
+// |dz| <= A, |dy| <= Ay, |dx| <= Ax, and no entry wrapping across a line or
+// plane edge.  See dia.cu.
 constexpr int kMaxDiags = 16;
 struct DiaInfo {
   int ndiag;                  // 0: no such structure
+  int dim;                    // 2 or 3
   int off[kMaxDiags];         // ascending
   int L;                      // line stride
-  int A;                      // lines -A .. A
-  int cmin, cw;               // c ranges over [cmin, cmin + cw]
-  int line[kMaxDiags];        // line of each diagonal
-  int cpos[kMaxDiags];        // c - cmin of each diagonal
+  int A;                      // lines (dim 2) or planes (dim 3) -A .. A
+  int cmin, cw;               // dim 2: c ranges over [cmin, cmin + cw]
+  int line[kMaxDiags];        // line (dim 2) or plane (dim 3) offset of each diagonal
+  int cpos[kMaxDiags];        // dim 2: c - cmin of each diagonal
+  int P, ny, nz, Ay, Ax;      // dim 3: plane stride, grid lines per plane, planes, radii
+  int dy[kMaxDiags], dx[kMaxDiags];  // dim 3: in-plane offsets of each diagonal
 };
 
 

@@ -44,6 +44,54 @@ static int nearest_line(int o, int L) {
   return o >= 0 ? l : -l;
 }
 
+// 3D grid stencil: L = the smallest offset magnitude >= 2 (the line), P =
+// the largest (the plane), ny = P / L, nz = n / P; every offset split as
+// dz P + dy L + dx (nearest), small radii, and no entry whose grid
+// neighbour would wrap across a line or plane edge (so that reading a
+// zero-filled point outside the grid stands for "no entry").
+static bool plane_structure(const std::vector<int>& offs, int n, const int* rowptr,
+                            const int* colind, DiaInfo* out) {
+  int L = INT_MAX, P = 0;
+  for (int o : offs) {
+    const int a = o >= 0 ? o : -o;
+    if (a >= 2) {
+      L = std::min(L, a);
+      P = std::max(P, a);
+    }
+  }
+  if (P == 0 || L < 4 || P % L || P / L < 2 || n % P || n / P < 2) return false;
+  DiaInfo d;
+  memset(&d, 0, sizeof d);
+  d.ndiag = (int)offs.size();
+  d.dim = 3;
+  d.L = L;
+  d.P = P;
+  d.ny = P / L;
+  d.nz = n / P;
+  for (int q = 0; q < d.ndiag; ++q) {
+    const int o = offs[q];
+    d.off[q] = o;
+    d.line[q] = nearest_line(o, P);
+    const int rem = o - d.line[q] * P;
+    d.dy[q] = nearest_line(rem, L);
+    d.dx[q] = rem - d.dy[q] * L;
+    d.A = std::max(d.A, std::abs(d.line[q]));
+    d.Ay = std::max(d.Ay, std::abs(d.dy[q]));
+    d.Ax = std::max(d.Ax, std::abs(d.dx[q]));
+  }
+  if (d.A > kPlaneMaxA || d.Ay > 2 || d.Ax > kPlaneMaxR) return false;
+  for (int i = 0; i < n; ++i) {
+    const int x = i % L, y = (i / L) % d.ny;
+    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+      const int k = (int)(std::lower_bound(offs.begin(), offs.end(), colind[q] - i) - offs.begin());
+      if (x + d.dx[k] < 0 || x + d.dx[k] >= L || y + d.dy[k] < 0 || y + d.dy[k] >= d.ny)
+        return false;
+    }
+  }
+  *out = d;
+  return true;
+}
+
 int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
   memset(&h->dia, 0, sizeof h->dia);
   const int n = h->n;
@@ -73,6 +121,7 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
     DiaInfo d;
     memset(&d, 0, sizeof d);
     d.ndiag = nd;
+    d.dim = 2;
     d.L = L;
     int cmin = INT_MAX, cmax = INT_MIN;
     for (int q = 0; q < nd; ++q) {
@@ -99,7 +148,7 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
       best = d;
     }
   }
-  if (best.ndiag == 0) return LOGDET_OK;
+  if (best.ndiag == 0 && !plane_structure(offs, n, rowptr, colind, &best)) return LOGDET_OK;
   // CSR entry -> diagonal index.
   std::vector<int> slot((size_t)h->nnz);
   for (int i = 0; i < n; ++i)
@@ -144,13 +193,19 @@ int dia_values_f32(const logdet_ctx* h, double c, float* out, cudaStream_t st) {
   return LOGDET_OK;
 }
 
-// Floats of one ring slot: the x window (T + cw rows of width floats), then
-// the values of T rows; each part rounded up to 128 bytes (TMA destinations).
-__host__ __device__ inline int sweep_win_floats(int T, int cw, int width) {
-  return ((T + cw) * width + 31) / 32 * 32;
+// Points of one x window: dim 2, T + cw rows; dim 3, the tile of tx x ty
+// points with its halo of Ax, Ay on each side.
+__host__ __device__ inline int sweep_win_points(const DiaInfo& d, int T, int tx, int ty) {
+  return d.dim == 3 ? (tx + 2 * d.Ax) * (ty + 2 * d.Ay) : T + d.cw;
 }
-static int sweep_slot_floats(const DiaInfo& d, int T, int width) {
-  return sweep_win_floats(T, d.cw, width) + (T * dia_pad(d.ndiag) + 31) / 32 * 32;
+// Floats of one ring slot: the x window (its points x width floats), then the
+// values of T points; each part rounded up to 128 bytes (TMA destinations).
+__host__ __device__ inline int sweep_win_floats(int points, int width) {
+  return (points * width + 31) / 32 * 32;
+}
+static int sweep_slot_floats(const DiaInfo& d, int T, int tx, int ty, int width) {
+  return sweep_win_floats(sweep_win_points(d, T, tx, ty), width) +
+         (T * dia_pad(d.ndiag) + 31) / 32 * 32;
 }
 // Shared memory of a CTA: barriers, the window-offset table (nr rotations x
 // kMaxDiags), the dot reduction (threads x 4 accumulators), the ring.
@@ -167,21 +222,54 @@ bool dia_sweep_geom(const logdet_ctx* h, int width, int threads, SweepGeom* out)
   const int R = threads / G;
   if (R < 1 || threads > 512) return false;
   const int nr = 2 * d.A + 1 + kSweepPrefetch;
-  int T = 0;
-  for (int m = 1;; ++m) {
-    const int t = R * m;
-    if (t + d.cw > 256 || (m > 1 && t > d.L)) break;
-    if (sweep_smem_bytes(nr, sweep_slot_floats(d, t, width), threads) > (size_t)kSweepSmemBudget)
-      break;
-    T = t;
-  }
-  if (T == 0) return false;
   SweepGeom g;
-  g.T = T;
-  g.nseg = (d.L + T - 1) / T;
-  g.nlines = (h->n + d.L - 1) / d.L;
-  // About eight units per SM; at least 4A lines per unit (each unit first
-  // loads 2A windows that only fill the ring).
+  memset(&g, 0, sizeof g);
+  if (d.dim == 3) {
+    // Tile tx x ty (tx a power of two): the smallest DRAM-to-SM traffic per
+    // point, (tx + 2 Ax)(ty + 2 Ay) / (tx ty) times the tiles' overhang of
+    // the grid, that fits the budget; at least R points, and tiles of at
+    // least 2R points (two per thread) are preferred.
+    double best = 1e30;
+    for (int txs = 5; txs >= 3; --txs) {
+      const int tx = 1 << txs;
+      if (tx > 8 && tx / 2 >= d.L) continue;
+      for (int ty = 1; ty <= 16 && ty <= d.ny; ++ty) {
+        const int T = tx * ty;
+        if (T < R || tx + 2 * d.Ax > 256 || ty + 2 * d.Ay > 256) continue;
+        if (sweep_smem_bytes(nr, sweep_slot_floats(d, T, tx, ty, width), threads) >
+            (size_t)kSweepSmemBudget)
+          continue;
+        const double over = (double)((d.L + tx - 1) / tx * tx) / d.L *
+                            ((double)((d.ny + ty - 1) / ty * ty) / d.ny);
+        double cost = (double)(tx + 2 * d.Ax) * (ty + 2 * d.Ay) / T * over;
+        if (T < 2 * R) cost *= 1.15;
+        if (cost < best) {
+          best = cost;
+          g.T = T;
+          g.tx = tx;
+          g.ty = ty;
+          g.txs = txs;
+        }
+      }
+    }
+    if (g.T == 0) return false;
+    g.nseg = (d.L + g.tx - 1) / g.tx * ((d.ny + g.ty - 1) / g.ty);
+    g.nlines = d.nz;
+  } else {
+    for (int m = 1;; ++m) {
+      const int t = R * m;
+      if (t + d.cw > 256 || (m > 1 && t > d.L)) break;
+      if (sweep_smem_bytes(nr, sweep_slot_floats(d, t, 0, 0, width), threads) >
+          (size_t)kSweepSmemBudget)
+        break;
+      g.T = t;
+    }
+    if (g.T == 0) return false;
+    g.nseg = (d.L + g.T - 1) / g.T;
+    g.nlines = (h->n + d.L - 1) / d.L;
+  }
+  // About eight units per SM; at least 4A lines or planes per unit (each
+  // unit first loads 2A windows that only fill the ring).
   const int chunks = std::max(1, 8 * sm_count() / g.nseg);
   g.kc = (g.nlines + chunks - 1) / chunks;
   g.kc = std::min(g.nlines, std::max(g.kc, 4 * d.A));
@@ -215,6 +303,27 @@ static int encode_2d(CUtensorMap* map, const float* base, int inner, int outer, 
   return LOGDET_OK;
 }
 
+// 4D map of an L x ny x nz grid of rows of `inner` floats (pitch floats
+// apart), box of box_inner x bx x by x 1.
+static int encode_grid(CUtensorMap* map, const float* base, const DiaInfo& d, int inner,
+                       int pitch, int box_inner, int bx, int by) {
+  const cuuint64_t dims[4] = {(cuuint64_t)inner, (cuuint64_t)d.L, (cuuint64_t)d.ny,
+                              (cuuint64_t)d.nz};
+  const cuuint64_t rowb = (cuuint64_t)pitch * sizeof(float);
+  const cuuint64_t strides[3] = {rowb, rowb * d.L, rowb * d.P};
+  const cuuint32_t box[4] = {(cuuint32_t)box_inner, (cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LOGDET_ECUDA;
+  }
+  return LOGDET_OK;
+}
+
 int dia_encode(SpmmJob<float>& J, const float* x, int n, int ld, int width) {
   std::call_once(g_encode_once, [] {
     void* fn = nullptr;
@@ -230,16 +339,26 @@ int dia_encode(SpmmJob<float>& J, const float* x, int n, int ld, int width) {
     set_error("cuTensorMapEncodeTiled is not available");
     return LOGDET_ECUDA;
   }
+  const DiaInfo& d = J.dinfo;
   const int T = J.dia_T;
-  const int box_rows = T + J.dinfo.cw;
-  const int dp = dia_pad(J.dinfo.ndiag);
+  const int dp = dia_pad(d.ndiag);
+  const bool grid3 = d.dim == 3;
+  const int bx = J.dia_tx + 2 * d.Ax, by = J.dia_ty + 2 * d.Ay;
+  const int box_rows = T + d.cw;
   // TMA: 16-byte aligned bases and row pitches; the innermost box extent and
   // every innermost coordinate (J.col_off for x, 0 for the values) a
-  // multiple of four floats.
+  // multiple of four floats; box extents at most 256.
   if (((uintptr_t)x & 15) || ((uintptr_t)J.dia & 15) || (ld * 4) % 16 || width > 256 ||
-      width < 4 || width % 4 || J.col_off % 4 || box_rows > 256 || T < 1 || dp > 256) {
-    set_error("line sweep: block not aligned for TMA");
+      width < 4 || width % 4 || J.col_off % 4 || T < 1 || dp > 256 ||
+      (grid3 ? (bx > 256 || by > 256 || J.dia_tx * J.dia_ty != T ||
+                (long long)d.P * d.nz != n)
+             : box_rows > 256)) {
+    set_error("grid sweep: block not aligned for TMA");
     return LOGDET_EINVAL;
+  }
+  if (grid3) {
+    LD_TRY(encode_grid(&J.tmap, x, d, ld, ld, width, bx, by));
+    return encode_grid(&J.vmap, J.dia, d, dp, dp, dp, J.dia_tx, J.dia_ty);
   }
   LD_TRY(encode_2d(&J.tmap, x, ld, n, ld, width, box_rows));
   return encode_2d(&J.vmap, J.dia, dp, n, dp, dp, T);
@@ -290,6 +409,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase,
   }
   return false;
 }
+// 4D tiled copy of the box at (column, x, y, z) into shared memory.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c, int x,
+                                            int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
 // 2D tiled copy of the box at (x = column, y = row) into shared memory.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
                                             uint32_t bar) {
@@ -308,25 +437,38 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 // unit (q = 0 .. nl + 2A - 1) holds line k0 - A + q, and from q = 2A on it
 // also carries the values of line k0 + q - 2A.
 // ---------------------------------------------------------------------------
+// (plane sweep: seg0, segT hold the tile origin x0, y0)
 struct SwUnit {
   int gu, jb, seg0, segT, k0, nl;
 };
 
+template <int DIM>
 __device__ __forceinline__ void sw_unit(SwUnit& U, const SpmmBatch<float>& B, int gu) {
   U.gu = gu;
   if (gu >= B.total_tiles) return;
   U.jb = find_job(B, gu);
   const SpmmJob<float>& J = B.jobs[U.jb];
+  const DiaInfo& D = J.dinfo;
   const int u = gu - B.tile_start[U.jb];
   const int seg = u % J.dia_nseg, chunk = u / J.dia_nseg;
-  U.seg0 = seg * J.dia_T;
-  U.segT = min(J.dia_T, J.dinfo.L - U.seg0);
+  if constexpr (DIM == 3) {
+    const int nsx = (D.L + J.dia_tx - 1) >> J.dia_txs;
+    const int sy = seg / nsx, sx = seg - sy * nsx;
+    U.seg0 = sx << J.dia_txs;  // x0
+    U.segT = sy * J.dia_ty;    // y0
+  } else {
+    U.seg0 = seg * J.dia_T;
+    U.segT = min(J.dia_T, D.L - U.seg0);
+  }
   U.k0 = chunk * J.dia_kc;
   U.nl = min(J.dia_kc, J.dia_nlines - U.k0);
 }
 
 // Thread 0: arm the slot's barrier with the window's byte count and issue
-// its copies.
+// its copies (dim 2: T + cw rows of line k0 - A + q; dim 3: the tile and
+// its halo in plane k0 - A + q; from q = 2A on also the values of line or
+// plane k0 + q - 2A).
+template <int DIM>
 __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit& U, int q,
                                          float* slot, uint32_t bar, unsigned extra_tx) {
   const SpmmJob<float>& J = B.jobs[U.jb];
@@ -334,14 +476,21 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
   const int T = J.dia_T;
   const int dp = dia_pad(D.ndiag);
   const bool vals = q >= 2 * D.A;
+  const int wp = sweep_win_points(D, T, J.dia_tx, J.dia_ty);
   const uint32_t bytes =
-      (uint32_t)(((T + D.cw) * J.width + (vals ? T * dp : 0)) * (int)sizeof(float)) + extra_tx;
+      (uint32_t)((wp * J.width + (vals ? T * dp : 0)) * (int)sizeof(float)) + extra_tx;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_expect_tx(bar, bytes);
-  tma_load_2d(smem_addr(slot), &J.tmap, J.col_off, U.seg0 + (U.k0 - D.A + q) * D.L + D.cmin, bar);
-  if (vals)
-    tma_load_2d(smem_addr(slot + sweep_win_floats(T, D.cw, J.width)), &J.vmap, 0,
-                U.seg0 + (U.k0 + q - 2 * D.A) * D.L, bar);
+  const uint32_t vdst = smem_addr(slot + sweep_win_floats(wp, J.width));
+  if constexpr (DIM == 3) {
+    tma_load_4d(smem_addr(slot), &J.tmap, J.col_off, U.seg0 - D.Ax, U.segT - D.Ay,
+                U.k0 - D.A + q, bar);
+    if (vals) tma_load_4d(vdst, &J.vmap, 0, U.seg0, U.segT, U.k0 + q - 2 * D.A, bar);
+  } else {
+    tma_load_2d(smem_addr(slot), &J.tmap, J.col_off, U.seg0 + (U.k0 - D.A + q) * D.L + D.cmin,
+                bar);
+    if (vals) tma_load_2d(vdst, &J.vmap, 0, U.seg0 + (U.k0 + q - 2 * D.A) * D.L, bar);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -371,8 +520,9 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 // dots, two CTAs per SM are asked for (the register budget follows).  NDC:
 // the diagonal count when every job of the launch has it (5: 2D Laplacian,
 // 13: Matérn), fixed at compile time, which removes a third of the
-// instructions; 0 = any count up to kMaxDiags.
-template <int NDOT, int MAXT, int NDC>
+// instructions; 7: the 3D Laplacian; 0 = any count up to kMaxDiags.  DIM:
+// 2 = line sweep, 3 = plane sweep (see DiaInfo).
+template <int NDOT, int MAXT, int NDC, int DIM>
 __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
     k_spmm_sweep(const __grid_constant__ SpmmBatch<float> B, int slot_floats, int nr,
                  unsigned extra_tx, unsigned long long wait_ns) {
@@ -390,7 +540,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   float* ring = reinterpret_cast<float*>(smem_raw + ring_bytes);
 
   SwUnit C;
-  sw_unit(C, B, blockIdx.x);
+  sw_unit<DIM>(C, B, blockIdx.x);
   if (C.gu >= B.total_tiles) return;
   if (threadIdx.x == 0) {
     for (int q = 0; q < nr; ++q) mbar_init(bar0 + 8 * q, 1);
@@ -404,11 +554,11 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   auto produce = [&](int released) {
     while (P.gu < B.total_tiles && issued < released + nr) {
       if (threadIdx.x == 0)
-        sw_issue(B, P, pq, ring + (size_t)pslot * slot_floats, bar0 + 8 * pslot, extra_tx);
+        sw_issue<DIM>(B, P, pq, ring + (size_t)pslot * slot_floats, bar0 + 8 * pslot, extra_tx);
       ++issued;
       if (++pslot == nr) pslot = 0;
       if (++pq == P.nl + 2 * B.jobs[P.jb].dinfo.A) {
-        sw_unit(P, B, P.gu + gridDim.x);
+        sw_unit<DIM>(P, B, P.gu + gridDim.x);
         pq = 0;
       }
     }
@@ -423,6 +573,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
   // Constants of the current job.
   int cur_jb = -1, G = 1, R = 1, r = 0, g = 0, width = 0, nd = 0, dp = 0, A = 0, L = 0;
   int win_floats = 0, dself = 0, col0 = 0, ldy = 0, ndots = 0, n = 0;
+  int PL = 0, txs = 0, tmask = 0, WX = 0, hoff = 0;  // plane sweep: P, tile shape, halo offset
   float* yv = nullptr;
   float csh[V], csc[V];
   bool has_shift = false, has_scale = false;
@@ -451,7 +602,14 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       A = D.A;
       L = D.L;
       n = J.n;
-      win_floats = sweep_win_floats(J.dia_T, D.cw, width);
+      win_floats = sweep_win_floats(sweep_win_points(D, J.dia_T, J.dia_tx, J.dia_ty), width);
+      if constexpr (DIM == 3) {
+        PL = D.P;
+        txs = J.dia_txs;
+        tmask = J.dia_tx - 1;
+        WX = J.dia_tx + 2 * D.Ax;
+        hoff = D.Ay * WX + D.Ax;
+      }
       for (int d = 0; d < nd; ++d)
         if (D.off[d] == 0) dself = d;
       col0 = J.col_off + g * V;
@@ -473,9 +631,9 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
       // (every read of the previous table ended before the last barrier)
       for (int e = threadIdx.x; e < nr * kMaxDiags; e += blockDim.x) {
         const int rot = e / kMaxDiags, d = e - rot * kMaxDiags;
-        xo_tab[e] = d < nd ? ring_bytes +
-                                 (((rot + A + D.line[d]) % nr) * slot_floats + D.cpos[d] * width) *
-                                     (int)sizeof(float)
+        const int pos = DIM == 3 ? D.dy[d] * (J.dia_tx + 2 * D.Ax) + D.dx[d] : D.cpos[d];
+        xo_tab[e] = d < nd ? ring_bytes + (((rot + A + D.line[d]) % nr) * slot_floats +
+                                           pos * width) * (int)sizeof(float)
                            : 0;
       }
       __syncthreads();
@@ -524,24 +682,40 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
         const int xself = xt[dself];
         const int vslot = rslot + 2 * A < nr ? rslot + 2 * A : rslot + 2 * A - nr;
         const int vs_b = ring_bytes + (vslot * slot_floats + win_floats) * (int)sizeof(float);
-        const int rowbase = C.seg0 + (C.k0 + j) * L;
-        // Window vectors other than x itself are loaded before the sums, so
-        // that their latency overlaps them (up to four; the registers of
-        // more would spill).
-        constexpr bool kEarly = NDOT <= 4;
+        // First row of the segment (dim 2) or tile (dim 3) in this line or
+        // plane, and its point count.
+        const int rowbase =
+            DIM == 3 ? (C.k0 + j) * PL + C.segT * L + C.seg0 : C.seg0 + (C.k0 + j) * L;
+        const int npts = DIM == 3 ? J.dia_T : C.segT;
+        // plane sweep: the tile's points inside the grid
+        const int wx = DIM == 3 ? min(tmask + 1, L - C.seg0) : 0;
+        const int wy = DIM == 3 ? min(J.dia_ty, J.dinfo.ny - C.segT) : 0;
         // kRows rows of the segment per thread at a time (rows rr, rr + R,
         // ...): independent FMA chains interleave.  Each row's sum, y and
         // dot updates are those of one row at a time, in row order.
         auto rows_loop = [&](auto krows) {
         constexpr int kRows = decltype(krows)::value;
-        for (int rr = r; rr < C.segT; rr += kRows * R) {
-          if (rowbase + rr >= n) break;
+        // Window vectors other than x itself are loaded before the sums, so
+        // that their latency overlaps them (up to four; more would spill).
+        constexpr bool kEarly = NDOT <= 4;
+        for (int rr = r; rr < npts; rr += kRows * R) {
+          if (DIM == 2 && rowbase + rr >= n) break;
+          // Point rq (its window position) and row rowq (global) of each of
+          // the thread's kRows points; an absent point re-reads point rr
+          // (dim 2) or its smem position and the tile's first row (dim 3).
           bool on[kRows];
-          int rq[kRows];
+          int rq[kRows], rowq3[DIM == 3 ? kRows : 1];
 #pragma unroll
           for (int q = 0; q < kRows; ++q) {
-            on[q] = rr + q * R < C.segT && rowbase + rr + q * R < n;
-            rq[q] = on[q] ? rr + q * R : rr;  // an absent row re-reads row rr
+            const int p = rr + q * R;
+            if constexpr (DIM == 3) {
+              on[q] = p < npts && (p & tmask) < wx && (p >> txs) < wy;
+              rq[q] = p < npts ? p : rr;
+              rowq3[q] = on[q] ? rowbase + (p >> txs) * L + (p & tmask) : rowbase;
+            } else {
+              on[q] = p < npts && rowbase + p < n;
+              rq[q] = on[q] ? p : rr;
+            }
           }
           // x, y and the window vectors move as pairs of packed columns
           // (16 bytes = two f32x2 pairs); the row sums use fma.rn.f32x2,
@@ -553,11 +727,13 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
             for (int d = 0; d < NDOT; ++d)
               if (kEarly && d < ndots && !((selfmask >> d) & 1u))
                 u[q][d] = __ldg(reinterpret_cast<const ulonglong2*>(
-                    J.dotv[d] + (size_t)(rowbase + rq[q]) * ldy + col0));
+                    J.dotv[d] +
+                    (size_t)(DIM == 3 ? rowq3[DIM == 3 ? q : 0] : rowbase + rq[q]) * ldy + col0));
           int xb[kRows], vb[kRows];  // byte offsets of the row's chunk and values
 #pragma unroll
           for (int q = 0; q < kRows; ++q) {
-            xb[q] = (rq[q] * width + g * V) * (int)sizeof(float);
+            const int wpos = DIM == 3 ? (rq[q] >> txs) * WX + (rq[q] & tmask) + hoff : rq[q];
+            xb[q] = (wpos * width + g * V) * (int)sizeof(float);
             vb[q] = vs_b + rq[q] * dp * (int)sizeof(float);
           }
           unsigned long long s2[kRows][2];
@@ -586,7 +762,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
 #pragma unroll
           for (int q = 0; q < kRows; ++q) {
             if (!on[q]) continue;
-            const int row = rowbase + rq[q];
+            const int row = DIM == 3 ? rowq3[DIM == 3 ? q : 0] : rowbase + rq[q];
             const ulonglong2 xs2 = *reinterpret_cast<const ulonglong2*>(smem_raw + xb[q] + xself);
             if (has_shift || has_scale) {
               float sc[V], xs[V];
@@ -619,9 +795,11 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
           }
         }
         };
-        // (pairs in the CTAs of up to 320 threads only: the larger ones run
-        // at two per SM on 64 registers, which pairs would spill)
-        if (NDOT <= 4 && MAXT <= 320 && C.segT >= 2 * R)
+        // (pairs with at most two dots, in CTAs of up to 320 threads only:
+        // the larger ones run at two per SM on 64 registers, and four dots'
+        // early loads for two rows exceed the 168 registers a thread of a
+        // 320-thread CTA can have)
+        if (NDOT <= 2 && MAXT <= 320 && npts >= 2 * R)
           rows_loop(std::integral_constant<int, 2>{});
         else
           rows_loop(std::integral_constant<int, 1>{});
@@ -650,7 +828,7 @@ __global__ void __launch_bounds__(MAXT, NDOT <= 2 ? 2 : 1)
     rslot += 2 * A;
     if (rslot >= nr) rslot -= nr;
     t0 += nwin;
-    sw_unit(C, B, C.gu + gridDim.x);
+    sw_unit<DIM>(C, B, C.gu + gridDim.x);
   }
 }
 
@@ -662,7 +840,7 @@ static void sweep_launch_geom(const SpmmBatch<float>& b, int* slot_floats, int* 
   int sf = 0, a = 0;
   for (int j = 0; j < b.njobs; ++j) {
     const SpmmJob<float>& J = b.jobs[j];
-    sf = std::max(sf, sweep_slot_floats(J.dinfo, J.dia_T, J.width));
+    sf = std::max(sf, sweep_slot_floats(J.dinfo, J.dia_T, J.dia_tx, J.dia_ty, J.width));
     a = std::max(a, J.dinfo.A);
   }
   *slot_floats = (sf + 31) / 32 * 32;
@@ -689,15 +867,21 @@ int launch_spmm_dia(const SpmmBatch<float>& b, int threads, cudaStream_t s) {
   const bool stall = stall_env && stall_env[0] == '1';
   const unsigned extra_tx = stall ? 16u : 0u;
   const unsigned long long wait_ns = stall ? 20000000ull : kDiaWaitNs;
+  // Every job of a launch has the same dimension (launch_spmm_jobs splits).
+  const int dim = b.jobs[0].dinfo.dim;
   int ndc = b.jobs[0].dinfo.ndiag;
   for (int j = 1; j < b.njobs; ++j)
     if (b.jobs[j].dinfo.ndiag != ndc) ndc = 0;
-  if (ndc != 5 && ndc != 13) ndc = 0;
+  if (dim == 3 ? ndc != 7 : (ndc != 5 && ndc != 13)) ndc = 0;
   ProfScope prof(KC_SPMM, s, flops, bytes);
-#define LD_SW_KERN(ND, NC) (threads <= 320 ? k_spmm_sweep<ND, 320, NC> : k_spmm_sweep<ND, 512, NC>)
+#define LD_SW_KERN(ND, NC, DM) \
+  (threads <= 320 ? k_spmm_sweep<ND, 320, NC, DM> : k_spmm_sweep<ND, 512, NC, DM>)
 #define LD_SW_CASE(ND)                                                                       \
   {                                                                                          \
-    auto kern = ndc == 13 ? LD_SW_KERN(ND, 13) : ndc == 5 ? LD_SW_KERN(ND, 5) : LD_SW_KERN(ND, 0); \
+    auto kern = dim == 3 ? (ndc == 7 ? LD_SW_KERN(ND, 7, 3) : LD_SW_KERN(ND, 0, 3))           \
+                         : ndc == 13 ? LD_SW_KERN(ND, 13, 2)                                  \
+                         : ndc == 5  ? LD_SW_KERN(ND, 5, 2)                                   \
+                                     : LD_SW_KERN(ND, 0, 2);                                  \
     const int nr = 2 * amax + 1 + kSweepPrefetch;                                            \
     const size_t smem = sweep_smem_bytes(nr, slot_floats, threads);                          \
     if (smem > 48 * 1024)                                                                    \

@@ -118,14 +118,15 @@ int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* lo, double* h
   return LOGDET_OK;
 }
 
-int logdet_line_structure(logdet_handle h, int32_t* line_stride, int32_t* lines) {
-  if (!h || !line_stride || !lines) {
+int logdet_grid_structure(logdet_handle h, int32_t* dim, int32_t* line_stride, int32_t* reach) {
+  if (!h || !dim || !line_stride || !reach) {
     set_error("NULL handle or output pointer");
     return LOGDET_EINVAL;
   }
   const bool on = h->dia.ndiag > 0 && h->dia_slot;
+  *dim = on ? h->dia.dim : 0;
   *line_stride = on ? h->dia.L : 0;
-  *lines = on ? h->dia.A : 0;
+  *reach = on ? h->dia.A : 0;
   return LOGDET_OK;
 }
 

@@ -55,16 +55,18 @@ struct SpmmJob {
   int col_off, width;              // columns [col_off, col_off+width) of the block (width % vec == 0)
   int b;                           // live columns in this slice (accounting only)
   long long nnz;                   // (accounting only)
-  // Line-sweep path (FP32 blocks of a matrix with line structure, see
-  // dia.cu); dia == nullptr: CSR path.  The rows are cut into segments of
-  // dia_T rows within each line of L rows; a unit is one segment position
-  // swept over dia_kc consecutive lines, and ntiles counts the units (their
-  // index is the partial slot).  dia: values per row and diagonal
+  // Line- and plane-sweep paths (FP32 blocks of a matrix with grid
+  // structure, see dia.cu); dia == nullptr: CSR path.  dim 2: the rows are
+  // cut into segments of dia_T rows within each line of L rows; dim 3: each
+  // plane into tiles of dia_tx x dia_ty points.  A unit is one segment or
+  // tile position swept over dia_kc consecutive lines or planes, and ntiles
+  // counts the units (their index is the partial slot).  dia: values per row and diagonal
   // [n][dia_pad(ndiag)]; tmap: x, box of width columns x (dia_T + cw) rows;
   // vmap: the values, box of dia_T rows; err: set if a bounded wait gives up.
   const float* dia;
   int* err;
   int dia_T, dia_kc, dia_nseg, dia_nlines;
+  int dia_tx, dia_ty, dia_txs;     // plane sweep: tile of tx (= 1 << txs) x ty points, T = tx ty
   DiaInfo dinfo;
   CUtensorMap tmap;
   CUtensorMap vmap;

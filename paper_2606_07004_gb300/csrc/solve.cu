@@ -160,6 +160,9 @@ int KRun<T>::init(const int* rp, const int* ci, const typename ValOf<T>::type* v
       sw_kc = sg.kc;
       sw_nseg = sg.nseg;
       sw_nlines = sg.nlines;
+      sw_tx = sg.tx;
+      sw_ty = sg.ty;
+      sw_txs = sg.txs;
       nslots = sg.units;
     }
   }
@@ -239,6 +242,9 @@ int KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
         J.dia_kc = sw_kc;
         J.dia_nseg = sw_nseg;
         J.dia_nlines = sw_nlines;
+        J.dia_tx = sw_tx;
+        J.dia_ty = sw_ty;
+        J.dia_txs = sw_txs;
         J.dinfo = hctx->dia;
         LD_TRY(dia_encode(J, ptr(j), n, ld, width));
       }
@@ -328,17 +334,17 @@ template struct KRun<bf16>;
 template <typename T>
 int launch_spmm_jobs(const std::vector<SpmmJob<T>>& jobs, int threads, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
-    // Diagonal-path jobs launch apart from CSR jobs (same stream, in order).
-    bool any = false, all = true;
-    for (const auto& J : jobs) {
-      any |= J.dia != nullptr;
-      all &= J.dia != nullptr;
-    }
-    if (any && !all) {
-      std::vector<SpmmJob<T>> a, c;
-      for (const auto& J : jobs) (J.dia ? a : c).push_back(J);
-      LD_TRY(launch_spmm_jobs<T>(c, threads, s));
-      return launch_spmm_jobs<T>(a, threads, s);
+    // Sweep jobs launch apart from CSR jobs, line sweeps apart from plane
+    // sweeps (same stream, in order).
+    auto kind = [](const SpmmJob<T>& J) { return J.dia ? J.dinfo.dim : 0; };
+    bool mixed = false;
+    for (const auto& J : jobs) mixed |= kind(J) != kind(jobs[0]);
+    if (mixed) {
+      std::vector<SpmmJob<T>> part[4];
+      for (const auto& J : jobs) part[kind(J)].push_back(J);
+      for (int k : {0, 2, 3})
+        if (!part[k].empty()) LD_TRY(launch_spmm_jobs<T>(part[k], threads, s));
+      return LOGDET_OK;
     }
   }
   for (size_t i0 = 0; i0 < jobs.size(); i0 += kMaxJobs) {

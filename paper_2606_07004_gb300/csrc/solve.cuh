@@ -98,7 +98,7 @@ struct KRun {
   const float* diavals = nullptr;  // FP32 values per row and diagonal: the line-sweep path
   DevBuf<int> dia_err;             // set if a staged copy's wait gave up
   bool sweep = false;              // pass 1 runs the line sweep
-  int sw_T = 0, sw_kc = 0, sw_nseg = 0, sw_nlines = 0;
+  int sw_T = 0, sw_kc = 0, sw_nseg = 0, sw_nlines = 0, sw_tx = 0, sw_ty = 0, sw_txs = 0;
   int done_steps = 0;  // steps whose pass 1 has been issued
   cudaStream_t st;
 

@@ -193,6 +193,9 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
           J.dia_kc = sg.kc;
           J.dia_nseg = sg.nseg;
           J.dia_nlines = sg.nlines;
+          J.dia_tx = sg.tx;
+          J.dia_ty = sg.ty;
+          J.dia_txs = sg.txs;
           J.dinfo = h->dia;
           LD_TRY(dia_encode(J, x.p, n, ld, width));
         }

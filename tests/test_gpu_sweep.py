@@ -1,10 +1,11 @@
-"""Line-sweep path of the FP32 SpMM pass (x rows of 2A + 1 grid lines staged
-by TMA copies in a ring of shared-memory windows).  A handle created from
-host arrays of a 2D grid stencil takes it for mixed-FP32 solves; a handle
-over device arrays of the same matrix keeps the CSR gathers.  y is the same
-FP32 sum on both paths; the window dots are reduced per sweep unit instead
-of per CSR tile, so the two agree to the rounding of compensated partial
-sums, far inside the mixed-precision budget (1e-4 against FP64)."""
+"""Sweep paths of the FP32 SpMM pass: x staged by TMA copies in a ring of
+shared-memory windows, 2A + 1 grid lines (2D stencils) or planes (3D
+stencils) at a time.  A handle created from host arrays of a grid stencil
+takes the sweep for mixed-FP32 solves; a handle over device arrays of the
+same matrix keeps the CSR gathers.  y is the same FP32 sum on both paths;
+the window dots are reduced per sweep unit instead of per CSR tile, so the
+two agree to the rounding of compensated partial sums, far inside the
+mixed-precision budget (1e-4 against FP64)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -31,19 +32,34 @@ def _device_handle(A):
     return B.Handle(A.n, rp, ci, va, device=True)
 
 
+def _csr(Q, dtype=np.float32):
+    Q = Q.tocsr()
+    Q.sort_indices()
+    return W.CSR(Q.shape[0], Q.indptr.astype(np.int32), Q.indices.astype(np.int32),
+                 Q.data.astype(dtype))
+
+
 def _band(L, n, dtype=np.float32):
     # 5-diagonal SPD band (offsets 0, +-1, +-L) whose last line is ragged
     # (n not a multiple of L).
-    Q = sp.diags([np.full(n - L, -1.0), np.full(n - 1, -1.0), np.full(n, 4.2),
-                  np.full(n - 1, -1.0), np.full(n - L, -1.0)], [-L, -1, 0, 1, L], format="csr")
-    Q.sort_indices()
-    return W.CSR(n, Q.indptr.astype(np.int32), Q.indices.astype(np.int32), Q.data.astype(dtype))
+    return _csr(sp.diags([np.full(n - L, -1.0), np.full(n - 1, -1.0), np.full(n, 4.2),
+                          np.full(n - 1, -1.0), np.full(n - L, -1.0)], [-L, -1, 0, 1, L]), dtype)
+
+
+def _band3(nx, ny, nz):
+    # The 3D Laplacian's 7 offsets as full bands: entries wrap across line and
+    # plane edges, so the matrix is no grid stencil.
+    n = nx * ny * nz
+    offs = [-nx * ny, -nx, -1, 0, 1, nx, nx * ny]
+    return _csr(sp.diags([np.full(n - abs(o), 6.5 if o == 0 else -1.0) for o in offs], offs))
 
 
 MATS = {
-    "lap2d": (lambda: W.laplacian_2d(100, 90, shift=0.05), (100, 1)),
-    "matern": (lambda: W.matern_2d(70, 0.05, dtype=np.float32), (70, 2)),
-    "band-ragged": (lambda: _band(64, 5001), (64, 1)),
+    "lap2d": (lambda: W.laplacian_2d(100, 90, shift=0.05), (2, 100, 1)),
+    "matern": (lambda: W.matern_2d(70, 0.05, dtype=np.float32), (2, 70, 2)),
+    "band-ragged": (lambda: _band(64, 5001), (2, 64, 1)),
+    "lap3d": (lambda: W.laplacian_3d(24, 21, 19, shift=0.01), (3, 24, 1)),
+    "lap3d-thin": (lambda: W.laplacian_3d(37, 5, 40, shift=0.02, dtype=np.float32), (3, 37, 1)),
 }
 
 
@@ -59,15 +75,15 @@ def _same(a, b):
     assert np.array_equal(a.z_norm2, b.z_norm2)
 
 
-def test_line_structure_detection():
+def test_grid_structure_detection():
     for name, (mk, want) in MATS.items():
         A = mk()
         with B.Handle.from_csr(A) as h, _device_handle(A) as hd:
-            assert h.line_structure() == want, name
-            assert hd.line_structure() == (0, 0)
-    for A in (W.laplacian_3d(24, 21, 19, shift=0.01), W.laplacian_2d(40, 40, shift=0.1)):
-        with B.Handle.from_csr(A) as h:   # 3D stencil; n < 4096
-            assert h.line_structure() == (0, 0)
+            assert h.grid_structure() == want, name
+            assert hd.grid_structure() == (0, 0, 0)
+    for A in (W.laplacian_2d(40, 40, shift=0.1), _band3(24, 21, 19)):
+        with B.Handle.from_csr(A) as h:   # n < 4096; bands that wrap
+            assert h.grid_structure() == (0, 0, 0)
 
 
 @pytest.mark.parametrize("name", list(MATS))
@@ -85,7 +101,7 @@ def test_sweep_matches_csr_path(name, method, k):
             _close(a, b)
 
 
-@pytest.mark.parametrize("name", ["matern", "band-ragged"])
+@pytest.mark.parametrize("name", ["matern", "band-ragged", "lap3d", "lap3d-thin"])
 def test_sweep_against_fp64_oracle(name):
     A = MATS[name][0]()
     Q = A.to_scipy()
@@ -119,12 +135,13 @@ def test_sweep_wide_block_deterministic_server_and_plan():
 
 
 def test_sweep_mixed_batch_in_server():
-    # One server batch holds sweep jobs of different stencils (5 and 13
-    # diagonals, A = 1 and 2, one ragged last line), a CSR job (3D stencil)
-    # and both methods: the launch takes the generic diagonal-count instance
-    # and the largest ring.  Each result must equal the same request alone.
+    # One server batch holds line-sweep jobs of different stencils (5 and 13
+    # diagonals, A = 1 and 2, one ragged last line), a plane-sweep job (3D
+    # stencil), a CSR job (wrapping bands) and both methods: the launch takes
+    # the generic diagonal-count instance and the largest ring, and splits
+    # by path.  Each result must equal the same request alone.
     mats = [W.laplacian_2d(100, 90, shift=0.05), W.matern_2d(70, 0.05, dtype=np.float32),
-            _band(64, 5001), W.laplacian_3d(24, 21, 19, shift=0.01)]
+            _band(64, 5001), W.laplacian_3d(24, 21, 19, shift=0.01), _band3(24, 21, 19)]
     hs = [B.Handle.from_csr(A) for A in mats]
     try:
         reqs = []
