@@ -164,6 +164,13 @@ int logdet_info(logdet_handle h, int32_t* n, int64_t* nnz, double* gersh_lo, dou
  * matrices).  Errors: EINVAL (null pointer). */
 int logdet_grid_structure(logdet_handle h, int32_t* dim, int32_t* line_stride, int32_t* reach);
 
+/* The same detection on host CSR arrays (n rows, rowptr[n + 1] and sorted
+ * colind, int32, caller-owned), without a handle: host code only, no GPU
+ * needed.  Outputs as for logdet_grid_structure.  Errors: EINVAL (null
+ * pointer, n < 1). */
+int logdet_grid_structure_csr(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                              int32_t* dim, int32_t* line_stride, int32_t* reach);
+
 /* ---- estimators --------------------------------------------------------
  * logdet_oslq: Algorithm 3 (OSLQ, Sec. 3): J = Q/alpha with alpha the upper
  * spectral bound; s = floor(num_probes/3) Rademacher sketch columns give

@@ -35,7 +35,7 @@ ST_BREAKDOWN, ST_NONPOS_RITZ, ST_RANK_DEFICIENT, ST_LOG_FAILED = 1, 2, 4, 8
 EXPORTED = [
     "logdet_opts_default", "logdet_strerror", "logdet_last_error",
     "logdet_create", "logdet_create_device", "logdet_create_grid", "logdet_destroy", "logdet_info",
-    "logdet_grid_structure", "logdet_oslq", "logdet_osaiop",
+    "logdet_grid_structure", "logdet_grid_structure_csr", "logdet_oslq", "logdet_osaiop",
     "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_quadform", "logdet_orth",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
@@ -99,6 +99,8 @@ _sig("logdet_create_grid", C.c_int, [_i32, _i32, _i32, _P, C.POINTER(_P)])
 _sig("logdet_destroy", None, [_P])
 _sig("logdet_info", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl)])
 _sig("logdet_grid_structure", C.c_int, [_P, C.POINTER(_i32), C.POINTER(_i32), C.POINTER(_i32)])
+_sig("logdet_grid_structure_csr", C.c_int, [_i32, _P, _P, C.POINTER(_i32), C.POINTER(_i32),
+                                            C.POINTER(_i32)])
 for _n in ("logdet_oslq", "logdet_osaiop"):
     _sig(_n, C.c_int, [_P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts), C.POINTER(logdet_result)])
 _sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
@@ -134,6 +136,18 @@ _sig("logdet_profile_enable", C.c_int, [C.c_int])
 _sig("logdet_profile_reset", C.c_int, [])
 _sig("logdet_profile_read", C.c_int, [_i32, C.POINTER(_i64), C.POINTER(_dbl), C.POINTER(_dbl),
                                       C.POINTER(_dbl)])
+
+
+def grid_structure_csr(A):
+    """(dim, L, reach) of host CSR arrays (object with n, rowptr, colind), as
+    a handle would report it (logdet_grid_structure_csr; host only)."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    dim, L, R = _i32(), _i32(), _i32()
+    _check(_lib.logdet_grid_structure_csr(int(A.n), rp.ctypes.data, ci.ctypes.data,
+                                          C.byref(dim), C.byref(L), C.byref(R)),
+           "logdet_grid_structure_csr")
+    return dim.value, L.value, R.value
 
 
 class LogdetError(RuntimeError):

@@ -44,42 +44,59 @@ static int nearest_line(int o, int L) {
   return o >= 0 ? l : -l;
 }
 
-// 3D grid stencil: L = the smallest offset magnitude >= 2 (the line), P =
-// the largest (the plane), ny = P / L, nz = n / P; every offset split as
-// dz P + dy L + dx (nearest), small radii, and no entry whose grid
-// neighbour would wrap across a line or plane edge (so that reading a
-// zero-filled point outside the grid stands for "no entry").
+// 3D grid stencil: L = the smallest offset magnitude above kPlaneMaxR (the
+// grid's row length), P (the plane stride, a multiple of L with ny = P / L
+// >= 2 and nz = n / P >= 2) = the first of the offset magnitudes and their
+// halves, in ascending order, for which every offset splits as
+// dz P + dy L + dx (nearest) with |dz| <= kPlaneMaxA, |dy| <= 2,
+// |dx| <= kPlaneMaxR; and no entry whose grid neighbour would wrap across a
+// line or plane edge (so that reading a zero-filled point outside the grid
+// stands for "no entry").
+static bool plane_split(const std::vector<int>& offs, int n, int L, int P, DiaInfo* d) {
+  if (P % L || P / L < 2 || n % P || n / P < 2) return false;
+  memset(d, 0, sizeof *d);
+  d->ndiag = (int)offs.size();
+  d->dim = 3;
+  d->L = L;
+  d->P = P;
+  d->ny = P / L;
+  d->nz = n / P;
+  for (int q = 0; q < d->ndiag; ++q) {
+    const int o = offs[q];
+    d->off[q] = o;
+    d->line[q] = nearest_line(o, P);
+    const int rem = o - d->line[q] * P;
+    d->dy[q] = nearest_line(rem, L);
+    d->dx[q] = rem - d->dy[q] * L;
+    d->A = std::max(d->A, std::abs(d->line[q]));
+    d->Ay = std::max(d->Ay, std::abs(d->dy[q]));
+    d->Ax = std::max(d->Ax, std::abs(d->dx[q]));
+  }
+  return d->A <= kPlaneMaxA && d->Ay <= 2 && d->Ax <= kPlaneMaxR;
+}
+
 static bool plane_structure(const std::vector<int>& offs, int n, const int* rowptr,
                             const int* colind, DiaInfo* out) {
-  int L = INT_MAX, P = 0;
+  int L = INT_MAX;
+  std::vector<int> cand;
   for (int o : offs) {
-    const int a = o >= 0 ? o : -o;
-    if (a >= 2) {
-      L = std::min(L, a);
-      P = std::max(P, a);
+    const int a = std::abs(o);
+    if (a > kPlaneMaxR) L = std::min(L, a);
+    if (a > 0) {
+      cand.push_back(a);
+      if (a % 2 == 0) cand.push_back(a / 2);
     }
   }
-  if (P == 0 || L < 4 || P % L || P / L < 2 || n % P || n / P < 2) return false;
+  if (L == INT_MAX) return false;
+  std::sort(cand.begin(), cand.end());
   DiaInfo d;
-  memset(&d, 0, sizeof d);
-  d.ndiag = (int)offs.size();
-  d.dim = 3;
-  d.L = L;
-  d.P = P;
-  d.ny = P / L;
-  d.nz = n / P;
-  for (int q = 0; q < d.ndiag; ++q) {
-    const int o = offs[q];
-    d.off[q] = o;
-    d.line[q] = nearest_line(o, P);
-    const int rem = o - d.line[q] * P;
-    d.dy[q] = nearest_line(rem, L);
-    d.dx[q] = rem - d.dy[q] * L;
-    d.A = std::max(d.A, std::abs(d.line[q]));
-    d.Ay = std::max(d.Ay, std::abs(d.dy[q]));
-    d.Ax = std::max(d.Ax, std::abs(d.dx[q]));
-  }
-  if (d.A > kPlaneMaxA || d.Ay > 2 || d.Ax > kPlaneMaxR) return false;
+  bool found = false;
+  for (int P : cand)
+    if (plane_split(offs, n, L, P, &d)) {
+      found = true;
+      break;
+    }
+  if (!found) return false;
   for (int i = 0; i < n; ++i) {
     const int x = i % L, y = (i / L) % d.ny;
     for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
@@ -92,17 +109,16 @@ static bool plane_structure(const std::vector<int>& offs, int n, const int* rowp
   return true;
 }
 
-int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
-  memset(&h->dia, 0, sizeof h->dia);
-  const int n = h->n;
-  if (n < 4096 || h->nnz <= 0) return LOGDET_OK;
+bool dia_detect(int n, const int* rowptr, const int* colind, DiaInfo* out) {
+  memset(out, 0, sizeof *out);
+  if (n < 4096 || rowptr[n] <= 0) return false;
   std::vector<int> offs;
   for (int i = 0; i < n; ++i) {
     for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
       const int o = colind[q] - i;
       if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
         offs.push_back(o);
-        if ((int)offs.size() > kMaxDiags) return LOGDET_OK;  // not a stencil
+        if ((int)offs.size() > kMaxDiags) return false;  // not a stencil
       }
     }
   }
@@ -148,12 +164,24 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
       best = d;
     }
   }
-  if (best.ndiag == 0 && !plane_structure(offs, n, rowptr, colind, &best)) return LOGDET_OK;
+  if (best.ndiag == 0 && !plane_structure(offs, n, rowptr, colind, &best)) return false;
+  *out = best;
+  return true;
+}
+
+int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
+  memset(&h->dia, 0, sizeof h->dia);
+  const int n = h->n;
+  if (h->nnz <= 0) return LOGDET_OK;
+  DiaInfo best;
+  if (!dia_detect(n, rowptr, colind, &best)) return LOGDET_OK;
+  const int nd = best.ndiag;
+  const int* offs = best.off;
   // CSR entry -> diagonal index.
   std::vector<int> slot((size_t)h->nnz);
   for (int i = 0; i < n; ++i)
     for (int q = rowptr[i]; q < rowptr[i + 1]; ++q)
-      slot[q] = (int)(std::lower_bound(offs.begin(), offs.end(), colind[q] - i) - offs.begin());
+      slot[q] = (int)(std::lower_bound(offs, offs + nd, colind[q] - i) - offs);
   if (cudaMalloc(&h->dia_slot, sizeof(int) * slot.size()) != cudaSuccess) {
     cudaGetLastError();
     h->dia_slot = nullptr;

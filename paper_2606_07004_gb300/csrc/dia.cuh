@@ -19,6 +19,11 @@ constexpr int kSweepSmemBudget = 110 * 1024;  // per CTA (two CTAs per SM)
 // per four diagonals).
 __host__ __device__ inline int dia_pad(int ndiag) { return (ndiag + 3) & ~3; }
 
+// Grid structure of host CSR arrays (sorted columns, n >= 4096), see
+// DiaInfo: a 2D line structure if there is one, else a 3D grid stencil;
+// false (and *out zeroed) when there is neither.  Host only.
+bool dia_detect(int n, const int* rowptr, const int* colind, DiaInfo* out);
+
 // At handle creation (host CSR): record the grid structure when every entry
 // lies on at most kMaxDiags diagonals that fit one (see DiaInfo): a 2D line
 // structure if there is one, else a 3D grid stencil.

@@ -1,6 +1,7 @@
 // OSLQ (Algorithm 3) and OSA-IOP (Algorithm 2 with Algorithm 1) on the
 // device, and the C-ABI of liblogdet.
 #include "dense.cuh"
+#include "dia.cuh"
 #include "grid.cuh"
 #include "handle.cuh"
 #include "krylov.cuh"
@@ -127,6 +128,20 @@ int logdet_grid_structure(logdet_handle h, int32_t* dim, int32_t* line_stride, i
   *dim = on ? h->dia.dim : 0;
   *line_stride = on ? h->dia.L : 0;
   *reach = on ? h->dia.A : 0;
+  return LOGDET_OK;
+}
+
+int logdet_grid_structure_csr(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                              int32_t* dim, int32_t* line_stride, int32_t* reach) {
+  if (n < 1 || !rowptr || !colind || !dim || !line_stride || !reach) {
+    set_error("n < 1 or NULL pointer");
+    return LOGDET_EINVAL;
+  }
+  ld::DiaInfo d;
+  const bool on = ld::dia_detect(n, rowptr, colind, &d);
+  *dim = on ? d.dim : 0;
+  *line_stride = on ? d.L : 0;
+  *reach = on ? d.A : 0;
   return LOGDET_OK;
 }
 

@@ -54,12 +54,20 @@ def _band3(nx, ny, nz):
     return _csr(sp.diags([np.full(n - abs(o), 6.5 if o == 0 else -1.0) for o in offs], offs))
 
 
+FACES = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+
 MATS = {
     "lap2d": (lambda: W.laplacian_2d(100, 90, shift=0.05), (2, 100, 1)),
     "matern": (lambda: W.matern_2d(70, 0.05, dtype=np.float32), (2, 70, 2)),
     "band-ragged": (lambda: _band(64, 5001), (2, 64, 1)),
     "lap3d": (lambda: W.laplacian_3d(24, 21, 19, shift=0.01), (3, 24, 1)),
     "lap3d-thin": (lambda: W.laplacian_3d(37, 5, 40, shift=0.02, dtype=np.float32), (3, 37, 1)),
+    # wider 3D stencils: |dx|, |dy| <= 2 (halo of two points), |dz| <= 2 (ring of 5 planes)
+    "grid3-wide": (lambda: W.grid_stencil_3d(20, 15, 30, FACES + [(2, 0, 0), (-2, 0, 0),
+                                                                   (0, 2, 0), (0, -2, 0)]),
+                   (3, 20, 1)),
+    "grid3-deep": (lambda: W.grid_stencil_3d(16, 16, 20, FACES + [(0, 0, 2), (0, 0, -2)]),
+                   (3, 16, 2)),
 }
 
 
@@ -101,7 +109,8 @@ def test_sweep_matches_csr_path(name, method, k):
             _close(a, b)
 
 
-@pytest.mark.parametrize("name", ["matern", "band-ragged", "lap3d", "lap3d-thin"])
+@pytest.mark.parametrize("name", ["matern", "band-ragged", "lap3d", "lap3d-thin", "grid3-wide",
+                                  "grid3-deep"])
 def test_sweep_against_fp64_oracle(name):
     A = MATS[name][0]()
     Q = A.to_scipy()

@@ -11,6 +11,7 @@ from .matrices import (  # noqa: F401
     laplacian_3d,
     matern_2d,
     powerlaw_graph_laplacian,
+    grid_stencil_3d,
     graph_laplacian,
     wendland_c2,
     wendland_table,

@@ -208,6 +208,26 @@ def matern_2d(N: int, kappa2: float, dtype=np.float64) -> CSR:
     return _from_scipy(Q, dtype)
 
 
+def grid_stencil_3d(nx: int, ny: int, nz: int, taps, diag: float = 30.0,
+                    dtype=np.float64) -> CSR:
+    """A 3D stencil on an nx x ny x nz grid (row (z ny + y) nx + x): diag on
+    the diagonal and -1 for each (dx, dy, dz) tap whose neighbour lies in the
+    grid (no wrapping across edges).  Diagonally dominant (SPD) when diag
+    exceeds the number of taps."""
+    n = nx * ny * nz
+    idx = np.arange(n, dtype=np.int64)
+    x, y, z = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+    rows, cols = [idx], [idx]
+    for dx, dy, dz in taps:
+        ok = ((x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny)
+              & (z + dz >= 0) & (z + dz < nz))
+        rows.append(idx[ok])
+        cols.append(idx[ok] + dx + dy * nx + dz * nx * ny)
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    v = np.where(r == c, diag, -1.0)
+    return _from_scipy(sp.csr_matrix((v, (r, c)), shape=(n, n)), dtype)
+
+
 def powerlaw_graph_laplacian(n: int, exponent: float = 2.3, mean_degree: float = 8.0,
                              seed: int = 0, dtype=np.float64) -> CSR:
     """Chung-Lu random graph Laplacian L = D - A (unit weights, no self loops).
