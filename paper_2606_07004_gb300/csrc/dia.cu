@@ -1,23 +1,29 @@
-// Line-sweep path of the SpMM pass for FP32 blocks of stencil matrices.
+// Sweep paths of the SpMM pass for FP32 blocks of grid stencil matrices.
 //
-// A 2D grid stencil (the 2D Laplacians, the Matérn operator (kappa^2 I + L)^2)
-// keeps every entry on a few diagonals whose offsets are line * L + c, with L
-// the grid's row length, |line| <= A and c in a short range [cmin, cmin + cw].
-// Output row i needs x rows from the lines i/L - A .. i/L + A.  A CTA owns a
-// segment of T consecutive rows within a line and sweeps it over kc
-// consecutive lines (a "unit").  It keeps the 2A + 1 line windows the current
-// line needs (T + cw rows of x each) in a ring of shared-memory slots; moving
-// to the next line needs one new window, which a TMA 2D copy
-// (cp.async.bulk.tensor, completion on the slot's mbarrier) brings in, with
-// the values of the new line, two lines ahead of the computation.  So each x
-// row crosses from L2 to the SM about (T + cw) / T times per pass instead of
-// once per diagonal line.
+// Line sweep (2D grid stencils: the 2D Laplacians, the Matérn operator
+// (kappa^2 I + L)^2).  Every entry lies on a few diagonals whose offsets are
+// line * L + c, with L the grid's row length, |line| <= A and c in a short
+// range [cmin, cmin + cw].  Output row i needs x rows from the lines
+// i/L - A .. i/L + A.  A CTA owns a segment of T consecutive rows within a
+// line and sweeps it over kc consecutive lines (a "unit").  It keeps the
+// 2A + 1 line windows the current line needs (T + cw rows of x each) in a
+// ring of shared-memory slots; moving to the next line needs one new
+// window, which a TMA 2D copy (cp.async.bulk.tensor, completion on the
+// slot's mbarrier) brings in, with the values of the new line, ahead of the
+// computation.  So each x row crosses from L2 to the SM about (T + cw) / T
+// times per pass instead of once per diagonal line.
 //
-// Rows outside the matrix are filled with zeros by the copy; the value of a
-// diagonal is 0 where a row has no entry.  Each row sums over the diagonals
-// in ascending offset order, the CSR column order, so y is the same FP32 sum
-// as on the CSR path; the window dots are accumulated per unit (the unit is
-// the partial slot), so they differ from the CSR path's only by the order of
+// Plane sweep (3D grid stencils on an L x ny x nz grid).  The same with
+// tiles of tx x ty points of a plane in place of segments, planes in place
+// of lines, and a 4D TMA box (columns, x, y, z) holding the tile and its
+// halo in place of a 2D box.
+//
+// Points outside the matrix (or the grid) are filled with zeros by the copy;
+// the value of a diagonal is 0 where a row has no entry (and, in 3D, no
+// entry wraps across a grid edge).  Each row sums over the diagonals in
+// ascending offset order, the CSR column order, so y is the same FP32 sum as
+// on the CSR path; the window dots are accumulated per unit (the unit is the
+// partial slot), so they differ from the CSR path's only by the order of
 // their compensated partial sums.
 #include "dia.cuh"
 #include "profile.cuh"
@@ -460,10 +466,11 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 // ---------------------------------------------------------------------------
 // Units.  Unit u of a job covers segment u % nseg (rows seg0 .. seg0 + segT
-// of every line) over the lines k0 .. k0 + nl - 1, chunk u / nseg.  A CTA
-// takes units gu = blockIdx.x, + gridDim.x, ... of the batch; window q of a
-// unit (q = 0 .. nl + 2A - 1) holds line k0 - A + q, and from q = 2A on it
-// also carries the values of line k0 + q - 2A.
+// of every line; plane sweep: tile u % nseg of every plane) over the lines
+// or planes k0 .. k0 + nl - 1, chunk u / nseg.  A CTA takes units
+// gu = blockIdx.x, + gridDim.x, ... of the batch; window q of a unit
+// (q = 0 .. nl + 2A - 1) holds line or plane k0 - A + q, and from q = 2A on
+// it also carries the values of line or plane k0 + q - 2A.
 // ---------------------------------------------------------------------------
 // (plane sweep: seg0, segT hold the tile origin x0, y0)
 struct SwUnit {
@@ -522,9 +529,9 @@ __device__ __forceinline__ void sw_issue(const SpmmBatch<float>& B, const SwUnit
 }
 
 // ---------------------------------------------------------------------------
-// y = A x and the window dots for FP32 blocks of a matrix with line
-// structure.  Thread (r, g) owns rows r, r + R, ... of the segment and
-// 16-byte column chunk g (R = threads / G, G = width / 4).
+// y = A x and the window dots for FP32 blocks of a matrix with grid
+// structure.  Thread (r, g) owns points r, r + R, ... of the segment or tile
+// and 16-byte column chunk g (R = threads / G, G = width / 4).
 //
 // Ring protocol (uniform across the CTA): load t (a window) goes to slot
 // t % nr and completes phase (t / nr) & 1 of that slot's mbarrier.  The
