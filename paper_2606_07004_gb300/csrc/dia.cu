@@ -55,9 +55,9 @@ static int nearest_line(int o, int L) {
 // >= 2 and nz = n / P >= 2) = the first of the offset magnitudes and their
 // halves, in ascending order, for which every offset splits as
 // dz P + dy L + dx (nearest) with |dz| <= kPlaneMaxA, |dy| <= 2,
-// |dx| <= kPlaneMaxR; and no entry whose grid neighbour would wrap across a
-// line or plane edge (so that reading a zero-filled point outside the grid
-// stands for "no entry").
+// |dx| <= kPlaneMaxR and no entry's grid neighbour wraps across a line or
+// plane edge (so that reading a zero-filled point outside the grid stands
+// for "no entry").
 static bool plane_split(const std::vector<int>& offs, int n, int L, int P, DiaInfo* d) {
   if (P % L || P / L < 2 || n % P || n / P < 2) return false;
   memset(d, 0, sizeof *d);
@@ -95,24 +95,29 @@ static bool plane_structure(const std::vector<int>& offs, int n, const int* rowp
   }
   if (L == INT_MAX) return false;
   std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  // A plane stride can split every offset within the radii and still not be
+  // the grid's (half the true plane, say): then some entry wraps in its view,
+  // and the next candidate is tried.
+  auto no_wrap = [&](const DiaInfo& d) {
+    for (int i = 0; i < n; ++i) {
+      const int x = i % L, y = (i / L) % d.ny;
+      for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        const int k =
+            (int)(std::lower_bound(offs.begin(), offs.end(), colind[q] - i) - offs.begin());
+        if (x + d.dx[k] < 0 || x + d.dx[k] >= L || y + d.dy[k] < 0 || y + d.dy[k] >= d.ny)
+          return false;
+      }
+    }
+    return true;
+  };
   DiaInfo d;
-  bool found = false;
   for (int P : cand)
-    if (plane_split(offs, n, L, P, &d)) {
-      found = true;
-      break;
+    if (plane_split(offs, n, L, P, &d) && no_wrap(d)) {
+      *out = d;
+      return true;
     }
-  if (!found) return false;
-  for (int i = 0; i < n; ++i) {
-    const int x = i % L, y = (i / L) % d.ny;
-    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-      const int k = (int)(std::lower_bound(offs.begin(), offs.end(), colind[q] - i) - offs.begin());
-      if (x + d.dx[k] < 0 || x + d.dx[k] >= L || y + d.dy[k] < 0 || y + d.dy[k] >= d.ny)
-        return false;
-    }
-  }
-  *out = d;
-  return true;
+  return false;
 }
 
 bool dia_detect(int n, const int* rowptr, const int* colind, DiaInfo* out) {

@@ -38,6 +38,8 @@ FACES = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
     (_bands(8000, [-300, -3, 0, 3, 300]), (2, 300, 1)),
     (W.laplacian_3d(24, 21, 19), (3, 24, 1)),
     (W.laplacian_3d(37, 5, 40), (3, 37, 1)),
+    (W.laplacian_3d(20, 20, 30), (3, 20, 1)),   # half the plane also splits, but wraps
+    (W.laplacian_3d(100), (3, 100, 1)),
     (_grid3(20, 15, 30, FACES + [(2, 0, 0), (-2, 0, 0), (0, 2, 0), (0, -2, 0)]), (3, 20, 1)),
     (_grid3(16, 16, 20, FACES + [(0, 0, 2), (0, 0, -2)]), (3, 16, 2)),
 ])
