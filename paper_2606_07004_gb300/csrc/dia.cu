@@ -35,6 +35,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -43,6 +44,26 @@ namespace ld {
 // ---------------------------------------------------------------------------
 // Structure
 // ---------------------------------------------------------------------------
+// Runs fn(i0, i1) over row ranges of [0, n) on up to 8 host threads (the
+// structure passes are linear in nnz; a 2M-row stencil takes tens of ms on
+// one core).  Returns the AND of the ranges' results.
+template <typename Fn>
+static bool rows_parallel(int n, Fn fn) {
+  const int nt = std::max(1, std::min(8, std::min((int)std::thread::hardware_concurrency(),
+                                                  n / 65536)));
+  if (nt == 1) return fn(0, n);
+  std::vector<char> ok(nt, 1);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) {
+    const int i0 = (int)((long long)n * t / nt), i1 = (int)((long long)n * (t + 1) / nt);
+    th.emplace_back([&, t, i0, i1] { ok[t] = fn(i0, i1) ? 1 : 0; });
+  }
+  for (auto& x : th) x.join();
+  for (char c : ok)
+    if (!c) return false;
+  return true;
+}
+
 // Nearest line of offset o for stride L (ties toward zero).
 static int nearest_line(int o, int L) {
   const int a = o >= 0 ? o : -o;
@@ -100,16 +121,20 @@ static bool plane_structure(const std::vector<int>& offs, int n, const int* rowp
   // the grid's (half the true plane, say): then some entry wraps in its view,
   // and the next candidate is tried.
   auto no_wrap = [&](const DiaInfo& d) {
-    for (int i = 0; i < n; ++i) {
-      const int x = i % L, y = (i / L) % d.ny;
-      for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-        const int k =
-            (int)(std::lower_bound(offs.begin(), offs.end(), colind[q] - i) - offs.begin());
-        if (x + d.dx[k] < 0 || x + d.dx[k] >= L || y + d.dy[k] < 0 || y + d.dy[k] >= d.ny)
-          return false;
+    const int nd = (int)offs.size();
+    return rows_parallel(n, [&](int i0, int i1) {
+      for (int i = i0; i < i1; ++i) {
+        const int x = i % L, y = (i / L) % d.ny;
+        int k = 0;
+        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+          const int o = colind[q] - i;
+          while (k < nd && offs[k] < o) ++k;  // (every offset is in offs)
+          if (x + d.dx[k] < 0 || x + d.dx[k] >= L || y + d.dy[k] < 0 || y + d.dy[k] >= d.ny)
+            return false;
+        }
       }
-    }
-    return true;
+      return true;
+    });
   };
   DiaInfo d;
   for (int P : cand)
@@ -123,17 +148,38 @@ static bool plane_structure(const std::vector<int>& offs, int n, const int* rowp
 bool dia_detect(int n, const int* rowptr, const int* colind, DiaInfo* out) {
   memset(out, 0, sizeof *out);
   if (n < 4096 || rowptr[n] <= 0) return false;
-  std::vector<int> offs;
-  for (int i = 0; i < n; ++i) {
-    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
-      const int o = colind[q] - i;
-      if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
-        offs.push_back(o);
-        if ((int)offs.size() > kMaxDiags) return false;  // not a stencil
+  // Distinct offsets, kept sorted: a row's offsets ascend with its columns,
+  // so one forward walk per row finds (or places) each (linear in nnz); row
+  // ranges on several threads, their sets merged.
+  const int nt_max = 8;
+  std::vector<std::vector<int>> part(nt_max);
+  std::mutex pm;
+  int next_part = 0;
+  const bool few = rows_parallel(n, [&](int i0, int i1) {
+    std::vector<int> offs;
+    for (int i = i0; i < i1; ++i) {
+      size_t k = 0;
+      for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        if (q > rowptr[i] && colind[q] <= colind[q - 1]) return false;  // unsorted row
+        const int o = colind[q] - i;
+        while (k < offs.size() && offs[k] < o) ++k;
+        if (k == offs.size() || offs[k] != o) {
+          offs.insert(offs.begin() + k, o);
+          if ((int)offs.size() > kMaxDiags) return false;  // not a stencil
+        }
+        ++k;
       }
     }
-  }
+    std::lock_guard<std::mutex> lk(pm);
+    part[next_part++] = std::move(offs);
+    return true;
+  });
+  if (!few) return false;
+  std::vector<int> offs;
+  for (const auto& v : part) offs.insert(offs.end(), v.begin(), v.end());
   std::sort(offs.begin(), offs.end());
+  offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+  if ((int)offs.size() > kMaxDiags) return false;
   const int nd = (int)offs.size();
   // Line stride: the candidate (an offset's magnitude) with the smallest ring
   // (2A + 1 windows of a nominal 32 + cw rows); among equal rings the one
@@ -188,11 +234,19 @@ int dia_build(logdet_ctx* h, const int* rowptr, const int* colind) {
   if (!dia_detect(n, rowptr, colind, &best)) return LOGDET_OK;
   const int nd = best.ndiag;
   const int* offs = best.off;
-  // CSR entry -> diagonal index.
+  // CSR entry -> diagonal index (a forward walk per row, as above).
   std::vector<int> slot((size_t)h->nnz);
-  for (int i = 0; i < n; ++i)
-    for (int q = rowptr[i]; q < rowptr[i + 1]; ++q)
-      slot[q] = (int)(std::lower_bound(offs, offs + nd, colind[q] - i) - offs);
+  rows_parallel(n, [&](int i0, int i1) {
+    for (int i = i0; i < i1; ++i) {
+      int k = 0;
+      for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        const int o = colind[q] - i;
+        while (k < nd && offs[k] < o) ++k;
+        slot[q] = k;
+      }
+    }
+    return true;
+  });
   if (cudaMalloc(&h->dia_slot, sizeof(int) * slot.size()) != cudaSuccess) {
     cudaGetLastError();
     h->dia_slot = nullptr;
