@@ -883,7 +883,11 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
   const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
-  const size_t vals = h->kind == 1 ? grid_table_count(h) * 8 : (size_t)h->nnz * (f32 ? 4 : 8);
+  // Scaled values, plus (FP32 blocks of a grid stencil) the values per row
+  // and diagonal of the sweep paths.
+  const bool sweep_vals = f32 && !b16 && h->kind == 0 && h->dia.ndiag > 0 && h->dia_slot;
+  const size_t vals = (h->kind == 1 ? grid_table_count(h) * 8 : (size_t)h->nnz * (f32 ? 4 : 8)) +
+                      (sweep_vals ? (size_t)dia_pad(h->dia.ndiag) * n * 4 : 0);
   const TileGeom g = tile_geom((int)ld, vec, 0, 0, (int)n);
   const size_t ntiles = div_up((int)n, g.tile_rows);
   const size_t part = (size_t)std::max(k, 2) * ld * ntiles * (f32 ? 8 : 8);

@@ -186,3 +186,14 @@ def test_sweep_wait_timeout_reports_and_recovers(monkeypatch):
         assert e.value.code == B.ETIMEOUT
         monkeypatch.delenv("LOGDET_TEST_SWEEP_STALL")
         _same(h.oslq(30, 6, seed=1, precision=B.MIXED_FP32), want)
+
+
+def test_memory_estimate_counts_sweep_values():
+    # Admission by memory: an FP32 solve of a grid stencil also holds the
+    # values per row and diagonal (16 floats per row for 13 diagonals).
+    A = W.matern_2d(90, 0.05, dtype=np.float32)
+    with B.Handle.from_csr(A) as hs, _device_handle(A) as hc:
+        a = hs.estimate_bytes(B.METHOD_OSLQ, 30, 12, precision=B.MIXED_FP32)
+        b = hc.estimate_bytes(B.METHOD_OSLQ, 30, 12, precision=B.MIXED_FP32)
+        assert a - b == 16 * A.n * 4
+        assert hs.estimate_bytes(B.METHOD_OSLQ, 30, 12) == hc.estimate_bytes(B.METHOD_OSLQ, 30, 12)
