@@ -32,6 +32,9 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
                                                        int n, int s, int ntiles,
                                                        double* __restrict__ part) {
   __shared__ double sy[kGramChunk * kMaxSketch];
+  // Rows staged at a time: the buffer's capacity for s columns (32 for the
+  // largest sketch, more for small ones: fewer barriers per tile).
+  const int chunk = kGramChunk * (kMaxSketch / s);
   const int npairs = s * (s + 1) / 2;
   // Pairs owned by this thread: threadIdx.x + q * blockDim.x for q < nq.
   const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
@@ -48,8 +51,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
     for (int q = 0; q < kGramNP; ++q) acc[q] = 0.0;
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
-    for (int c0 = row0; c0 < row1; c0 += kGramChunk) {
-      const int rows = min(kGramChunk, row1 - c0);
+    for (int c0 = row0; c0 < row1; c0 += chunk) {
+      const int rows = min(chunk, row1 - c0);
       __syncthreads();
       for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
         int r = e / s, i = e - r * s;
@@ -201,7 +204,14 @@ size_t orth_workspace_doubles(int n, int s) {
   return npairs * ntiles + 2 * (size_t)s * s + 64;
 }
 
-static int grid_for(int tiles) { return std::max(1, std::min(tiles, 4 * sm_count())); }
+// Persistent grids: 4 CTAs per SM, or for CTAs of fewer than 256 threads
+// (small sketches: one thread per Gram pair, one warp per 4 columns) enough
+// CTAs for 32 warps per SM, up to 16 (with 4 CTAs of 64 threads an SM held 8
+// warps, and these latency-bound loops idled).
+static int grid_for(int tiles, int threads = 256) {
+  const int per_sm = threads >= 256 ? 4 : std::min(16, std::max(4, 1024 / std::max(32, threads)));
+  return std::max(1, std::min(tiles, per_sm * sm_count()));
+}
 
 int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
               int* keep_dev, int* s_eff_host, cudaStream_t st) {
@@ -235,14 +245,15 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
     prof_count();
     prof_count();
     prof_count();
-    k_gram<<<grid_for(ntiles), gram_threads, 0, st>>>(src, ldsrc, n, s, ntiles, part);
+    k_gram<<<grid_for(ntiles, gram_threads), gram_threads, 0, st>>>(src, ldsrc, n, s, ntiles,
+                                                                     part);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<npairs, 128, 0, st>>>(part, ntiles, s, C);
     LD_CHECK_LAUNCH();
     // R14: |R_ii| <= 1e-6 max_j |y_j|  <=>  R_ii^2 <= 1e-12 max_j C_jj.
     k_chol_inv<<<1, 256, 0, st>>>(C, s, 1e-12, Rinv, keep);
     LD_CHECK_LAUNCH();
-    k_apply_rinv<<<grid_for(div_up(n, 32)), apply_threads, apply_smem, st>>>(src, ldsrc, n, s,
+    k_apply_rinv<<<grid_for(div_up(n, 32), apply_threads), apply_threads, apply_smem, st>>>(src, ldsrc, n, s,
                                                                              Rinv, A, lda);
     LD_CHECK_LAUNCH();
     src = A;
@@ -273,6 +284,7 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
   if (keyp) key = *keyp;
   __shared__ double sa[kGramChunk * kMaxSketch];
   __shared__ double sg[kGramChunk * kMaxSketch];
+  const int chunk = kGramChunk * (kMaxSketch / max(s, r));  // rows staged at a time
   const int npairs = s * r;
   const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
   int pi[kProjNP], pj[kProjNP];
@@ -288,8 +300,8 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
     for (int q = 0; q < kProjNP; ++q) acc[q] = 0.0;
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
-    for (int c0 = row0; c0 < row1; c0 += kGramChunk) {
-      const int rows = min(kGramChunk, row1 - c0);
+    for (int c0 = row0; c0 < row1; c0 += chunk) {
+      const int rows = min(chunk, row1 - c0);
       __syncthreads();
       for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
         int rr = e / s, i = e - rr * s;
@@ -314,6 +326,12 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
   }
 }
 
+// Rows of A that k_project stages at a time: the buffer's capacity for s
+// columns (at least kGramChunk).
+__host__ __device__ inline int project_chunk(int s) {
+  return kGramChunk * (kMaxSketch / (s > 0 ? s : kMaxSketch));
+}
+
 // X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j]
 __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n, int s, int r,
                                                  uint64_t key, const uint64_t* __restrict__ keyp,
@@ -323,8 +341,9 @@ __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n
   __shared__ double sb[kMaxSketch * kMaxSketch];
   __shared__ double sa[kGramChunk * kMaxSketch];
   for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = Bm[e];
-  for (int c0 = blockIdx.x * kGramChunk; c0 < n; c0 += gridDim.x * kGramChunk) {
-    const int rows = min(kGramChunk, n - c0);
+  const int chunk = project_chunk(s);  // rows staged at a time
+  for (int c0 = blockIdx.x * chunk; c0 < n; c0 += gridDim.x * chunk) {
+    const int rows = min(chunk, n - c0);
     __syncthreads();
     for (int e = threadIdx.x; e < rows * s; e += blockDim.x) {
       int rr = e / s, i = e - rr * s;
@@ -370,13 +389,13 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
     // As few threads as keep the per-thread pair count at its minimum.
     const int np = s * r, per = div_up(np, kGramThreads);
     const int atg_threads = std::min(kGramThreads, div_up(div_up(np, per), 32) * 32);
-    k_atg<<<grid_for(ntiles), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp, ntiles, part,
-                                                    gaussian);
+    k_atg<<<grid_for(ntiles, atg_threads), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp,
+                                                                 ntiles, part, gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
   }
-  k_project<<<grid_for(div_up(n, kGramChunk)), 256, 0, st>>>(A, lda, n, s, r, key, keyp, Bm, X,
+  k_project<<<grid_for(div_up(n, project_chunk(s))), 256, 0, st>>>(A, lda, n, s, r, key, keyp, Bm, X,
                                                              ldx, zcol0, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
