@@ -18,7 +18,6 @@ namespace ld {
 constexpr int kGramThreads = 256;
 constexpr int kGramRows = 256;   // rows per tile (one partial per tile)
 constexpr int kGramChunk = 32;   // rows staged in shared memory at a time
-constexpr int kGramNP = (kMaxSketch * (kMaxSketch + 1) / 2 + kGramThreads - 1) / kGramThreads;
 
 __device__ __forceinline__ void unrank_upper(int q, int s, int& i, int& j) {
   i = 0;
@@ -28,6 +27,11 @@ __device__ __forceinline__ void unrank_upper(int q, int s, int& i, int& j) {
 }
 
 // Per-tile partial Gram sums sum_rows y_i y_j (i <= j), written [pair][tile].
+// Thread t owns pairs t + q * blockDim.x for q < NP, NP the smallest count
+// that covers all pairs (a compile-time loop: the FP64 pipe sees no
+// predicated-off multiply-adds; spare slots repeat pair (0, 0) and are not
+// written).
+template <int NP>
 __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict__ Y, int ldy,
                                                        int n, int s, int ntiles,
                                                        double* __restrict__ part) {
@@ -36,19 +40,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
   // largest sketch, more for small ones: fewer barriers per tile).
   const int chunk = kGramChunk * (kMaxSketch / s);
   const int npairs = s * (s + 1) / 2;
-  // Pairs owned by this thread: threadIdx.x + q * blockDim.x for q < nq.
-  const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
-  int pi[kGramNP], pj[kGramNP];
+  int pi[NP], pj[NP];
 #pragma unroll
-  for (int q = 0; q < kGramNP; ++q) {
+  for (int q = 0; q < NP; ++q) {
     int idx = threadIdx.x + q * blockDim.x;
     if (idx < npairs) unrank_upper(idx, s, pi[q], pj[q]);
     else { pi[q] = 0; pj[q] = 0; }
   }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double acc[kGramNP];
+    double acc[NP];
 #pragma unroll
-    for (int q = 0; q < kGramNP; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
     for (int c0 = row0; c0 < row1; c0 += chunk) {
@@ -59,14 +61,14 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
         sy[r * s + i] = Y[(size_t)(c0 + r) * ldy + i];
       }
       __syncthreads();
-      for (int r = 0; r < rows; ++r) {
+      const double* row = sy;
+      for (int r = 0; r < rows; ++r, row += s) {
 #pragma unroll
-        for (int q = 0; q < kGramNP; ++q)
-          if (q < nq) acc[q] = fma(sy[r * s + pi[q]], sy[r * s + pj[q]], acc[q]);
+        for (int q = 0; q < NP; ++q) acc[q] = fma(row[pi[q]], row[pj[q]], acc[q]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kGramNP; ++q) {
+    for (int q = 0; q < NP; ++q) {
       int idx = threadIdx.x + q * blockDim.x;
       if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
     }
@@ -207,10 +209,44 @@ size_t orth_workspace_doubles(int n, int s) {
 // Persistent grids: 4 CTAs per SM, or for CTAs of fewer than 256 threads
 // (small sketches: one thread per Gram pair, one warp per 4 columns) enough
 // CTAs for 32 warps per SM, up to 16 (with 4 CTAs of 64 threads an SM held 8
-// warps, and these latency-bound loops idled).
-static int grid_for(int tiles, int threads = 256) {
-  const int per_sm = threads >= 256 ? 4 : std::min(16, std::max(4, 1024 / std::max(32, threads)));
+// warps, and these loops idled) -- never more than the SM can hold at once
+// with the kernel's shared memory and registers: a grid past that runs its
+// last CTAs as a second wave, each with a whole CTA's share of the tiles
+// (16 CTAs of 16 KB asked for, 14 resident: the Gram took twice its time).
+template <typename Kern>
+static int grid_for(Kern kern, int tiles, int threads = 256, size_t dyn_smem = 0) {
+  int per_sm = threads >= 256 ? 4 : std::min(16, std::max(4, 1024 / std::max(32, threads)));
+  int fit = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, threads, dyn_smem) == cudaSuccess &&
+      fit > 0)
+    per_sm = std::min(per_sm, fit);
+  else
+    (void)cudaGetLastError();
   return std::max(1, std::min(tiles, per_sm * sm_count()));
+}
+
+// Pairs per thread of the Gram and A^T G kernels: the smallest instance that
+// covers `per` (the pair count over at most kGramThreads threads; up to 9 for
+// the Gram of 64 columns, 16 for A^T G of 64 x 64).
+static int pairs_instance(int per) {
+  static const int kInst[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  for (int v : kInst)
+    if (v >= per) return v;
+  return 16;
+}
+
+using GramKern = void (*)(const double*, int, int, int, int, double*);
+static GramKern gram_kernel(int np) {
+  switch (np) {
+    case 1: return k_gram<1>;
+    case 2: return k_gram<2>;
+    case 3: return k_gram<3>;
+    case 4: return k_gram<4>;
+    case 6: return k_gram<6>;
+    case 8: return k_gram<8>;
+    case 12: return k_gram<12>;
+    default: return k_gram<16>;
+  }
 }
 
 int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
@@ -232,9 +268,12 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
   }
   const double* src = Y;
   int ldsrc = ldy;
-  // Gram: one thread per (i <= j) pair while they fit in one CTA, so few
-  // lanes idle.  Apply: one warp per 4 output columns.
-  const int gram_threads = npairs <= kGramThreads ? (npairs + 31) / 32 * 32 : kGramThreads;
+  // Gram: one thread per (i <= j) pair while they fit in one CTA, else as
+  // few threads as keep the pairs per thread at their minimum.  Apply: one
+  // warp per 4 output columns.
+  const int gram_np = pairs_instance(div_up(npairs, kGramThreads));
+  const int gram_threads = std::min(kGramThreads, div_up(div_up(npairs, gram_np), 32) * 32);
+  const GramKern gram = gram_kernel(gram_np);
   const int apply_threads = 32 * div_up(s, kApplyCols);
   const size_t apply_smem = sizeof(double) * ((size_t)s * s + 32 * (size_t)(s | 1));
   if (apply_smem > 48 * 1024)
@@ -245,16 +284,16 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
     prof_count();
     prof_count();
     prof_count();
-    k_gram<<<grid_for(ntiles, gram_threads), gram_threads, 0, st>>>(src, ldsrc, n, s, ntiles,
-                                                                     part);
+    gram<<<grid_for(gram, ntiles, gram_threads), gram_threads, 0, st>>>(src, ldsrc, n, s, ntiles,
+                                                                         part);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<npairs, 128, 0, st>>>(part, ntiles, s, C);
     LD_CHECK_LAUNCH();
     // R14: |R_ii| <= 1e-6 max_j |y_j|  <=>  R_ii^2 <= 1e-12 max_j C_jj.
     k_chol_inv<<<1, 256, 0, st>>>(C, s, 1e-12, Rinv, keep);
     LD_CHECK_LAUNCH();
-    k_apply_rinv<<<grid_for(div_up(n, 32), apply_threads), apply_threads, apply_smem, st>>>(src, ldsrc, n, s,
-                                                                             Rinv, A, lda);
+    k_apply_rinv<<<grid_for(k_apply_rinv, div_up(n, 32), apply_threads, apply_smem),
+                   apply_threads, apply_smem, st>>>(src, ldsrc, n, s, Rinv, A, lda);
     LD_CHECK_LAUNCH();
     src = A;
     ldsrc = lda;
@@ -274,8 +313,9 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
 // ===========================================================================
 // Hutch++ residual probes: Z = G - A (A^T G), G generated from the probe hash.
 // ===========================================================================
-constexpr int kProjNP = (kMaxSketch * kMaxSketch + kGramThreads - 1) / kGramThreads;
-
+// Per-tile partials of A^T G, written [i * r + j][tile]; thread t owns pairs
+// t + q * blockDim.x for q < NP (compile-time, as in k_gram).
+template <int NP>
 __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__ A, int lda,
                                                       int n, int s, int r, uint64_t key,
                                                       const uint64_t* __restrict__ keyp,
@@ -286,18 +326,17 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
   __shared__ double sg[kGramChunk * kMaxSketch];
   const int chunk = kGramChunk * (kMaxSketch / max(s, r));  // rows staged at a time
   const int npairs = s * r;
-  const int nq = npairs > (int)threadIdx.x ? (npairs - 1 - (int)threadIdx.x) / (int)blockDim.x + 1 : 0;
-  int pi[kProjNP], pj[kProjNP];
+  int pi[NP], pj[NP];
 #pragma unroll
-  for (int q = 0; q < kProjNP; ++q) {
+  for (int q = 0; q < NP; ++q) {
     int idx = threadIdx.x + q * blockDim.x;
     pi[q] = idx < npairs ? idx / r : 0;
     pj[q] = idx < npairs ? idx - (idx / r) * r : 0;
   }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double acc[kProjNP];
+    double acc[NP];
 #pragma unroll
-    for (int q = 0; q < kProjNP; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
     for (int c0 = row0; c0 < row1; c0 += chunk) {
@@ -312,14 +351,15 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
         sg[rr * r + j] = probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
       }
       __syncthreads();
-      for (int rr = 0; rr < rows; ++rr) {
+      const double* ra = sa;
+      const double* rg = sg;
+      for (int rr = 0; rr < rows; ++rr, ra += s, rg += r) {
 #pragma unroll
-        for (int q = 0; q < kProjNP; ++q)
-          if (q < nq) acc[q] = fma(sa[rr * s + pi[q]], sg[rr * r + pj[q]], acc[q]);
+        for (int q = 0; q < NP; ++q) acc[q] = fma(ra[pi[q]], rg[pj[q]], acc[q]);
       }
     }
 #pragma unroll
-    for (int q = 0; q < kProjNP; ++q) {
+    for (int q = 0; q < NP; ++q) {
       int idx = threadIdx.x + q * blockDim.x;
       if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
     }
@@ -372,6 +412,21 @@ size_t project_workspace_doubles(int n, int s, int r) {
   return (size_t)s * r * ntiles + (size_t)s * r + 64;
 }
 
+using AtgKern = void (*)(const double*, int, int, int, int, uint64_t, const uint64_t*, int,
+                        double*, int);
+static AtgKern atg_kernel(int np) {
+  switch (np) {
+    case 1: return k_atg<1>;
+    case 2: return k_atg<2>;
+    case 3: return k_atg<3>;
+    case 4: return k_atg<4>;
+    case 6: return k_atg<6>;
+    case 8: return k_atg<8>;
+    case 12: return k_atg<12>;
+    default: return k_atg<16>;
+  }
+}
+
 int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
                           double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
                           int gaussian, const uint64_t* keyp) {
@@ -387,16 +442,17 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
     prof_count();
     prof_count();
     // As few threads as keep the per-thread pair count at its minimum.
-    const int np = s * r, per = div_up(np, kGramThreads);
+    const int np = s * r, per = pairs_instance(div_up(np, kGramThreads));
     const int atg_threads = std::min(kGramThreads, div_up(div_up(np, per), 32) * 32);
-    k_atg<<<grid_for(ntiles, atg_threads), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp,
-                                                                 ntiles, part, gaussian);
+    const AtgKern atg = atg_kernel(per);
+    atg<<<grid_for(atg, ntiles, atg_threads), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp,
+                                                                     ntiles, part, gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
   }
-  k_project<<<grid_for(div_up(n, project_chunk(s))), 256, 0, st>>>(A, lda, n, s, r, key, keyp, Bm, X,
-                                                             ldx, zcol0, gaussian);
+  k_project<<<grid_for(k_project, div_up(n, project_chunk(s))), 256, 0, st>>>(
+      A, lda, n, s, r, key, keyp, Bm, X, ldx, zcol0, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
@@ -452,7 +508,8 @@ int colnorm_partials(const T* X, int n, int ld, int tile_rows, int ntiles,
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
   ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ld, (double)n * ld * sizeof(T));
-  k_colnorm<T><<<grid_for(ntiles), threads, smem, st>>>(X, n, ld, tile_rows, ntiles, part);
+  k_colnorm<T><<<grid_for(k_colnorm<T>, ntiles, threads, smem), threads, smem, st>>>(
+      X, n, ld, tile_rows, ntiles, part);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
