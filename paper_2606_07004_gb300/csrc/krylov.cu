@@ -61,8 +61,17 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
 
+// FP64 instances with the full dot window hold two CTAs per SM: at 85
+// registers one 480-thread CTA fit, and the update pass of OSA-IOP k = 8
+// then ran at half the FP64 and HBM peaks (a few spilled registers cost
+// less than the second CTA gains).  0 leaves every other instance's
+// register choice to the compiler, as without the hint.
+template <typename T, int N>
+constexpr int fp64_wide_min_ctas() { return (std::is_same<T, double>::value && N >= kMaxWin) ? 2 : 0; }
+
 template <typename T, int NDOT>
-__global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<T> B) {
+__global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
+    k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
   using CT = typename Compute<T>::type;
@@ -297,7 +306,8 @@ __global__ void __launch_bounds__(512) k_spmm(const __grid_constant__ SpmmBatch<
 // pass 2: out = ycoef*y - sum_i coef_i basis_i;  |out|^2 [; extra . out]
 // ---------------------------------------------------------------------------
 template <typename T, int NB>
-__global__ void __launch_bounds__(512) k_update(const __grid_constant__ UpdBatch<T> B) {
+__global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NB>())
+    k_update(const __grid_constant__ UpdBatch<T> B) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
   using CT = typename Compute<T>::type;
