@@ -305,8 +305,16 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
 // ---------------------------------------------------------------------------
 // pass 2: out = ycoef*y - sum_i coef_i basis_i;  |out|^2 [; extra . out]
 // ---------------------------------------------------------------------------
+// FP64 update instances held at two CTAs per SM: the full window (see
+// fp64_wide_min_ctas) and the software-pipelined NB <= 2 loop below (its
+// prefetched row fits 64 registers).
 template <typename T, int NB>
-__global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NB>())
+constexpr int update_min_ctas() {
+  return (std::is_same<T, double>::value && (NB >= kMaxWin || NB <= 2)) ? 2 : 0;
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
     k_update(const __grid_constant__ UpdBatch<T> B) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
@@ -394,6 +402,58 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NB>())
 #pragma unroll
             for (int v = 0; v < V; ++v) ex[v].fma(ue[q][v], o[q][v]);
           }
+        }
+      }
+      } else if constexpr (std::is_same<T, double>::value && NB <= 2) {
+      // FP64 with up to two basis vectors: the next row's loads are issued
+      // before this row's arithmetic, so the FP64 pipe works while they are
+      // in flight (one row at a time left it and HBM both half idle).  The
+      // operations and their order per row are those of the loop below.
+      CT py[V], pu[NB][V], pe[V];
+      int row = row0 + r;
+      if (row < row1) {
+        const size_t off = (size_t)row * J.ld + col0;
+        load_vec<T>(J.y + off, py);
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+          if (i < nb) load_vec<T>(J.basis[i] + off, pu[i]);
+        if (has_extra) load_vec<T>(J.extra + off, pe);
+      }
+      for (; row < row1; row += R) {
+        const size_t off = (size_t)row * J.ld + col0;
+        CT o[V], u[NB][V], e[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          o[v] = py[v];
+          e[v] = pe[v];
+#pragma unroll
+          for (int i = 0; i < NB; ++i) u[i][v] = pu[i][v];
+        }
+        if (row + R < row1) {
+          const size_t noff = off + (size_t)R * J.ld;
+          load_vec<T>(J.y + noff, py);
+#pragma unroll
+          for (int i = 0; i < NB; ++i)
+            if (i < nb) load_vec<T>(J.basis[i] + noff, pu[i]);
+          if (has_extra) load_vec<T>(J.extra + noff, pe);
+        }
+        if (!unit) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          if (i < nb) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[i][v], o[v]);
+          }
+        }
+        store_vec<T>(J.out + off, o);
+#pragma unroll
+        for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
+        if (has_extra) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) ex[v].fma(e[v], o[v]);
         }
       }
       } else {
