@@ -40,7 +40,8 @@ SOLVES_PER_STEP = 1 + len(WINDOWS)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 FMA lanes x clock
 PROFILE_MD = os.path.join(ROOT, "profiles", "k_spmm_fp64_laplacian3d_100.md")  # noqa
-KRYLOV_SRC = os.path.join(ROOT, "paper_2606_07004_gb300", "csrc", "krylov.cu")
+CSRC = os.path.join(ROOT, "paper_2606_07004_gb300", "csrc")
+KRYLOV_SRC = os.path.join(CSRC, "krylov.cu")
 
 
 def workload_config():
@@ -321,13 +322,33 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 # CUDA arm
 # ---------------------------------------------------------------------------
+def spmm_kernel_digest():
+    """SHA-256 of the CSR SpMM kernel's source: krylov.cu from its launch-bound
+    helper through the kernel's closing brace, then krylov.cuh and common.cuh
+    (the headers it includes).  Edits elsewhere in krylov.cu leave it alone."""
+    text = open(KRYLOV_SRC).read()
+    i0 = text.index("constexpr int fp64_wide_min_ctas()")
+    i1 = text.index("k_spmm(const __grid_constant__ SpmmBatch<T> B) {", i0)
+    depth, j = 0, text.index("{", i1)
+    while True:
+        c = text[j]
+        depth += (c == "{") - (c == "}")
+        j += 1
+        if depth == 0:
+            break
+    h = hashlib.sha256(text[i0:j].encode())
+    for name in ("krylov.cuh", "common.cuh"):
+        h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()
+
+
 def traffic_ratio_from_profile():
     """DRAM bytes / algorithmic bytes of the SpMM kernel from the committed ncu
     summary (a smaller grid of the same operator), if it was taken on the
     current kernel source; the bench scales it by its own per-launch bytes."""
     try:
         text = open(PROFILE_MD).read()
-        src = hashlib.sha256(open(KRYLOV_SRC, "rb").read()).hexdigest()
+        src = spmm_kernel_digest()
         m_src = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
         m_tr = re.search(r"traffic_over_algorithmic:\s*([0-9.eE+]+)", text)
         if m_src and m_tr and m_src.group(1) == src:
