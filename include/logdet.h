@@ -49,7 +49,9 @@ extern "C" {
 
 #define LOGDET_FP64        0  /* everything in IEEE binary64 */
 #define LOGDET_MIXED_FP32  1  /* FP32 values and vectors, compensated FP32 dots,
-                                 FP64 Hutch++ QR and small solves */
+                                 OSLQ's Hutch++ QR and projection in FP32 with
+                                 compensated Gram sums (FP64 Cholesky factor),
+                                 FP64 small solves */
 #define LOGDET_MIXED_BF16VEC 2 /* as MIXED_FP32 but the Krylov vectors are stored in
                                  BF16 (FP32 arithmetic): a trial of the error budget */
 

@@ -26,16 +26,25 @@ __device__ __forceinline__ void unrank_upper(int q, int s, int& i, int& j) {
   j = i + rem;
 }
 
+// Accumulator of the Gram and A^T G sums per element type: FP64 FMA for
+// FP64 blocks; for FP32 blocks the compensated dot (Dot2) of FP32 inputs,
+// whose partial is read out in FP64 (error ~ (rows eps_32)^2 of the sum of
+// |products|, far below FP32 rounding).
+template <typename TY> struct GramAcc;
+template <> struct GramAcc<double> { using type = AccD; };
+template <> struct GramAcc<float> { using type = AccF; };
+
 // Per-tile partial Gram sums sum_rows y_i y_j (i <= j), written [pair][tile].
 // Thread t owns pairs t + q * blockDim.x for q < NP, NP the smallest count
 // that covers all pairs (a compile-time loop: the FP64 pipe sees no
 // predicated-off multiply-adds; spare slots repeat pair (0, 0) and are not
 // written).
-template <int NP>
-__global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict__ Y, int ldy,
+template <int NP, typename TY>
+__global__ void __launch_bounds__(kGramThreads) k_gram(const TY* __restrict__ Y, int ldy,
                                                        int n, int s, int ntiles,
                                                        double* __restrict__ part) {
-  __shared__ double sy[kGramChunk * kMaxSketch];
+  __shared__ double sy_raw[kGramChunk * kMaxSketch];
+  TY* sy = reinterpret_cast<TY*>(sy_raw);
   // Rows staged at a time: the buffer's capacity for s columns (32 for the
   // largest sketch, more for small ones: fewer barriers per tile).
   const int chunk = kGramChunk * (kMaxSketch / s);
@@ -48,9 +57,9 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
     else { pi[q] = 0; pj[q] = 0; }
   }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double acc[NP];
+    typename GramAcc<TY>::type acc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NP; ++q) acc[q].zero();
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
     for (int c0 = row0; c0 < row1; c0 += chunk) {
@@ -61,16 +70,16 @@ __global__ void __launch_bounds__(kGramThreads) k_gram(const double* __restrict_
         sy[r * s + i] = Y[(size_t)(c0 + r) * ldy + i];
       }
       __syncthreads();
-      const double* row = sy;
+      const TY* row = sy;
       for (int r = 0; r < rows; ++r, row += s) {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) acc[q] = fma(row[pi[q]], row[pj[q]], acc[q]);
+        for (int q = 0; q < NP; ++q) acc[q].fma(row[pi[q]], row[pj[q]]);
       }
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       int idx = threadIdx.x + q * blockDim.x;
-      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
+      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q].value();
     }
   }
 }
@@ -157,21 +166,24 @@ __global__ void __launch_bounds__(256) k_chol_inv(const double* __restrict__ C, 
 }
 
 // A[row, l] = sum_{i <= l} Y[row, i] Rinv[i, l]; A may alias Y.  A chunk of
-// 32 rows is staged in shared memory (row stride odd, so the lanes' 8-byte
-// reads of one column spread over the banks); warp w computes output columns
+// 32 rows is staged in shared memory (row stride odd, so the lanes' reads of
+// one column spread over the banks); warp w computes output columns
 // [4w, 4w + 4) of all 32 rows, lane = row, so every lane of a warp runs the
 // same triangular loop (i <= 4w + 3; the extra terms multiply zeros of the
-// upper-triangular Rinv and change nothing).  Dynamic shared memory:
-// s * s + 32 * (s | 1) doubles.
+// upper-triangular Rinv and change nothing).  FP32 blocks take Rinv rounded
+// to FP32 (a slightly different triangular preconditioner: the second
+// round orthonormalises what the first leaves).  Dynamic shared memory:
+// s * s + 32 * (s | 1) elements.
 constexpr int kApplyCols = 4;
-__global__ void __launch_bounds__(512) k_apply_rinv(const double* Y, int ldy, int n, int s,
-                                                    const double* __restrict__ Rinv, double* A,
+template <typename TY>
+__global__ void __launch_bounds__(512) k_apply_rinv(const TY* Y, int ldy, int n, int s,
+                                                    const double* __restrict__ Rinv, TY* A,
                                                     int lda) {
   extern __shared__ double smem_ar[];
   const int S1 = s | 1;
-  double* sr = smem_ar;
-  double* sy = smem_ar + s * s;
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) sr[e] = Rinv[e];
+  TY* sr = reinterpret_cast<TY*>(smem_ar);
+  TY* sy = sr + s * s;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) sr[e] = (TY)Rinv[e];
   const int lane = threadIdx.x & 31;
   const int l0 = (threadIdx.x >> 5) * kApplyCols;
   for (int c0 = blockIdx.x * 32; c0 < n; c0 += gridDim.x * 32) {
@@ -183,12 +195,12 @@ __global__ void __launch_bounds__(512) k_apply_rinv(const double* Y, int ldy, in
     }
     __syncthreads();
     if (lane < rows && l0 < s) {
-      double acc[kApplyCols];
+      TY acc[kApplyCols];
 #pragma unroll
-      for (int q = 0; q < kApplyCols; ++q) acc[q] = 0.0;
+      for (int q = 0; q < kApplyCols; ++q) acc[q] = TY(0);
       const int lmax = min(l0 + kApplyCols, s);
       for (int i = 0; i < lmax; ++i) {
-        const double y = sy[lane * S1 + i];
+        const TY y = sy[lane * S1 + i];
 #pragma unroll
         for (int q = 0; q < kApplyCols; ++q)
           if (l0 + q < s) acc[q] = fma(y, sr[i * s + l0 + q], acc[q]);
@@ -235,22 +247,24 @@ static int pairs_instance(int per) {
   return 16;
 }
 
-using GramKern = void (*)(const double*, int, int, int, int, double*);
-static GramKern gram_kernel(int np) {
+template <typename TY>
+using GramKern = void (*)(const TY*, int, int, int, int, double*);
+template <typename TY>
+static GramKern<TY> gram_kernel(int np) {
   switch (np) {
-    case 1: return k_gram<1>;
-    case 2: return k_gram<2>;
-    case 3: return k_gram<3>;
-    case 4: return k_gram<4>;
-    case 6: return k_gram<6>;
-    case 8: return k_gram<8>;
-    case 12: return k_gram<12>;
-    default: return k_gram<16>;
+    case 1: return k_gram<1, TY>;
+    case 2: return k_gram<2, TY>;
+    case 3: return k_gram<3, TY>;
+    case 4: return k_gram<4, TY>;
+    case 6: return k_gram<6, TY>;
+    case 8: return k_gram<8, TY>;
+    default: return k_gram<12, TY>;  // 64 columns: 2080 pairs, 9 per thread
   }
 }
 
-int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
-              int* keep_dev, int* s_eff_host, cudaStream_t st) {
+template <typename TY>
+static int orth_t(int n, int s, const TY* Y, int ldy, TY* A, int lda, double* ws,
+                  int* keep_dev, int* s_eff_host, cudaStream_t st) {
   if (s < 1 || s > kMaxSketch || n < 1) {
     set_error("orth: s=%d must be in [1, %d]", s, kMaxSketch);
     return LOGDET_EINVAL;
@@ -266,21 +280,21 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
     LD_CUDA(cudaMallocAsync(&keep_tmp, sizeof(int) * s, st));
     keep = keep_tmp;
   }
-  const double* src = Y;
+  const TY* src = Y;
   int ldsrc = ldy;
   // Gram: one thread per (i <= j) pair while they fit in one CTA, else as
   // few threads as keep the pairs per thread at their minimum.  Apply: one
   // warp per 4 output columns.
   const int gram_np = pairs_instance(div_up(npairs, kGramThreads));
   const int gram_threads = std::min(kGramThreads, div_up(div_up(npairs, gram_np), 32) * 32);
-  const GramKern gram = gram_kernel(gram_np);
+  const GramKern<TY> gram = gram_kernel<TY>(gram_np);
   const int apply_threads = 32 * div_up(s, kApplyCols);
-  const size_t apply_smem = sizeof(double) * ((size_t)s * s + 32 * (size_t)(s | 1));
+  const size_t apply_smem = sizeof(TY) * ((size_t)s * s + 32 * (size_t)(s | 1));
   if (apply_smem > 48 * 1024)
-    LD_CUDA(cudaFuncSetAttribute(k_apply_rinv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LD_CUDA(cudaFuncSetAttribute(k_apply_rinv<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)apply_smem));
   for (int round = 0; round < 2; ++round) {
-    ProfScope prof(KC_QR, st, 2.0 * n * (double)s * s * 2.0, 2.0 * 8.0 * n * s);
+    ProfScope prof(KC_QR, st, 2.0 * n * (double)s * s * 2.0, 2.0 * sizeof(TY) * n * s);
     prof_count();
     prof_count();
     prof_count();
@@ -292,8 +306,8 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
     // R14: |R_ii| <= 1e-6 max_j |y_j|  <=>  R_ii^2 <= 1e-12 max_j C_jj.
     k_chol_inv<<<1, 256, 0, st>>>(C, s, 1e-12, Rinv, keep);
     LD_CHECK_LAUNCH();
-    k_apply_rinv<<<grid_for(k_apply_rinv, div_up(n, 32), apply_threads, apply_smem),
-                   apply_threads, apply_smem, st>>>(src, ldsrc, n, s, Rinv, A, lda);
+    k_apply_rinv<TY><<<grid_for(k_apply_rinv<TY>, div_up(n, 32), apply_threads, apply_smem),
+                       apply_threads, apply_smem, st>>>(src, ldsrc, n, s, Rinv, A, lda);
     LD_CHECK_LAUNCH();
     src = A;
     ldsrc = lda;
@@ -310,20 +324,32 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
   return LOGDET_OK;
 }
 
+int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double* ws,
+              int* keep_dev, int* s_eff_host, cudaStream_t st) {
+  return orth_t<double>(n, s, Y, ldy, A, lda, ws, keep_dev, s_eff_host, st);
+}
+
+int orth_f32(int n, int s, const float* Y, int ldy, float* A, int lda, double* ws,
+             int* keep_dev, cudaStream_t st) {
+  return orth_t<float>(n, s, Y, ldy, A, lda, ws, keep_dev, nullptr, st);
+}
+
 // ===========================================================================
 // Hutch++ residual probes: Z = G - A (A^T G), G generated from the probe hash.
 // ===========================================================================
 // Per-tile partials of A^T G, written [i * r + j][tile]; thread t owns pairs
 // t + q * blockDim.x for q < NP (compile-time, as in k_gram).
-template <int NP>
-__global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__ A, int lda,
+template <int NP, typename TY>
+__global__ void __launch_bounds__(kGramThreads) k_atg(const TY* __restrict__ A, int lda,
                                                       int n, int s, int r, uint64_t key,
                                                       const uint64_t* __restrict__ keyp,
                                                       int ntiles, double* __restrict__ part,
                                                       int gaussian) {
   if (keyp) key = *keyp;
-  __shared__ double sa[kGramChunk * kMaxSketch];
-  __shared__ double sg[kGramChunk * kMaxSketch];
+  __shared__ double sa_raw[kGramChunk * kMaxSketch];
+  __shared__ double sg_raw[kGramChunk * kMaxSketch];
+  TY* sa = reinterpret_cast<TY*>(sa_raw);
+  TY* sg = reinterpret_cast<TY*>(sg_raw);
   const int chunk = kGramChunk * (kMaxSketch / max(s, r));  // rows staged at a time
   const int npairs = s * r;
   int pi[NP], pj[NP];
@@ -334,9 +360,9 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
     pj[q] = idx < npairs ? idx - (idx / r) * r : 0;
   }
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    double acc[NP];
+    typename GramAcc<TY>::type acc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NP; ++q) acc[q].zero();
     const int row0 = tile * kGramRows;
     const int row1 = min(row0 + kGramRows, n);
     for (int c0 = row0; c0 < row1; c0 += chunk) {
@@ -348,20 +374,20 @@ __global__ void __launch_bounds__(kGramThreads) k_atg(const double* __restrict__
       }
       for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
         int rr = e / r, j = e - rr * r;
-        sg[rr * r + j] = probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
+        sg[rr * r + j] = (TY)probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
       }
       __syncthreads();
-      const double* ra = sa;
-      const double* rg = sg;
+      const TY* ra = sa;
+      const TY* rg = sg;
       for (int rr = 0; rr < rows; ++rr, ra += s, rg += r) {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) acc[q] = fma(ra[pi[q]], rg[pj[q]], acc[q]);
+        for (int q = 0; q < NP; ++q) acc[q].fma(ra[pi[q]], rg[pj[q]]);
       }
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       int idx = threadIdx.x + q * blockDim.x;
-      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q];
+      if (idx < npairs) part[(size_t)idx * ntiles + tile] = acc[q].value();
     }
   }
 }
@@ -372,15 +398,19 @@ __host__ __device__ inline int project_chunk(int s) {
   return kGramChunk * (kMaxSketch / (s > 0 ? s : kMaxSketch));
 }
 
-// X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j]
-__global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n, int s, int r,
+// X[row, zcol0 + j] = g(row, j) - sum_i A[row, i] B[i, j] (FP32 blocks: B
+// and g rounded to FP32, the s-term sum in FP32).
+template <typename TY>
+__global__ void __launch_bounds__(256) k_project(const TY* A, int lda, int n, int s, int r,
                                                  uint64_t key, const uint64_t* __restrict__ keyp,
                                                  const double* __restrict__ Bm,
-                                                 double* X, int ldx, int zcol0, int gaussian) {
+                                                 TY* X, int ldx, int zcol0, int gaussian) {
   if (keyp) key = *keyp;
-  __shared__ double sb[kMaxSketch * kMaxSketch];
-  __shared__ double sa[kGramChunk * kMaxSketch];
-  for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = Bm[e];
+  __shared__ double sb_raw[kMaxSketch * kMaxSketch];
+  __shared__ double sa_raw[kGramChunk * kMaxSketch];
+  TY* sb = reinterpret_cast<TY*>(sb_raw);
+  TY* sa = reinterpret_cast<TY*>(sa_raw);
+  for (int e = threadIdx.x; e < s * r; e += blockDim.x) sb[e] = (TY)Bm[e];
   const int chunk = project_chunk(s);  // rows staged at a time
   for (int c0 = blockIdx.x * chunk; c0 < n; c0 += gridDim.x * chunk) {
     const int rows = min(chunk, n - c0);
@@ -392,9 +422,9 @@ __global__ void __launch_bounds__(256) k_project(const double* A, int lda, int n
     __syncthreads();
     for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
       int rr = e / r, j = e - rr * r;
-      double acc = 0.0;
+      TY acc = TY(0);
       for (int i = 0; i < s; ++i) acc = fma(sa[rr * s + i], sb[i * r + j], acc);
-      double g = probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
+      TY g = (TY)probe_value(key, (uint32_t)j, (uint32_t)(c0 + rr), gaussian);
       X[(size_t)(c0 + rr) * ldx + zcol0 + j] = g - acc;
     }
   }
@@ -412,24 +442,27 @@ size_t project_workspace_doubles(int n, int s, int r) {
   return (size_t)s * r * ntiles + (size_t)s * r + 64;
 }
 
-using AtgKern = void (*)(const double*, int, int, int, int, uint64_t, const uint64_t*, int,
-                        double*, int);
-static AtgKern atg_kernel(int np) {
+template <typename TY>
+using AtgKern = void (*)(const TY*, int, int, int, int, uint64_t, const uint64_t*, int, double*,
+                         int);
+template <typename TY>
+static AtgKern<TY> atg_kernel(int np) {
   switch (np) {
-    case 1: return k_atg<1>;
-    case 2: return k_atg<2>;
-    case 3: return k_atg<3>;
-    case 4: return k_atg<4>;
-    case 6: return k_atg<6>;
-    case 8: return k_atg<8>;
-    case 12: return k_atg<12>;
-    default: return k_atg<16>;
+    case 1: return k_atg<1, TY>;
+    case 2: return k_atg<2, TY>;
+    case 3: return k_atg<3, TY>;
+    case 4: return k_atg<4, TY>;
+    case 6: return k_atg<6, TY>;
+    case 8: return k_atg<8, TY>;
+    case 12: return k_atg<12, TY>;
+    default: return k_atg<16, TY>;
   }
 }
 
-int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
-                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
-                          int gaussian, const uint64_t* keyp) {
+template <typename TY>
+static int project_residual_t(int n, int s, int r, const TY* A, int lda, uint64_t key, TY* X,
+                              int ldx, int zcol0, double* ws, cudaStream_t st, int gaussian,
+                              const uint64_t* keyp) {
   if (s > kMaxSketch || r > kMaxSketch || r < 1) {
     set_error("project: s=%d r=%d out of range", s, r);
     return LOGDET_EINVAL;
@@ -437,24 +470,36 @@ int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_
   const int ntiles = div_up(n, kGramRows);
   double* part = ws;
   double* Bm = ws + (size_t)s * r * ntiles;
-  ProfScope prof(KC_PROJECT, st, 4.0 * n * (double)s * r, 8.0 * n * (2.0 * s + r));
+  ProfScope prof(KC_PROJECT, st, 4.0 * n * (double)s * r, sizeof(TY) * n * (2.0 * s + r));
   if (s > 0) {
     prof_count();
     prof_count();
     // As few threads as keep the per-thread pair count at its minimum.
     const int np = s * r, per = pairs_instance(div_up(np, kGramThreads));
     const int atg_threads = std::min(kGramThreads, div_up(div_up(np, per), 32) * 32);
-    const AtgKern atg = atg_kernel(per);
+    const AtgKern<TY> atg = atg_kernel<TY>(per);
     atg<<<grid_for(atg, ntiles, atg_threads), atg_threads, 0, st>>>(A, lda, n, s, r, key, keyp,
                                                                      ntiles, part, gaussian);
     LD_CHECK_LAUNCH();
     k_reduce_rows<<<s * r, 128, 0, st>>>(part, ntiles, 0, Bm);
     LD_CHECK_LAUNCH();
   }
-  k_project<<<grid_for(k_project, div_up(n, project_chunk(s))), 256, 0, st>>>(
+  k_project<TY><<<grid_for(k_project<TY>, div_up(n, project_chunk(s))), 256, 0, st>>>(
       A, lda, n, s, r, key, keyp, Bm, X, ldx, zcol0, gaussian);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
+}
+
+int project_residual_fp64(int n, int s, int r, const double* A, int lda, uint64_t key,
+                          double* X, int ldx, int zcol0, double* ws, cudaStream_t st,
+                          int gaussian, const uint64_t* keyp) {
+  return project_residual_t<double>(n, s, r, A, lda, key, X, ldx, zcol0, ws, st, gaussian, keyp);
+}
+
+int project_residual_f32(int n, int s, int r, const float* A, int lda, uint64_t key, float* X,
+                         int ldx, int zcol0, double* ws, cudaStream_t st, int gaussian,
+                         const uint64_t* keyp) {
+  return project_residual_t<float>(n, s, r, A, lda, key, X, ldx, zcol0, ws, st, gaussian, keyp);
 }
 
 // ===========================================================================

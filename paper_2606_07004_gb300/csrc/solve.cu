@@ -482,6 +482,21 @@ static int hutchpp_split(int n, int s, int r, const double* Y64, int lds, uint64
   return LOGDET_OK;
 }
 
+// The split for an FP32 block computed in FP32 (compensated sums): A into
+// X[:, 0:s], Z into X[:, s:s+r] of the block the Krylov run starts from, so
+// the mixed path needs no FP64 copy of Y or of the block.
+static int hutchpp_split_f32(int n, int s, int r, const float* Y, int lds, uint64_t key_g,
+                             DevBuf<float>& X, int ld, int* keep, cudaStream_t st, int gaussian,
+                             const uint64_t* keyp_g) {
+  LD_TRY(X.alloc((size_t)n * ld));
+  LD_TRY(X.zero());
+  DevBuf<double> ws(st);
+  LD_TRY(ws.alloc(std::max(orth_workspace_doubles(n, s), project_workspace_doubles(n, s, r))));
+  LD_TRY(orth_f32(n, s, Y, lds, X.p, ld, ws.p, keep, st));
+  LD_TRY(project_residual_f32(n, s, r, X.p, ld, key_g, X.p, ld, s, ws.p, st, gaussian, keyp_g));
+  return LOGDET_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Solve<T>
 // ---------------------------------------------------------------------------
@@ -661,9 +676,16 @@ struct Solve : ISolve {
         else LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
       }
       S.release();
+      T* X0;
       if constexpr (std::is_same<T, double>::value) {
         LD_TRY(hutchpp_split(n, s, r, Yt.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
                              dkey(1)));
+        LD_TRY(make_x0(&X0));
+      } else if constexpr (std::is_same<T, float>::value) {
+        LD_TRY(hutchpp_split_f32(n, s, r, Yt.p, lds, probe_key(c.seed, 1), Xc, ld, keep.p, st,
+                                 c.gaussian, dkey(1)));
+        Yt.release();
+        X0 = Xc.p;
       } else {
         DevBuf<double> Y64(st);
         LD_TRY(Y64.alloc((size_t)n * lds));
@@ -671,9 +693,8 @@ struct Solve : ISolve {
         Yt.release();
         LD_TRY(hutchpp_split(n, s, r, Y64.p, lds, probe_key(c.seed, 1), X64, ld, keep.p, st, c.gaussian,
                              dkey(1)));
+        LD_TRY(make_x0(&X0));
       }
-      T* X0;
-      LD_TRY(make_x0(&X0));
       run->colshift = cshift.p;
       run->hctx = h;
       run->gtab = gtabs.p;
