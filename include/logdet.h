@@ -235,6 +235,18 @@ int logdet_spmm(logdet_handle h, const double* x_dev, double* y_dev, int32_t b, 
 int logdet_orth(int32_t n, int32_t s, const double* y_dev, int32_t ldy, double* a_dev,
                 int32_t lda, int32_t* s_eff, void* cuda_stream);
 
+/* logdet_orth_f32: the same step for an FP32 block, as mixed-precision OSLQ
+ * runs it (Algorithm 3's QR of Y = J S): two rounds of Cholesky QR whose Gram
+ * sums are compensated FP32 dots (Dot2) accumulated per 256-row tile and
+ * summed in FP64, an FP64 Cholesky factor, and FP32 applies of its inverse.
+ * A (FP32, n x s in a block of leading dimension lda, a_dev may alias y_dev)
+ * is orthonormal to FP32 rounding and spans the FP32 Y's columns; the column
+ * drop rule and *s_eff are those of logdet_orth.  Device pointers; blocks
+ * until done.  Errors: EINVAL (NULL pointer, s outside [1, 64], ld < s),
+ * ENOMEM, ECUDA. */
+int logdet_orth_f32(int32_t n, int32_t s, const float* y_dev, int32_t ldy, float* a_dev,
+                    int32_t lda, int32_t* s_eff, void* cuda_stream);
+
 /* logdet_quadform: *out = x^T (Q + shift I) x for the handle's operator
  * (CSR or gridded), x an n-vector of doubles on the device — the data term
  * of the Gaussian log-likelihood L(theta) of the GRF study (Sec. 4).  The

@@ -36,7 +36,8 @@ EXPORTED = [
     "logdet_opts_default", "logdet_strerror", "logdet_last_error",
     "logdet_create", "logdet_create_device", "logdet_create_grid", "logdet_destroy", "logdet_info",
     "logdet_grid_structure", "logdet_grid_structure_csr", "logdet_oslq", "logdet_osaiop",
-    "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_quadform", "logdet_orth",
+    "logdet_probe_fill", "logdet_probe_fill_gaussian", "logdet_spmm", "logdet_quadform",
+    "logdet_orth", "logdet_orth_f32",
     "logdet_gauss_quadrature_log", "logdet_hessenberg_log_e1",
     "logdet_launch_count", "logdet_autotune_clear", "logdet_profile_enable", "logdet_profile_reset", "logdet_profile_read",
     "logdet_hessenberg_log_e1_noalloc", "logdet_hessenberg_log_e1_banded",
@@ -108,6 +109,7 @@ _sig("logdet_probe_fill_gaussian", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _
 _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
 _sig("logdet_quadform", C.c_int, [_P, _P, _dbl, C.POINTER(_dbl), _P])
 _sig("logdet_orth", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
+_sig("logdet_orth_f32", C.c_int, [_i32, _i32, _P, _i32, _P, _i32, C.POINTER(_i32), _P])
 _sig("logdet_gauss_quadrature_log", C.c_int, [_P, _P, _P, _i32, _i32, _dbl, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1", C.c_int, [_P, _i32, _P, _i32, _i32, _P, C.POINTER(_u32), _P])
 _sig("logdet_hessenberg_log_e1_banded", C.c_int,
@@ -498,6 +500,13 @@ def logdet_orth(n, s, y, ldy, a, lda, stream=None) -> int:
     se = _i32()
     _check(_lib.logdet_orth(n, s, _ptr(y), ldy, _ptr(a), lda, C.byref(se), _stream(stream)),
            "logdet_orth")
+    return se.value
+
+
+def logdet_orth_f32(n, s, y, ldy, a, lda, stream=None) -> int:
+    se = _i32()
+    _check(_lib.logdet_orth_f32(n, s, _ptr(y), ldy, _ptr(a), lda, C.byref(se), _stream(stream)),
+           "logdet_orth_f32")
     return se.value
 
 

@@ -330,8 +330,8 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
 }
 
 int orth_f32(int n, int s, const float* Y, int ldy, float* A, int lda, double* ws,
-             int* keep_dev, cudaStream_t st) {
-  return orth_t<float>(n, s, Y, ldy, A, lda, ws, keep_dev, nullptr, st);
+             int* keep_dev, int* s_eff_host, cudaStream_t st) {
+  return orth_t<float>(n, s, Y, ldy, A, lda, ws, keep_dev, s_eff_host, st);
 }
 
 // ===========================================================================

@@ -24,9 +24,9 @@ int orth_fp64(int n, int s, const double* Y, int ldy, double* A, int lda, double
 // sums are compensated FP32 dots (Dot2) read out in FP64, the Cholesky
 // factor and its inverse FP64, the applies and the residual in FP32.  A is
 // orthonormal to FP32 rounding, the accuracy the FP32 Krylov runs start
-// from in any case.  No host synchronisation.
+// from in any case.  s_eff_host as for orth_fp64.
 int orth_f32(int n, int s, const float* Y, int ldy, float* A, int lda, double* ws,
-             int* keep_dev, cudaStream_t st);
+             int* keep_dev, int* s_eff_host, cudaStream_t st);
 int project_residual_f32(int n, int s, int r, const float* A, int lda, uint64_t key, float* X,
                          int ldx, int zcol0, double* ws, cudaStream_t st, int gaussian = 0,
                          const uint64_t* keyp = nullptr);

@@ -258,6 +258,22 @@ int logdet_orth(int32_t n, int32_t s, const double* y, int32_t ldy, double* a, i
   return LOGDET_OK;
 }
 
+int logdet_orth_f32(int32_t n, int32_t s, const float* y, int32_t ldy, float* a, int32_t lda,
+                    int32_t* s_eff, void* cuda_stream) {
+  if (n < 1 || s < 1 || s > kMaxSketch || ldy < s || lda < s || !y || !a) {
+    set_error("orth_f32: bad arguments (1 <= s <= %d)", kMaxSketch);
+    return LOGDET_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBuf<double> ws(st);
+  LD_TRY(ws.alloc(orth_workspace_doubles(n, s)));
+  int se = 0;
+  LD_TRY(orth_f32(n, s, y, ldy, a, lda, ws.p, nullptr, &se, st));
+  if (s_eff) *s_eff = se;
+  LD_CUDA(cudaStreamSynchronize(st));
+  return LOGDET_OK;
+}
+
 int logdet_gauss_quadrature_log(const double* alpha, const double* beta, const int32_t* msteps,
                                 int32_t m, int32_t nprobe, double clamp_lo, double* out,
                                 uint32_t* status, void* cuda_stream) {

@@ -492,7 +492,7 @@ static int hutchpp_split_f32(int n, int s, int r, const float* Y, int lds, uint6
   LD_TRY(X.zero());
   DevBuf<double> ws(st);
   LD_TRY(ws.alloc(std::max(orth_workspace_doubles(n, s), project_workspace_doubles(n, s, r))));
-  LD_TRY(orth_f32(n, s, Y, lds, X.p, ld, ws.p, keep, st));
+  LD_TRY(orth_f32(n, s, Y, lds, X.p, ld, ws.p, keep, nullptr, st));
   LD_TRY(project_residual_f32(n, s, r, X.p, ld, key_g, X.p, ld, s, ws.p, st, gaussian, keyp_g));
   return LOGDET_OK;
 }

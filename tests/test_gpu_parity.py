@@ -104,6 +104,56 @@ def test_orth_rank_deficient_drops_column():
     assert np.max(np.abs(A[:, keep] - O.orth(Y))) < 1e-12
 
 
+# FP32 Cholesky QR (mixed-precision OSLQ).  The reference is the oracle's
+# FP64 thin QR of the same FP32 Y.  Bounds: A is stored and applied in FP32,
+# so A^T A - I is a few s eps_32 (<= 1e-5 here); A differs from the FP64
+# factor by about kappa(Y) s eps_32 (kappa = 100 here: <= 2e-3 bounds it with
+# room); the projector onto span(Y) applied to random vectors by the same.
+@pytest.mark.parametrize("n,s", [(100003, 10), (3001, 20), (257, 40), (70, 64)])
+def test_orth_f32_orthonormal_basis_of_span(n, s):
+    rng = np.random.default_rng(n + s)
+    Y = (rng.standard_normal((n, s)) @ np.diag(np.logspace(0, 2, s))).astype(np.float32)
+    ld = s + (-s) % 4
+    Yd = np.zeros((n, ld), dtype=np.float32)
+    Yd[:, :s] = Y
+    yd = cuda(Yd.ravel(), torch.float32)
+    ad = torch.full((n * ld,), 7.0, dtype=torch.float32, device="cuda")
+    s_eff = B.logdet_orth_f32(n, s, yd, ld, ad, ld)
+    A = ad.view(n, ld).cpu().numpy()[:, :s].astype(np.float64)
+    assert s_eff == s
+    assert np.max(np.abs(A.T @ A - np.eye(s))) < 1e-5
+    Q = O.orth(Y.astype(np.float64))
+    assert np.max(np.abs(A - Q)) < 2e-3
+    V = rng.standard_normal((n, 3))
+    assert np.max(np.abs(A @ (A.T @ V) - Q @ (Q.T @ V))) < 2e-3 * np.max(np.abs(V))
+    # in place (A aliases Y) gives the same bits
+    s2 = B.logdet_orth_f32(n, s, yd, ld, yd, ld)
+    assert s2 == s
+    assert torch.equal(yd.view(n, ld)[:, :s], ad.view(n, ld)[:, :s])
+
+
+def test_orth_f32_rank_deficient_and_wide():
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((500, 6))
+    Y[:, 3] = Y[:, 0] - 2 * Y[:, 1]
+    Y32 = Y.astype(np.float32)
+    ad = torch.zeros(500 * 8, dtype=torch.float32, device="cuda")
+    Yd = np.zeros((500, 8), dtype=np.float32)
+    Yd[:, :6] = Y32
+    assert B.logdet_orth_f32(500, 6, cuda(Yd.ravel(), torch.float32), 8, ad, 8) == 5
+    A = ad.view(500, 8).cpu().numpy()[:, :6].astype(np.float64)
+    assert np.all(A[:, 3] == 0.0)
+    keep = [0, 1, 2, 4, 5]
+    assert np.max(np.abs(A[:, keep].T @ A[:, keep] - np.eye(5))) < 1e-5
+    assert np.max(np.abs(A[:, keep] - O.orth(Y32.astype(np.float64)[:, keep]))) < 1e-4
+    # more columns than rows: only n of them are independent
+    W5 = rng.standard_normal((5, 8)).astype(np.float32)
+    ad = torch.zeros(5 * 8, dtype=torch.float32, device="cuda")
+    assert B.logdet_orth_f32(5, 8, cuda(W5.ravel(), torch.float32), 8, ad, 8) == 5
+    with pytest.raises(B.LogdetError):
+        B.logdet_orth_f32(5, 65, cuda(W5.ravel(), torch.float32), 65, ad, 65)
+
+
 def test_gauss_quadrature_matches_eigh_tridiagonal():
     rng = np.random.default_rng(1)
     nprobe, m = 37, 60
