@@ -241,9 +241,11 @@ int logdet_orth(int32_t n, int32_t s, const double* y_dev, int32_t ldy, double* 
  * summed in FP64, an FP64 Cholesky factor, and FP32 applies of its inverse.
  * A (FP32, n x s in a block of leading dimension lda, a_dev may alias y_dev)
  * is orthonormal to FP32 rounding and spans the FP32 Y's columns; the column
- * drop rule and *s_eff are those of logdet_orth.  Device pointers; blocks
- * until done.  Errors: EINVAL (NULL pointer, s outside [1, 64], ld < s),
- * ENOMEM, ECUDA. */
+ * drop rule and *s_eff are those of logdet_orth.  Products y_i y_j are formed
+ * in FP32, so entries need magnitudes within about [1e-18, 1e18] (A does not
+ * depend on the scale of Y: scale it first otherwise; the estimators' sketch
+ * J S has entries of order 1).  Device pointers; blocks until done.  Errors:
+ * EINVAL (NULL pointer, s outside [1, 64], ld < s), ENOMEM, ECUDA. */
 int logdet_orth_f32(int32_t n, int32_t s, const float* y_dev, int32_t ldy, float* a_dev,
                     int32_t lda, int32_t* s_eff, void* cuda_stream);
 
