@@ -114,9 +114,9 @@ const char* logdet_last_error(void);
 
 /* ---- matrix handle -----------------------------------------------------
  * logdet_create: copies a host CSR matrix to the current CUDA device,
- * validates it (Sec. 2, "Q symmetric positive definite"; structural checks
- * only) and computes its Gershgorin interval (Sec. 2.1, the spectral interval
- * used by both estimators).  vals_dtype is LOGDET_VALS_F64 or _F32.  The
+ * validates it (Sec. 2 takes Q symmetric positive definite; the checks here
+ * are structural only) and computes its Gershgorin interval (Sec. 2.1, the
+ * spectral interval used by both estimators).  vals_dtype is LOGDET_VALS_F64 or _F32.  The
  * caller may free its arrays on return.  Errors: EINVAL (n < 1, bad rowptr,
  * column out of range or unsorted or duplicated, missing diagonal, NaN),
  * ENOTSPD (Gershgorin upper bound <= 0), ENOMEM, ECUDA.
@@ -215,7 +215,7 @@ int logdet_probe_fill(uint64_t seed, int32_t stream, int32_t n, int32_t ncols, i
                       double* out_dev, int32_t ld, void* cuda_stream);
 
 /* logdet_probe_fill_gaussian: the Gaussian alternative for the probes
- * (Algorithms 2/3 allow "Rademacher or Gaussian"), entry formula as for
+ * (Algorithms 2/3 admit Gaussian entries besides +-1), entry formula as for
  * logdet_opts.gaussian_probes; layout as logdet_probe_fill. */
 int logdet_probe_fill_gaussian(uint64_t seed, int32_t stream, int32_t n, int32_t ncols,
                                int32_t col0, double* out_dev, int32_t ld, void* cuda_stream);
@@ -228,8 +228,8 @@ int logdet_spmm(logdet_handle h, const double* x_dev, double* y_dev, int32_t b, 
                 void* cuda_stream);
 
 /* logdet_orth: A = orth(Y) for a device block Y (n x s, ld) in FP64 by two
- * rounds of Cholesky QR (the "Form an orthonormal basis A via QR" step of
- * Algorithms 2 and 3).  Column i of A equals column i of the thin QR factor
+ * rounds of Cholesky QR (the QR step of Algorithms 2 and 3: an orthonormal
+ * basis of span(Y)).  Column i of A equals column i of the thin QR factor
  * with positive diag(R).  A column whose |R_ii| <= 1e-6 max_j |y_j| is set to
  * zero and *s_eff counts the kept ones.  a_dev may alias y_dev. */
 int logdet_orth(int32_t n, int32_t s, const double* y_dev, int32_t ldy, double* a_dev,

@@ -1,7 +1,7 @@
 """Counter-based Rademacher probes: the oracle's own implementation.
 
 The paper draws the sketch S and the residual probes from i.i.d. +-1 entries
-(Algorithm 2 and Algorithm 3, "Sample sketching matrix S"; Sec. 2.2 and
+(the sketch-sampling step of Algorithms 2 and 3; Sec. 2.2 and
 Sec. 3.2) but does not name a generator.  Both sides of the parity check
 implement this one from the published SplitMix64 definition (Steele, Lea and
 Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014):

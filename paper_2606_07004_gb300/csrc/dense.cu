@@ -1,4 +1,5 @@
-// Dense and small-matrix kernels (see dense.cuh).  All arithmetic is FP64.
+// Dense and small-matrix kernels (see dense.cuh).  Arithmetic is FP64, except
+// the FP32 instances of the Hutch++ split kernels (mixed-precision OSLQ).
 #include "dense.cuh"
 #include "krylov.cuh"
 #include "profile.cuh"
@@ -10,8 +11,8 @@
 namespace ld {
 
 // ===========================================================================
-// Hutch++ QR: A = orth(Y) by two rounds of Cholesky QR (Algorithms 2 and 3,
-// "form an orthonormal basis A for the span of Y via QR").  For full-rank Y
+// Hutch++ QR: A = orth(Y) by two rounds of Cholesky QR (the QR step of
+// Algorithms 2 and 3: an orthonormal basis of span(Y)).  For full-rank Y
 // this gives the thin QR factor with positive diag(R), the same columns as a
 // Householder QR with that sign convention.
 // ===========================================================================

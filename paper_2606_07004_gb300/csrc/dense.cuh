@@ -1,6 +1,7 @@
-// Dense and small-matrix kernels of the estimators (all FP64 arithmetic):
-// Hutch++ QR and projection, batched tridiagonal Gauss rules, batched
-// Hessenberg logarithms, OSA-IOP sketch assembly and quadratic forms.
+// Dense and small-matrix kernels of the estimators: Hutch++ QR and
+// projection (FP64, or FP32 with compensated sums for FP32 blocks), batched
+// tridiagonal Gauss rules, batched Hessenberg logarithms, OSA-IOP sketch
+// assembly and quadratic forms (FP64).
 #pragma once
 
 #include "common.cuh"
