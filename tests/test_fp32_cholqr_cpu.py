@@ -6,9 +6,9 @@ Cholesky factor is FP64, and whose applies A = Y R^-1 run in FP32 with R^-1
 rounded to FP32, leave A orthonormal to FP32 rounding for kappa(Y) up to 1e6
 (the largest the column-drop rule |R_jj| > 1e-6 max |y| admits; measured
 max |A^T A - I| ~1e-7 after two rounds, 4e-3 after one at kappa = 1e6), and
-A spans the FP32 Y to FP32 rounding (relative residual <= 5e-7 measured).  This is an emulation of the
-arithmetic, not of the kernels; the kernels are checked against the oracle on
-the GPU."""
+A spans the FP32 Y to FP32 rounding (relative residual <= 5e-7 measured).
+This is an emulation of the arithmetic, not of the kernels; the kernels are
+checked against the oracle on the GPU."""
 import numpy as np
 import pytest
 
