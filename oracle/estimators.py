@@ -38,7 +38,11 @@ R13 Probes come from the SplitMix64 spec in ``rademacher.py``.
 R14 orth(Y) is the thin QR factor with diag(R) > 0; a column whose |R_ii| is
     at most 1e-6 * max_j ||y_j|| is dropped (rank-deficient sketch).
 R15 A residual probe with ||z_j|| = 0 contributes 0.
-R16 log(H_m) is the principal matrix logarithm (scipy.linalg.logm).
+R16 log(H_m) is the principal matrix logarithm (scipy.linalg.logm); an H_m
+    whose logarithm is not real (an eigenvalue on the negative real axis) sets
+    FLAG_COMPLEX_LOG and its real part is used.
+R17 A Ritz value theta <= 0 (an indefinite T_m) sets FLAG_NONPOSITIVE_RITZ and
+    is clamped to lambda_lo / alpha, the lower spectral bound of J (Sec. 2.1).
 """
 from __future__ import annotations
 
@@ -95,8 +99,9 @@ def gershgorin_interval(Q: sp.csr_matrix) -> tuple[float, float]:
 
 
 def _gershgorin_fast(Q: sp.csr_matrix) -> tuple[float, float]:
-    """Vectorised form of the same sums, for large n (identical for <= 8 off-diagonals
-    per row, where NumPy's reduction is sequential)."""
+    """Vectorised form of the same sums, for large n.  NumPy's segment reduction
+    adds a row's entries in its own order, so the bounds can differ from the
+    row loop's in the last bits."""
     Q = sp.csr_matrix(Q)
     n = Q.shape[0]
     rows = np.repeat(np.arange(n), np.diff(Q.indptr))
@@ -245,15 +250,18 @@ def principal_logm_e1(Hm: np.ndarray) -> tuple[np.ndarray, bool]:
 
 
 def iop_log_action(Qt, v, m_max: int, k: int, shift: float, tol: float = DEFAULT_TOL,
-                   dot="numpy") -> np.ndarray:
+                   dot="numpy", report: list | None = None) -> np.ndarray:
     """y = ||v|| V_m log(H_m) e_1 + shift * v  (Algorithm 1's return line with the
     constant term generalised: shift = log(gamma) gives log(Q) v, shift =
-    log(gamma/alpha) gives L v of Sec. 2.2)."""
+    log(gamma/alpha) gives L v of Sec. 2.2).  If ``report`` is a list, False is
+    appended to it when log(H_m) is not real (R16)."""
     v = np.asarray(v, dtype=np.float64)
     if not np.any(v):
         return np.zeros_like(v)
     run = arnoldi_iop(Qt, v, m_max, k, tol, dot)
-    c, _ = principal_logm_e1(run.H)
+    c, ok = principal_logm_e1(run.H)
+    if report is not None and not ok:
+        report.append(False)
     return run.v_norm * (run.V @ c) + shift * v
 
 
@@ -335,6 +343,7 @@ def oslq(Q, num_probes: int, m: int, seed: int = 0, *, S=None, G=None, lam=None,
     n = Q.shape[0]
     lam_lo, lam_hi = spectral_interval(Q, lam)
     alpha = lam_hi                                   # R1
+    clamp = lam_lo / alpha                           # R17
     J = sp.csr_matrix((Q.data / alpha, Q.indices, Q.indptr), shape=Q.shape)
     s, r = _split(num_probes) if hutchpp else (0, num_probes)
     if S is not None:
@@ -351,7 +360,7 @@ def oslq(Q, num_probes: int, m: int, seed: int = 0, *, S=None, G=None, lam=None,
     tr_sub = 0.0
     for i in range(A.shape[1]):                      # deterministic subspace part
         a_, b_ = lanczos(J, A[:, i], m, tol, reorth, dot)
-        qd = gauss_quadrature_log(a_, b_)
+        qd = gauss_quadrature_log(a_, b_, clamp)
         flags |= FLAG_NONPOSITIVE_RITZ if qd.nonpositive else 0
         per.append(qd.value)
         tr_sub += qd.value
@@ -363,7 +372,7 @@ def oslq(Q, num_probes: int, m: int, seed: int = 0, *, S=None, G=None, lam=None,
             per.append(0.0)
             continue
         a_, b_ = lanczos(J, Z[:, j], m, tol, reorth, dot)
-        qd = gauss_quadrature_log(a_, b_)
+        qd = gauss_quadrature_log(a_, b_, clamp)
         flags |= FLAG_NONPOSITIVE_RITZ if qd.nonpositive else 0
         per.append(qd.value)
         tr_res += zn2[j] * qd.value
@@ -396,8 +405,10 @@ def osaiop(Q, num_probes: int, m: int, k: int = 2, seed: int = 0, *, S=None, G=N
         r = G.shape[1]
     S, G = _probes(n, s, r, seed, S, G, gaussian)
 
+    complex_logs: list = []
+
     def L_action(v):
-        return iop_log_action(Qt, v, m, k, shift, tol, dot)
+        return iop_log_action(Qt, v, m, k, shift, tol, dot, complex_logs)
 
     flags = 0
     Y = (np.stack([L_action(S[:, i]) for i in range(s)], axis=1) if s
@@ -422,6 +433,8 @@ def osaiop(Q, num_probes: int, m: int, k: int = 2, seed: int = 0, *, S=None, G=N
         per.append(qf / zn2[j])
         tr_res += qf
     tr_res /= r
+    if complex_logs:
+        flags |= FLAG_COMPLEX_LOG                    # R16
     logdet = n * math.log(alpha) + tr_sub + tr_res
     return Estimate(logdet, tr_sub, tr_res, math.log(alpha), math.log(gamma), s, r,
                     A.shape[1], np.array(per), zn2, flags)

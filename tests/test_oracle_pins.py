@@ -443,3 +443,149 @@ def test_paper_tolerance_mode_stops_probes_early():
     exact = float(np.sum(np.log(d)))
     assert O.osaiop(Q, 9, 20, k=2, S=S, G=G, tol=1e-6).logdet == pytest.approx(exact, rel=1e-10)
     assert O.oslq(Q, 9, 20, S=S, G=G, tol=1e-6).logdet == pytest.approx(exact, rel=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Spectral interval above n = 20000, where spectral_interval switches from the
+# row loop to the vectorised sums (Sec. 2.1, Gershgorin; clamp R3).  Every
+# full-size oracle run takes that branch.
+# ---------------------------------------------------------------------------
+
+LARGE_CLOSED_FORMS = [
+    # (matrix, its Gershgorin interval from the stencil's row sums)
+    ("lap2d_151x149", lambda: W.laplacian_2d(151, 149, shift=0.3), 0.3, 8.3),
+    ("lap3d_31x29x27", lambda: W.laplacian_3d(31, 29, 27, shift=0.02), 0.02, 12.02),
+    # (k2 + 4)^2 + 4 on the diagonal; off-diagonal |.| sums to 8 (k2 + 4) + 4 + 8
+    ("matern_150", lambda: W.matern_2d(150, 0.05), -23.9975, 64.8025),
+]
+
+
+@pytest.mark.parametrize("name,make,lo,hi", LARGE_CLOSED_FORMS, ids=[c[0] for c in LARGE_CLOSED_FORMS])
+def test_gershgorin_fast_closed_forms(name, make, lo, hi):
+    A = make()
+    assert A.n > 20000
+    glo, ghi = E._gershgorin_fast(A.to_scipy())
+    assert glo == pytest.approx(lo, abs=1e-12) and ghi == pytest.approx(hi, abs=1e-12)
+    # the branch spectral_interval takes at this size, with the clamp (R3)
+    slo, shi = O.spectral_interval(A.to_scipy())
+    assert shi == pytest.approx(hi, abs=1e-12)
+    assert slo == pytest.approx(lo if lo > 0 else 1e-6 * hi, rel=1e-12)
+
+
+def test_gershgorin_fast_full_size_workloads():
+    # The 128^3 Laplacian + 0.01 I and the 1024^2 Matern operator at the
+    # sizes the benchmark's oracle baseline runs.
+    lo, hi = E._gershgorin_fast(W.laplacian_3d(128, shift=0.01).to_scipy())
+    assert lo == pytest.approx(0.01, abs=1e-13) and hi == pytest.approx(12.01, abs=1e-13)
+    lo, hi = E._gershgorin_fast(W.matern_2d(1024, 0.05).to_scipy())
+    assert lo == pytest.approx(-23.9975, abs=1e-12) and hi == pytest.approx(64.8025, abs=1e-12)
+
+
+def test_gershgorin_fast_power_law_graph():
+    # L + s I of a graph with unit weights: row i has diagonal deg_i + s and
+    # off-diagonal sum deg_i, so the interval is [s, 2 max deg + s].
+    G = W.powerlaw_graph_laplacian(30000, seed=2).with_diagonal_shift(0.07)
+    deg = np.diff(G.rowptr) - 1
+    lo, hi = E._gershgorin_fast(G.to_scipy())
+    assert lo == pytest.approx(0.07, abs=1e-12)
+    assert hi == pytest.approx(2 * deg.max() + 0.07, abs=1e-9)
+
+
+def test_gershgorin_fast_brute_force_random_signs():
+    # Random symmetric matrix with mixed signs, rows of 1 to ~60 entries, an
+    # empty row and a row without its diagonal, against row sums of |Q| formed
+    # by a sparse product (an independent evaluation of the same definition).
+    rng = np.random.default_rng(17)
+    n = 25000
+    nnz = 400000
+    r = rng.integers(0, n, nnz)
+    c = np.minimum(r + rng.geometric(0.02, nnz), n - 1)
+    v = rng.standard_normal(nnz)
+    U = sp.coo_matrix((v, (r, c)), shape=(n, n)).tocsr()
+    D = sp.diags(rng.standard_normal(n) * 30.0)
+    Q = (U + U.T + D).tocsr()
+    Q = Q.tolil()
+    Q[123, :] = 0.0                      # empty row (and column)
+    Q[:, 123] = 0.0
+    Q[4567, 4567] = 0.0                  # row without a stored diagonal
+    Q = Q.tocsr()
+    Q.eliminate_zeros()
+    Q.sort_indices()
+    assert Q.indptr[124] == Q.indptr[123]
+    diag = Q.diagonal()
+    R_ = np.asarray(abs(Q) @ np.ones(n)).ravel() - np.abs(diag)
+    want_lo, want_hi = float(np.min(diag - R_)), float(np.max(diag + R_))
+    lo, hi = E._gershgorin_fast(Q)
+    assert lo == pytest.approx(want_lo, rel=1e-13) and hi == pytest.approx(want_hi, rel=1e-13)
+
+
+def test_gershgorin_fast_equals_row_loop():
+    # The vectorised sums and the row loop are the same sums in different
+    # orders: equal to a few units in the last place.
+    for A in (W.laplacian_2d(151, 149, shift=0.3), W.laplacian_3d(31, 29, 27, shift=0.02),
+              W.matern_2d(150, 0.05)):
+        Qs = A.to_scipy()
+        Qs.data = Qs.data * (1.0 + 0.01 * np.sin(np.arange(Qs.nnz)))   # distinct values
+        assert E._gershgorin_fast(Qs) == pytest.approx(O.gershgorin_interval(Qs), rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Degenerate spectra: a non-positive Ritz value (Sec. 3.1 Gauss rule, R17) and
+# a Hessenberg matrix whose principal logarithm is not real (Algorithm 1, R16)
+# ---------------------------------------------------------------------------
+
+def test_gauss_rule_clamps_nonpositive_ritz_value():
+    # T = [[1/2, 1], [1, 1/2]] has eigenvalues -1/2 and 3/2 with eigenvectors
+    # (1, -1)/sqrt 2 and (1, 1)/sqrt 2, so both weights are 1/2.
+    qd = O.gauss_quadrature_log([0.5, 0.5], [1.0], clamp=1e-3)
+    assert qd.nonpositive
+    assert np.allclose(np.sort(qd.theta), [1e-3, 1.5], rtol=1e-14)
+    assert np.allclose(qd.tau2, [0.5, 0.5], rtol=1e-14)
+    assert qd.value == pytest.approx(0.5 * math.log(1e-3) + 0.5 * math.log(1.5), rel=1e-14)
+    ok = O.gauss_quadrature_log([2.0, 2.0], [1.0])          # eigenvalues 1 and 3
+    assert not ok.nonpositive
+    assert ok.value == pytest.approx(0.5 * math.log(3.0), rel=1e-14)
+
+
+def test_oslq_indefinite_diagonal_clamps_to_lower_bound():
+    # Q = diag(-1 (a times), 2 (n - a times)): Gershgorin [-1, 2], clamped
+    # lambda_lo = 2e-6 (R3), alpha = 2, J has eigenvalues -1/2 and 1.  Two
+    # Lanczos steps from a +-1 probe g give theta = {-1/2, 1} with weights
+    # a/n and (n-a)/n; -1/2 is clamped to lambda_lo/alpha = 1e-6 (R17), so
+    # K(g) = (a/n) log(1e-6) and, without the Hutch++ split,
+    # log det = n log 2 + (1/r) sum_j |g_j|^2 K(g_j) = n log 2 + a log(1e-6).
+    n, a = 30, 7
+    Q = W.diagonal_matrix(np.r_[np.full(a, -1.0), np.full(n - a, 2.0)]).to_scipy()
+    est = O.oslq(Q, 5, 2, seed=3, hutchpp=False)
+    assert est.flags & E.FLAG_NONPOSITIVE_RITZ
+    assert est.logdet == pytest.approx(n * math.log(2.0) + a * math.log(1e-6), rel=1e-12)
+    assert np.allclose(est.per_probe, (a / n) * math.log(1e-6), rtol=1e-12)
+    spd = O.oslq(W.diagonal_matrix(np.r_[np.full(a, 1.0), np.full(n - a, 2.0)]).to_scipy(),
+                 5, 2, seed=3, hutchpp=False)
+    assert not spd.flags & E.FLAG_NONPOSITIVE_RITZ
+
+
+def test_principal_logm_flags_negative_eigenvalue():
+    # An eigenvalue on the negative real axis has no real logarithm:
+    # log(-1) = i pi.  Upper triangular H = [[-1, 1/2], [0, 2]].
+    c, ok = E.principal_logm_e1(np.array([[-1.0, 0.5], [0.0, 2.0]]))
+    assert not ok
+    assert c == pytest.approx([0.0, 0.0], abs=1e-12)       # real part of (i pi, 0)
+    c, ok = E.principal_logm_e1(np.array([[1.0, 0.5], [0.0, 2.0]]))
+    assert ok
+    # log of [[1, b], [0, 2]] has first column (log 1, 0)
+    assert c == pytest.approx([0.0, 0.0], abs=1e-14)
+    c, ok = E.principal_logm_e1(np.array([[2.0, 0.0], [0.5, 1.0]]))
+    assert ok
+    # lower triangular [[l1, 0], [b, l2]]: (log A)_21 = b (log l1 - log l2)/(l1 - l2)
+    assert c == pytest.approx([math.log(2.0), 0.5 * math.log(2.0)], rel=1e-13)
+
+
+def test_osaiop_indefinite_sets_complex_log_flag():
+    # Q = diag(-1, 2): gamma = sqrt(2e-6 * 2), the Hessenberg matrix of every
+    # probe has the eigenvalue -1/gamma, so its principal log is not real.
+    n, a = 24, 5
+    Q = W.diagonal_matrix(np.r_[np.full(a, -1.0), np.full(n - a, 2.0)]).to_scipy()
+    assert O.osaiop(Q, 6, 2, k=2, seed=1).flags & E.FLAG_COMPLEX_LOG
+    spd = W.diagonal_matrix(np.r_[np.full(a, 1.0), np.full(n - a, 2.0)]).to_scipy()
+    assert not O.osaiop(spd, 6, 2, k=2, seed=1).flags & E.FLAG_COMPLEX_LOG
