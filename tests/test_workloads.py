@@ -121,3 +121,30 @@ def test_grf_client_table_matches_generator():
     grf = pytest.importorskip("paper_2606_07004_gb300.grf")  # needs the built library
     for theta, nug in ((3.0, 0.0), (20.0, 0.1), (7.5, 0.3)):
         assert np.array_equal(grf.wendland_table(theta, nug), W.wendland_table(theta, nug))
+
+
+def _csr_equal(a, b):
+    return (np.array_equal(a.rowptr, b.rowptr) and np.array_equal(a.colind, b.colind)
+            and np.array_equal(a.vals, b.vals) and a.vals.dtype == b.vals.dtype)
+
+
+@pytest.mark.parametrize("nx,ny,shift", [(6, 2, 0.1), (7, 9, 0.0), (64, 64, 0.1), (40, 37, 0.05),
+                                         (151, 149, 0.3)])
+def test_laplacian_2d_direct_equals_kronecker_form(nx, ny, shift):
+    # The direct stencil construction gives the same CSR (indices and doubles)
+    # as kron(I, T) + kron(T, I) + shift I, T = tridiag(-1, 2, -1).
+    import scipy.sparse as sp
+    from workloads.matrices import _from_scipy, _lap1d
+    L = sp.kron(sp.eye(ny), _lap1d(nx)) + sp.kron(_lap1d(ny), sp.eye(nx)) + shift * sp.eye(nx * ny)
+    assert _csr_equal(W.laplacian_2d(nx, ny, shift), _from_scipy(L))
+
+
+@pytest.mark.parametrize("N,k2", [(5, 0.05), (6, 0.05), (13, 0.3), (64, 0.05)])
+def test_matern_direct_equals_sparse_product(N, k2):
+    # Q = M M, M = k2 I + L_2D, formed by a sparse matrix product.
+    import scipy.sparse as sp
+    from workloads.matrices import _from_scipy, _lap1d
+    M = sp.csr_matrix(sp.kron(sp.eye(N), _lap1d(N)) + sp.kron(_lap1d(N), sp.eye(N)) + k2 * sp.eye(N * N))
+    assert _csr_equal(W.matern_2d(N, k2), _from_scipy(M @ M))
+    a = W.matern_2d(N, k2, dtype=np.float32)
+    assert a.vals.dtype == np.float32 and np.array_equal(a.vals, _from_scipy(M @ M).vals.astype(np.float32))

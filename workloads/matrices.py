@@ -152,12 +152,42 @@ def _lap1d(N: int) -> sp.csr_matrix:
     return sp.diags([-np.ones(N - 1), 2 * np.ones(N), -np.ones(N - 1)], [-1, 0, 1], format="csr")
 
 
+def _grid_stencil_csr(nx: int, ny: int, taps, dtype) -> CSR:
+    """CSR of a 2D stencil on an nx x ny grid (row y nx + x), built directly.
+
+    taps: (dx, dy, value) in ascending column order (dy nx + dx); value is a
+    scalar or a per-row array.  A tap is stored for a row when its neighbour
+    lies in the grid (no wrapping across grid edges)."""
+    n = nx * ny
+    T = len(taps)
+    x = np.tile(np.arange(nx, dtype=np.int32), ny)
+    y = np.repeat(np.arange(ny, dtype=np.int32), nx)
+    # n x T tables in row-major order: a row's stored taps come out in tap
+    # (= ascending column) order when the valid ones are selected.
+    valid = np.empty((n, T), dtype=bool)
+    cols = np.empty((n, T), dtype=np.int32)
+    vals = np.empty((n, T), dtype=np.float64)
+    rows = np.arange(n, dtype=np.int32)
+    for t, (dx, dy, val) in enumerate(taps):
+        valid[:, t] = (x + dx >= 0) & (x + dx < nx) & (y + dy >= 0) & (y + dy < ny)
+        cols[:, t] = rows + (dy * nx + dx)
+        vals[:, t] = val
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(valid.sum(axis=1), out=rowptr[1:])
+    return CSR(n, rowptr.astype(np.int32), cols[valid], vals[valid].astype(dtype, copy=False))
+
+
 def laplacian_2d(nx: int, ny: int | None = None, shift: float = 0.0, dtype=np.float64) -> CSR:
-    """5-point Dirichlet Laplacian on an nx x ny grid, plus shift*I."""
+    """5-point Dirichlet Laplacian on an nx x ny grid, plus shift*I (diagonal
+    4 + shift, neighbours -1; built directly, the same doubles as
+    kron(I, T) + kron(T, I) + shift I with T = tridiag(-1, 2, -1))."""
     ny = nx if ny is None else ny
-    L = sp.kron(sp.eye(ny), _lap1d(nx)) + sp.kron(_lap1d(ny), sp.eye(nx))
-    L = L + shift * sp.eye(nx * ny)
-    return _from_scipy(L, dtype)
+    if nx < 6 or ny < 2:   # small grids: the Kronecker form (it also stores some zeros)
+        L = sp.kron(sp.eye(ny), _lap1d(nx)) + sp.kron(_lap1d(ny), sp.eye(nx))
+        return _from_scipy(L + shift * sp.eye(nx * ny), dtype)
+    d = 4.0 + shift
+    taps = [(0, -1, -1.0), (-1, 0, -1.0), (0, 0, d), (1, 0, -1.0), (0, 1, -1.0)]
+    return _grid_stencil_csr(nx, ny, taps, dtype)
 
 
 def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None,
@@ -199,13 +229,31 @@ def laplacian_3d(nx: int, ny: int | None = None, nz: int | None = None,
 def matern_2d(N: int, kappa2: float, dtype=np.float64) -> CSR:
     """SPDE-style Matern precision Q = M @ M with M = kappa2*I + L_2D (N x N grid).
 
-    In the interior this is the 13-point stencil.  The product is formed in
-    FP64 and cast at the end.
+    In the interior this is the 13-point stencil.  Entry (i, j) of M M sums
+    M_ik M_kj over the paths i -> k -> j of the grid: c^2 plus one per
+    in-grid neighbour on the diagonal (c = 4 + kappa2, the neighbours added in
+    column order around c^2, as a sparse product forms it), -2c for a
+    neighbour, 1 for a point two steps away in a line and 2 for a diagonal
+    neighbour.  Built directly in FP64 and cast at the end.
     """
-    M = sp.kron(sp.eye(N), _lap1d(N)) + sp.kron(_lap1d(N), sp.eye(N)) + kappa2 * sp.eye(N * N)
-    M = sp.csr_matrix(M)
-    Q = M @ M
-    return _from_scipy(Q, dtype)
+    if N < 5:
+        M = sp.kron(sp.eye(N), _lap1d(N)) + sp.kron(_lap1d(N), sp.eye(N)) + kappa2 * sp.eye(N * N)
+        M = sp.csr_matrix(M)
+        return _from_scipy(M @ M, dtype)
+    c = (2.0 + 2.0) + kappa2
+    idx = np.arange(N * N, dtype=np.int64)
+    x, y = idx % N, idx // N
+    diag = np.zeros(N * N)
+    diag += (y > 0)
+    diag += (x > 0)
+    diag += c * c
+    diag += (x < N - 1)
+    diag += (y < N - 1)
+    e = -c + -c
+    taps = [(0, -2, 1.0), (-1, -1, 2.0), (0, -1, e), (1, -1, 2.0),
+            (-2, 0, 1.0), (-1, 0, e), (0, 0, diag), (1, 0, e), (2, 0, 1.0),
+            (-1, 1, 2.0), (0, 1, e), (1, 1, 2.0), (0, 2, 1.0)]
+    return _grid_stencil_csr(N, N, taps, dtype)
 
 
 def grid_stencil_3d(nx: int, ny: int, nz: int, taps, diag: float = 30.0,
