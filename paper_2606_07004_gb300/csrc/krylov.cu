@@ -304,7 +304,25 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
 
 // ---------------------------------------------------------------------------
 // pass 2: out = ycoef*y - sum_i coef_i basis_i;  |out|^2 [; extra . out]
+//
+// EX: the batch has jobs with the extra dot (OSA-IOP's u_1 . u_{j+1});
+// without it the instance carries no code for it.  For FP64 blocks a column
+// scale ycoef != 1 (a power of two once sigma drifted, 0 for an inactive
+// probe) is applied to y in place before the row loop (y is this step's
+// pass-1 output and nothing reads it after this pass), so the loop issues
+// only the FMAs the update needs; the product is the one the loop would
+// form, so results do not change.
 // ---------------------------------------------------------------------------
+// load_vec through L2 only (ld.global.cg), for FP64 data this kernel may
+// have written earlier: the non-coherent path of load_vec must not read it.
+template <typename T>
+__device__ __forceinline__ void load_vec_cg(const T* p, typename Compute<T>::type (&v)[Vec16<T>::N]) {
+  static_assert(std::is_same<T, double>::value, "coherent vector loads are used for FP64 blocks");
+  const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+  v[0] = t.x;
+  v[1] = t.y;
+}
+
 // FP64 update instances held at two CTAs per SM: the full window (see
 // fp64_wide_min_ctas) and the software-pipelined NB <= 2 loop below (its
 // prefetched row fits 64 registers).
@@ -313,7 +331,7 @@ constexpr int update_min_ctas() {
   return (std::is_same<T, double>::value && (NB >= kMaxWin || NB <= 2)) ? 2 : 0;
 }
 
-template <typename T, int NB>
+template <typename T, int NB, bool EX>
 __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
     k_update(const __grid_constant__ UpdBatch<T> B) {
   constexpr int V = Vec16<T>::N;
@@ -335,7 +353,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
     const int row1 = min(row0 + J.tile_rows, J.n);
     const int col0 = J.col_off + g * V;
     const int nb = J.nbasis;
-    const bool has_extra = J.extra != nullptr;
+    const bool has_extra = EX && J.extra != nullptr;
 
     Acc nrm[V], ex[V];
 #pragma unroll
@@ -356,6 +374,28 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
 #pragma unroll
         for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? CT(J.coef[i * J.ld + col0 + v]) : CT(0);
 
+      // FP64: scale y in place where ycoef != 1 (rows and chunk of this
+      // thread only), then read y through L2 so the loop sees those stores.
+      constexpr bool kPre = std::is_same<T, double>::value;
+      if constexpr (kPre) {
+        if (!unit) {
+          T* yw = const_cast<T*>(J.y);
+          for (int row = row0 + r; row < row1; row += R) {
+            const size_t off = (size_t)row * J.ld + col0;
+            CT o[V];
+            load_vec_cg<T>(yw + off, o);
+#pragma unroll
+            for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
+            store_vec<T>(yw + off, o);
+          }
+        }
+      }
+      auto load_y = [&](size_t off, CT (&o)[V]) {
+        if constexpr (kPre) load_vec_cg<T>(J.y + off, o);
+        else load_vec<T>(J.y + off, o);
+      };
+      const bool scale_in_loop = !kPre && !unit;
+
       // kU rows per thread at a time (rows row, row + R): every load of
       // both rows is issued before their arithmetic, doubling the bytes in
       // flight of the HBM-bound FP32 pass; each row's operations, and the
@@ -375,7 +415,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
         CT o[kU][V], ub[kU][NB > 0 ? NB : 1][V], ue[kU][V];
 #pragma unroll
         for (int q = 0; q < kU; ++q) {
-          load_vec<T>(J.y + off[q], o[q]);
+          load_y(off[q], o[q]);
 #pragma unroll
           for (int i = 0; i < NB; ++i)
             if (i < nb) load_vec<T>(J.basis[i] + off[q], ub[q][i]);
@@ -384,7 +424,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
 #pragma unroll
         for (int q = 0; q < kU; ++q) {
           if (!on[q]) continue;
-          if (!unit) {
+          if (scale_in_loop) {
 #pragma unroll
             for (int v = 0; v < V; ++v) o[q][v] = o[q][v] * yc[v];
           }
@@ -413,7 +453,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
       int row = row0 + r;
       if (row < row1) {
         const size_t off = (size_t)row * J.ld + col0;
-        load_vec<T>(J.y + off, py);
+        load_y(off, py);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
           if (i < nb) load_vec<T>(J.basis[i] + off, pu[i]);
@@ -431,13 +471,13 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
         }
         if (row + R < row1) {
           const size_t noff = off + (size_t)R * J.ld;
-          load_vec<T>(J.y + noff, py);
+          load_y(noff, py);
 #pragma unroll
           for (int i = 0; i < NB; ++i)
             if (i < nb) load_vec<T>(J.basis[i] + noff, pu[i]);
           if (has_extra) load_vec<T>(J.extra + noff, pe);
         }
-        if (!unit) {
+        if (scale_in_loop) {
 #pragma unroll
           for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
         }
@@ -460,8 +500,8 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
       for (int row = row0 + r; row < row1; row += R) {
         const size_t off = (size_t)row * J.ld + col0;
         CT o[V];
-        load_vec<T>(J.y + off, o);
-        if (!unit) {
+        load_y(off, o);
+        if (scale_in_loop) {
 #pragma unroll
           for (int v = 0; v < V; ++v) o[v] = o[v] * yc[v];
         }
@@ -732,7 +772,11 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
 template <typename T>
 int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
   int nb = 0;
-  for (int j = 0; j < b.njobs; ++j) nb = std::max(nb, b.jobs[j].nbasis);
+  bool ex = false;
+  for (int j = 0; j < b.njobs; ++j) {
+    nb = std::max(nb, b.jobs[j].nbasis);
+    ex = ex || b.jobs[j].extra != nullptr;
+  }
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
   double flops = 0.0, bytes = 0.0;
@@ -746,7 +790,7 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
   ProfScope prof(KC_UPDATE, s, flops, bytes);
 #define LD_UPD_CASE(NB)                                                       \
   {                                                                           \
-    auto kern = k_update<T, NB>;                                              \
+    auto kern = ex ? k_update<T, NB, true> : k_update<T, NB, false>;          \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
     kern<<<grid, threads, smem, s>>>(b);                                      \
     break;                                                                    \

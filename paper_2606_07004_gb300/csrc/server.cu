@@ -107,7 +107,10 @@ void logdet_server::complete(const std::shared_ptr<Request>& r, int state_, int 
 // Kernel variant of a job (the template width it launches with).
 static int width_class(int k) { return k <= 0 ? 0 : k == 1 ? 1 : k == 2 ? 2 : k <= 4 ? 4 : 9; }
 template <typename T> static int job_class(const SpmmJob<T>& j) { return width_class(j.ndots); }
-template <typename T> static int job_class(const UpdJob<T>& j) { return width_class(j.nbasis); }
+// Update jobs with the extra dot (OSA-IOP) run in their own instance.
+template <typename T> static int job_class(const UpdJob<T>& j) {
+  return width_class(j.nbasis) + (j.extra ? 16 : 0);
+}
 
 int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   NvtxRange nv("logdet server tick");
@@ -124,10 +127,10 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   // 2. one batched Krylov step over every request in a Krylov phase, grouped
   //    by element type, CTA size and kernel variant (dots / basis vectors
   //    class): a job never runs in a wider variant than its own, which would
-  //    cost registers and occupancy.  Group key: threads * 16 + class.
+  //    cost registers and occupancy.  Group key: threads * 32 + class.
   auto put = [&](auto& groups, auto& tmp, int th) {
     if (tmp.empty()) return;
-    auto& dst = groups[th * 16 + job_class(tmp[0])];
+    auto& dst = groups[th * 32 + job_class(tmp[0])];
     dst.insert(dst.end(), tmp.begin(), tmp.end());
   };
   std::map<int, std::vector<SpmmJob<double>>> sd;
@@ -165,9 +168,9 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
     stepping.push_back(sv);
   }
   if (stepping.empty()) return 0;
-  for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first / 16, st));
-  for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first / 16, st));
-  for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first / 16, st));
+  for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first / 32, st));
+  for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first / 32, st));
+  for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first / 32, st));
   LD_TRY(launch_scalar_jobs(coef, wc, SK_COEF, st));
   for (ISolve* sv : stepping) {
     const int th = sv->krylov_threads();
@@ -186,9 +189,9 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
       put(ub, tmp, th);
     }
   }
-  for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first / 16, st));
-  for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first / 16, st));
-  for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first / 16, st));
+  for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first / 32, st));
+  for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first / 32, st));
+  for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first / 32, st));
   if (!norm.empty()) LD_TRY(launch_scalar_jobs(norm, wn, SK_NORM, st));
   for (ISolve* sv : stepping) sv->step_issued();
   n_batched_steps += (int64_t)stepping.size();
