@@ -104,6 +104,17 @@ typedef struct {
   int32_t gaussian_probes; /* 1 = N(0,1) probes by Box-Muller from the same counters:
                           u1 = ((z>>11)+1) 2^-53, u2 = (mix(z)>>11) 2^-53,
                           g = sqrt(-2 log u1) cos(2 pi u2); 0 = Rademacher */
+  int32_t block_width; /* probe columns per Krylov pass: each block of probes
+                          (the s + r probes, and OSA-IOP's s sketch columns; both
+                          rounded up to a multiple of 2 columns for FP64, 4 for the
+                          mixed precisions) runs as slices of min(block_width, its
+                          columns) columns, one job per slice, with the default CTA
+                          size and tile depth.  0 = the default full-width block, or
+                          the autotuner's choice when autotune = 1.  A width that is
+                          not a multiple of 2 (FP64) / 4 (mixed), or that does not
+                          divide a block's rounded column count, is EINVAL.  Ignored
+                          for gridded operators.  Changes results at rounding level
+                          only (the order of the fixed-order partial sums). */
 } logdet_opts;
 
 /* Fill an opts struct with the defaults. */
@@ -182,8 +193,12 @@ int logdet_grid_structure_csr(int32_t n, const int32_t* rowptr, const int32_t* c
  * Sec. 3.1.  log det = n log(alpha) + tr_sub + (1/r) sum_j |z_j|^2 K(z_j).
  * iop_window must be 0 or 2 (three-term Lanczos).  Probes are the
  * SplitMix64 Rademacher entries of (seed, stream 0 = S, 1 = G).
- * Blocks until the result is on the host.  Errors: EINVAL (num_probes < 3,
- * krylov_steps < 1 or > n, bad window), ENOTSPD, ENOMEM, ECUDA.
+ * Blocks until the result is on the host.  Errors: EINVAL (num_probes < 3;
+ * s = floor(num_probes/3) or r = num_probes - 2s above 64, the widest sketch
+ * the Hutch++ QR kernels take; krylov_steps < 1, > n or > 256, the largest
+ * tridiagonal the small-solve kernels take; bad window; a block_width that
+ * does not fit the blocks; negative or non-finite shift), ENOTSPD (spectral
+ * bounds not positive), ENOMEM, ECUDA.
  */
 int logdet_oslq(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
                 int32_t iop_window, uint64_t seed, const logdet_opts* opts,
@@ -197,7 +212,8 @@ int logdet_oslq(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
  * krylov_steps is full Arnoldi), log(H_m) e_1 of the small Hessenberg
  * matrix.  Y = L S, A = orth(Y), tr_sub = sum_i a_i^T L a_i,
  * tr_res = (1/r) sum_j z_j^T L z_j, log det = n log(alpha) + tr_sub + tr_res.
- * Errors as logdet_oslq; EINVAL also for iop_window < 1.
+ * Errors as logdet_oslq (the same limits on s, r and krylov_steps); EINVAL
+ * also for iop_window outside [1, 8].
  */
 int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
                   int32_t iop_window, uint64_t seed, const logdet_opts* opts,
@@ -376,19 +392,23 @@ void logdet_plan_destroy(logdet_plan p);
 
 /* logdet_hessenberg_log_e1_noalloc: the same computation as
  * logdet_hessenberg_log_e1, for callers that cannot allocate device memory
- * while they run (inside a stream capture that must not gain allocation
- * nodes, on hosts whose memory budget is fixed at start-up, or under an
- * allocator that forbids cudaMalloc/cudaFree).  The paper has no counterpart;
- * this is a deployment variant.  It allocates nothing: its scratch is a
- * statically sized device array of 8 MiB + 16 KiB inside the library, which
- * every GPU that loads the library holds until the process exits.  The first
- * call on each device looks up that array's device address; make that first
- * call before any stream capture.  Limits: nprobe <= 4096 and, for m >= 80
- * (work matrices beyond shared memory), 4 m^2 nprobe <= 1048576; larger
- * requests return LOGDET_EINVAL without running.  All calls share the one
- * array, so calls whose kernels may overlap on the GPU (different streams
- * with no ordering between them) race; order them on one stream.  Arguments,
- * layouts and status bits as logdet_hessenberg_log_e1. */
+ * while they run: hosts whose device memory is handed out once at start-up
+ * under a fixed budget, callers under an external allocator that owns all
+ * device memory and forbids cudaMalloc/cudaFree, and loops that must not pay
+ * for cudaFree, which synchronises the whole device.  The paper has no
+ * counterpart; this is a deployment variant.  It allocates nothing: its
+ * scratch is a statically sized device array of 8 MiB + 16 KiB inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on each device looks up that array's device address
+ * and keeps it for the life of the process: make that first call before any
+ * stream capture, and do not use this entry point after a reset of the
+ * device (cudaDeviceReset) in the same process.  Limits: nprobe <= 4096 and,
+ * for m >= 81 (work matrices beyond shared memory), 4 m^2 nprobe <= 1048576;
+ * larger requests return LOGDET_EINVAL without running.  All calls share the
+ * one array, so calls whose kernels may overlap on the GPU (different streams
+ * with no ordering between them) race; order them on one stream.  Each call
+ * clears the status words it uses and blocks until they are read back.
+ * Arguments, layouts and status bits as logdet_hessenberg_log_e1. */
 int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int32_t* msteps_dev,
                                      int32_t m, int32_t nprobe, double* c_dev, uint32_t* status,
                                      void* cuda_stream);

@@ -77,6 +77,7 @@ class logdet_opts(C.Structure):
         ("per_probe", C.POINTER(C.c_double)), ("z_norm2", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("shift", C.c_double),
         ("plain_slq", C.c_int32), ("gaussian_probes", C.c_int32),
+        ("block_width", C.c_int32),
     ]
 
 
@@ -181,7 +182,8 @@ def _stream(stream) -> int:
     return getattr(stream, "cuda_stream", stream)
 
 
-def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0, plain=0, gaussian=0):
+def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0, plain=0, gaussian=0,
+               block_width=0):
     o = logdet_opts()
     _lib.logdet_opts_default(C.byref(o))
     o.precision = precision
@@ -196,6 +198,7 @@ def _make_opts(precision, tol, lam, stream, shift, per, zn, autotune=0, plain=0,
     o.autotune = int(autotune)
     o.plain_slq = int(plain)
     o.gaussian_probes = int(gaussian)
+    o.block_width = int(block_width)
     return o
 
 
@@ -303,27 +306,31 @@ class Handle:
         return dim.value, L.value, A.value
 
     def _run(self, fn, name, num_probes, krylov_steps, iop_window, seed, precision, tol,
-             lam, stream, shift=0.0, autotune=0, plain=0, gaussian=0):
+             lam, stream, shift=0.0, autotune=0, plain=0, gaussian=0, block_width=0):
         s = 0 if plain else num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = _make_opts(precision, tol, lam, stream, shift, per, zn, autotune, plain, gaussian)
+        o = _make_opts(precision, tol, lam, stream, shift, per, zn, autotune, plain, gaussian,
+                       block_width)
         res = logdet_result()
         _check(fn(self._h, num_probes, krylov_steps, iop_window, seed, C.byref(o), C.byref(res)),
                name)
         return _result(res, per, zn, s, r)
 
     def oslq(self, num_probes, krylov_steps, seed=0, iop_window=0, precision=FP64, tol=None,
-             lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0) -> Result:
+             lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0,
+             block_width=0) -> Result:
         return self._run(_lib.logdet_oslq, "logdet_oslq", num_probes, krylov_steps, iop_window,
-                         seed, precision, tol, lam, stream, shift, autotune, plain, gaussian)
+                         seed, precision, tol, lam, stream, shift, autotune, plain, gaussian,
+                         block_width)
 
     def osaiop(self, num_probes, krylov_steps, iop_window=2, seed=0, precision=FP64, tol=None,
-               lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0) -> Result:
+               lam=None, stream=None, shift=0.0, autotune=0, plain=0, gaussian=0,
+               block_width=0) -> Result:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
                          iop_window, seed, precision, tol, lam, stream, shift, autotune, plain,
-                         gaussian)
+                         gaussian, block_width)
 
     def estimate_bytes(self, method, num_probes, krylov_steps, iop_window=0, precision=FP64,
                        shift=0.0) -> int:
@@ -354,13 +361,14 @@ class Plan:
 
     def __init__(self, handle: Handle, method: int, num_probes: int, krylov_steps: int,
                  iop_window: int = 0, precision=FP64, tol=None, lam=None, stream=None,
-                 shift=0.0, autotune=0, plain=0, gaussian=0):
+                 shift=0.0, autotune=0, plain=0, gaussian=0, block_width=0):
         self._p = _P()
         self._handle = handle
         self.s = 0 if plain else num_probes // 3
         self.r = num_probes - 2 * self.s
         dummy = np.zeros(1)
-        o = _make_opts(precision, tol, lam, stream, shift, dummy, dummy, autotune, plain, gaussian)
+        o = _make_opts(precision, tol, lam, stream, shift, dummy, dummy, autotune, plain, gaussian,
+                       block_width)
         o.per_probe = None
         o.z_norm2 = None
         _check(_lib.logdet_plan_create(handle.raw, method, num_probes, krylov_steps, iop_window,
@@ -408,12 +416,12 @@ class Server:
 
     def submit(self, handle: Handle, method: int, num_probes: int, krylov_steps: int,
                iop_window: int = 0, seed: int = 0, precision=FP64, tol=None, lam=None,
-               shift=0.0, autotune=0) -> int:
+               shift=0.0, autotune=0, block_width=0) -> int:
         s = num_probes // 3
         r = num_probes - 2 * s
         per = np.zeros(max(s + r, 1))
         zn = np.zeros(max(r, 1))
-        o = _make_opts(precision, tol, lam, None, shift, per, zn, autotune)
+        o = _make_opts(precision, tol, lam, None, shift, per, zn, autotune, block_width=block_width)
         rid = _u64()
         _check(_lib.logdet_submit(self._s, handle.raw, method, num_probes, krylov_steps, iop_window,
                                   seed, C.byref(o), C.byref(rid)), "logdet_submit")

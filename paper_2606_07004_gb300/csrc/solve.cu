@@ -61,6 +61,24 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
     set_error("gridded operators support FP64 and mixed FP32 blocks only");
     return LOGDET_EINVAL;
   }
+  if (c.block_width < 0) {
+    set_error("block_width=%d must be >= 0", c.block_width);
+    return LOGDET_EINVAL;
+  }
+  if (c.block_width > 0 && h->kind != 1) {
+    // Every Krylov block (s + r probes; OSA-IOP's s sketch columns) rounded
+    // up to whole 16-byte vectors must split into slices of the width.
+    const int vec = c.precision == LOGDET_FP64 ? 2 : 4;
+    const int ld = round_up(s + r, vec), lds = std::max(round_up(s, vec), vec);
+    bool ok = c.block_width % vec == 0;
+    for (int w : {ld, c.method == 1 && s > 0 ? lds : ld})
+      ok = ok && w % std::min(c.block_width, w) == 0;
+    if (!ok) {
+      set_error("block_width=%d must be a multiple of %d dividing the block widths %d and %d",
+                c.block_width, vec, ld, lds);
+      return LOGDET_EINVAL;
+    }
+  }
   double lo, hi;
   spectral_bounds(h, c, lo, hi);
   if (!(hi > 0.0) || !(lo > 0.0) || lo > hi) {
@@ -598,7 +616,12 @@ struct Solve : ISolve {
   // autotuner's choice for this matrix.
   int layout(int w, bool track_e, TuneCfg* tc) {
     *tc = TuneCfg();
-    if (!c.autotune || h->kind == 1) return LOGDET_OK;
+    if (h->kind == 1) return LOGDET_OK;
+    if (c.block_width > 0) {  // the caller's slice width (validated to divide w)
+      tc->split = w / std::min(c.block_width, w);
+      return LOGDET_OK;
+    }
+    if (!c.autotune) return LOGDET_OK;
     const int nd = c.method == 0 ? 1 : kk, nb = c.method == 0 ? 2 : kk;
     return autotune_krylov<T>(h, vals.p, w, nd, nb, track_e ? 1 : 0,
                               st, tc);
@@ -955,6 +978,7 @@ SolveCfg make_solve_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t se
     c.autotune = opts->autotune;
     c.plain = opts->plain_slq;
     c.gaussian = opts->gaussian_probes;
+    c.block_width = opts->block_width;
   }
   return c;
 }

@@ -38,6 +38,7 @@ struct SolveCfg {
   int autotune = 0;    // layout of the Krylov kernels from the autotuner
   int plain = 0;       // 1 = plain SLQ: no sketch, s = 0, r = P
   int gaussian = 0;    // 1 = Gaussian probes
+  int block_width = 0; // > 0: columns per Krylov pass slice (logdet_opts.block_width)
 };
 
 struct SolveOut {
