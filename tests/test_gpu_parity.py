@@ -385,6 +385,50 @@ def test_autotuned_layout_parity(method, tmp_path, monkeypatch):
     assert lines and all(len(l.split()) == 11 for l in lines)
 
 
+@pytest.mark.parametrize("method,k", [("oslq", 0), ("osaiop", 4)])
+def test_block_width_forced_layouts_parity(method, k):
+    # logdet_opts.block_width: 60 probes give a 40-column block (OSA-IOP's
+    # sketch block: 20 columns); widths 10 and 20 run them as 4/2 slices
+    # (2/1 for the sketch block), each against the FP64 oracle.
+    A = W.laplacian_3d(22, 20, 19, shift=0.02)      # n = 8360
+    Q = A.to_scipy()
+    est = O.oslq(Q, 60, 20, seed=6) if method == "oslq" else O.osaiop(Q, 60, 20, k=k, seed=6)
+    with B.Handle.from_csr(A) as h:
+        f = h.oslq if method == "oslq" else (lambda *a, **kw: h.osaiop(*a, iop_window=k, **kw))
+        full = f(60, 20, seed=6)
+        for w in (10, 20):
+            res = f(60, 20, seed=6, block_width=w)
+            assert rel(res.logdet, est.logdet) <= RTOL_FP64, w
+            np.testing.assert_allclose(res.per_probe, full.per_probe, rtol=0, atol=1e-9)
+        # mixed FP32: 4-column vectors, width 20 divides both blocks
+        r32 = f(60, 20, seed=6, precision=B.MIXED_FP32, block_width=20)
+        assert rel(r32.logdet, full.logdet) <= RTOL_MIXED
+        # widths that do not fit the blocks are argument errors
+        for w, prec in [(3, B.FP64), (6, B.FP64)] + ([(8, B.MIXED_FP32)] if method == "osaiop" else []):
+            with pytest.raises(B.LogdetError) as e:
+                f(60, 20, seed=6, precision=prec, block_width=w)
+            assert e.value.code == B.EINVAL, (w, prec)
+        with pytest.raises(B.LogdetError) as e:
+            f(60, 20, seed=6, block_width=-2)
+        assert e.value.code == B.EINVAL
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_indefinite_diagonal_clamps_like_oracle(m):
+    # Q = diag(-1, 2): Gershgorin lower bound -1 is clamped (1e-6 of the upper
+    # bound), J = Q/2 has the eigenvalue -1/2, every Gauss rule meets a Ritz
+    # value <= 0, which both sides clamp to lambda_lo/alpha and flag.
+    n, a = 3000, 700
+    A = W.diagonal_matrix(np.r_[np.full(a, -1.0), np.full(n - a, 2.0)])
+    for plain in (1, 0):
+        est = O.oslq(A.to_scipy(), 9, m, seed=5, hutchpp=not plain)
+        with B.Handle.from_csr(A) as h:
+            res = h.oslq(9, m, seed=5, plain=plain)
+        assert est.flags & O.estimators.FLAG_NONPOSITIVE_RITZ
+        assert res.status_bits & B.ST_NONPOS_RITZ
+        assert rel(res.logdet, est.logdet) <= RTOL_FP64, plain
+
+
 def test_autotuned_mixed_within_1e4_of_fp64():
     A = W.matern_2d(200, 0.05)
     with B.Handle.from_csr(A) as h:
