@@ -1284,19 +1284,23 @@ template int sketch_assemble<bf16>(const bf16*, int, int, int, const double*, do
 // ===========================================================================
 // Allocation-free Hessenberg logarithm.
 //
-// Some callers cannot allocate device memory while they run: code executing
-// inside a CUDA stream capture that must not add allocation nodes, real-time
-// or embedded hosts whose memory budget is fixed at start-up, and callers
-// running under an external allocator that forbids cudaMalloc/cudaFree on
-// their stream.  For them the same Hessenberg-log kernel can run on scratch
-// that lives in this file: a statically sized device array, loaded once with
-// the library and held by every GPU that loads it until the process exits.
+// Some callers cannot allocate device memory while they run: hosts whose
+// device memory is handed out once at start-up under a fixed budget,
+// callers running under an external allocator (a framework's caching pool)
+// that owns all device memory and forbids cudaMalloc/cudaFree, and loops
+// that must not pay for cudaFree, which synchronises the whole device.  For
+// them the same Hessenberg-log kernel can run on scratch that lives in this
+// file: a statically sized device array, loaded once with the library and
+// held by every GPU that loads it until the process exits.
 //
 // Limits: nprobe <= kNoAllocMaxProbes (status words), and when the four m x m
-// work matrices do not fit in shared memory (m >= 80), 4 m^2 nprobe doubles
-// must fit in kNoAllocMatDoubles (8 MiB).  Larger requests are rejected.
-// All calls share the one array; two calls whose kernels overlap on the GPU
-// (different streams, no ordering between them) race on it.
+// work matrices do not fit in shared memory (m >= 81: 4 m^2 doubles above
+// 200 KiB), 4 m^2 nprobe doubles must fit in kNoAllocMatDoubles (8 MiB).
+// Larger requests are rejected.  All calls share the one array; two calls
+// whose kernels overlap on the GPU (different streams, no ordering between
+// them) race on it.  The array's device address is looked up once per device
+// and kept for the life of the process, so the entry point must not be used
+// after a reset of that device (cudaDeviceReset) in the same process.
 // ===========================================================================
 namespace ld {
 
@@ -1312,7 +1316,7 @@ void* g_noalloc_ptr[64] = {nullptr};
 
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device (the first call on a device does it; make that first call
-// outside any stream capture).
+// before any stream capture).
 int noalloc_scratch(void** out) {
   int dev = 0;
   LD_CUDA(cudaGetDevice(&dev));
