@@ -11,6 +11,13 @@ tridiagonal Gauss rules, Hessenberg logarithms, assembly).
   python bench.py [--gpus N --steps K --warmup W]           # CUDA path
   python bench.py --impl reference [...]                    # FP64 CPU oracle
 
+At N = 1 the line also carries two bounded objects, each with its own clock
+record: matern_mixed (the mixed-precision configuration: Matern 1024^2, FP32
+vectors, OSLQ m = 80, 120 probes; solves/s, error against the FP64 CUDA path,
+HBM roofline of the Krylov passes) and serving (the continuous-batching
+configuration at a reduced request count: mixed batched server against plain
+FP64 one at a time, solves/s and p50/p99 latency).
+
 Under torchrun every rank solves its own copy of the workload (independent
 problems, no data-path collective: weak scaling); the barrier and the max over
 ranks of the timed region use torch.distributed.  Rank 0 prints one JSON line.
@@ -107,14 +114,25 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 class ClockSampler:
-    def __init__(self, gpu_index):
+    """nvidia-smi samples (every 200 ms) of one GPU while a region runs, kept in
+    a temporary file (or under --clock-dir when given) and summarised at stop."""
+    clock_dir = None
+
+    def __init__(self, gpu_index, tag="main"):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
         self.gpu = gpu_index
+        if self.clock_dir:
+            os.makedirs(self.clock_dir, exist_ok=True)
+            self.path = os.path.join(self.clock_dir, f"clocks_{tag}_gpu{gpu_index}.csv")
+            self.keep = True
+        else:
+            fd, self.path = tempfile.mkstemp(prefix=f"logdet_clocks_{tag}_", suffix=".csv")
+            os.close(fd)
+            self.keep = False
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}", "--format=csv",
@@ -145,6 +163,11 @@ class ClockSampler:
             for k, v in zip(keys, parts[5:9]):
                 if v.lower() == "active":
                     names.add(k)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
@@ -456,7 +479,6 @@ def cuda_arm(args):
     kr_gbs = kr_bytes / (kr_ms / 1e3) / 1e9 if kr_ms > 0 else 0.0
     ratio = traffic_ratio_from_profile()
     traffic = ratio * sp["bytes"] / max(1, sp["launches"]) if ratio else None
-    all_lat = sorted(x for v in lat.values() for x in v)
 
     def pct(xs, q):
         xs = sorted(xs)
@@ -492,9 +514,24 @@ def cuda_arm(args):
         "clocks": clk,
         "latency_ms": {k: {"p50": pct(v, 0.5), "p99": pct(v, 0.99), "mean": statistics.mean(v)}
                        for k, v in lat.items()},
-        "latency_ms_all": {"p50": pct(all_lat, 0.5), "p99": pct(all_lat, 0.99)},
+        "latency_note": "device time per blocking solve of each kind (CUDA events); serving "
+                        "latencies (submit to result) are in the serving object",
         "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
     }
+    if rank == 0 and ws == 1 and not args.no_extras:
+        # The mixed-precision and serving configurations, bounded, each with
+        # its own clock record (one GPU only: at N > 1 every rank would repeat them).
+        for key, fn in (("matern_mixed", lambda: matern_measure(args.extra_solves, 2, at)),
+                        ("serving", lambda: serving_measure(args.serving_requests, args.slots,
+                                                            args.budget_gb))):
+            try:
+                line[key] = fn()
+            except Exception as e:  # reported, not hidden
+                line[key] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+        if "serving" in line and "requests" in line["serving"]:
+            line["serving"]["note"] = ("the configured stream has 2000 requests; this line runs "
+                                       "%d of the same law to bound the benchmark's run time"
+                                       % args.serving_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         try:
             res = run_oracle_sample_child(1000, all_cores=True)
@@ -519,82 +556,98 @@ def cuda_arm(args):
     return 0
 
 
-def matern_case(args):
+MATERN_N, MATERN_K2, MATERN_P, MATERN_M = 1024, 0.05, 120, 80
+
+
+def matern_measure(solves: int, warmup: int, autotune: int, bf16_trial: bool = False) -> dict:
     """Mixed-precision workload: SPDE Matern precision (0.05 I + L_2D)^2 on a
     1024^2 grid (n = 1,048,576, 13-point stencil), FP32 values and vectors,
     compensated FP32 dots and Hutch++ split, FP64 small solves; OSLQ m = 80
-    with 120 probes.  Reports solves/s, the HBM roofline of the Krylov passes and the
-    relative error against the FP64 path on the same (FP32-valued) matrix and
-    seed.  An extra measurement line, not the default benchmark."""
+    with 120 probes.  Solves/s (CUDA events on the solve stream, inputs
+    resident), the HBM roofline of the Krylov passes, per-solve device
+    latency, and the relative error against the FP64 CUDA path on the same
+    (FP32-valued) matrix and seed.  With bf16_trial, the same solves with the
+    Krylov vectors stored in BF16."""
     import numpy as np
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
 
-    A = W.matern_2d(1024, 0.05, dtype=np.float32)
+    A = W.matern_2d(MATERN_N, MATERN_K2, dtype=np.float32)
     h = B.Handle.from_csr(A)
-    P, m = 120, 80
+    P, m = MATERN_P, MATERN_M
     stream = torch.cuda.Stream()
-    for i in range(args.warmup):
-        h.oslq(P, m, seed=i, precision=B.MIXED_FP32, stream=stream,
-                   autotune=args.autotune)
+    for i in range(warmup):
+        h.oslq(P, m, seed=i, precision=B.MIXED_FP32, stream=stream, autotune=autotune)
     torch.cuda.synchronize()
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device(), "matern")
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_FP32, stream=stream,
-                  autotune=args.autotune) for i in range(args.steps)]
+    res = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_FP32, stream=stream, autotune=autotune)
+           for i in range(solves)]
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     B.logdet_profile_enable(False)
     prof = B.profile_snapshot()
     t = e0.elapsed_time(e1) / 1e3
-    ref = h.oslq(P, m, seed=100, precision=B.FP64)
+    ref = h.oslq(P, m, seed=100, precision=B.FP64, stream=stream)
     err = abs(res[0].logdet - ref.logdet) / abs(ref.logdet)
-    # BF16 vector storage trial: same workload, Krylov vectors in BF16.
-    h.oslq(P, m, seed=0, precision=B.MIXED_BF16VEC)
-    B.logdet_profile_reset()
-    B.logdet_profile_enable(True)
-    e0.record(stream)
-    rb = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_BF16VEC, stream=stream)
-          for i in range(args.steps)]
-    e1.record(stream)
-    torch.cuda.synchronize()
-    B.logdet_profile_enable(False)
-    pb = B.profile_snapshot()
-    tb = e0.elapsed_time(e1) / 1e3
-    errb = abs(rb[0].logdet - ref.logdet) / abs(ref.logdet)
-    kbb = pb["spmm"]["bytes"] + pb["update"]["bytes"]
-    kmb = pb["spmm"]["ms"] + pb["update"]["ms"]
-    h.close()
     pk, kind = peaks()
     kb = prof["spmm"]["bytes"] + prof["update"]["bytes"]
     kms = prof["spmm"]["ms"] + prof["update"]["ms"]
     gbs = kb / (kms / 1e3) / 1e9
-    sp = prof["spmm"]
-    lat = sorted(r.device_ms for r in res)
-    print(json.dumps({
+    sp_ = prof["spmm"]
+    lat = [r.device_ms for r in res]
+    out = {
         "workload": "Matern (0.05 I + L)^2 on 1024^2 (n=1048576, nnz=%d), mixed FP32, OSLQ m=80, "
-                    "120 probes" % A.nnz,
-        "metric": METRIC, "value": args.steps / t, "unit": UNIT, "dtype": "f32 (compensated dots and "
-        "Hutch++ Gram sums; FP64 small solves)", "steps": args.steps, "warmup": args.warmup,
-        "rel_err_vs_fp64": err, "logdet": res[0].logdet, "logdet_fp64": ref.logdet,
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[-1]},
-        "roofline": {"kernels": "k_spmm<float> + k_update<float>", "bound": "hbm",
-                     "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "120 probes, seed 100 + solve index" % A.nnz,
+        "value": solves / t, "unit": UNIT, "solves": solves, "warmup": warmup,
+        "dtype": "f32 (compensated dots and Hutch++ Gram sums; FP64 small solves)",
+        "rel_err_vs_fp64": err, "within_1e-4": err <= 1e-4, "logdet": res[0].logdet,
+        "logdet_fp64": ref.logdet, "fp64_solve_ms": ref.device_ms,
+        "latency_ms": {"p50": _pct(lat, 0.5), "p99": _pct(lat, 0.99),
+                       "what": "device time per blocking solve (CUDA events)"},
+        "roofline": {"kernels": "k_spmm_sweep<float> + k_update<float> (SpMM + Krylov passes)",
+                     "bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": gbs / pk["hbm_gbs"], "peak_source": kind,
-                     "spmm_gbs": sp["bytes"] / (sp["ms"] / 1e3) / 1e9,
+                     "spmm_gbs": sp_["bytes"] / (sp_["ms"] / 1e3) / 1e9,
                      "update_gbs": prof["update"]["bytes"] / (prof["update"]["ms"] / 1e3) / 1e9},
-        "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "bf16_vector_trial": {"value": args.steps / tb, "unit": UNIT, "rel_err_vs_fp64": errb,
-                              "within_1e-4": errb <= 1e-4, "krylov_gbs": kbb / (kmb / 1e3) / 1e9,
-                              "kernel_ms_per_solve": {k: v["ms"] / args.steps for k, v in pb.items()}},
-        "clocks": clk}))
+        "kernel_ms_per_solve": {k: v["ms"] / solves for k, v in prof.items()},
+        "clocks": clk,
+    }
+    if bf16_trial:
+        h.oslq(P, m, seed=0, precision=B.MIXED_BF16VEC)
+        B.logdet_profile_reset()
+        B.logdet_profile_enable(True)
+        e0.record(stream)
+        rb = [h.oslq(P, m, seed=100 + i, precision=B.MIXED_BF16VEC, stream=stream)
+              for i in range(solves)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        B.logdet_profile_enable(False)
+        pb = B.profile_snapshot()
+        tb = e0.elapsed_time(e1) / 1e3
+        errb = abs(rb[0].logdet - ref.logdet) / abs(ref.logdet)
+        kbb = pb["spmm"]["bytes"] + pb["update"]["bytes"]
+        kmb = pb["spmm"]["ms"] + pb["update"]["ms"]
+        out["bf16_vector_trial"] = {
+            "value": solves / tb, "unit": UNIT, "rel_err_vs_fp64": errb, "within_1e-4": errb <= 1e-4,
+            "krylov_gbs": kbb / (kmb / 1e3) / 1e9,
+            "kernel_ms_per_solve": {k: v["ms"] / solves for k, v in pb.items()}}
+    h.close()
+    return out
+
+
+def matern_case(args):
+    """--workload matern: the mixed-precision line on its own, with the BF16
+    vector-storage trial."""
+    out = matern_measure(args.steps, args.warmup, args.autotune, bf16_trial=True)
+    print(json.dumps(dict(out, metric=METRIC)))
     return 0
 
 
@@ -603,70 +656,91 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
 
 
-def serving_case(args):
+SERVING_P, SERVING_M = 30, 50
+
+
+def serving_requests(N: int, seed: int = 2024):
+    """The request stream of the serving workload: request i has type uniform
+    over {2D 5-point Laplacian, 3D 7-point Laplacian, Matern}, a size n drawn
+    log-uniformly from [1e4, 4e6] and rounded to a grid side (sqrt n for the 2D
+    grids, cbrt n for the 3D grid), and a value t drawn log-uniformly from
+    [1e-3, 1]: the diagonal shift of a Laplacian (Q + t I, applied
+    matrix-free), the kappa^2 of a Matern operator (k^2 I + L)^2.  Seed =
+    request index.  Returns [(type, side, t)]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(N):
+        typ = ("l2d", "l3d", "mat")[int(rng.integers(3))]
+        n = math.exp(rng.uniform(math.log(1e4), math.log(4e6)))
+        t = math.exp(rng.uniform(math.log(1e-3), 0.0))
+        side = int(round(n ** (1 / 3))) if typ == "l3d" else int(round(n ** 0.5))
+        out.append((typ, side, t))
+    return out
+
+
+def serving_measure(N: int, slots: int, budget_gb: float) -> dict:
     """Continuous-batching serving workload (a GP hyper-parameter search's
-    stream of log-determinants).  Requests: type uniform over {2D Laplacian,
-    3D Laplacian, Matern (kappa^2 = 0.05)}, n log-uniform in [1e4, 4e6]
-    (snapped to a pool of 4 grid sizes per type), diagonal shift log-uniform in
-    [1e-3, 1] (applied matrix-free), OSLQ m = 50 with 30 probes, seed = index.
-    The mixed-precision batched server is timed on a burst (capacity) and on a
-    Poisson stream at 0.8 x capacity; the plain FP64 one-at-a-time form is
-    timed solve by solve and its FIFO queue replayed on the same arrival times.
-    """
+    stream of log-determinants; request law in serving_requests), OSLQ m = 50
+    with 30 probes per request.  The mixed-precision batched server is timed on
+    a burst (all requests at t = 0: capacity) and on a Poisson stream at 0.8 x
+    that capacity; the plain FP64 form is timed one blocking solve at a time
+    and its FIFO queue replayed on the same arrival times.  Latencies are host
+    wall clock, submit to result."""
     import threading
+    from concurrent.futures import ThreadPoolExecutor
     import numpy as np
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
 
-    rng = np.random.default_rng(2024)
-    N = args.requests
+    reqs = serving_requests(N)
     t_build = time.perf_counter()
-    pool = {}
-    for typ in ("l2d", "l3d", "mat"):
-        for nt in np.geomspace(1e4, 4e6, 4):
-            if typ == "l3d":
-                side = int(round(nt ** (1 / 3)))
-                A = W.laplacian_3d(side)
-            elif typ == "l2d":
-                side = int(round(nt ** 0.5))
-                A = W.laplacian_2d(side)
-            else:
-                side = int(round(nt ** 0.5))
-                A = W.matern_2d(side, 0.05)
-            pool[(typ, int(nt))] = (A.n, B.Handle.from_csr(A))
+    keys = sorted({(typ, side, t if typ == "mat" else 0.0) for typ, side, t in reqs})
+
+    def make(key):
+        typ, side, k2 = key
+        if typ == "l3d":
+            return W.laplacian_3d(side)
+        if typ == "l2d":
+            return W.laplacian_2d(side)
+        return W.matern_2d(side, k2)
+
+    handles, rows = {}, 0
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        for key, A in zip(keys, ex.map(make, keys)):
+            handles[key] = B.Handle.from_csr(A)
+            rows += A.n
     t_build = time.perf_counter() - t_build
-    sizes = sorted({k[1] for k in pool})
-    reqs = []
-    for i in range(N):
-        typ = ("l2d", "l3d", "mat")[int(rng.integers(3))]
-        n = math.exp(rng.uniform(math.log(1e4), math.log(4e6)))
-        nt = min(sizes, key=lambda s: abs(math.log(s) - math.log(n)))
-        shift = math.exp(rng.uniform(math.log(1e-3), 0.0))
-        reqs.append((pool[(typ, nt)][1], shift, i, pool[(typ, nt)][0]))
-    P, m = 30, 50
-    budget = int(args.budget_gb * (1 << 30))
+    jobs = []
+    for i, (typ, side, t) in enumerate(reqs):
+        key = (typ, side, t if typ == "mat" else 0.0)
+        jobs.append((handles[key], 0.0 if typ == "mat" else t, i))
+    P, m = SERVING_P, SERVING_M
+    budget = int(budget_gb * (1 << 30))
+    clocks = ClockSampler(torch.cuda.current_device(), "serving")
+    clocks.start()
     # 1. burst through the server (mixed FP32): capacity
-    with B.Server(budget, max_slots=args.slots) as srv:
-        srv.wait(srv.submit(reqs[0][0], B.METHOD_OSLQ, P, m, seed=0, precision=B.MIXED_FP32,
-                            shift=reqs[0][1]))  # warm-up
+    with B.Server(budget, max_slots=slots) as srv:
+        srv.wait(srv.submit(jobs[0][0], B.METHOD_OSLQ, P, m, seed=0, precision=B.MIXED_FP32,
+                            shift=jobs[0][1]))  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ids = [srv.submit(h, B.METHOD_OSLQ, P, m, seed=s, precision=B.MIXED_FP32, shift=sh)
-               for h, sh, s, _ in reqs]
+               for h, sh, s in jobs]
         burst = [srv.wait(i) for i in ids]
         t_burst = time.perf_counter() - t0
         st_burst = srv.stats()
     cap = N / t_burst
     lam = 0.8 * cap
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+    arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / lam, N))
     # 2. Poisson stream through the server
-    with B.Server(budget, max_slots=args.slots) as srv:
+    with B.Server(budget, max_slots=slots) as srv:
         ids = [None] * N
         t0 = time.perf_counter()
 
         def feeder():
-            for i, (h, sh, s, _) in enumerate(reqs):
+            for i, (h, sh, s) in enumerate(jobs):
                 dt = arrivals[i] - (time.perf_counter() - t0)
                 if dt > 0:
                     time.sleep(dt)
@@ -680,34 +754,49 @@ def serving_case(args):
         st_stream = srv.stats()
     lat_srv = [r.latency_ms for r in stream]
     # 3. plain FP64 one at a time (blocking), FIFO replay on the same arrivals
+    jobs[0][0].oslq(P, m, seed=0, shift=jobs[0][1])  # warm-up
     svc, r64 = [], []
-    for h, sh, s, _ in reqs:
+    for h, sh, s in jobs:
         t1 = time.perf_counter()
         r64.append(h.oslq(P, m, seed=s, shift=sh))
         svc.append(time.perf_counter() - t1)
+    clk = clocks.stop()
     done, lat64 = 0.0, []
     for a, sv in zip(arrivals, svc):
         done = max(done, a) + sv
         lat64.append(1e3 * (done - a))
     errs = [abs(a.logdet - b.logdet) / abs(b.logdet) for a, b in zip(stream, r64)]
     same = all(a.logdet == b.logdet for a, b in zip(stream, burst))
-    for _, h in pool.values():
+    for h in handles.values():
         h.close()
-    print(json.dumps({
-        "workload": "serving: %d OSLQ requests (m=50, 30 probes), 2D/3D Laplacian and Matern, "
-                    "n log-uniform [1e4, 4e6] (pool of 4 sizes per type), shift log-uniform "
-                    "[1e-3, 1]" % N,
-        "metric": METRIC, "unit": UNIT,
+    ns = sorted(side ** (3 if typ == "l3d" else 2) for typ, side, _ in reqs)
+    fp64_rate = N / sum(svc)
+    return {
+        "workload": "serving: %d OSLQ requests (m=50, 30 probes), type uniform over {2D Laplacian, "
+                    "3D Laplacian, Matern}, n log-uniform [1e4, 4e6] rounded to a grid side, "
+                    "shift (Laplacians) / kappa^2 (Matern) log-uniform [1e-3, 1]" % N,
+        "requests": N, "distinct_matrices": len(handles),
+        "n": {"min": ns[0], "median": ns[len(ns) // 2], "max": ns[-1], "total_rows": rows},
+        "unit": UNIT,
         "mixed_batched": {"burst_solves_per_s": cap, "stream_rate": lam,
                           "stream_solves_per_s": N / t_stream,
                           "p50_ms": _pct(lat_srv, 0.5), "p99_ms": _pct(lat_srv, 0.99),
-                          "max_resident": st_stream["max_resident"],
+                          "max_resident": st_stream["max_resident"], "slots": slots,
                           "batched_steps_per_tick": st_burst["batched_steps"] / max(1, st_burst["ticks"])},
-        "fp64_one_at_a_time": {"solves_per_s": N / sum(svc), "p50_ms": _pct(lat64, 0.5),
+        "fp64_one_at_a_time": {"solves_per_s": fp64_rate, "p50_ms": _pct(lat64, 0.5),
                                "p99_ms": _pct(lat64, 0.99)},
-        "speedup_solves_per_s": cap / (N / sum(svc)),
-        "max_rel_err_mixed_vs_fp64": max(errs), "burst_equals_stream_bitwise": same,
-        "matrix_build_s": t_build}))
+        "speedup_solves_per_s": cap / fp64_rate,
+        "max_rel_err_mixed_vs_fp64": max(errs), "within_1e-4": max(errs) <= 1e-4,
+        "burst_equals_stream_bitwise": same,
+        "latency": "host wall clock, submit to result; FP64 latencies from a FIFO replay of "
+                   "the measured service times on the same Poisson arrivals",
+        "matrix_build_s": t_build, "clocks": clk}
+
+
+def serving_case(args):
+    """--workload serving: the serving line on its own (--requests N)."""
+    out = serving_measure(args.requests, args.slots, args.budget_gb)
+    print(json.dumps(dict(out, metric=METRIC)))
     return 0
 
 
@@ -980,12 +1069,21 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--slots", type=int, default=64, help="serving: server slots")
     ap.add_argument("--budget-gb", type=float, default=200.0, help="server memory budget")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the matern_mixed and serving objects")
+    ap.add_argument("--extra-solves", type=int, default=10,
+                    help="timed solves of the matern_mixed object of the default line")
+    ap.add_argument("--serving-requests", type=int, default=120,
+                    help="requests of the serving object of the default line")
+    ap.add_argument("--clock-dir", default=None,
+                    help="keep the nvidia-smi clock samples as CSV files in this directory")
     ap.add_argument("--small-case", action="store_true",
                     help="one OSLQ + one OSA-IOP solve on a 100^3 Laplacian (profiling target)")
     ap.add_argument("--small-case-fp32", action="store_true", help="the small case in mixed FP32")
     ap.add_argument("--oracle-sample-child", type=int, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-all-cores", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    ClockSampler.clock_dir = args.clock_dir
     if args.small_case or args.small_case_fp32:
         return small_case(args)
     if args.workload == "matern":

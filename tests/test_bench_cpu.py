@@ -43,3 +43,24 @@ def test_digest_follows_the_spmm_kernel_and_its_headers(csrc_copy):
     assert bench.spmm_kernel_digest() not in (before, inside)
     # A stale digest turns the traffic figure off.
     assert bench.traffic_ratio_from_profile() is None
+
+
+def test_serving_request_law():
+    # Type uniform over the three operators, n log-uniform in [1e4, 4e6]
+    # rounded to a grid side, shift / kappa^2 log-uniform in [1e-3, 1].
+    import math
+    import numpy as np
+    reqs = bench.serving_requests(3000, seed=5)
+    assert bench.serving_requests(3000, seed=5) == reqs          # seeded
+    types = [r[0] for r in reqs]
+    for t in ("l2d", "l3d", "mat"):
+        assert abs(types.count(t) / len(reqs) - 1 / 3) < 0.04
+    n = np.array([side ** (3 if typ == "l3d" else 2) for typ, side, _ in reqs], dtype=float)
+    assert n.min() >= 0.9e4 and n.max() <= 4.1e6
+    u = (np.log(n) - math.log(1e4)) / (math.log(4e6) - math.log(1e4))
+    assert abs(u.mean() - 0.5) < 0.03 and abs(np.median(u) - 0.5) < 0.05
+    t = np.array([r[2] for r in reqs])
+    assert t.min() >= 1e-3 and t.max() <= 1.0
+    assert abs(np.mean(np.log10(t)) + 1.5) < 0.05
+    # no pool of sizes: most requests get a grid of their own size
+    assert len({(typ, side) for typ, side, _ in reqs}) > 1000
