@@ -835,6 +835,9 @@ def multishift_case(args):
     serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh),
                        autotune=args.autotune) for t, sh in enumerate(shifts)]
     t_serial = time.perf_counter() - t1
+    # Error of each mixed estimate against the FP64 CUDA path (same seed).
+    r64 = [h.osaiop(P, m, iop_window=k, seed=t, shift=float(sh)) for t, sh in enumerate(shifts)]
+    errs = [abs(a.logdet - b.logdet) / abs(b.logdet) for a, b in zip(batched, r64)]
     # Device time per kernel class of one of the solves run alone.
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
@@ -851,6 +854,7 @@ def multishift_case(args):
         "batched_s": t_batched, "serial_s": t_serial,
         "bitwise_equal_batched_vs_serial": all(a.logdet == b.logdet for a, b in zip(batched, serial)),
         "logdets": [r.logdet for r in batched], "shifts": list(map(float, shifts)),
+        "rel_err_mixed_vs_fp64": errs, "fp64_solve_ms": [r.device_ms for r in r64],
         "bytes_per_solve_estimate": need, "max_resident": st["max_resident"],
         "kernel_ms_one_solve": {k: v["ms"] for k, v in prof.items()},
         "krylov_algorithmic_gbs_one_solve": (prof["spmm"]["bytes"] + prof["update"]["bytes"]) /

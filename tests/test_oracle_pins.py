@@ -589,3 +589,37 @@ def test_osaiop_indefinite_sets_complex_log_flag():
     assert O.osaiop(Q, 6, 2, k=2, seed=1).flags & E.FLAG_COMPLEX_LOG
     spd = W.diagonal_matrix(np.r_[np.full(a, 1.0), np.full(n - a, 2.0)]).to_scipy()
     assert not O.osaiop(spd, 6, 2, k=2, seed=1).flags & E.FLAG_COMPLEX_LOG
+
+
+def test_iop_window_amplifies_rounding_on_ill_conditioned_graph():
+    # The batched irregular regime (power-law graph Laplacian + 3.84e-3 I,
+    # kappa ~ 1e5; Algorithm 1 with window k = 4): one FP32 rounding of the
+    # first Krylov vector changes the quadratic form z^T L z by more than
+    # 5e-6 (relative) after m = 100 steps, by less than 1e-7 after m = 40.
+    # Once Ritz values converge the incomplete orthogonalisation lets early
+    # rounding grow, so at m = 100 no implementation with FP32 vectors can
+    # follow the FP64 result to 1e-4 for small shifts (the tolerance of the
+    # mixed path there is set by this, not by the kernels).
+    n, sigma = 2 ** 15, 3.84e-3
+    L = W.powerlaw_graph_laplacian(n, exponent=2.3, mean_degree=8.0, seed=7).to_scipy()
+    Q = (L + sigma * sp.identity(n, format="csr")).tocsr()
+    lo, hi = O.spectral_interval(Q)
+    g = math.sqrt(lo * hi)
+    Qt = Q / g
+    z = O.rademacher_block(0, 1, n, 1)[:, 0]
+
+    class RoundFirst:              # Q~ whose first product is rounded to FP32
+        shape = Qt.shape
+
+        def __init__(self):
+            self.calls = 0
+
+        def __matmul__(self, x):
+            self.calls += 1
+            y = Qt @ x
+            return y.astype(np.float32).astype(np.float64) if self.calls == 1 else y
+
+    for m, lo_bound, hi_bound in ((100, 5e-6, 1.0), (40, 0.0, 1e-7)):
+        a = float(z @ O.iop_log_action(Qt, z, m, 4, math.log(g / lo)))
+        b = float(z @ O.iop_log_action(RoundFirst(), z, m, 4, math.log(g / lo)))
+        assert lo_bound < abs(a - b) / abs(a) < hi_bound, m
