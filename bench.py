@@ -867,7 +867,8 @@ def small2d_case(args):
     """Latency-bound workload: 2D 5-point Dirichlet Laplacian 64^2 + 0.1 I
     (n = 4096, nnz = 20,224; the whole working set sits in L2), OSLQ m = 30
     with 30 probes, FP64, one seed per solve.  Three ways to run the same
-    solves: the blocking call (about 135 launches issued from the host per
+    solves: the blocking call (the Krylov phase as one persistent launch;
+    also timed step by step, about 135 launches issued from the host per
     solve), a graph plan (the solve captured once, one graph launch per seed;
     bit-identical results) and the batched server (many solves per launch).
     Reports solves/s and per-solve latency of each."""
@@ -893,6 +894,23 @@ def small2d_case(args):
             lat_b.append((time.perf_counter() - t1) * 1e3)
         t_b = time.perf_counter() - t0
         launches_b = (B.logdet_launch_count() - c0) / N
+        # the same blocking solves with the Krylov phase issued step by step
+        # (four launches per step) instead of one persistent launch
+        os.environ["LOGDET_KRYLOV_PERSISTENT"] = "0"
+        h.oslq(P, m, seed=0)
+        c0 = B.logdet_launch_count()
+        t0 = time.perf_counter()
+        lat_s = []
+        stepwise = []
+        for i in range(N):
+            t1 = time.perf_counter()
+            stepwise.append(h.oslq(P, m, seed=1000 + i))
+            lat_s.append((time.perf_counter() - t1) * 1e3)
+        t_s_b = time.perf_counter() - t0
+        launches_s = (B.logdet_launch_count() - c0) / N
+        del os.environ["LOGDET_KRYLOV_PERSISTENT"]
+        same_steps = all(a.logdet == b.logdet and np.array_equal(a.per_probe, b.per_probe)
+                         for a, b in zip(blocking, stepwise))
         t0 = time.perf_counter()
         plan = B.Plan(h, B.METHOD_OSLQ, P, m)
         t_plan_make = time.perf_counter() - t0
@@ -932,7 +950,12 @@ def small2d_case(args):
         "workload": "2D Laplacian 64^2 + 0.1 I (n=4096, nnz=%d), OSLQ m=30, 30 probes, FP64" % A.nnz,
         "metric": METRIC, "unit": UNIT, "dtype": "f64",
         "blocking": {"value": N / t_b, "latency_ms": {"p50": _pct(lat_b, 0.5), "p99": _pct(lat_b, 0.99)},
-                     "launches_per_solve": launches_b},
+                     "launches_per_solve": launches_b,
+                     "krylov": "one persistent launch per Krylov phase"},
+        "blocking_step_by_step": {"value": N / t_s_b,
+                                  "latency_ms": {"p50": _pct(lat_s, 0.5), "p99": _pct(lat_s, 0.99)},
+                                  "launches_per_solve": launches_s,
+                                  "bitwise_equal_to_persistent": same_steps},
         "graph_plan": {"value": N / t_p, "latency_ms": {"p50": _pct(lat_p, 0.5), "p99": _pct(lat_p, 0.99)},
                        "kernels_per_replay": kernels, "capture_s": t_plan_make,
                        "bitwise_equal_to_blocking": same},

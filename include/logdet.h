@@ -424,7 +424,8 @@ int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int
  * waits for the recorded events.  Classes: 0 SpMM pass, 1 update pass,
  * 2 per-probe scalar kernels, 3 Cholesky QR, 4 residual projection,
  * 5 small solves (Gauss rules, Hessenberg logs), 6 other, 7 gridded-operator
- * applications.
+ * applications, 8 persistent Krylov runs (all passes and scalar steps of a
+ * small run in one launch).
  */
 #define LOGDET_KC_SPMM    0
 #define LOGDET_KC_UPDATE  1
@@ -434,7 +435,8 @@ int logdet_hessenberg_log_e1_noalloc(const double* H_dev, int32_t ldh, const int
 #define LOGDET_KC_SMALL   5
 #define LOGDET_KC_OTHER   6
 #define LOGDET_KC_GRID    7
-#define LOGDET_KC_COUNT   8
+#define LOGDET_KC_KRUN    8
+#define LOGDET_KC_COUNT   9
 int64_t logdet_launch_count(void);
 /* Forget the autotuner's in-memory cache (the file, if any, is kept). */
 int logdet_autotune_clear(void);

@@ -45,7 +45,7 @@ EXPORTED = [
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
 ]
-KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid"]
+KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
 
 class logdet_result(C.Structure):

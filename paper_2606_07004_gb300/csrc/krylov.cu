@@ -3,6 +3,7 @@
 #include "profile.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 namespace ld {
@@ -61,6 +62,31 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
 
+// Vector load of block data: through the non-coherent path for the step
+// kernels (the block is read-only while they run), through L2 only (.cg)
+// when COH, for the persistent run, whose blocks other CTAs write between
+// its phases.
+template <bool COH, typename T>
+__device__ __forceinline__ void load_v(const T* p, typename Compute<T>::type (&v)[Vec16<T>::N]) {
+  if constexpr (!COH) {
+    load_vec<T>(p, v);
+  } else {
+    using V = typename Vec16<T>::type;
+    const V t = __ldcg(reinterpret_cast<const V*>(p));
+    if constexpr (std::is_same<T, double>::value) { v[0] = t.x; v[1] = t.y; }
+    else if constexpr (std::is_same<T, float>::value) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else {
+      const uint32_t w[2] = {t.x, t.y};
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+      }
+    }
+  }
+}
+
 // FP64 instances with the full dot window hold two CTAs per SM: at 85
 // registers one 480-thread CTA fit, and the update pass of OSA-IOP k = 8
 // then ran at half the FP64 and HBM peaks (a few spilled registers cost
@@ -69,16 +95,17 @@ constexpr int kGather = 4;
 template <typename T, int N>
 constexpr int fp64_wide_min_ctas() { return (std::is_same<T, double>::value && N >= kMaxWin) ? 2 : 0; }
 
-template <typename T, int NDOT>
-__global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
-    k_spmm(const __grid_constant__ SpmmBatch<T> B) {
+// Pass 1 over the tiles (or work items) gt0, gt0 + stride, ... of a batch,
+// each by the whole CTA; the dynamic shared memory holds blockDim.x * V
+// accumulators.  Batch: SpmmBatch or any type with the same members.
+template <typename T, int NDOT, typename Batch, bool COH = false>
+__device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
+                                           unsigned char* smem_raw) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
   using CT = typename Compute<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* smem = reinterpret_cast<Acc*>(smem_raw);
-
-  for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
+  for (int gt = gt0; gt < B.total_tiles; gt += stride) {
     const int jb = find_job(B, gt);
     const SpmmJob<T>& J = B.jobs[jb];
     const int G = J.width / V;
@@ -127,7 +154,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
             a[u] = __ldg(J.vals + q + u * R);
           }
 #pragma unroll
-          for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+          for (int u = 0; u < kGather; ++u) load_v<COH, T>(xcol + (size_t)c[u] * J.ld, xv[u]);
 #pragma unroll
           for (int u = 0; u < kGather; ++u)
 #pragma unroll
@@ -137,7 +164,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
           const int c = __ldg(J.colind + q);
           const CT a = __ldg(J.vals + q);
           CT xv[V];
-          load_vec<T>(xcol + (size_t)c * J.ld, xv);
+          load_v<COH, T>(xcol + (size_t)c * J.ld, xv);
 #pragma unroll
           for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
         }
@@ -158,7 +185,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
           for (int v = 0; v < V; ++v) t[v] += sred[(rr * G + g) * V + v];
         if (has_shift || has_scale) {
           CT xr[V];
-          load_vec<T>(xcol + (size_t)row * J.ld, xr);
+          load_v<COH, T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             if (has_shift) t[v] = fma(CT(J.colshift[col0 + v]), xr[v], t[v]);
@@ -170,7 +197,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
         for (int d = 0; d < NDOT; ++d) {
           if (d < ndots) {
             CT u[V];
-            load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+            load_v<COH, T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], t[v]);
           }
@@ -221,7 +248,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
           for (; q + kGather <= q1; q += kGather) {
             CT xv[kGather][V];
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+            for (int u = 0; u < kGather; ++u) load_v<COH, T>(xcol + (size_t)c[u] * J.ld, xv[u]);
             const bool more = q + 2 * kGather <= q1;
             int cn[kGather];
             CT an[kGather];
@@ -254,7 +281,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
               a[u] = __ldg(J.vals + q + u);
             }
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) load_vec<T>(xcol + (size_t)c[u] * J.ld, xv[u]);
+            for (int u = 0; u < kGather; ++u) load_v<COH, T>(xcol + (size_t)c[u] * J.ld, xv[u]);
 #pragma unroll
             for (int u = 0; u < kGather; ++u)
 #pragma unroll
@@ -265,13 +292,13 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
           const int c = __ldg(J.colind + q);
           const CT a = __ldg(J.vals + q);
           CT xv[V];
-          load_vec<T>(xcol + (size_t)c * J.ld, xv);
+          load_v<COH, T>(xcol + (size_t)c * J.ld, xv);
 #pragma unroll
           for (int v = 0; v < V; ++v) s[v] = fma(a, xv[v], s[v]);
         }
         if (has_shift || has_scale) {
           CT xr[V];
-          load_vec<T>(xcol + (size_t)row * J.ld, xr);
+          load_v<COH, T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             if (has_shift) s[v] = fma(CT(J.colshift[col0 + v]), xr[v], s[v]);
@@ -283,7 +310,7 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
         for (int d = 0; d < NDOT; ++d) {
           if (d < ndots) {
             CT u[V];
-            load_vec<T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+            load_v<COH, T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
           }
@@ -300,6 +327,13 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
     }
     __syncthreads();
   }
+}
+
+template <typename T, int NDOT>
+__global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
+    k_spmm(const __grid_constant__ SpmmBatch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,16 +365,16 @@ constexpr int update_min_ctas() {
   return (std::is_same<T, double>::value && (NB >= kMaxWin || NB <= 2)) ? 2 : 0;
 }
 
-template <typename T, int NB, bool EX>
-__global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
-    k_update(const __grid_constant__ UpdBatch<T> B) {
+// Pass 2 over the tiles gt0, gt0 + stride, ... of a batch (UpdBatch or a
+// type with the same members), each by the whole CTA.
+template <typename T, int NB, bool EX, typename Batch, bool COH = false>
+__device__ __forceinline__ void update_tiles(const Batch& B, int gt0, int stride,
+                                             unsigned char* smem_raw) {
   constexpr int V = Vec16<T>::N;
   using Acc = typename AccOf<T>::type;
   using CT = typename Compute<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Acc* smem = reinterpret_cast<Acc*>(smem_raw);
-
-  for (int gt = blockIdx.x; gt < B.total_tiles; gt += gridDim.x) {
+  for (int gt = gt0; gt < B.total_tiles; gt += stride) {
     const int jb = find_job(B, gt);
     const UpdJob<T>& J = B.jobs[jb];
     const int tile = gt - B.tile_start[jb];
@@ -365,14 +399,17 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
       bool unit = true;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        double a = J.ycoef[col0 + v];
+        double a = COH ? __ldcg(J.ycoef + col0 + v) : J.ycoef[col0 + v];
         yc[v] = CT(a);
         unit = unit && (a == 1.0);
       }
 #pragma unroll
       for (int i = 0; i < NB; ++i)
 #pragma unroll
-        for (int v = 0; v < V; ++v) cf[i][v] = (i < nb) ? CT(J.coef[i * J.ld + col0 + v]) : CT(0);
+        for (int v = 0; v < V; ++v)
+          cf[i][v] = (i < nb) ? CT(COH ? __ldcg(J.coef + i * J.ld + col0 + v)
+                                       : J.coef[i * J.ld + col0 + v])
+                              : CT(0);
 
       // FP64: scale y in place where ycoef != 1 (rows and chunk of this
       // thread only), then read y through L2 so the loop sees those stores.
@@ -392,7 +429,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
       }
       auto load_y = [&](size_t off, CT (&o)[V]) {
         if constexpr (kPre) load_vec_cg<T>(J.y + off, o);
-        else load_vec<T>(J.y + off, o);
+        else load_v<COH, T>(J.y + off, o);
       };
       const bool scale_in_loop = !kPre && !unit;
 
@@ -418,8 +455,8 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
           load_y(off[q], o[q]);
 #pragma unroll
           for (int i = 0; i < NB; ++i)
-            if (i < nb) load_vec<T>(J.basis[i] + off[q], ub[q][i]);
-          if (has_extra) load_vec<T>(J.extra + off[q], ue[q]);
+            if (i < nb) load_v<COH, T>(J.basis[i] + off[q], ub[q][i]);
+          if (has_extra) load_v<COH, T>(J.extra + off[q], ue[q]);
         }
 #pragma unroll
         for (int q = 0; q < kU; ++q) {
@@ -456,8 +493,8 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
         load_y(off, py);
 #pragma unroll
         for (int i = 0; i < NB; ++i)
-          if (i < nb) load_vec<T>(J.basis[i] + off, pu[i]);
-        if (has_extra) load_vec<T>(J.extra + off, pe);
+          if (i < nb) load_v<COH, T>(J.basis[i] + off, pu[i]);
+        if (has_extra) load_v<COH, T>(J.extra + off, pe);
       }
       for (; row < row1; row += R) {
         const size_t off = (size_t)row * J.ld + col0;
@@ -474,8 +511,8 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
           load_y(noff, py);
 #pragma unroll
           for (int i = 0; i < NB; ++i)
-            if (i < nb) load_vec<T>(J.basis[i] + noff, pu[i]);
-          if (has_extra) load_vec<T>(J.extra + noff, pe);
+            if (i < nb) load_v<COH, T>(J.basis[i] + noff, pu[i]);
+          if (has_extra) load_v<COH, T>(J.extra + noff, pe);
         }
         if (scale_in_loop) {
 #pragma unroll
@@ -509,7 +546,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
         for (int i = 0; i < NB; ++i) {
           if (i < nb) {
             CT u[V];
-            load_vec<T>(J.basis[i] + off, u);
+            load_v<COH, T>(J.basis[i] + off, u);
 #pragma unroll
             for (int v = 0; v < V; ++v) o[v] = fma(-cf[i][v], u[v], o[v]);
           }
@@ -519,7 +556,7 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
         for (int v = 0; v < V; ++v) nrm[v].fma(o[v], o[v]);
         if (has_extra) {
           CT u[V];
-          load_vec<T>(J.extra + off, u);
+          load_v<COH, T>(J.extra + off, u);
 #pragma unroll
           for (int v = 0; v < V; ++v) ex[v].fma(u[v], o[v]);
         }
@@ -535,35 +572,59 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
   }
 }
 
+template <typename T, int NB, bool EX>
+__global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
+    k_update(const __grid_constant__ UpdBatch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  update_tiles<T, NB, EX>(B, blockIdx.x, gridDim.x, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Scalar kernels.  One CTA per (probe, dot) reduces that dot's ntiles
 // partials in a fixed order; the last CTA of a probe to finish (an arrival
 // counter behind a fence) runs the probe's scalar recurrence on the reduced
 // values.  Which CTA arrives last does not change any value.
 // ---------------------------------------------------------------------------
-constexpr int kRedThreads = 256;
 constexpr int kRedLanes = 4;  // independent accumulators per thread
 
 
-// Sum of the ntiles partials of (dot d, column p): thread t adds tiles
-// t + blockDim*(kRedLanes*i + l) into accumulator l, the lanes are combined in
-// order, then a shared-memory tree.  Returns the value to every thread.
-template <typename Acc, typename PartT>
+// CTA barriers of the scalar reduction: the whole CTA (k_scalar), or the
+// first kRedThreads threads of a larger CTA (named barrier 1; the persistent
+// Krylov run).
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct RedSync {
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync 1, %0;" ::"n"(kRedThreads) : "memory");
+  }
+};
+
+// Sum of the ntiles partials of (dot d, column p) by threads 0..kRedThreads-1:
+// thread t adds tiles t + kRedThreads*(kRedLanes*i + l) into accumulator l,
+// the lanes are combined in order, then a shared-memory tree.  Returns the
+// value to every participating thread.
+template <typename Acc, typename PartT, typename Sync, bool COH = false>
 __device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, int p,
-                                  Acc* sh) {
+                                  Acc* sh, Sync sync) {
   const int t = threadIdx.x;
   const PartT* src = part + ((size_t)d * ld + p) * ntiles;
   Acc a[kRedLanes];
 #pragma unroll
   for (int l = 0; l < kRedLanes; ++l) a[l].zero();
-  const int stride = blockDim.x * kRedLanes;
+  const int stride = kRedThreads * kRedLanes;
   for (int base = t; base < ntiles; base += stride) {
 #pragma unroll
     for (int l = 0; l < kRedLanes; ++l) {
-      const int i = base + l * blockDim.x;
+      const int i = base + l * kRedThreads;
       if (i < ntiles) {
         Acc o;
-        get_part(src + i, o);
+        if constexpr (COH) {
+          const PartT t = __ldcg(src + i);
+          get_part(&t, o);
+        } else {
+          get_part(src + i, o);
+        }
         a[l].add(o);
       }
     }
@@ -571,17 +632,17 @@ __device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, 
 #pragma unroll
   for (int l = 1; l < kRedLanes; ++l) a[0].add(a[l]);
   sh[t] = a[0];
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+  sync();
+  for (int w = kRedThreads / 2; w > 0; w >>= 1) {
     if (t < w) {
       Acc x = sh[t];
       x.add(sh[t + w]);
       sh[t] = x;
     }
-    __syncthreads();
+    sync();
   }
   const double r = sh[0].value();
-  __syncthreads();
+  sync();
   return r;
 }
 
@@ -676,24 +737,18 @@ __device__ void scalar_norm(const ScalarJob& J, int p, const double* D) {
   if (S.edot) S.edot[p * m2 + j + 1] = ee;
 }
 
-template <typename Acc, typename PartT>
-__device__ void scalar_body(const ScalarBatch& B, int kind, Acc* sh) {
-  __shared__ int s_last;
-  const int gp = blockIdx.x;
-  const int d = blockIdx.y;
-  const int jb = find_probe_job(B, gp);
-  const ScalarJob& J = B.jobs[jb];
-  const int p = gp - B.probe_start[jb];
-  if (d >= J.ndots) return;
+// Dot d of probe p of a scalar job by threads 0..kRedThreads-1: reduce its
+// partials; the last of the probe's dots to arrive runs the recurrence.
+template <typename Acc, typename PartT, typename Sync, bool COH = false>
+__device__ void scalar_item(const ScalarJob& J, int kind, int p, int d, Acc* sh, Sync sync) {
   const KrylovState& S = J.st;
-  const double v = reduce_partials<Acc, PartT>(static_cast<const PartT*>(J.part), S.ld, J.ntiles,
-                                               d, p, sh);
+  const double v = reduce_partials<Acc, PartT, Sync, COH>(static_cast<const PartT*>(J.part), S.ld,
+                                                          J.ntiles, d, p, sh, sync);
   if (threadIdx.x == 0) {
     S.dbuf[d * S.ld + p] = v;
     __threadfence();
     const unsigned ticket = atomicAdd(S.cnt + p, 1u);
-    s_last = ticket == (unsigned)(J.ndots - 1);
-    if (s_last) {
+    if (ticket == (unsigned)(J.ndots - 1)) {
       S.cnt[p] = 0;
       __threadfence();
       double D[kMaxWin];
@@ -705,12 +760,160 @@ __device__ void scalar_body(const ScalarBatch& B, int kind, Acc* sh) {
   }
 }
 
+template <typename Acc, typename PartT>
+__device__ void scalar_body(const ScalarBatch& B, int kind, Acc* sh) {
+  const int gp = blockIdx.x;
+  const int d = blockIdx.y;
+  const int jb = find_probe_job(B, gp);
+  const ScalarJob& J = B.jobs[jb];
+  const int p = gp - B.probe_start[jb];
+  if (d >= J.ndots) return;
+  scalar_item<Acc, PartT>(J, kind, p, d, sh, CtaSync());
+}
+
 __global__ void __launch_bounds__(kRedThreads) k_scalar(const __grid_constant__ ScalarBatch B,
                                                         int kind, int f32) {
   __shared__ AccD shd[kRedThreads];
   __shared__ AccF shf[kRedThreads];
   if (f32) scalar_body<AccF, float2>(B, kind, shf);
   else scalar_body<AccD, double>(B, kind, shd);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent Krylov run (see krylov.cuh).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of the cooperative run: a counter and a generation
+// word.  Every wait is bounded (P.limit_ns of the global timer, 2^26 polls);
+// a CTA that gives up, or sees that another one did, sets / keeps P.err and
+// the whole CTA returns false, so every CTA leaves the kernel.
+template <typename T>
+__device__ bool run_barrier(const PersistRun<T>& P) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = P.bar + 1;
+    volatile int* err = P.err;
+    int ok = 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(P.bar, 1u) + 1u;
+    if (arrived == P.nwait) {
+      atomicExch(P.bar, 0u);
+      __threadfence();
+      atomicAdd(P.bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
+      while (*gen == g0) {
+        if (*err || ++polls > (1u << 26) ||
+            (long long)(global_ns() - t0) > P.limit_ns) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (!ok) atomicExch(P.err, 1);
+    __threadfence();
+    s_ok = ok && !*err;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T* run_ptr(const PersistRun<T>& P, int i) {
+  if (P.Vfull) return P.Vfull + (size_t)(i - 1) * P.blk;
+  if (i == 1) return P.X0;
+  return P.ring + (size_t)((i - 2) % P.nring) * P.blk;
+}
+
+template <typename T, int NDOT, int NB, bool EX>
+__global__ void __maxnreg__(128) k_krylov_run(const __grid_constant__ PersistRun<T> P) {
+  constexpr bool kF32 = !std::is_same<T, double>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ OneJob<SpmmJob<T>> sb;
+  __shared__ OneJob<UpdJob<T>> ub;
+  __shared__ ScalarJob scj;
+  __shared__ AccD shd[kRedThreads];
+  __shared__ AccF shf[kRedThreads];
+  const int ld = P.sj.ld;
+  for (int j = P.j0; j <= P.m; ++j) {
+    // the step's jobs, as KRun::spmm_jobs / upd_jobs / scalar_job build them
+    const int lo = P.method == 0 ? j : max(1, j - P.k + 1);
+    const int nd = P.method == 0 ? 1 : j - lo + 1;
+    if (threadIdx.x == 0) {
+      sb.njobs = 1;
+      sb.total_tiles = P.ntiles;
+      sb.tile_start[0] = 0;
+      sb.tile_start[1] = P.ntiles;
+      sb.jobs[0] = P.sj;
+      sb.jobs[0].x = run_ptr(P, j);
+      sb.jobs[0].ndots = nd;
+      if (P.method == 0) sb.jobs[0].dotv[0] = run_ptr(P, j);
+      else
+        for (int i = lo; i <= j; ++i) sb.jobs[0].dotv[i - lo] = run_ptr(P, i);
+      scj = P.cj;
+      scj.ntiles = P.ntiles;
+      scj.step = j;
+      scj.ndots = nd;
+      scj.win_lo = lo;
+      scj.last = j == P.m;
+    }
+    __syncthreads();
+    spmm_tiles<T, NDOT, OneJob<SpmmJob<T>>, true>(sb, blockIdx.x, gridDim.x, smem_raw);
+    if (!run_barrier(P)) return;
+    if (threadIdx.x < kRedThreads) {
+      for (int it = blockIdx.x; it < ld * nd; it += gridDim.x) {
+        const int p = it / nd, d = it - p * nd;
+        if (kF32) scalar_item<AccF, float2, RedSync, true>(scj, SK_COEF, p, d, shf, RedSync());
+        else scalar_item<AccD, double, RedSync, true>(scj, SK_COEF, p, d, shd, RedSync());
+      }
+    }
+    if (!run_barrier(P)) return;
+    if (j >= P.m) break;
+    const int nd2 = P.track_e ? 2 : 1;
+    if (threadIdx.x == 0) {
+      ub.njobs = 1;
+      ub.total_tiles = P.ntiles;
+      ub.tile_start[0] = 0;
+      ub.tile_start[1] = P.ntiles;
+      ub.jobs[0] = P.uj;
+      UpdJob<T>& U = ub.jobs[0];
+      if (P.method == 0) {
+        if (j >= 2) {
+          U.nbasis = 2;
+          U.basis[0] = run_ptr(P, j - 1);
+          U.basis[1] = run_ptr(P, j);
+        } else {
+          U.nbasis = 1;
+          U.basis[0] = run_ptr(P, j);
+        }
+      } else {
+        U.nbasis = j - lo + 1;
+        for (int i = lo; i <= j; ++i) U.basis[i - lo] = run_ptr(P, i);
+      }
+      U.out = run_ptr(P, j + 1);
+      scj.ndots = nd2;
+    }
+    __syncthreads();
+    update_tiles<T, NB, EX, OneJob<UpdJob<T>>, true>(ub, blockIdx.x, gridDim.x, smem_raw);
+    if (!run_barrier(P)) return;
+    if (threadIdx.x < kRedThreads) {
+      for (int it = blockIdx.x; it < ld * nd2; it += gridDim.x) {
+        const int p = it / nd2, d = it - p * nd2;
+        if (kF32) scalar_item<AccF, float2, RedSync, true>(scj, SK_NORM, p, d, shf, RedSync());
+        else scalar_item<AccD, double, RedSync, true>(scj, SK_NORM, p, d, shd, RedSync());
+      }
+    }
+    if (!run_barrier(P)) return;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -805,6 +1008,63 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
+
+// Test hook: LOGDET_TEST_KRUN_STALL=1 makes every barrier of a persistent run
+// wait for one arrival more than the grid has, with a 20 ms bound, so that
+// every wait runs out (the error path, exercised without a fault).
+static bool krun_stall_test() {
+  const char* e = std::getenv("LOGDET_TEST_KRUN_STALL");
+  return e && e[0] == '1';
+}
+
+template <typename T>
+int launch_krylov_run(const PersistRun<T>& P0, int threads, int nd_max, int nb_max,
+                      cudaStream_t s) {
+  using Acc = typename AccOf<T>::type;
+  PersistRun<T> P = P0;
+  const size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
+  auto cls = [](int w) { return w <= 1 ? 1 : w == 2 ? 2 : w <= 4 ? 4 : kMaxWin; };
+  const int cd = cls(nd_max), cb = cls(nb_max);
+  void* kern = nullptr;
+#define LD_KRUN(ND, NB, EX)                                                     \
+  if (cd == ND && cb == NB && (P.track_e != 0) == EX)                         \
+    kern = reinterpret_cast<void*>(k_krylov_run<T, ND, NB, EX>);
+  LD_KRUN(1, 2, false)
+  LD_KRUN(1, 1, false) LD_KRUN(1, 1, true)
+  LD_KRUN(2, 2, false) LD_KRUN(2, 2, true)
+  LD_KRUN(4, 4, false) LD_KRUN(4, 4, true)
+  LD_KRUN(kMaxWin, kMaxWin, false) LD_KRUN(kMaxWin, kMaxWin, true)
+#undef LD_KRUN
+  if (!kern || threads < kRedThreads || threads > 512) {
+    set_error("no persistent Krylov kernel for %d dots / %d basis vectors at %d threads", nd_max,
+              nb_max, threads);
+    return LOGDET_EINVAL;
+  }
+  int per_sm = 0;
+  LD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  if (per_sm < 1) {
+    set_error("persistent Krylov kernel does not fit an SM at %d threads", threads);
+    return LOGDET_ECUDA;
+  }
+  const int work = std::max(P.ntiles, P.sj.ld * std::max(nd_max, 2));
+  const int grid = std::max(1, std::min(work, per_sm * sm_count()));
+  const bool stall = krun_stall_test();
+  P.nwait = (unsigned)grid + (stall ? 1u : 0u);
+  P.limit_ns = stall ? 20000000LL : 2000000000LL;
+  LD_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), s));
+  ProfScope prof(KC_KRUN, s);
+  void* args[] = {&P};
+  cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("persistent Krylov launch failed: %s", cudaGetErrorString(e));
+    return LOGDET_ECUDA;
+  }
+  return LOGDET_OK;
+}
+
+template int launch_krylov_run<double>(const PersistRun<double>&, int, int, int, cudaStream_t);
+template int launch_krylov_run<float>(const PersistRun<float>&, int, int, int, cudaStream_t);
 
 static int total_probes(const ScalarBatch& b) { return b.probe_start[b.njobs]; }
 

@@ -29,6 +29,7 @@ namespace ld {
 constexpr int kMaxWin = 9;    // window vectors per pass (window k <= 8, plus slack)
 constexpr int kMaxJobs = 24;  // jobs per batched launch
 constexpr int kSplitRowNnz = 64;  // rows longer than this are split across a whole CTA
+constexpr int kRedThreads = 256;  // threads of one scalar reduction (a k_scalar CTA)
 
 // ---------------------------------------------------------------------------
 // pass 1: SpMM with fused window dots
@@ -141,6 +142,44 @@ struct ScalarBatch {
   int probe_start[kMaxJobs + 1];
   ScalarJob jobs[kMaxJobs];
 };
+
+// ---------------------------------------------------------------------------
+// persistent Krylov run: every remaining step of one run (pass 1, scalar
+// coefficients, pass 2, scalar norms) in one cooperative launch, for blocks
+// small enough that launch gaps, not the passes, set the step time.  The
+// passes and scalar steps run the same device code as the step kernels, in
+// the same CTA size and tile geometry, so results are bit-identical to the
+// step-by-step path.
+// ---------------------------------------------------------------------------
+template <typename Job>
+struct OneJob {  // a batch of one job (the members the tile loops read)
+  int njobs, total_tiles;
+  int tile_start[2];
+  Job jobs[1];
+};
+
+template <typename T>
+struct PersistRun {
+  SpmmJob<T> sj;   // pass-1 job: fields that do not change with the step
+  UpdJob<T> uj;    // pass-2 job: the same
+  ScalarJob cj;    // scalar jobs: st, part, part_f32
+  T* X0;           // u_1
+  T* ring;         // ring of nring blocks for u_2, u_3, ... (no Vfull)
+  T* Vfull;        // or the full basis, u_j at Vfull + (j-1) blk
+  size_t blk;      // n * ld
+  int nring, method, k, m, j0, track_e, ntiles;
+  unsigned* bar;   // [2]: arrivals and generation of the grid barrier (zero at launch)
+  int* err;        // set to 1 when a barrier wait gives up
+  unsigned nwait;  // arrivals that complete a barrier (the grid size)
+  long long limit_ns;  // bound of one barrier wait (global timer)
+};
+
+// Cooperative launch of the run (CTA size threads; nd_max / nb_max: the
+// most window dots / basis vectors a step of it takes).  LOGDET_ECUDA when
+// the launch is refused.
+template <typename T>
+int launch_krylov_run(const PersistRun<T>& P, int threads, int nd_max, int nb_max,
+                      cudaStream_t s);
 
 // Tile geometry for a block of leading dimension ld with elements of
 // `vec` entries per 16-byte load: threads per CTA and rows per tile.

@@ -17,7 +17,8 @@ enum KClass {
   KC_SMALL = 5,   // tridiagonal Gauss rules, Hessenberg logarithms
   KC_OTHER = 6,   // probe fill, conversions, sketch assembly, Gershgorin, scaling
   KC_GRID = 7,    // gridded-operator application (the pass-1 SpMM of a grid handle)
-  KC_COUNT = 8
+  KC_KRUN = 8,    // persistent Krylov run: every step of a small run in one launch
+  KC_COUNT = 9
 };
 
 void prof_count();  // one kernel launch

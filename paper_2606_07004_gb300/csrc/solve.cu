@@ -6,6 +6,7 @@
 #include "tune.cuh"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 namespace ld {
@@ -340,6 +341,62 @@ ScalarJob KRun<T>::scalar_job(int j, int ndots, bool spmm_pass) const {
   sj.win_lo = j >= 1 ? win_lo(j) : 1;
   sj.last = j == m;
   return sj;
+}
+
+template <typename T>
+bool KRun<T>::persistent_ok() const {
+  if constexpr (std::is_same<T, bf16>::value) {
+    return false;
+  } else {
+    const char* e = std::getenv("LOGDET_KRYLOV_PERSISTENT");
+    if (e && e[0] == '0') return false;
+    if (sweep || items || (hctx && hctx->kind == 1) || tune.split != 1 || nslots != ntiles)
+      return false;
+    // the scalar steps run on the first kRedThreads threads of each CTA
+    if (g.threads < kRedThreads || g.threads > 512) return false;
+    return finished() ? false : blk * sizeof(T) <= kPersistMaxBlock;
+  }
+}
+
+template <typename T>
+int KRun<T>::issue_rest_persistent() {
+  if constexpr (std::is_same<T, bf16>::value) {
+    return LOGDET_EINVAL;
+  } else {
+    const int j = next_step();
+    PersistRun<T> P;
+    memset(&P, 0, sizeof P);
+    std::vector<SpmmJob<T>> sj;
+    std::vector<UpdJob<T>> uj;
+    LD_TRY(spmm_jobs(j, sj));
+    upd_jobs(j, uj);
+    P.sj = sj[0];
+    P.uj = uj[0];
+    P.cj = scalar_job(j, 1, true);
+    P.X0 = X0;
+    P.ring = ring.p;
+    P.Vfull = Vfull;
+    P.blk = blk;
+    P.nring = nring;
+    P.method = method;
+    P.k = k;
+    P.m = m;
+    P.j0 = j;
+    P.track_e = track_e ? 1 : 0;
+    P.ntiles = ntiles;
+    if (!krun_bar.p) LD_TRY(krun_bar.alloc(2));
+    if (!dia_err.p) {
+      LD_TRY(dia_err.alloc(1));
+      LD_TRY(dia_err.zero());
+    }
+    P.bar = krun_bar.p;
+    P.err = dia_err.p;
+    const int nd_max = method == 0 ? 1 : std::min(k, m);
+    const int nb_max = method == 0 ? 2 : std::min(k, m);
+    LD_TRY(launch_krylov_run<T>(P, g.threads, nd_max, nb_max, st));
+    done_steps = m;
+    return LOGDET_OK;
+  }
 }
 
 template struct KRun<double>;
@@ -861,10 +918,23 @@ struct Solve : ISolve {
     if (run->finished()) ph = (c.method == 1 && ph == PH_K1) ? PH_MID : PH_FINISH;
   }
 
+  int issue_krylov_rest() override {
+    if (!run || !run->persistent_ok()) return 1;
+    NvtxRange nv("logdet persistent krylov run");
+    const int rc = run->issue_rest_persistent();
+    if (rc) {
+      ph = PH_FAILED;
+      return rc;
+    }
+    ph = (c.method == 1 && ph == PH_K1) ? PH_MID : PH_FINISH;
+    return LOGDET_OK;
+  }
+
   int assemble(SolveOut& o) override {
     memset(&o.res, 0, sizeof o.res);
     if (h_err && (h_err[0] || h_err[1])) {
-      set_error("a staged copy of the diagonal SpMM path did not complete in time");
+      set_error("a bounded device wait gave up (a staged copy of the diagonal SpMM path, or "
+                "a grid barrier of the persistent Krylov run)");
       return LOGDET_ETIMEOUT;
     }
     uint32_t status = 0;
@@ -1013,6 +1083,12 @@ int issue_solve(ISolve* sv, cudaStream_t st) {
       rc = sv->run_phase();
       if (rc) return rc;
       continue;
+    }
+    {
+      // Small runs: every remaining step in one persistent launch.
+      const int pr = sv->issue_krylov_rest();
+      if (pr < 0) return pr;
+      if (pr == 0) continue;
     }
     NvtxRange nv("logdet krylov step");
     const int th = sv->krylov_threads();

@@ -103,7 +103,7 @@ struct KRun {
   int done_steps = 0;  // steps whose pass 1 has been issued
   cudaStream_t st;
 
-  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), dia_err(s), st(s) {}
+  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), dia_err(s), st(s), krun_bar(s) {}
 
   // Allocate and queue the start-block norms and sigma_1 (one launch pair).
   int init(const int* rp, const int* ci, const typename ValOf<T>::type* v, int n_, long long nnz_,
@@ -125,7 +125,18 @@ struct KRun {
   int slice_live(int q) const;
   // Scalar job over pass-1 partials (spmm_pass) or pass-2 / norm partials.
   ScalarJob scalar_job(int j, int ndots, bool spmm_pass = false) const;
+  // Persistent run: whether the remaining steps qualify (uniform CSR tiles,
+  // one column slice, FP64 or FP32 blocks of at most kPersistMaxBlock bytes,
+  // LOGDET_KRYLOV_PERSISTENT not 0), and the launch that issues them all.
+  bool persistent_ok() const;
+  int issue_rest_persistent();
+  DevBuf<unsigned> krun_bar;
 };
+
+// Blocks up to this size (bytes of one n x ld block) run their Krylov steps
+// as one persistent launch in the blocking and graph-plan paths: below it
+// the launch gaps of four kernels per step outweigh the passes.
+constexpr size_t kPersistMaxBlock = (size_t)16 << 20;
 
 // Batched launches of jobs that share element type and CTA size.
 template <typename T>
@@ -152,6 +163,10 @@ struct ISolve {
   virtual int add_pass1(void* spmm_vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) = 0;
   virtual bool add_pass2(void* upd_vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) = 0;
   virtual void step_issued() = 0;
+  // Issue every remaining step of the current Krylov phase as one persistent
+  // launch: LOGDET_OK when issued, 1 when the run does not qualify (step by
+  // step then), a negative code on error.
+  virtual int issue_krylov_rest() = 0;
   // After FINISH's copies completed: assemble the host result.
   virtual int assemble(SolveOut& o) = 0;
   virtual cudaEvent_t done_event() const = 0;
