@@ -346,11 +346,13 @@ def reference_arm(args):
 # CUDA arm
 # ---------------------------------------------------------------------------
 def spmm_kernel_digest():
-    """SHA-256 of the CSR SpMM kernel's source: krylov.cu from its launch-bound
-    helper through the kernel's closing brace, then krylov.cuh and common.cuh
-    (the headers it includes).  Edits elsewhere in krylov.cu leave it alone."""
+    """SHA-256 of the CSR SpMM kernel's source: krylov.cu from its gather
+    batch constant (the vector-load helper, the launch-bound helper and the
+    tile loop follow) through the kernel's closing brace, then krylov.cuh and
+    common.cuh (the headers it includes).  Edits elsewhere in krylov.cu leave
+    it alone."""
     text = open(KRYLOV_SRC).read()
-    i0 = text.index("constexpr int fp64_wide_min_ctas()")
+    i0 = text.index("constexpr int kGather = 4;")
     i1 = text.index("k_spmm(const __grid_constant__ SpmmBatch<T> B) {", i0)
     depth, j = 0, text.index("{", i1)
     while True:
@@ -867,10 +869,11 @@ def small2d_case(args):
     """Latency-bound workload: 2D 5-point Dirichlet Laplacian 64^2 + 0.1 I
     (n = 4096, nnz = 20,224; the whole working set sits in L2), OSLQ m = 30
     with 30 probes, FP64, one seed per solve.  Three ways to run the same
-    solves: the blocking call (the Krylov phase as one persistent launch;
-    also timed step by step, about 135 launches issued from the host per
-    solve), a graph plan (the solve captured once, one graph launch per seed;
-    bit-identical results) and the batched server (many solves per launch).
+    solves: the blocking call (about 135 launches issued from the host per
+    solve; also timed with the Krylov phase as one persistent launch, 18
+    launches), a graph plan (the solve captured once, one graph launch per
+    seed; bit-identical results) and the batched server (many solves per
+    launch).
     Reports solves/s and per-solve latency of each."""
     import numpy as np
     import torch
@@ -894,9 +897,9 @@ def small2d_case(args):
             lat_b.append((time.perf_counter() - t1) * 1e3)
         t_b = time.perf_counter() - t0
         launches_b = (B.logdet_launch_count() - c0) / N
-        # the same blocking solves with the Krylov phase issued step by step
-        # (four launches per step) instead of one persistent launch
-        os.environ["LOGDET_KRYLOV_PERSISTENT"] = "0"
+        # the same blocking solves with the Krylov phase as one persistent
+        # launch (opt-in) instead of four launches per step
+        os.environ["LOGDET_KRYLOV_PERSISTENT"] = "1"
         h.oslq(P, m, seed=0)
         c0 = B.logdet_launch_count()
         t0 = time.perf_counter()
@@ -950,12 +953,13 @@ def small2d_case(args):
         "workload": "2D Laplacian 64^2 + 0.1 I (n=4096, nnz=%d), OSLQ m=30, 30 probes, FP64" % A.nnz,
         "metric": METRIC, "unit": UNIT, "dtype": "f64",
         "blocking": {"value": N / t_b, "latency_ms": {"p50": _pct(lat_b, 0.5), "p99": _pct(lat_b, 0.99)},
-                     "launches_per_solve": launches_b,
-                     "krylov": "one persistent launch per Krylov phase"},
-        "blocking_step_by_step": {"value": N / t_s_b,
-                                  "latency_ms": {"p50": _pct(lat_s, 0.5), "p99": _pct(lat_s, 0.99)},
-                                  "launches_per_solve": launches_s,
-                                  "bitwise_equal_to_persistent": same_steps},
+                     "launches_per_solve": launches_b, "krylov": "four launches per step"},
+        "blocking_persistent": {"value": N / t_s_b,
+                                "latency_ms": {"p50": _pct(lat_s, 0.5), "p99": _pct(lat_s, 0.99)},
+                                "launches_per_solve": launches_s,
+                                "krylov": "one persistent launch per Krylov phase "
+                                          "(LOGDET_KRYLOV_PERSISTENT=1)",
+                                "bitwise_equal_to_step_path": same_steps},
         "graph_plan": {"value": N / t_p, "latency_ms": {"p50": _pct(lat_p, 0.5), "p99": _pct(lat_p, 0.99)},
                        "kernels_per_replay": kernels, "capture_s": t_plan_make,
                        "bitwise_equal_to_blocking": same},

@@ -399,7 +399,7 @@ __device__ __forceinline__ void update_tiles(const Batch& B, int gt0, int stride
       bool unit = true;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        double a = COH ? __ldcg(J.ycoef + col0 + v) : J.ycoef[col0 + v];
+        double a = J.ycoef[col0 + v];
         yc[v] = CT(a);
         unit = unit && (a == 1.0);
       }
@@ -407,9 +407,7 @@ __device__ __forceinline__ void update_tiles(const Batch& B, int gt0, int stride
       for (int i = 0; i < NB; ++i)
 #pragma unroll
         for (int v = 0; v < V; ++v)
-          cf[i][v] = (i < nb) ? CT(COH ? __ldcg(J.coef + i * J.ld + col0 + v)
-                                       : J.coef[i * J.ld + col0 + v])
-                              : CT(0);
+          cf[i][v] = (i < nb) ? CT(J.coef[i * J.ld + col0 + v]) : CT(0);
 
       // FP64: scale y in place where ycoef != 1 (rows and chunk of this
       // thread only), then read y through L2 so the loop sees those stores.
@@ -588,25 +586,12 @@ __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
 constexpr int kRedLanes = 4;  // independent accumulators per thread
 
 
-// CTA barriers of the scalar reduction: the whole CTA (k_scalar), or the
-// first kRedThreads threads of a larger CTA (named barrier 1; the persistent
-// Krylov run).
-struct CtaSync {
-  __device__ __forceinline__ void operator()() const { __syncthreads(); }
-};
-struct RedSync {
-  __device__ __forceinline__ void operator()() const {
-    asm volatile("bar.sync 1, %0;" ::"n"(kRedThreads) : "memory");
-  }
-};
-
-// Sum of the ntiles partials of (dot d, column p) by threads 0..kRedThreads-1:
-// thread t adds tiles t + kRedThreads*(kRedLanes*i + l) into accumulator l,
-// the lanes are combined in order, then a shared-memory tree.  Returns the
-// value to every participating thread.
-template <typename Acc, typename PartT, typename Sync, bool COH = false>
-__device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, int p,
-                                  Acc* sh, Sync sync) {
+// Sum of the ntiles partials of (dot d, column p) by a CTA of kRedThreads
+// threads: thread t adds tiles t + kRedThreads*(kRedLanes*i + l) into
+// accumulator l, the lanes are combined in order, then a shared-memory tree.
+// Returns the value to every thread.
+template <typename Acc, typename PartT>
+__device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, int p, Acc* sh) {
   const int t = threadIdx.x;
   const PartT* src = part + ((size_t)d * ld + p) * ntiles;
   Acc a[kRedLanes];
@@ -619,12 +604,7 @@ __device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, 
       const int i = base + l * kRedThreads;
       if (i < ntiles) {
         Acc o;
-        if constexpr (COH) {
-          const PartT t = __ldcg(src + i);
-          get_part(&t, o);
-        } else {
-          get_part(src + i, o);
-        }
+        get_part(src + i, o);
         a[l].add(o);
       }
     }
@@ -632,17 +612,17 @@ __device__ double reduce_partials(const PartT* part, int ld, int ntiles, int d, 
 #pragma unroll
   for (int l = 1; l < kRedLanes; ++l) a[0].add(a[l]);
   sh[t] = a[0];
-  sync();
+  __syncthreads();
   for (int w = kRedThreads / 2; w > 0; w >>= 1) {
     if (t < w) {
       Acc x = sh[t];
       x.add(sh[t + w]);
       sh[t] = x;
     }
-    sync();
+    __syncthreads();
   }
   const double r = sh[0].value();
-  sync();
+  __syncthreads();
   return r;
 }
 
@@ -653,7 +633,12 @@ __device__ __forceinline__ int find_probe_job(const ScalarBatch& B, int gp) {
 }
 
 // Power-of-two factor keeping the stored vectors near unit norm when sigma drifts.
+// Sigma within 2^+-(lim - 1) is well inside the limit whatever log2 rounds
+// to, so the answer 1 needs no FP64 logarithm there.
 __device__ __forceinline__ double rescale_factor(double sigma, double lim) {
+  const long long e = (long long)lim - 1;  // 2^+-e built from its bits (1 <= e <= 1000)
+  const double lo = __longlong_as_double((1023 - e) << 52), hi = __longlong_as_double((1023 + e) << 52);
+  if (sigma >= lo && sigma <= hi) return 1.0;
   double l2 = log2(sigma);
   if (fabs(l2) <= lim) return 1.0;
   return exp2(rint(l2));
@@ -737,13 +722,13 @@ __device__ void scalar_norm(const ScalarJob& J, int p, const double* D) {
   if (S.edot) S.edot[p * m2 + j + 1] = ee;
 }
 
-// Dot d of probe p of a scalar job by threads 0..kRedThreads-1: reduce its
-// partials; the last of the probe's dots to arrive runs the recurrence.
-template <typename Acc, typename PartT, typename Sync, bool COH = false>
-__device__ void scalar_item(const ScalarJob& J, int kind, int p, int d, Acc* sh, Sync sync) {
+// Dot d of probe p of a scalar job by one CTA: reduce its partials; the last
+// of the probe's dots to arrive runs the recurrence.
+template <typename Acc, typename PartT>
+__device__ void scalar_item(const ScalarJob& J, int kind, int p, int d, Acc* sh) {
   const KrylovState& S = J.st;
-  const double v = reduce_partials<Acc, PartT, Sync, COH>(static_cast<const PartT*>(J.part), S.ld,
-                                                          J.ntiles, d, p, sh, sync);
+  const double v = reduce_partials<Acc, PartT>(static_cast<const PartT*>(J.part), S.ld, J.ntiles,
+                                               d, p, sh);
   if (threadIdx.x == 0) {
     S.dbuf[d * S.ld + p] = v;
     __threadfence();
@@ -768,7 +753,7 @@ __device__ void scalar_body(const ScalarBatch& B, int kind, Acc* sh) {
   const ScalarJob& J = B.jobs[jb];
   const int p = gp - B.probe_start[jb];
   if (d >= J.ndots) return;
-  scalar_item<Acc, PartT>(J, kind, p, d, sh, CtaSync());
+  scalar_item<Acc, PartT>(J, kind, p, d, sh);
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_scalar(const __grid_constant__ ScalarBatch B,
@@ -834,57 +819,232 @@ __device__ __forceinline__ T* run_ptr(const PersistRun<T>& P, int i) {
   return P.ring + (size_t)((i - 2) % P.nring) * P.blk;
 }
 
+// One warp's copy of reduce_partials for (dot d, column p): lane L stands in
+// for the reduction threads L, L + 32, ..., L + 224, each accumulating the
+// same tiles into the same lanes, then the same tree (the first three levels
+// within a lane, the last five by shuffles), so the value is bit-identical
+// to the 256-thread reduction of k_scalar.  Partials are read through L2.
+template <typename Acc>
+__device__ __forceinline__ Acc shfl_down_acc(const Acc& a, int w);
+template <>
+__device__ __forceinline__ AccD shfl_down_acc<AccD>(const AccD& a, int w) {
+  AccD o;
+  o.s = __shfl_down_sync(0xffffffffu, a.s, w);
+  return o;
+}
+template <>
+__device__ __forceinline__ AccF shfl_down_acc<AccF>(const AccF& a, int w) {
+  AccF o;
+  o.s = __shfl_down_sync(0xffffffffu, a.s, w);
+  o.e = __shfl_down_sync(0xffffffffu, a.e, w);
+  return o;
+}
+
+template <typename Acc, typename PartT>
+__device__ double warp_reduce_partials(const PartT* part, int ld, int ntiles, int d, int p) {
+  static_assert(kRedThreads == 256, "the warp copy stands in for 8 threads per lane");
+  const int L = threadIdx.x & 31;
+  const PartT* src = part + ((size_t)d * ld + p) * ntiles;
+  // Slots (reduction threads) that hold data: the others stay +0, and the
+  // additions of +0 that the 256-thread tree makes leave a value unchanged
+  // (accumulators start at +0 and never become -0), so they are skipped.
+  int nz = min(ntiles, kRedThreads);
+  Acc v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int t = L + 32 * k;
+    Acc a[kRedLanes];
+#pragma unroll
+    for (int l = 0; l < kRedLanes; ++l) a[l].zero();
+    if (t < nz) {
+      for (int base = t; base < ntiles; base += kRedThreads * kRedLanes) {
+#pragma unroll
+        for (int l = 0; l < kRedLanes; ++l) {
+          const int i = base + l * kRedThreads;
+          if (i < ntiles) {
+            const PartT x = __ldcg(src + i);
+            Acc o;
+            get_part(&x, o);
+            a[l].add(o);
+          }
+        }
+      }
+#pragma unroll
+      for (int l = 1; l < kRedLanes; ++l) a[0].add(a[l]);
+    }
+    v[k] = a[0];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k)                       // w = 128
+    if (L + 32 * k + 128 < nz) v[k].add(v[k + 4]);
+  nz = min(nz, 128);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)                       // w = 64
+    if (L + 32 * k + 64 < nz) v[k].add(v[k + 2]);
+  nz = min(nz, 64);
+  if (L + 32 < nz) v[0].add(v[1]);                  // w = 32
+  nz = min(nz, 32);
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {               // w = 16 .. 1
+    const Acc o = shfl_down_acc(v[0], w);
+    if (L + w < nz) v[0].add(o);                    // (implies L < w: nz <= 2w here)
+    nz = min(nz, w);
+  }
+  return __shfl_sync(0xffffffffu, v[0].value(), 0);
+}
+
+// Shared-memory state of a persistent run: every CTA keeps the per-probe
+// scalars the recurrences read (recent sigmas, the last beta, the active
+// flags) and the pass-2 coefficients, and runs the recurrences itself, so a
+// step needs two grid barriers (after each pass) instead of four.
+constexpr int kRunMaxLd = 128;         // ld <= 2 * kMaxSketch
+constexpr int kSgRing = kMaxWin + 3;   // sigma_{j-k+1} .. sigma_{j+1}
+
+struct RunShared {
+  double sg[kRunMaxLd][kSgRing];
+  double cf[kMaxWin * kRunMaxLd];      // pass-2 coefficients, [t][ld] as in KrylovState::coef
+  double yc[kRunMaxLd];
+  double D[kMaxWin][kRunMaxLd];
+  double beta_prev[kRunMaxLd];
+  int act[kRunMaxLd];
+};
+
+// The coefficient step of probe p (the expressions of scalar_coef, with the
+// sigmas and beta from shared memory); CTA 0 also writes the history.
+__device__ __forceinline__ void run_coef(const KrylovState& S, RunShared& R, int p, int j, int lo,
+                                         int nd, bool writer) {
+  const int ld = S.ld;
+  if (!R.act[p]) {
+    R.yc[p] = 0.0;
+    for (int t = 0; t < kMaxWin; ++t) R.cf[t * ld + p] = 0.0;
+    return;
+  }
+  if (writer) S.meff[p] = j;
+  const double* sg = R.sg[p];
+  const double sj = sg[j % kSgRing];
+  const double a = rescale_factor(sj, S.rescale_lim);
+  if (S.method == 0) {
+    const double al = sj * sj * R.D[0][p];
+    if (writer) S.alpha[p * S.m + j - 1] = al;
+    if (j >= 2) {
+      R.cf[0 * ld + p] = a * R.beta_prev[p] * sg[(j - 1) % kSgRing] / sj;
+      R.cf[1 * ld + p] = a * al;
+    } else {
+      R.cf[0 * ld + p] = a * al;
+    }
+  } else {
+    double* Hc = S.H + (size_t)p * (S.m + 1) * S.m + (size_t)(j - 1) * (S.m + 1);
+    for (int t = 0; t < nd; ++t) {
+      const int i = lo + t;
+      const double si = sg[i % kSgRing];
+      if (writer) Hc[i - 1] = si * sj * R.D[t][p];
+      R.cf[t * ld + p] = a * si * si * R.D[t][p];
+    }
+  }
+  R.yc[p] = a;
+}
+
+// The norm step of probe p (the expressions of scalar_norm).
+__device__ __forceinline__ void run_norm(const KrylovState& S, RunShared& R, int p, int j, int nd2,
+                                         bool writer) {
+  if (!R.act[p]) return;
+  const double nn = R.D[0][p];
+  const double ee = nd2 > 1 ? R.D[1][p] : 0.0;
+  const int m2 = S.m + 2;
+  const double a = R.yc[p];
+  const double sgj = R.sg[p][j % kSgRing];
+  const double h = sgj * sqrt(nn) / a;
+  bool stop;
+  if (S.method == 0) {
+    R.beta_prev[p] = h;
+    if (writer) S.beta[p * S.m + j - 1] = h;
+    stop = !(h > S.tol);
+  } else {
+    if (writer) S.H[(size_t)p * (S.m + 1) * S.m + (size_t)(j - 1) * (S.m + 1) + j] = h;
+    stop = h < S.tol;
+  }
+  double next;
+  if (stop) {
+    R.act[p] = 0;
+    if (writer) {
+      S.active[p] = 0;
+      S.status[p] |= LOGDET_ST_BREAKDOWN;
+    }
+    next = 0.0;
+  } else {
+    next = sgj / (a * h);
+  }
+  R.sg[p][(j + 1) % kSgRing] = next;
+  if (writer) {
+    S.sig[p * m2 + j + 1] = next;
+    if (S.edot) S.edot[p * m2 + j + 1] = ee;
+  }
+}
+
 template <typename T, int NDOT, int NB, bool EX>
 __global__ void __maxnreg__(128) k_krylov_run(const __grid_constant__ PersistRun<T> P) {
-  constexpr bool kF32 = !std::is_same<T, double>::value;
+  using Acc = typename AccOf<T>::type;
+  using PartT = typename PartOf<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ OneJob<SpmmJob<T>> sb;
   __shared__ OneJob<UpdJob<T>> ub;
-  __shared__ ScalarJob scj;
-  __shared__ AccD shd[kRedThreads];
-  __shared__ AccF shf[kRedThreads];
-  const int ld = P.sj.ld;
+  __shared__ RunShared R;
+  const KrylovState& S = P.cj.st;
+  const int ld = S.ld;
+  const int m2 = S.m + 2;
+  const bool writer = blockIdx.x == 0;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // start state (written by the kernels before this launch)
+  for (int p = threadIdx.x; p < ld; p += blockDim.x) {
+    R.sg[p][P.j0 % kSgRing] = __ldcg(S.sig + p * m2 + P.j0);
+    R.act[p] = __ldcg(S.active + p);
+    R.beta_prev[p] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    sb.njobs = 1;
+    sb.total_tiles = P.ntiles;
+    sb.tile_start[0] = 0;
+    sb.tile_start[1] = P.ntiles;
+    sb.jobs[0] = P.sj;
+    ub.njobs = 1;
+    ub.total_tiles = P.ntiles;
+    ub.tile_start[0] = 0;
+    ub.tile_start[1] = P.ntiles;
+    ub.jobs[0] = P.uj;
+    ub.jobs[0].coef = R.cf;   // this CTA's copy of the coefficients
+    ub.jobs[0].ycoef = R.yc;
+  }
+  // Pass-1 and pass-2 partials live in separate buffers: with no barrier
+  // after the reductions, a CTA may start the next pass while another one
+  // still reads the previous pass's partials.
+  const PartT* part = static_cast<const PartT*>(P.cj.part);
+  const PartT* part2 = P.uj.part;
   for (int j = P.j0; j <= P.m; ++j) {
-    // the step's jobs, as KRun::spmm_jobs / upd_jobs / scalar_job build them
+    // the step's jobs, as KRun::spmm_jobs / upd_jobs build them
     const int lo = P.method == 0 ? j : max(1, j - P.k + 1);
     const int nd = P.method == 0 ? 1 : j - lo + 1;
     if (threadIdx.x == 0) {
-      sb.njobs = 1;
-      sb.total_tiles = P.ntiles;
-      sb.tile_start[0] = 0;
-      sb.tile_start[1] = P.ntiles;
-      sb.jobs[0] = P.sj;
-      sb.jobs[0].x = run_ptr(P, j);
-      sb.jobs[0].ndots = nd;
-      if (P.method == 0) sb.jobs[0].dotv[0] = run_ptr(P, j);
+      SpmmJob<T>& J = sb.jobs[0];
+      J.x = run_ptr(P, j);
+      J.ndots = nd;
+      if (P.method == 0) J.dotv[0] = run_ptr(P, j);
       else
-        for (int i = lo; i <= j; ++i) sb.jobs[0].dotv[i - lo] = run_ptr(P, i);
-      scj = P.cj;
-      scj.ntiles = P.ntiles;
-      scj.step = j;
-      scj.ndots = nd;
-      scj.win_lo = lo;
-      scj.last = j == P.m;
+        for (int i = lo; i <= j; ++i) J.dotv[i - lo] = run_ptr(P, i);
     }
     __syncthreads();
     spmm_tiles<T, NDOT, OneJob<SpmmJob<T>>, true>(sb, blockIdx.x, gridDim.x, smem_raw);
     if (!run_barrier(P)) return;
-    if (threadIdx.x < kRedThreads) {
-      for (int it = blockIdx.x; it < ld * nd; it += gridDim.x) {
-        const int p = it / nd, d = it - p * nd;
-        if (kF32) scalar_item<AccF, float2, RedSync, true>(scj, SK_COEF, p, d, shf, RedSync());
-        else scalar_item<AccD, double, RedSync, true>(scj, SK_COEF, p, d, shd, RedSync());
-      }
+    // coefficients: every CTA reduces all dots and runs every recurrence
+    for (int it = warp; it < ld * nd; it += nwarps) {
+      const int p = it / nd, d = it - p * nd;
+      const double v = warp_reduce_partials<Acc, PartT>(part, ld, P.ntiles, d, p);
+      if ((threadIdx.x & 31) == 0) R.D[d][p] = v;
     }
-    if (!run_barrier(P)) return;
+    __syncthreads();
+    for (int p = threadIdx.x; p < ld; p += blockDim.x) run_coef(S, R, p, j, lo, nd, writer);
+    __syncthreads();
     if (j >= P.m) break;
-    const int nd2 = P.track_e ? 2 : 1;
     if (threadIdx.x == 0) {
-      ub.njobs = 1;
-      ub.total_tiles = P.ntiles;
-      ub.tile_start[0] = 0;
-      ub.tile_start[1] = P.ntiles;
-      ub.jobs[0] = P.uj;
       UpdJob<T>& U = ub.jobs[0];
       if (P.method == 0) {
         if (j >= 2) {
@@ -900,19 +1060,19 @@ __global__ void __maxnreg__(128) k_krylov_run(const __grid_constant__ PersistRun
         for (int i = lo; i <= j; ++i) U.basis[i - lo] = run_ptr(P, i);
       }
       U.out = run_ptr(P, j + 1);
-      scj.ndots = nd2;
     }
     __syncthreads();
     update_tiles<T, NB, EX, OneJob<UpdJob<T>>, true>(ub, blockIdx.x, gridDim.x, smem_raw);
     if (!run_barrier(P)) return;
-    if (threadIdx.x < kRedThreads) {
-      for (int it = blockIdx.x; it < ld * nd2; it += gridDim.x) {
-        const int p = it / nd2, d = it - p * nd2;
-        if (kF32) scalar_item<AccF, float2, RedSync, true>(scj, SK_NORM, p, d, shf, RedSync());
-        else scalar_item<AccD, double, RedSync, true>(scj, SK_NORM, p, d, shd, RedSync());
-      }
+    const int nd2 = P.track_e ? 2 : 1;
+    for (int it = warp; it < ld * nd2; it += nwarps) {
+      const int p = it / nd2, d = it - p * nd2;
+      const double v = warp_reduce_partials<Acc, PartT>(part2, ld, P.ntiles, d, p);
+      if ((threadIdx.x & 31) == 0) R.D[d][p] = v;
     }
-    if (!run_barrier(P)) return;
+    __syncthreads();
+    for (int p = threadIdx.x; p < ld; p += blockDim.x) run_norm(S, R, p, j, nd2, writer);
+    __syncthreads();
   }
 }
 
@@ -1035,7 +1195,7 @@ int launch_krylov_run(const PersistRun<T>& P0, int threads, int nd_max, int nb_m
   LD_KRUN(4, 4, false) LD_KRUN(4, 4, true)
   LD_KRUN(kMaxWin, kMaxWin, false) LD_KRUN(kMaxWin, kMaxWin, true)
 #undef LD_KRUN
-  if (!kern || threads < kRedThreads || threads > 512) {
+  if (!kern || threads % 32 || threads > 512) {
     set_error("no persistent Krylov kernel for %d dots / %d basis vectors at %d threads", nd_max,
               nb_max, threads);
     return LOGDET_EINVAL;
@@ -1046,7 +1206,11 @@ int launch_krylov_run(const PersistRun<T>& P0, int threads, int nd_max, int nb_m
     set_error("persistent Krylov kernel does not fit an SM at %d threads", threads);
     return LOGDET_ECUDA;
   }
-  const int work = std::max(P.ntiles, P.sj.ld * std::max(nd_max, 2));
+  if (P.sj.ld > kRunMaxLd) {
+    set_error("persistent Krylov run: block width %d above %d", P.sj.ld, kRunMaxLd);
+    return LOGDET_EINVAL;
+  }
+  const int work = P.ntiles;
   const int grid = std::max(1, std::min(work, per_sm * sm_count()));
   const bool stall = krun_stall_test();
   P.nwait = (unsigned)grid + (stall ? 1u : 0u);

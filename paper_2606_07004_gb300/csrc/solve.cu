@@ -348,13 +348,17 @@ bool KRun<T>::persistent_ok() const {
   if constexpr (std::is_same<T, bf16>::value) {
     return false;
   } else {
+    // Opt-in: measured on GB300 (2D Laplacian 64^2, FP64) it issues as fast
+    // as the step path, not faster (see krylov.cuh), so the step path stays
+    // the default.
     const char* e = std::getenv("LOGDET_KRYLOV_PERSISTENT");
-    if (e && e[0] == '0') return false;
+    if (!e || e[0] != '1') return false;
     if (sweep || items || (hctx && hctx->kind == 1) || tune.split != 1 || nslots != ntiles)
       return false;
-    // the scalar steps run on the first kRedThreads threads of each CTA
-    if (g.threads < kRedThreads || g.threads > 512) return false;
-    return finished() ? false : blk * sizeof(T) <= kPersistMaxBlock;
+    // the scalar reductions run one per warp (whole warps only)
+    if (g.threads % 32 || g.threads > 512) return false;
+    // from the first step (the run seeds its sigmas from sigma_1)
+    return done_steps == 0 && ld <= 128 && blk * sizeof(T) <= kPersistMaxBlock;
   }
 }
 
@@ -370,8 +374,10 @@ int KRun<T>::issue_rest_persistent() {
     std::vector<UpdJob<T>> uj;
     LD_TRY(spmm_jobs(j, sj));
     upd_jobs(j, uj);
+    if (!krun_part2.p) LD_TRY(krun_part2.alloc((size_t)2 * ld * ntiles));
     P.sj = sj[0];
     P.uj = uj[0];
+    P.uj.part = krun_part2.p;  // pass-2 partials apart from pass 1's
     P.cj = scalar_job(j, 1, true);
     P.X0 = X0;
     P.ring = ring.p;

@@ -103,7 +103,8 @@ struct KRun {
   int done_steps = 0;  // steps whose pass 1 has been issued
   cudaStream_t st;
 
-  explicit KRun(cudaStream_t s) : part(s), y(s), ring(s), ks(s), dia_err(s), st(s), krun_bar(s) {}
+  explicit KRun(cudaStream_t s)
+      : part(s), y(s), ring(s), ks(s), dia_err(s), st(s), krun_bar(s), krun_part2(s) {}
 
   // Allocate and queue the start-block norms and sigma_1 (one launch pair).
   int init(const int* rp, const int* ci, const typename ValOf<T>::type* v, int n_, long long nnz_,
@@ -125,17 +126,18 @@ struct KRun {
   int slice_live(int q) const;
   // Scalar job over pass-1 partials (spmm_pass) or pass-2 / norm partials.
   ScalarJob scalar_job(int j, int ndots, bool spmm_pass = false) const;
-  // Persistent run: whether the remaining steps qualify (uniform CSR tiles,
-  // one column slice, FP64 or FP32 blocks of at most kPersistMaxBlock bytes,
-  // LOGDET_KRYLOV_PERSISTENT not 0), and the launch that issues them all.
+  // Persistent run: whether the remaining steps qualify (LOGDET_KRYLOV_PERSISTENT=1,
+  // uniform CSR tiles, one column slice, whole-warp CTAs, FP64 or FP32 blocks
+  // of at most kPersistMaxBlock bytes and 128 columns, from the first step),
+  // and the launch that issues them all.
   bool persistent_ok() const;
   int issue_rest_persistent();
   DevBuf<unsigned> krun_bar;
+  DevBuf<Part> krun_part2;  // persistent run: pass-2 partials
 };
 
-// Blocks up to this size (bytes of one n x ld block) run their Krylov steps
-// as one persistent launch in the blocking and graph-plan paths: below it
-// the launch gaps of four kernels per step outweigh the passes.
+// Blocks up to this size (bytes of one n x ld block) may run their Krylov
+// steps as one persistent launch in the blocking and graph-plan paths.
 constexpr size_t kPersistMaxBlock = (size_t)16 << 20;
 
 // Batched launches of jobs that share element type and CTA size.

@@ -1,9 +1,10 @@
-"""The persistent Krylov run: for small blocks every step of a Krylov phase
-(pass 1, the scalar coefficients, pass 2, the norms) runs in one cooperative
-launch, with bounded grid barriers.  Its results must be bit-identical to
-the step-by-step path (LOGDET_KRYLOV_PERSISTENT=0), match the FP64 oracle,
-replay bit-identically from a graph plan, and a barrier wait that runs out
-must fail the solve with LOGDET_ETIMEOUT and leave the context usable."""
+"""The persistent Krylov run (opt-in, LOGDET_KRYLOV_PERSISTENT=1): for small
+blocks every step of a Krylov phase (pass 1, the coefficients, pass 2, the
+norms) runs in one cooperative launch, with bounded grid barriers.  Its
+results must be bit-identical to the step-by-step path (the default), match
+the FP64 oracle, replay bit-identically from a graph plan, and a barrier wait
+that runs out must fail the solve with LOGDET_ETIMEOUT and leave the context
+usable."""
 import numpy as np
 import pytest
 
@@ -42,6 +43,7 @@ def test_persistent_run_equals_step_path(method, k, prec, monkeypatch):
     # sweep): every Krylov phase qualifies for the persistent run.
     A = W.laplacian_2d(50, 47, shift=0.05)
     with B.Handle.from_csr(A) as h:
+        monkeypatch.setenv("LOGDET_KRYLOV_PERSISTENT", "1")
         B.logdet_profile_reset()
         B.logdet_profile_enable(True)
         fast = _runs(h, method, k, precision=prec)
@@ -62,6 +64,7 @@ def test_persistent_run_matches_oracle_and_variants(monkeypatch):
     A = W.laplacian_2d(64, shift=0.1)
     Q = A.to_scipy()
     est = O.oslq(Q, 30, 30, seed=0)
+    monkeypatch.setenv("LOGDET_KRYLOV_PERSISTENT", "1")
     with B.Handle.from_csr(A) as h:
         res = h.oslq(30, 30, seed=0)
         assert abs(res.logdet - est.logdet) / abs(est.logdet) <= 1e-10
@@ -75,8 +78,9 @@ def test_persistent_run_matches_oracle_and_variants(monkeypatch):
         _same(a, b)
 
 
-def test_persistent_run_breakdown_and_single_step():
+def test_persistent_run_breakdown_and_single_step(monkeypatch):
     # Breakdown at step 1 (Q = c I) and m = 1 (no pass 2 at all).
+    monkeypatch.setenv("LOGDET_KRYLOV_PERSISTENT", "1")
     A = W.scaled_identity(3000, 2.5)
     with B.Handle.from_csr(A) as h:
         r = h.oslq(9, 10)
@@ -89,15 +93,19 @@ def test_persistent_run_breakdown_and_single_step():
     assert abs(r.logdet - est.logdet) / abs(est.logdet) <= 1e-10
 
 
-def test_plan_replays_persistent_run_bit_identically():
+def test_plan_replays_persistent_run_bit_identically(monkeypatch):
+    # plans captured with the persistent run, against blocking step-path solves
     A = W.laplacian_2d(64, shift=0.1)
     with B.Handle.from_csr(A) as h:
-        with B.Plan(h, B.METHOD_OSLQ, 30, 30) as plan:
+        monkeypatch.setenv("LOGDET_KRYLOV_PERSISTENT", "1")
+        p1 = B.Plan(h, B.METHOD_OSLQ, 30, 30)
+        p2 = B.Plan(h, B.METHOD_OSAIOP, 30, 20, iop_window=4)
+        monkeypatch.delenv("LOGDET_KRYLOV_PERSISTENT")
+        with p1, p2:
+            assert p1.kernels() < 40
             for seed in (0, 11):
-                _same(plan.run(seed), h.oslq(30, 30, seed=seed))
-            assert plan.kernels() < 40
-        with B.Plan(h, B.METHOD_OSAIOP, 30, 20, iop_window=4) as plan:
-            _same(plan.run(4), h.osaiop(30, 20, iop_window=4, seed=4))
+                _same(p1.run(seed), h.oslq(30, 30, seed=seed))
+            _same(p2.run(4), h.osaiop(30, 20, iop_window=4, seed=4))
 
 
 def test_barrier_wait_timeout_reports_and_recovers(monkeypatch):
@@ -106,6 +114,7 @@ def test_barrier_wait_timeout_reports_and_recovers(monkeypatch):
     # flag the run and return.  The solve fails with LOGDET_ETIMEOUT; the
     # next solve on the same handle is exact.
     A = W.laplacian_2d(40, shift=0.05)
+    monkeypatch.setenv("LOGDET_KRYLOV_PERSISTENT", "1")
     with B.Handle.from_csr(A) as h:
         want = h.oslq(30, 12, seed=1)
         monkeypatch.setenv("LOGDET_TEST_KRUN_STALL", "1")
