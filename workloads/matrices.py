@@ -316,22 +316,23 @@ def powerlaw_graph_laplacian(n: int, exponent: float = 2.3, mean_degree: float =
     np.minimum(v, n - 1, out=v)
     keep = u != v
     u, v = u[keep], v[keep]
-    keys = np.unique(np.concatenate([u * n + v, v * n + u]))
+    # Entry keys row * n + col of both triangles and the diagonal, sorted
+    # (row-major CSR order), duplicates merged.
+    idx = np.arange(n, dtype=np.int64)
+    keys = np.concatenate([u * n + v, v * n + u, idx * (n + 1)])
+    keys.sort()
+    keys = keys[np.concatenate(([True], keys[1:] != keys[:-1]))]
     rows = keys // n
-    cols = keys % n
-    deg = np.bincount(rows, minlength=n).astype(np.float64)
-    # Assemble with the diagonal in its sorted position.
-    all_rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
-    all_cols = np.concatenate([cols, np.arange(n, dtype=np.int64)])
-    all_vals = np.concatenate([-np.ones(rows.size), deg])
-    order = np.lexsort((all_cols, all_rows))
-    all_rows, all_cols, all_vals = all_rows[order], all_cols[order], all_vals[order]
-    counts = np.bincount(all_rows, minlength=n)
+    cols = keys - rows * n
+    diag = rows == cols
+    deg = np.bincount(rows[~diag], minlength=n).astype(np.float64)
+    all_vals = np.where(diag, deg[rows], -1.0)
+    counts = np.bincount(rows, minlength=n)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=rowptr[1:])
     if rowptr[-1] >= 2**31:
         raise ValueError("nnz does not fit int32 CSR indices")
-    return CSR(n, rowptr.astype(np.int32), all_cols.astype(np.int32), all_vals.astype(dtype))
+    return CSR(n, rowptr.astype(np.int32), cols.astype(np.int32), all_vals.astype(dtype))
 
 
 def diagonal_matrix(d, dtype=np.float64) -> CSR:
