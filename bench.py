@@ -11,12 +11,15 @@ tridiagonal Gauss rules, Hessenberg logarithms, assembly).
   python bench.py [--gpus N --steps K --warmup W]           # CUDA path
   python bench.py --impl reference [...]                    # FP64 CPU oracle
 
-At N = 1 the line also carries two bounded objects, each with its own clock
+At N = 1 the line also carries three bounded objects, each with its own clock
 record: matern_mixed (the mixed-precision configuration: Matern 1024^2, FP32
 vectors, OSLQ m = 80, 120 probes; solves/s, error against the FP64 CUDA path,
-HBM roofline of the Krylov passes) and serving (the continuous-batching
+HBM roofline of the Krylov passes), serving (the continuous-batching
 configuration at a reduced request count: mixed batched server against plain
-FP64 one at a time, solves/s and p50/p99 latency).
+FP64 one at a time, solves/s and p50/p99 latency) and irregular_batch (8
+shifts of a 2M-row power-law graph Laplacian advanced together, OSA-IOP
+m = 100, k = 4: batched against serial, error of the extreme shifts against
+FP64).
 
 Under torchrun every rank solves its own copy of the workload (independent
 problems, no data-path collective: weak scaling); the barrier and the max over
@@ -521,11 +524,14 @@ def cuda_arm(args):
         "kernel_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
     }
     if rank == 0 and ws == 1 and not args.no_extras:
-        # The mixed-precision and serving configurations, bounded, each with
-        # its own clock record (one GPU only: at N > 1 every rank would repeat them).
+        # The mixed-precision, serving and batched irregular configurations,
+        # bounded, each with its own clock record (one GPU only: at N > 1
+        # every rank would repeat them).
         for key, fn in (("matern_mixed", lambda: matern_measure(args.extra_solves, 2, at)),
                         ("serving", lambda: serving_measure(args.serving_requests, args.slots,
-                                                            args.budget_gb))):
+                                                            args.budget_gb)),
+                        ("irregular_batch", lambda: multishift_measure(args.budget_gb, at,
+                                                                       fp64_all=False))):
             try:
                 line[key] = fn()
             except Exception as e:  # reported, not hidden
@@ -802,13 +808,15 @@ def serving_case(args):
     return 0
 
 
-def multishift_case(args):
+def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -> dict:
     """Batched irregular workload: the Laplacian of a Chung-Lu power-law graph
     (n = 2,097,152, exponent 2.3, mean degree 8) with 8 diagonal shifts drawn
     uniformly from [1e-3, 1e-1]; OSA-IOP m = 100, k = 4, 64 probes per shift,
     FP32 values and vectors.  The 8 shifted operators share the CSR and
-    advance together (one launch per pass); compared with the same 8 solves
-    one after the other."""
+    advance together through the server (one launch per pass); compared with
+    the same 8 solves one after the other (bitwise equal), and each mixed
+    estimate with the FP64 CUDA path (same seed): every shift, or with
+    fp64_all False the smallest and the largest."""
     import numpy as np
     import torch
     from paper_2606_07004_gb300 import binding as B
@@ -822,46 +830,61 @@ def multishift_case(args):
     P, m, k = 64, 100, 4
     h = B.Handle.from_csr(A)
     need = h.estimate_bytes(B.METHOD_OSAIOP, P, m, k, precision=B.MIXED_FP32)
-    budget = int(min(args.budget_gb * (1 << 30), 8 * need * 1.05))
+    budget = int(min(budget_gb * (1 << 30), 8 * need * 1.05))
+    clocks = ClockSampler(torch.cuda.current_device(), "irregular")
+    clocks.start()
     with B.Server(budget, max_slots=8) as srv:
         srv.wait(srv.submit(h, B.METHOD_OSAIOP, P, 10, k, seed=0, precision=B.MIXED_FP32,
-                            shift=float(shifts[0]), autotune=args.autotune))
+                            shift=float(shifts[0]), autotune=autotune))
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         ids = [srv.submit(h, B.METHOD_OSAIOP, P, m, k, seed=t, precision=B.MIXED_FP32,
-                          shift=float(sh), autotune=args.autotune) for t, sh in enumerate(shifts)]
+                          shift=float(sh), autotune=autotune) for t, sh in enumerate(shifts)]
         batched = [srv.wait(i) for i in ids]
         t_batched = time.perf_counter() - t1
         st = srv.stats()
     t1 = time.perf_counter()
     serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh),
-                       autotune=args.autotune) for t, sh in enumerate(shifts)]
+                       autotune=autotune) for t, sh in enumerate(shifts)]
     t_serial = time.perf_counter() - t1
-    # Error of each mixed estimate against the FP64 CUDA path (same seed).
-    r64 = [h.osaiop(P, m, iop_window=k, seed=t, shift=float(sh)) for t, sh in enumerate(shifts)]
-    errs = [abs(a.logdet - b.logdet) / abs(b.logdet) for a, b in zip(batched, r64)]
+    clk = clocks.stop()
+    # Error of the mixed estimates against the FP64 CUDA path (same seed).
+    which = list(range(8)) if fp64_all else sorted({int(np.argmin(shifts)), int(np.argmax(shifts))})
+    r64 = {t: h.osaiop(P, m, iop_window=k, seed=t, shift=float(shifts[t])) for t in which}
+    errs = {t: abs(batched[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
     # Device time per kernel class of one of the solves run alone.
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
     h.osaiop(P, m, iop_window=k, seed=0, precision=B.MIXED_FP32, shift=float(shifts[0]),
-             autotune=args.autotune)
+             autotune=autotune)
     B.logdet_profile_enable(False)
     prof = B.profile_snapshot()
     h.close()
-    print(json.dumps({
+    return {
         "workload": "power-law graph Laplacian n=%d nnz=%d, 8 shifts U[1e-3,1e-1], OSA-IOP m=100 "
                     "k=4, 64 probes each, mixed FP32" % (A.n, A.nnz),
-        "metric": METRIC, "unit": UNIT,
+        "unit": UNIT,
         "batched_solves_per_s": 8 / t_batched, "serial_solves_per_s": 8 / t_serial,
         "batched_s": t_batched, "serial_s": t_serial,
         "bitwise_equal_batched_vs_serial": all(a.logdet == b.logdet for a, b in zip(batched, serial)),
         "logdets": [r.logdet for r in batched], "shifts": list(map(float, shifts)),
-        "rel_err_mixed_vs_fp64": errs, "fp64_solve_ms": [r.device_ms for r in r64],
+        "rel_err_mixed_vs_fp64": {f"shift_{t}": errs[t] for t in which},
+        "within_1e-4": all(e <= 1e-4 for e in errs.values()),
+        "within_1e-3": all(e <= 1e-3 for e in errs.values()),
+        "error_note": "at m = 100 the IOP recurrence amplifies FP32 vector rounding on this "
+                      "graph; FP64 itself moves by ~4e-5 against extended arithmetic",
+        "fp64_solve_ms": {f"shift_{t}": r64[t].device_ms for t in which},
         "bytes_per_solve_estimate": need, "max_resident": st["max_resident"],
-        "kernel_ms_one_solve": {k: v["ms"] for k, v in prof.items()},
+        "kernel_ms_one_solve": {k_: v["ms"] for k_, v in prof.items()},
         "krylov_algorithmic_gbs_one_solve": (prof["spmm"]["bytes"] + prof["update"]["bytes"]) /
         ((prof["spmm"]["ms"] + prof["update"]["ms"]) / 1e3) / 1e9,
-        "graph_build_s": t_build}))
+        "graph_build_s": t_build, "clocks": clk}
+
+
+def multishift_case(args):
+    """--workload multishift: the batched irregular line on its own."""
+    out = multishift_measure(args.budget_gb, args.autotune, fp64_all=True)
+    print(json.dumps(dict(out, metric=METRIC)))
     return 0
 
 

@@ -338,6 +338,32 @@ def test_mixed_precision_within_1e4_of_fp64(method, k):
     assert rel(r32.logdet, r64.logdet) <= RTOL_MIXED
 
 
+def test_maximum_sizes_parity_and_limits():
+    # The largest solves the boundary takes: s = r = 64 (192 probes, the
+    # widest Hutch++ QR) with m = 256 Krylov steps (the largest small solve),
+    # and OSA-IOP with the widest window k = 8 at m = 256; one more probe,
+    # sketch column or step is EINVAL.  2D Laplacian 30 x 31 + 0.5 I
+    # (n = 930): well conditioned, the oracle's two dot orders agree to 2e-16.
+    A = W.laplacian_2d(30, 31, shift=0.5)
+    Q = A.to_scipy()
+    est = O.oslq(Q, 192, 256, seed=3)
+    est2 = O.osaiop(Q, 30, 256, k=8, seed=3)
+    with B.Handle.from_csr(A) as h:
+        res = h.oslq(192, 256, seed=3)
+        assert (res.s, res.r) == (64, 64)
+        _compare(est, res)
+        res2 = h.osaiop(30, 256, iop_window=8, seed=3)
+        _compare(est2, res2)
+        for call in (lambda: h.oslq(193, 20),            # r = 65
+                     lambda: h.oslq(195, 20),            # s = 65
+                     lambda: h.oslq(30, 257),            # m above 256 (n = 930)
+                     lambda: h.osaiop(30, 257, iop_window=2),
+                     lambda: h.oslq(65, 20, plain=1)):   # 65 residual probes
+            with pytest.raises(B.LogdetError) as e:
+                call()
+            assert e.value.code == B.EINVAL
+
+
 def test_invalid_arguments_are_errors():
     A = W.laplacian_2d(10, shift=0.1)
     with B.Handle.from_csr(A) as h:
