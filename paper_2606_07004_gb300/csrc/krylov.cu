@@ -231,6 +231,19 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           q0 = __ldg(J.rowptr + row);
           q1 = __ldg(J.rowptr + row + 1);
         }
+        // FP32 / BF16 blocks with two window dots: the row's window vectors
+        // are requested before its gathers, so their latency overlaps them
+        // (the dot products keep their order).  Measured on the 2M-row
+        // power-law graph (OSA-IOP k = 2, m = 100): SpMM 334 -> 295 ms per
+        // solve; with four dots the registers cost the second CTA per SM
+        // (428 -> 666 ms), so the instance for up to four keeps late loads.
+        constexpr bool kEarlyDots = !std::is_same<T, double>::value && NDOT == 2;
+        CT ue[kEarlyDots ? NDOT : 1][V];
+        if constexpr (kEarlyDots) {
+#pragma unroll
+          for (int d = 0; d < NDOT; ++d)
+            if (d < ndots) load_v<COH, T>(J.dotv[d] + (size_t)row * J.ld + col0, ue[d]);
+        }
         CT s[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) s[v] = CT(0);
@@ -310,7 +323,12 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
         for (int d = 0; d < NDOT; ++d) {
           if (d < ndots) {
             CT u[V];
-            load_v<COH, T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+            if constexpr (kEarlyDots) {
+#pragma unroll
+              for (int v = 0; v < V; ++v) u[v] = ue[d][v];
+            } else {
+              load_v<COH, T>(J.dotv[d] + (size_t)row * J.ld + col0, u);
+            }
 #pragma unroll
             for (int v = 0; v < V; ++v) acc[d][v].fma(u[v], s[v]);
           }
