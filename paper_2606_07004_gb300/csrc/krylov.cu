@@ -235,8 +235,9 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
         // are requested before its gathers, so their latency overlaps them
         // (the dot products keep their order).  Measured on the 2M-row
         // power-law graph (OSA-IOP k = 2, m = 100): SpMM 334 -> 295 ms per
-        // solve; with four dots the registers cost the second CTA per SM
-        // (428 -> 666 ms), so the instance for up to four keeps late loads.
+        // solve.  The instance for up to four dots keeps late loads: early
+        // loads of all four cost the second CTA per SM (428 -> 666 ms), and
+        // of the first two, at two CTAs per SM, still lost (427 -> 584 ms).
         constexpr bool kEarlyDots = !std::is_same<T, double>::value && NDOT == 2;
         CT ue[kEarlyDots ? NDOT : 1][V];
         if constexpr (kEarlyDots) {
