@@ -219,6 +219,34 @@ int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
                   int32_t iop_window, uint64_t seed, const logdet_opts* opts,
                   logdet_result* out);
 
+/* logdet_oslq_shifts / logdet_osaiop_shifts: nshift solves of
+ * log det(Q + shifts[t] I), t < nshift, each exactly the solve of
+ * logdet_oslq / logdet_osaiop with opts->shift = shifts[t] and seed
+ * seed0 + t (same probes, steps, window, precision and options otherwise),
+ * run in lockstep: the Krylov phases of all of them go through one Krylov
+ * run over a block of all their probe columns, so each SpMM gather fetches
+ * the x row of every shift at once (the shifts scale the matrix differently,
+ * Proposition 2.1; each column carries its own diagonal shift and scale).
+ * The paper solves one operator at a time: this batches the shifted
+ * log-determinants a likelihood scan over a diagonal parameter needs.
+ * shifts: host array of nshift finite values >= 0 (caller-owned, read before
+ * return); out: host array of nshift results.  out[t].device_ms is the whole
+ * group's device time.  opts->shift, opts->per_probe and opts->z_norm2 are
+ * not used.  Results agree with the separate solves to rounding (one SpMM
+ * per step computes (Q/c_0 + shift_t/c_0) x c_0/c_t instead of
+ * (Q + shift_t) x / c_t).  Blocks until the results are on the host.
+ * Device memory: about nshift times one solve's.  Errors: EINVAL (nshift < 1;
+ * NULL pointers; any member's configuration as logdet_oslq / logdet_osaiop;
+ * a gridded operator; more than 1024 block columns in all: nshift times
+ * num_probes - floor(num_probes/3) rounded up to 2 (FP64) or 4 (FP32/BF16)
+ * columns), ENOTSPD, ENOMEM, ECUDA. */
+int logdet_oslq_shifts(logdet_handle h, int32_t nshift, const double* shifts, int32_t num_probes,
+                       int32_t krylov_steps, int32_t iop_window, uint64_t seed0,
+                       const logdet_opts* opts, logdet_result* out);
+int logdet_osaiop_shifts(logdet_handle h, int32_t nshift, const double* shifts,
+                         int32_t num_probes, int32_t krylov_steps, int32_t iop_window,
+                         uint64_t seed0, const logdet_opts* opts, logdet_result* out);
+
 /* ---- step-level entry points (each one row of the hot path) ------------
  * logdet_probe_fill: the Rademacher probe entries of Algorithms 2/3
  * ("sample S with i.i.d. +-1 entries") by the SplitMix64 counter spec:

@@ -44,6 +44,7 @@ EXPORTED = [
     "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
+    "logdet_oslq_shifts", "logdet_osaiop_shifts",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
@@ -105,6 +106,9 @@ _sig("logdet_grid_structure_csr", C.c_int, [_i32, _P, _P, C.POINTER(_i32), C.POI
                                             C.POINTER(_i32)])
 for _n in ("logdet_oslq", "logdet_osaiop"):
     _sig(_n, C.c_int, [_P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts), C.POINTER(logdet_result)])
+for _n in ("logdet_oslq_shifts", "logdet_osaiop_shifts"):
+    _sig(_n, C.c_int, [_P, _i32, _P, _i32, _i32, _i32, _u64, C.POINTER(logdet_opts),
+                       C.POINTER(logdet_result)])
 _sig("logdet_probe_fill", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
 _sig("logdet_probe_fill_gaussian", C.c_int, [_u64, _i32, _i32, _i32, _i32, _P, _i32, _P])
 _sig("logdet_spmm", C.c_int, [_P, _P, _P, _i32, _i32, _P])
@@ -331,6 +335,38 @@ class Handle:
         return self._run(_lib.logdet_osaiop, "logdet_osaiop", num_probes, krylov_steps,
                          iop_window, seed, precision, tol, lam, stream, shift, autotune, plain,
                          gaussian, block_width)
+
+    def _run_shifts(self, fn, name, shifts, num_probes, krylov_steps, iop_window, seed0,
+                    precision, tol, lam, stream, autotune, plain, gaussian, block_width):
+        sh = np.ascontiguousarray(shifts, dtype=np.float64).ravel()
+        s = 0 if plain else num_probes // 3
+        r = num_probes - 2 * s
+        empty_p, empty_z = np.zeros(0), np.zeros(0)
+        o = _make_opts(precision, tol, lam, stream, 0.0, empty_p, empty_z, autotune, plain,
+                       gaussian, block_width)
+        o.per_probe = None
+        o.z_norm2 = None
+        res = (logdet_result * max(len(sh), 1))()
+        _check(fn(self._h, len(sh), sh.ctypes.data_as(C.c_void_p), num_probes, krylov_steps,
+                  iop_window, seed0, C.byref(o), res), name)
+        return [_result(res[t], empty_p, empty_z, 0, 0) for t in range(len(sh))]
+
+    def oslq_shifts(self, shifts, num_probes, krylov_steps, seed0=0, iop_window=0,
+                    precision=FP64, tol=None, lam=None, stream=None, autotune=0, plain=0,
+                    gaussian=0, block_width=0) -> list:
+        """log det(Q + shifts[t] I) for every t in one lockstep group
+        (logdet_oslq_shifts); member t is oslq(..., seed=seed0 + t, shift=shifts[t])."""
+        return self._run_shifts(_lib.logdet_oslq_shifts, "logdet_oslq_shifts", shifts,
+                                num_probes, krylov_steps, iop_window, seed0, precision, tol, lam,
+                                stream, autotune, plain, gaussian, block_width)
+
+    def osaiop_shifts(self, shifts, num_probes, krylov_steps, iop_window=2, seed0=0,
+                      precision=FP64, tol=None, lam=None, stream=None, autotune=0, plain=0,
+                      gaussian=0, block_width=0) -> list:
+        """The OSA-IOP counterpart (logdet_osaiop_shifts)."""
+        return self._run_shifts(_lib.logdet_osaiop_shifts, "logdet_osaiop_shifts", shifts,
+                                num_probes, krylov_steps, iop_window, seed0, precision, tol, lam,
+                                stream, autotune, plain, gaussian, block_width)
 
     def estimate_bytes(self, method, num_probes, krylov_steps, iop_window=0, precision=FP64,
                        shift=0.0) -> int:

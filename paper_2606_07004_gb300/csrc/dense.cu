@@ -1275,6 +1275,42 @@ int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
+// The same for ncols columns of basis blocks with leading dimension ldv (a
+// column slice of a wider basis): Y[:, p] = sum_j w[j][p] V_j[:, p], p < ncols,
+// each element's sum in the order above.
+template <typename T>
+__global__ void k_sketch_assemble_cols(const T* __restrict__ V, int n, int ncols, int ldv, int m,
+                                       const double* __restrict__ w, double* __restrict__ Y,
+                                       int ldy) {
+  const size_t total = (size_t)n * ncols;
+  const size_t stride_v = (size_t)n * ldv;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    int row = (int)(e / ncols), p = (int)(e - (size_t)row * ncols);
+    const size_t ve = (size_t)row * ldv + p;
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j)
+      acc = fma(w[(size_t)j * ncols + p], cvt<double>(V[j * stride_v + ve]), acc);
+    if (p < ldy) Y[(size_t)row * ldy + p] = acc;
+  }
+}
+
+template <typename T>
+int sketch_assemble_cols(const T* V, int n, int ncols, int ldv, int m, const double* w, double* Y,
+                         int ldy, cudaStream_t st) {
+  ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ncols * m,
+                 (double)n * ncols * (m * sizeof(T) + 8.0));
+  k_sketch_assemble_cols<T><<<8 * sm_count(), 256, 0, st>>>(V, n, ncols, ldv, m, w, Y, ldy);
+  LD_CHECK_LAUNCH();
+  return LOGDET_OK;
+}
+template int sketch_assemble_cols<double>(const double*, int, int, int, int, const double*, double*,
+                                          int, cudaStream_t);
+template int sketch_assemble_cols<float>(const float*, int, int, int, int, const double*, double*,
+                                         int, cudaStream_t);
+template int sketch_assemble_cols<bf16>(const bf16*, int, int, int, int, const double*, double*,
+                                        int, cudaStream_t);
+
 template int sketch_assemble<double>(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 template int sketch_assemble<float>(const float*, int, int, int, const double*, double*, int, cudaStream_t);
 template int sketch_assemble<bf16>(const bf16*, int, int, int, const double*, double*, int, cudaStream_t);

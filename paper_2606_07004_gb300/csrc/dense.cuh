@@ -83,5 +83,9 @@ int convert_block(const Tin* in, int ldin, Tout* out, int ldout, int n, int cols
 template <typename T>
 int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y, int ldy,
                     cudaStream_t st);
+// The same for ncols columns of basis blocks of leading dimension ldv.
+template <typename T>
+int sketch_assemble_cols(const T* V, int n, int ncols, int ldv, int m, const double* w, double* Y,
+                         int ldy, cudaStream_t st);
 
 }  // namespace ld

@@ -60,6 +60,39 @@ static int run_estimator(int method, logdet_handle h, int32_t P, int32_t m, int3
   return LOGDET_OK;
 }
 
+// Several shifts of one matrix in lockstep (solve_shifts); member t takes
+// shift shifts[t] and seed seed0 + t, everything else from opts.
+static int run_shifts(int method, logdet_handle h, int32_t nshift, const double* shifts, int32_t P,
+                      int32_t m, int32_t k, uint64_t seed0, const logdet_opts* opts,
+                      logdet_result* out) {
+  if (!h || !out || !shifts) { set_error("NULL handle, shifts or results"); return LOGDET_EINVAL; }
+  if (nshift < 1) { set_error("nshift=%d must be >= 1", nshift); return LOGDET_EINVAL; }
+  std::vector<SolveCfg> cfgs;
+  for (int t = 0; t < nshift; ++t) {
+    SolveCfg c = make_solve_cfg(method, P, m, k, seed0 + (uint64_t)t, opts);
+    c.shift = shifts[t];
+    cfgs.push_back(c);
+  }
+  cudaStream_t st = (opts && opts->stream) ? (cudaStream_t)opts->stream : h->stream;
+  if (cudaSetDevice(h->device) != cudaSuccess) { set_error("cudaSetDevice failed"); return LOGDET_ECUDA; }
+  Events ev;
+  LD_CUDA(cudaEventCreate(&ev.a));
+  LD_CUDA(cudaEventCreate(&ev.b));
+  LD_CUDA(cudaEventRecord(ev.a, st));
+  std::vector<SolveOut> outs;
+  LD_TRY(solve_shifts(h, cfgs, st, outs));
+  LD_CUDA(cudaEventRecord(ev.b, st));
+  LD_CUDA(cudaEventSynchronize(ev.b));
+  float ms = 0.f;
+  LD_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+  for (int t = 0; t < nshift; ++t) {
+    out[t] = outs[t].res;
+    out[t].device_ms = ms;
+  }
+  LD_CUDA(cudaGetLastError());
+  return LOGDET_OK;
+}
+
 }  // namespace ld
 
 // ===========================================================================
@@ -153,6 +186,16 @@ int logdet_oslq(logdet_handle h, int32_t P, int32_t m, int32_t k, uint64_t seed,
 int logdet_osaiop(logdet_handle h, int32_t P, int32_t m, int32_t k, uint64_t seed,
                   const logdet_opts* opts, logdet_result* out) {
   return run_estimator(1, h, P, m, k, seed, opts, out);
+}
+
+int logdet_oslq_shifts(logdet_handle h, int32_t nshift, const double* shifts, int32_t P, int32_t m,
+                       int32_t k, uint64_t seed0, const logdet_opts* opts, logdet_result* out) {
+  return run_shifts(0, h, nshift, shifts, P, m, k, seed0, opts, out);
+}
+
+int logdet_osaiop_shifts(logdet_handle h, int32_t nshift, const double* shifts, int32_t P, int32_t m,
+                         int32_t k, uint64_t seed0, const logdet_opts* opts, logdet_result* out) {
+  return run_shifts(1, h, nshift, shifts, P, m, k, seed0, opts, out);
 }
 
 int logdet_probe_fill(uint64_t seed, int32_t stream, int32_t n, int32_t ncols, int32_t col0,

@@ -245,6 +245,7 @@ int KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
     J.ntiles = nslots;
     J.items = items;
     J.colshift = colshift;
+    J.colscale = colscale;
     if (method == 0) {
       J.ndots = 1;
       J.dotv[0] = ptr(j);
@@ -610,6 +611,14 @@ struct Solve : ISolve {
   int* h_err = nullptr;  // [2]: a diagonal-path wait gave up (phase 1, last run)
   cudaEvent_t ev_done = nullptr;
   const uint64_t* dev_keys = nullptr;  // graph plans: probe keys in device memory
+  // Group member (solve_shifts): the Krylov phases run in one wide run over
+  // every member's columns; start_run hands the start block to the group,
+  // adopt takes this member's scalar history back from the wide run.
+  bool grouped = false, awaiting = false;
+  T* pend_x0 = nullptr;          // start block of the phase that waits for the group
+  int pend_b = 0, pend_ld = 0;   // its live columns and width
+  const T* vst_ext = nullptr;    // phase-1 basis: this member's columns of the group's
+  int vst_ld = 0;                //   basis blocks (leading dimension vst_ld)
 
   Solve(logdet_ctx* h_, const SolveCfg& c_, cudaStream_t st_)
       : h(h_), c(c_), st(st_), vals(st_), gtabs(st_), diav(st_), Vst(st_), Xc(st_), X64(st_), outv(st_), cshift(st_),
@@ -690,6 +699,68 @@ struct Solve : ISolve {
                               st, tc);
   }
 
+  // Start the Krylov run of the current phase on X0 (a group member only
+  // records it for the group).
+  int start_run(int b_, int ld_, int k_, int method_, bool track_e_, T* X0, T* Vfull, TuneCfg tc) {
+    if (grouped) {
+      pend_x0 = X0;
+      pend_b = b_;
+      pend_ld = ld_;
+      awaiting = true;
+      return LOGDET_OK;
+    }
+    return run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b_, ld_, m, k_, method_, track_e_, X0,
+                     Vfull, c.tol, tc);
+  }
+
+  double cscale() const { return c.method == 0 ? alpha : gamma; }
+  // Group member: free the start block once the group has copied it.
+  void release_start() {
+    if (pend_x0 == Vst.p) Vst.release();
+    else if (pend_x0 == Xc.p) Xc.release();
+    else if (static_cast<void*>(pend_x0) == static_cast<void*>(X64.p)) X64.release();
+  }
+
+  // Group member: this member's per-probe scalar history (probes p0 ..
+  // p0 + pend_ld - 1 of the wide run w) into a run of its own, then the next
+  // phase.
+  int adopt(const KRun<T>& w, int p0) {
+    const int ldm = pend_ld;
+    run.reset(new KRun<T>(st));
+    KRun<T>& rr = *run;
+    rr.m = m;
+    rr.ld = ldm;
+    rr.b = pend_b;
+    rr.k = w.k;
+    rr.method = w.method;
+    rr.track_e = w.track_e;
+    LD_TRY(rr.ks.alloc(w.method, pend_b, ldm, m, w.k, c.tol, rescale_limit<T>()));
+    auto cp = [&](auto* dst, const auto* src, size_t cnt) {
+      return cudaMemcpyAsync(dst, src, cnt * sizeof(*dst), cudaMemcpyDeviceToDevice, st);
+    };
+    const size_t pm2 = (size_t)m + 2;
+    if (w.method == 0) {
+      LD_CUDA(cp(rr.ks.alpha.p, w.ks.alpha.p + (size_t)p0 * m, (size_t)ldm * m));
+      LD_CUDA(cp(rr.ks.beta.p, w.ks.beta.p + (size_t)p0 * m, (size_t)ldm * m));
+    } else {
+      const size_t hb = (size_t)(m + 1) * m;
+      LD_CUDA(cp(rr.ks.H.p, w.ks.H.p + (size_t)p0 * hb, (size_t)ldm * hb));
+    }
+    LD_CUDA(cp(rr.ks.sig.p, w.ks.sig.p + (size_t)p0 * pm2, (size_t)ldm * pm2));
+    LD_CUDA(cp(rr.ks.edot.p, w.ks.edot.p + (size_t)p0 * pm2, (size_t)ldm * pm2));
+    LD_CUDA(cp(rr.ks.meff.p, w.ks.meff.p + p0, (size_t)ldm));
+    LD_CUDA(cp(rr.ks.active.p, w.ks.active.p + p0, (size_t)ldm));
+    LD_CUDA(cp(rr.ks.status.p, w.ks.status.p + p0, (size_t)ldm));
+    if (w.dia_err.p) {
+      LD_TRY(rr.dia_err.alloc(1));
+      LD_CUDA(cp(rr.dia_err.p, w.dia_err.p, 1));
+    }
+    awaiting = false;
+    pend_x0 = nullptr;
+    ph = (c.method == 1 && ph == PH_K1) ? PH_MID : PH_FINISH;
+    return LOGDET_OK;
+  }
+
   // X0 for the next Krylov run from X64 (a copy in FP32 for the mixed path).
   int make_x0(T** X0) {
     if constexpr (std::is_same<T, double>::value) {
@@ -739,12 +810,10 @@ struct Solve : ISolve {
       TuneCfg tc;
       LD_TRY(layout(ld, c.method == 1, &tc));
       if (c.method == 0) {
-        LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
-                         nullptr, c.tol, tc));
+        LD_TRY(start_run(b, ld, 2, 0, false, X0, nullptr, tc));
         ph = PH_K1;
       } else {
-        LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0,
-                         nullptr, c.tol, tc));
+        LD_TRY(start_run(b, ld, kk, 1, true, X0, nullptr, tc));
         ph = PH_K2;
       }
       return LOGDET_OK;
@@ -787,11 +856,11 @@ struct Solve : ISolve {
       run->diavals = diav.p;
       TuneCfg tc;
       LD_TRY(layout(ld, false, &tc));
-      LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, 2, 0, false, X0,
-                       nullptr, c.tol, tc));
+      LD_TRY(start_run(b, ld, 2, 0, false, X0, nullptr, tc));
     } else {
       // Algorithm 2, phase 1: each sketch column through Algorithm 1, basis kept.
-      LD_TRY(Vst.alloc((size_t)n * lds * m));
+      // (a group member fills only the start block; the group keeps the basis)
+      LD_TRY(Vst.alloc((size_t)n * lds * (grouped ? 1 : m)));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, Vst.p, lds, st, c.gaussian, dkey(0)));
       run->colshift = cshift.p;
       run->hctx = h;
@@ -799,8 +868,7 @@ struct Solve : ISolve {
       run->diavals = diav.p;
       TuneCfg tc;
       LD_TRY(layout(lds, false, &tc));
-      LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, s, lds, m, kk, 1, false, Vst.p,
-                       Vst.p, c.tol, tc));
+      LD_TRY(start_run(s, lds, kk, 1, false, Vst.p, Vst.p, tc));
     }
     ph = PH_K1;
     return LOGDET_OK;
@@ -822,7 +890,10 @@ struct Solve : ISolve {
       LD_CHECK_LAUNCH();
     }
     LD_TRY(Y64.alloc((size_t)n * lds));
-    LD_TRY(sketch_assemble<T>(Vst.p, n, lds, m, w.p, Y64.p, lds, st));
+    if (grouped)
+      LD_TRY(sketch_assemble_cols<T>(vst_ext, n, lds, vst_ld, m, w.p, Y64.p, lds, st));
+    else
+      LD_TRY(sketch_assemble<T>(Vst.p, n, lds, m, w.p, Y64.p, lds, st));
     LD_CUDA(cudaMemcpyAsync(h_status1, r1.ks.status.p, sizeof(uint32_t) * lds, cudaMemcpyDeviceToHost, st));
     if (r1.dia_err.p)
       LD_CUDA(cudaMemcpyAsync(h_err, r1.dia_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -843,8 +914,7 @@ struct Solve : ISolve {
     run->diavals = diav.p;
     TuneCfg tc;
     LD_TRY(layout(ld, true, &tc));
-    LD_TRY(run->init(h->rowptr, h->colind, vals.p, n, h->nnz, b, ld, m, kk, 1, true, X0, nullptr,
-                     c.tol, tc));
+    LD_TRY(start_run(b, ld, kk, 1, true, X0, nullptr, tc));
     ph = PH_K2;
     return LOGDET_OK;
   }
@@ -1057,6 +1127,157 @@ SolveCfg make_solve_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t se
     c.block_width = opts->block_width;
   }
   return c;
+}
+
+// ---------------------------------------------------------------------------
+// Several diagonal shifts of one matrix in lockstep
+// ---------------------------------------------------------------------------
+// The Krylov phases of the members run as one run over a wide block: member
+// t owns columns [t w, (t + 1) w) (w its block width); the values are member
+// 0's (Q / c_0), and column p of member t is scaled by c_0 / c_t after the
+// shift sigma_t / c_0, so y = (Q + sigma_t I) x / c_t as in the member's own
+// run.  Everything else of a member's solve (sketch, Hutch++ split, small
+// solves, assembly) is its own.  One gather of the SpMM pass then fetches
+// the x row of every member at once.
+template <typename T>
+static int group_krylov(logdet_ctx* h, std::vector<Solve<T>*>& ms, DevBuf<T>& Vw, cudaStream_t st) {
+  const int R = (int)ms.size();
+  Solve<T>& m0 = *ms[0];
+  const bool phase1 = m0.c.method == 1 && m0.ph == PH_K1;
+  const int wm = m0.pend_ld;
+  const int ldw = R * wm;
+  const int n = m0.n, m = m0.m;
+  const int method = m0.c.method == 0 ? 0 : 1;
+  const bool track_e = m0.c.method == 1 && !phase1;
+  for (Solve<T>* sv : ms)
+    if (!sv->awaiting || sv->ph != m0.ph || sv->pend_ld != wm || sv->pend_b != m0.pend_b) {
+      set_error("shift group: members out of step");
+      return LOGDET_EINVAL;
+    }
+  DevBuf<T> Xw(st);
+  T* X0w;
+  if (phase1) {
+    LD_TRY(Vw.alloc((size_t)n * ldw * m));
+    X0w = Vw.p;
+  } else {
+    LD_TRY(Xw.alloc((size_t)n * ldw));
+    X0w = Xw.p;
+  }
+  for (int t = 0; t < R; ++t) {
+    LD_CUDA(cudaMemcpy2DAsync(X0w + (size_t)t * wm, sizeof(T) * ldw, ms[t]->pend_x0, sizeof(T) * wm,
+                              sizeof(T) * wm, n, cudaMemcpyDeviceToDevice, st));
+    ms[t]->release_start();
+  }
+  std::vector<double> hsc((size_t)ldw), hsh((size_t)ldw);
+  const double c0 = m0.cscale();
+  for (int t = 0; t < R; ++t)
+    for (int q = 0; q < wm; ++q) {
+      hsc[(size_t)t * wm + q] = c0 / ms[t]->cscale();
+      hsh[(size_t)t * wm + q] = ms[t]->c.shift / c0;
+    }
+  DevBuf<double> csc(st), csh(st);
+  LD_TRY(csc.alloc(ldw));
+  LD_TRY(csh.alloc(ldw));
+  LD_CUDA(cudaMemcpyAsync(csc.p, hsc.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
+  LD_CUDA(cudaMemcpyAsync(csh.p, hsh.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
+  KRun<T> w(st);
+  w.colshift = csh.p;
+  w.colscale = csc.p;
+  w.hctx = h;
+  w.diavals = m0.diav.p;
+  TuneCfg tc;
+  LD_TRY(m0.layout(ldw, track_e, &tc));
+  LD_TRY(w.init(h->rowptr, h->colind, m0.vals.p, n, h->nnz, ldw, ldw, m, m0.kk, method, track_e,
+                X0w, phase1 ? Vw.p : nullptr, m0.c.tol, tc));
+  if (m0.pend_b < wm)  // each member's padding columns stay out of the run, as in its own
+    for (int t = 0; t < R; ++t)
+      LD_CUDA(cudaMemsetAsync(w.ks.active.p + (size_t)t * wm + m0.pend_b, 0,
+                              sizeof(*w.ks.active.p) * (wm - m0.pend_b), st));
+  std::vector<SpmmJob<T>> sj;
+  std::vector<UpdJob<T>> uj;
+  const std::vector<int> widths{ldw};
+  for (int j = 1; j <= m; ++j) {
+    NvtxRange nv("logdet shift-group krylov step");
+    sj.clear();
+    LD_TRY(w.spmm_jobs(j, sj));
+    LD_TRY(launch_spmm_jobs<T>(sj, w.g.threads, st));
+    LD_TRY(launch_scalar_jobs({w.scalar_job(j, w.pass1_dots(j), true)}, widths, SK_COEF, st));
+    if (w.has_pass2(j)) {
+      uj.clear();
+      w.upd_jobs(j, uj);
+      LD_TRY(launch_update_jobs<T>(uj, w.g.threads, st));
+      LD_TRY(launch_scalar_jobs({w.scalar_job(j, w.track_e ? 2 : 1)}, widths, SK_NORM, st));
+    }
+    w.done_steps++;
+  }
+  for (int t = 0; t < R; ++t) {
+    LD_TRY(ms[t]->adopt(w, t * wm));
+    if (phase1) {
+      ms[t]->vst_ext = Vw.p + (size_t)t * wm;
+      ms[t]->vst_ld = ldw;
+    }
+  }
+  return LOGDET_OK;
+}
+
+template <typename T>
+static int solve_shifts_t(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
+                          std::vector<SolveOut>& outs) {
+  std::vector<std::unique_ptr<Solve<T>>> own;
+  std::vector<Solve<T>*> ms;
+  for (const SolveCfg& c : cfgs) {
+    own.emplace_back(new Solve<T>(h, c, st));
+    own.back()->grouped = true;
+    ms.push_back(own.back().get());
+  }
+  DevBuf<T> Vw(st);
+  // setup -> [phase 1] -> mid -> [phase 2] -> finish, every member in step
+  for (int round = 0; round < 6; ++round) {
+    bool all_done = true;
+    for (Solve<T>* sv : ms) {
+      if (sv->ph == PH_SETUP || sv->ph == PH_MID || sv->ph == PH_FINISH) LD_TRY(sv->run_phase());
+      all_done = all_done && sv->ph == PH_WAIT;
+    }
+    if (all_done) break;
+    if (ms[0]->ph == PH_K2) Vw.release();  // every mid has read the phase-1 basis
+    LD_TRY(group_krylov<T>(h, ms, Vw, st));
+  }
+  for (Solve<T>* sv : ms)
+    if (sv->ph != PH_WAIT) {
+      set_error("shift group: solve did not finish");
+      return LOGDET_ECUDA;
+    }
+  LD_CUDA(cudaEventSynchronize(ms.back()->done_event()));
+  outs.resize(ms.size());
+  for (size_t t = 0; t < ms.size(); ++t) LD_TRY(ms[t]->assemble(outs[t]));
+  return LOGDET_OK;
+}
+
+int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
+                 std::vector<SolveOut>& outs) {
+  if (cfgs.empty()) {
+    set_error("shift group: no shifts");
+    return LOGDET_EINVAL;
+  }
+  if (h->kind == 1) {
+    set_error("shift group: gridded operators take one shift per solve");
+    return LOGDET_EINVAL;
+  }
+  for (const SolveCfg& c : cfgs) LD_TRY(validate_cfg(h, c));
+  const int vec = cfgs[0].precision == LOGDET_FP64 ? 2 : 4;
+  const int s = cfgs[0].plain ? 0 : cfgs[0].P / 3, r = cfgs[0].plain ? cfgs[0].P : cfgs[0].P - 2 * s;
+  const int wide = (int)cfgs.size() * std::max(round_up(s + r, vec), std::max(round_up(s, vec), vec));
+  if (wide > kMaxGroupWidth) {
+    set_error("shift group: %zu shifts of this block are %d columns, above %d", cfgs.size(), wide,
+              kMaxGroupWidth);
+    return LOGDET_EINVAL;
+  }
+  int rc;
+  if (cfgs[0].precision == LOGDET_FP64) rc = solve_shifts_t<double>(h, cfgs, st, outs);
+  else if (cfgs[0].precision == LOGDET_MIXED_BF16VEC) rc = solve_shifts_t<bf16>(h, cfgs, st, outs);
+  else rc = solve_shifts_t<float>(h, cfgs, st, outs);
+  if (rc) cudaStreamSynchronize(st);
+  return rc;
 }
 
 // The blocking path: one solve advanced step by step with batches of one.

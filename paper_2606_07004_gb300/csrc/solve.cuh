@@ -84,6 +84,7 @@ struct KRun {
   T* X0 = nullptr;
   T* Vfull = nullptr;
   const double* colshift = nullptr;  // optional [ld]: the scaled diagonal shift
+  const double* colscale = nullptr;  // optional [ld]: a factor per column after the shift
   logdet_ctx* hctx = nullptr;        // matrix handle (work items of irregular matrices)
   const void* gtab = nullptr;        // gridded operator: scaled expanded table (compute type)
   TileGeom g{};
@@ -184,6 +185,13 @@ size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c);
 
 // Run one solve to completion on its stream (the blocking API).
 int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& o);
+
+// Solves that differ only in shift and seed (same method, probes, steps,
+// window and precision), run in lockstep with their Krylov phases as one run
+// over a block of all their columns (at most kMaxGroupWidth); blocking.
+constexpr int kMaxGroupWidth = 1024;
+int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
+                 std::vector<SolveOut>& outs);
 
 // Queue every phase of a solve on its stream, with batches of one, until it
 // waits for its result copies; no host synchronisation (so the sequence can

@@ -1,0 +1,146 @@
+"""Shift groups (logdet_oslq_shifts / logdet_osaiop_shifts) through the C-ABI.
+
+Member t of a group is by definition the solve of log det(Q + shifts[t] I)
+with seed seed0 + t; the group only changes how its Krylov phases are run
+(one run over all members' columns, each column with its own diagonal shift
+and scale).  So:
+  - a group of one is bit-identical to the ordinary solve (the column scale
+    is exactly 1 and every sum keeps its order);
+  - in FP64 each member is within 1e-12 of its ordinary solve (one rounding
+    more per SpMM: (Q/c_0 + shift/c_0) x c_0/c_t) and within 1e-10 of the
+    oracle on Q + shift I;
+  - mixed FP32 members are within 1e-5 of their ordinary mixed solve on
+    well-conditioned operators, and within the 1e-4 mixed band of FP64;
+  - malformed groups are refused with EINVAL.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_07004_gb300 import binding as B  # noqa: E402
+
+
+def rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+def _single(h, method, P, m, k, seed, shift, **kw):
+    if method == 0:
+        return h.oslq(P, m, seed=seed, shift=shift, **kw)
+    return h.osaiop(P, m, iop_window=k, seed=seed, shift=shift, **kw)
+
+
+def _group(h, method, shifts, P, m, k, seed0, **kw):
+    if method == 0:
+        return h.oslq_shifts(shifts, P, m, seed0=seed0, **kw)
+    return h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=seed0, **kw)
+
+
+@pytest.mark.parametrize("method,k", [(0, 0), (1, 2), (1, 4)])
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED_FP32, B.MIXED_BF16VEC])
+@pytest.mark.parametrize("plain", [0, 1])
+def test_group_of_one_is_the_ordinary_solve(method, k, precision, plain):
+    A = W.laplacian_2d(61, 47, shift=0.0)
+    with B.Handle.from_csr(A) as h:
+        g = _group(h, method, [0.35], 31, 24, k, 5, precision=precision, plain=plain)
+        o = _single(h, method, 31, 24, k, 5, 0.35, precision=precision, plain=plain)
+    assert len(g) == 1
+    assert g[0].logdet == o.logdet
+    assert (g[0].tr_sub, g[0].tr_res, g[0].s_eff) == (o.tr_sub, o.tr_res, o.s_eff)
+    assert (g[0].steps_min, g[0].steps_max, g[0].status_bits) == (o.steps_min, o.steps_max,
+                                                                   o.status_bits)
+
+
+@pytest.mark.parametrize("method,k", [(0, 0), (1, 2), (1, 3)])
+@pytest.mark.parametrize("P", [30, 31])  # 31: FP64 block 21 columns wide, padded to 22
+def test_fp64_members_equal_their_own_solves_and_the_oracle(method, k, P):
+    A = W.laplacian_2d(45, 37, shift=0.0)
+    shifts = [0.05, 0.4, 1.0, 3.0]
+    m, seed0 = 25, 11
+    with B.Handle.from_csr(A) as h:
+        grp = _group(h, method, shifts, P, m, k, seed0)
+        own = [_single(h, method, P, m, k, seed0 + t, sh) for t, sh in enumerate(shifts)]
+    Q = A.to_scipy()
+    I = sp.identity(A.n, format="csr")
+    for t, sh in enumerate(shifts):
+        assert rel(grp[t].logdet, own[t].logdet) <= 1e-12, t
+        assert (grp[t].s_eff, grp[t].steps_max) == (own[t].s_eff, own[t].steps_max)
+        Qs = (Q + sh * I).tocsr()
+        est = (O.oslq(Qs, P, m, seed=seed0 + t) if method == 0
+               else O.osaiop(Qs, P, m, k=k, seed=seed0 + t))
+        assert rel(grp[t].logdet, est.logdet) <= 1e-10, t
+        # the exact value for orientation: a 1.7k-row Laplacian has it cheaply
+        exact = np.linalg.slogdet(Qs.toarray())[1]
+        assert rel(grp[t].logdet, exact) <= 5e-2
+
+
+@pytest.mark.parametrize("method,k", [(0, 0), (1, 4)])
+def test_mixed_members_within_1e5_of_their_own_and_1e4_of_fp64(method, k):
+    # m = 40 steps on a 2D Laplacian (n = 16384, padded FP32 sketch block:
+    # s = 21 of 24 columns) and 6 shifts: 6 x 44 = 264 block columns
+    A = W.laplacian_2d(128, shift=0.0)
+    shifts = [0.02, 0.05, 0.1, 0.3, 1.0, 2.5]
+    P, m, seed0 = 64, 40, 3
+    with B.Handle.from_csr(A) as h:
+        grp = _group(h, method, shifts, P, m, k, seed0, precision=B.MIXED_FP32)
+        own = [_single(h, method, P, m, k, seed0 + t, sh, precision=B.MIXED_FP32)
+               for t, sh in enumerate(shifts)]
+        g64 = _group(h, method, shifts, P, m, k, seed0)
+    for t in range(len(shifts)):
+        assert rel(grp[t].logdet, own[t].logdet) <= 1e-5, t
+        assert rel(grp[t].logdet, g64[t].logdet) <= 1e-4, t
+    assert np.all(np.diff([r.logdet for r in g64]) > 0)
+
+
+def test_irregular_graph_group_matches_own_solves():
+    # power-law graph Laplacian: the SpMM runs on work items (irregular rows)
+    A = W.powerlaw_graph_laplacian(30011, exponent=2.3, mean_degree=8.0, seed=4)
+    shifts = [1e-2, 3e-2, 1e-1]
+    P, m, k = 24, 30, 4
+    with B.Handle.from_csr(A) as h:
+        g64 = h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0)
+        o64 = [h.osaiop(P, m, iop_window=k, seed=t, shift=sh) for t, sh in enumerate(shifts)]
+        g32 = h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, precision=B.MIXED_FP32)
+    for t in range(len(shifts)):
+        assert rel(g64[t].logdet, o64[t].logdet) <= 1e-10, t
+        assert rel(g32[t].logdet, g64[t].logdet) <= 1e-3, t
+
+
+def test_group_reuses_nothing_between_calls():
+    A = W.laplacian_3d(14, shift=0.0)
+    with B.Handle.from_csr(A) as h:
+        a = h.oslq_shifts([0.1, 0.2], 12, 15, seed0=7)
+        b = h.oslq_shifts([0.1, 0.2], 12, 15, seed0=7)
+        c = h.oslq_shifts([0.2], 12, 15, seed0=8)
+    assert [r.logdet for r in a] == [r.logdet for r in b]
+    assert c[0].logdet == pytest.approx(a[1].logdet, rel=1e-12)
+
+
+def test_malformed_groups_refused():
+    A = W.laplacian_2d(20, shift=0.0)
+    with B.Handle.from_csr(A) as h:
+        with pytest.raises(B.LogdetError) as e:
+            h.oslq_shifts([], 12, 10)
+        assert e.value.code == B.EINVAL
+        with pytest.raises(B.LogdetError) as e:
+            h.oslq_shifts([0.1, -1.0], 12, 10)
+        assert e.value.code == B.EINVAL
+        with pytest.raises(B.LogdetError) as e:  # 24 x 44 = 1056 FP64 columns > 1024
+            h.osaiop_shifts(np.linspace(0.1, 1.0, 24), 64, 10, iop_window=2)
+        assert e.value.code == B.EINVAL
+        # 23 x 44 = 1012 columns is accepted
+        r = h.osaiop_shifts(np.linspace(0.1, 1.0, 23), 64, 4, iop_window=2)
+        assert len(r) == 23 and all(np.isfinite(x.logdet) for x in r)
+    with B.Handle.grid(24, 24, np.array([[4.5, -1.0], [-1.0, 0.0]])) as hg:
+        with pytest.raises(B.LogdetError) as e:
+            hg.oslq_shifts([0.1, 0.2], 12, 10)
+        assert e.value.code == B.EINVAL
