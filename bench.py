@@ -17,9 +17,9 @@ vectors, OSLQ m = 80, 120 probes; solves/s, error against the FP64 CUDA path,
 HBM roofline of the Krylov passes), serving (the continuous-batching
 configuration at a reduced request count: mixed batched server against plain
 FP64 one at a time, solves/s and p50/p99 latency) and irregular_batch (8
-shifts of a 2M-row power-law graph Laplacian advanced together, OSA-IOP
-m = 100, k = 4: batched against serial, error of the extreme shifts against
-FP64).
+shifts of a 2M-row power-law graph Laplacian, OSA-IOP m = 100, k = 4: as one
+shift group, through the server and one after the other; error of the
+extreme shifts against FP64).
 
 Under torchrun every rank solves its own copy of the workload (independent
 problems, no data-path collective: weak scaling); the barrier and the max over
@@ -812,11 +812,14 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     """Batched irregular workload: the Laplacian of a Chung-Lu power-law graph
     (n = 2,097,152, exponent 2.3, mean degree 8) with 8 diagonal shifts drawn
     uniformly from [1e-3, 1e-1]; OSA-IOP m = 100, k = 4, 64 probes per shift,
-    FP32 values and vectors.  The 8 shifted operators share the CSR and
-    advance together through the server (one launch per pass); compared with
-    the same 8 solves one after the other (bitwise equal), and each mixed
-    estimate with the FP64 CUDA path (same seed): every shift, or with
-    fp64_all False the smallest and the largest."""
+    FP32 values and vectors.  The 8 shifted operators share the CSR and run
+    three ways: as one shift group (logdet_osaiop_shifts: one Krylov run over
+    all 8 x 64 probe columns), through the server (8 solves advancing
+    together, one launch per pass) and one after the other.  The server
+    results are bitwise those of the serial solves; the group's agree to
+    rounding.  Each mixed estimate is compared with the FP64 CUDA path (same
+    seed): every shift, or with fp64_all False the smallest and the
+    largest."""
     import numpy as np
     import torch
     from paper_2606_07004_gb300 import binding as B
@@ -833,6 +836,17 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     budget = int(min(budget_gb * (1 << 30), 8 * need * 1.05))
     clocks = ClockSampler(torch.cuda.current_device(), "irregular")
     clocks.start()
+    # The same 8 solves as one shift group: one Krylov run over all 8 x 64
+    # probe columns, so each gather fetches the x row of every shift.  Timed
+    # first, after a short group that tunes its block widths: it grows the
+    # memory pool that the server and the serial solves then reuse.
+    h.osaiop_shifts(shifts, P, 10, iop_window=k, seed0=0, precision=B.MIXED_FP32,
+                    autotune=autotune)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    group = h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, precision=B.MIXED_FP32,
+                            autotune=autotune)
+    t_group = time.perf_counter() - t1
     with B.Server(budget, max_slots=8) as srv:
         srv.wait(srv.submit(h, B.METHOD_OSAIOP, P, 10, k, seed=0, precision=B.MIXED_FP32,
                             shift=float(shifts[0]), autotune=autotune))
@@ -852,6 +866,13 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     which = list(range(8)) if fp64_all else sorted({int(np.argmin(shifts)), int(np.argmax(shifts))})
     r64 = {t: h.osaiop(P, m, iop_window=k, seed=t, shift=float(shifts[t])) for t in which}
     errs = {t: abs(batched[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
+    gerrs = {t: abs(group[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
+    B.logdet_profile_reset()
+    B.logdet_profile_enable(True)
+    h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, precision=B.MIXED_FP32,
+                    autotune=autotune)
+    B.logdet_profile_enable(False)
+    gprof = B.profile_snapshot()
     # Device time per kernel class of one of the solves run alone.
     B.logdet_profile_reset()
     B.logdet_profile_enable(True)
@@ -864,8 +885,13 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
         "workload": "power-law graph Laplacian n=%d nnz=%d, 8 shifts U[1e-3,1e-1], OSA-IOP m=100 "
                     "k=4, 64 probes each, mixed FP32" % (A.n, A.nnz),
         "unit": UNIT,
-        "batched_solves_per_s": 8 / t_batched, "serial_solves_per_s": 8 / t_serial,
-        "batched_s": t_batched, "serial_s": t_serial,
+        "group_solves_per_s": 8 / t_group, "batched_solves_per_s": 8 / t_batched,
+        "serial_solves_per_s": 8 / t_serial,
+        "group_s": t_group, "batched_s": t_batched, "serial_s": t_serial,
+        "rel_err_group_mixed_vs_fp64": {f"shift_{t}": gerrs[t] for t in which},
+        "max_rel_diff_group_vs_serial": max(abs(a.logdet - b.logdet) / abs(b.logdet)
+                                            for a, b in zip(group, serial)),
+        "kernel_ms_group_8_solves": {k_: v["ms"] for k_, v in gprof.items()},
         "bitwise_equal_batched_vs_serial": all(a.logdet == b.logdet for a, b in zip(batched, serial)),
         "logdets": [r.logdet for r in batched], "shifts": list(map(float, shifts)),
         "rel_err_mixed_vs_fp64": {f"shift_{t}": errs[t] for t in which},

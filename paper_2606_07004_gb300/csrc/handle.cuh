@@ -50,6 +50,17 @@ struct DevBuf {
     release();
     count = std::max<size_t>(n, 1);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+    if (e == cudaErrorMemoryAllocation) {
+      // The pool keeps freed memory (release threshold: never); memory it
+      // holds unused in blocks of other sizes goes back once, then retry.
+      cudaGetLastError();
+      int dev = 0;
+      cudaMemPool_t pool;
+      if (cudaStreamSynchronize(st) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
+          cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+          cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
+        e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+    }
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();

@@ -355,6 +355,33 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
   spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
+// FP32 / BF16 blocks: the pass is bound by the latency of its dependent
+// loads (row range -> column indices -> gathers of x), so resident warps
+// count for more than registers.  A register cap that fits three 352-thread
+// CTAs per SM instead of two (two instead of one for the full window)
+// trades a few spilled accumulators for 50% more loads in flight.  Measured
+// on the 2M-row power-law graph, OSA-IOP m = 20, mixed FP32, SpMM time:
+// window 4 82.5 -> 55.5 ms (8-shift group 403 -> 282 ms), window 2
+// 58.4 -> 43.7 ms, window 8 176 -> 151 ms; a cap of 48 lost again (58.1 ms).
+// The same caps on the update pass lost (window 4 11.6 -> 13.0 ms, window 8
+// 26.4 -> 38.4 ms): it streams, and keeps its registers.  Register
+// allocation does not change the arithmetic: results are bitwise the same.
+template <int NDOT>
+constexpr int lo_spmm_regs() { return NDOT > 4 ? 88 : 56; }
+
+template <typename T, int NDOT>
+__global__ void __maxnreg__(lo_spmm_regs<NDOT>())
+    k_spmm_lo(const __grid_constant__ SpmmBatch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
+}
+
+template <typename T, int NDOT>
+constexpr auto spmm_kernel() {
+  if constexpr (std::is_same<T, double>::value) return k_spmm<T, NDOT>;
+  else return k_spmm_lo<T, NDOT>;
+}
+
 // ---------------------------------------------------------------------------
 // pass 2: out = ycoef*y - sum_i coef_i basis_i;  |out|^2 [; extra . out]
 //
@@ -1134,7 +1161,7 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   ProfScope prof(KC_SPMM, s, flops, bytes);
 #define LD_SPMM_CASE(ND)                                                      \
   {                                                                           \
-    auto kern = k_spmm<T, ND>;                                                \
+    auto kern = spmm_kernel<T, ND>();                                         \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
     kern<<<grid, threads, smem, s>>>(b);                                      \
     break;                                                                    \
