@@ -1091,7 +1091,9 @@ def small_case(args):
     --workload grf: one mixed-FP32 OSLQ solve (m=4, 30 probes) on the
     Wendland theta=50 gridded operator, 900 x 1200; with --workload
     multishift: one mixed-FP32 OSA-IOP solve (k=4, m=4, 64 probes, shift
-    0.01) on the 2M-row power-law graph Laplacian."""
+    0.01) on the 2M-row power-law graph Laplacian, then a shift group of 8
+    such solves (m=4) on the 512k-row graph of the same law (the group's
+    block is 8 x 44 columns wide; about 3 GB on the device)."""
     import torch
     from paper_2606_07004_gb300 import binding as B
     import workloads as W
@@ -1101,8 +1103,15 @@ def small_case(args):
                                        dtype=np.float32)
         with B.Handle.from_csr(A) as h:
             r = h.osaiop(64, 4, iop_window=4, seed=1, precision=B.MIXED_FP32, shift=0.01)
+        del A
+        A = W.powerlaw_graph_laplacian(2 ** 19, exponent=2.3, mean_degree=8.0, seed=7,
+                                       dtype=np.float32)
+        shifts = np.random.default_rng(11).uniform(1e-3, 1e-1, 8)
+        with B.Handle.from_csr(A) as h:
+            g = h.osaiop_shifts(shifts, 64, 4, iop_window=4, seed0=0, precision=B.MIXED_FP32)
         torch.cuda.synchronize()
-        print(json.dumps({"small_case": "multishift", "osaiop": r.logdet, "ms": r.device_ms}))
+        print(json.dumps({"small_case": "multishift", "osaiop": r.logdet, "ms": r.device_ms,
+                          "group_512k": [x.logdet for x in g], "group_ms": g[0].device_ms}))
         return 0
     if args.workload == "grf":
         from paper_2606_07004_gb300 import grf

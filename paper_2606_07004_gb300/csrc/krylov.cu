@@ -214,6 +214,17 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
       // accumulation order is the same either way.
       constexpr bool kPipe = !std::is_same<T, double>::value && NDOT <= 1;
       const T* xcol = J.x + col0;
+      // FP32 / BF16: the thread's column shift and scale converted from
+      // FP64 once per tile, not once per row (the conversion runs on the
+      // FP64 pipe: per row it kept that pipe 21-31 % busy).
+      CT csh[V], csc[V];
+      if constexpr (!std::is_same<T, double>::value) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          csh[v] = has_shift ? CT(J.colshift[col0 + v]) : CT(0);
+          csc[v] = has_scale ? CT(J.colscale[col0 + v]) : CT(1);
+        }
+      }
       int row = row0 + r;
       int q0 = 0, q1 = 0;
       if (kPipe && row < row1) {
@@ -315,8 +326,13 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           load_v<COH, T>(xcol + (size_t)row * J.ld, xr);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
-            if (has_shift) s[v] = fma(CT(J.colshift[col0 + v]), xr[v], s[v]);
-            if (has_scale) s[v] = s[v] * CT(J.colscale[col0 + v]);
+            if constexpr (std::is_same<T, double>::value) {
+              if (has_shift) s[v] = fma(CT(J.colshift[col0 + v]), xr[v], s[v]);
+              if (has_scale) s[v] = s[v] * CT(J.colscale[col0 + v]);
+            } else {
+              if (has_shift) s[v] = fma(csh[v], xr[v], s[v]);
+              if (has_scale) s[v] = s[v] * csc[v];
+            }
           }
         }
         store_vec<T>(J.y + (size_t)row * J.ld + col0, s);
