@@ -234,12 +234,16 @@ int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
  * group's device time.  opts->shift, opts->per_probe and opts->z_norm2 are
  * not used.  Results agree with the separate solves to rounding (one SpMM
  * per step computes (Q/c_0 + shift_t/c_0) x c_0/c_t instead of
- * (Q + shift_t) x / c_t).  Blocks until the results are on the host.
- * Device memory: about nshift times one solve's.  Errors: EINVAL (nshift < 1;
+ * (Q + shift_t) x / c_t); a member that runs alone is bit-identical to its
+ * separate solve.  The shifts go through in consecutive runs of equal size
+ * (the last one possibly smaller), as few as allow at most floor(1024 / w)
+ * members per run (w: one member's block width, num_probes -
+ * floor(num_probes/3) rounded up to 2 for FP64, 4 for FP32/BF16) and an
+ * estimated device memory (logdet_estimate_bytes per member) within 85 % of
+ * the device's; the split depends only on the shapes and the device.
+ * Blocks until the results are on the host.  Errors: EINVAL (nshift < 1;
  * NULL pointers; any member's configuration as logdet_oslq / logdet_osaiop;
- * a gridded operator; more than 1024 block columns in all: nshift times
- * num_probes - floor(num_probes/3) rounded up to 2 (FP64) or 4 (FP32/BF16)
- * columns), ENOTSPD, ENOMEM, ECUDA. */
+ * a gridded operator), ENOTSPD, ENOMEM, ECUDA. */
 int logdet_oslq_shifts(logdet_handle h, int32_t nshift, const double* shifts, int32_t num_probes,
                        int32_t krylov_steps, int32_t iop_window, uint64_t seed0,
                        const logdet_opts* opts, logdet_result* out);

@@ -1264,20 +1264,36 @@ int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t 
     return LOGDET_EINVAL;
   }
   for (const SolveCfg& c : cfgs) LD_TRY(validate_cfg(h, c));
+  // Members per run: at most kMaxGroupWidth block columns, and (about R
+  // solves' device memory) at most 85 % of the device's memory.  The split
+  // depends only on the shapes and the device, so results do not depend on
+  // what else is allocated.
   const int vec = cfgs[0].precision == LOGDET_FP64 ? 2 : 4;
   const int s = cfgs[0].plain ? 0 : cfgs[0].P / 3, r = cfgs[0].plain ? cfgs[0].P : cfgs[0].P - 2 * s;
-  const int wide = (int)cfgs.size() * std::max(round_up(s + r, vec), std::max(round_up(s, vec), vec));
-  if (wide > kMaxGroupWidth) {
-    set_error("shift group: %zu shifts of this block are %d columns, above %d", cfgs.size(), wide,
-              kMaxGroupWidth);
-    return LOGDET_EINVAL;
+  const int width = std::max(round_up(s + r, vec), std::max(round_up(s, vec), vec));
+  size_t free_b = 0, total_b = 0;
+  LD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const size_t each = estimate_solve_bytes(h, cfgs[0]);
+  const size_t by_mem = std::max<size_t>(1, (size_t)(0.85 * (double)total_b) / std::max<size_t>(each, 1));
+  const int cap = (int)std::max<size_t>(1, std::min<size_t>(kMaxGroupWidth / width, by_mem));
+  const int runs = div_up((int)cfgs.size(), cap);
+  const int per_run = div_up((int)cfgs.size(), runs);  // balanced runs
+  outs.clear();
+  for (size_t t0 = 0; t0 < cfgs.size(); t0 += per_run) {
+    const std::vector<SolveCfg> part(cfgs.begin() + t0,
+                                     cfgs.begin() + std::min(cfgs.size(), t0 + per_run));
+    std::vector<SolveOut> po;
+    int rc;
+    if (cfgs[0].precision == LOGDET_FP64) rc = solve_shifts_t<double>(h, part, st, po);
+    else if (cfgs[0].precision == LOGDET_MIXED_BF16VEC) rc = solve_shifts_t<bf16>(h, part, st, po);
+    else rc = solve_shifts_t<float>(h, part, st, po);
+    if (rc) {
+      cudaStreamSynchronize(st);
+      return rc;
+    }
+    for (SolveOut& o : po) outs.push_back(std::move(o));
   }
-  int rc;
-  if (cfgs[0].precision == LOGDET_FP64) rc = solve_shifts_t<double>(h, cfgs, st, outs);
-  else if (cfgs[0].precision == LOGDET_MIXED_BF16VEC) rc = solve_shifts_t<bf16>(h, cfgs, st, outs);
-  else rc = solve_shifts_t<float>(h, cfgs, st, outs);
-  if (rc) cudaStreamSynchronize(st);
-  return rc;
+  return LOGDET_OK;
 }
 
 // The blocking path: one solve advanced step by step with batches of one.

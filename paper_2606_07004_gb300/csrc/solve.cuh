@@ -188,7 +188,8 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
 
 // Solves that differ only in shift and seed (same method, probes, steps,
 // window and precision), run in lockstep with their Krylov phases as one run
-// over a block of all their columns (at most kMaxGroupWidth); blocking.
+// over a block of all their columns; blocking.  Members go in balanced runs
+// of at most kMaxGroupWidth block columns and 85 % of the device's memory.
 constexpr int kMaxGroupWidth = 1024;
 int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
                  std::vector<SolveOut>& outs);

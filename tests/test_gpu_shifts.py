@@ -134,13 +134,23 @@ def test_malformed_groups_refused():
         with pytest.raises(B.LogdetError) as e:
             h.oslq_shifts([0.1, -1.0], 12, 10)
         assert e.value.code == B.EINVAL
-        with pytest.raises(B.LogdetError) as e:  # 24 x 44 = 1056 FP64 columns > 1024
-            h.osaiop_shifts(np.linspace(0.1, 1.0, 24), 64, 10, iop_window=2)
-        assert e.value.code == B.EINVAL
-        # 23 x 44 = 1012 columns is accepted
-        r = h.osaiop_shifts(np.linspace(0.1, 1.0, 23), 64, 4, iop_window=2)
-        assert len(r) == 23 and all(np.isfinite(x.logdet) for x in r)
     with B.Handle.grid(24, 24, np.array([[4.5, -1.0], [-1.0, 0.0]])) as hg:
         with pytest.raises(B.LogdetError) as e:
             hg.oslq_shifts([0.1, 0.2], 12, 10)
         assert e.value.code == B.EINVAL
+
+
+@pytest.mark.parametrize("nshift", [23, 24, 47])
+def test_wide_groups_split_into_runs(nshift):
+    # 44 FP64 block columns per member and at most 1024 per run: 23 shifts
+    # run together (1012 columns, the widest tile geometry), 24 as two runs
+    # of 12, 47 as 16 + 16 + 15
+    A = W.laplacian_2d(20, shift=0.0)
+    shifts = np.linspace(0.1, 1.0, nshift)
+    with B.Handle.from_csr(A) as h:
+        r = h.osaiop_shifts(shifts, 64, 6, iop_window=2, seed0=5)
+        own = [h.osaiop(64, 6, iop_window=2, seed=5 + t, shift=float(sh))
+               for t, sh in enumerate(shifts)]
+    assert len(r) == nshift
+    for t in range(nshift):
+        assert rel(r[t].logdet, own[t].logdet) <= 1e-12, t
