@@ -1251,56 +1251,119 @@ template int convert_block<bf16, double>(const bf16*, int, double*, int, int, in
 // ===========================================================================
 // OSA-IOP sketch assembly: Y[:, p] = sum_j w[j][p] V_j[:, p]
 // ===========================================================================
-template <typename T>
-__global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ld, int m,
+// Thread-level work: one vector chunk (Vec16<T>::N columns) of one row, the
+// m basis blocks read four at a time (independent loads in flight), each
+// column's sum over j in increasing order.  V has row stride ldv and block
+// stride n * ldv; columns [0, ncols) are assembled (ncols and ldv multiples
+// of N, V aligned to the chunk).
+//
+// FP64 blocks: FP64 fused multiply-adds, w read as vectors.  FP32 / BF16
+// blocks: the FP64 pipe of this GPU (1/64 of the FP32 rate) would bound the
+// kernel at m n ncols FMAs, so each sum runs in double-float arithmetic on
+// the FP32 pipe instead: w_j split once per CTA into hi + lo floats (shared
+// memory), the product with x (exact in hi: an FMA gives its rounding
+// error) added by an error-free two-sum into a (hi, lo) pair; relative error
+// about 2^-44 per sum, returned as hi + lo in FP64.  (Tables of more than
+// kSketchSmemW weights, m ncols > 4096, take the FP64 form.)
+constexpr int kSketchSmemW = 4096;
+
+template <typename T, bool kDF>
+__global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ncols, int ldv, int m,
                                   const double* __restrict__ w, double* __restrict__ Y,
                                   int ldy) {
-  const size_t total = (size_t)n * ld;
-  const size_t stride_v = (size_t)n * ld;
+  constexpr int N = Vec16<T>::N;
+  using CT = typename Compute<T>::type;
+  __shared__ float2 sw[kDF ? kSketchSmemW : 1];
+  if constexpr (kDF) {
+    for (int i = threadIdx.x; i < m * ncols; i += blockDim.x) {
+      const double x = w[i];
+      const float hi = (float)x;
+      sw[i] = make_float2(hi, (float)(x - (double)hi));
+    }
+    __syncthreads();
+  }
+  const int chunks = ncols / N;
+  const size_t total = (size_t)n * chunks;
+  const size_t stride_v = (size_t)n * ldv;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
-    int row = (int)(e / ld), p = (int)(e - (size_t)row * ld);
-    double acc = 0.0;
-    for (int j = 0; j < m; ++j)
-      acc = fma(w[(size_t)j * ld + p], cvt<double>(V[j * stride_v + e]), acc);
-    if (p < ldy) Y[(size_t)row * ldy + p] = acc;
+    const int row = (int)(e / chunks), p0 = (int)(e - (size_t)row * chunks) * N;
+    const T* v0 = V + (size_t)row * ldv + p0;
+    double acc[N];
+    float sh[N], sl[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) acc[c] = 0.0, sh[c] = 0.f, sl[c] = 0.f;
+    auto term = [&](int j, const CT (&x)[N]) {
+      if constexpr (kDF) {
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+          const float2 wj = sw[j * ncols + p0 + c];
+          const float p = wj.x * x[c];
+          float pe = fmaf(wj.x, x[c], -p);
+          pe = fmaf(wj.y, x[c], pe);
+          const float t = sh[c] + p;
+          const float z = t - sh[c];
+          const float err = (sh[c] - (t - z)) + (p - z);
+          sl[c] += err + pe;
+          sh[c] = t;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < N; c += 2) {
+          const double2 wv = *reinterpret_cast<const double2*>(w + (size_t)j * ncols + p0 + c);
+          acc[c] = fma(wv.x, (double)x[c], acc[c]);
+          acc[c + 1] = fma(wv.y, (double)x[c + 1], acc[c + 1]);
+        }
+      }
+    };
+    int j = 0;
+    for (; j + 4 <= m; j += 4) {
+      CT x[4][N];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) load_vec<T>(v0 + (size_t)(j + u) * stride_v, x[u]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) term(j + u, x[u]);
+    }
+    for (; j < m; ++j) {
+      CT x[N];
+      load_vec<T>(v0 + (size_t)j * stride_v, x);
+      term(j, x);
+    }
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+      if constexpr (kDF) acc[c] = (double)sh[c] + (double)sl[c];
+      if (p0 + c < ldy) Y[(size_t)row * ldy + p0 + c] = acc[c];
+    }
   }
 }
 
 template <typename T>
 int sketch_assemble(const T* V, int n, int ld, int m, const double* w, double* Y, int ldy,
                     cudaStream_t st) {
-  ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ld * m, (double)n * ld * (m * sizeof(T) + 8.0));
-  k_sketch_assemble<T><<<8 * sm_count(), 256, 0, st>>>(V, n, ld, m, w, Y, ldy);
-  LD_CHECK_LAUNCH();
-  return LOGDET_OK;
-}
-// The same for ncols columns of basis blocks with leading dimension ldv (a
-// column slice of a wider basis): Y[:, p] = sum_j w[j][p] V_j[:, p], p < ncols,
-// each element's sum in the order above.
-template <typename T>
-__global__ void k_sketch_assemble_cols(const T* __restrict__ V, int n, int ncols, int ldv, int m,
-                                       const double* __restrict__ w, double* __restrict__ Y,
-                                       int ldy) {
-  const size_t total = (size_t)n * ncols;
-  const size_t stride_v = (size_t)n * ldv;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    int row = (int)(e / ncols), p = (int)(e - (size_t)row * ncols);
-    const size_t ve = (size_t)row * ldv + p;
-    double acc = 0.0;
-    for (int j = 0; j < m; ++j)
-      acc = fma(w[(size_t)j * ncols + p], cvt<double>(V[j * stride_v + ve]), acc);
-    if (p < ldy) Y[(size_t)row * ldy + p] = acc;
-  }
+  return sketch_assemble_cols<T>(V, n, ld, ld, m, w, Y, ldy, st);
 }
 
+// The same for ncols columns of basis blocks with leading dimension ldv (a
+// column slice of a wider basis).
 template <typename T>
 int sketch_assemble_cols(const T* V, int n, int ncols, int ldv, int m, const double* w, double* Y,
                          int ldy, cudaStream_t st) {
+  constexpr uintptr_t kAlign = sizeof(typename Vec16<T>::type);
+  if (ncols % Vec16<T>::N || ldv % Vec16<T>::N || (reinterpret_cast<uintptr_t>(V) % kAlign)) {
+    set_error("sketch assembly: columns %d / stride %d not in whole vector chunks", ncols, ldv);
+    return LOGDET_EINVAL;
+  }
   ProfScope prof(KC_OTHER, st, 2.0 * n * (double)ncols * m,
                  (double)n * ncols * (m * sizeof(T) + 8.0));
-  k_sketch_assemble_cols<T><<<8 * sm_count(), 256, 0, st>>>(V, n, ncols, ldv, m, w, Y, ldy);
+  bool launched = false;
+  if constexpr (!std::is_same<T, double>::value) {
+    if ((size_t)m * ncols <= (size_t)kSketchSmemW) {
+      k_sketch_assemble<T, true><<<8 * sm_count(), 256, 0, st>>>(V, n, ncols, ldv, m, w, Y, ldy);
+      launched = true;
+    }
+  }
+  if (!launched)
+    k_sketch_assemble<T, false><<<8 * sm_count(), 256, 0, st>>>(V, n, ncols, ldv, m, w, Y, ldy);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
