@@ -28,7 +28,13 @@ namespace ld {
 
 constexpr int kMaxWin = 9;    // window vectors per pass (window k <= 8, plus slack)
 constexpr int kMaxJobs = 24;  // jobs per batched launch
-constexpr int kSplitRowNnz = 64;  // rows longer than this are split across a whole CTA
+// Rows longer than this are split across a whole CTA.  Measured on the
+// 2M-row power-law graph (SpMM, OSA-IOP m = 20, FP32, window 4): threshold
+// 64 (24k split rows) 55.8 ms, 128 46.2, 256 43.3, 512 43.0, 1024 48.8,
+// 2048 59.2; window 8 151.9 -> 108.7 ms and FP64 138.1 -> 114.1 ms at 256:
+// each split row pays two CTA barriers and its item's dot reduction, while
+// a row of up to 256 entries takes 64 four-gather batches in one row group.
+constexpr int kSplitRowNnz = 256;
 constexpr int kRedThreads = 256;  // threads of one scalar reduction (a k_scalar CTA)
 
 // ---------------------------------------------------------------------------

@@ -1,5 +1,5 @@
 """Matrices with long rows (irregular sparsity): rows longer than the split
-threshold (64 stored entries) are SpMM work items of their own, shared by a
+threshold (256 stored entries) are SpMM work items of their own, shared by a
 whole CTA, and the remaining rows are cut into ranges of bounded work.
 Checks: integer SpMM bit-exact against scipy, FP64 estimates against the
 oracle at the FP64 bar, the mixed path against FP64, and the autotuned
@@ -51,13 +51,16 @@ def grid_plus_weak_hubs(nx, ny, hubs, seed, shift, w):
 CASES = {
     # one hub joined to every other node: a row of n entries
     "star": lambda: hubs_and_ring(3001, [(0, 3000)], 1, 0.05),
-    # rows right at the threshold: rows 5 and 2048 hold 65 entries (split),
-    # row 700 holds 64 (not split), row 4086 holds 203.  (A ring plus unit hubs
+    # rows right at the threshold: rows 5 and 2048 hold 257 entries (split),
+    # row 700 holds 256 (not split), row 4086 holds 802.  (A ring plus unit hubs
     # is far more rounding-sensitive: the oracle alone moves by 6e-7 between
     # two dot summation orders; with weak hub edges it moves by 4e-16.)
-    "threshold": lambda: grid_plus_weak_hubs(67, 61, [(5, 61), (700, 59), (2048, 60), (4086, 200)],
-                                             2, 0.1, 1e-2),
+    "threshold": lambda: grid_plus_weak_hubs(67, 61, [(5, 253), (700, 252), (2048, 251),
+                                                      (4086, 800)], 2, 0.1, 1e-2),
+    # largest row 214 entries: no work items (uniform tiles)
     "powerlaw": lambda: W.powerlaw_graph_laplacian(7001, seed=9).with_diagonal_shift(0.02),
+    # 35 rows above the threshold (largest 459 entries)
+    "powerlaw30k": lambda: W.powerlaw_graph_laplacian(30011, seed=4).with_diagonal_shift(0.02),
 }
 
 
@@ -92,7 +95,7 @@ def test_long_rows_fp64_parity(name, method, k):
     np.testing.assert_allclose(res.per_probe, est.per_probe, rtol=1e-9, atol=1e-9)
 
 
-@pytest.mark.parametrize("name", ["star", "powerlaw"])
+@pytest.mark.parametrize("name", ["star", "powerlaw", "powerlaw30k"])
 def test_long_rows_mixed_and_autotuned(name):
     A = CASES[name]()
     with B.Handle.from_csr(A) as h:

@@ -154,3 +154,32 @@ def test_wide_groups_split_into_runs(nshift):
     assert len(r) == nshift
     for t in range(nshift):
         assert rel(r[t].logdet, own[t].logdet) <= 1e-12, t
+
+
+@pytest.mark.parametrize("method,k", [(0, 0), (1, 2)])
+def test_group_breakdown_and_tiny_matrices(method, k):
+    # identity: every probe breaks down after one step, in every member
+    A = W.scaled_identity(300, 2.5)
+    shifts = [0.0, 0.5, 4.0]
+    with B.Handle.from_csr(A) as h:
+        g = _group(h, method, shifts, 9, 10, k, 0)
+    for t, sh in enumerate(shifts):
+        assert g[t].steps_max == 1 and g[t].status_bits & B.ST_BREAKDOWN
+        assert g[t].logdet == pytest.approx(300 * np.log(2.5 + sh), rel=1e-13)
+    # 5 distinct diagonal values: every run breaks down at the distinct count
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 7.0], 40)
+    A = W.diagonal_matrix(d)
+    with B.Handle.from_csr(A) as h:
+        g = _group(h, method, shifts, 12, 8, k, 2)
+        own = [_single(h, method, 12, 8, k, 2 + t, sh) for t, sh in enumerate(shifts)]
+    for t, sh in enumerate(shifts):
+        assert rel(g[t].logdet, own[t].logdet) <= 1e-12
+        assert (g[t].steps_max, g[t].status_bits) == (own[t].steps_max, own[t].status_bits)
+    # n = 9 with 29 probes: the sketch has rank n, the residual vanishes
+    A = W.laplacian_2d(3, shift=1.0)
+    with B.Handle.from_csr(A) as h:
+        g = _group(h, method, shifts, 29, 7, k, 1)
+        own = [_single(h, method, 29, 7, k, 1 + t, sh) for t, sh in enumerate(shifts)]
+    for t in range(len(shifts)):
+        assert g[t].s_eff == own[t].s_eff
+        assert rel(g[t].logdet, own[t].logdet) <= 1e-12
