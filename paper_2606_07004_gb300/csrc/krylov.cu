@@ -62,6 +62,17 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
 
+// Programmatic dependent launch of the step kernels: a step kernel may be
+// launched while its predecessor in the stream still runs (its CTAs get
+// resident early, which hides the launch latency of small steps).  On entry
+// it waits for the predecessor grid to complete and its writes to be
+// visible, then lets its own successor launch.  A launch without the
+// attribute, or after a kernel that does not trigger, orders as usual.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Vector load of block data: through the non-coherent path for the step
 // kernels (the block is read-only while they run), through L2 only (.cg)
 // when COH, for the persistent run, whose blocks other CTAs write between
@@ -368,6 +379,7 @@ template <typename T, int NDOT>
 __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
     k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_entry();
   spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
@@ -389,6 +401,7 @@ template <typename T, int NDOT>
 __global__ void __maxnreg__(lo_spmm_regs<NDOT>())
     k_spmm_lo(const __grid_constant__ SpmmBatch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_entry();
   spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
@@ -636,6 +649,7 @@ template <typename T, int NB, bool EX>
 __global__ void __launch_bounds__(512, update_min_ctas<T, NB>())
     k_update(const __grid_constant__ UpdBatch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_entry();
   update_tiles<T, NB, EX>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
@@ -822,6 +836,7 @@ __global__ void __launch_bounds__(kRedThreads) k_scalar(const __grid_constant__ 
                                                         int kind, int f32) {
   __shared__ AccD shd[kRedThreads];
   __shared__ AccF shf[kRedThreads];
+  pdl_entry();
   if (f32) scalar_body<AccF, float2>(B, kind, shf);
   else scalar_body<AccD, double>(B, kind, shd);
 }
@@ -1159,6 +1174,23 @@ static int persistent_grid(K kernel, int threads, size_t smem, int total_tiles) 
   return std::max(1, std::min(total_tiles, per_sm * sm_count()));
 }
 
+// Launch with programmatic stream serialization (see pdl_entry).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T>
 int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   int nd = 0;
@@ -1179,7 +1211,7 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   {                                                                           \
     auto kern = spmm_kernel<T, ND>();                                         \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
-    kern<<<grid, threads, smem, s>>>(b);                                      \
+    launch_pdl(kern, dim3(grid), dim3(threads), smem, s, b);                  \
     break;                                                                    \
   }
   do {
@@ -1217,7 +1249,7 @@ int launch_update(const UpdBatch<T>& b, int threads, cudaStream_t s) {
   {                                                                           \
     auto kern = ex ? k_update<T, NB, true> : k_update<T, NB, false>;          \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
-    kern<<<grid, threads, smem, s>>>(b);                                      \
+    launch_pdl(kern, dim3(grid), dim3(threads), smem, s, b);                  \
     break;                                                                    \
   }
   do {
@@ -1298,7 +1330,7 @@ static int launch_scalar(const ScalarBatch& b, int kind, cudaStream_t s) {
   int nd = 1, f32 = b.jobs[0].part_f32;
   for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
   ProfScope prof(KC_SCALAR, s);
-  k_scalar<<<dim3(total_probes(b), nd), kRedThreads, 0, s>>>(b, kind, f32);
+  launch_pdl(k_scalar, dim3(total_probes(b), nd), dim3(kRedThreads), 0, s, b, kind, f32);
   LD_CHECK_LAUNCH();
   return LOGDET_OK;
 }
