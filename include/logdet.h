@@ -379,6 +379,9 @@ typedef struct {
   int64_t batched_steps;  /* request-steps advanced by batched launches */
   size_t bytes_in_use, bytes_budget;
   double busy_ms;         /* scheduler time spent issuing work */
+  int64_t suspended;      /* requests held by logdet_suspend now */
+  int64_t suspensions;    /* suspensions so far */
+  int64_t suspended_in_krylov; /* of those, taken in the middle of a Krylov phase */
 } logdet_stats;
 int logdet_server_create(size_t device_mem_budget, int32_t max_slots, void* cuda_stream,
                          logdet_server** out);
@@ -391,6 +394,22 @@ int logdet_wait(logdet_server* s, uint64_t req_id, int64_t timeout_us, logdet_re
 int logdet_cancel(logdet_server* s, uint64_t req_id);
 int logdet_release(logdet_server* s, uint64_t req_id);
 int logdet_server_stats(logdet_server* s, logdet_stats* out);
+/* logdet_suspend: preemption.  A queued request leaves the queue; a running
+ *   one leaves the batch at the next tick boundary (unless its result is
+ *   already being copied out, in which case it just finishes): the scheduler
+ *   waits for the server's stream, copies every device buffer of the solve
+ *   (Krylov blocks, window ring, scalar state, sketch) to host memory and
+ *   frees them, so its slot and budget go to other requests.  poll / wait
+ *   report LOGDET_PENDING meanwhile.  Returns at once.  Errors: ENOENT,
+ *   EINVAL (finished, failed or cancelled).
+ * logdet_resume: puts a suspended request at the front of the queue; when
+ *   admitted again its buffers are reallocated and filled from the host copy
+ *   and it continues from the step where it stopped.  Its result is
+ *   bit-identical to an uninterrupted run.  Resuming a running request whose
+ *   suspension has not happened yet withdraws it.  Errors: ENOENT, EINVAL
+ *   (not suspended).  logdet_cancel also ends a suspended request. */
+int logdet_suspend(logdet_server* s, uint64_t req_id);
+int logdet_resume(logdet_server* s, uint64_t req_id);
 
 /* ---- graph plans (the paper has no counterpart: a deployment variant of
  * Algorithms 2 and 3 for repeated estimates of one shape) -------------------

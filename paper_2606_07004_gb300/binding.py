@@ -44,7 +44,7 @@ EXPORTED = [
     "logdet_estimate_bytes", "logdet_server_create", "logdet_server_destroy", "logdet_submit", "logdet_poll",
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
-    "logdet_oslq_shifts", "logdet_osaiop_shifts",
+    "logdet_oslq_shifts", "logdet_osaiop_shifts", "logdet_suspend", "logdet_resume",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
@@ -66,7 +66,8 @@ class logdet_server_stats(C.Structure):
         ("failed", C.c_int64), ("cancelled", C.c_int64), ("queued", C.c_int64),
         ("resident", C.c_int64), ("max_resident", C.c_int64), ("ticks", C.c_int64),
         ("batched_steps", C.c_int64), ("bytes_in_use", C.c_size_t), ("bytes_budget", C.c_size_t),
-        ("busy_ms", C.c_double),
+        ("busy_ms", C.c_double), ("suspended", C.c_int64), ("suspensions", C.c_int64),
+        ("suspended_in_krylov", C.c_int64),
     ]
 
 
@@ -130,6 +131,8 @@ _sig("logdet_submit", C.c_int, [_P, _P, _i32, _i32, _i32, _i32, _u64, C.POINTER(
 _sig("logdet_poll", C.c_int, [_P, _u64, C.POINTER(logdet_result)])
 _sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
 _sig("logdet_cancel", C.c_int, [_P, _u64])
+_sig("logdet_suspend", C.c_int, [_P, _u64])
+_sig("logdet_resume", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
 _sig("logdet_server_stats", C.c_int, [_P, C.POINTER(logdet_server_stats)])
 _sig("logdet_plan_create", C.c_int, [_P, _i32, _i32, _i32, _i32, C.POINTER(logdet_opts),
@@ -482,6 +485,14 @@ class Server:
 
     def cancel(self, rid: int):
         _check(_lib.logdet_cancel(self._s, rid), "logdet_cancel")
+
+    def suspend(self, rid: int):
+        """Preempt a request: its device state moves to host memory (logdet_suspend)."""
+        _check(_lib.logdet_suspend(self._s, rid), "logdet_suspend")
+
+    def resume(self, rid: int):
+        """Re-queue a suspended request at the front (logdet_resume)."""
+        _check(_lib.logdet_resume(self._s, rid), "logdet_resume")
 
     def release(self, rid: int):
         _check(_lib.logdet_release(self._s, rid), "logdet_release")

@@ -33,7 +33,7 @@ static double now_us() {
   return duration_cast<duration<double, std::micro>>(steady_clock::now().time_since_epoch()).count();
 }
 
-enum ReqState { RQ_QUEUED = 0, RQ_RUNNING, RQ_DONE, RQ_FAILED, RQ_CANCELLED };
+enum ReqState { RQ_QUEUED = 0, RQ_RUNNING, RQ_DONE, RQ_FAILED, RQ_CANCELLED, RQ_SUSPENDED };
 
 struct Request {
   uint64_t id = 0;
@@ -46,6 +46,7 @@ struct Request {
   int rc = LOGDET_OK;
   size_t bytes = 0;
   bool cancel = false;
+  bool suspend = false;   // logdet_suspend asked; the scheduler acts at a tick boundary
   double t_submit = 0, t_admit = 0, t_done = 0;
   SolveOut out;
 };
@@ -73,6 +74,8 @@ struct logdet_server {
   // statistics
   int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_failed = 0, n_cancelled = 0;
   int64_t n_ticks = 0, n_batched_steps = 0, max_resident = 0;
+  int64_t n_suspensions = 0, n_suspended_in_krylov = 0;
+  std::vector<std::shared_ptr<Request>> held;  // suspended requests
   double busy_us = 0.0;
 
   void loop();
@@ -228,24 +231,51 @@ void logdet_server::loop() {
         cv_work.wait_for(lk, std::chrono::milliseconds(20));
         continue;
       }
-      // Running requests that were cancelled leave at the tick boundary.
+      // Running requests that were cancelled leave at the tick boundary;
+      // suspended ones leave with their state copied to host memory (a
+      // request whose result copies are in flight finishes instead).
       for (size_t i = 0; i < active.size();) {
-        if (active[i]->cancel) {
-          complete(active[i], RQ_CANCELLED, LOGDET_ECANCEL);
+        auto& r = active[i];
+        if (r->cancel) {
+          complete(r, RQ_CANCELLED, LOGDET_ECANCEL);
           active.erase(active.begin() + i);
-        } else {
-          ++i;
+          continue;
         }
+        if (r->suspend && !r->rc && (!r->solve || r->solve->phase() != PH_WAIT)) {
+          r->suspend = false;
+          const bool mid_krylov = r->solve && r->solve->in_krylov();
+          const int src = r->solve ? r->solve->suspend() : LOGDET_OK;
+          if (src) {
+            r->rc = src;
+            ++i;
+            continue;
+          }
+          used -= r->bytes;
+          r->state = RQ_SUSPENDED;
+          held.push_back(r);
+          ++n_suspensions;
+          if (mid_krylov) ++n_suspended_in_krylov;
+          active.erase(active.begin() + i);
+          cv_done.notify_all();
+          continue;
+        }
+        r->suspend = false;
+        ++i;
       }
+      if (active.empty()) continue;
       act = active;
     }
     const double t0 = now_us();
-    // Solves for newly admitted requests (allocation happens in their SETUP phase).
+    // Solves for newly admitted requests (allocation happens in their SETUP
+    // phase); resumed requests get their device state back.
     for (auto& r : act) {
       if (!r->solve && !r->rc) {
         int rc = LOGDET_OK;
         r->solve = make_solve(r->h, r->cfg, st, &rc);
         if (!r->solve) r->rc = rc ? rc : LOGDET_EINVAL;
+      } else if (r->solve && r->solve->suspended() && !r->rc) {
+        const int rc = r->solve->resume();
+        if (rc) r->rc = rc;
       }
     }
     int rc = tick(act);
@@ -349,6 +379,12 @@ void logdet_server_destroy(logdet_server* s) {
       ++s->n_cancelled;
     }
     s->queue.clear();
+    for (auto& r : s->held) {
+      r->state = RQ_CANCELLED;
+      r->solve.reset();
+      ++s->n_cancelled;
+    }
+    s->held.clear();
     s->stop = true;
   }
   s->cv_work.notify_all();
@@ -369,20 +405,8 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
   auto r = std::make_shared<Request>();
   r->h = h;
   SolveCfg& c = r->cfg;
-  c.method = method;
-  c.P = num_probes;
-  c.m = krylov_steps;
-  c.k = iop_window;
-  c.seed = seed;
+  c = make_solve_cfg(method, num_probes, krylov_steps, iop_window, seed, opts);
   if (opts) {
-    c.precision = opts->precision;
-    c.tol = opts->tol > 0.0 ? opts->tol : kDefaultTol;
-    c.lam_lo = opts->lambda_lo;
-    c.lam_hi = opts->lambda_hi;
-    c.shift = opts->shift;
-    c.autotune = opts->autotune;
-    c.plain = opts->plain_slq;
-    c.gaussian = opts->gaussian_probes;
     r->user_per_probe = opts->per_probe;
     r->user_zn2 = opts->z_norm2;
   }
@@ -412,20 +436,7 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
 int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes, int32_t krylov_steps,
                           int32_t iop_window, const logdet_opts* opts, size_t* bytes) {
   if (!h || !bytes) { set_error("estimate_bytes: NULL argument"); return LOGDET_EINVAL; }
-  SolveCfg c;
-  c.method = method;
-  c.P = num_probes;
-  c.m = krylov_steps;
-  c.k = iop_window;
-  if (opts) {
-    c.precision = opts->precision;
-    c.lam_lo = opts->lambda_lo;
-    c.lam_hi = opts->lambda_hi;
-    c.shift = opts->shift;
-    c.autotune = opts->autotune;
-    c.plain = opts->plain_slq;
-    c.gaussian = opts->gaussian_probes;
-  }
+  const SolveCfg c = make_solve_cfg(method, num_probes, krylov_steps, iop_window, 0, opts);
   LD_TRY(validate_cfg(h, c));
   *bytes = estimate_solve_bytes(h, c);
   return LOGDET_OK;
@@ -434,7 +445,8 @@ int logdet_estimate_bytes(logdet_handle h, int32_t method, int32_t num_probes, i
 static int result_of(const std::shared_ptr<Request>& r, logdet_result* out) {
   switch (r->state) {
     case RQ_QUEUED:
-    case RQ_RUNNING: return LOGDET_PENDING;
+    case RQ_RUNNING:
+    case RQ_SUSPENDED: return LOGDET_PENDING;
     case RQ_DONE:
       if (out) *out = r->out.res;
       return LOGDET_OK;
@@ -457,7 +469,9 @@ int logdet_wait(logdet_server* s, uint64_t id, int64_t timeout_us, logdet_result
   auto it = s->all.find(id);
   if (it == s->all.end()) { set_error("wait: unknown request %llu", (unsigned long long)id); return LOGDET_ENOENT; }
   auto r = it->second;
-  auto pending = [&] { return r->state == RQ_QUEUED || r->state == RQ_RUNNING; };
+  auto pending = [&] {
+    return r->state == RQ_QUEUED || r->state == RQ_RUNNING || r->state == RQ_SUSPENDED;
+  };
   if (timeout_us < 0) {
     s->cv_done.wait(lk, [&] { return !pending() || s->stop; });
   } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return !pending(); })) {
@@ -473,7 +487,19 @@ int logdet_cancel(logdet_server* s, uint64_t id) {
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->all.find(id);
     if (it == s->all.end()) { set_error("cancel: unknown request"); return LOGDET_ENOENT; }
-    it->second->cancel = true;
+    auto r = it->second;
+    r->cancel = true;
+    if (r->state == RQ_SUSPENDED) {  // held: no slot and no budget to give back
+      for (size_t i = 0; i < s->held.size(); ++i)
+        if (s->held[i] == r) {
+          s->held.erase(s->held.begin() + i);
+          break;
+        }
+      r->state = RQ_CANCELLED;
+      r->solve.reset();
+      ++s->n_cancelled;
+      s->cv_done.notify_all();
+    }
   }
   s->cv_work.notify_all();
   return LOGDET_OK;
@@ -485,8 +511,66 @@ int logdet_release(logdet_server* s, uint64_t id) {
   auto it = s->all.find(id);
   if (it == s->all.end()) { set_error("release: unknown request"); return LOGDET_ENOENT; }
   const int st = it->second->state;
-  if (st == RQ_QUEUED || st == RQ_RUNNING) { set_error("release: request still pending"); return LOGDET_PENDING; }
+  if (st == RQ_QUEUED || st == RQ_RUNNING || st == RQ_SUSPENDED) {
+    set_error("release: request still pending");
+    return LOGDET_PENDING;
+  }
   s->all.erase(it);
+  return LOGDET_OK;
+}
+
+int logdet_suspend(logdet_server* s, uint64_t id) {
+  if (!s) { set_error("suspend: NULL server"); return LOGDET_EINVAL; }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) { set_error("suspend: unknown request"); return LOGDET_ENOENT; }
+    auto r = it->second;
+    if (r->state == RQ_QUEUED) {  // not admitted yet: leaves the queue, holds nothing
+      for (size_t i = 0; i < s->queue.size(); ++i)
+        if (s->queue[i] == r) {
+          s->queue.erase(s->queue.begin() + i);
+          break;
+        }
+      r->state = RQ_SUSPENDED;
+      s->held.push_back(r);
+      ++s->n_suspensions;
+      return LOGDET_OK;
+    }
+    if (r->state != RQ_RUNNING) {
+      set_error("suspend: request %llu is not queued or running", (unsigned long long)id);
+      return LOGDET_EINVAL;
+    }
+    r->suspend = true;
+  }
+  s->cv_work.notify_all();
+  return LOGDET_OK;
+}
+
+int logdet_resume(logdet_server* s, uint64_t id) {
+  if (!s) { set_error("resume: NULL server"); return LOGDET_EINVAL; }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) { set_error("resume: unknown request"); return LOGDET_ENOENT; }
+    auto r = it->second;
+    if (r->state == RQ_RUNNING && r->suspend) {  // not acted on yet: withdrawn
+      r->suspend = false;
+      return LOGDET_OK;
+    }
+    if (r->state != RQ_SUSPENDED) {
+      set_error("resume: request %llu is not suspended", (unsigned long long)id);
+      return LOGDET_EINVAL;
+    }
+    for (size_t i = 0; i < s->held.size(); ++i)
+      if (s->held[i] == r) {
+        s->held.erase(s->held.begin() + i);
+        break;
+      }
+    r->state = RQ_QUEUED;
+    s->queue.push_front(r);
+  }
+  s->cv_work.notify_all();
   return LOGDET_OK;
 }
 
@@ -506,6 +590,9 @@ int logdet_server_stats(logdet_server* s, logdet_stats* out) {
   out->bytes_in_use = s->used;
   out->bytes_budget = s->budget;
   out->busy_ms = s->busy_us / 1e3;
+  out->suspended = (int64_t)s->held.size();
+  out->suspensions = s->n_suspensions;
+  out->suspended_in_krylov = s->n_suspended_in_krylov;
   return LOGDET_OK;
 }
 

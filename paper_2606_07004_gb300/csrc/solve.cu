@@ -678,6 +678,128 @@ struct Solve : ISolve {
 
   int phase() const override { return ph; }
   bool in_krylov() const override { return ph == PH_K1 || ph == PH_K2; }
+
+  // ---- suspension (see ISolve) ----
+  struct BufRef {
+    void** p;
+    size_t bytes;  // allocated size (0: no buffer)
+  };
+  struct Saved {
+    void* old;
+    size_t off, bytes;
+  };
+  std::vector<unsigned char> susp_host;
+  std::vector<Saved> susp_list;
+  bool is_susp = false;
+
+  template <typename U>
+  static BufRef ref(DevBuf<U>& b) {
+    return {reinterpret_cast<void**>(&b.p), b.p ? b.count * sizeof(U) : 0};
+  }
+  std::vector<BufRef> buffers() {
+    std::vector<BufRef> v = {ref(vals), ref(gtabs), ref(diav), ref(Vst), ref(Xc),
+                             ref(X64),  ref(outv),  ref(cshift), ref(keep)};
+    if (run) {
+      KRun<T>& R = *run;
+      KState& K = R.ks;
+      for (BufRef b : {ref(R.part), ref(R.y), ref(R.ring), ref(R.dia_err), ref(R.krun_bar),
+                       ref(R.krun_part2), ref(K.alpha), ref(K.beta), ref(K.H), ref(K.sig),
+                       ref(K.edot), ref(K.coef), ref(K.ycoef), ref(K.dbuf), ref(K.meff),
+                       ref(K.active), ref(K.status), ref(K.cnt)})
+        v.push_back(b);
+    }
+    return v;
+  }
+  bool suspended() const override { return is_susp; }
+
+  int suspend() override {
+    if (is_susp) return LOGDET_OK;
+    LD_CUDA(cudaStreamSynchronize(st));
+    std::vector<BufRef> bufs = buffers();
+    size_t total = 0;
+    for (const BufRef& b : bufs) total += b.bytes;
+    susp_host.resize(total);
+    susp_list.clear();
+    size_t off = 0;
+    for (const BufRef& b : bufs) {
+      susp_list.push_back({*b.p, off, b.bytes});
+      if (b.bytes)
+        LD_CUDA(cudaMemcpyAsync(susp_host.data() + off, *b.p, b.bytes, cudaMemcpyDeviceToHost, st));
+      off += b.bytes;
+    }
+    LD_CUDA(cudaStreamSynchronize(st));
+    for (const BufRef& b : bufs)
+      if (*b.p) {
+        cudaFreeAsync(*b.p, st);
+        *b.p = nullptr;
+      }
+    is_susp = true;
+    return LOGDET_OK;
+  }
+
+  int resume() override {
+    if (!is_susp) return LOGDET_OK;
+    std::vector<BufRef> bufs = buffers();  // (same order; every pointer is null now)
+    if (bufs.size() != susp_list.size()) {
+      set_error("resume: the solve's buffer list changed while suspended");
+      return LOGDET_ECUDA;
+    }
+    std::vector<std::pair<const void*, void*>> moved;
+    for (size_t i = 0; i < bufs.size(); ++i) {
+      const Saved& sv = susp_list[i];
+      if (!sv.bytes) continue;
+      void* q = nullptr;
+      cudaError_t e = cudaMallocAsync(&q, sv.bytes, st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("resume: device allocation of %zu bytes failed", sv.bytes);
+        for (size_t j = 0; j < i; ++j)
+          if (*bufs[j].p) { cudaFreeAsync(*bufs[j].p, st); *bufs[j].p = nullptr; }
+        return LOGDET_ENOMEM;
+      }
+      *bufs[i].p = q;
+      LD_CUDA(cudaMemcpyAsync(q, susp_host.data() + sv.off, sv.bytes, cudaMemcpyHostToDevice, st));
+      moved.push_back({sv.old, q});
+    }
+    LD_CUDA(cudaStreamSynchronize(st));
+    // Raw pointers held next to the buffers: the run's inputs and its state table.
+    auto fix = [&](auto& ptr) {
+      for (const auto& mv : moved)
+        if (static_cast<const void*>(ptr) == mv.first) {
+          ptr = static_cast<std::remove_reference_t<decltype(ptr)>>(mv.second);
+          return;
+        }
+    };
+    if (run) {
+      KRun<T>& R = *run;
+      fix(R.X0);
+      fix(R.Vfull);
+      fix(R.vals);
+      fix(R.colshift);
+      fix(R.colscale);
+      fix(R.diavals);
+      fix(R.gtab);
+      KrylovState& S = R.ks.st;
+      fix(S.alpha);
+      fix(S.beta);
+      fix(S.H);
+      fix(S.sig);
+      fix(S.edot);
+      fix(S.coef);
+      fix(S.ycoef);
+      fix(S.meff);
+      fix(S.active);
+      fix(S.status);
+      fix(S.cnt);
+      fix(S.dbuf);
+    }
+    fix(pend_x0);
+    susp_host.clear();
+    susp_host.shrink_to_fit();
+    susp_list.clear();
+    is_susp = false;
+    return LOGDET_OK;
+  }
   int krylov_threads() const override { return run ? run->g.threads : 0; }
   bool is_fp32() const override { return !std::is_same<T, double>::value; }
   int elem_kind() const override { return std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2; }

@@ -178,6 +178,14 @@ struct ISolve {
   // memory at run time, and take the pinned result buffer before capture.
   virtual void set_dev_keys(const uint64_t* keys) = 0;
   virtual int prepare_host() = 0;
+  // Suspension between steps (the server's preemption): suspend() waits for
+  // the stream, copies every device buffer of the solve to host memory and
+  // frees it; resume() allocates the buffers again (new addresses), copies
+  // the contents back and repoints the run at them.  The solve continues
+  // exactly where it stopped: results are bit-identical.
+  virtual int suspend() = 0;
+  virtual int resume() = 0;
+  virtual bool suspended() const = 0;
 };
 
 std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, int* rc);
