@@ -411,6 +411,20 @@ int logdet_server_stats(logdet_server* s, logdet_stats* out);
 int logdet_suspend(logdet_server* s, uint64_t req_id);
 int logdet_resume(logdet_server* s, uint64_t req_id);
 
+/* ---- checked builds (a substitute for the sanitizers in tests) ----------
+ * The library built with -DLOGDET_CHECKED (liblogdet_checked.so) checks, in
+ * the Krylov passes on the device, every index it takes from memory before
+ * using it: work-item rows and partial slots, row ranges from rowptr,
+ * column indices.  A violation sets a bit in the device word reported here
+ * (1 work item, 2 row range, 4 column index, 8 partial slot) and the access
+ * is redirected in range; nothing traps.  Every workspace buffer gets 256
+ * guard bytes of 0xA5 on each side, read back when it is freed; changed
+ * bytes are counted.  logdet_checked_report: *checked = 1 in a checked
+ * build (0 otherwise, with both counts 0); *device_violations = the bits so
+ * far (synchronises the device); *canary_bytes = changed guard bytes so far.
+ * Errors: EINVAL (NULL pointer), ECUDA. */
+int logdet_checked_report(int32_t* checked, uint32_t* device_violations, uint64_t* canary_bytes);
+
 /* ---- graph plans (the paper has no counterpart: a deployment variant of
  * Algorithms 2 and 3 for repeated estimates of one shape) -------------------
  * A plan captures one complete OSLQ (method 0) or OSA-IOP (method 1) solve,

@@ -45,6 +45,7 @@ EXPORTED = [
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
     "logdet_oslq_shifts", "logdet_osaiop_shifts", "logdet_suspend", "logdet_resume",
+    "logdet_checked_report",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
@@ -132,6 +133,7 @@ _sig("logdet_poll", C.c_int, [_P, _u64, C.POINTER(logdet_result)])
 _sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
 _sig("logdet_cancel", C.c_int, [_P, _u64])
 _sig("logdet_suspend", C.c_int, [_P, _u64])
+_sig("logdet_checked_report", C.c_int, [C.POINTER(_i32), C.POINTER(_u32), C.POINTER(_u64)])
 _sig("logdet_resume", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
 _sig("logdet_server_stats", C.c_int, [_P, C.POINTER(logdet_server_stats)])
@@ -623,3 +625,10 @@ def profile_snapshot() -> dict:
 
 def exported_symbols() -> list[str]:
     return [name for name in EXPORTED if hasattr(_lib, name)]
+
+
+def checked_report() -> dict:
+    """State of the checks of a checked build (logdet_checked_report)."""
+    c, v, b = _i32(), _u32(), _u64()
+    _check(_lib.logdet_checked_report(C.byref(c), C.byref(v), C.byref(b)), "logdet_checked_report")
+    return {"checked": bool(c.value), "device_violations": v.value, "canary_bytes": b.value}

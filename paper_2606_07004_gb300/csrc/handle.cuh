@@ -37,6 +37,14 @@ struct logdet_ctx {
 
 namespace ld {
 
+// Checked builds (LOGDET_CHECKED): every workspace buffer is allocated with
+// kCanaryBytes of guard on each side, filled with kCanaryByte; release reads
+// both guards back and counts any byte that changed (canary_fault_count).
+constexpr size_t kCanaryBytes = 256;  // keeps the buffer 256-byte aligned
+constexpr unsigned char kCanaryByte = 0xA5;
+void canary_fault(size_t bytes_changed);
+unsigned long long canary_fault_count();
+
 // Stream-ordered device buffer freed when it goes out of scope.
 template <typename T>
 struct DevBuf {
@@ -46,10 +54,27 @@ struct DevBuf {
   explicit DevBuf(cudaStream_t s) : st(s) {}
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
+#ifdef LOGDET_CHECKED
+  static constexpr size_t kGuard = kCanaryBytes;
+#else
+  static constexpr size_t kGuard = 0;
+#endif
+  cudaError_t raw_alloc() {
+    void* base = nullptr;
+    cudaError_t e = cudaMallocAsync(&base, count * sizeof(T) + 2 * kGuard, st);
+    if (e != cudaSuccess) return e;
+    p = reinterpret_cast<T*>(static_cast<unsigned char*>(base) + kGuard);
+    if (kGuard) {
+      cudaMemsetAsync(base, kCanaryByte, kGuard, st);
+      cudaMemsetAsync(reinterpret_cast<unsigned char*>(p) + count * sizeof(T), kCanaryByte, kGuard,
+                      st);
+    }
+    return cudaSuccess;
+  }
   int alloc(size_t n) {
     release();
     count = std::max<size_t>(n, 1);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+    cudaError_t e = raw_alloc();
     if (e == cudaErrorMemoryAllocation) {
       // The pool keeps freed memory (release threshold: never); memory it
       // holds unused in blocks of other sizes goes back once, then retry.
@@ -59,7 +84,7 @@ struct DevBuf {
       if (cudaStreamSynchronize(st) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess &&
           cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
           cudaMemPoolTrimTo(pool, 0) == cudaSuccess)
-        e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), st);
+        e = raw_alloc();
     }
     if (e != cudaSuccess) {
       p = nullptr;
@@ -71,7 +96,22 @@ struct DevBuf {
   }
   int zero() { return cudaMemsetAsync(p, 0, count * sizeof(T), st) == cudaSuccess ? LOGDET_OK : LOGDET_ECUDA; }
   void release() {
-    if (p) cudaFreeAsync(p, st);
+    if (!p) return;
+    unsigned char* base = reinterpret_cast<unsigned char*>(p) - kGuard;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (kGuard && cudaStreamIsCapturing(st, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {  // (no reads back inside a graph capture)
+      unsigned char g[2 * kCanaryBytes];
+      if (cudaMemcpyAsync(g, base, kGuard, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+          cudaMemcpyAsync(g + kGuard, reinterpret_cast<unsigned char*>(p) + count * sizeof(T), kGuard,
+                          cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+          cudaStreamSynchronize(st) == cudaSuccess) {
+        size_t bad = 0;
+        for (size_t i = 0; i < 2 * kGuard; ++i) bad += g[i] != kCanaryByte;
+        if (bad) canary_fault(bad);
+      }
+    }
+    cudaFreeAsync(base, st);
     p = nullptr;
   }
   ~DevBuf() { release(); }

@@ -1,4 +1,5 @@
 // Krylov step kernels (see krylov.cuh for the recurrence they implement).
+#include "handle.cuh"
 #include "krylov.cuh"
 #include "profile.cuh"
 
@@ -61,6 +62,49 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // capacity away from the gathers of x.
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
+
+// Checked builds (LOGDET_CHECKED): bounds checks on the indices the passes
+// take from memory -- work-item rows and slots, row ranges from rowptr,
+// column indices -- before they address anything.  A violation sets a bit
+// of g_violations (logdet_checked_report) and the access is redirected in
+// range (column 0, an empty row range, slot 0); nothing traps.  In other
+// builds the checks are the identity.
+enum : unsigned { kViolItem = 1u, kViolRowRange = 2u, kViolColumn = 4u, kViolSlot = 8u };
+#ifdef LOGDET_CHECKED
+__device__ unsigned int g_violations;
+__device__ __forceinline__ int chk_col(int c, int n) {
+  if ((unsigned)c >= (unsigned)n) {
+    atomicOr(&g_violations, kViolColumn);
+    return 0;
+  }
+  return c;
+}
+__device__ __forceinline__ void chk_range(int& q0, int& q1, long long nnz) {
+  if (q0 < 0 || q1 < q0 || (long long)q1 > nnz) {
+    atomicOr(&g_violations, kViolRowRange);
+    q0 = q1 = 0;
+  }
+}
+__device__ __forceinline__ int chk_slot(int t, int nslots) {
+  if ((unsigned)t >= (unsigned)nslots) {
+    atomicOr(&g_violations, kViolSlot);
+    return 0;
+  }
+  return t;
+}
+__device__ __forceinline__ void chk_item(int& r0, int& r1, bool split, int n) {
+  if (r0 < 0 || r0 >= n || (!split && (r1 < r0 || r1 > n))) {
+    atomicOr(&g_violations, kViolItem);
+    r0 = 0;
+    r1 = split ? -1 : 0;
+  }
+}
+#else
+__device__ __forceinline__ int chk_col(int c, int) { return c; }
+__device__ __forceinline__ void chk_range(int&, int&, long long) {}
+__device__ __forceinline__ int chk_slot(int t, int) { return t; }
+__device__ __forceinline__ void chk_item(int&, int&, bool, int) {}
+#endif
 
 // Programmatic dependent launch of the step kernels: a step kernel may be
 // launched while its predecessor in the stream still runs (its CTAs get
@@ -132,8 +176,9 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
       const int4 it = __ldg(J.items + tile);
       row0 = it.x;
       row1 = it.y;
-      tile = it.z;
+      tile = chk_slot(it.z, J.ntiles);
       split = it.y < 0;
+      chk_item(row0, row1, split, J.n);
     }
     const int col0 = J.col_off + g * V;
     const int ndots = J.ndots;
@@ -154,14 +199,15 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
 #pragma unroll
       for (int v = 0; v < V; ++v) s[v] = CT(0);
       if (live) {
-        const int q0 = __ldg(J.rowptr + row), q1 = __ldg(J.rowptr + row + 1);
+        int q0 = __ldg(J.rowptr + row), q1 = __ldg(J.rowptr + row + 1);
+        chk_range(q0, q1, J.nnz);
         int q = q0 + r;
         for (; q + (kGather - 1) * R < q1; q += kGather * R) {
           int c[kGather];
           CT a[kGather], xv[kGather][V];
 #pragma unroll
           for (int u = 0; u < kGather; ++u) {
-            c[u] = __ldg(J.colind + q + u * R);
+            c[u] = chk_col(__ldg(J.colind + q + u * R), J.n);
             a[u] = __ldg(J.vals + q + u * R);
           }
 #pragma unroll
@@ -172,7 +218,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
             for (int v = 0; v < V; ++v) s[v] = fma(a[u], xv[u][v], s[v]);
         }
         for (; q < q1; q += R) {
-          const int c = __ldg(J.colind + q);
+          const int c = chk_col(__ldg(J.colind + q), J.n);
           const CT a = __ldg(J.vals + q);
           CT xv[V];
           load_v<COH, T>(xcol + (size_t)c * J.ld, xv);
@@ -241,6 +287,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
       if (kPipe && row < row1) {
         q0 = __ldg(J.rowptr + row);
         q1 = __ldg(J.rowptr + row + 1);
+        chk_range(q0, q1, J.nnz);
       }
       for (; row < row1; row += R) {
         int nq0 = 0, nq1 = 0;
@@ -248,10 +295,12 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           if (row + R < row1) {
             nq0 = __ldg(J.rowptr + row + R);
             nq1 = __ldg(J.rowptr + row + R + 1);
+            chk_range(nq0, nq1, J.nnz);
           }
         } else {
           q0 = __ldg(J.rowptr + row);
           q1 = __ldg(J.rowptr + row + 1);
+          chk_range(q0, q1, J.nnz);
         }
         // FP32 / BF16 blocks with two window dots: the row's window vectors
         // are requested before its gathers, so their latency overlaps them
@@ -277,7 +326,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           if (q + kGather <= q1) {
 #pragma unroll
             for (int u = 0; u < kGather; ++u) {
-              c[u] = __ldg(J.colind + q + u);
+              c[u] = chk_col(__ldg(J.colind + q + u), J.n);
               a[u] = __ldg(J.vals + q + u);
             }
           }
@@ -291,7 +340,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
             if (more) {
 #pragma unroll
               for (int u = 0; u < kGather; ++u) {
-                cn[u] = __ldg(J.colind + q + kGather + u);
+                cn[u] = chk_col(__ldg(J.colind + q + kGather + u), J.n);
                 an[u] = __ldg(J.vals + q + kGather + u);
               }
             }
@@ -313,7 +362,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
             CT a[kGather], xv[kGather][V];
 #pragma unroll
             for (int u = 0; u < kGather; ++u) {
-              c[u] = __ldg(J.colind + q + u);
+              c[u] = chk_col(__ldg(J.colind + q + u), J.n);
               a[u] = __ldg(J.vals + q + u);
             }
 #pragma unroll
@@ -325,7 +374,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           }
         }
         for (; q < q1; ++q) {
-          const int c = __ldg(J.colind + q);
+          const int c = chk_col(__ldg(J.colind + q), J.n);
           const CT a = __ldg(J.vals + q);
           CT xv[V];
           load_v<COH, T>(xcol + (size_t)c * J.ld, xv);
@@ -1347,3 +1396,25 @@ template int launch_update<float>(const UpdBatch<float>&, int, cudaStream_t);
 template int launch_update<bf16>(const UpdBatch<bf16>&, int, cudaStream_t);
 
 }  // namespace ld
+
+// ---------------------------------------------------------------------------
+// C-ABI: state of the checks of a checked build
+// ---------------------------------------------------------------------------
+extern "C" int logdet_checked_report(int32_t* checked, uint32_t* device_violations,
+                                     uint64_t* canary_bytes) {
+  if (!checked || !device_violations || !canary_bytes) {
+    ld::set_error("checked_report: NULL argument");
+    return LOGDET_EINVAL;
+  }
+  unsigned v = 0;
+#ifdef LOGDET_CHECKED
+  *checked = 1;
+  LD_CUDA(cudaDeviceSynchronize());
+  LD_CUDA(cudaMemcpyFromSymbol(&v, ld::g_violations, sizeof v));
+#else
+  *checked = 0;
+#endif
+  *device_violations = v;
+  *canary_bytes = ld::canary_fault_count();
+  return LOGDET_OK;
+}

@@ -5,6 +5,7 @@
 #include "krylov.cuh"
 #include "profile.cuh"
 
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <mutex>
@@ -36,10 +37,16 @@ int ensure_pool(int device) {
   return LOGDET_OK;
 }
 
+// Canary bytes found changed when checked builds release a buffer.
+static std::atomic<unsigned long long> g_canary_bytes{0};
+void canary_fault(size_t bytes_changed) { g_canary_bytes += bytes_changed; }
+unsigned long long canary_fault_count() { return g_canary_bytes.load(); }
+
 // ---------------------------------------------------------------------------
 // Pinned host block cache (see handle.cuh).  At most kPinnedCacheMax bytes
 // stay cached; beyond that a released block is freed.
 // ---------------------------------------------------------------------------
+
 namespace {
 struct PinnedFree {
   void* p;
@@ -422,7 +429,7 @@ int spmm_block(const int* rowptr, const int* colind, const typename ValOf<T>::ty
   J.col_off = 0;
   J.width = ld;
   J.b = ld;
-  J.nnz = 0;
+  J.nnz = h ? h->nnz : 0;  // (every caller passes the handle; the checked build bounds rows by it)
   J.tile_rows = g.tile_rows;
   J.ntiles = div_up(n, g.tile_rows);
   if (h) {

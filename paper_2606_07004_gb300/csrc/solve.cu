@@ -6,6 +6,7 @@
 #include "tune.cuh"
 
 #include <cmath>
+#include <functional>
 #include <cstdlib>
 #include <cstring>
 
@@ -680,9 +681,11 @@ struct Solve : ISolve {
   bool in_krylov() const override { return ph == PH_K1 || ph == PH_K2; }
 
   // ---- suspension (see ISolve) ----
-  struct BufRef {
-    void** p;
+  struct BufRef {  // one DevBuf of the solve, whatever its element type
+    std::function<void*()> ptr;
     size_t bytes;  // allocated size (0: no buffer)
+    std::function<void()> release;
+    std::function<int()> realloc;  // the same element count again
   };
   struct Saved {
     void* old;
@@ -694,7 +697,8 @@ struct Solve : ISolve {
 
   template <typename U>
   static BufRef ref(DevBuf<U>& b) {
-    return {reinterpret_cast<void**>(&b.p), b.p ? b.count * sizeof(U) : 0};
+    return {[&b] { return static_cast<void*>(b.p); }, b.p ? b.count * sizeof(U) : 0,
+            [&b] { b.release(); }, [&b] { return b.alloc(b.count); }};
   }
   std::vector<BufRef> buffers() {
     std::vector<BufRef> v = {ref(vals), ref(gtabs), ref(diav), ref(Vst), ref(Xc),
@@ -722,17 +726,13 @@ struct Solve : ISolve {
     susp_list.clear();
     size_t off = 0;
     for (const BufRef& b : bufs) {
-      susp_list.push_back({*b.p, off, b.bytes});
+      susp_list.push_back({b.ptr(), off, b.bytes});
       if (b.bytes)
-        LD_CUDA(cudaMemcpyAsync(susp_host.data() + off, *b.p, b.bytes, cudaMemcpyDeviceToHost, st));
+        LD_CUDA(cudaMemcpyAsync(susp_host.data() + off, b.ptr(), b.bytes, cudaMemcpyDeviceToHost, st));
       off += b.bytes;
     }
     LD_CUDA(cudaStreamSynchronize(st));
-    for (const BufRef& b : bufs)
-      if (*b.p) {
-        cudaFreeAsync(*b.p, st);
-        *b.p = nullptr;
-      }
+    for (const BufRef& b : bufs) b.release();
     is_susp = true;
     return LOGDET_OK;
   }
@@ -748,16 +748,11 @@ struct Solve : ISolve {
     for (size_t i = 0; i < bufs.size(); ++i) {
       const Saved& sv = susp_list[i];
       if (!sv.bytes) continue;
-      void* q = nullptr;
-      cudaError_t e = cudaMallocAsync(&q, sv.bytes, st);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        set_error("resume: device allocation of %zu bytes failed", sv.bytes);
-        for (size_t j = 0; j < i; ++j)
-          if (*bufs[j].p) { cudaFreeAsync(*bufs[j].p, st); *bufs[j].p = nullptr; }
+      if (bufs[i].realloc() != LOGDET_OK) {  // (the message is set)
+        for (size_t j = 0; j < i; ++j) bufs[j].release();
         return LOGDET_ENOMEM;
       }
-      *bufs[i].p = q;
+      void* q = bufs[i].ptr();
       LD_CUDA(cudaMemcpyAsync(q, susp_host.data() + sv.off, sv.bytes, cudaMemcpyHostToDevice, st));
       moved.push_back({sv.old, q});
     }
