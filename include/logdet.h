@@ -410,6 +410,14 @@ int logdet_server_stats(logdet_server* s, logdet_stats* out);
  *   (not suspended).  logdet_cancel also ends a suspended request. */
 int logdet_suspend(logdet_server* s, uint64_t req_id);
 int logdet_resume(logdet_server* s, uint64_t req_id);
+/* logdet_server_set_log: append one JSON line per request that leaves the
+ *   server after admission (done, failed, or cancelled while resident) to
+ *   the file `path` (opened for appending; NULL or
+ *   "" stops logging): id, state, rc, n, nnz, method, precision, probes,
+ *   steps, window, shift, seed, logdet, steps_min, steps_max, status_bits,
+ *   latency_ms and queue_ms (submit -> result and submit -> admission, host
+ *   clock).  Errors: EINVAL (NULL server, file not openable). */
+int logdet_server_set_log(logdet_server* s, const char* path);
 
 /* ---- checked builds (a substitute for the sanitizers in tests) ----------
  * The library built with -DLOGDET_CHECKED (liblogdet_checked.so) checks, in

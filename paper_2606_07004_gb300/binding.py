@@ -45,7 +45,7 @@ EXPORTED = [
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
     "logdet_oslq_shifts", "logdet_osaiop_shifts", "logdet_suspend", "logdet_resume",
-    "logdet_checked_report",
+    "logdet_checked_report", "logdet_server_set_log",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
@@ -133,6 +133,7 @@ _sig("logdet_poll", C.c_int, [_P, _u64, C.POINTER(logdet_result)])
 _sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
 _sig("logdet_cancel", C.c_int, [_P, _u64])
 _sig("logdet_suspend", C.c_int, [_P, _u64])
+_sig("logdet_server_set_log", C.c_int, [_P, C.c_char_p])
 _sig("logdet_checked_report", C.c_int, [C.POINTER(_i32), C.POINTER(_u32), C.POINTER(_u64)])
 _sig("logdet_resume", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
@@ -487,6 +488,11 @@ class Server:
 
     def cancel(self, rid: int):
         _check(_lib.logdet_cancel(self._s, rid), "logdet_cancel")
+
+    def set_log(self, path):
+        """Append one JSON line per finished request to `path` (None stops)."""
+        p = None if path is None else str(path).encode()
+        _check(_lib.logdet_server_set_log(self._s, p), "logdet_server_set_log")
 
     def suspend(self, rid: int):
         """Preempt a request: its device state moves to host memory (logdet_suspend)."""

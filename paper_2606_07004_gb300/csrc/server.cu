@@ -16,6 +16,7 @@
 #include "profile.cuh"
 
 #include <chrono>
+#include <cstdio>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -76,6 +77,7 @@ struct logdet_server {
   int64_t n_ticks = 0, n_batched_steps = 0, max_resident = 0;
   int64_t n_suspensions = 0, n_suspended_in_krylov = 0;
   std::vector<std::shared_ptr<Request>> held;  // suspended requests
+  FILE* log = nullptr;  // per-request records (logdet_server_set_log), one JSON line each
   double busy_us = 0.0;
 
   void loop();
@@ -100,6 +102,24 @@ void logdet_server::complete(const std::shared_ptr<Request>& r, int state_, int 
     ++n_failed;
   } else if (state_ == RQ_CANCELLED) {
     ++n_cancelled;
+  }
+  if (log) {
+    const SolveCfg& c = r->cfg;
+    const logdet_result& o = r->out.res;
+    const char* sname = state_ == RQ_DONE ? "done" : state_ == RQ_FAILED ? "failed" : "cancelled";
+    fprintf(log,
+            "{\"id\": %llu, \"state\": \"%s\", \"rc\": %d, \"n\": %d, \"nnz\": %lld, "
+            "\"method\": \"%s\", \"precision\": %d, \"probes\": %d, \"steps\": %d, "
+            "\"window\": %d, \"shift\": %.17g, \"seed\": %llu, \"logdet\": %.17g, "
+            "\"steps_min\": %d, \"steps_max\": %d, \"status_bits\": %u, "
+            "\"latency_ms\": %.3f, \"queue_ms\": %.3f}\n",
+            (unsigned long long)r->id, sname, rc_, r->h ? r->h->n : 0, r->h ? r->h->nnz : 0LL,
+            c.method == 0 ? "oslq" : "osaiop", c.precision, c.P, c.m, c.k, c.shift,
+            (unsigned long long)c.seed, state_ == RQ_DONE ? o.logdet : 0.0,
+            state_ == RQ_DONE ? o.steps_min : 0, state_ == RQ_DONE ? o.steps_max : 0,
+            state_ == RQ_DONE ? o.status_bits : 0u, (r->t_done - r->t_submit) / 1e3,
+            r->t_admit > 0 ? (r->t_admit - r->t_submit) / 1e3 : 0.0);
+    fflush(log);
   }
   // Device buffers are freed in stream order, after any work still queued.
   r->solve.reset();
@@ -392,6 +412,7 @@ void logdet_server_destroy(logdet_server* s) {
   if (s->worker.joinable()) s->worker.join();
   cudaStreamSynchronize(s->st);
   if (s->own_stream) cudaStreamDestroy(s->st);
+  if (s->log) fclose(s->log);
   delete s;
 }
 
@@ -516,6 +537,19 @@ int logdet_release(logdet_server* s, uint64_t id) {
     return LOGDET_PENDING;
   }
   s->all.erase(it);
+  return LOGDET_OK;
+}
+
+int logdet_server_set_log(logdet_server* s, const char* path) {
+  if (!s) { set_error("set_log: NULL server"); return LOGDET_EINVAL; }
+  FILE* f = nullptr;
+  if (path && path[0]) {
+    f = fopen(path, "a");
+    if (!f) { set_error("set_log: cannot open %s", path); return LOGDET_EINVAL; }
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->log) fclose(s->log);
+  s->log = f;
   return LOGDET_OK;
 }
 

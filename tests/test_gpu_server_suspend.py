@@ -138,3 +138,25 @@ def test_server_honours_block_width():
         with B.Server(8 << 30, max_slots=2) as srv:
             got = srv.wait(srv.submit(h, B.METHOD_OSLQ, 30, 20, seed=3, block_width=10))
     _same(got, ref)
+
+
+def test_server_request_log(tmp_path):
+    import json
+    A = W.laplacian_2d(120, shift=0.1)
+    path = tmp_path / "requests.jsonl"
+    with B.Handle.from_csr(A) as h:
+        with B.Server(8 << 30, max_slots=4) as srv:
+            srv.set_log(path)
+            ids = [srv.submit(h, B.METHOD_OSLQ, 30, 20, seed=s) for s in range(3)]
+            ids.append(srv.submit(h, B.METHOD_OSAIOP, 30, 16, 2, seed=5, precision=B.MIXED_FP32))
+            res = [srv.wait(i) for i in ids]
+            srv.set_log(None)
+    recs = {r["id"]: r for r in map(json.loads, path.read_text().splitlines())}
+    assert sorted(recs) == sorted(ids)
+    for i, r in zip(ids, res):
+        rec = recs[i]
+        assert rec["state"] == "done" and rec["rc"] == 0
+        assert rec["n"] == A.n and rec["nnz"] == A.nnz
+        assert rec["logdet"] == r.logdet and rec["steps_max"] == r.steps_max
+        assert rec["latency_ms"] >= rec["queue_ms"] >= 0.0
+    assert recs[ids[-1]]["method"] == "osaiop" and recs[ids[-1]]["precision"] == B.MIXED_FP32
