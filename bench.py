@@ -857,6 +857,13 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
         batched = [srv.wait(i) for i in ids]
         t_batched = time.perf_counter() - t1
         st = srv.stats()
+        # the same 8 as one shift group through the server (logdet_submit_shifts)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        gids = srv.submit_shifts(h, B.METHOD_OSAIOP, shifts, P, m, k, seed0=0,
+                                 precision=B.MIXED_FP32, autotune=autotune)
+        sgroup = [srv.wait(i) for i in gids]
+        t_sgroup = time.perf_counter() - t1
     t1 = time.perf_counter()
     serial = [h.osaiop(P, m, iop_window=k, seed=t, precision=B.MIXED_FP32, shift=float(sh),
                        autotune=autotune) for t, sh in enumerate(shifts)]
@@ -897,6 +904,9 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
                     "k=4, 64 probes each, mixed FP32" % (A.n, A.nnz),
         "unit": UNIT,
         "group_solves_per_s": 8 / t_group, "batched_solves_per_s": 8 / t_batched,
+        "server_group_solves_per_s": 8 / t_sgroup,
+        "server_group_equals_group_bitwise": all(a.logdet == b.logdet
+                                                 for a, b in zip(sgroup, group)),
         "serial_solves_per_s": 8 / t_serial,
         "group_s": t_group, "batched_s": t_batched, "serial_s": t_serial,
         "rel_err_group_mixed_vs_fp64": {f"shift_{t}": gerrs[t] for t in which},

@@ -389,6 +389,22 @@ void logdet_server_destroy(logdet_server* s);
 int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num_probes,
                   int32_t krylov_steps, int32_t iop_window, uint64_t seed, const logdet_opts* opts,
                   uint64_t* req_id);
+/* logdet_submit_shifts: the server form of logdet_oslq_shifts /
+ *   logdet_osaiop_shifts (method LOGDET_METHOD_OSLQ / _OSAIOP): nshift
+ *   requests, member t the solve with shift shifts[t] and seed seed0 + t,
+ *   whose ids go to req_ids[0 .. nshift).  They are split into the same
+ *   runs as the blocking call; each run is admitted as a whole (its members'
+ *   estimates together against the budget, one slot) and advances in the
+ *   batch as one Krylov run over all its members' columns, so the results
+ *   are bit-identical to logdet_*_shifts with the same arguments.  Members
+ *   are polled, waited for, logged and released one by one; cancelling one
+ *   cancels its run; they cannot be suspended (EINVAL).  opts->per_probe /
+ *   z_norm2 are not used.  Errors: as logdet_oslq_shifts, and ENOMEM when a
+ *   run alone exceeds the budget (nothing is submitted then). */
+int logdet_submit_shifts(logdet_server* s, logdet_handle h, int32_t method, int32_t nshift,
+                         const double* shifts, int32_t num_probes, int32_t krylov_steps,
+                         int32_t iop_window, uint64_t seed0, const logdet_opts* opts,
+                         uint64_t* req_ids);
 int logdet_poll(logdet_server* s, uint64_t req_id, logdet_result* out);
 int logdet_wait(logdet_server* s, uint64_t req_id, int64_t timeout_us, logdet_result* out);
 int logdet_cancel(logdet_server* s, uint64_t req_id);

@@ -45,7 +45,7 @@ EXPORTED = [
     "logdet_wait", "logdet_cancel", "logdet_release", "logdet_server_stats",
     "logdet_plan_create", "logdet_plan_run", "logdet_plan_kernels", "logdet_plan_destroy",
     "logdet_oslq_shifts", "logdet_osaiop_shifts", "logdet_suspend", "logdet_resume",
-    "logdet_checked_report", "logdet_server_set_log",
+    "logdet_checked_report", "logdet_server_set_log", "logdet_submit_shifts",
 ]
 KC_NAMES = ["spmm", "update", "scalar", "qr", "project", "small", "other", "grid", "krylov_run"]
 
@@ -134,6 +134,8 @@ _sig("logdet_wait", C.c_int, [_P, _u64, _i64, C.POINTER(logdet_result)])
 _sig("logdet_cancel", C.c_int, [_P, _u64])
 _sig("logdet_suspend", C.c_int, [_P, _u64])
 _sig("logdet_server_set_log", C.c_int, [_P, C.c_char_p])
+_sig("logdet_submit_shifts", C.c_int, [_P, _P, _i32, _i32, _P, _i32, _i32, _i32, _u64,
+                                       C.POINTER(logdet_opts), _P])
 _sig("logdet_checked_report", C.c_int, [C.POINTER(_i32), C.POINTER(_u32), C.POINTER(_u64)])
 _sig("logdet_resume", C.c_int, [_P, _u64])
 _sig("logdet_release", C.c_int, [_P, _u64])
@@ -469,6 +471,25 @@ class Server:
                                   seed, C.byref(o), C.byref(rid)), "logdet_submit")
         self._pending[rid.value] = (per, zn, s, r, handle)
         return rid.value
+
+    def submit_shifts(self, handle: Handle, method: int, shifts, num_probes: int,
+                      krylov_steps: int, iop_window: int = 0, seed0: int = 0, precision=FP64,
+                      tol=None, lam=None, autotune=0, block_width=0) -> list:
+        """A shift group through the server (logdet_submit_shifts): one id per shift."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64).ravel()
+        e = np.zeros(0)
+        o = _make_opts(precision, tol, lam, None, 0.0, e, e, autotune, block_width=block_width)
+        o.per_probe = None
+        o.z_norm2 = None
+        ids = np.zeros(max(len(sh), 1), dtype=np.uint64)
+        _check(_lib.logdet_submit_shifts(self._s, handle.raw, method, len(sh),
+                                         sh.ctypes.data_as(C.c_void_p), num_probes, krylov_steps,
+                                         iop_window, seed0, C.byref(o),
+                                         ids.ctypes.data_as(C.c_void_p)), "logdet_submit_shifts")
+        out = [int(x) for x in ids[:len(sh)]]
+        for rid in out:
+            self._pending[rid] = (e, e, 0, 0, handle)
+        return out
 
     def poll(self, rid: int):
         """None while pending, else the Result (raises LogdetError on failure)."""

@@ -50,6 +50,12 @@ struct Request {
   bool suspend = false;   // logdet_suspend asked; the scheduler acts at a tick boundary
   double t_submit = 0, t_admit = 0, t_done = 0;
   SolveOut out;
+  // Shift groups (logdet_submit_shifts): a run of members goes through the
+  // queue and the batch as one internal request (the run's GroupSolve) whose
+  // members are the requests the caller sees.
+  std::vector<SolveCfg> group_cfgs;               // run: its members' configurations
+  std::vector<std::shared_ptr<Request>> members;  // run: its member requests
+  std::weak_ptr<Request> run;                     // member: its run
 };
 
 }  // namespace ld
@@ -87,6 +93,26 @@ struct logdet_server {
 
 void logdet_server::complete(const std::shared_ptr<Request>& r, int state_, int rc_) {
   // Called with mu held.
+  if (!r->members.empty()) {
+    // A shift-group run: every member finishes with it (the run itself is
+    // internal: it is not counted, logged or visible).
+    for (size_t t = 0; t < r->members.size(); ++t) {
+      auto& mb = r->members[t];
+      int st_m = state_, rc_m = rc_;
+      if (state_ == RQ_DONE) {
+        rc_m = r->solve->assemble_member((int)t, mb->out);
+        if (rc_m) st_m = RQ_FAILED;
+      }
+      mb->t_admit = r->t_admit;
+      complete(mb, st_m, rc_m);
+    }
+    r->state = state_;
+    r->t_done = now_us();
+    r->solve.reset();
+    used -= r->bytes;
+    cv_done.notify_all();
+    return;
+  }
   r->state = state_;
   r->rc = rc_;
   r->t_done = now_us();
@@ -234,6 +260,11 @@ void logdet_server::loop() {
           queue.pop_front();
           r->state = RQ_CANCELLED;
           ++n_cancelled;
+          for (auto& mb : r->members) {
+            mb->state = RQ_CANCELLED;
+            ++n_cancelled;
+          }
+          if (!r->members.empty()) --n_cancelled;  // (a run counts through its members)
           cv_done.notify_all();
           continue;
         }
@@ -243,7 +274,15 @@ void logdet_server::loop() {
         r->state = RQ_RUNNING;
         r->t_admit = now_us();
         active.push_back(r);
-        ++n_admitted;
+        if (r->members.empty()) {
+          ++n_admitted;
+        } else {
+          for (auto& mb : r->members) {
+            mb->state = RQ_RUNNING;
+            mb->t_admit = r->t_admit;
+          }
+          n_admitted += (int64_t)r->members.size();
+        }
       }
       max_resident = std::max<int64_t>(max_resident, (int64_t)active.size());
       if (active.empty()) {
@@ -291,7 +330,8 @@ void logdet_server::loop() {
     for (auto& r : act) {
       if (!r->solve && !r->rc) {
         int rc = LOGDET_OK;
-        r->solve = make_solve(r->h, r->cfg, st, &rc);
+        r->solve = r->group_cfgs.empty() ? make_solve(r->h, r->cfg, st, &rc)
+                                         : make_group_solve(r->h, r->group_cfgs, st, &rc);
         if (!r->solve) r->rc = rc ? rc : LOGDET_EINVAL;
       } else if (r->solve && r->solve->suspended() && !r->rc) {
         const int rc = r->solve->resume();
@@ -339,7 +379,7 @@ void logdet_server::loop() {
         gone = true;
       } else if (r->solve && r->solve->phase() == PH_WAIT &&
                  cudaEventQuery(r->solve->done_event()) == cudaSuccess) {
-        int arc = r->solve->assemble(r->out);
+        const int arc = r->members.empty() ? r->solve->assemble(r->out) : LOGDET_OK;
         complete(r, arc ? RQ_FAILED : RQ_DONE, arc);
         gone = true;
       }
@@ -397,6 +437,8 @@ void logdet_server_destroy(logdet_server* s) {
     for (auto& r : s->queue) {
       r->state = RQ_CANCELLED;
       ++s->n_cancelled;
+      for (auto& mb : r->members) mb->state = RQ_CANCELLED;
+      if (!r->members.empty()) s->n_cancelled += (int64_t)r->members.size() - 1;
     }
     s->queue.clear();
     for (auto& r : s->held) {
@@ -449,6 +491,73 @@ int logdet_submit(logdet_server* s, logdet_handle h, int32_t method, int32_t num
     s->queue.push_back(r);
     ++s->n_submitted;
     *req_id = r->id;
+  }
+  s->cv_work.notify_all();
+  return LOGDET_OK;
+}
+
+int logdet_submit_shifts(logdet_server* s, logdet_handle h, int32_t method, int32_t nshift,
+                         const double* shifts, int32_t num_probes, int32_t krylov_steps,
+                         int32_t iop_window, uint64_t seed0, const logdet_opts* opts,
+                         uint64_t* req_ids) {
+  if (!s || !h || !shifts || !req_ids) {
+    set_error("submit_shifts: NULL server, handle, shifts or req_ids");
+    return LOGDET_EINVAL;
+  }
+  if (nshift < 1) {
+    set_error("submit_shifts: nshift=%d must be >= 1", nshift);
+    return LOGDET_EINVAL;
+  }
+  std::vector<SolveCfg> cfgs;
+  for (int t = 0; t < nshift; ++t) {
+    SolveCfg c = make_solve_cfg(method, num_probes, krylov_steps, iop_window, seed0 + (uint64_t)t,
+                                opts);
+    c.shift = shifts[t];
+    cfgs.push_back(c);
+  }
+  std::vector<std::pair<size_t, size_t>> runs;
+  LD_TRY(shift_runs(h, cfgs, runs));
+  std::vector<std::shared_ptr<Request>> rs;
+  const double now = now_us();
+  for (const auto& rg : runs) {
+    auto run = std::make_shared<Request>();
+    run->h = h;
+    run->group_cfgs.assign(cfgs.begin() + rg.first, cfgs.begin() + rg.second);
+    run->cfg = run->group_cfgs[0];
+    run->t_submit = now;
+    for (const SolveCfg& c : run->group_cfgs) run->bytes += estimate_solve_bytes(h, c);
+    if (run->bytes > s->budget) {
+      set_error("submit_shifts: a run of %zu shifts needs ~%zu bytes, more than the budget %zu",
+                run->group_cfgs.size(), run->bytes, s->budget);
+      return LOGDET_ENOMEM;
+    }
+    for (const SolveCfg& c : run->group_cfgs) {
+      auto mb = std::make_shared<Request>();
+      mb->h = h;
+      mb->cfg = c;
+      mb->t_submit = now;
+      mb->run = run;
+      run->members.push_back(mb);
+    }
+    rs.push_back(run);
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      set_error("submit_shifts: server is shutting down");
+      return LOGDET_ECANCEL;
+    }
+    size_t t = 0;
+    for (auto& run : rs) {
+      run->id = 0;  // internal
+      for (auto& mb : run->members) {
+        mb->id = s->next_id++;
+        s->all[mb->id] = mb;
+        req_ids[t++] = mb->id;
+        ++s->n_submitted;
+      }
+      s->queue.push_back(run);
+    }
   }
   s->cv_work.notify_all();
   return LOGDET_OK;
@@ -509,6 +618,10 @@ int logdet_cancel(logdet_server* s, uint64_t id) {
     auto it = s->all.find(id);
     if (it == s->all.end()) { set_error("cancel: unknown request"); return LOGDET_ENOENT; }
     auto r = it->second;
+    if (auto run = r->run.lock()) {  // a shift-group member: its whole run stops
+      run->cancel = true;
+      r = run;
+    }
     r->cancel = true;
     if (r->state == RQ_SUSPENDED) {  // held: no slot and no budget to give back
       for (size_t i = 0; i < s->held.size(); ++i)
@@ -560,6 +673,10 @@ int logdet_suspend(logdet_server* s, uint64_t id) {
     auto it = s->all.find(id);
     if (it == s->all.end()) { set_error("suspend: unknown request"); return LOGDET_ENOENT; }
     auto r = it->second;
+    if (!r->run.expired()) {
+      set_error("suspend: request %llu is a shift-group member", (unsigned long long)id);
+      return LOGDET_EINVAL;
+    }
     if (r->state == RQ_QUEUED) {  // not admitted yet: leaves the queue, holds nothing
       for (size_t i = 0; i < s->queue.size(); ++i)
         if (s->queue[i] == r) {

@@ -1255,123 +1255,195 @@ SolveCfg make_solve_cfg(int method, int32_t P, int32_t m, int32_t k, uint64_t se
 // shift sigma_t / c_0, so y = (Q + sigma_t I) x / c_t as in the member's own
 // run.  Everything else of a member's solve (sketch, Hutch++ split, small
 // solves, assembly) is its own.  One gather of the SpMM pass then fetches
-// the x row of every member at once.
+// the x row of every member at once.  GroupSolve is the resumable form: the
+// blocking call drives it with issue_solve, the server steps it like any
+// other solve.
 template <typename T>
-static int group_krylov(logdet_ctx* h, std::vector<Solve<T>*>& ms, DevBuf<T>& Vw, cudaStream_t st) {
-  const int R = (int)ms.size();
-  Solve<T>& m0 = *ms[0];
-  const bool phase1 = m0.c.method == 1 && m0.ph == PH_K1;
-  const int wm = m0.pend_ld;
-  const int ldw = R * wm;
-  const int n = m0.n, m = m0.m;
-  const int method = m0.c.method == 0 ? 0 : 1;
-  const bool track_e = m0.c.method == 1 && !phase1;
-  for (Solve<T>* sv : ms)
-    if (!sv->awaiting || sv->ph != m0.ph || sv->pend_ld != wm || sv->pend_b != m0.pend_b) {
-      set_error("shift group: members out of step");
-      return LOGDET_EINVAL;
+struct GroupSolve : ISolve {
+  logdet_ctx* h;
+  cudaStream_t st;
+  std::vector<std::unique_ptr<Solve<T>>> ms;
+  std::unique_ptr<KRun<T>> w;  // the wide run of the current Krylov phase
+  DevBuf<T> Vw, Xw;            // phase-1 basis (OSA-IOP) or start block of the wide run
+  DevBuf<double> csc, csh;     // per-column scale c_0 / c_t and shift s_t / c_0
+  int ph = PH_SETUP;
+  bool phase1 = false;
+  int wm = 0, ldw = 0;
+
+  GroupSolve(logdet_ctx* h_, const std::vector<SolveCfg>& cfgs, cudaStream_t st_)
+      : h(h_), st(st_), Vw(st_), Xw(st_), csc(st_), csh(st_) {
+    for (const SolveCfg& c : cfgs) {
+      ms.emplace_back(new Solve<T>(h_, c, st_));
+      ms.back()->grouped = true;
     }
-  DevBuf<T> Xw(st);
-  T* X0w;
-  if (phase1) {
-    LD_TRY(Vw.alloc((size_t)n * ldw * m));
-    X0w = Vw.p;
-  } else {
-    LD_TRY(Xw.alloc((size_t)n * ldw));
-    X0w = Xw.p;
   }
-  for (int t = 0; t < R; ++t) {
-    LD_CUDA(cudaMemcpy2DAsync(X0w + (size_t)t * wm, sizeof(T) * ldw, ms[t]->pend_x0, sizeof(T) * wm,
-                              sizeof(T) * wm, n, cudaMemcpyDeviceToDevice, st));
-    ms[t]->release_start();
+
+  int phase() const override { return ph; }
+  bool in_krylov() const override { return ph == PH_K1 || ph == PH_K2; }
+  int krylov_threads() const override { return w ? w->g.threads : 0; }
+  bool is_fp32() const override { return !std::is_same<T, double>::value; }
+  int elem_kind() const override { return ms[0]->elem_kind(); }
+  cudaEvent_t done_event() const override { return ms.back()->done_event(); }
+  size_t bytes_estimate() const override {
+    size_t b = 0;
+    for (const auto& m : ms) b += m->bytes_estimate();
+    return b;
   }
-  std::vector<double> hsc((size_t)ldw), hsh((size_t)ldw);
-  const double c0 = m0.cscale();
-  for (int t = 0; t < R; ++t)
-    for (int q = 0; q < wm; ++q) {
-      hsc[(size_t)t * wm + q] = c0 / ms[t]->cscale();
-      hsh[(size_t)t * wm + q] = ms[t]->c.shift / c0;
+  void set_dev_keys(const uint64_t*) override {}
+  int prepare_host() override {
+    for (auto& m : ms) LD_TRY(m->prepare_host());
+    return LOGDET_OK;
+  }
+  int suspend() override {
+    set_error("shift groups are not suspended");
+    return LOGDET_EINVAL;
+  }
+  int resume() override { return LOGDET_OK; }
+  bool suspended() const override { return false; }
+  int issue_krylov_rest() override { return 1; }
+  int members() const override { return (int)ms.size(); }
+  int assemble(SolveOut& o) override { return ms[0]->assemble(o); }
+  int assemble_member(int t, SolveOut& o) override { return ms[t]->assemble(o); }
+
+  // Every member's current non-Krylov phase; when they all wait for the
+  // group, the wide run of the next Krylov phase starts.
+  int run_phase() override {
+    const int rc = step_members();
+    if (rc) ph = PH_FAILED;
+    return rc;
+  }
+
+  int step_members() {
+    for (auto& m : ms)
+      if (m->ph == PH_SETUP || m->ph == PH_MID || m->ph == PH_FINISH) LD_TRY(m->run_phase());
+    for (auto& m : ms)
+      if (m->ph == PH_FAILED) return LOGDET_ECUDA;
+    if (ms[0]->ph == PH_WAIT) {
+      for (auto& m : ms)
+        if (m->ph != PH_WAIT) {
+          set_error("shift group: members out of step");
+          return LOGDET_ECUDA;
+        }
+      ph = PH_WAIT;
+      return LOGDET_OK;
     }
-  DevBuf<double> csc(st), csh(st);
-  LD_TRY(csc.alloc(ldw));
-  LD_TRY(csh.alloc(ldw));
-  LD_CUDA(cudaMemcpyAsync(csc.p, hsc.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
-  LD_CUDA(cudaMemcpyAsync(csh.p, hsh.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
-  KRun<T> w(st);
-  w.colshift = csh.p;
-  w.colscale = csc.p;
-  w.hctx = h;
-  w.diavals = m0.diav.p;
-  TuneCfg tc;
-  LD_TRY(m0.layout(ldw, track_e, &tc));
-  LD_TRY(w.init(h->rowptr, h->colind, m0.vals.p, n, h->nnz, ldw, ldw, m, m0.kk, method, track_e,
-                X0w, phase1 ? Vw.p : nullptr, m0.c.tol, tc));
-  if (m0.pend_b < wm)  // each member's padding columns stay out of the run, as in its own
-    for (int t = 0; t < R; ++t)
-      LD_CUDA(cudaMemsetAsync(w.ks.active.p + (size_t)t * wm + m0.pend_b, 0,
-                              sizeof(*w.ks.active.p) * (wm - m0.pend_b), st));
-  std::vector<SpmmJob<T>> sj;
-  std::vector<UpdJob<T>> uj;
-  const std::vector<int> widths{ldw};
-  for (int j = 1; j <= m; ++j) {
-    NvtxRange nv("logdet shift-group krylov step");
-    sj.clear();
-    LD_TRY(w.spmm_jobs(j, sj));
-    LD_TRY(launch_spmm_jobs<T>(sj, w.g.threads, st));
-    LD_TRY(launch_scalar_jobs({w.scalar_job(j, w.pass1_dots(j), true)}, widths, SK_COEF, st));
-    if (w.has_pass2(j)) {
-      uj.clear();
-      w.upd_jobs(j, uj);
-      LD_TRY(launch_update_jobs<T>(uj, w.g.threads, st));
-      LD_TRY(launch_scalar_jobs({w.scalar_job(j, w.track_e ? 2 : 1)}, widths, SK_NORM, st));
-    }
-    w.done_steps++;
+    // every mid (OSA-IOP) has read the phase-1 basis: it goes in stream order
+    Vw.release();
+    return start_wide();
   }
-  for (int t = 0; t < R; ++t) {
-    LD_TRY(ms[t]->adopt(w, t * wm));
+
+  int start_wide() {
+    const int R = (int)ms.size();
+    Solve<T>& m0 = *ms[0];
+    phase1 = m0.c.method == 1 && m0.ph == PH_K1;
+    wm = m0.pend_ld;
+    ldw = R * wm;
+    const int n = m0.n, m = m0.m;
+    const int method = m0.c.method == 0 ? 0 : 1;
+    const bool track_e = m0.c.method == 1 && !phase1;
+    for (auto& sv : ms)
+      if (!sv->awaiting || sv->ph != m0.ph || sv->pend_ld != wm || sv->pend_b != m0.pend_b) {
+        set_error("shift group: members out of step");
+        return LOGDET_EINVAL;
+      }
+    T* X0w;
     if (phase1) {
-      ms[t]->vst_ext = Vw.p + (size_t)t * wm;
-      ms[t]->vst_ld = ldw;
+      LD_TRY(Vw.alloc((size_t)n * ldw * m));
+      X0w = Vw.p;
+    } else {
+      LD_TRY(Xw.alloc((size_t)n * ldw));
+      X0w = Xw.p;
     }
+    for (int t = 0; t < R; ++t) {
+      LD_CUDA(cudaMemcpy2DAsync(X0w + (size_t)t * wm, sizeof(T) * ldw, ms[t]->pend_x0, sizeof(T) * wm,
+                                sizeof(T) * wm, n, cudaMemcpyDeviceToDevice, st));
+      ms[t]->release_start();
+    }
+    std::vector<double> hsc((size_t)ldw), hsh((size_t)ldw);
+    const double c0 = m0.cscale();
+    for (int t = 0; t < R; ++t)
+      for (int q = 0; q < wm; ++q) {
+        hsc[(size_t)t * wm + q] = c0 / ms[t]->cscale();
+        hsh[(size_t)t * wm + q] = ms[t]->c.shift / c0;
+      }
+    LD_TRY(csc.alloc(ldw));
+    LD_TRY(csh.alloc(ldw));
+    LD_CUDA(cudaMemcpyAsync(csc.p, hsc.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
+    LD_CUDA(cudaMemcpyAsync(csh.p, hsh.data(), sizeof(double) * ldw, cudaMemcpyHostToDevice, st));
+    // (the host arrays must outlive the copies: the copies are pageable, so
+    // they complete before cudaMemcpyAsync returns)
+    w.reset(new KRun<T>(st));
+    w->colshift = csh.p;
+    w->colscale = csc.p;
+    w->hctx = h;
+    w->diavals = m0.diav.p;
+    TuneCfg tc;
+    LD_TRY(m0.layout(ldw, track_e, &tc));
+    LD_TRY(w->init(h->rowptr, h->colind, m0.vals.p, n, h->nnz, ldw, ldw, m, m0.kk, method, track_e,
+                   X0w, phase1 ? Vw.p : nullptr, m0.c.tol, tc));
+    if (m0.pend_b < wm)  // each member's padding columns stay out of the run, as in its own
+      for (int t = 0; t < R; ++t)
+        LD_CUDA(cudaMemsetAsync(w->ks.active.p + (size_t)t * wm + m0.pend_b, 0,
+                                sizeof(*w->ks.active.p) * (wm - m0.pend_b), st));
+    ph = m0.ph;  // PH_K1 or PH_K2
+    return LOGDET_OK;
   }
-  return LOGDET_OK;
-}
+
+  int add_pass1(void* vec, std::vector<ScalarJob>& coef, std::vector<int>& widths) override {
+    auto& v = *static_cast<std::vector<SpmmJob<T>>*>(vec);
+    const int j = w->next_step();
+    LD_TRY(w->spmm_jobs(j, v));
+    coef.push_back(w->scalar_job(j, w->pass1_dots(j), true));
+    widths.push_back(w->ld);
+    return LOGDET_OK;
+  }
+
+  bool add_pass2(void* vec, std::vector<ScalarJob>& norm, std::vector<int>& widths) override {
+    const int j = w->next_step();
+    if (!w->has_pass2(j)) return false;
+    auto& v = *static_cast<std::vector<UpdJob<T>>*>(vec);
+    w->upd_jobs(j, v);
+    norm.push_back(w->scalar_job(j, w->track_e ? 2 : 1));
+    widths.push_back(w->ld);
+    return true;
+  }
+
+  void step_issued() override {
+    w->done_steps++;
+    if (!w->finished()) return;
+    // every member takes its probes' scalar history back
+    for (int t = 0; t < (int)ms.size(); ++t) {
+      if (ms[t]->adopt(*w, t * wm)) {
+        ph = PH_FAILED;
+        return;
+      }
+      if (phase1) {
+        ms[t]->vst_ext = Vw.p + (size_t)t * wm;
+        ms[t]->vst_ld = ldw;
+      }
+    }
+    w.reset();
+    Xw.release();
+    csc.release();
+    csh.release();
+    ph = ms[0]->ph;  // PH_MID or PH_FINISH
+  }
+};
 
 template <typename T>
 static int solve_shifts_t(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
                           std::vector<SolveOut>& outs) {
-  std::vector<std::unique_ptr<Solve<T>>> own;
-  std::vector<Solve<T>*> ms;
-  for (const SolveCfg& c : cfgs) {
-    own.emplace_back(new Solve<T>(h, c, st));
-    own.back()->grouped = true;
-    ms.push_back(own.back().get());
-  }
-  DevBuf<T> Vw(st);
-  // setup -> [phase 1] -> mid -> [phase 2] -> finish, every member in step
-  for (int round = 0; round < 6; ++round) {
-    bool all_done = true;
-    for (Solve<T>* sv : ms) {
-      if (sv->ph == PH_SETUP || sv->ph == PH_MID || sv->ph == PH_FINISH) LD_TRY(sv->run_phase());
-      all_done = all_done && sv->ph == PH_WAIT;
-    }
-    if (all_done) break;
-    if (ms[0]->ph == PH_K2) Vw.release();  // every mid has read the phase-1 basis
-    LD_TRY(group_krylov<T>(h, ms, Vw, st));
-  }
-  for (Solve<T>* sv : ms)
-    if (sv->ph != PH_WAIT) {
-      set_error("shift group: solve did not finish");
-      return LOGDET_ECUDA;
-    }
-  LD_CUDA(cudaEventSynchronize(ms.back()->done_event()));
-  outs.resize(ms.size());
-  for (size_t t = 0; t < ms.size(); ++t) LD_TRY(ms[t]->assemble(outs[t]));
+  GroupSolve<T> g(h, cfgs, st);
+  LD_TRY(issue_solve(&g, st));
+  LD_CUDA(cudaEventSynchronize(g.done_event()));
+  outs.resize(cfgs.size());
+  for (int t = 0; t < g.members(); ++t) LD_TRY(g.assemble_member(t, outs[t]));
   return LOGDET_OK;
 }
 
-int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
-                 std::vector<SolveOut>& outs) {
+int shift_runs(logdet_ctx* h, const std::vector<SolveCfg>& cfgs,
+               std::vector<std::pair<size_t, size_t>>& runs) {
+  runs.clear();
   if (cfgs.empty()) {
     set_error("shift group: no shifts");
     return LOGDET_EINVAL;
@@ -1393,12 +1465,34 @@ int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t 
   const size_t each = estimate_solve_bytes(h, cfgs[0]);
   const size_t by_mem = std::max<size_t>(1, (size_t)(0.85 * (double)total_b) / std::max<size_t>(each, 1));
   const int cap = (int)std::max<size_t>(1, std::min<size_t>(kMaxGroupWidth / width, by_mem));
-  const int runs = div_up((int)cfgs.size(), cap);
-  const int per_run = div_up((int)cfgs.size(), runs);  // balanced runs
+  const int nruns = div_up((int)cfgs.size(), cap);
+  const size_t per_run = (size_t)div_up((int)cfgs.size(), nruns);  // balanced runs
+  for (size_t t0 = 0; t0 < cfgs.size(); t0 += per_run)
+    runs.push_back({t0, std::min(cfgs.size(), t0 + per_run)});
+  return LOGDET_OK;
+}
+
+std::unique_ptr<ISolve> make_group_solve(logdet_ctx* h, const std::vector<SolveCfg>& cfgs,
+                                         cudaStream_t st, int* rc) {
+  *rc = LOGDET_OK;
+  if (cfgs.empty()) {
+    *rc = LOGDET_EINVAL;
+    return nullptr;
+  }
+  if (cfgs[0].precision == LOGDET_FP64)
+    return std::unique_ptr<ISolve>(new GroupSolve<double>(h, cfgs, st));
+  if (cfgs[0].precision == LOGDET_MIXED_BF16VEC)
+    return std::unique_ptr<ISolve>(new GroupSolve<bf16>(h, cfgs, st));
+  return std::unique_ptr<ISolve>(new GroupSolve<float>(h, cfgs, st));
+}
+
+int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
+                 std::vector<SolveOut>& outs) {
+  std::vector<std::pair<size_t, size_t>> runs;
+  LD_TRY(shift_runs(h, cfgs, runs));
   outs.clear();
-  for (size_t t0 = 0; t0 < cfgs.size(); t0 += per_run) {
-    const std::vector<SolveCfg> part(cfgs.begin() + t0,
-                                     cfgs.begin() + std::min(cfgs.size(), t0 + per_run));
+  for (const auto& rg : runs) {
+    const std::vector<SolveCfg> part(cfgs.begin() + rg.first, cfgs.begin() + rg.second);
     std::vector<SolveOut> po;
     int rc;
     if (cfgs[0].precision == LOGDET_FP64) rc = solve_shifts_t<double>(h, part, st, po);

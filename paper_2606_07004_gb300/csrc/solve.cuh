@@ -186,6 +186,9 @@ struct ISolve {
   virtual int suspend() = 0;
   virtual int resume() = 0;
   virtual bool suspended() const = 0;
+  // Shift groups hold several solves: member t's result.
+  virtual int members() const { return 1; }
+  virtual int assemble_member(int t, SolveOut& o) { return t == 0 ? assemble(o) : LOGDET_EINVAL; }
 };
 
 std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, int* rc);
@@ -201,6 +204,12 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
 constexpr int kMaxGroupWidth = 1024;
 int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t st,
                  std::vector<SolveOut>& outs);
+// The consecutive runs [begin, end) those solves go through (validates them).
+int shift_runs(logdet_ctx* h, const std::vector<SolveCfg>& cfgs,
+               std::vector<std::pair<size_t, size_t>>& runs);
+// One run as a resumable solve (the server steps it like any other).
+std::unique_ptr<ISolve> make_group_solve(logdet_ctx* h, const std::vector<SolveCfg>& cfgs,
+                                         cudaStream_t st, int* rc);
 
 // Queue every phase of a solve on its stream, with batches of one, until it
 // waits for its result copies; no host synchronisation (so the sequence can

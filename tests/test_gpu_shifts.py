@@ -183,3 +183,52 @@ def test_group_breakdown_and_tiny_matrices(method, k):
     for t in range(len(shifts)):
         assert g[t].s_eff == own[t].s_eff
         assert rel(g[t].logdet, own[t].logdet) <= 1e-12
+
+
+@pytest.mark.parametrize("method,k,precision", [(0, 0, B.FP64), (1, 4, B.MIXED_FP32)])
+def test_server_shift_groups_equal_the_blocking_group(method, k, precision):
+    # through the server, alongside ordinary requests: each member equals the
+    # blocking group call bit for bit, and the ordinary requests their
+    # blocking solves
+    A = W.laplacian_2d(70, 60, shift=0.0)
+    shifts = list(np.linspace(0.05, 1.0, 5))
+    with B.Handle.from_csr(A) as h:
+        ref = _group(h, method, shifts, 30, 20, k, 4, precision=precision)
+        plain_ref = _single(h, method, 30, 20, k, 9, 0.2, precision=precision)
+        with B.Server(16 << 30, max_slots=8) as srv:
+            other = srv.submit(h, method, 30, 20, k, seed=9, precision=precision, shift=0.2)
+            ids = srv.submit_shifts(h, method, shifts, 30, 20, k, seed0=4, precision=precision)
+            got = [srv.wait(i) for i in ids]
+            plain = srv.wait(other)
+            assert srv.stats()["completed"] == len(shifts) + 1
+    for a, b in zip(got, ref):
+        assert a.logdet == b.logdet
+        assert (a.tr_sub, a.tr_res, a.steps_max, a.status_bits) == \
+            (b.tr_sub, b.tr_res, b.steps_max, b.status_bits)
+    assert plain.logdet == plain_ref.logdet
+
+
+def test_server_shift_group_runs_cancel_and_suspend():
+    A = W.laplacian_2d(20, shift=0.0)
+    shifts = np.linspace(0.1, 1.0, 24)          # two runs of 12 (FP64, 44 columns each)
+    with B.Handle.from_csr(A) as h:
+        ref = h.osaiop_shifts(shifts, 64, 6, iop_window=2, seed0=5)
+        with B.Server(16 << 30, max_slots=4) as srv:
+            ids = srv.submit_shifts(h, B.METHOD_OSAIOP, shifts, 64, 6, 2, seed0=5)
+            got = [srv.wait(i) for i in ids]
+            with pytest.raises(B.LogdetError) as e:
+                srv.suspend(ids[0])              # finished member
+            assert e.value.code == B.EINVAL
+            # cancelling one member cancels its run (and nothing else)
+            big = W.laplacian_3d(64, shift=0.0)
+            with B.Handle.from_csr(big) as hb:
+                ids2 = srv.submit_shifts(hb, B.METHOD_OSLQ, [0.1, 0.2, 0.3], 30, 200, seed0=1)
+                with pytest.raises(B.LogdetError) as e:
+                    srv.suspend(ids2[1])
+                assert e.value.code == B.EINVAL
+                srv.cancel(ids2[1])
+                for i in ids2:
+                    with pytest.raises(B.LogdetError) as e:
+                        srv.wait(i)
+                    assert e.value.code == B.ECANCEL
+    assert [r.logdet for r in got] == [r.logdet for r in ref]
