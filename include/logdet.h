@@ -54,6 +54,14 @@ extern "C" {
                                  FP64 small solves */
 #define LOGDET_MIXED_BF16VEC 2 /* as MIXED_FP32 but the Krylov vectors are stored in
                                  BF16 (FP32 arithmetic): a trial of the error budget */
+#define LOGDET_MIXED_F32X2 3  /* FP32 matrix values; Krylov vectors stored as
+                                 double-float pairs (hi + lo, two FP32 words, about
+                                 48 significand bits) and computed on in double-float
+                                 arithmetic on the FP32 pipe, compensated dots; the
+                                 Hutch++ split and small solves in FP64.  For
+                                 ill-conditioned matrices whose FP32-vector error
+                                 exceeds the budget.  CSR operators only (EINVAL for
+                                 gridded operators) */
 
 #define LOGDET_METHOD_OSLQ    0
 #define LOGDET_METHOD_OSAIOP  1
@@ -84,7 +92,7 @@ typedef struct {
 } logdet_result;
 
 typedef struct {
-  int32_t precision;   /* LOGDET_FP64 (default) or LOGDET_MIXED_FP32 */
+  int32_t precision;   /* LOGDET_FP64 (default), LOGDET_MIXED_FP32, _BF16VEC or _F32X2 */
   double tol;          /* breakdown threshold on h_{m+1,m} / beta_j; 0 = 1e-12 */
   double lambda_lo;    /* spectral bounds; both 0 = clamped Gershgorin interval */
   double lambda_hi;

@@ -27,7 +27,7 @@ _lib = C.CDLL(LIB_PATH)
 OK, PENDING = 0, 1
 EINVAL, ENOMEM, ENOTSPD, ETIMEOUT, ECUDA, ENOENT, ECANCEL = -1, -2, -3, -4, -5, -6, -7
 VALS_F64, VALS_F32 = 0, 1
-FP64, MIXED_FP32, MIXED_BF16VEC = 0, 1, 2
+FP64, MIXED_FP32, MIXED_BF16VEC, MIXED_F32X2 = 0, 1, 2, 3
 METHOD_OSLQ, METHOD_OSAIOP = 0, 1
 ST_BREAKDOWN, ST_NONPOS_RITZ, ST_RANK_DEFICIENT, ST_LOG_FAILED = 1, 2, 4, 8
 

@@ -110,15 +110,80 @@ __device__ __forceinline__ double probe_value(uint64_t key, uint32_t col, uint32
 // ---------------------------------------------------------------------------
 using bf16 = __nv_bfloat16;
 
+// Double-float vectors (LOGDET_MIXED_F32X2): each entry is stored as the
+// unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2 (about 48
+// significand bits in 8 bytes), and computed on in dfloat arithmetic built
+// from error-free transformations on the FP32 pipe (Knuth's TwoSum, the
+// FMA TwoProduct; the double-double algorithms of Hida, Li and Bailey 2001
+// at single precision).  The _rn intrinsics keep the compiler from
+// contracting the error terms into FMAs.
+struct f32x2 {
+  float hi, lo;
+};
+// dfloat and its operators live in a namespace of their own: found by
+// argument-dependent lookup for dfloat operands, they do not hide ::fma
+// from unqualified calls on doubles and floats elsewhere in ld.
+namespace dfl {
+struct dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr dfloat(float h) : hi(h), lo(0.f) {}
+  __host__ __device__ constexpr dfloat(int i) : hi((float)i), lo(0.f) {}
+  __host__ __device__ explicit dfloat(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfloat df_renorm(float s, float e) {  // quick TwoSum, |s| >= |e|
+  const float t = __fadd_rn(s, e);
+  return dfloat(t, __fsub_rn(e, __fsub_rn(t, s)));
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_renorm(p, e);
+}
+// a b + c: the unnormalised TwoProduct of a b (with both cross terms) fed
+// straight into the TwoSum with c, one renormalisation at the end.
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  const float s = __fadd_rn(p, c.hi);
+  const float bb = __fsub_rn(s, p);
+  float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(c.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(pe, c.lo));
+  return df_renorm(s, e);
+}
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) { return df_mul(a, b); }
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(a, b); }
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = df_add(a, b); }
+}  // namespace dfl
+using dfl::dfloat;
+
 template <typename T> struct Compute { using type = T; };
 template <> struct Compute<bf16> { using type = float; };
+template <> struct Compute<f32x2> { using type = dfloat; };
 template <typename T> struct ValOf { using type = T; };
 template <> struct ValOf<bf16> { using type = float; };
+template <> struct ValOf<f32x2> { using type = float; };
 
 template <typename T> struct Vec16;
 template <> struct Vec16<double> { using type = double2; static constexpr int N = 2; };
 template <> struct Vec16<float>  { using type = float4;  static constexpr int N = 4; };
 template <> struct Vec16<bf16>   { using type = uint2;   static constexpr int N = 4; };
+template <> struct Vec16<f32x2>  { using type = float4;  static constexpr int N = 2; };
 
 template <typename T>
 __device__ __forceinline__ void load_vec(const T* p, typename Compute<T>::type (&v)[Vec16<T>::N]) {
@@ -126,6 +191,7 @@ __device__ __forceinline__ void load_vec(const T* p, typename Compute<T>::type (
   V t = __ldg(reinterpret_cast<const V*>(p));
   if constexpr (std::is_same<T, double>::value) { v[0] = t.x; v[1] = t.y; }
   else if constexpr (std::is_same<T, float>::value) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+  else if constexpr (std::is_same<T, f32x2>::value) { v[0] = dfloat(t.x, t.y); v[1] = dfloat(t.z, t.w); }
   else {
     const uint32_t w[2] = {t.x, t.y};
 #pragma unroll
@@ -144,6 +210,9 @@ __device__ __forceinline__ void store_vec(T* p, const typename Compute<T>::type 
   V t;
   if constexpr (std::is_same<T, double>::value) { t.x = v[0]; t.y = v[1]; }
   else if constexpr (std::is_same<T, float>::value) { t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = v[3]; }
+  else if constexpr (std::is_same<T, f32x2>::value) {
+    t.x = v[0].hi; t.y = v[0].lo; t.z = v[1].hi; t.w = v[1].lo;
+  }
   else {
     uint32_t w[2];
 #pragma unroll
@@ -161,6 +230,10 @@ template <typename To, typename From>
 __host__ __device__ __forceinline__ To cvt(From x) {
   if constexpr (std::is_same<To, bf16>::value) return __float2bfloat16_rn((float)x);
   else if constexpr (std::is_same<From, bf16>::value) return (To)__bfloat162float(x);
+  else if constexpr (std::is_same<To, f32x2>::value) {
+    const dfloat d((double)x);
+    return f32x2{d.hi, d.lo};
+  } else if constexpr (std::is_same<From, f32x2>::value) return (To)((double)x.hi + (double)x.lo);
   else return (To)x;
 }
 
@@ -277,6 +350,23 @@ template <typename T> struct PartOf;
 template <> struct PartOf<double> { using type = double; };
 template <> struct PartOf<float>  { using type = float2; };
 template <> struct PartOf<bf16>   { using type = float2; };
+
+// Double-float blocks: a compensated FP32 sum of hi * hi (as AccF) with the
+// cross terms hi * lo + lo * hi added to its error word; partials as AccF's.
+struct AccDF {
+  AccF a;
+  __device__ __forceinline__ void zero() { a.zero(); }
+  __device__ __forceinline__ void fma(dfloat u, dfloat y) {
+    a.fma(u.hi, y.hi);
+    a.e = __fadd_rn(a.e, __fmaf_rn(u.hi, y.lo, __fmul_rn(u.lo, y.hi)));
+  }
+  __device__ __forceinline__ void add(const AccDF& o) { a.add(o.a); }
+  __device__ __forceinline__ double value() const { return a.value(); }
+};
+template <> struct AccOf<f32x2> { using type = AccDF; };
+template <> struct PartOf<f32x2> { using type = float2; };
+__device__ __forceinline__ void put_part(float2* p, const AccDF& a) { *p = make_float2(a.a.s, a.a.e); }
+__device__ __forceinline__ void get_part(const float2* p, AccDF& a) { float2 t = *p; a.a.s = t.x; a.a.e = t.y; }
 
 __device__ __forceinline__ void put_part(double* p, const AccD& a) { *p = a.s; }
 __device__ __forceinline__ void put_part(float2* p, const AccF& a) { *p = make_float2(a.s, a.e); }

@@ -562,6 +562,7 @@ int colnorm_partials(const T* X, int n, int ld, int tile_rows, int ntiles,
 template int colnorm_partials<double>(const double*, int, int, int, int, double*, int, cudaStream_t);
 template int colnorm_partials<float>(const float*, int, int, int, int, float2*, int, cudaStream_t);
 template int colnorm_partials<bf16>(const bf16*, int, int, int, int, float2*, int, cudaStream_t);
+template int colnorm_partials<f32x2>(const f32x2*, int, int, int, int, float2*, int, cudaStream_t);
 
 // ===========================================================================
 // Gauss quadrature of a symmetric tridiagonal (Sec. 3.1): eigenvalues theta_k
@@ -1210,6 +1211,8 @@ template int probe_fill<float>(uint64_t, int, int, int, float*, int, cudaStream_
                                  const uint64_t*);
 template int probe_fill<bf16>(uint64_t, int, int, int, bf16*, int, cudaStream_t, int,
                                  const uint64_t*);
+template int probe_fill<f32x2>(uint64_t, int, int, int, f32x2*, int, cudaStream_t, int,
+                                 const uint64_t*);
 
 __global__ void k_fill_double(double* out, size_t count, double value) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
@@ -1247,6 +1250,8 @@ template int convert_block<double, float>(const double*, int, float*, int, int, 
 template int convert_block<float, double>(const float*, int, double*, int, int, int, cudaStream_t);
 template int convert_block<double, bf16>(const double*, int, bf16*, int, int, int, cudaStream_t);
 template int convert_block<bf16, double>(const bf16*, int, double*, int, int, int, cudaStream_t);
+template int convert_block<double, f32x2>(const double*, int, f32x2*, int, int, int, cudaStream_t);
+template int convert_block<f32x2, double>(const f32x2*, int, double*, int, int, int, cudaStream_t);
 
 // ===========================================================================
 // OSA-IOP sketch assembly: Y[:, p] = sum_j w[j][p] V_j[:, p]
@@ -1298,14 +1303,28 @@ __global__ void k_sketch_assemble(const T* __restrict__ V, int n, int ncols, int
 #pragma unroll
         for (int c = 0; c < N; ++c) {
           const float2 wj = sw[j * ncols + p0 + c];
-          const float p = wj.x * x[c];
-          float pe = fmaf(wj.x, x[c], -p);
-          pe = fmaf(wj.y, x[c], pe);
-          const float t = sh[c] + p;
-          const float z = t - sh[c];
-          const float err = (sh[c] - (t - z)) + (p - z);
-          sl[c] += err + pe;
-          sh[c] = t;
+          if constexpr (std::is_same<T, f32x2>::value) {
+            // double-float x: the product's cross term w_hi x_lo joins the
+            // error word (w_lo x_lo is below the pair's precision)
+            const float p = __fmul_rn(wj.x, x[c].hi);
+            float pe = __fmaf_rn(wj.x, x[c].hi, -p);
+            pe = __fmaf_rn(wj.y, x[c].hi, pe);
+            pe = __fmaf_rn(wj.x, x[c].lo, pe);
+            const float t = __fadd_rn(sh[c], p);
+            const float z = __fsub_rn(t, sh[c]);
+            const float err = __fadd_rn(__fsub_rn(sh[c], __fsub_rn(t, z)), __fsub_rn(p, z));
+            sl[c] = __fadd_rn(sl[c], __fadd_rn(err, pe));
+            sh[c] = t;
+          } else {
+            const float p = wj.x * x[c];
+            float pe = fmaf(wj.x, x[c], -p);
+            pe = fmaf(wj.y, x[c], pe);
+            const float t = sh[c] + p;
+            const float z = t - sh[c];
+            const float err = (sh[c] - (t - z)) + (p - z);
+            sl[c] += err + pe;
+            sh[c] = t;
+          }
         }
       } else {
 #pragma unroll
@@ -1373,10 +1392,13 @@ template int sketch_assemble_cols<float>(const float*, int, int, int, int, const
                                          int, cudaStream_t);
 template int sketch_assemble_cols<bf16>(const bf16*, int, int, int, int, const double*, double*,
                                         int, cudaStream_t);
+template int sketch_assemble_cols<f32x2>(const f32x2*, int, int, int, int, const double*, double*,
+                                         int, cudaStream_t);
 
 template int sketch_assemble<double>(const double*, int, int, int, const double*, double*, int, cudaStream_t);
 template int sketch_assemble<float>(const float*, int, int, int, const double*, double*, int, cudaStream_t);
 template int sketch_assemble<bf16>(const bf16*, int, int, int, const double*, double*, int, cudaStream_t);
+template int sketch_assemble<f32x2>(const f32x2*, int, int, int, const double*, double*, int, cudaStream_t);
 
 }  // namespace ld
 

@@ -130,6 +130,7 @@ __device__ __forceinline__ void load_v(const T* p, typename Compute<T>::type (&v
     const V t = __ldcg(reinterpret_cast<const V*>(p));
     if constexpr (std::is_same<T, double>::value) { v[0] = t.x; v[1] = t.y; }
     else if constexpr (std::is_same<T, float>::value) { v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (std::is_same<T, f32x2>::value) { v[0] = dfloat(t.x, t.y); v[1] = dfloat(t.z, t.w); }
     else {
       const uint32_t w[2] = {t.x, t.y};
 #pragma unroll
@@ -147,6 +148,13 @@ __device__ __forceinline__ void load_v(const T* p, typename Compute<T>::type (&v
 // then ran at half the FP64 and HBM peaks (a few spilled registers cost
 // less than the second CTA gains).  0 leaves every other instance's
 // register choice to the compiler, as without the hint.
+// Blocks whose passes are bound by memory latency and computed on the FP32
+// pipe (FP32, BF16 and double-float entries: a double-float thread holds two
+// entries where an FP32 one holds four, so their registers match); FP64
+// blocks are bound by the FP64 pipe and take the register-rich instances.
+template <typename T>
+constexpr bool narrow_block() { return !std::is_same<T, double>::value; }
+
 template <typename T, int N>
 constexpr int fp64_wide_min_ctas() { return (std::is_same<T, double>::value && N >= kMaxWin) ? 2 : 0; }
 
@@ -269,7 +277,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
       // FP64, the extra registers cost more occupancy than the overlap gains
       // (power-law graph, four dots: 435 -> 720 ms per solve).  The
       // accumulation order is the same either way.
-      constexpr bool kPipe = !std::is_same<T, double>::value && NDOT <= 1;
+      constexpr bool kPipe = narrow_block<T>() && NDOT <= 1;
       const T* xcol = J.x + col0;
       // FP32 / BF16: the thread's column shift and scale converted from
       // FP64 once per tile, not once per row (the conversion runs on the
@@ -309,7 +317,7 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
         // solve.  The instance for up to four dots keeps late loads: early
         // loads of all four cost the second CTA per SM (428 -> 666 ms), and
         // of the first two, at two CTAs per SM, still lost (427 -> 584 ms).
-        constexpr bool kEarlyDots = !std::is_same<T, double>::value && NDOT == 2;
+        constexpr bool kEarlyDots = narrow_block<T>() && NDOT == 2;
         CT ue[kEarlyDots ? NDOT : 1][V];
         if constexpr (kEarlyDots) {
 #pragma unroll
@@ -443,11 +451,15 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
 // The same caps on the update pass lost (window 4 11.6 -> 13.0 ms, window 8
 // 26.4 -> 38.4 ms): it streams, and keeps its registers.  Register
 // allocation does not change the arithmetic: results are bitwise the same.
-template <int NDOT>
-constexpr int lo_spmm_regs() { return NDOT > 4 ? 88 : 56; }
+// (Double-float blocks with the software-pipelined single-dot loop keep 64:
+// at 56 that instance spilled its prefetched row.)
+template <typename T, int NDOT>
+constexpr int lo_spmm_regs() {
+  return NDOT > 4 ? 88 : (std::is_same<T, f32x2>::value && NDOT <= 1) ? 64 : 56;
+}
 
 template <typename T, int NDOT>
-__global__ void __maxnreg__(lo_spmm_regs<NDOT>())
+__global__ void __maxnreg__((lo_spmm_regs<T, NDOT>()))
     k_spmm_lo(const __grid_constant__ SpmmBatch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_entry();
@@ -456,7 +468,7 @@ __global__ void __maxnreg__(lo_spmm_regs<NDOT>())
 
 template <typename T, int NDOT>
 constexpr auto spmm_kernel() {
-  if constexpr (std::is_same<T, double>::value) return k_spmm<T, NDOT>;
+  if constexpr (!narrow_block<T>()) return k_spmm<T, NDOT>;
   else return k_spmm_lo<T, NDOT>;
 }
 
@@ -561,7 +573,7 @@ __device__ __forceinline__ void update_tiles(const Batch& B, int gt0, int stride
       // order in which the rows enter the norm, are those of one row at a
       // time.  (FP64 is bound by its ALU; BF16 blocks measured 2x slower
       // with two rows: their registers cost occupancy.)
-      constexpr int kU = (std::is_same<T, float>::value && NB <= 4) ? 2 : 1;
+      constexpr int kU = ((std::is_same<T, float>::value || std::is_same<T, f32x2>::value) && NB <= 4) ? 2 : 1;
       if constexpr (kU > 1) {
       for (int row = row0 + r; row < row1; row += kU * R) {
         bool on[kU];
@@ -1391,9 +1403,11 @@ int launch_init_sigma(const ScalarBatch& b, cudaStream_t s) { return launch_scal
 template int launch_spmm<double>(const SpmmBatch<double>&, int, cudaStream_t);
 template int launch_spmm<float>(const SpmmBatch<float>&, int, cudaStream_t);
 template int launch_spmm<bf16>(const SpmmBatch<bf16>&, int, cudaStream_t);
+template int launch_spmm<f32x2>(const SpmmBatch<f32x2>&, int, cudaStream_t);
 template int launch_update<double>(const UpdBatch<double>&, int, cudaStream_t);
 template int launch_update<float>(const UpdBatch<float>&, int, cudaStream_t);
 template int launch_update<bf16>(const UpdBatch<bf16>&, int, cudaStream_t);
+template int launch_update<f32x2>(const UpdBatch<f32x2>&, int, cudaStream_t);
 
 }  // namespace ld
 

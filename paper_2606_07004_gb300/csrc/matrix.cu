@@ -448,5 +448,7 @@ template int spmm_block<float>(const int*, const int*, const float*, int, const 
                                 cudaStream_t, const double*, logdet_ctx*);
 template int spmm_block<bf16>(const int*, const int*, const float*, int, const bf16*, bf16*, int,
                                 cudaStream_t, const double*, logdet_ctx*);
+template int spmm_block<f32x2>(const int*, const int*, const float*, int, const f32x2*, f32x2*, int,
+                                 cudaStream_t, const double*, logdet_ctx*);
 
 }  // namespace ld

@@ -188,28 +188,32 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   std::map<int, std::vector<UpdJob<double>>> ud;
   std::map<int, std::vector<UpdJob<float>>> uf;
   std::map<int, std::vector<UpdJob<bf16>>> ub;
+  std::map<int, std::vector<SpmmJob<f32x2>>> sx;
+  std::map<int, std::vector<UpdJob<f32x2>>> ux;
   std::vector<ScalarJob> coef, norm;
   std::vector<int> wc, wn;
   std::vector<ISolve*> stepping;
+  // A solve's jobs of one pass into the groups of its element type.
+  auto pass1 = [&](auto& groups, ISolve* sv, int th) {
+    typename std::decay_t<decltype(groups)>::mapped_type tmp;
+    const int rc = sv->add_pass1(&tmp, coef, wc);
+    if (!rc) put(groups, tmp, th);
+    return rc;
+  };
+  auto pass2 = [&](auto& groups, ISolve* sv, int th) {
+    typename std::decay_t<decltype(groups)>::mapped_type tmp;
+    sv->add_pass2(&tmp, norm, wn);
+    put(groups, tmp, th);
+  };
   for (auto& r : act) {
     ISolve* sv = r->solve.get();
     if (!sv || !sv->in_krylov() || r->rc) continue;
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
-    int rc;
-    if (ek == 0) {
-      std::vector<SpmmJob<double>> tmp;
-      rc = sv->add_pass1(&tmp, coef, wc);
-      if (!rc) put(sd, tmp, th);
-    } else if (ek == 1) {
-      std::vector<SpmmJob<float>> tmp;
-      rc = sv->add_pass1(&tmp, coef, wc);
-      if (!rc) put(sf, tmp, th);
-    } else {
-      std::vector<SpmmJob<bf16>> tmp;
-      rc = sv->add_pass1(&tmp, coef, wc);
-      if (!rc) put(sb, tmp, th);
-    }
+    const int rc = ek == 0   ? pass1(sd, sv, th)
+                   : ek == 1 ? pass1(sf, sv, th)
+                   : ek == 2 ? pass1(sb, sv, th)
+                             : pass1(sx, sv, th);
     if (rc) {
       r->rc = rc;  // this request fails; the others step on
       continue;
@@ -220,27 +224,20 @@ int logdet_server::tick(std::vector<std::shared_ptr<Request>>& act) {
   for (auto& kv : sd) LD_TRY(launch_spmm_jobs<double>(kv.second, kv.first / 32, st));
   for (auto& kv : sf) LD_TRY(launch_spmm_jobs<float>(kv.second, kv.first / 32, st));
   for (auto& kv : sb) LD_TRY(launch_spmm_jobs<bf16>(kv.second, kv.first / 32, st));
+  for (auto& kv : sx) LD_TRY(launch_spmm_jobs<f32x2>(kv.second, kv.first / 32, st));
   LD_TRY(launch_scalar_jobs(coef, wc, SK_COEF, st));
   for (ISolve* sv : stepping) {
     const int th = sv->krylov_threads();
     const int ek = sv->elem_kind();
-    if (ek == 0) {
-      std::vector<UpdJob<double>> tmp;
-      sv->add_pass2(&tmp, norm, wn);
-      put(ud, tmp, th);
-    } else if (ek == 1) {
-      std::vector<UpdJob<float>> tmp;
-      sv->add_pass2(&tmp, norm, wn);
-      put(uf, tmp, th);
-    } else {
-      std::vector<UpdJob<bf16>> tmp;
-      sv->add_pass2(&tmp, norm, wn);
-      put(ub, tmp, th);
-    }
+    if (ek == 0) pass2(ud, sv, th);
+    else if (ek == 1) pass2(uf, sv, th);
+    else if (ek == 2) pass2(ub, sv, th);
+    else pass2(ux, sv, th);
   }
   for (auto& kv : ud) LD_TRY(launch_update_jobs<double>(kv.second, kv.first / 32, st));
   for (auto& kv : uf) LD_TRY(launch_update_jobs<float>(kv.second, kv.first / 32, st));
   for (auto& kv : ub) LD_TRY(launch_update_jobs<bf16>(kv.second, kv.first / 32, st));
+  for (auto& kv : ux) LD_TRY(launch_update_jobs<f32x2>(kv.second, kv.first / 32, st));
   if (!norm.empty()) LD_TRY(launch_scalar_jobs(norm, wn, SK_NORM, st));
   for (ISolve* sv : stepping) sv->step_issued();
   n_batched_steps += (int64_t)stepping.size();

@@ -55,11 +55,11 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
     return LOGDET_EINVAL;
   }
   if (c.precision != LOGDET_FP64 && c.precision != LOGDET_MIXED_FP32 &&
-      c.precision != LOGDET_MIXED_BF16VEC) {
+      c.precision != LOGDET_MIXED_BF16VEC && c.precision != LOGDET_MIXED_F32X2) {
     set_error("precision %d unknown", c.precision);
     return LOGDET_EINVAL;
   }
-  if (h->kind == 1 && c.precision == LOGDET_MIXED_BF16VEC) {
+  if (h->kind == 1 && (c.precision == LOGDET_MIXED_BF16VEC || c.precision == LOGDET_MIXED_F32X2)) {
     set_error("gridded operators support FP64 and mixed FP32 blocks only");
     return LOGDET_EINVAL;
   }
@@ -70,7 +70,7 @@ int validate_cfg(const logdet_ctx* h, const SolveCfg& c) {
   if (c.block_width > 0 && h->kind != 1) {
     // Every Krylov block (s + r probes; OSA-IOP's s sketch columns) rounded
     // up to whole 16-byte vectors must split into slices of the width.
-    const int vec = c.precision == LOGDET_FP64 ? 2 : 4;
+    const int vec = precision_vec(c.precision);
     const int ld = round_up(s + r, vec), lds = std::max(round_up(s, vec), vec);
     bool ok = c.block_width % vec == 0;
     for (int w : {ld, c.method == 1 && s > 0 ? lds : ld})
@@ -277,8 +277,8 @@ int KRun<T>::spmm_jobs(int j, std::vector<SpmmJob<T>>& out) const {
 
 template <typename T>
 int KRun<T>::grid_pass1(int j) {
-  if constexpr (std::is_same<T, bf16>::value) {
-    set_error("gridded operators do not take BF16 blocks");
+  if constexpr (std::is_same<T, bf16>::value || std::is_same<T, f32x2>::value) {
+    set_error("gridded operators take FP64 and FP32 blocks only");
     return LOGDET_EINVAL;
   } else {
     using CT = typename Compute<T>::type;
@@ -347,7 +347,7 @@ ScalarJob KRun<T>::scalar_job(int j, int ndots, bool spmm_pass) const {
 
 template <typename T>
 bool KRun<T>::persistent_ok() const {
-  if constexpr (std::is_same<T, bf16>::value) {
+  if constexpr (std::is_same<T, bf16>::value || std::is_same<T, f32x2>::value) {
     return false;
   } else {
     // Opt-in: measured on GB300 (2D Laplacian 64^2, FP64) it issues as fast
@@ -366,7 +366,7 @@ bool KRun<T>::persistent_ok() const {
 
 template <typename T>
 int KRun<T>::issue_rest_persistent() {
-  if constexpr (std::is_same<T, bf16>::value) {
+  if constexpr (std::is_same<T, bf16>::value || std::is_same<T, f32x2>::value) {
     return LOGDET_EINVAL;
   } else {
     const int j = next_step();
@@ -410,6 +410,7 @@ int KRun<T>::issue_rest_persistent() {
 template struct KRun<double>;
 template struct KRun<float>;
 template struct KRun<bf16>;
+template struct KRun<f32x2>;
 
 // ---------------------------------------------------------------------------
 // batched launches
@@ -477,9 +478,11 @@ int launch_update_jobs(const std::vector<UpdJob<T>>& jobs, int threads, cudaStre
 template int launch_spmm_jobs<double>(const std::vector<SpmmJob<double>>&, int, cudaStream_t);
 template int launch_spmm_jobs<float>(const std::vector<SpmmJob<float>>&, int, cudaStream_t);
 template int launch_spmm_jobs<bf16>(const std::vector<SpmmJob<bf16>>&, int, cudaStream_t);
+template int launch_spmm_jobs<f32x2>(const std::vector<SpmmJob<f32x2>>&, int, cudaStream_t);
 template int launch_update_jobs<double>(const std::vector<UpdJob<double>>&, int, cudaStream_t);
 template int launch_update_jobs<float>(const std::vector<UpdJob<float>>&, int, cudaStream_t);
 template int launch_update_jobs<bf16>(const std::vector<UpdJob<bf16>>&, int, cudaStream_t);
+template int launch_update_jobs<f32x2>(const std::vector<UpdJob<f32x2>>&, int, cudaStream_t);
 
 int launch_scalar_jobs(const std::vector<ScalarJob>& jobs, const std::vector<int>& widths, int kind,
                        cudaStream_t s) {
@@ -797,7 +800,12 @@ struct Solve : ISolve {
   }
   int krylov_threads() const override { return run ? run->g.threads : 0; }
   bool is_fp32() const override { return !std::is_same<T, double>::value; }
-  int elem_kind() const override { return std::is_same<T, double>::value ? 0 : std::is_same<T, float>::value ? 1 : 2; }
+  int elem_kind() const override {
+    return std::is_same<T, double>::value  ? 0
+           : std::is_same<T, float>::value ? 1
+           : std::is_same<T, bf16>::value  ? 2
+                                           : 3;
+  }
   cudaEvent_t done_event() const override { return ev_done; }
   size_t bytes_estimate() const override { return estimate_solve_bytes(h, c); }
 
@@ -897,8 +905,13 @@ struct Solve : ISolve {
     const double cscale = c.method == 0 ? alpha : gamma;
     if (h->kind == 1) {
       // Gridded operator: the table of W / c replaces the scaled CSR values.
-      LD_TRY(gtabs.alloc(grid_table_count(h)));
-      LD_TRY(grid_table<typename Compute<T>::type>(h, cscale, gtabs.p, st));
+      if constexpr (std::is_same<T, f32x2>::value) {
+        set_error("gridded operators support FP64 and mixed FP32 blocks only");
+        return LOGDET_EINVAL;
+      } else {
+        LD_TRY(gtabs.alloc(grid_table_count(h)));
+        LD_TRY(grid_table<typename Compute<T>::type>(h, cscale, gtabs.p, st));
+      }
     } else {
       LD_TRY(vals.alloc(h->nnz));
       LD_TRY(scaled_values<typename ValOf<T>::type>(h, cscale, vals.p, st));
@@ -941,7 +954,7 @@ struct Solve : ISolve {
       LD_TRY(S.alloc((size_t)n * lds));
       LD_TRY(Yt.alloc((size_t)n * lds));
       LD_TRY(probe_fill<T>(probe_key(c.seed, 0), n, s, 0, S.p, lds, st, c.gaussian, dkey(0)));
-      if constexpr (std::is_same<T, bf16>::value) {
+      if constexpr (std::is_same<T, bf16>::value || std::is_same<T, f32x2>::value) {
         LD_TRY(spmm_block<T>(h->rowptr, h->colind, vals.p, n, S.p, Yt.p, lds, st, cshift.p, h));
       } else {
         if (h->kind == 1) LD_TRY(grid_apply<T>(h, gtabs.p, S.p, Yt.p, lds, cshift.p, st));
@@ -1182,17 +1195,18 @@ struct Solve : ISolve {
 };
 
 size_t estimate_solve_bytes(const logdet_ctx* h, const SolveCfg& c) {
-  const bool f32 = c.precision != LOGDET_FP64;
+  const bool f32 = c.precision != LOGDET_FP64;  // FP32 matrix values
   const bool b16 = c.precision == LOGDET_MIXED_BF16VEC;
-  const size_t es = b16 ? 2 : f32 ? 4 : 8;
-  const int vec = f32 ? 4 : 2;  // Vec16<T>::N (BF16 blocks use 8-byte vectors)
+  const bool df = c.precision == LOGDET_MIXED_F32X2;
+  const size_t es = b16 ? 2 : (f32 && !df) ? 4 : 8;
+  const int vec = precision_vec(c.precision);
   const size_t n = h->n;
   const int s = c.plain ? 0 : c.P / 3, r = c.plain ? c.P : c.P - 2 * s, b = s + r;
   const size_t ld = round_up(b, vec), lds = std::max(round_up(s, vec), vec);
   const int m = c.m, k = c.method == 0 ? 2 : std::min(c.k, c.m);
   // Scaled values, plus (FP32 blocks of a grid stencil) the values per row
   // and diagonal of the sweep paths.
-  const bool sweep_vals = f32 && !b16 && h->kind == 0 && h->dia.ndiag > 0 && h->dia_slot;
+  const bool sweep_vals = f32 && !b16 && !df && h->kind == 0 && h->dia.ndiag > 0 && h->dia_slot;
   const size_t vals = (h->kind == 1 ? grid_table_count(h) * 8 : (size_t)h->nnz * (f32 ? 4 : 8)) +
                       (sweep_vals ? (size_t)dia_pad(h->dia.ndiag) * n * 4 : 0);
   const TileGeom g = tile_geom((int)ld, vec, 0, 0, (int)n);
@@ -1221,6 +1235,7 @@ std::unique_ptr<ISolve> make_solve(logdet_ctx* h, const SolveCfg& c, cudaStream_
   if (*rc) return nullptr;
   if (c.precision == LOGDET_FP64) return std::unique_ptr<ISolve>(new Solve<double>(h, c, st));
   if (c.precision == LOGDET_MIXED_BF16VEC) return std::unique_ptr<ISolve>(new Solve<bf16>(h, c, st));
+  if (c.precision == LOGDET_MIXED_F32X2) return std::unique_ptr<ISolve>(new Solve<f32x2>(h, c, st));
   return std::unique_ptr<ISolve>(new Solve<float>(h, c, st));
 }
 
@@ -1457,7 +1472,7 @@ int shift_runs(logdet_ctx* h, const std::vector<SolveCfg>& cfgs,
   // solves' device memory) at most 85 % of the device's memory.  The split
   // depends only on the shapes and the device, so results do not depend on
   // what else is allocated.
-  const int vec = cfgs[0].precision == LOGDET_FP64 ? 2 : 4;
+  const int vec = precision_vec(cfgs[0].precision);
   const int s = cfgs[0].plain ? 0 : cfgs[0].P / 3, r = cfgs[0].plain ? cfgs[0].P : cfgs[0].P - 2 * s;
   const int width = std::max(round_up(s + r, vec), std::max(round_up(s, vec), vec));
   size_t free_b = 0, total_b = 0;
@@ -1483,6 +1498,8 @@ std::unique_ptr<ISolve> make_group_solve(logdet_ctx* h, const std::vector<SolveC
     return std::unique_ptr<ISolve>(new GroupSolve<double>(h, cfgs, st));
   if (cfgs[0].precision == LOGDET_MIXED_BF16VEC)
     return std::unique_ptr<ISolve>(new GroupSolve<bf16>(h, cfgs, st));
+  if (cfgs[0].precision == LOGDET_MIXED_F32X2)
+    return std::unique_ptr<ISolve>(new GroupSolve<f32x2>(h, cfgs, st));
   return std::unique_ptr<ISolve>(new GroupSolve<float>(h, cfgs, st));
 }
 
@@ -1497,6 +1514,7 @@ int solve_shifts(logdet_ctx* h, const std::vector<SolveCfg>& cfgs, cudaStream_t 
     int rc;
     if (cfgs[0].precision == LOGDET_FP64) rc = solve_shifts_t<double>(h, part, st, po);
     else if (cfgs[0].precision == LOGDET_MIXED_BF16VEC) rc = solve_shifts_t<bf16>(h, part, st, po);
+    else if (cfgs[0].precision == LOGDET_MIXED_F32X2) rc = solve_shifts_t<f32x2>(h, part, st, po);
     else rc = solve_shifts_t<float>(h, part, st, po);
     if (rc) {
       cudaStreamSynchronize(st);
@@ -1521,16 +1539,28 @@ int solve_blocking(logdet_ctx* h, const SolveCfg& c, cudaStream_t st, SolveOut& 
   return sv->assemble(o);
 }
 
+// One Krylov step of a solve whose blocks hold T: pass 1, its scalar
+// kernel, then (where the step has one) pass 2 and its scalar kernel.
+template <typename T>
+static int issue_step_t(ISolve* sv, int th, cudaStream_t st) {
+  thread_local std::vector<SpmmJob<T>> sp;
+  thread_local std::vector<UpdJob<T>> up;
+  thread_local std::vector<ScalarJob> sj;
+  thread_local std::vector<int> widths;
+  sp.clear(); up.clear(); sj.clear(); widths.clear();
+  LD_TRY(sv->add_pass1(&sp, sj, widths));
+  LD_TRY(launch_spmm_jobs<T>(sp, th, st));
+  LD_TRY(launch_scalar_jobs(sj, widths, SK_COEF, st));
+  sj.clear(); widths.clear();
+  if (sv->add_pass2(&up, sj, widths)) {
+    LD_TRY(launch_update_jobs<T>(up, th, st));
+    LD_TRY(launch_scalar_jobs(sj, widths, SK_NORM, st));
+  }
+  return LOGDET_OK;
+}
+
 int issue_solve(ISolve* sv, cudaStream_t st) {
   int rc = LOGDET_OK;
-  std::vector<SpmmJob<double>> sd;
-  std::vector<SpmmJob<float>> sf;
-  std::vector<SpmmJob<bf16>> sb;
-  std::vector<UpdJob<double>> ud;
-  std::vector<UpdJob<float>> uf;
-  std::vector<UpdJob<bf16>> ub;
-  std::vector<ScalarJob> sj;
-  std::vector<int> widths;
   while (sv->phase() != PH_WAIT) {
     if (sv->phase() == PH_FAILED) return rc ? rc : LOGDET_ECUDA;
     if (!sv->in_krylov()) {
@@ -1546,19 +1576,11 @@ int issue_solve(ISolve* sv, cudaStream_t st) {
     }
     NvtxRange nv("logdet krylov step");
     const int th = sv->krylov_threads();
-    const int ek = sv->elem_kind();
-    sd.clear(); sf.clear(); sb.clear(); ud.clear(); uf.clear(); ub.clear(); sj.clear(); widths.clear();
-    LD_TRY(sv->add_pass1(ek == 0 ? (void*)&sd : ek == 1 ? (void*)&sf : (void*)&sb, sj, widths));
-    if (ek == 0) LD_TRY(launch_spmm_jobs<double>(sd, th, st));
-    else if (ek == 1) LD_TRY(launch_spmm_jobs<float>(sf, th, st));
-    else LD_TRY(launch_spmm_jobs<bf16>(sb, th, st));
-    LD_TRY(launch_scalar_jobs(sj, widths, SK_COEF, st));
-    sj.clear(); widths.clear();
-    if (sv->add_pass2(ek == 0 ? (void*)&ud : ek == 1 ? (void*)&uf : (void*)&ub, sj, widths)) {
-      if (ek == 0) LD_TRY(launch_update_jobs<double>(ud, th, st));
-      else if (ek == 1) LD_TRY(launch_update_jobs<float>(uf, th, st));
-      else LD_TRY(launch_update_jobs<bf16>(ub, th, st));
-      LD_TRY(launch_scalar_jobs(sj, widths, SK_NORM, st));
+    switch (sv->elem_kind()) {
+      case 0: LD_TRY(issue_step_t<double>(sv, th, st)); break;
+      case 1: LD_TRY(issue_step_t<float>(sv, th, st)); break;
+      case 2: LD_TRY(issue_step_t<bf16>(sv, th, st)); break;
+      default: LD_TRY(issue_step_t<f32x2>(sv, th, st)); break;
     }
     sv->step_issued();
   }

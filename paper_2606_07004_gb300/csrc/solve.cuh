@@ -48,6 +48,11 @@ struct SolveOut {
 };
 
 int validate_cfg(const logdet_ctx* h, const SolveCfg& c);
+// Block entries per 16-byte vector for a precision (Vec16<T>::N of its
+// block type): two for FP64 and double-float blocks, four for FP32 and BF16.
+inline int precision_vec(int precision) {
+  return (precision == LOGDET_FP64 || precision == LOGDET_MIXED_F32X2) ? 2 : 4;
+}
 void spectral_bounds(const logdet_ctx* h, const SolveCfg& c, double& lo, double& hi);
 
 // Device arrays of one Krylov run (see KrylovState).
@@ -66,6 +71,7 @@ template <typename T> constexpr double rescale_limit();
 template <> constexpr double rescale_limit<double>() { return 200.0; }
 template <> constexpr double rescale_limit<float>() { return 20.0; }
 template <> constexpr double rescale_limit<bf16>() { return 20.0; }
+template <> constexpr double rescale_limit<f32x2>() { return 20.0; }
 
 // One Krylov run over a block X0 (n x ld, b live columns): method 0 is
 // three-term Lanczos, method 1 IOP with window k.  With Vfull the basis is
@@ -158,7 +164,7 @@ struct ISolve {
   virtual bool in_krylov() const = 0;
   virtual int krylov_threads() const = 0;
   virtual bool is_fp32() const = 0;
-  virtual int elem_kind() const = 0;  // 0 FP64, 1 FP32, 2 BF16 vectors
+  virtual int elem_kind() const = 0;  // 0 FP64, 1 FP32, 2 BF16, 3 double-float vectors
   // Run the current non-Krylov phase (SETUP, MID, FINISH) and move on.
   virtual int run_phase() = 0;
   // Krylov step: append this solve's pass-1 job etc. for its next step.

@@ -83,7 +83,8 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
                      h->dia_slot != nullptr;
   const int kind = std::is_same<T, double>::value ? 0
                    : std::is_same<T, float>::value ? (sw_ok ? 3 : 1)
-                                                   : 2;
+                   : std::is_same<T, bf16>::value  ? 2
+                                                   : 4;
   const Key key(kind, ld, n, nnz, sm_count(), ndots, nbasis, extra);
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -253,6 +254,8 @@ template int autotune_krylov<float>(logdet_ctx*, const float*, int, int, int, in
                                     TuneCfg*);
 template int autotune_krylov<bf16>(logdet_ctx*, const float*, int, int, int, int, cudaStream_t,
                                     TuneCfg*);
+template int autotune_krylov<f32x2>(logdet_ctx*, const float*, int, int, int, int, cudaStream_t,
+                                     TuneCfg*);
 
 }  // namespace ld
 

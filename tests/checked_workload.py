@@ -1,8 +1,9 @@
 """Workload run by test_gpu_checked.py in a subprocess, once against the
 library named by LOGDET_LIB (the checked build) and once against the normal
-build: every kind of solve on small inputs (FP64 and mixed FP32, OSLQ and
-OSA-IOP, uniform tiles and work items of an irregular graph, the line and
-plane sweeps, a shift group, graph plans, the server with a suspension).
+build: every kind of solve on small inputs (FP64, mixed FP32 and double-float
+vectors, OSLQ and OSA-IOP, uniform tiles and work items of an irregular
+graph, the line and plane sweeps, shift groups, graph plans, the server with
+a suspension).
 Prints one JSON line: the results (repr of each estimate, so that the two
 builds can be compared bit for bit) and the checked build's report."""
 import json
@@ -34,6 +35,9 @@ def main():
                                                                      iop_window=2, seed0=3)]
         with B.Plan(h, B.METHOD_OSLQ, 30, 20) as p:
             out["lap3_plan"] = repr(p.run(1).logdet)
+        out["lap3_oslq_df"] = repr(h.oslq(30, 20, seed=1, precision=B.MIXED_F32X2).logdet)
+        out["lap3_group_df"] = [repr(r.logdet) for r in h.oslq_shifts([0.0, 0.3], 24, 12, seed0=3,
+                                                                      precision=B.MIXED_F32X2)]
     with B.Handle.from_csr(mat) as h:
         out["matern_oslq_mixed"] = repr(h.oslq(36, 20, seed=2, precision=B.MIXED_FP32).logdet)
     with B.Handle.from_csr(lap3f) as h:
@@ -42,6 +46,8 @@ def main():
     with B.Handle.from_csr(graph) as h:
         out["graph_iop4"] = repr(h.osaiop(24, 20, iop_window=4, seed=5).logdet)
         out["graph_oslq_mixed"] = repr(h.oslq(24, 20, seed=5, precision=B.MIXED_FP32).logdet)
+        out["graph_iop4_df"] = repr(h.osaiop(24, 20, iop_window=4, seed=5,
+                                             precision=B.MIXED_F32X2).logdet)
         with B.Server(8 << 30, max_slots=4) as srv:
             a = srv.submit(h, B.METHOD_OSAIOP, 24, 120, 4, seed=6)
             b = srv.submit(h, B.METHOD_OSLQ, 24, 60, seed=7, precision=B.MIXED_FP32)

@@ -103,6 +103,8 @@ def test_grid_invalid_arguments():
     with B.Handle.grid(10, 10, T) as h:
         with pytest.raises(B.LogdetError):
             h.oslq(9, 5, precision=B.MIXED_BF16VEC)
+        with pytest.raises(B.LogdetError):
+            h.osaiop(9, 5, precision=B.MIXED_F32X2)
 
 
 def test_quadform_csr_and_grid():

@@ -43,6 +43,8 @@ REQS = [  # (matrix, method, probes, m, k, seed, precision)
     ("graph", B.METHOD_OSAIOP, 24, 18, 4, 3, B.FP64),
     ("l3d", B.METHOD_OSLQ, 30, 12, 0, 4, B.MIXED_FP32),
     ("l2d", B.METHOD_OSAIOP, 33, 15, 8, 5, B.MIXED_FP32),
+    ("graph", B.METHOD_OSLQ, 24, 20, 0, 6, B.MIXED_F32X2),
+    ("mat", B.METHOD_OSAIOP, 21, 16, 4, 7, B.MIXED_F32X2),
 ]
 
 

@@ -46,7 +46,7 @@ def _group(h, method, shifts, P, m, k, seed0, **kw):
 
 
 @pytest.mark.parametrize("method,k", [(0, 0), (1, 2), (1, 4)])
-@pytest.mark.parametrize("precision", [B.FP64, B.MIXED_FP32, B.MIXED_BF16VEC])
+@pytest.mark.parametrize("precision", [B.FP64, B.MIXED_FP32, B.MIXED_BF16VEC, B.MIXED_F32X2])
 @pytest.mark.parametrize("plain", [0, 1])
 def test_group_of_one_is_the_ordinary_solve(method, k, precision, plain):
     A = W.laplacian_2d(61, 47, shift=0.0)
