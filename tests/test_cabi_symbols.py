@@ -52,3 +52,25 @@ def test_error_strings_without_gpu(lib_path):
     from paper_2606_07004_gb300 import binding as B
     assert B._lib.logdet_strerror(B.EINVAL) == b"invalid argument"
     assert B._lib.logdet_strerror(B.OK) == b"ok"
+
+
+def header_constants():
+    """Integer #defines of the header: LOGDET_<NAME> -> value."""
+    out = {}
+    for name, val in re.findall(r"^#define LOGDET_([A-Z0-9_]+)\s+\(?(-?(?:0x)?[0-9A-Fa-f]+)u?\)?",
+                                open(HEADER).read(), flags=re.M):
+        out[name] = int(val, 0)
+    return out
+
+
+def test_binding_constants_match_the_header(lib_path):
+    # every constant the binding mirrors (the header's name without the
+    # LOGDET_ prefix) has the header's value
+    from paper_2606_07004_gb300 import binding as B
+    consts = header_constants()
+    for must in ("FP64", "MIXED_FP32", "MIXED_BF16VEC", "MIXED_F32X2", "METHOD_OSLQ",
+                 "METHOD_OSAIOP", "EINVAL", "ST_BREAKDOWN"):
+        assert must in consts and hasattr(B, must), must
+    for name, val in consts.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == val, name
