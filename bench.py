@@ -876,8 +876,10 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     errs = {t: abs(batched[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
     gerrs = {t: abs(group[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
     # The configuration at the 1e-4 budget: FP64 vectors as a shift group
-    # (two runs of 4: eight FP64 phase-1 bases do not fit the device).
-    h.osaiop_shifts(shifts, P, 10, iop_window=k, seed0=0, autotune=autotune)  # tunes its widths
+    # (two runs of 4: eight FP64 phase-1 bases do not fit the device).  The
+    # warm-up is the full group: a short one (m = 10) fits in one run of 8,
+    # so the layouts of the runs of 4 would be tuned inside the timed call.
+    h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, autotune=autotune)
     clocks64 = ClockSampler(torch.cuda.current_device(), "irregular_fp64")
     clocks64.start()
     torch.cuda.synchronize()
@@ -888,8 +890,8 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     g64errs = {t: abs(group64[t].logdet - r64[t].logdet) / abs(r64[t].logdet) for t in which}
     # Double-float vectors (FP32 values, vectors as hi + lo float pairs):
     # the same group, for the 1e-4 budget at FP32-pipe arithmetic.
-    h.osaiop_shifts(shifts, P, 10, iop_window=k, seed0=0, precision=B.MIXED_F32X2,
-                    autotune=autotune)
+    h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, precision=B.MIXED_F32X2,
+                    autotune=autotune)  # the full group as warm-up, as for FP64
     clocksdf = ClockSampler(torch.cuda.current_device(), "irregular_f32x2")
     clocksdf.start()
     torch.cuda.synchronize()
