@@ -22,8 +22,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 namespace ld {
 
@@ -114,7 +116,12 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
     *out = TuneCfg();
     return LOGDET_OK;
   }
-  // Scratch: three blocks, partials for the deepest geometry, coefficients.
+  // Scratch: x (the pass-1 input), y (its output), z (the update's output),
+  // partials for the deepest geometry, coefficients, and the other vectors of
+  // the window as blocks of their own, so that the timed passes read as many
+  // distinct blocks as a Krylov step does (with the window's vectors aliased
+  // to x they hit in L2 where a real step streams them from HBM).  Where
+  // free memory is short the window's vectors share x.
   const size_t blk = (size_t)n * ld;
   DevBuf<T> x(st), y(st), z(st);
   DevBuf<Part> part(st);
@@ -122,6 +129,28 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
   LD_TRY(x.alloc(blk));
   LD_TRY(y.alloc(blk));
   LD_TRY(z.alloc(blk));
+  const int nw = std::max(ndots, nbasis);  // window vectors, x the last
+  std::vector<std::unique_ptr<DevBuf<T>>> win;
+  {
+    size_t free_b = 0, total_b = 0;
+    LD_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const size_t want = (size_t)(nw - 1) * blk * sizeof(T);
+    if (2 * want <= free_b) {
+      for (int i = 0; i + 1 < nw; ++i) {
+        win.emplace_back(new DevBuf<T>(st));
+        if (win.back()->alloc(blk) != LOGDET_OK) {
+          win.pop_back();
+          break;
+        }
+        LD_TRY(probe_fill<T>(probe_key(12345, 8 + i), n, ld, 0, win.back()->p, ld, st));
+      }
+    }
+  }
+  // Window vector i of nw (i = nw - 1 is x).
+  auto wv = [&](int i) -> const T* {
+    const int back = nw - 1 - i;
+    return (back == 0 || back > (int)win.size()) ? x.p : win[back - 1]->p;
+  };
   int max_slots = 1;
   for (auto& c : cands) {
     TileGeom g = tile_geom(ld / c.split, V, c.threads, c.iters);
@@ -174,7 +203,7 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
       J.x = x.p;
       J.y = y.p;
       J.ndots = ndots;
-      for (int d = 0; d < ndots; ++d) J.dotv[d] = (d & 1) ? z.p : x.p;
+      for (int d = 0; d < ndots; ++d) J.dotv[d] = wv(nw - ndots + d);
       J.part = part.p;
       J.n = n;
       J.ld = ld;
@@ -206,8 +235,8 @@ int autotune_krylov(logdet_ctx* h, const typename ValOf<T>::type* vals, int ld, 
       memset(&U, 0, sizeof U);
       U.y = y.p;
       U.nbasis = nbasis;
-      for (int i = 0; i < nbasis; ++i) U.basis[i] = (i & 1) ? y.p : x.p;
-      U.extra = extra ? x.p : nullptr;
+      for (int i = 0; i < nbasis; ++i) U.basis[i] = wv(nw - nbasis + i);
+      U.extra = extra ? wv(0) : nullptr;
       U.coef = coef.p;
       U.ycoef = ycoef.p;
       U.out = z.p;
