@@ -62,6 +62,7 @@ TileGeom tile_geom(int width, int vec, int threads_hint, int iters_hint, int n) 
 // capacity away from the gathers of x.
 // ---------------------------------------------------------------------------
 constexpr int kGather = 4;
+constexpr int kPrefetch = 8;  // entries of a row whose x rows are prefetched
 
 // Checked builds (LOGDET_CHECKED): bounds checks on the indices the passes
 // take from memory -- work-item rows and slots, row ranges from rowptr,
@@ -105,6 +106,11 @@ __device__ __forceinline__ void chk_range(int&, int&, long long) {}
 __device__ __forceinline__ int chk_slot(int t, int) { return t; }
 __device__ __forceinline__ void chk_item(int&, int&, bool, int) {}
 #endif
+
+// L2 prefetch of the 16-byte-aligned chunk at p (no register, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.L2 [%0];" ::"l"(p));
+}
 
 // Programmatic dependent launch of the step kernels: a step kernel may be
 // launched while its predecessor in the stream still runs (its CTAs get
@@ -309,6 +315,23 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           q0 = __ldg(J.rowptr + row);
           q1 = __ldg(J.rowptr + row + 1);
           chk_range(q0, q1, J.nnz);
+        }
+        // Latency-bound blocks: the x rows of the row's first kPrefetch
+        // entries, and the row of each window vector, are requested into L2
+        // in one wave before the row's own loads (one round trip for their
+        // indices).  The gathers that follow, one batch and then the tail
+        // one entry at a time, and the dot loads then wait for DRAM once per
+        // row instead of once per batch and per tail entry (most rows of a
+        // power-law graph are shorter than a batch).  The arithmetic is
+        // unchanged.
+        if constexpr (narrow_block<T>()) {
+#pragma unroll
+          for (int u = 0; u < kPrefetch; ++u) {
+            if (q0 + u < q1) prefetch_l2(xcol + (size_t)chk_col(__ldg(J.colind + q0 + u), J.n) * J.ld);
+          }
+#pragma unroll
+          for (int d = 0; d < NDOT; ++d)
+            if (d < ndots) prefetch_l2(J.dotv[d] + (size_t)row * J.ld + col0);
         }
         // FP32 / BF16 blocks with two window dots: the row's window vectors
         // are requested before its gathers, so their latency overlaps them
