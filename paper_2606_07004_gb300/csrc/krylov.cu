@@ -167,7 +167,10 @@ constexpr int fp64_wide_min_ctas() { return (std::is_same<T, double>::value && N
 // Pass 1 over the tiles (or work items) gt0, gt0 + stride, ... of a batch,
 // each by the whole CTA; the dynamic shared memory holds blockDim.x * V
 // accumulators.  Batch: SpmmBatch or any type with the same members.
-template <typename T, int NDOT, typename Batch, bool COH = false>
+// PF: the row-start L2 prefetch below (always for FP32, BF16 and
+// double-float blocks; for FP64 blocks an instance of its own, launched for
+// matrices cut into work items).
+template <typename T, int NDOT, typename Batch, bool COH = false, bool PF = narrow_block<T>()>
 __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
                                            unsigned char* smem_raw) {
   constexpr int V = Vec16<T>::N;
@@ -322,9 +325,13 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
         // indices).  The gathers that follow, one batch and then the tail
         // one entry at a time, and the dot loads then wait for DRAM once per
         // row instead of once per batch and per tail entry (most rows of a
-        // power-law graph are shorter than a batch).  The arithmetic is
+        // power-law graph are shorter than a batch).  FP64 blocks, bound by
+        // the FP64 pipe on regular matrices, prefetch only for matrices cut
+        // into work items (irregular rows), whose pass waits on loads too;
+        // as a runtime switch the prefetch cost the single-dot FP64 instance
+        // a spill, so it is an instance of its own.  The arithmetic is
         // unchanged.
-        if constexpr (narrow_block<T>()) {
+        if constexpr (PF) {
 #pragma unroll
           for (int u = 0; u < kPrefetch; ++u) {
             if (q0 + u < q1) prefetch_l2(xcol + (size_t)chk_col(__ldg(J.colind + q0 + u), J.n) * J.ld);
@@ -455,12 +462,12 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
   }
 }
 
-template <typename T, int NDOT>
+template <typename T, int NDOT, bool PF>
 __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
     k_spmm(const __grid_constant__ SpmmBatch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_entry();
-  spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
+  spmm_tiles<T, NDOT, SpmmBatch<T>, false, PF>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // FP32 / BF16 blocks: the pass is bound by the latency of its dependent
@@ -489,9 +496,11 @@ __global__ void __maxnreg__((lo_spmm_regs<T, NDOT>()))
   spmm_tiles<T, NDOT>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
-template <typename T, int NDOT>
+// PF: matrices cut into work items (FP64 blocks take the prefetching
+// instance there; the other block types always prefetch).
+template <typename T, int NDOT, bool PF>
 constexpr auto spmm_kernel() {
-  if constexpr (!narrow_block<T>()) return k_spmm<T, NDOT>;
+  if constexpr (!narrow_block<T>()) return k_spmm<T, NDOT, PF>;
   else return k_spmm_lo<T, NDOT>;
 }
 
@@ -1278,7 +1287,11 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 template <typename T>
 int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   int nd = 0;
-  for (int j = 0; j < b.njobs; ++j) nd = std::max(nd, b.jobs[j].ndots);
+  bool items = false;
+  for (int j = 0; j < b.njobs; ++j) {
+    nd = std::max(nd, b.jobs[j].ndots);
+    items = items || b.jobs[j].items != nullptr;
+  }
   using Acc = typename AccOf<T>::type;
   size_t smem = (size_t)threads * Vec16<T>::N * sizeof(Acc);
   double flops = 0.0, bytes = 0.0;
@@ -1293,7 +1306,7 @@ int launch_spmm(const SpmmBatch<T>& b, int threads, cudaStream_t s) {
   ProfScope prof(KC_SPMM, s, flops, bytes);
 #define LD_SPMM_CASE(ND)                                                      \
   {                                                                           \
-    auto kern = spmm_kernel<T, ND>();                                         \
+    auto kern = items ? spmm_kernel<T, ND, true>() : spmm_kernel<T, ND, false>(); \
     int grid = persistent_grid(kern, threads, smem, b.total_tiles);           \
     launch_pdl(kern, dim3(grid), dim3(threads), smem, s, b);                  \
     break;                                                                    \
