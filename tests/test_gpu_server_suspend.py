@@ -43,10 +43,11 @@ def _until(srv, key, value, timeout=30.0):
     (B.METHOD_OSLQ, 0, B.FP64),
     (B.METHOD_OSAIOP, 4, B.FP64),          # phase-1 basis, window ring, Hessenberg state
     (B.METHOD_OSAIOP, 2, B.MIXED_FP32),    # line sweep of a grid stencil
+    (B.METHOD_OSAIOP, 4, B.MIXED_F32X2),   # double-float blocks
 ])
 def test_suspend_mid_krylov_resume_is_bit_identical(method, k, precision):
-    A = (W.laplacian_3d(96, shift=0.01) if precision == B.FP64
-         else W.matern_2d(512, 0.05, dtype=np.float32))
+    A = (W.matern_2d(512, 0.05, dtype=np.float32) if precision == B.MIXED_FP32
+         else W.laplacian_3d(96, shift=0.01))
     P, m = 60, 120
     with B.Handle.from_csr(A) as h:
         ref = (h.oslq(P, m, seed=4, precision=precision) if method == B.METHOD_OSLQ
