@@ -839,9 +839,11 @@ def multishift_measure(budget_gb: float, autotune: int, fp64_all: bool = True) -
     clocks.start()
     # The same 8 solves as one shift group: one Krylov run over all 8 x 64
     # probe columns, so each gather fetches the x row of every shift.  Timed
-    # first, after a short group that tunes its block widths: it grows the
-    # memory pool that the server and the serial solves then reuse.
-    h.osaiop_shifts(shifts, P, 10, iop_window=k, seed0=0, precision=B.MIXED_FP32,
+    # first, after one untimed group of the same size: it tunes the block
+    # widths and grows the memory pool to the group's working set (a short
+    # warm-up group left the timed one paying for the pool's growth), which
+    # the server and the serial solves then reuse.
+    h.osaiop_shifts(shifts, P, m, iop_window=k, seed0=0, precision=B.MIXED_FP32,
                     autotune=autotune)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
