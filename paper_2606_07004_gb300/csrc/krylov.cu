@@ -149,11 +149,6 @@ __device__ __forceinline__ void load_v(const T* p, typename Compute<T>::type (&v
   }
 }
 
-// FP64 instances with the full dot window hold two CTAs per SM: at 85
-// registers one 480-thread CTA fit, and the update pass of OSA-IOP k = 8
-// then ran at half the FP64 and HBM peaks (a few spilled registers cost
-// less than the second CTA gains).  0 leaves every other instance's
-// register choice to the compiler, as without the hint.
 // Blocks whose passes are bound by memory latency and computed on the FP32
 // pipe (FP32, BF16 and double-float entries: a double-float thread holds two
 // entries where an FP32 one holds four, so their registers match); FP64
@@ -161,6 +156,11 @@ __device__ __forceinline__ void load_v(const T* p, typename Compute<T>::type (&v
 template <typename T>
 constexpr bool narrow_block() { return !std::is_same<T, double>::value; }
 
+// FP64 instances with the full dot window hold two CTAs per SM: at 85
+// registers one 480-thread CTA fit, and the update pass of OSA-IOP k = 8
+// then ran at half the FP64 and HBM peaks (a few spilled registers cost
+// less than the second CTA gains).  0 leaves every other instance's
+// register choice to the compiler, as without the hint.
 template <typename T, int N>
 constexpr int fp64_wide_min_ctas() { return (std::is_same<T, double>::value && N >= kMaxWin) ? 2 : 0; }
 
@@ -278,17 +278,18 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
         }
       }
     } else if (live) {
-      // FP32 / BF16 blocks with at most one dot (memory-latency bound, and
-      // with registers to spare) are software pipelined: the next row's range
-      // and the next batch's column indices are requested before the current
-      // gathers are consumed, one round trip per batch instead of two
-      // (measured 39.3 -> 32.7 ms per Matérn solve).  With more dots, or
+      // FP32, BF16 and double-float blocks with at most one dot
+      // (memory-latency bound, and with registers to spare) are software
+      // pipelined: the next row's range and the next batch's column indices
+      // are requested before the current gathers are consumed, one round
+      // trip per batch instead of two (measured 39.3 -> 32.7 ms per Matérn
+      // solve).  With more dots, or
       // FP64, the extra registers cost more occupancy than the overlap gains
       // (power-law graph, four dots: 435 -> 720 ms per solve).  The
       // accumulation order is the same either way.
       constexpr bool kPipe = narrow_block<T>() && NDOT <= 1;
       const T* xcol = J.x + col0;
-      // FP32 / BF16: the thread's column shift and scale converted from
+      // Other than FP64: the thread's column shift and scale converted from
       // FP64 once per tile, not once per row (the conversion runs on the
       // FP64 pipe: per row it kept that pipe 21-31 % busy).
       CT csh[V], csc[V];
@@ -340,9 +341,9 @@ __device__ __forceinline__ void spmm_tiles(const Batch& B, int gt0, int stride,
           for (int d = 0; d < NDOT; ++d)
             if (d < ndots) prefetch_l2(J.dotv[d] + (size_t)row * J.ld + col0);
         }
-        // FP32 / BF16 blocks with two window dots: the row's window vectors
-        // are requested before its gathers, so their latency overlaps them
-        // (the dot products keep their order).  Measured on the 2M-row
+        // FP32, BF16 and double-float blocks with two window dots: the row's
+        // window vectors are requested before its gathers, so their latency
+        // overlaps them (the dot products keep their order).  Measured on the 2M-row
         // power-law graph (OSA-IOP k = 2, m = 100): SpMM 334 -> 295 ms per
         // solve.  The instance for up to four dots keeps late loads: early
         // loads of all four cost the second CTA per SM (428 -> 666 ms), and
@@ -470,8 +471,8 @@ __global__ void __launch_bounds__(512, fp64_wide_min_ctas<T, NDOT>())
   spmm_tiles<T, NDOT, SpmmBatch<T>, false, PF>(B, blockIdx.x, gridDim.x, smem_raw);
 }
 
-// FP32 / BF16 blocks: the pass is bound by the latency of its dependent
-// loads (row range -> column indices -> gathers of x), so resident warps
+// FP32, BF16 and double-float blocks: the pass is bound by the latency of
+// its dependent loads (row range -> column indices -> gathers of x), so resident warps
 // count for more than registers.  A register cap that fits three 352-thread
 // CTAs per SM instead of two (two instead of one for the full window)
 // trades a few spilled accumulators for 50% more loads in flight.  Measured
