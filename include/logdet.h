@@ -114,12 +114,14 @@ typedef struct {
                           g = sqrt(-2 log u1) cos(2 pi u2); 0 = Rademacher */
   int32_t block_width; /* probe columns per Krylov pass: each block of probes
                           (the s + r probes, and OSA-IOP's s sketch columns; both
-                          rounded up to a multiple of 2 columns for FP64, 4 for the
-                          mixed precisions) runs as slices of min(block_width, its
-                          columns) columns, one job per slice, with the default CTA
-                          size and tile depth.  0 = the default full-width block, or
-                          the autotuner's choice when autotune = 1.  A width that is
-                          not a multiple of 2 (FP64) / 4 (mixed), or that does not
+                          rounded up to a multiple of 2 columns for FP64 and
+                          LOGDET_MIXED_F32X2, 4 for FP32 and BF16 vectors) runs
+                          as slices of min(block_width, its columns) columns, one
+                          job per slice, with the default CTA size and tile
+                          depth.  0 = the default full-width block, or the
+                          autotuner's choice when autotune = 1.  A width that is
+                          not a multiple of 2 (FP64, F32X2) / 4 (FP32, BF16
+                          vectors), or that does not
                           divide a block's rounded column count, is EINVAL.  Ignored
                           for gridded operators.  Changes results at rounding level
                           only (the order of the fixed-order partial sums). */
@@ -160,7 +162,7 @@ int logdet_create_device(int32_t n, const int32_t* rowptr_dev, const int32_t* co
  * a nugget there).  The caller guarantees that Q is SPD.  The handle works
  * with every estimator, the server, plans and logdet_spmm (applied by a
  * convolution kernel, nothing n x stencil is stored); FP64 and mixed FP32
- * only (EINVAL for LOGDET_MIXED_BF16VEC).  logdet_info reports n = nx * ny
+ * only (EINVAL for LOGDET_MIXED_BF16VEC and LOGDET_MIXED_F32X2).  logdet_info reports n = nx * ny
  * and nnz = the entries of the implied matrix.  Errors: EINVAL (nx, ny < 1,
  * nx * ny >= 2^31, radius outside [0, 96], non-finite w), ENOTSPD
  * (Gershgorin upper bound <= 0), ENOMEM, ECUDA. */
@@ -246,7 +248,8 @@ int logdet_osaiop(logdet_handle h, int32_t num_probes, int32_t krylov_steps,
  * separate solve.  The shifts go through in consecutive runs of equal size
  * (the last one possibly smaller), as few as allow at most floor(1024 / w)
  * members per run (w: one member's block width, num_probes -
- * floor(num_probes/3) rounded up to 2 for FP64, 4 for FP32/BF16) and an
+ * floor(num_probes/3) rounded up to 2 for FP64 and double-float blocks, 4
+ * for FP32/BF16) and an
  * estimated device memory (logdet_estimate_bytes per member) within 85 % of
  * the device's; the split depends only on the shapes and the device.
  * Blocks until the results are on the host.  Errors: EINVAL (nshift < 1;
