@@ -17,9 +17,10 @@ vectors, OSLQ m = 80, 120 probes; solves/s, error against the FP64 CUDA path,
 HBM roofline of the Krylov passes), serving (the continuous-batching
 configuration at a reduced request count: mixed batched server against plain
 FP64 one at a time, solves/s and p50/p99 latency) and irregular_batch (8
-shifts of a 2M-row power-law graph Laplacian, OSA-IOP m = 100, k = 4: as one
-shift group, through the server and one after the other; error of the
-extreme shifts against FP64).
+shifts of a 2M-row power-law graph Laplacian, OSA-IOP m = 100, k = 4, FP32
+vectors: as one shift group, through the server and one after the other;
+error of the extreme shifts against FP64; then the forms within the 1e-4
+budget, the same group with FP64 vectors and with double-float vectors).
 
 Under torchrun every rank solves its own copy of the workload (independent
 problems, no data-path collective: weak scaling); the barrier and the max over
